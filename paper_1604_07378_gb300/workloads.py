@@ -1,0 +1,231 @@
+"""Seeded synthetic inputs: tetrahedral lattices, clamps, initial states, materials.
+
+This module generates inputs only.  It holds none of the solver's arithmetic
+(no energies, gradients, stiffness fits, matrices or solves), so the CPU oracle
+and the CUDA path can both draw their inputs from it without sharing any part
+of the method.
+
+Meshes are Kuhn subdivisions of a cube lattice: every cube is split into the six
+tetrahedra that share its main diagonal, one per ordering of the three axes.
+The paper's own meshes (Table 1) are not available; these lattices stand in for
+them with the same element type and comparable tets-per-vertex ratio (~5.6).
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# material kinds, same integer codes as the C header's sim_material_kind
+NEOHOOKEAN, STVK, SPLINE_VL, COROTATED, POLY4 = 0, 1, 2, 3, 4
+MATERIAL_NAMES = {NEOHOOKEAN: "neohookean", STVK: "stvk", SPLINE_VL: "spline",
+                  COROTATED: "corotated", POLY4: "poly4"}
+
+# knots of the synthetic spline materials (principal stretch for a, products for b, c)
+SPLINE_KNOTS = (0.3, 0.5, 0.7, 0.85, 1.0, 1.2, 1.6, 2.5)
+
+
+@dataclass
+class Material:
+    kind: int
+    E: float
+    nu: float
+    density: float = 1000.0
+    # spline control points, shape (3, 8, 3): function (a, b, c) x knot x (x, value, slope)
+    spline: np.ndarray | None = None
+
+    @property
+    def mu(self) -> float:
+        return self.E / (2.0 * (1.0 + self.nu))
+
+    @property
+    def lam(self) -> float:
+        return self.E * self.nu / ((1.0 + self.nu) * (1.0 - 2.0 * self.nu))
+
+
+@dataclass
+class Workload:
+    name: str
+    rest_pos: np.ndarray          # (n, 3) float64, rest positions X
+    tets: np.ndarray              # (T, 4) int32, positively oriented
+    clamped: np.ndarray           # (n,) uint8, 1 = position prescribed
+    q_cur: np.ndarray             # (n, 3) float64, state q_l
+    q_prev: np.ndarray            # (n, 3) float64, state q_{l-1}
+    material: Material
+    h: float = 1.0 / 30.0
+    gravity: tuple = (0.0, 0.0, -9.81)
+    iters: int = 10
+    history: int = 5
+    dims: tuple = ()
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_verts(self) -> int:
+        return self.rest_pos.shape[0]
+
+    @property
+    def n_tets(self) -> int:
+        return self.tets.shape[0]
+
+
+def kuhn_lattice(nx: int, ny: int, nz: int, edge: float = 0.05):
+    """Vertices and tets of an nx*ny*nz cube lattice, 6 tets per cube.
+
+    Vertex (i, j, k) has index i + (nx+1)*(j + (ny+1)*k).  Each tet walks from
+    the cube's low corner to its high corner along one ordering of the axes;
+    odd orderings swap their last two vertices so every tet is positively
+    oriented (orientation follows from the permutation's parity alone).
+    """
+    gi, gj, gk = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1),
+                             indexing="ij")
+    # order vertices by the index formula (k slowest)
+    pos = np.zeros(((nx + 1) * (ny + 1) * (nz + 1), 3))
+    vid = lambda i, j, k: i + (nx + 1) * (j + (ny + 1) * k)
+    ids = vid(gi, gj, gk)
+    pos[ids.ravel(), 0] = gi.ravel() * edge
+    pos[ids.ravel(), 1] = gj.ravel() * edge
+    pos[ids.ravel(), 2] = gk.ravel() * edge
+
+    ci, cj, ck = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    # cubes ordered with i fastest
+    ci = ci.transpose(2, 1, 0).ravel()
+    cj = cj.transpose(2, 1, 0).ravel()
+    ck = ck.transpose(2, 1, 0).ravel()
+    tets = []
+    for perm in itertools.permutations(range(3)):
+        parity = sum(1 for a in range(3) for b in range(a + 1, 3) if perm[a] > perm[b]) % 2
+        path = [np.array([0, 0, 0])]
+        for ax in perm:
+            step = path[-1].copy()
+            step[ax] += 1
+            path.append(step)
+        v = [vid(ci + p[0], cj + p[1], ck + p[2]) for p in path]
+        if parity:
+            v[2], v[3] = v[3], v[2]
+        tets.append(np.stack(v, axis=1))
+    # interleave so the 6 tets of one cube are adjacent in memory
+    tets = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int32)
+    return pos, tets
+
+
+def spline_control_points(mu: float, lam: float, rng: np.random.Generator,
+                          spread: float = 0.3) -> np.ndarray:
+    """Control points of a synthetic spline Valanis-Landel material.
+
+    The base curves are the Neo-Hookean choice a(x) = mu/2 (x^2 - 1), b = 0,
+    c(J) = -mu ln J + lam/2 ln^2 J, sampled at the knots; every value and slope
+    is scaled by (1 + u) with u ~ U[-spread, spread].  The slope of c at J = 1
+    is then set so that a'(1) + 2 b'(1) + c'(1) = 0 (stress-free rest state).
+    Returns (3, 8, 3): function (a, b, c) x knot x (knot, value, slope).
+    """
+    k = np.asarray(SPLINE_KNOTS, dtype=np.float64)
+    a_v, a_s = 0.5 * mu * (k * k - 1.0), mu * k
+    b_v, b_s = np.zeros_like(k), np.zeros_like(k)
+    lk = np.log(k)
+    c_v, c_s = -mu * lk + 0.5 * lam * lk * lk, (-mu + lam * lk) / k
+    out = np.zeros((3, k.size, 3))
+    for f, (v, s) in enumerate(((a_v, a_s), (b_v, b_s), (c_v, c_s))):
+        out[f, :, 0] = k
+        out[f, :, 1] = v * (1.0 + rng.uniform(-spread, spread, k.size))
+        out[f, :, 2] = s * (1.0 + rng.uniform(-spread, spread, k.size))
+    one = int(np.argmin(np.abs(k - 1.0)))
+    out[2, one, 2] = -(out[0, one, 2] + 2.0 * out[1, one, 2])
+    return out
+
+
+def _with_velocity(rest, clamped, v0, h):
+    """States (q_l, q_{l-1}) with q_l = rest and finite-difference velocity v0."""
+    q_cur = rest.copy()
+    q_prev = rest - h * v0
+    q_prev[clamped.astype(bool)] = rest[clamped.astype(bool)]
+    return q_cur, q_prev
+
+
+def lattice_workload(dims, material: Material, *, clamp_axis: int = 2, seed: int = 0,
+                     v_range: float = 0.0, edge: float = 0.05, iters: int = 10,
+                     history: int = 5, gravity=(0.0, 0.0, -9.81), h: float = 1.0 / 30.0,
+                     twist_deg: float = 0.0, name: str = "lattice") -> Workload:
+    """A Kuhn lattice with its clamp_axis = 0 face clamped.
+
+    v_range > 0 draws each free vertex's initial velocity component iid
+    U[-v_range, v_range]; twist_deg rotates the initial state about the long
+    (x) axis by twist_deg * x / L.
+    """
+    nx, ny, nz = dims
+    rest, tets = kuhn_lattice(nx, ny, nz, edge)
+    clamped = (np.abs(rest[:, clamp_axis]) < 1e-12 * edge).astype(np.uint8)
+    rng = np.random.default_rng(seed)
+    v0 = np.zeros_like(rest)
+    if v_range > 0.0:
+        v0 = rng.uniform(-v_range, v_range, rest.shape)
+        v0[clamped.astype(bool)] = 0.0
+    q_cur, q_prev = _with_velocity(rest, clamped, v0, h)
+    if twist_deg != 0.0:
+        L = nx * edge
+        yc, zc = 0.5 * ny * edge, 0.5 * nz * edge
+        th = math.radians(twist_deg) * rest[:, 0] / L
+        c, s = np.cos(th), np.sin(th)
+        dy, dz = rest[:, 1] - yc, rest[:, 2] - zc
+        q_cur = rest.copy()
+        q_cur[:, 1] = yc + c * dy - s * dz
+        q_cur[:, 2] = zc + s * dy + c * dz
+        q_prev = q_cur.copy()
+    return Workload(name=name, rest_pos=rest, tets=tets, clamped=clamped, q_cur=q_cur,
+                    q_prev=q_prev, material=material, h=h, gravity=tuple(gravity),
+                    iters=iters, history=history, dims=tuple(dims),
+                    meta={"seed": seed, "v_range": v_range, "twist_deg": twist_deg})
+
+
+# ---- the five measured workloads -------------------------------------------------
+
+def bar_4x4x16_fp64() -> Workload:
+    """4x4x16 cube bar (1536 tets, 425 vertices), Neo-Hookean E=1e5 nu=0.45, z=0 end clamped."""
+    return lattice_workload((4, 4, 16), Material(NEOHOOKEAN, 1e5, 0.45), clamp_axis=2,
+                            seed=1604, name="bar4x4x16_nh")
+
+
+def cube40(kind: int = NEOHOOKEAN, n: int = 40) -> Workload:
+    """n^3 cube lattice (n=40: 384,000 tets, 68,921 vertices), E=5e5 nu=0.4,
+    z=0 face clamped, free-vertex velocities iid U[-0.5, 0.5] m/s."""
+    return lattice_workload((n, n, n), Material(kind, 5e5, 0.4), clamp_axis=2, seed=1605,
+                            v_range=0.5, name=f"cube{n}_{MATERIAL_NAMES[kind]}")
+
+
+def spline_bar_80x40x40(scale: int = 1) -> Workload:
+    """80x40x40 bar (768,000 tets), synthetic spline VL material, x=0 end clamped,
+    initial state twisted 90 degrees along the bar.  scale > 1 divides each
+    dimension (small cases for tests)."""
+    dims = (80 // scale, 40 // scale, 40 // scale)
+    mat = Material(SPLINE_VL, 5e5, 0.4)
+    rng = np.random.default_rng(1606)
+    mat.spline = spline_control_points(mat.mu, mat.lam, rng)
+    return lattice_workload(dims, mat, clamp_axis=0, seed=1606, twist_deg=90.0,
+                            name=f"splinebar{dims[0]}x{dims[1]}x{dims[2]}")
+
+
+def batch_512(count: int = 512, lo: int = 4, hi: int = 24, seed: int = 1607) -> list:
+    """Independent simulations: per-axis dims uniform in [lo, hi], material uniform
+    over {Neo-Hookean, StVK, spline}, E log-uniform in [1e4, 1e6], nu ~ U[0.3, 0.48],
+    x=0 face clamped, gravity, zero initial velocity."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(count):
+        dims = tuple(int(d) for d in rng.integers(lo, hi + 1, size=3))
+        kind = (NEOHOOKEAN, STVK, SPLINE_VL)[int(rng.integers(0, 3))]
+        E = float(10.0 ** rng.uniform(4.0, 6.0))
+        nu = float(rng.uniform(0.3, 0.48))
+        mat = Material(kind, E, nu)
+        if kind == SPLINE_VL:
+            mat.spline = spline_control_points(mat.mu, mat.lam, rng)
+        out.append(lattice_workload(dims, mat, clamp_axis=0, seed=seed + 1 + s,
+                                    name=f"batch{s}"))
+    return out
+
+
+def large_48x48x192() -> Workload:
+    """48x48x192 bar (2,654,208 tets, 463,393 vertices), Neo-Hookean E=5e5 nu=0.4,
+    z=0 end clamped, free-vertex velocities iid U[-0.5, 0.5] m/s, 20 iterations, m=8."""
+    return lattice_workload((48, 48, 192), Material(NEOHOOKEAN, 5e5, 0.4), clamp_axis=2,
+                            seed=1608, v_range=0.5, iters=20, history=8, name="bar48x48x192_nh")

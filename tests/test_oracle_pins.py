@@ -1,0 +1,348 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: hand-derived
+closed forms, finite differences, invariances, an independent polar-decomposition
+implementation of the projective-dynamics local/global step (Sec. 3-4), the BFGS
+secant condition (Alg. 2), exact centre-of-mass motion, and a Newton minimiser.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import hqn_oracle as O
+from paper_1604_07378_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _problem(dims=(2, 2, 3), kind=W.NEOHOOKEAN, E=1e5, nu=0.4, seed=3, v=0.0, clamp=True,
+             spline=None, gravity=(0.0, 0.0, -9.81)):
+    mat = W.Material(kind, E, nu)
+    if kind == W.SPLINE_VL:
+        mat.spline = spline if spline is not None else W.spline_control_points(
+            mat.mu, mat.lam, np.random.default_rng(seed))
+    w = W.lattice_workload(dims, mat, seed=seed, v_range=v, gravity=gravity)
+    if not clamp:
+        w.clamped[:] = 0
+    return w, O.problem_from_workload(w)
+
+
+MATERIALS = [W.NEOHOOKEAN, W.STVK, W.SPLINE_VL, W.COROTATED, W.POLY4]
+
+
+# ---------------------------------------------------------------- mesh, mass
+
+def test_kuhn_lattice_volumes_and_mass():
+    dims, a = (2, 3, 4), 0.05
+    w, P = _problem(dims)
+    assert w.n_tets == 6 * 2 * 3 * 4
+    assert w.n_verts == 3 * 4 * 5
+    np.testing.assert_allclose(P.vol, a**3 / 6.0, rtol=1e-12)
+    box = dims[0] * dims[1] * dims[2] * a**3
+    assert abs(P.vol.sum() - box) < 1e-12 * box
+    assert abs(P.mass.sum() - 1000.0 * box) < 1e-12 * 1000.0 * box
+    # every cube's 6 tets cover it: each tet vertex set spans the main diagonal
+    t = w.tets.reshape(-1, 6, 4)
+    assert np.all(t[:, :, 0] == t[:, :1, 0])
+
+
+# ---------------------------------------------------------------- signed SVD
+
+def test_signed_svd_convention():
+    rng = np.random.default_rng(0)
+    F = rng.normal(size=(2000, 3, 3))
+    F[:1000] += 2.0 * np.eye(3)
+    U, s, V = O.signed_svd(F)
+    rec = U @ (s[:, :, None] * np.swapaxes(V, -1, -2))
+    assert np.max(np.abs(rec - F)) < 1e-12 * np.max(np.abs(F))
+    np.testing.assert_allclose(np.linalg.det(U), 1.0, atol=1e-12)
+    np.testing.assert_allclose(np.linalg.det(V), 1.0, atol=1e-12)
+    assert np.all(s[:, 0] >= s[:, 1] - 1e-14) and np.all(s[:, 1] >= np.abs(s[:, 2]) - 1e-14)
+    assert np.all(np.sign(s[:, 2]) == np.sign(np.linalg.det(F)))
+    # reflection through one axis: stretches (3, 2, -1)
+    _, s1, _ = O.signed_svd(np.diag([3.0, -2.0, 1.0])[None])
+    np.testing.assert_allclose(s1[0], [3.0, 2.0, -1.0], atol=1e-14)
+    # a rotation: unit stretches and U V^T = R
+    R = scipy.linalg.expm(np.array([[0, -0.3, 0.2], [0.3, 0, -0.7], [-0.2, 0.7, 0]]))
+    U, s2, V = O.signed_svd(R[None])
+    np.testing.assert_allclose(s2[0], 1.0, atol=1e-14)
+    np.testing.assert_allclose(U[0] @ V[0].T, R, atol=1e-14)
+
+
+# ---------------------------------------------------------------- materials
+
+def _random_F(rng, n, spread=0.3, allow_inverted=False):
+    F = np.eye(3) + spread * rng.normal(size=(n, 3, 3))
+    if not allow_inverted:
+        F[np.linalg.det(F) < 0.2] = np.eye(3)
+    return F
+
+
+def test_neohookean_matches_invariant_form():
+    mu, lam = O.lame(1e5, 0.45)
+    mat = O.NeoHookean(mu, lam)
+    F = _random_F(np.random.default_rng(1), 500)
+    _, s, _ = O.signed_svd(F)
+    J = np.linalg.det(F)
+    I1 = np.einsum("nij,nij->n", F, F)
+    ref = 0.5 * mu * (I1 - 3.0) - mu * np.log(J) + 0.5 * lam * np.log(J) ** 2
+    np.testing.assert_allclose(O.psi(mat, s), ref, rtol=1e-11, atol=1e-9 * mu)
+
+
+def test_stvk_matches_invariant_form():
+    mu, lam = O.lame(5e5, 0.4)
+    mat = O.StVK(mu, lam)
+    F = _random_F(np.random.default_rng(2), 500, allow_inverted=True)
+    _, s, _ = O.signed_svd(F)
+    Eg = 0.5 * (np.swapaxes(F, -1, -2) @ F - np.eye(3))
+    ref = mu * np.einsum("nij,nij->n", Eg, Eg) + 0.5 * lam * np.trace(Eg, axis1=1, axis2=2) ** 2
+    np.testing.assert_allclose(O.psi(mat, s), ref, rtol=1e-11, atol=1e-9 * mu)
+
+
+def test_corotated_and_poly4_match_polar_forms():
+    mu, lam = 20.0, 100.0
+    F = _random_F(np.random.default_rng(3), 300)
+    _, s, _ = O.signed_svd(F)
+    R = np.stack([scipy.linalg.polar(f)[0] for f in F])
+    J = np.linalg.det(F)
+    ref = mu * np.einsum("nij,nij->n", F - R, F - R) + 0.5 * lam * (J - 1.0) ** 2
+    np.testing.assert_allclose(O.psi(O.Corotated(mu, lam), s), ref, rtol=1e-10, atol=1e-12)
+    ev = np.sqrt(np.linalg.eigvalsh(np.swapaxes(F, -1, -2) @ F))
+    np.testing.assert_allclose(O.psi(O.Poly4(mu), s), mu * np.sum((ev - 1.0) ** 4, axis=1),
+                               rtol=1e-10, atol=1e-12)
+
+
+def test_spline_reproduces_quadratic_material_exactly():
+    """Cubic Hermite splines sampling a quadratic reproduce it everywhere,
+    including the quadratic extension outside the knots."""
+    mu, lam = 7.0, 11.0
+    k = np.asarray(W.SPLINE_KNOTS)
+    ctrl = np.zeros((3, k.size, 3))
+    ctrl[:, :, 0] = k
+    ctrl[0, :, 1], ctrl[0, :, 2] = mu * (k - 1) ** 2, 2 * mu * (k - 1)
+    ctrl[2, :, 1], ctrl[2, :, 2] = 0.5 * lam * (k - 1) ** 2, lam * (k - 1)
+    spl, cor = O.SplineVL(ctrl), O.Corotated(mu, lam)
+    t = np.linspace(-0.5, 4.0, 301)
+    for f in ("a", "da", "b", "db", "c", "dc"):
+        np.testing.assert_allclose(getattr(spl, f)(t), getattr(cor, f)(t), atol=1e-11)
+    assert abs(O.stiffness_k(spl) - (2 * mu + lam)) < 1e-10 * (2 * mu + lam)
+
+
+# ---------------------------------------------------------------- stiffness k (Eq. stiffness)
+
+def test_stiffness_closed_forms():
+    """k = 12 * integral_{1/2}^{3/2} (s - 1) f(s) ds, derived by hand per material."""
+    mu, lam = O.lame(5e5, 0.4)
+    k_cor = 2 * mu + lam
+    k_poly = 0.6 * mu
+    F = lambda s: s * math.log(s) - s - 0.5 * math.log(s) ** 2
+    k_nh = mu * (12.0 * math.log(3.0) - 11.0) + lam * 12.0 * (F(1.5) - F(0.5))
+    k_stvk = 2.15 * (mu + 0.5 * lam)              # 12 * 43/240 = 43/20
+    assert abs(O.stiffness_k(O.Corotated(mu, lam)) - k_cor) < 1e-10 * k_cor
+    assert abs(O.stiffness_k(O.Poly4(mu)) - k_poly) < 1e-10 * k_poly
+    assert abs(O.stiffness_k(O.NeoHookean(mu, lam)) - k_nh) < 1e-10 * k_nh
+    assert abs(O.stiffness_k(O.StVK(mu, lam)) - k_stvk) < 1e-10 * k_stvk
+    # the paper: for the polynomial material k depends linearly on mu
+    assert abs(O.stiffness_k(O.Poly4(3 * mu)) - 3 * k_poly) < 1e-9 * k_poly
+
+
+def test_paper_parameters_golden():
+    with open(os.path.join(GOLDEN, "paper_parameters.json")) as f:
+        g = json.load(f)
+    assert g["h"] == pytest.approx(1.0 / 30.0)
+    assert (g["x_start"], g["x_end"]) == (0.5, 1.5)
+    w = W.cube40(n=2)
+    assert w.h == pytest.approx(g["h"]) and w.history == g["history_m"] and w.iters == g["iterations"]
+    # the oracle's defaults are the paper's
+    import inspect
+    sig = inspect.signature(O.solve_step).parameters
+    assert sig["gamma"].default == g["gamma"] and sig["backtrack"].default == g["backtrack"]
+    assert sig["m"].default == g["history_m"] and sig["iters"].default == g["iterations"]
+
+
+# ---------------------------------------------------------------- gradient of g
+
+@pytest.mark.parametrize("kind", MATERIALS)
+def test_gradient_matches_central_differences(kind):
+    w, P = _problem((2, 2, 3), kind=kind, seed=5)
+    rng = np.random.default_rng(11)
+    x = w.rest_pos + 0.012 * rng.normal(size=w.rest_pos.shape)
+    y = w.rest_pos + 0.01 * rng.normal(size=w.rest_pos.shape)
+    x[P.clamped] = w.rest_pos[P.clamped]
+    y[P.clamped] = w.rest_pos[P.clamped]
+    if kind == W.NEOHOOKEAN:
+        # push one vertex through its neighbours: inverted tets use the J < J0 extension
+        v = P.free[len(P.free) // 2]
+        x[v] += np.array([0.06, 0.05, -0.055])
+        J = np.linalg.det(O.deformation_gradients(P, x))
+        assert np.any(J < 0.0) and np.any(J > O.J0_NEOHOOKEAN)
+    grad = O.gradient(P, x, y)
+    eps = 1e-7
+    fd = np.zeros_like(x)
+    for v in P.free:
+        for c in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[v, c] += eps
+            xm[v, c] -= eps
+            fd[v, c] = (O.objective(P, xp, y) - O.objective(P, xm, y)) / (2 * eps)
+    err = np.linalg.norm(fd - grad) / np.linalg.norm(grad)
+    assert err < 1e-6, err
+    assert np.all(grad[P.clamped] == 0.0)
+
+
+@pytest.mark.parametrize("kind", MATERIALS)
+def test_zero_force_and_energy_at_rest(kind):
+    w, P = _problem((2, 2, 3), kind=kind)
+    X = w.rest_pos
+    grad = O.gradient(P, X, X)
+    scale = P.k * 0.05**2
+    assert np.max(np.abs(grad)) < 1e-9 * scale
+    assert abs(O.objective(P, X, X)) < 1e-12 * scale * 0.05
+
+
+@pytest.mark.parametrize("kind", MATERIALS)
+def test_energy_rotation_translation_invariance(kind):
+    w, P = _problem((2, 2, 2), kind=kind)
+    rng = np.random.default_rng(7)
+    x = w.rest_pos + 0.01 * rng.normal(size=w.rest_pos.shape)
+    R = scipy.linalg.expm(np.array([[0, -1.1, 0.4], [1.1, 0, -0.9], [-0.4, 0.9, 0]]))
+    x2 = x @ R.T + np.array([0.3, -2.0, 5.0])
+    e1 = np.sum(O.elastic_energy_per_tet(P, x))
+    e2 = np.sum(O.elastic_energy_per_tet(P, x2))
+    assert abs(e1 - e2) < 1e-10 * abs(e1)
+
+
+# ---------------------------------------------------------------- A0 = M/h^2 + L
+
+def test_A0_spd_residual_and_laplacian():
+    w, P = _problem((3, 2, 4))
+    A = P.A.toarray()
+    assert np.allclose(A, A.T, atol=1e-12 * np.abs(A).max())
+    np.linalg.cholesky(A)                                   # SPD
+    rng = np.random.default_rng(1)
+    q = rng.normal(size=(P.n, 3))
+    q[P.clamped] = 0.0
+    r = O.solve_A(P, q)
+    res = P.A @ r[P.free] - q[P.free]
+    assert np.linalg.norm(res) < 1e-12 * np.linalg.norm(q)
+    # constants are in the null space of every G_t
+    L = O.laplacian(P)
+    assert np.max(np.abs(L @ np.ones(P.n))) < 1e-10 * np.abs(L).max()
+    # x^T L x = sum_t w_t ||G_t x||_F^2 with G_t x = F(x)^T built from Ds Dm^{-1}
+    x = rng.normal(size=(P.n, 3))
+    Fx = O.deformation_gradients(P, x)
+    lhs = np.sum(x * (L @ x))
+    rhs = np.sum(P.vol * P.k * np.einsum("tij,tij->t", Fx, Fx))
+    assert abs(lhs - rhs) < 1e-10 * abs(rhs)
+
+
+# ---------------------------------------------------------------- Alg. 2
+
+def test_two_loop_m0_is_alg1_direction():
+    w, P = _problem((2, 2, 3), seed=2, v=0.3)
+    y = O.predictor(P, w.q_cur, w.q_prev)
+    grad = O.gradient(P, y + 0.003, y)
+    d = O.lbfgs_direction(P, grad, [])
+    np.testing.assert_allclose(d, -O.solve_A(P, grad), rtol=0, atol=1e-15)
+
+
+def test_two_loop_secant_condition_and_symmetry():
+    """The L-BFGS inverse-Hessian operator B satisfies B t_newest = s_newest and
+    is symmetric (Nocedal-Wright Ch. 7); d = -B grad in Alg. 2."""
+    w, P = _problem((2, 2, 3), seed=4)
+    rng = np.random.default_rng(9)
+    nf = P.free.size
+    Q = rng.normal(size=(3 * nf, 3 * nf))
+    H = Q @ Q.T + 3 * nf * np.eye(3 * nf)
+    hist = []
+    for _ in range(4):
+        s = np.zeros((P.n, 3))
+        s[P.free] = rng.normal(size=(nf, 3))
+        t = np.zeros((P.n, 3))
+        t[P.free] = (H @ s[P.free].ravel()).reshape(nf, 3)
+        hist.append((s, t, O.tr_dot(t, s)))
+    s_new, t_new, _ = hist[-1]
+    d = O.lbfgs_direction(P, -t_new, hist)
+    assert np.linalg.norm(d - s_new) < 1e-10 * np.linalg.norm(s_new)
+    u = np.zeros((P.n, 3)); u[P.free] = rng.normal(size=(nf, 3))
+    v = np.zeros((P.n, 3)); v[P.free] = rng.normal(size=(nf, 3))
+    Bu = -O.lbfgs_direction(P, u, hist)
+    Bv = -O.lbfgs_direction(P, v, hist)
+    assert abs(O.tr_dot(v, Bu) - O.tr_dot(u, Bv)) < 1e-10 * abs(O.tr_dot(v, Bu))
+    assert O.tr_dot(u, Bu) > 0
+
+
+# ---------------------------------------------------------------- Sec. 4: projective dynamics
+
+def test_projective_dynamics_identity_arap():
+    """For ARAP (corotated, lam = 0) the energy is a projective-dynamics energy
+    with w = V k, k = 2 mu.  Then d = x* - x where x* is the local/global step
+    (Eq. PDsolution), built here from polar projections, and alpha = 1 always
+    passes the Armijo test with gamma = 0.3."""
+    w, P = _problem((2, 2, 4), kind=W.COROTATED, E=2e4, nu=0.0, v=0.4, seed=8)
+    assert abs(P.k - 2 * P.mat.mu) < 1e-10 * P.k
+    y = O.predictor(P, w.q_cur, w.q_prev)
+    x = y.copy()
+    rng = np.random.default_rng(5)
+    x[P.free] += 0.004 * rng.normal(size=(P.free.size, 3))
+    d = O.lbfgs_direction(P, O.gradient(P, x, y), [])
+    # independent local step: p_t = polar rotation of F_t; residual of the global step
+    Fx = O.deformation_gradients(P, x)
+    res = P.mass[:, None] * (x - y) / P.h**2
+    B = np.array([[-1.0, 1.0, 0.0, 0.0], [-1.0, 0.0, 1.0, 0.0], [-1.0, 0.0, 0.0, 1.0]])
+    for t in range(P.tets.shape[0]):
+        R = scipy.linalg.polar(Fx[t])[0]
+        Gt = P.Dm_inv[t].T @ B                       # 3 x 4
+        contrib = P.vol[t] * P.k * Gt.T @ (Fx[t].T - R.T)   # 4 x 3
+        for c in range(4):
+            res[P.tets[t, c]] += contrib[c]
+    delta = np.zeros_like(x)
+    delta[P.free] = np.linalg.solve(P.A.toarray(), -res[P.free])
+    assert np.linalg.norm(delta - d) < 1e-9 * np.linalg.norm(d)
+    _, st = O.solve_step(P, w.q_cur, w.q_prev, iters=10, m=0)
+    assert st.trials == [1] * 10
+
+
+# ---------------------------------------------------------------- whole step
+
+def test_centre_of_mass_follows_ballistic_motion():
+    """Unclamped body: elastic forces sum to zero and 1^T L = 0, so every iterate
+    keeps sum_v m_v x_v = sum_v m_v y_v (Eq. PD with y = 2q_l - q_{l-1} + h^2 g)."""
+    w, P = _problem((2, 3, 3), kind=W.STVK, v=0.6, seed=12, clamp=False)
+    x, st = O.solve_step(P, w.q_cur, w.q_prev, iters=10, m=5)
+    M = P.mass.sum()
+    com = (P.mass[:, None] * x).sum(0) / M
+    com_ref = (P.mass[:, None] * (2 * w.q_cur - w.q_prev)).sum(0) / M + P.h**2 * np.array(w.gravity)
+    assert np.linalg.norm(com - com_ref) < 1e-12 * np.linalg.norm(com_ref)
+    assert st.g[-1] < st.g0
+
+
+@pytest.mark.parametrize("dims,kind", [((1, 1, 2), W.NEOHOOKEAN), ((2, 2, 3), W.STVK)])
+def test_converged_lbfgs_equals_newton_minimiser(dims, kind):
+    w, P = _problem(dims, kind=kind, v=0.8, seed=21)
+    x_newton, g_newton = O.newton_minimise(P, w.q_cur, w.q_prev)
+    x_lbfgs, st = O.solve_step(P, w.q_cur, w.q_prev, iters=300, m=5)
+    y = O.predictor(P, w.q_cur, w.q_prev)
+    scale = np.linalg.norm(x_newton - y)
+    assert scale > 1e-4
+    assert np.linalg.norm(x_lbfgs - x_newton) < 1e-6 * scale
+    assert abs(st.g[-1] - g_newton) <= 1e-10 * abs(st.g0 - g_newton)
+
+
+def test_lbfgs_history_speeds_convergence():
+    """Sec. 5: L-BFGS (m = 5) reaches a lower relative error (Eq. RelativeError)
+    than the plain quasi-Newton direction (m = 0) after 10 iterations."""
+    w = W.spline_bar_80x40x40(scale=10)
+    w.material = W.Material(W.NEOHOOKEAN, 5e5, 0.4)
+    P = O.problem_from_workload(w)
+    _, st_ref = O.solve_step(P, w.q_cur, w.q_prev, iters=400, m=5)
+    g_star = st_ref.g[-1]
+    _, st0 = O.solve_step(P, w.q_cur, w.q_prev, iters=10, m=0)
+    _, st5 = O.solve_step(P, w.q_cur, w.q_prev, iters=10, m=5)
+    e0 = O.relative_error(st0.g[-1], st0.g0, g_star)
+    e5 = O.relative_error(st5.g[-1], st5.g0, g_star)
+    assert 0 <= e5 < e0 < 1
