@@ -1,0 +1,180 @@
+/*
+ * hqn.h - C ABI of the GB300 quasi-Newton implicit-Euler solver for
+ * hyperelastic tetrahedral meshes.
+ *
+ * Method: Liu, Bouaziz & Kavan, "Towards Real-time Simulation of Hyperelastic
+ * Materials" (arXiv 1604.07378).  One implicit-Euler time step is the
+ * minimisation of
+ *     g(x) = 1/(2h^2) tr((x - y)^T M (x - y)) + E(x),
+ *     y    = 2 q_l - q_{l-1} + h^2 M^{-1} f_ext                      (Eq. PD)
+ * by Alg. 1 (quasi-Newton iterations with backtracking Armijo line search),
+ * whose descent direction comes from the L-BFGS two-loop recursion of Alg. 2
+ * with the constant initial Hessian A0 = M/h^2 + L (Sec. 4.2, Eq. PDsolution),
+ * prefactored once.  E is a Valanis-Landel energy in principal stretches
+ * (Eq. valanis-landel); L is weighted by the stiffness fit of Eq. stiffness.
+ *
+ * Conventions common to every entry point
+ *   - Positions are absolute coordinates in the caller's vertex order, host
+ *     arrays of n_verts x 3 doubles, row-major (x, y, z per vertex).
+ *   - Every pointer argument is owned by the caller; the library copies what it
+ *     needs and keeps no reference after the call returns.
+ *   - A handle owns all the device memory it allocates (on the device that is
+ *     current when sim_create runs) and frees it in sim_destroy.  All device
+ *     work of a handle is issued on the CUDA stream given to sim_create.
+ *   - Return codes: 0 = success, > 0 = warning (the result is usable), < 0 =
+ *     error (the handle's state is unchanged unless stated otherwise).
+ *     sim_strerror() maps a code to a static string.  No C++ exception ever
+ *     crosses this boundary.
+ *   - Calls on one handle must not overlap (thread-compatible, not
+ *     thread-safe); different handles are independent.
+ */
+#ifndef HQN_H
+#define HQN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define HQN_OK                    0
+#define HQN_WARN_LS_EXHAUSTED     1  /* a line search hit ls_max trials; that step's
+                                        iterations ended at the last accepted x   */
+#define HQN_WARN_NONDESCENT       2  /* grad^T d >= 0 (only at a stationary point);
+                                        that step's iterations ended             */
+#define HQN_ERR_ARG              -1  /* null pointer, bad size, index out of range */
+#define HQN_ERR_DEGENERATE_TET   -2  /* a rest tet has det(Dm) <= 0              */
+#define HQN_ERR_NONFINITE        -3  /* NaN/Inf in an input or in the state       */
+#define HQN_ERR_NOT_SPD          -4  /* A0 is not positive definite               */
+#define HQN_ERR_CUDA             -5  /* a CUDA runtime call failed                */
+#define HQN_ERR_NO_MEMORY        -6  /* host or device allocation failed          */
+#define HQN_ERR_UNSUPPORTED      -7  /* option not available in this build        */
+
+/* ---- materials (Eq. valanis-landel: Psi = sum a(s_i) + sum b(s_i s_j) + c(J)) */
+typedef enum {
+    HQN_NEOHOOKEAN = 0, /* a = mu/2 (x^2-1), b = 0, c = -mu ln J + lam/2 ln^2 J;
+                           for J < 0.05, c is its 2nd-order Taylor polynomial at 0.05 */
+    HQN_STVK       = 1, /* mu ||E||^2 + lam/2 tr^2 E, E = (F^T F - I)/2              */
+    HQN_SPLINE_VL  = 2, /* a, b, c are C1 cubic Hermite splines (Sec. 4.1,
+                           "spline-based materials"); quadratic extension outside  */
+    HQN_COROTATED  = 3, /* a = mu (x-1)^2, c = lam/2 (J-1)^2                           */
+    HQN_POLY4      = 4  /* a = mu (x-1)^4 (the paper's polynomial material)           */
+} hqn_material_kind;
+
+typedef enum {
+    HQN_FP64_PLAIN = 0, /* every kernel in float64                                  */
+    HQN_FP32_MIXED = 1  /* float32 tets, two-loop vectors and triangular solves;
+                           float64 energy sums, Armijo test and inner products      */
+} hqn_precision;
+
+typedef struct {
+    int32_t        n_verts;
+    int32_t        n_tets;
+    const double  *rest_pos;  /* n_verts x 3 rest positions X                        */
+    const int32_t *tets;      /* n_tets x 4 vertex indices; det[X1-X0,X2-X0,X3-X0] > 0 */
+    const uint8_t *clamped;   /* n_verts flags, nonzero = position prescribed (held
+                                 at its current state); NULL = none clamped          */
+} hqn_mesh;
+
+typedef struct {
+    int32_t       kind;       /* hqn_material_kind                                    */
+    double        E, nu;      /* Young's modulus [Pa], Poisson ratio -> mu, lambda    */
+    double        density;    /* [kg/m^3]; lumped mass m_v = density * sum V_t / 4    */
+    const double *spline;     /* HQN_SPLINE_VL only: 3 x 8 x 3 doubles, function
+                                 (a, b, c) x knot x (knot, value, slope), knots
+                                 strictly increasing; otherwise ignored (may be NULL) */
+} hqn_material;
+
+typedef struct {
+    double  h;            /* time step [s]; paper: 1/30 (Sec. 3)                       */
+    double  gamma;        /* Armijo constant; paper: 0.3 (Sec. 4.1)                    */
+    double  backtrack;    /* step shrink factor; paper: 0.5 (Alg. 1)                   */
+    double  x_start;      /* stiffness-fit interval; paper: [0.5, 1.5] (Sec. 5)        */
+    double  x_end;
+    double  gravity[3];   /* [m/s^2], f_ext = m_v * gravity                           */
+    int32_t iters;        /* quasi-Newton iterations per step; paper: 10 (Table 1)    */
+    int32_t history_m;    /* L-BFGS window; paper: 5 (Sec. 4.2); 0 = Alg. 1 direction  */
+    int32_t ls_max;       /* line-search trials before giving up (paper is silent)    */
+    int32_t precision;    /* hqn_precision                                            */
+    int32_t leaf_size;    /* max vertices of a nested-dissection leaf (0 = default 64) */
+} hqn_params;
+
+#define HQN_MAX_HISTORY 16
+#define HQN_MAX_ITERS   64
+
+/* Per-step record of the most recent step taken by sim_step. */
+typedef struct {
+    int32_t steps;                          /* steps taken by this sim_step call     */
+    int32_t iters;                          /* iterations of the last step           */
+    int32_t status;                         /* worst status over the call's steps    */
+    int32_t trials_total;                   /* line-search trials, all steps         */
+    int32_t iters_total;                    /* iterations, all steps                 */
+    int32_t trials[HQN_MAX_ITERS];          /* trials of each iteration, last step   */
+    double  g0;                             /* g(x_1), x_1 = y, last step            */
+    double  g[HQN_MAX_ITERS];               /* g(x_{k+1}) after each iteration       */
+} hqn_step_stats;
+
+typedef struct {
+    int32_t n_verts, n_tets, n_free;
+    int32_t n_supernodes, n_levels;
+    int64_t factor_entries;     /* stored entries of the solve operators [Linv; K]    */
+    int64_t factor_nnz;         /* nonzeros of the Cholesky factor L (incl. padding)  */
+    double  stiffness_k;        /* fitted k of Eq. stiffness                          */
+    double  setup_seconds;      /* host time spent in sim_create                      */
+    int64_t device_bytes;       /* device memory held by the handle                   */
+} hqn_info;
+
+typedef struct sim_handle sim_handle;
+
+/* Paper defaults: h = 1/30, gamma = 0.3, backtrack = 0.5, [0.5, 1.5], gravity
+ * (0, 0, -9.81), 10 iterations, m = 5, ls_max = 30, FP32_MIXED, leaf 64. */
+void hqn_default_params(hqn_params *p);
+
+/* Builds a simulation: rest data (Dm^-1, volumes, lumped mass), the stiffness k
+ * of Eq. stiffness, A0 = M/h^2 + sum_t V_t k G_t^T G_t on the free vertices
+ * (Eq. PDmatrixForm, PDsolution), its nested-dissection ordering and float64
+ * supernodal Cholesky factor, and the device operators of the triangular
+ * solves.  The state starts at rest (q_l = q_{l-1} = X).  `stream` is a
+ * cudaStream_t (NULL = legacy default stream).
+ * Errors: HQN_ERR_ARG, HQN_ERR_DEGENERATE_TET, HQN_ERR_NONFINITE,
+ * HQN_ERR_NOT_SPD, HQN_ERR_CUDA, HQN_ERR_NO_MEMORY.  *out is NULL on error. */
+int sim_create(const hqn_mesh *mesh, const hqn_material *material,
+               const hqn_params *params, void *stream, sim_handle **out);
+
+/* Sets the state (q_l, q_{l-1}); each n_verts x 3 host doubles.  Clamped
+ * vertices are held at their q_l.  q_prev may be NULL (= q_cur, zero velocity). */
+int sim_set_state(sim_handle *sim, const double *q_cur, const double *q_prev);
+
+/* Copies the state out (either pointer may be NULL).  Synchronises the stream. */
+int sim_get_state(sim_handle *sim, double *q_cur, double *q_prev);
+
+/* Advances nsteps time steps (Alg. 1 with Alg. 2) on the device.  stats may be
+ * NULL.  Returns the worst status over the steps (a warning keeps going). */
+int sim_step(sim_handle *sim, int32_t nsteps, hqn_step_stats *stats);
+
+/* Evaluates g and grad g (Eq. PD) at positions x with inertial target y (both
+ * n_verts x 3 host doubles).  grad is zero on clamped vertices.  g_out or
+ * grad_out may be NULL.  Does not change the state. */
+int sim_energy_grad(sim_handle *sim, const double *x, const double *y,
+                    double *g_out, double *grad_out);
+
+/* r = A0^{-1} q on the free vertices by the device forward and backward
+ * triangular solves (3 right-hand sides); rows of clamped vertices are ignored
+ * in q and set to zero in r.  Host arrays n_verts x 3. */
+int sim_solve_A0(sim_handle *sim, const double *q, double *r);
+
+/* Alg. 2 on the device: d from grad and `npairs` history pairs (s_i, t_i),
+ * oldest first, each n_verts x 3 (s and t are npairs x n_verts x 3).  Pairs are
+ * used as given (no curvature filtering); npairs <= history_m. */
+int sim_direction(sim_handle *sim, const double *grad, int32_t npairs,
+                  const double *s, const double *t, double *d);
+
+int  sim_get_info(const sim_handle *sim, hqn_info *info);
+void sim_destroy(sim_handle *sim);
+const char *sim_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HQN_H */

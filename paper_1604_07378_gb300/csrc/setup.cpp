@@ -1,0 +1,701 @@
+// Host-side set-up: rest data, lumped mass, stiffness fit (Eq. stiffness),
+// A0 = M/h^2 + L (Eq. PDmatrixForm, PDsolution), nested-dissection ordering,
+// float64 multifrontal Cholesky and the per-supernode solve operators.
+#include "setup.hpp"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <numeric>
+
+#include "dense.hpp"
+
+namespace hqn {
+
+namespace {
+
+// ---------------------------------------------------------------- quadrature
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on P_n.
+void gauss_legendre(int npts, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(npts, 0.0);
+    w.assign(npts, 0.0);
+    const double pi = std::acos(-1.0);
+    for (int i = 0; i < npts; ++i) {
+        double t = std::cos(pi * (i + 0.75) / (npts + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= npts; ++k) {
+                double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = npts * (t * p1 - p0) / (t * t - 1.0);
+            double dt = p1 / dp;
+            t -= dt;
+            if (std::fabs(dt) < 1e-16) break;
+        }
+        x[i] = t;
+        w[i] = 2.0 / ((1.0 - t * t) * dp * dp);
+    }
+}
+
+// cubic Hermite segment value/derivative with quadratic continuation outside
+void hermite_eval(const double *kx, const double *kv, const double *ks, double t, double &val,
+                  double &der) {
+    const double lo = kx[0], hi = kx[7];
+    const double tc = std::min(std::max(t, lo), hi);
+    int i = 0;
+    for (int k = 1; k < 7; ++k)
+        if (tc >= kx[k]) i = k;
+    const double hh = kx[i + 1] - kx[i];
+    const double u = (tc - kx[i]) / hh;
+    const double v0 = kv[i], v1 = kv[i + 1], m0 = ks[i] * hh, m1 = ks[i + 1] * hh;
+    // p(u) = v0 + m0 u + (3(v1-v0) - 2m0 - m1) u^2 + (2(v0-v1) + m0 + m1) u^3
+    const double c2 = 3.0 * (v1 - v0) - 2.0 * m0 - m1;
+    const double c3 = 2.0 * (v0 - v1) + m0 + m1;
+    const double p = v0 + u * (m0 + u * (c2 + u * c3));
+    const double dp = (m0 + u * (2.0 * c2 + 3.0 * u * c3)) / hh;
+    const double ddp = (2.0 * c2 + 6.0 * u * c3) / (hh * hh);
+    const double dt = t - tc;
+    val = p + dp * dt + 0.5 * ddp * dt * dt;
+    der = dp + ddp * dt;
+}
+
+// a'(s) + 2 b'(s) + c'(s), the function whose best linear fit gives k
+double fit_target(const MaterialHost &m, double s) {
+    const double mu = m.mu, lam = m.lam;
+    switch (m.kind) {
+        case HQN_NEOHOOKEAN: {
+            double dc = s >= m.J0 ? (-mu + lam * std::log(s)) / s : m.c1 + m.c2 * (s - m.J0);
+            return mu * s + dc;
+        }
+        case HQN_STVK: {
+            double da = (mu + 0.5 * lam) * (s * s - 1.0) * s - lam * s;
+            double db = 0.5 * lam * s;
+            return da + 2.0 * db;
+        }
+        case HQN_COROTATED: return 2.0 * mu * (s - 1.0) + lam * (s - 1.0);
+        case HQN_POLY4: return 4.0 * mu * (s - 1.0) * (s - 1.0) * (s - 1.0);
+        case HQN_SPLINE_VL: {
+            double v, da, db, dc;
+            hermite_eval(m.sx[0], m.sv[0], m.ss[0], s, v, da);
+            hermite_eval(m.sx[1], m.sv[1], m.ss[1], s, v, db);
+            hermite_eval(m.sx[2], m.sv[2], m.ss[2], s, v, dc);
+            return da + 2.0 * db + dc;
+        }
+    }
+    return 0.0;
+}
+
+// ---------------------------------------------------------------- small linear algebra
+
+double det3(const double *M) {
+    return M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+           M[2] * (M[3] * M[7] - M[4] * M[6]);
+}
+
+void inv3(const double *M, double *R) {
+    const double d = det3(M);
+    R[0] = (M[4] * M[8] - M[5] * M[7]) / d;
+    R[1] = (M[2] * M[7] - M[1] * M[8]) / d;
+    R[2] = (M[1] * M[5] - M[2] * M[4]) / d;
+    R[3] = (M[5] * M[6] - M[3] * M[8]) / d;
+    R[4] = (M[0] * M[8] - M[2] * M[6]) / d;
+    R[5] = (M[2] * M[3] - M[0] * M[5]) / d;
+    R[6] = (M[3] * M[7] - M[4] * M[6]) / d;
+    R[7] = (M[1] * M[6] - M[0] * M[7]) / d;
+    R[8] = (M[0] * M[4] - M[1] * M[3]) / d;
+}
+
+// ---------------------------------------------------------------- nested dissection
+
+struct NDState {
+    const std::vector<double> *X;      // caller-order rest positions
+    const std::vector<int> *adj_ptr;   // caller-order adjacency of free vertices
+    const std::vector<int> *adj;
+    std::vector<char> side;            // scratch: 0 none, 1 = A, 2 = B
+    std::vector<int> order;            // elimination order (caller ids)
+    std::vector<SupernodeHost> nodes;
+    std::vector<std::vector<int>> node_verts;
+    int leaf = 64;
+};
+
+int nd_recurse(NDState &st, std::vector<int> &V) {
+    const std::vector<double> &X = *st.X;
+    if ((int)V.size() <= st.leaf) {
+        std::sort(V.begin(), V.end());
+        SupernodeHost s;
+        s.col = (int)st.order.size();
+        s.ncol = (int)V.size();
+        for (int v : V) st.order.push_back(v);
+        st.nodes.push_back(s);
+        st.node_verts.push_back(V);
+        return (int)st.nodes.size() - 1;
+    }
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int v : V)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], X[3 * v + a]);
+            hi[a] = std::max(hi[a], X[3 * v + a]);
+        }
+    int axes[3] = {0, 1, 2};
+    std::sort(axes, axes + 3, [&](int a, int b) { return hi[a] - lo[a] > hi[b] - lo[b]; });
+    std::vector<int> A, B;
+    for (int ai = 0; ai < 3 && A.empty(); ++ai) {
+        const int ax = axes[ai];
+        const double ext = hi[ax] - lo[ax];
+        if (!(ext > 0)) continue;
+        std::vector<int> sorted = V;
+        std::sort(sorted.begin(), sorted.end(), [&](int a, int b) {
+            double xa = X[3 * a + ax], xb = X[3 * b + ax];
+            return xa < xb || (xa == xb && a < b);
+        });
+        const double c = X[3 * sorted[sorted.size() / 2] + ax];
+        const double tol = 1e-9 * ext;
+        A.clear();
+        B.clear();
+        for (int v : V) (X[3 * v + ax] < c - tol ? A : B).push_back(v);
+        if (A.empty() || B.empty()) A.clear();
+    }
+    if (A.empty()) {  // cannot split geometrically: make it one leaf-like node
+        std::sort(V.begin(), V.end());
+        SupernodeHost s;
+        s.col = (int)st.order.size();
+        s.ncol = (int)V.size();
+        for (int v : V) st.order.push_back(v);
+        st.nodes.push_back(s);
+        st.node_verts.push_back(V);
+        return (int)st.nodes.size() - 1;
+    }
+    for (int v : A) st.side[v] = 1;
+    for (int v : B) st.side[v] = 2;
+    std::vector<int> S, Bp;
+    for (int v : B) {
+        bool touches = false;
+        for (int e = (*st.adj_ptr)[v]; e < (*st.adj_ptr)[v + 1] && !touches; ++e)
+            touches = st.side[(*st.adj)[e]] == 1;
+        (touches ? S : Bp).push_back(v);
+    }
+    if (S.empty()) {  // disconnected halves: still give the node one column
+        S.push_back(Bp.back());
+        Bp.pop_back();
+    }
+    for (int v : A) st.side[v] = 0;
+    for (int v : B) st.side[v] = 0;
+    std::vector<int> children;
+    children.push_back(nd_recurse(st, A));
+    if (!Bp.empty()) children.push_back(nd_recurse(st, Bp));
+    std::sort(S.begin(), S.end());
+    SupernodeHost s;
+    s.col = (int)st.order.size();
+    s.ncol = (int)S.size();
+    s.children = children;
+    for (int v : S) st.order.push_back(v);
+    st.nodes.push_back(s);
+    st.node_verts.push_back(S);
+    const int id = (int)st.nodes.size() - 1;
+    for (int c : children) st.nodes[c].parent = id;
+    return id;
+}
+
+}  // namespace
+
+double fit_stiffness(const MaterialHost &m, double x_start, double x_end) {
+    // k = int (s - sbar) f(s) ds / int (s - sbar)^2 ds on [x_start, x_end]
+    // (continuous least-squares slope), integrated piecewise with 8-point
+    // Gauss-Legendre between breakpoints (spline knots, J0) and 16 panels.
+    std::vector<double> gx, gw;
+    gauss_legendre(8, gx, gw);
+    std::vector<double> br;
+    for (int p = 0; p <= 16; ++p) br.push_back(x_start + (x_end - x_start) * p / 16.0);
+    if (m.kind == HQN_SPLINE_VL)
+        for (int f = 0; f < 3; ++f)
+            for (int i = 0; i < 8; ++i)
+                if (m.sx[f][i] > x_start && m.sx[f][i] < x_end) br.push_back(m.sx[f][i]);
+    if (m.kind == HQN_NEOHOOKEAN && m.J0 > x_start && m.J0 < x_end) br.push_back(m.J0);
+    std::sort(br.begin(), br.end());
+    const double sbar = 0.5 * (x_start + x_end);
+    double num = 0.0;
+    for (size_t p = 0; p + 1 < br.size(); ++p) {
+        const double a = br[p], b = br[p + 1];
+        if (!(b > a)) continue;
+        const double half = 0.5 * (b - a), mid = 0.5 * (a + b);
+        for (int q = 0; q < 8; ++q) {
+            const double s = mid + half * gx[q];
+            num += half * gw[q] * (s - sbar) * fit_target(m, s);
+        }
+    }
+    const double len = x_end - x_start;
+    return num / (len * len * len / 12.0);
+}
+
+int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_params &prm,
+                Setup &S, std::string &err) {
+    auto t_start = std::chrono::steady_clock::now();
+    const int n = mesh.n_verts, T = mesh.n_tets;
+    if (n <= 0 || T <= 0 || !mesh.rest_pos || !mesh.tets) {
+        err = "empty mesh or null pointer";
+        return HQN_ERR_ARG;
+    }
+    if (!(prm.h > 0) || !(prm.x_end > prm.x_start) || prm.iters < 0 || prm.iters > HQN_MAX_ITERS ||
+        prm.history_m < 0 || prm.history_m > HQN_MAX_HISTORY || prm.ls_max <= 0 ||
+        !(prm.gamma > 0 && prm.gamma < 1) || !(prm.backtrack > 0 && prm.backtrack < 1)) {
+        err = "parameter out of range";
+        return HQN_ERR_ARG;
+    }
+    for (int64_t i = 0; i < 3LL * n; ++i)
+        if (!std::isfinite(mesh.rest_pos[i])) {
+            err = "non-finite rest position";
+            return HQN_ERR_NONFINITE;
+        }
+    for (int64_t i = 0; i < 4LL * T; ++i)
+        if (mesh.tets[i] < 0 || mesh.tets[i] >= n) {
+            err = "tet vertex index out of range";
+            return HQN_ERR_ARG;
+        }
+    if (!(matin.density > 0) || !std::isfinite(matin.E) || !std::isfinite(matin.nu)) {
+        err = "material density must be positive and E, nu finite";
+        return matin.density <= 0 ? HQN_ERR_NOT_SPD : HQN_ERR_NONFINITE;
+    }
+
+    // ---- material
+    MaterialHost &M = S.mat;
+    M.kind = matin.kind;
+    M.mu = matin.E / (2.0 * (1.0 + matin.nu));
+    M.lam = matin.E * matin.nu / ((1.0 + matin.nu) * (1.0 - 2.0 * matin.nu));
+    if (M.kind == HQN_NEOHOOKEAN) {
+        const double J0 = M.J0, l0 = std::log(J0);
+        M.c0 = -M.mu * l0 + 0.5 * M.lam * l0 * l0;
+        M.c1 = (-M.mu + M.lam * l0) / J0;
+        M.c2 = (M.mu + M.lam - M.lam * l0) / (J0 * J0);
+    } else if (M.kind == HQN_SPLINE_VL) {
+        if (!matin.spline) {
+            err = "spline material needs control points";
+            return HQN_ERR_ARG;
+        }
+        for (int f = 0; f < 3; ++f)
+            for (int i = 0; i < 8; ++i) {
+                M.sx[f][i] = matin.spline[(f * 8 + i) * 3 + 0];
+                M.sv[f][i] = matin.spline[(f * 8 + i) * 3 + 1];
+                M.ss[f][i] = matin.spline[(f * 8 + i) * 3 + 2];
+                if (i > 0 && !(M.sx[f][i] > M.sx[f][i - 1])) {
+                    err = "spline knots must increase";
+                    return HQN_ERR_ARG;
+                }
+            }
+    } else if (M.kind != HQN_STVK && M.kind != HQN_COROTATED && M.kind != HQN_POLY4) {
+        err = "unknown material kind";
+        return HQN_ERR_ARG;
+    }
+    S.k = fit_stiffness(M, prm.x_start, prm.x_end);
+    if (!(S.k > 0) || !std::isfinite(S.k)) {
+        err = "stiffness fit is not positive";
+        return HQN_ERR_NOT_SPD;
+    }
+    S.h = prm.h;
+    S.density = matin.density;
+
+    // ---- rest data in caller order
+    std::vector<double> dminv0((size_t)T * 9), vol0(T);
+    for (int t = 0; t < T; ++t) {
+        const int *tv = mesh.tets + 4 * t;
+        double Dm[9];
+        for (int j = 0; j < 3; ++j)
+            for (int a = 0; a < 3; ++a)
+                Dm[3 * a + j] = mesh.rest_pos[3 * tv[j + 1] + a] - mesh.rest_pos[3 * tv[0] + a];
+        const double d = det3(Dm);
+        if (!(d > 0)) {
+            err = "degenerate or inverted rest tet " + std::to_string(t);
+            return HQN_ERR_DEGENERATE_TET;
+        }
+        vol0[t] = d / 6.0;
+        inv3(Dm, &dminv0[9 * (size_t)t]);
+    }
+
+    // ---- free vertices and their adjacency (caller ids)
+    std::vector<char> clamped(n, 0);
+    if (mesh.clamped)
+        for (int v = 0; v < n; ++v) clamped[v] = mesh.clamped[v] != 0;
+    std::vector<int> deg(n + 1, 0);
+    for (int t = 0; t < T; ++t)
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b)
+                if (a != b) deg[mesh.tets[4 * t + a]]++;
+    std::vector<int> adj_ptr(n + 1, 0);
+    for (int v = 0; v < n; ++v) adj_ptr[v + 1] = adj_ptr[v] + deg[v];
+    std::vector<int> adj(adj_ptr[n]);
+    {
+        std::vector<int> fill(adj_ptr.begin(), adj_ptr.end() - 1);
+        for (int t = 0; t < T; ++t)
+            for (int a = 0; a < 4; ++a)
+                for (int b = 0; b < 4; ++b)
+                    if (a != b) adj[fill[mesh.tets[4 * t + a]]++] = mesh.tets[4 * t + b];
+        // dedupe, drop clamped neighbours
+        std::vector<int> nptr(n + 1, 0);
+        int w = 0;
+        for (int v = 0; v < n; ++v) {
+            int b0 = adj_ptr[v], b1 = adj_ptr[v + 1];
+            std::sort(adj.begin() + b0, adj.begin() + b1);
+            nptr[v] = w;
+            int last = -1;
+            for (int e = b0; e < b1; ++e) {
+                int u = adj[e];
+                if (u == last) continue;
+                last = u;
+                if (!clamped[u]) adj[w++] = u;
+            }
+        }
+        nptr[n] = w;
+        adj.resize(w);
+        adj_ptr.swap(nptr);
+    }
+
+    // ---- nested dissection of the free vertices
+    std::vector<double> Xc(mesh.rest_pos, mesh.rest_pos + 3 * (size_t)n);
+    NDState st;
+    st.X = &Xc;
+    st.adj_ptr = &adj_ptr;
+    st.adj = &adj;
+    st.side.assign(n, 0);
+    st.leaf = prm.leaf_size > 0 ? prm.leaf_size : 64;
+    std::vector<int> freev;
+    for (int v = 0; v < n; ++v)
+        if (!clamped[v]) freev.push_back(v);
+    if (freev.empty()) {
+        err = "every vertex is clamped";
+        return HQN_ERR_ARG;
+    }
+    nd_recurse(st, freev);
+    S.n = n;
+    S.T = T;
+    S.n_free = (int)st.order.size();
+    S.perm = st.order;
+    for (int v = 0; v < n; ++v)
+        if (clamped[v]) S.perm.push_back(v);
+    S.iperm.assign(n, 0);
+    for (int i = 0; i < n; ++i) S.iperm[S.perm[i]] = i;
+    S.sn = std::move(st.nodes);
+    const int nf = S.n_free;
+
+    // ---- renumbered rest data, tets sorted by smallest vertex id
+    S.X.resize(3 * (size_t)n);
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < 3; ++a) S.X[3 * i + a] = Xc[3 * S.perm[i] + a];
+    std::vector<int> torder(T);
+    std::vector<int> tmin(T);
+    for (int t = 0; t < T; ++t) {
+        int m = n;
+        for (int a = 0; a < 4; ++a) m = std::min(m, S.iperm[mesh.tets[4 * t + a]]);
+        tmin[t] = m;
+    }
+    std::iota(torder.begin(), torder.end(), 0);
+    std::stable_sort(torder.begin(), torder.end(), [&](int a, int b) { return tmin[a] < tmin[b]; });
+    S.tets.resize(4 * (size_t)T);
+    S.dminv.resize(9 * (size_t)T);
+    S.vol.resize(T);
+    for (int i = 0; i < T; ++i) {
+        const int t = torder[i];
+        for (int a = 0; a < 4; ++a) S.tets[4 * i + a] = S.iperm[mesh.tets[4 * t + a]];
+        for (int e = 0; e < 9; ++e) S.dminv[9 * (size_t)i + e] = dminv0[9 * (size_t)t + e];
+        S.vol[i] = vol0[t];
+    }
+    // lumped mass: a quarter of each incident tet's mass
+    S.mass.assign(n, 0.0);
+    for (int t = 0; t < T; ++t)
+        for (int a = 0; a < 4; ++a) S.mass[S.tets[4 * t + a]] += 0.25 * matin.density * S.vol[t];
+    // vertex -> corner slots, ascending tet
+    S.vt_ptr.assign(n + 1, 0);
+    for (int t = 0; t < T; ++t)
+        for (int a = 0; a < 4; ++a) S.vt_ptr[S.tets[4 * t + a] + 1]++;
+    for (int v = 0; v < n; ++v) S.vt_ptr[v + 1] += S.vt_ptr[v];
+    S.vt_slot.assign(4 * (size_t)T, 0);
+    {
+        std::vector<int> fill(S.vt_ptr.begin(), S.vt_ptr.end() - 1);
+        for (int t = 0; t < T; ++t)
+            for (int a = 0; a < 4; ++a) S.vt_slot[fill[S.tets[4 * t + a]]++] = 4 * t + a;
+    }
+
+    // ---- A0 = M/h^2 + sum_t V_t k G_t^T G_t on free vertices, lower part by column
+    // element block: K_e[a][b] = V k (B^T Dm^{-1} Dm^{-T} B)[a][b]
+    std::vector<std::vector<std::pair<int, double>>> Acol(nf);
+    for (int t = 0; t < T; ++t) {
+        const double *Di = &S.dminv[9 * (size_t)t];
+        // G = Dm^{-T} B : column a of G (a = 0..3) is the gradient of the a-th hat function
+        double G[3][4];
+        for (int i = 0; i < 3; ++i) {
+            double s = 0;
+            for (int j = 0; j < 3; ++j) {
+                G[i][j + 1] = Di[3 * j + i];  // (Dm^{-T})_{i j} = Dm^{-1}_{j i}
+                s += Di[3 * j + i];
+            }
+            G[i][0] = -s;
+        }
+        const double w = S.vol[t] * S.k;
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b) {
+                const int va = S.tets[4 * t + a], vb = S.tets[4 * t + b];
+                if (va >= nf || vb >= nf || va < vb) continue;
+                const double kab = w * (G[0][a] * G[0][b] + G[1][a] * G[1][b] + G[2][a] * G[2][b]);
+                Acol[vb].push_back({va, kab});
+            }
+    }
+    const double inv_h2 = 1.0 / (prm.h * prm.h);
+    for (int j = 0; j < nf; ++j) {
+        Acol[j].push_back({j, S.mass[j] * inv_h2});
+        auto &c = Acol[j];
+        std::sort(c.begin(), c.end(), [](auto &p, auto &q) { return p.first < q.first; });
+        size_t w = 0;
+        for (size_t e = 0; e < c.size(); ++e) {
+            if (w > 0 && c[w - 1].first == c[e].first) c[w - 1].second += c[e].second;
+            else c[w++] = c[e];
+        }
+        c.resize(w);
+    }
+
+    // ---- symbolic: row structures R_s (postorder = node order)
+    const int ns = (int)S.sn.size();
+    std::vector<int> mark(nf, -1);
+    S.rows.clear();
+    for (int s = 0; s < ns; ++s) {
+        SupernodeHost &sn = S.sn[s];
+        const int last = sn.col + sn.ncol - 1;
+        std::vector<int> R;
+        for (int j = sn.col; j <= last; ++j)
+            for (auto &e : Acol[j])
+                if (e.first > last && mark[e.first] != s) {
+                    mark[e.first] = s;
+                    R.push_back(e.first);
+                }
+        for (int c : sn.children) {
+            const SupernodeHost &cs = S.sn[c];
+            for (int k = 0; k < cs.nrow; ++k) {
+                const int i = S.rows[cs.roff + k];
+                if (i < sn.col) {
+                    err = "nested dissection produced an invalid assembly tree";
+                    return HQN_ERR_ARG;
+                }
+                if (i > last && mark[i] != s) {
+                    mark[i] = s;
+                    R.push_back(i);
+                }
+            }
+        }
+        std::sort(R.begin(), R.end());
+        sn.roff = (int)S.rows.size();
+        sn.nrow = (int)R.size();
+        S.rows.insert(S.rows.end(), R.begin(), R.end());
+        sn.level = 0;
+        for (int c : sn.children) sn.level = std::max(sn.level, S.sn[c].level + 1);
+    }
+    // check every child's rows fit in the parent's front
+    for (int s = 0; s < ns; ++s) {
+        const SupernodeHost &sn = S.sn[s];
+        if (sn.parent < 0) continue;
+        const SupernodeHost &p = S.sn[sn.parent];
+        for (int k = 0; k < sn.nrow; ++k) {
+            const int i = S.rows[sn.roff + k];
+            if (i >= p.col && i < p.col + p.ncol) continue;
+            if (!std::binary_search(S.rows.begin() + p.roff, S.rows.begin() + p.roff + p.nrow, i)) {
+                err = "child row structure not contained in parent front";
+                return HQN_ERR_ARG;
+            }
+        }
+    }
+
+    // ---- offsets
+    int64_t qtot = 0;
+    int utot = 0;
+    S.factor_nnz = 0;
+    S.max_front_cols = 0;
+    for (auto &sn : S.sn) {
+        sn.qoff = qtot;
+        qtot += (int64_t)(sn.ncol + sn.nrow) * sn.ncol;
+        sn.uoff = utot;
+        utot += sn.nrow;
+        S.factor_nnz += (int64_t)sn.ncol * (sn.ncol + 1) / 2 + (int64_t)sn.ncol * sn.nrow;
+        S.max_front_cols = std::max(S.max_front_cols, sn.ncol);
+    }
+    S.n_upd = utot;
+    S.Q.assign(qtot, 0.0);
+
+    // ---- numeric multifrontal factorisation (postorder)
+    std::vector<std::vector<double>> upd(ns);  // update matrices U_s (nrow x nrow, lower)
+    std::vector<int> pos(nf, -1);
+    for (int s = 0; s < ns; ++s) {
+        SupernodeHost &sn = S.sn[s];
+        const int nc = sn.ncol, nr = sn.nrow, fs = nc + nr;
+        const int *R = S.rows.data() + sn.roff;
+        for (int j = 0; j < nc; ++j) pos[sn.col + j] = j;
+        for (int k = 0; k < nr; ++k) pos[R[k]] = nc + k;
+        std::vector<double> F((size_t)fs * fs, 0.0);
+        for (int j = 0; j < nc; ++j)
+            for (auto &e : Acol[sn.col + j]) F[(size_t)pos[e.first] * fs + j] += e.second;
+        for (int c : sn.children) {
+            const SupernodeHost &cs = S.sn[c];
+            const int *Rc = S.rows.data() + cs.roff;
+            const std::vector<double> &U = upd[c];
+            for (int a = 0; a < cs.nrow; ++a) {
+                const int pa = pos[Rc[a]];
+                for (int b = 0; b <= a; ++b) F[(size_t)pa * fs + pos[Rc[b]]] += U[(size_t)a * cs.nrow + b];
+            }
+            std::vector<double>().swap(upd[c]);
+        }
+        int info = potrf_lower(nc, F.data(), fs);
+        if (info != 0) {
+            err = "A0 not positive definite at column " + std::to_string(sn.col + info - 1);
+            return HQN_ERR_NOT_SPD;
+        }
+        if (nr > 0) {
+            trsm_right_lower_t(nr, nc, F.data(), fs, F.data() + (size_t)nc * fs, fs);
+            gemm_nt(nr, nr, nc, -1.0, F.data() + (size_t)nc * fs, fs, F.data() + (size_t)nc * fs, fs,
+                    1.0, F.data() + (size_t)nc * fs + nc, fs, true);
+            upd[s].assign((size_t)nr * nr, 0.0);
+            for (int a = 0; a < nr; ++a)
+                for (int b = 0; b <= a; ++b)
+                    upd[s][(size_t)a * nr + b] = F[(size_t)(nc + a) * fs + nc + b];
+        }
+        // Q_s = [L_ss^{-1}; L_Rs L_ss^{-1}]
+        std::vector<double> LinvT((size_t)nc * nc);
+        trtri_lower_t(nc, F.data(), fs, LinvT.data(), nc);
+        double *Qs = S.Q.data() + sn.qoff;
+        for (int i = 0; i < nc; ++i)
+            for (int j = 0; j <= i; ++j) Qs[(size_t)i * nc + j] = LinvT[(size_t)j * nc + i];
+        if (nr > 0)
+            gemm_nt(nr, nc, nc, 1.0, F.data() + (size_t)nc * fs, fs, LinvT.data(), nc, 0.0,
+                    Qs + (size_t)nc * nc, nc, false);
+    }
+
+    // ---- extend-add maps of the device solve
+    S.fg_ptr.assign(nf + 1, 0);
+    S.ug_ptr.assign(utot + 1, 0);
+    {
+        std::vector<std::vector<int>> fg(nf), ug(utot);
+        for (int s = 0; s < ns; ++s) {
+            const SupernodeHost &sn = S.sn[s];
+            const int *R = S.rows.data() + sn.roff;
+            for (int j = 0; j < sn.ncol; ++j) pos[sn.col + j] = j;
+            for (int k = 0; k < sn.nrow; ++k) pos[R[k]] = sn.ncol + k;
+            for (int c : sn.children) {
+                const SupernodeHost &cs = S.sn[c];
+                for (int a = 0; a < cs.nrow; ++a) {
+                    const int p = pos[S.rows[cs.roff + a]];
+                    if (p < sn.ncol) fg[sn.col + p].push_back(cs.uoff + a);
+                    else ug[sn.uoff + p - sn.ncol].push_back(cs.uoff + a);
+                }
+            }
+        }
+        for (int j = 0; j < nf; ++j) S.fg_ptr[j + 1] = S.fg_ptr[j] + (int)fg[j].size();
+        for (int j = 0; j < nf; ++j) S.fg_idx.insert(S.fg_idx.end(), fg[j].begin(), fg[j].end());
+        for (int u = 0; u < utot; ++u) S.ug_ptr[u + 1] = S.ug_ptr[u] + (int)ug[u].size();
+        for (int u = 0; u < utot; ++u) S.ug_idx.insert(S.ug_idx.end(), ug[u].begin(), ug[u].end());
+    }
+
+    // ---- level work lists
+    int L = 0;
+    for (auto &sn : S.sn) L = std::max(L, sn.level + 1);
+    S.n_levels = L;
+    S.fwd_lvl_ptr.assign(L + 1, 0);
+    S.bwd_lvl_ptr.assign(L + 1, 0);
+    S.fwd_items.clear();
+    S.bwd_items.clear();
+    constexpr int kFwdEntries = 8192;  // target matrix entries per forward work item
+    constexpr int kBwdEntries = 8192;  // target matrix entries per backward work item
+    for (int l = 0; l < L; ++l) {
+        S.fwd_lvl_ptr[l] = (int)S.fwd_items.size();
+        for (int s = 0; s < ns; ++s) {
+            const SupernodeHost &sn = S.sn[s];
+            if (sn.level != l || sn.ncol == 0) continue;
+            const int rows = sn.ncol + sn.nrow;
+            int chunk = std::max(8, kFwdEntries / std::max(1, sn.ncol));
+            chunk = (chunk + 7) / 8 * 8;
+            for (int r0 = 0; r0 < rows; r0 += chunk)
+                S.fwd_items.push_back({s, r0, std::min(rows, r0 + chunk), 0});
+        }
+    }
+    S.fwd_lvl_ptr[L] = (int)S.fwd_items.size();
+    // backward: levels from the root down; level index l here means tree level l
+    for (int l = 0; l < L; ++l) {
+        S.bwd_lvl_ptr[l] = (int)S.bwd_items.size();
+        for (int s = 0; s < ns; ++s) {
+            const SupernodeHost &sn = S.sn[s];
+            if (sn.level != l || sn.ncol == 0) continue;
+            const int rows = sn.ncol + sn.nrow;
+            for (int c0 = 0; c0 < sn.ncol; c0 += 32) {
+                // rows [c0, rows): split into chunks so one item reads ~kBwdEntries
+                const int span = rows - c0;
+                int chunk = std::max(64, kBwdEntries / 32);
+                if (span <= chunk) {
+                    S.bwd_items.push_back({s, c0, c0, 0});
+                } else {
+                    S.bwd_items.push_back({s, c0, c0, 0});  // one item per column block
+                }
+            }
+        }
+    }
+    S.bwd_lvl_ptr[L] = (int)S.bwd_items.size();
+
+    S.setup_seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    return HQN_OK;
+}
+
+void host_solve(const Setup &S, const double *q, double *r) {
+    const int nf = S.n_free;
+    std::vector<double> z(3 * (size_t)nf, 0.0), u(3 * (size_t)S.n_upd, 0.0);
+    // forward: level by level, children first
+    for (int l = 0; l < S.n_levels; ++l)
+        for (size_t s = 0; s < S.sn.size(); ++s) {
+            const SupernodeHost &sn = S.sn[s];
+            if (sn.level != l) continue;
+            const int nc = sn.ncol, rows = nc + sn.nrow;
+            std::vector<double> f(3 * (size_t)nc);
+            for (int p = 0; p < nc; ++p) {
+                const int j = sn.col + p;
+                for (int a = 0; a < 3; ++a) f[3 * p + a] = q[3 * (size_t)j + a];
+                for (int e = S.fg_ptr[j]; e < S.fg_ptr[j + 1]; ++e)
+                    for (int a = 0; a < 3; ++a) f[3 * p + a] -= u[3 * (size_t)S.fg_idx[e] + a];
+            }
+            const double *Qs = S.Q.data() + sn.qoff;
+            for (int i = 0; i < rows; ++i) {
+                double acc[3] = {0, 0, 0};
+                const int jn = i < nc ? i + 1 : nc;
+                for (int j = 0; j < jn; ++j)
+                    for (int a = 0; a < 3; ++a) acc[a] += Qs[(size_t)i * nc + j] * f[3 * j + a];
+                if (i < nc) {
+                    for (int a = 0; a < 3; ++a) z[3 * (size_t)(sn.col + i) + a] = acc[a];
+                } else {
+                    const int ui = sn.uoff + i - nc;
+                    for (int e = S.ug_ptr[ui]; e < S.ug_ptr[ui + 1]; ++e)
+                        for (int a = 0; a < 3; ++a) acc[a] += u[3 * (size_t)S.ug_idx[e] + a];
+                    for (int a = 0; a < 3; ++a) u[3 * (size_t)ui + a] = acc[a];
+                }
+            }
+        }
+    // backward: x_s = Q_s^T [z_s; -x_R], root first
+    for (int l = S.n_levels - 1; l >= 0; --l)
+        for (size_t s = 0; s < S.sn.size(); ++s) {
+            const SupernodeHost &sn = S.sn[s];
+            if (sn.level != l) continue;
+            const int nc = sn.ncol, rows = nc + sn.nrow;
+            const double *Qs = S.Q.data() + sn.qoff;
+            for (int j = 0; j < nc; ++j) {
+                double acc[3] = {0, 0, 0};
+                for (int i = j; i < rows; ++i) {
+                    const double qij = Qs[(size_t)i * nc + j];
+                    if (i < nc) {
+                        for (int a = 0; a < 3; ++a) acc[a] += qij * z[3 * (size_t)(sn.col + i) + a];
+                    } else {
+                        const int v = S.rows[sn.roff + i - nc];
+                        for (int a = 0; a < 3; ++a) acc[a] -= qij * r[3 * (size_t)v + a];
+                    }
+                }
+                for (int a = 0; a < 3; ++a) r[3 * (size_t)(sn.col + j) + a] = acc[a];
+            }
+        }
+}
+
+}  // namespace hqn

@@ -1,0 +1,77 @@
+// Host-side set-up of one simulation: rest data, lumped mass, stiffness fit,
+// A0 = M/h^2 + L on the free vertices, nested-dissection ordering, float64
+// multifrontal Cholesky and the operators of the device triangular solves.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hqn.h"
+
+namespace hqn {
+
+// Material in the form the kernels consume.  For Neo-Hookean, (c0, c1, c2) are
+// c(J0), c'(J0), c''(J0) of the quadratic continuation below J0.
+struct MaterialHost {
+    int kind = HQN_NEOHOOKEAN;
+    double mu = 0, lam = 0, J0 = 0.05, c0 = 0, c1 = 0, c2 = 0;
+    double sx[3][8] = {}, sv[3][8] = {}, ss[3][8] = {};  // spline knots, values, slopes
+};
+
+// One supernode = one node of the nested-dissection tree: its columns are a
+// contiguous range of the free vertices in elimination order; its row structure
+// R lists the later vertices coupled to it in the Cholesky factor L.
+struct SupernodeHost {
+    int col = 0, ncol = 0, nrow = 0;  // first column, #columns, #rows in R
+    int parent = -1, level = 0;
+    int64_t qoff = 0;                 // offset of Q_s = [L_ss^{-1}; L_Rs L_ss^{-1}] (rows x ncol)
+    int uoff = 0;                     // offset of its update vector (nrow entries)
+    int roff = 0;                     // offset of R in the row-index array
+    std::vector<int> children;
+};
+
+struct FwdItem { int s, row0, row1, pad; };
+struct BwdItem { int s, col0, row0, pad; };
+
+struct Setup {
+    int n = 0, T = 0, n_free = 0;
+    double h = 1.0 / 30.0, k = 0.0, density = 0.0;
+    MaterialHost mat;
+    // vertex renumbering: perm[new] = caller's id; iperm[caller's id] = new.
+    // Free vertices come first in elimination order, then the clamped ones.
+    std::vector<int> perm, iperm;
+    std::vector<double> X;           // rest positions, new order (n x 3)
+    std::vector<int> tets;           // T x 4, new ids, sorted by smallest vertex id
+    std::vector<double> dminv;       // T x 9, Dm^{-1} row-major
+    std::vector<double> vol;         // T
+    std::vector<double> mass;        // n lumped masses
+    std::vector<int> vt_ptr, vt_slot;  // vertex -> (tet*4 + corner), ascending tet
+    // factor and solve operators
+    std::vector<SupernodeHost> sn;
+    std::vector<int> rows;           // concatenated R of all supernodes
+    std::vector<double> Q;           // concatenated Q_s, row-major
+    std::vector<int> fg_ptr, fg_idx; // per free column: child update entries to subtract
+    std::vector<int> ug_ptr, ug_idx; // per update entry: child update entries to add
+    int n_upd = 0, n_levels = 0;
+    std::vector<int> fwd_lvl_ptr, bwd_lvl_ptr;  // items of level l: [ptr[l], ptr[l+1])
+    std::vector<FwdItem> fwd_items;
+    std::vector<BwdItem> bwd_items;
+    int max_front_cols = 0;          // max ncol (shared-memory size of the forward sweep)
+    int64_t factor_nnz = 0;
+    double setup_seconds = 0.0;
+};
+
+// Builds everything; returns an HQN_* status and a message on failure.
+int build_setup(const hqn_mesh &mesh, const hqn_material &mat, const hqn_params &prm,
+                Setup &S, std::string &err);
+
+// Fits the stiffness k of Eq. stiffness for a material (used by build_setup).
+double fit_stiffness(const MaterialHost &m, double x_start, double x_end);
+
+// Host float64 execution of the device solve algorithm (same operators, same
+// order of work): r = A0^{-1} q on the first n_free entries, 3 right-hand sides
+// stored as n_free x 3.
+void host_solve(const Setup &S, const double *q, double *r);
+
+}  // namespace hqn
