@@ -12,7 +12,8 @@ taken by the CUDA path, written separately):
   * projective-dynamics element energy read as (w/2)||G x - p||^2, so that
     L = sum_t w_t G_t^T G_t with w_t = V_t k_t (Eq. PDtotalEnergy, PDmatrixForm);
   * stiffness k = continuous least-squares slope of a'(s) + 2b'(s) + c'(s)
-    over [x_start, x_end] = [0.5, 1.5] (Eq. stiffness), by Gauss-Legendre quadrature;
+    over [x_start, x_end] = [0.5, 1.5] (Eq. stiffness), by Gauss-Legendre
+    quadrature split at the material's breakpoints (spline knots, J0);
   * Neo-Hookean in Valanis-Landel form a = mu/2 (x^2 - 1), b = 0,
     c(J) = -mu ln J + lam/2 ln^2 J, with c replaced by its second-order Taylor
     polynomial at J0 = 0.05 for J < J0 (finite for inverted tets);
@@ -48,6 +49,7 @@ J0_NEOHOOKEAN = 0.05
 # ----------------------------------------------------------------------------
 
 class VLMaterial:
+    def breakpoints(self): return ()
     def a(self, x): return np.zeros_like(x)
     def da(self, x): return np.zeros_like(x)
     def b(self, y): return np.zeros_like(y)
@@ -61,6 +63,8 @@ class NeoHookean(VLMaterial):
 
     def __init__(self, mu, lam, J0=J0_NEOHOOKEAN):
         self.mu, self.lam, self.J0 = mu, lam, J0
+
+    def breakpoints(self): return (self.J0,)
 
     def a(self, x): return 0.5 * self.mu * (x * x - 1.0)
     def da(self, x): return self.mu * x
@@ -188,6 +192,9 @@ class SplineVL(VLMaterial):
         control = np.asarray(control, dtype=np.float64)
         self.sa, self.sb, self.sc = (HermiteSpline(control[f]) for f in range(3))
 
+    def breakpoints(self):
+        return tuple(self.sa.x) + tuple(self.sb.x) + tuple(self.sc.x)
+
     def a(self, x): return self.sa(x)
     def da(self, x): return self.sa.deriv(x)
     def b(self, y): return self.sb(y)
@@ -236,14 +243,20 @@ def dpsi(mat: VLMaterial, s):
 
 def stiffness_k(mat: VLMaterial, x_start=0.5, x_end=1.5, npts=64):
     """Eq. stiffness: slope of the least-squares line through
-    f(s) = a'(s) + 2 b'(s) + c'(s) on [x_start, x_end] (continuous fit)."""
+    f(s) = a'(s) + 2 b'(s) + c'(s) on [x_start, x_end] (continuous fit),
+    k = int (s - sbar) f ds / int (s - sbar)^2 ds.  The integral is split at
+    the material's breakpoints (spline knots, the Neo-Hookean J0) so that each
+    piece is smooth; Gauss-Legendre with npts nodes per piece."""
     t, w = np.polynomial.legendre.leggauss(npts)
-    half = 0.5 * (x_end - x_start)
     mid = 0.5 * (x_end + x_start)
-    s = mid + half * t
-    f = mat.da(s) + 2.0 * mat.db(s) + mat.dc(s)
-    num = half * np.sum(w * (s - mid) * f)
-    den = half * np.sum(w * (s - mid) ** 2)
+    cuts = sorted({x_start, x_end} | {float(b) for b in mat.breakpoints() if x_start < b < x_end})
+    num = 0.0
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        half = 0.5 * (b - a)
+        s = 0.5 * (a + b) + half * t
+        f = mat.da(s) + 2.0 * mat.db(s) + mat.dc(s)
+        num += half * np.sum(w * (s - mid) * f)
+    den = (x_end - x_start) ** 3 / 12.0
     return num / den
 
 

@@ -150,6 +150,20 @@ def test_stiffness_closed_forms():
     assert abs(O.stiffness_k(O.Poly4(3 * mu)) - 3 * k_poly) < 1e-9 * k_poly
 
 
+def test_stiffness_spline_matches_brute_force_integral():
+    """Eq. stiffness for a spline material, whose integrand is only piecewise
+    smooth: the oracle's k equals the defining integral ratio evaluated by a
+    composite midpoint rule on 2e6 cells (error O(h^2) ~ 1e-12 per piece)."""
+    mu, lam = O.lame(5e5, 0.4)
+    ctrl = W.spline_control_points(mu, lam, np.random.default_rng(1606))
+    mat = O.SplineVL(ctrl)
+    n = 2_000_000
+    s = 0.5 + (np.arange(n) + 0.5) / n
+    f = mat.da(s) + 2.0 * mat.db(s) + mat.dc(s)
+    k_brute = np.sum((s - 1.0) * f) / n / (1.0 / 12.0)
+    assert abs(O.stiffness_k(mat) - k_brute) < 1e-9 * abs(k_brute)
+
+
 def test_paper_parameters_golden():
     with open(os.path.join(GOLDEN, "paper_parameters.json")) as f:
         g = json.load(f)
