@@ -98,6 +98,11 @@ typedef struct {
     int32_t ls_max;       /* line-search trials before giving up (paper is silent)    */
     int32_t precision;    /* hqn_precision                                            */
     int32_t leaf_size;    /* max vertices of a nested-dissection leaf (0 = default 64) */
+    int32_t use_graph;    /* 1 = run each step as one CUDA graph with conditional
+                             (while / if) nodes for the iteration and line-search
+                             loops; 0 = host-driven launches (same kernels)        */
+    int32_t tet_block;    /* threads per block of the tet kernel: 64, 128 or 256
+                             (0 = default 128)                                     */
 } hqn_params;
 
 #define HQN_MAX_HISTORY 16
@@ -123,12 +128,16 @@ typedef struct {
     double  stiffness_k;        /* fitted k of Eq. stiffness                          */
     double  setup_seconds;      /* host time spent in sim_create                      */
     int64_t device_bytes;       /* device memory held by the handle                   */
+    int32_t precision;          /* hqn_precision in use                               */
+    int32_t graph_mode;         /* 1 if steps run as a CUDA graph                     */
+    int64_t n_update_entries;   /* entries of the forward-sweep update vectors        */
 } hqn_info;
 
 typedef struct sim_handle sim_handle;
 
 /* Paper defaults: h = 1/30, gamma = 0.3, backtrack = 0.5, [0.5, 1.5], gravity
- * (0, 0, -9.81), 10 iterations, m = 5, ls_max = 30, FP32_MIXED, leaf 64. */
+ * (0, 0, -9.81), 10 iterations, m = 5, ls_max = 30, FP32_MIXED, leaf 64,
+ * graph mode on, tet block 128. */
 void hqn_default_params(hqn_params *p);
 
 /* Builds a simulation: rest data (Dm^-1, volumes, lumped mass), the stiffness k
@@ -173,6 +182,9 @@ int sim_direction(sim_handle *sim, const double *grad, int32_t npairs,
 int  sim_get_info(const sim_handle *sim, hqn_info *info);
 void sim_destroy(sim_handle *sim);
 const char *sim_strerror(int code);
+
+/* Message of the last error raised on the calling thread ("" if none). */
+const char *hqn_last_error(void);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,81 @@
+// Device-side types shared by the kernels and the host orchestration of the
+// quasi-Newton implicit-Euler step (Alg. 1 with the L-BFGS direction of Alg. 2).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hqn.h"
+
+namespace hqn {
+
+// One vertex's 3-vector, padded to 16 B (float) or 32 B (double) so a gather
+// of a vertex is one aligned vector load.  The pad lane w is kept at zero.
+template <typename R>
+struct alignas(4 * sizeof(R)) V4 {
+    R x, y, z, w;
+};
+
+// Material as the tet kernel consumes it (Eq. valanis-landel).  For the
+// spline material each of a, b, c is 7 cubic segments p0 + u(p1 + u(p2 + u p3)),
+// u = (t - x_i) * inv_h, over knots x_0..x_7, continued quadratically outside.
+template <typename R>
+struct MatDev {
+    int kind;
+    R mu, lam;          // Lame parameters
+    R J0, c0, c1, c2;   // Neo-Hookean: c(J0), c'(J0), c''(J0) of the continuation below J0
+    R kx[3][8];         // spline knots of a, b, c
+    R inv_h[3][7];
+    R p[3][7][4];
+};
+
+// Control block of one simulation's step, resident on the device.  Every
+// scalar decision of Alg. 1 / Alg. 2 (inner products, alpha, Armijo, history
+// bookkeeping) is taken here, by the last block of the kernel that produces
+// its inputs, so a step runs without host round trips.
+struct Ctl {
+    double g_k;        // g(x_k)
+    double g_trial;    // g at the current line-search trial
+    double gd;         // tr(grad_k^T d)
+    double alpha;      // current step length
+    double g0;         // g(x_1), x_1 = y
+    double dot;        // scratch: last finalised inner product
+    double zeta[HQN_MAX_HISTORY + 1];  // first-loop coefficients by age (0 = newest)
+    double rho[HQN_MAX_HISTORY + 1];   // tr(t^T s) by ring slot
+    double iter_g[HQN_MAX_ITERS];
+    int iter_trials[HQN_MAX_ITERS];
+    int k;             // 1-based iteration index of x_k
+    int trials;        // trials of the current line search
+    int count;         // history pairs held (<= m)
+    int head;          // ring slot of the newest pair (ring has m + 1 slots)
+    int stop;          // the step's iterations have ended early
+    int status;        // worst status of the step (HQN_OK or a warning)
+    int accepted;      // the last trial passed the Armijo test
+    int nondescent;    // tr(grad^T d) >= 0 with history: reset and recompute
+    int trials_total;  // over the steps since the host last cleared it
+    int iters_total;
+    int steps;
+    int worst_status;
+    unsigned int ticket[8];  // arrival counters of the last-block reductions
+};
+
+// Ticket slots (one per kernel family so consecutive kernels never share one).
+enum { TK_TRIAL = 0, TK_TET = 1, TK_GATHER = 2, TK_VEC = 3, TK_PUSH = 4, TK_DOT = 5 };
+
+// Graph conditional handles a kernel may set (0 = not inside a graph).
+struct CondHandles {
+    unsigned long long it;   // while: iterations of the step
+    unsigned long long ls;   // while: line-search trials
+    unsigned long long nd;   // if: non-descent reset of the direction
+};
+
+// Per-simulation constants passed by value.
+template <typename R>
+struct StepConst {
+    int n, nf, T, m, iters, ls_max;
+    R h2;              // h^2
+    R gx, gy, gz;      // h^2 * gravity (the h^2 M^{-1} f_ext term of Eq. PD)
+    double gamma, backtrack;
+};
+
+}  // namespace hqn

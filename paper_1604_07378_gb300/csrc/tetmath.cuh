@@ -1,0 +1,300 @@
+// Per-tetrahedron mathematics of the energy/gradient kernel: deformation
+// gradient from displacements, signed 3x3 SVD, Valanis-Landel stress in
+// principal stretches (Eq. valanis-landel) and the corner gradients.
+//
+// Precision design.  The kernels store displacements u = x - X, so
+// F = I + G with G = [u1-u0, u2-u0, u3-u0] Dm^{-1} carries the strain at the
+// relative precision of the arithmetic instead of being the difference of two
+// nearly equal absolute positions.  The symmetric eigenproblem is solved for
+// S = F^T F - I = G + G^T + G^T G, whose eigenvalues are l_i = s_i^2 - 1, so
+// every material below is written in terms of l_i and s_i and no term of
+// size mu is cancelled against another near the rest state.
+#pragma once
+
+#include "common.cuh"
+
+namespace hqn {
+
+template <typename R> __device__ __forceinline__ R rsqrt_(R v);
+template <> __device__ __forceinline__ float rsqrt_<float>(float v) { return rsqrtf(v); }
+template <> __device__ __forceinline__ double rsqrt_<double>(double v) { return rsqrt(v); }
+
+template <typename R> __device__ __forceinline__ R sqrt_(R v) { return sqrt(v); }
+template <typename R> __device__ __forceinline__ R log1p_(R v) { return log1p(v); }
+template <typename R> __device__ __forceinline__ R abs_(R v) { return fabs(v); }
+
+template <typename R> struct Eps;
+template <> struct Eps<float> { static constexpr float v = 1.1920929e-7f; };
+template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
+
+// x - log(1 + x) without cancellation: its Taylor series sum_{k>=2} (-1)^k x^k / k
+// for |x| < 0.1 (truncation below 1e-11 relative), the direct form elsewhere.
+template <typename R>
+__device__ __forceinline__ R x_minus_log1p(R x) {
+    if (abs_(x) < R(0.1)) {
+        R s = R(0);
+        R pk = x * x;  // x^k, k = 2
+#pragma unroll
+        for (int k = 2; k <= 12; ++k) {
+            s += ((k & 1) ? -pk : pk) / R(k);
+            pk *= x;
+        }
+        return s;
+    }
+    return x - log1p_(x);
+}
+
+// One Jacobi rotation zeroing A[p][q] of the symmetric 3x3 A (Golub & Van Loan,
+// "Matrix Computations", the symmetric Schur decomposition of Sec. 8.5), with
+// the rotation accumulated into the columns of V.
+template <typename R, int p, int q>
+__device__ __forceinline__ void jacobi_rotate(R A[3][3], R V[3][3]) {
+    const R apq = A[p][q];
+    if (apq == R(0)) return;
+    const R theta = (A[q][q] - A[p][p]) / (R(2) * apq);
+    R t;
+    if (abs_(theta) > R(1e15)) t = R(0.5) / theta;
+    else t = (theta >= R(0) ? R(1) : R(-1)) / (abs_(theta) + sqrt_(theta * theta + R(1)));
+    const R c = rsqrt_(t * t + R(1));
+    const R s = t * c;
+    constexpr int r = 3 - p - q;
+    A[p][p] -= t * apq;
+    A[q][q] += t * apq;
+    A[p][q] = A[q][p] = R(0);
+    const R arp = A[r][p], arq = A[r][q];
+    A[r][p] = A[p][r] = c * arp - s * arq;
+    A[r][q] = A[q][r] = s * arp + c * arq;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const R vp = V[i][p], vq = V[i][q];
+        V[i][p] = c * vp - s * vq;
+        V[i][q] = s * vp + c * vq;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void swap_cols(R l[3], R V[3][3], int a, int b) {
+    R t = l[a]; l[a] = l[b]; l[b] = t;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { R v = V[i][a]; V[i][a] = V[i][b]; V[i][b] = v; }
+}
+
+// Signed SVD of F = I + G in the invertible-element convention: F = U diag(s) V^T,
+// U, V in SO(3), s1 >= s2 >= |s3|, s3 < 0 exactly when det F < 0.  Also returns
+// l_i = s_i^2 - 1 at the precision of G.
+//   1. Cyclic Jacobi on S = G + G^T + G^T G gives l and V (sorted, det V = +1).
+//   2. U from a Gram-Schmidt QR of B = F V: u1 = b1/|b1|, u2 from b2, u3 = u1 x u2.
+//   3. s_i = sqrt(1 + l_i) where l_i > -1/2 (relative precision near rest);
+//      below that, s_i = u_i . b_i, the R diagonal of the QR, which keeps the
+//      precision of nearly collapsed and inverted elements; l_i is then recomputed.
+template <typename R>
+__device__ __forceinline__ void signed_svd(const R G[3][3], R U[3][3], R s[3], R l[3], R V[3][3]) {
+    R A[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            A[a][b] = G[a][b] + G[b][a] + G[0][a] * G[0][b] + G[1][a] * G[1][b] + G[2][a] * G[2][b];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) V[a][b] = a == b ? R(1) : R(0);
+    for (int sweep = 0; sweep < 8; ++sweep) {
+        const R off = abs_(A[0][1]) + abs_(A[0][2]) + abs_(A[1][2]);
+        const R dia = abs_(A[0][0]) + abs_(A[1][1]) + abs_(A[2][2]);
+        if (!(off > R(0.25) * Eps<R>::v * dia)) break;
+        jacobi_rotate<R, 0, 1>(A, V);
+        jacobi_rotate<R, 0, 2>(A, V);
+        jacobi_rotate<R, 1, 2>(A, V);
+    }
+    l[0] = A[0][0]; l[1] = A[1][1]; l[2] = A[2][2];
+    if (l[0] < l[1]) swap_cols(l, V, 0, 1);
+    if (l[0] < l[2]) swap_cols(l, V, 0, 2);
+    if (l[1] < l[2]) swap_cols(l, V, 1, 2);
+    const R detV = V[0][0] * (V[1][1] * V[2][2] - V[1][2] * V[2][1]) -
+                   V[0][1] * (V[1][0] * V[2][2] - V[1][2] * V[2][0]) +
+                   V[0][2] * (V[1][0] * V[2][1] - V[1][1] * V[2][0]);
+    if (detV < R(0)) { V[0][2] = -V[0][2]; V[1][2] = -V[1][2]; V[2][2] = -V[2][2]; }
+    // B = F V = V + G V
+    R B[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) B[a][i] = V[a][i] + G[a][0] * V[0][i] + G[a][1] * V[1][i] + G[a][2] * V[2][i];
+    // u1
+    R n1 = sqrt_(B[0][0] * B[0][0] + B[1][0] * B[1][0] + B[2][0] * B[2][0]);
+    R u1[3];
+    if (n1 > R(1e-30)) {
+        const R inv = R(1) / n1;
+        u1[0] = B[0][0] * inv; u1[1] = B[1][0] * inv; u1[2] = B[2][0] * inv;
+    } else {
+        u1[0] = R(1); u1[1] = R(0); u1[2] = R(0);
+        n1 = R(0);
+    }
+    // u2
+    const R d12 = u1[0] * B[0][1] + u1[1] * B[1][1] + u1[2] * B[2][1];
+    R w[3] = {B[0][1] - d12 * u1[0], B[1][1] - d12 * u1[1], B[2][1] - d12 * u1[2]};
+    R n2 = sqrt_(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    R u2[3];
+    if (n2 > R(64) * Eps<R>::v * (n1 > R(1) ? n1 : R(1))) {
+        const R inv = R(1) / n2;
+        u2[0] = w[0] * inv; u2[1] = w[1] * inv; u2[2] = w[2] * inv;
+    } else {
+        // any unit vector orthogonal to u1
+        R e[3] = {R(0), R(0), R(0)};
+        const int k = (abs_(u1[0]) <= abs_(u1[1]) && abs_(u1[0]) <= abs_(u1[2])) ? 0
+                      : (abs_(u1[1]) <= abs_(u1[2]) ? 1 : 2);
+        e[k] = R(1);
+        R dd = u1[0] * e[0] + u1[1] * e[1] + u1[2] * e[2];
+        R v2[3] = {e[0] - dd * u1[0], e[1] - dd * u1[1], e[2] - dd * u1[2]};
+        const R inv = rsqrt_(v2[0] * v2[0] + v2[1] * v2[1] + v2[2] * v2[2]);
+        u2[0] = v2[0] * inv; u2[1] = v2[1] * inv; u2[2] = v2[2] * inv;
+        n2 = u2[0] * B[0][1] + u2[1] * B[1][1] + u2[2] * B[2][1];
+    }
+    const R u3[3] = {u1[1] * u2[2] - u1[2] * u2[1], u1[2] * u2[0] - u1[0] * u2[2],
+                     u1[0] * u2[1] - u1[1] * u2[0]};
+    const R n3 = u3[0] * B[0][2] + u3[1] * B[1][2] + u3[2] * B[2][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) { U[a][0] = u1[a]; U[a][1] = u2[a]; U[a][2] = u3[a]; }
+    const R half = R(-0.5);
+    if (l[0] > half) s[0] = sqrt_(R(1) + l[0]);
+    else { s[0] = n1; l[0] = n1 * n1 - R(1); }
+    if (l[1] > half) s[1] = sqrt_(R(1) + l[1]);
+    else { s[1] = n2; l[1] = n2 * n2 - R(1); }
+    if (l[2] > half) s[2] = n3 >= R(0) ? sqrt_(R(1) + l[2]) : -sqrt_(R(1) + l[2]);
+    else { s[2] = n3; l[2] = n3 * n3 - R(1); }
+}
+
+// s - 1 from (s, l = s^2 - 1) without cancellation near s = 1.
+template <typename R>
+__device__ __forceinline__ R stretch_minus_one(R s, R l) {
+    return s > R(0.5) ? l / (s + R(1)) : s - R(1);
+}
+
+// Cubic Hermite segment evaluation with quadratic continuation outside the knots.
+template <typename R>
+__device__ __forceinline__ void spline_eval(const MatDev<R> &M, int f, R t, R &val, R &der) {
+    const R lo = M.kx[f][0], hi = M.kx[f][7];
+    const R tc = t < lo ? lo : (t > hi ? hi : t);
+    int i = 0;
+#pragma unroll
+    for (int k = 1; k < 7; ++k) i = tc >= M.kx[f][k] ? k : i;
+    const R ih = M.inv_h[f][i];
+    const R u = (tc - M.kx[f][i]) * ih;
+    const R *p = M.p[f][i];
+    const R v = p[0] + u * (p[1] + u * (p[2] + u * p[3]));
+    const R d = (p[1] + u * (R(2) * p[2] + R(3) * u * p[3])) * ih;
+    const R dd = (R(2) * p[2] + R(6) * u * p[3]) * ih * ih;
+    const R dt = t - tc;
+    val = v + dt * (d + R(0.5) * dd * dt);
+    der = d + dd * dt;
+}
+
+// Energy density Psi and tau_i = dPsi/ds_i from (s, l) for the material.
+template <typename R>
+__device__ __forceinline__ R material_tau(const MatDev<R> &M, const R s[3], const R l[3], R tau[3]) {
+    const R mu = M.mu, lam = M.lam;
+    const R J = s[0] * s[1] * s[2];
+    switch (M.kind) {
+        case HQN_NEOHOOKEAN: {
+            // a = mu/2 (x^2 - 1), c = -mu ln J + lam/2 ln^2 J (Taylor below J0)
+            if (J >= M.J0) {
+                const R lnJ = R(0.5) * (log1p_(l[0]) + log1p_(l[1]) + log1p_(l[2]));
+                const R psi = R(0.5) * mu * (x_minus_log1p(l[0]) + x_minus_log1p(l[1]) + x_minus_log1p(l[2])) +
+                              R(0.5) * lam * lnJ * lnJ;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) tau[i] = (mu * l[i] + lam * lnJ) / s[i];
+                return psi;
+            }
+            const R dJ = J - M.J0;
+            const R dc = M.c1 + M.c2 * dJ;
+            const R psi = R(0.5) * mu * (l[0] + l[1] + l[2]) + M.c0 + dJ * (M.c1 + R(0.5) * M.c2 * dJ);
+            tau[0] = mu * s[0] + dc * s[1] * s[2];
+            tau[1] = mu * s[1] + dc * s[0] * s[2];
+            tau[2] = mu * s[2] + dc * s[0] * s[1];
+            return psi;
+        }
+        case HQN_STVK: {
+            // mu sum e_i^2 + lam/2 (sum e_i)^2, e_i = (s_i^2 - 1)/2
+            const R e0 = R(0.5) * l[0], e1 = R(0.5) * l[1], e2 = R(0.5) * l[2];
+            const R tr = e0 + e1 + e2;
+            tau[0] = (R(2) * mu * e0 + lam * tr) * s[0];
+            tau[1] = (R(2) * mu * e1 + lam * tr) * s[1];
+            tau[2] = (R(2) * mu * e2 + lam * tr) * s[2];
+            return mu * (e0 * e0 + e1 * e1 + e2 * e2) + R(0.5) * lam * tr * tr;
+        }
+        case HQN_COROTATED: {
+            // a = mu (x-1)^2, c = lam/2 (J-1)^2
+            const R d0 = stretch_minus_one(s[0], l[0]), d1 = stretch_minus_one(s[1], l[1]),
+                    d2 = stretch_minus_one(s[2], l[2]);
+            const R Jm1 = d0 + d1 + d2 + d0 * d1 + d0 * d2 + d1 * d2 + d0 * d1 * d2;
+            tau[0] = R(2) * mu * d0 + lam * Jm1 * s[1] * s[2];
+            tau[1] = R(2) * mu * d1 + lam * Jm1 * s[0] * s[2];
+            tau[2] = R(2) * mu * d2 + lam * Jm1 * s[0] * s[1];
+            return mu * (d0 * d0 + d1 * d1 + d2 * d2) + R(0.5) * lam * Jm1 * Jm1;
+        }
+        case HQN_POLY4: {
+            // a = mu (x-1)^4
+            R psi = R(0);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const R d = stretch_minus_one(s[i], l[i]);
+                const R d2 = d * d;
+                psi += mu * d2 * d2;
+                tau[i] = R(4) * mu * d2 * d;
+            }
+            return psi;
+        }
+        default: {  // HQN_SPLINE_VL
+            R va0, da0, va1, da1, va2, da2;
+            spline_eval(M, 0, s[0], va0, da0);
+            spline_eval(M, 0, s[1], va1, da1);
+            spline_eval(M, 0, s[2], va2, da2);
+            R vb01, db01, vb02, db02, vb12, db12;
+            spline_eval(M, 1, s[0] * s[1], vb01, db01);
+            spline_eval(M, 1, s[0] * s[2], vb02, db02);
+            spline_eval(M, 1, s[1] * s[2], vb12, db12);
+            R vc, dc;
+            spline_eval(M, 2, J, vc, dc);
+            tau[0] = da0 + db01 * s[1] + db02 * s[2] + dc * s[1] * s[2];
+            tau[1] = da1 + db01 * s[0] + db12 * s[2] + dc * s[0] * s[2];
+            tau[2] = da2 + db02 * s[0] + db12 * s[1] + dc * s[0] * s[1];
+            return va0 + va1 + va2 + vb01 + vb02 + vb12 + vc;
+        }
+    }
+}
+
+// Energy V*Psi of one tet and its gradients with respect to the four corner
+// positions.  du[j] = u_{j} - u_0 (j = 1..3 as 0..2), Di = Dm^{-1} row-major.
+// First Piola P = U diag(tau) V^T; corners 1..3 get the columns of V P Dm^{-T},
+// corner 0 minus their sum.
+template <typename R>
+__device__ __forceinline__ R tet_energy_grad(const MatDev<R> &M, const R du[3][3], const R Di[9], R vol,
+                                             R g[4][3]) {
+    R G[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            G[a][b] = du[0][a] * Di[0 * 3 + b] + du[1][a] * Di[1 * 3 + b] + du[2][a] * Di[2 * 3 + b];
+    R U[3][3], s[3], l[3], V[3][3];
+    signed_svd(G, U, s, l, V);
+    R tau[3];
+    const R psi = material_tau(M, s, l, tau);
+    R P[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            P[a][b] = vol * (U[a][0] * tau[0] * V[b][0] + U[a][1] * tau[1] * V[b][1] + U[a][2] * tau[2] * V[b][2]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            g[j + 1][a] = P[a][0] * Di[j * 3 + 0] + P[a][1] * Di[j * 3 + 1] + P[a][2] * Di[j * 3 + 2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[0][a] = -(g[1][a] + g[2][a] + g[3][a]);
+    return vol * psi;
+}
+
+}  // namespace hqn

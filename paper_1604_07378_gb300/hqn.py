@@ -1,0 +1,245 @@
+"""ctypes binding of the solver's C ABI (``include/hqn.h``).
+
+Argument marshalling only: every step of the method runs inside the CUDA
+library.  The library must be built (``build.build_library()``); importing
+this module without it raises, and there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HQN_OK = 0
+HQN_WARN_LS_EXHAUSTED = 1
+HQN_WARN_NONDESCENT = 2
+HQN_ERR_ARG = -1
+HQN_ERR_DEGENERATE_TET = -2
+HQN_ERR_NONFINITE = -3
+HQN_ERR_NOT_SPD = -4
+HQN_ERR_CUDA = -5
+HQN_ERR_NO_MEMORY = -6
+HQN_ERR_UNSUPPORTED = -7
+
+NEOHOOKEAN, STVK, SPLINE_VL, COROTATED, POLY4 = 0, 1, 2, 3, 4
+FP64_PLAIN, FP32_MIXED = 0, 1
+MAX_HISTORY, MAX_ITERS = 16, 64
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_up = C.POINTER(C.c_uint8)
+
+
+class Mesh(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("n_tets", C.c_int32), ("rest_pos", _dp),
+                ("tets", _ip), ("clamped", _up)]
+
+
+class Material(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("E", C.c_double), ("nu", C.c_double),
+                ("density", C.c_double), ("spline", _dp)]
+
+
+class Params(C.Structure):
+    _fields_ = [("h", C.c_double), ("gamma", C.c_double), ("backtrack", C.c_double),
+                ("x_start", C.c_double), ("x_end", C.c_double), ("gravity", C.c_double * 3),
+                ("iters", C.c_int32), ("history_m", C.c_int32), ("ls_max", C.c_int32),
+                ("precision", C.c_int32), ("leaf_size", C.c_int32), ("use_graph", C.c_int32),
+                ("tet_block", C.c_int32)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("iters", C.c_int32), ("status", C.c_int32),
+                ("trials_total", C.c_int32), ("iters_total", C.c_int32),
+                ("trials", C.c_int32 * MAX_ITERS), ("g0", C.c_double),
+                ("g", C.c_double * MAX_ITERS)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("n_tets", C.c_int32), ("n_free", C.c_int32),
+                ("n_supernodes", C.c_int32), ("n_levels", C.c_int32),
+                ("factor_entries", C.c_int64), ("factor_nnz", C.c_int64),
+                ("stiffness_k", C.c_double), ("setup_seconds", C.c_double),
+                ("device_bytes", C.c_int64), ("precision", C.c_int32),
+                ("graph_mode", C.c_int32), ("n_update_entries", C.c_int64)]
+
+
+_lib = None
+
+
+def library(path: str | None = None):
+    """Loads libhqn.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        path = _build.build_library()
+    if not os.path.exists(path):
+        raise RuntimeError(f"solver library not found at {path}")
+    lib = C.CDLL(path)
+    lib.hqn_default_params.argtypes = [C.POINTER(Params)]
+    lib.hqn_default_params.restype = None
+    lib.sim_create.argtypes = [C.POINTER(Mesh), C.POINTER(Material), C.POINTER(Params), C.c_void_p,
+                               C.POINTER(C.c_void_p)]
+    lib.sim_create.restype = C.c_int
+    lib.sim_set_state.argtypes = [C.c_void_p, _dp, _dp]
+    lib.sim_get_state.argtypes = [C.c_void_p, _dp, _dp]
+    lib.sim_step.argtypes = [C.c_void_p, C.c_int32, C.POINTER(StepStats)]
+    lib.sim_energy_grad.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
+    lib.sim_solve_A0.argtypes = [C.c_void_p, _dp, _dp]
+    lib.sim_direction.argtypes = [C.c_void_p, _dp, C.c_int32, _dp, _dp, _dp]
+    lib.sim_get_info.argtypes = [C.c_void_p, C.POINTER(Info)]
+    lib.sim_destroy.argtypes = [C.c_void_p]
+    lib.sim_destroy.restype = None
+    lib.sim_strerror.argtypes = [C.c_int]
+    lib.sim_strerror.restype = C.c_char_p
+    lib.hqn_last_error.argtypes = []
+    lib.hqn_last_error.restype = C.c_char_p
+    for f in ("sim_set_state", "sim_get_state", "sim_step", "sim_energy_grad", "sim_solve_A0",
+              "sim_direction", "sim_get_info"):
+        getattr(lib, f).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class HQNError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+def _check(code, what):
+    if code < 0:
+        lib = library()
+        raise HQNError(code, f"{what}: {lib.sim_strerror(code).decode()}: "
+                             f"{lib.hqn_last_error().decode()}")
+    return code
+
+
+def _ptr(a, ctype=_dp):
+    return a.ctypes.data_as(ctype)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    library().hqn_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "gravity":
+            p.gravity[:] = list(v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Sim:
+    """One simulation handle (``sim_create`` ... ``sim_destroy``)."""
+
+    def __init__(self, rest_pos, tets, clamped=None, *, kind=NEOHOOKEAN, E=1e5, nu=0.45,
+                 density=1000.0, spline=None, params: Params | None = None, stream=None, **pkw):
+        lib = library()
+        self._X = np.ascontiguousarray(rest_pos, dtype=np.float64)
+        self._tets = np.ascontiguousarray(tets, dtype=np.int32)
+        self.n = self._X.shape[0]
+        self._cl = None if clamped is None else np.ascontiguousarray(clamped, dtype=np.uint8)
+        mesh = Mesh(self.n, self._tets.shape[0], _ptr(self._X), _ptr(self._tets, _ip),
+                    None if self._cl is None else _ptr(self._cl, _up))
+        self._spline = None if spline is None else np.ascontiguousarray(spline, dtype=np.float64)
+        mat = Material(kind, E, nu, density, None if self._spline is None else _ptr(self._spline))
+        self.params = params if params is not None else default_params(**pkw)
+        h = C.c_void_p()
+        _check(lib.sim_create(C.byref(mesh), C.byref(mat), C.byref(self.params),
+                              C.c_void_p(stream or 0), C.byref(h)), "sim_create")
+        self._h = h
+        self.last_status = 0
+
+    @classmethod
+    def from_workload(cls, w, **pkw):
+        m = w.material
+        pkw.setdefault("iters", w.iters)
+        pkw.setdefault("history_m", w.history)
+        pkw.setdefault("h", w.h)
+        pkw.setdefault("gravity", w.gravity)
+        return cls(w.rest_pos, w.tets, w.clamped, kind=m.kind, E=m.E, nu=m.nu,
+                   density=m.density, spline=m.spline, **pkw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            library().sim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _vec(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if a.shape != (self.n, 3):
+            raise ValueError(f"expected shape ({self.n}, 3), got {a.shape}")
+        return a
+
+    def set_state(self, q_cur, q_prev=None):
+        qc = self._vec(q_cur)
+        qp = None if q_prev is None else self._vec(q_prev)
+        _check(library().sim_set_state(self._h, _ptr(qc), None if qp is None else _ptr(qp)),
+               "sim_set_state")
+
+    def get_state(self):
+        qc = np.empty((self.n, 3))
+        qp = np.empty((self.n, 3))
+        _check(library().sim_get_state(self._h, _ptr(qc), _ptr(qp)), "sim_get_state")
+        return qc, qp
+
+    def step(self, nsteps=1, stats=False):
+        st = StepStats()
+        rc = _check(library().sim_step(self._h, nsteps, C.byref(st) if stats else None), "sim_step")
+        self.last_status = rc
+        if not stats:
+            return rc
+        k = st.iters
+        return rc, {"steps": st.steps, "iters": k, "status": st.status,
+                    "trials_total": st.trials_total, "iters_total": st.iters_total,
+                    "trials": list(st.trials[:k]), "g0": st.g0, "g": list(st.g[:k])}
+
+    def energy_grad(self, x, y):
+        x, y = self._vec(x), self._vec(y)
+        g = C.c_double()
+        grad = np.empty((self.n, 3))
+        _check(library().sim_energy_grad(self._h, _ptr(x), _ptr(y), C.byref(g), _ptr(grad)),
+               "sim_energy_grad")
+        return g.value, grad
+
+    def solve_A0(self, q):
+        q = self._vec(q)
+        r = np.empty((self.n, 3))
+        _check(library().sim_solve_A0(self._h, _ptr(q), _ptr(r)), "sim_solve_A0")
+        return r
+
+    def direction(self, grad, s_list=(), t_list=()):
+        grad = self._vec(grad)
+        npairs = len(s_list)
+        d = np.empty((self.n, 3))
+        if npairs:
+            s = np.ascontiguousarray(np.stack([self._vec(v) for v in s_list]))
+            t = np.ascontiguousarray(np.stack([self._vec(v) for v in t_list]))
+            sp, tp = _ptr(s), _ptr(t)
+        else:
+            sp = tp = None
+        _check(library().sim_direction(self._h, _ptr(grad), npairs, sp, tp, _ptr(d)),
+               "sim_direction")
+        return d
+
+    def info(self) -> dict:
+        i = Info()
+        _check(library().sim_get_info(self._h, C.byref(i)), "sim_get_info")
+        return {f: getattr(i, f) for f, _ in Info._fields_}

@@ -1,0 +1,178 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances follow the accuracy targets of the method's FP32 form: gradient
+relative error <= 1e-5 and per-step position relative error <= 1e-4 after the
+step's fixed iterations, both against the FP64 oracle fed the same state.
+The FP64 form is held to round-off-level agreement.
+"""
+import numpy as np
+import pytest
+
+from oracle import hqn_oracle as O
+from paper_1604_07378_gb300 import workloads as W
+
+from _util import perturbed, problem_for, rel, sim_for, small_workloads
+
+pytestmark = pytest.mark.gpu
+
+FP64, FP32 = 0, 1
+WORKLOADS = small_workloads()
+IDS = [w.name for w in WORKLOADS]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1604_07378_gb300 import hqn
+    hqn.library()
+
+
+# ---------------------------------------------------------------- energy and gradient
+
+@pytest.mark.parametrize("w", WORKLOADS, ids=IDS)
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_energy_gradient_parity(w, prec):
+    P = problem_for(w)
+    y = O.predictor(P, w.q_cur, w.q_prev)
+    tol_g = 1e-11 if prec == FP64 else 1e-5
+    with sim_for(w, prec, use_graph=0) as sim:
+        for seed, scale in ((0, 0.0), (1, 2e-3), (2, 8e-3)):
+            x = perturbed(w, scale, seed) if scale else w.q_cur
+            g_ref = O.objective(P, x, y)
+            grad_ref = O.gradient(P, x, y)
+            g, grad = sim.energy_grad(x, y)
+            if np.linalg.norm(grad_ref) > 0:
+                assert rel(grad, grad_ref) <= tol_g, (seed, rel(grad, grad_ref))
+            assert abs(g - g_ref) <= (1e-11 if prec == FP64 else 2e-6) * max(abs(g_ref), 1e-12)
+            # clamped rows are exactly zero
+            assert np.all(grad[w.clamped.astype(bool)] == 0.0)
+
+
+def test_energy_gradient_inverted_tets():
+    """States with inverted elements exercise the Neo-Hookean continuation
+    below J0 and the signed SVD (s3 < 0)."""
+    w = W.lattice_workload((3, 3, 3), W.Material(W.NEOHOOKEAN, 1e5, 0.45), seed=5)
+    P = problem_for(w)
+    x = perturbed(w, 0.03, 7)
+    F = O.deformation_gradients(P, x)
+    assert np.sum(np.linalg.det(F) < 0) > 5
+    y = w.q_cur
+    for prec, tol in ((FP64, 1e-10), (FP32, 1e-5)):
+        with sim_for(w, prec, use_graph=0) as sim:
+            g, grad = sim.energy_grad(x, y)
+        assert rel(grad, O.gradient(P, x, y)) <= tol
+        assert abs(g - O.objective(P, x, y)) <= 10 * tol * abs(O.objective(P, x, y))
+
+
+@pytest.mark.parametrize("kind", [W.COROTATED, W.POLY4])
+def test_energy_gradient_other_materials(kind):
+    w = W.lattice_workload((4, 3, 5), W.Material(kind, 2e5, 0.35), seed=9, v_range=0.3)
+    P = problem_for(w)
+    x = perturbed(w, 4e-3, 3)
+    y = O.predictor(P, w.q_cur, w.q_prev)
+    with sim_for(w, FP64, use_graph=0) as sim:
+        g, grad = sim.energy_grad(x, y)
+    assert rel(grad, O.gradient(P, x, y)) <= 1e-10
+    assert abs(g - O.objective(P, x, y)) <= 1e-10 * abs(O.objective(P, x, y))
+
+
+# ---------------------------------------------------------------- A0 solve and two-loop
+
+@pytest.mark.parametrize("w", WORKLOADS[:3], ids=IDS[:3])
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_solve_A0_parity(w, prec):
+    P = problem_for(w)
+    rng = np.random.default_rng(4)
+    q = rng.normal(size=(w.n_verts, 3))
+    with sim_for(w, prec, use_graph=0) as sim:
+        r = sim.solve_A0(q)
+    r_ref = O.solve_A(P, q)
+    assert rel(r, r_ref) <= (1e-11 if prec == FP64 else 2e-5)
+    assert np.all(r[w.clamped.astype(bool)] == 0.0)
+
+
+@pytest.mark.parametrize("npairs", [0, 1, 3, 5])
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_direction_parity(npairs, prec):
+    w = WORKLOADS[1]
+    P = problem_for(w)
+    rng = np.random.default_rng(10 + npairs)
+    free = ~w.clamped.astype(bool)
+    grad = rng.normal(size=(w.n_verts, 3)) * free[:, None]
+    # t_i = A0 s_i + small noise keeps rho > 0 (a plausible curvature pair)
+    pairs = []
+    for _ in range(npairs):
+        s = rng.normal(size=(w.n_verts, 3)) * free[:, None]
+        t = np.zeros_like(s)
+        t[free] = P.A @ s[free] + 0.01 * rng.normal(size=s[free].shape) * np.abs(P.A @ s[free]).mean()
+        pairs.append((s, t, float(np.sum(s * t))))
+    d_ref = O.lbfgs_direction(P, grad, pairs)
+    with sim_for(w, prec, use_graph=0) as sim:
+        d = sim.direction(grad, [p[0] for p in pairs], [p[1] for p in pairs])
+    assert rel(d, d_ref) <= (1e-10 if prec == FP64 else 1e-4)
+
+
+# ---------------------------------------------------------------- whole steps
+
+def _step_parity(w, prec, use_graph, tol_x):
+    P = problem_for(w)
+    x_ref, st = O.solve_step(P, w.q_cur, w.q_prev, iters=w.iters, m=w.history)
+    with sim_for(w, prec, use_graph=use_graph) as sim:
+        sim.set_state(w.q_cur, w.q_prev)
+        rc, stats = sim.step(1, stats=True)
+        qc, qp = sim.get_state()
+    assert rc >= 0
+    np.testing.assert_allclose(qp, w.q_cur, rtol=0, atol=1e-6 if prec == FP32 else 1e-14)
+    ex = rel(qc, x_ref)
+    assert ex <= tol_x, (ex, stats["trials"], st.trials)
+    return stats, st, qc, x_ref
+
+
+@pytest.mark.parametrize("w", WORKLOADS, ids=IDS)
+def test_step_parity_fp64_eager(w):
+    stats, st, qc, x_ref = _step_parity(w, FP64, 0, 1e-9)
+    assert stats["trials"] == st.trials
+    np.testing.assert_allclose(stats["g"], st.g, rtol=1e-9)
+
+
+@pytest.mark.parametrize("w", WORKLOADS, ids=IDS)
+def test_step_parity_fp32_eager(w):
+    _step_parity(w, FP32, 0, 1e-4)
+
+
+@pytest.mark.parametrize("w", WORKLOADS, ids=IDS)
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_step_parity_graph(w, prec):
+    stats, st, qc, x_ref = _step_parity(w, prec, 1, 1e-9 if prec == FP64 else 1e-4)
+    if prec == FP64:
+        assert stats["trials"] == st.trials
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_graph_equals_eager_bitwise(prec):
+    w = WORKLOADS[2]
+    out = []
+    for g in (0, 1, 1):
+        with sim_for(w, prec, use_graph=g) as sim:
+            sim.set_state(w.q_cur, w.q_prev)
+            sim.step(3)
+            out.append(sim.get_state()[0])
+    np.testing.assert_array_equal(out[0], out[1])
+    np.testing.assert_array_equal(out[1], out[2])
+
+
+def test_trajectory_30_steps_fp64():
+    """The FP64 form tracks the oracle over the bar's 30-step trajectory."""
+    w = W.bar_4x4x16_fp64()
+    P = problem_for(w)
+    qc, qp = w.q_cur.copy(), w.q_prev.copy()
+    with sim_for(w, FP64) as sim:
+        sim.set_state(qc, qp)
+        for k in range(30):
+            x_ref, _ = O.solve_step(P, qc, qp, iters=10, m=5)
+            qp, qc = qc, x_ref
+            sim.step(1)
+            gq, _ = sim.get_state()
+            assert rel(gq, x_ref) <= 1e-8, k
