@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark: implicit-Euler time steps per second of the quasi-Newton /
+L-BFGS solver on the 40x40x40 Neo-Hookean tet lattice (384,000 tets,
+68,921 vertices, E = 5e5, nu = 0.4, bottom face clamped, seeded initial
+velocities U[-0.5, 0.5] m/s, 10 iterations, m = 5), FP32-mixed form, with the
+FP64-plain GPU form and the FP64 CPU oracle beside it.
+
+One "step" is one whole time step (predictor, 10 quasi-Newton iterations with
+their line searches, commit) launched as one CUDA graph.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): one independent replica per rank (the single-mesh
+path does not shard), value = all ranks' steps / slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-steps/s & tet grad-evals/s at 384k tets, FP32 vs FP64 GPU, pos err ≤1e-4"
+UNIT = "time-steps/s"
+WORKLOAD = "cube40_neohookean"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        rows = self.rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------- oracle (CPU)
+
+def oracle_sample(w, budget_s=25.0, counts=None):
+    """Times the FP64 CPU oracle on a bounded sample of the workload: repeated
+    (objective, gradient, A0 solve) evaluations on the full mesh, scaled to
+    one time step by the step's counts (trial evaluations, gradients, solves).
+    Returns (steps_per_s, tet_evals_per_s, description, cores)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import hqn_oracle as O
+    P = O.problem_from_workload(w)
+    y = O.predictor(P, w.q_cur, w.q_prev)
+    x = y.copy()
+    O.solve_A(P, y)  # factorisation: set-up, not timed
+    t_obj, t_grad, t_solve, reps = 0.0, 0.0, 0.0, 0
+    start = time.perf_counter()
+    while reps < 1 or (time.perf_counter() - start < budget_s and reps < 50):
+        t0 = time.perf_counter()
+        O.objective(P, x, y)
+        t1 = time.perf_counter()
+        g = O.gradient(P, x, y)
+        t2 = time.perf_counter()
+        O.solve_A(P, g)
+        t3 = time.perf_counter()
+        t_obj += t1 - t0
+        t_grad += t2 - t1
+        t_solve += t3 - t2
+        reps += 1
+    t_obj, t_grad, t_solve = t_obj / reps, t_grad / reps, t_solve / reps
+    trials, iters = counts if counts else (1.07 * w.iters, w.iters)
+    step_s = (trials + 1) * t_obj + (iters + 1) * t_grad + iters * t_solve
+    tet_evals = w.n_tets * (trials + iters + 2)
+    desc = (f"{reps} x (objective + gradient + A0 solve) on the full {w.n_tets}-tet mesh "
+            f"({t_obj:.3f} s + {t_grad:.3f} s + {t_solve:.3f} s), scaled to one step of "
+            f"{trials:.1f} line-search trials and {iters:.0f} iterations")
+    return 1.0 / step_s, tet_evals / step_s, desc, 1
+
+
+# ---------------------------------------------------------------------------- GPU arm
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_1604_07378_gb300 import hqn
+    from paper_1604_07378_gb300 import workloads as W
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    w = W.cube40(W.NEOHOOKEAN)
+    T = w.n_tets
+    graph = 0 if args.no_graph else 1
+    sim = hqn.Sim.from_workload(w, precision=hqn.FP32_MIXED, stream=stream.cuda_stream, use_graph=graph)
+    info = sim.info()
+    sim.set_state(w.q_cur, w.q_prev)
+    sim.step(args.warmup)
+    sim.set_state(w.q_cur, w.q_prev)
+
+    # ---- timed region: K steps, one graph launch each
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(dev.index)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc, stats = sim.step(args.steps, stats=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        if dist:
+            dist.barrier()
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    trials = stats["trials_total"] / args.steps
+    iters = stats["iters_total"] / args.steps
+    # energy evaluations per step: x_1 = y plus every line-search trial
+    tet_evals_step = T * (stats["trials_total"] + args.steps) / args.steps
+    value = world * args.steps / (ms / 1e3)
+
+    # ---- per-stage device times (CUDA events on the handle's stream)
+    stage_ms = {name: sim.time_stage(code, 20) for name, code in (
+        ("tet", hqn.STAGE_TET), ("gather", hqn.STAGE_GATHER), ("solve", hqn.STAGE_SOLVE),
+        ("ls_pass", hqn.STAGE_LS_PASS), ("two_loop_with_solve", hqn.STAGE_TWO_LOOP))}
+    passes = stats["ls_passes_total"] / args.steps
+    per_step = {"tet": stage_ms["tet"] * (iters + 1), "solve": stage_ms["solve"] * iters,
+                "gather": stage_ms["gather"] * (iters + 1),
+                "ls_pass": stage_ms["ls_pass"] * passes,
+                "two_loop": max(stage_ms["two_loop_with_solve"] - stage_ms["solve"], 0.0) * iters}
+    dominant = max(per_step, key=per_step.get)
+
+    # ---- end to end through the C ABI with host buffers
+    lib = hqn.library()
+    import ctypes as C
+    qc = np.ascontiguousarray(w.q_cur)
+    qp = np.ascontiguousarray(w.q_prev)
+    out = np.empty_like(qc)
+    dp = C.POINTER(C.c_double)
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        lib.sim_set_state(sim._h, qc.ctypes.data_as(dp), qp.ctypes.data_as(dp))
+        lib.sim_step(sim._h, 1, None)
+        lib.sim_get_state(sim._h, out.ctypes.data_as(dp), None)
+        qp, qc = qc, out.copy()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_wall = time.perf_counter() - t0
+    e2e_ms = max(f0.elapsed_time(f1), e2e_wall * 1e3)
+    n = w.n_verts
+    vbytes = 16  # FP32 vertex record
+    h2d = 2 * n * vbytes
+    d2h = n * vbytes + 1024  # state + control block (line-search statistics)
+
+    # ---- FP64-plain GPU form beside it, and the accuracy of the FP32 form against it
+    sim64 = hqn.Sim.from_workload(w, precision=hqn.FP64_PLAIN, stream=stream.cuda_stream, use_graph=graph)
+    sim64.set_state(w.q_cur, w.q_prev)
+    sim64.step(1)
+    x64, _ = sim64.get_state()
+    sim.set_state(w.q_cur, w.q_prev)
+    sim.step(1)
+    x32, _ = sim.get_state()
+    ex = float(np.linalg.norm(x32 - x64) / np.linalg.norm(x64))
+    k64 = max(2, min(args.steps, 4))
+    sim64.set_state(w.q_cur, w.q_prev)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    _, st64 = sim64.step(k64, stats=True)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = g0.elapsed_time(g1) / k64
+    tev64 = T * (st64["trials_total"] + k64) / k64
+    sim64.close()
+
+    # ---- roofline of the dominant kernel
+    peaks, src = _peaks()
+    fl = None
+    if dominant == "solve":
+        bytes_launch = 2 * info["factor_nnz"] * 4 + 2 * 12 * info["n_free"]
+        achieved = bytes_launch / (stage_ms["solve"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "trsv forward+backward sweeps (k_fwd, k_bwd)",
+                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "algorithmic_bytes_per_launch": bytes_launch}
+    else:
+        bytes_launch = T * 56 + n * 16 + T * 48
+        achieved = bytes_launch / (stage_ms[dominant] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "algorithmic_bytes_per_launch": bytes_launch}
+    roof["peak_source"] = f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (f64 energy sums, Armijo test, inner products)",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": "40x40x40 Kuhn cubes", "tets": T,
+                   "vertices": n, "material": "Neo-Hookean E=5e5 nu=0.4", "iters": w.iters,
+                   "history_m": w.history, "h": w.h, "parallelism": f"replicas{world}",
+                   "l2": "working set %.0f MB > 129 MB L2 (factor alone %.0f MB)" % (
+                       info["device_bytes"] / 1e6, info["factor_entries"] * 4 / 1e6)},
+        "tet_grad_evals_per_s": world * tet_evals_step * args.steps / (ms / 1e3),
+        "ls_trials_per_iter": trials / max(iters, 1),
+        "fp64_plain": {"value": 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64,
+                       "tet_grad_evals_per_s": tev64 * 1e3 / ms64, "steps": k64},
+        "pos_err_fp32_vs_fp64_gpu": ex,
+        "stage_ms_per_launch": stage_ms, "stage_ms_per_step": per_step,
+        "roofline": roof, "clocks": clocks,
+        "e2e": {"value": world * e2e_steps / (e2e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": None,
+        "status": rc,
+    }
+    # kernels per step: start (predictor, inertia, tet, gather) + commit, and per
+    # iteration: both loops of Alg. 2 (2m + 2), the sweeps (2 per tree level),
+    # direction final, line-search begin, tet gradient, gather; plus every
+    # line-search pass
+    m = w.history
+    per_iter = 2 * (m + 1) + 2 * info["n_levels"] + 4
+    launches = args.steps * 5 + stats["iters_total"] * per_iter + stats["ls_passes_total"]
+    line["gpu_launches"] = launches
+    if rank == 0 and not args.no_cpu_baseline:
+        v, te, desc, cores = oracle_sample(w, budget_s=args.cpu_budget, counts=(trials, iters))
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": desc, "tet_grad_evals_per_s": te}
+    sim.close()
+    return line
+
+
+def run_reference(args, rank):
+    """The FP64 CPU oracle as the reference arm (rank 0 only)."""
+    from paper_1604_07378_gb300 import workloads as W
+    w = W.cube40(W.NEOHOOKEAN)
+    from oracle import hqn_oracle as O
+    P = O.problem_from_workload(w)
+    y = O.predictor(P, w.q_cur, w.q_prev)
+    O.solve_A(P, y)
+    trials, iters = 1.07 * w.iters, w.iters
+
+    def one():
+        t0 = time.perf_counter()
+        O.objective(P, y, y)
+        t1 = time.perf_counter()
+        g = O.gradient(P, y, y)
+        t2 = time.perf_counter()
+        O.solve_A(P, g)
+        t3 = time.perf_counter()
+        return (trials + 1) * (t1 - t0) + (iters + 1) * (t2 - t1) + iters * (t3 - t2)
+
+    for _ in range(args.warmup):
+        one()
+    total = sum(one() for _ in range(args.steps))
+    value = args.steps / total
+    desc = (f"per step: one objective + one gradient + one A0 solve on the full mesh, scaled to "
+            f"{trials:.1f} trials and {iters} iterations per step")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "tets": w.n_tets, "vertices": w.n_verts},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-graph", action="store_true",
+                    help="issue the step's kernels one by one (same kernels; for profilers that "
+                         "cannot see inside graphs with conditional nodes)")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank)), flush=True)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    line = run_ours(args, rank, world, dist)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -103,6 +103,9 @@ typedef struct {
                              loops; 0 = host-driven launches (same kernels)        */
     int32_t tet_block;    /* threads per block of the tet kernel: 64, 128 or 256
                              (0 = default 128)                                     */
+    int32_t ls_batch;     /* line-search step lengths tested per tet pass: 1, 2, 4,
+                             8 or 16 (0 = default 8); the accepted alpha is the
+                             one Alg. 1's sequential backtracking would accept    */
 } hqn_params;
 
 #define HQN_MAX_HISTORY 16
@@ -118,6 +121,7 @@ typedef struct {
     int32_t trials[HQN_MAX_ITERS];          /* trials of each iteration, last step   */
     double  g0;                             /* g(x_1), x_1 = y, last step            */
     double  g[HQN_MAX_ITERS];               /* g(x_{k+1}) after each iteration       */
+    int32_t ls_passes_total;                /* line-search tet passes, all steps     */
 } hqn_step_stats;
 
 typedef struct {
@@ -137,7 +141,7 @@ typedef struct sim_handle sim_handle;
 
 /* Paper defaults: h = 1/30, gamma = 0.3, backtrack = 0.5, [0.5, 1.5], gravity
  * (0, 0, -9.81), 10 iterations, m = 5, ls_max = 30, FP32_MIXED, leaf 64,
- * graph mode on, tet block 128. */
+ * graph mode on, tet block 128, 8 line-search trials per pass. */
 void hqn_default_params(hqn_params *p);
 
 /* Builds a simulation: rest data (Dm^-1, volumes, lumped mass), the stiffness k
@@ -178,6 +182,21 @@ int sim_solve_A0(sim_handle *sim, const double *q, double *r);
  * used as given (no curvature filtering); npairs <= history_m. */
 int sim_direction(sim_handle *sim, const double *grad, int32_t npairs,
                   const double *s, const double *t, double *d);
+
+/* Stages that sim_time_stage can time in isolation. */
+typedef enum {
+    HQN_STAGE_TET      = 0, /* energy + corner gradients of every tet at the last trial x */
+    HQN_STAGE_GATHER   = 1, /* vertex gather of grad g                                  */
+    HQN_STAGE_SOLVE    = 2, /* forward + backward sweeps of A0^{-1} (3 right-hand sides) */
+    HQN_STAGE_LS_PASS  = 3, /* one multi-trial line-search pass (ls_batch energies/tet)  */
+    HQN_STAGE_TWO_LOOP = 4  /* both loops of Alg. 2 around one solve                     */
+} hqn_stage;
+
+/* Launches one stage `reps` times on the handle's stream, bracketed by CUDA
+ * events recorded on that stream, and returns the mean device time of one
+ * launch in *ms.  Uses the handle's current buffers (call after sim_step);
+ * leaves the state (q_l, q_{l-1}) unchanged.  Synchronises the stream. */
+int sim_time_stage(sim_handle *sim, int32_t stage, int32_t reps, double *ms);
 
 int  sim_get_info(const sim_handle *sim, hqn_info *info);
 void sim_destroy(sim_handle *sim);

@@ -64,6 +64,7 @@ struct SimBase {
     virtual int solve_A0(const double *q, double *r) = 0;
     virtual int direction(const double *grad, int np, const double *s, const double *t, double *d) = 0;
     virtual void info(hqn_info *out) const = 0;
+    virtual int time_stage(int stage, int reps, double *ms) = 0;
 };
 
 template <typename R>
@@ -75,7 +76,6 @@ struct Sim final : SimBase {
     DevSolve<R> dsol{};
     std::vector<void *> allocs;
     int64_t dev_bytes = 0;
-    std::vector<int> fwd_ptr, bwd_ptr, fwd_cols;
     Ctl *h_ctl = nullptr;  // pinned
     std::vector<V4<R>> hbuf;
     cudaGraph_t graph = nullptr;
@@ -121,8 +121,8 @@ struct Sim final : SimBase {
         prm = p;
         st = stream;
         const int n = S.n, T = S.T, nf = S.n_free, m = p.history_m;
-        if (!solve_smem_limit_ok<R>(S.max_front_cols))
-            return fail(HQN_ERR_UNSUPPORTED, "a separator is too large for the forward sweep's shared memory");
+        if (!solve_smem_limit_ok<R>(S.max_ld))
+            return fail(HQN_ERR_UNSUPPORTED, "a separator is too large for the sweeps' shared memory");
         CK(solve_prepare<R>());
         if (st == nullptr) {  // the legacy default stream cannot be captured: use an own stream
             CK(cudaStreamCreateWithFlags(&own_stream, cudaStreamNonBlocking));
@@ -130,6 +130,7 @@ struct Sim final : SimBase {
         }
         StepConst<R> &c = ds.c;
         c.n = n; c.nf = nf; c.T = T; c.m = m; c.iters = p.iters; c.ls_max = p.ls_max;
+        c.ls_batch = (p.ls_batch == 1 || p.ls_batch == 2 || p.ls_batch == 4 || p.ls_batch == 16) ? p.ls_batch : 8;
         c.h2 = (R)(p.h * p.h);
         c.gx = (R)(p.h * p.h * p.gravity[0]);
         c.gy = (R)(p.h * p.h * p.gravity[1]);
@@ -186,54 +187,75 @@ struct Sim final : SimBase {
         if ((rc = alloc(ds.part_in, nbv))) return rc;
         if ((rc = alloc(ds.part_el, nbt))) return rc;
         if ((rc = alloc(ds.part_g, (size_t)3 * nbf))) return rc;
-        if ((rc = alloc(ds.part_v, nbf))) return rc;
+        if ((rc = alloc(ds.part_v, (size_t)4 * nbf))) return rc;
+        if ((rc = alloc(ds.part_ls, (size_t)16 * ((T + 127) / 128)))) return rc;
         if ((rc = alloc(ds.ctl, 1))) return rc;
         CK(cudaMallocHost(&h_ctl, sizeof(Ctl)));
         // solve operators
         dsol.nf = nf;
         dsol.n_levels = S.n_levels;
-        std::vector<R> Q(S.Q.size());
-        for (size_t k = 0; k < Q.size(); ++k) Q[k] = (R)S.Q[k];
-        const R *p_Q;
-        if ((rc = upload(p_Q, Q.data(), Q.size()))) return rc;
-        dsol.Q = p_Q;
-        std::vector<int4> sn(S.sn.size());
-        std::vector<long long> snq(S.sn.size());
-        std::vector<int> snu(S.sn.size());
-        for (size_t s = 0; s < S.sn.size(); ++s) {
+        // the two padded copies of every Q_s (forward: row-major, backward: transposed)
+        std::vector<R> QF((size_t)S.qf_total, R(0)), QB((size_t)S.qb_total, R(0));
+        for (const SupernodeHost &sn : S.sn) {
+            const double *Qs = S.Q.data() + sn.qoff;
+            const int nc = sn.ncol, rows = sn.ncol + sn.nrow;
+            for (int i = 0; i < rows; ++i)
+                for (int j = 0; j < nc; ++j) {
+                    const R v = (R)Qs[(size_t)i * nc + j];
+                    QF[(size_t)sn.qf + (size_t)i * sn.ldc + j] = v;
+                    QB[(size_t)sn.qb + (size_t)j * sn.ldr + i] = v;
+                }
+        }
+        const R *p_QF, *p_QB;
+        if ((rc = upload(p_QF, QF.data(), QF.size()))) return rc;
+        if ((rc = upload(p_QB, QB.data(), QB.size()))) return rc;
+        std::vector<R>().swap(QF);
+        std::vector<R>().swap(QB);
+        dsol.QF = p_QF;
+        dsol.QB = p_QB;
+        const size_t ns = S.sn.size();
+        std::vector<int4> sn(ns);
+        std::vector<long long> snqf(ns), snqb(ns);
+        std::vector<int2> snld(ns);
+        std::vector<int> snu(ns);
+        for (size_t s = 0; s < ns; ++s) {
             sn[s] = make_int4(S.sn[s].col, S.sn[s].ncol, S.sn[s].nrow, S.sn[s].roff);
-            snq[s] = S.sn[s].qoff;
+            snqf[s] = S.sn[s].qf;
+            snqb[s] = S.sn[s].qb;
+            snld[s] = make_int2(S.sn[s].ldc, S.sn[s].ldr);
             snu[s] = S.sn[s].uoff;
         }
         const int4 *p_sn;
-        const long long *p_snq;
-        const int *p_snu, *p_rows, *p_fgp, *p_fgi, *p_ugp, *p_ugi;
-        if ((rc = upload(p_sn, sn.data(), sn.size()))) return rc;
-        if ((rc = upload(p_snq, snq.data(), snq.size()))) return rc;
-        if ((rc = upload(p_snu, snu.data(), snu.size()))) return rc;
+        const long long *p_snqf, *p_snqb;
+        const int2 *p_snld, *p_fg2, *p_ug2;
+        const int *p_snu, *p_rows;
+        if ((rc = upload(p_sn, sn.data(), ns))) return rc;
+        if ((rc = upload(p_snqf, snqf.data(), ns))) return rc;
+        if ((rc = upload(p_snqb, snqb.data(), ns))) return rc;
+        if ((rc = upload(p_snld, snld.data(), ns))) return rc;
+        if ((rc = upload(p_snu, snu.data(), ns))) return rc;
         if ((rc = upload(p_rows, S.rows.data(), S.rows.size()))) return rc;
-        if ((rc = upload(p_fgp, S.fg_ptr.data(), S.fg_ptr.size()))) return rc;
-        if ((rc = upload(p_fgi, S.fg_idx.data(), S.fg_idx.size()))) return rc;
-        if ((rc = upload(p_ugp, S.ug_ptr.data(), S.ug_ptr.size()))) return rc;
-        if ((rc = upload(p_ugi, S.ug_idx.data(), S.ug_idx.size()))) return rc;
-        dsol.sn = p_sn; dsol.sn_q = p_snq; dsol.sn_u = p_snu; dsol.rows = p_rows;
-        dsol.fg_ptr = p_fgp; dsol.fg_idx = p_fgi; dsol.ug_ptr = p_ugp; dsol.ug_idx = p_ugi;
+        if ((rc = upload(p_fg2, reinterpret_cast<const int2 *>(S.fg2.data()), S.fg2.size() / 2))) return rc;
+        if ((rc = upload(p_ug2, reinterpret_cast<const int2 *>(S.ug2.data()), S.ug2.size() / 2))) return rc;
+        dsol.sn = p_sn; dsol.sn_qf = p_snqf; dsol.sn_qb = p_snqb; dsol.sn_ld = p_snld;
+        dsol.sn_u = p_snu; dsol.rows = p_rows; dsol.fg2 = p_fg2; dsol.ug2 = p_ug2;
         std::vector<int4> fi(S.fwd_items.size()), bi(S.bwd_items.size());
-        for (size_t k = 0; k < fi.size(); ++k)
-            fi[k] = make_int4(S.fwd_items[k].s, S.fwd_items[k].row0, S.fwd_items[k].row1, 0);
-        for (size_t k = 0; k < bi.size(); ++k)
-            bi[k] = make_int4(S.bwd_items[k].s, S.bwd_items[k].col0, 0, 0);
+        for (size_t k = 0; k < fi.size(); ++k) {
+            const FwdItem &f = S.fwd_items[k];
+            fi[k] = make_int4(f.s, f.row0, f.row1, f.G);
+        }
+        for (size_t k = 0; k < bi.size(); ++k) {
+            const BwdItem &b = S.bwd_items[k];
+            bi[k] = make_int4(b.s, b.col0, b.col1, b.G);
+        }
         const int4 *p_fi, *p_bi;
         if ((rc = upload(p_fi, fi.data(), fi.size()))) return rc;
         if ((rc = upload(p_bi, bi.data(), bi.size()))) return rc;
         dsol.fwd_items = p_fi; dsol.bwd_items = p_bi;
-        fwd_ptr = S.fwd_lvl_ptr;
-        bwd_ptr = S.bwd_lvl_ptr;
-        fwd_cols.assign(S.n_levels, 0);
-        for (auto &s : S.sn) fwd_cols[s.level] = std::max(fwd_cols[s.level], s.ncol);
-        dsol.fwd_lvl_ptr = fwd_ptr.data();
-        dsol.bwd_lvl_ptr = bwd_ptr.data();
-        dsol.fwd_lvl_cols = fwd_cols.data();
+        dsol.fwd_lvl_ptr = S.fwd_lvl_ptr.data();
+        dsol.bwd_lvl_ptr = S.bwd_lvl_ptr.data();
+        dsol.fwd_lvl_ld = S.fwd_lvl_ld.data();
+        dsol.bwd_lvl_ld = S.bwd_lvl_ld.data();
         if ((rc = alloc(dsol.u, (size_t)S.n_upd))) return rc;
         hbuf.resize(n);
         CK(cudaStreamSynchronize(st));
@@ -322,15 +344,17 @@ struct Sim final : SimBase {
         launch_solve(dsol, ds.q, ds.z, ds.d, s);
         launch_direction_final(ds, CondHandles{0, 0, 0}, 0, s);
     }
-    void enqueue_trial(CondHandles h, cudaStream_t s) {
-        launch_trial(ds, 1, s);
-        launch_tet(ds, TET_TRIAL, h, s);
-    }
     void enqueue_start(CondHandles h, cudaStream_t s) {
         launch_predict(ds, s);
-        launch_trial(ds, 0, s);
-        launch_tet(ds, TET_INIT, CondHandles{0, 0, 0}, s);
+        launch_inertia(ds, s);
+        launch_tet(ds, TET_INIT, s);
         launch_gather(ds, G_INIT, h, s);
+    }
+    // x_{k+1} = x_k + alpha d: its gradient (corners, then the gather with the
+    // history push) once the line search has accepted alpha.
+    void enqueue_accept(CondHandles h, cudaStream_t s) {
+        launch_tet(ds, TET_GRAD, s);
+        launch_gather(ds, G_ITER, h, s);
     }
 
     int step_eager() {
@@ -343,11 +367,11 @@ struct Sim final : SimBase {
             if (h_ctl->nondescent) enqueue_reset_direction(st);
             launch_ls_begin(ds, none, st);
             for (int tr = 0; tr < prm.ls_max; ++tr) {
-                enqueue_trial(none, st);
+                launch_ls(ds, none, st);
                 if ((rc = read_ctl())) return rc;
                 if (h_ctl->accepted || h_ctl->stop) break;
             }
-            launch_gather(ds, G_ITER, none, st);
+            enqueue_accept(none, st);
             if ((rc = read_ctl())) return rc;
             if (h_ctl->stop) break;
         }
@@ -416,10 +440,10 @@ struct Sim final : SimBase {
             {
                 cudaStream_t s2 = cap_stream(1);
                 CK(cudaStreamBeginCaptureToGraph(s2, body_ls, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-                enqueue_trial(H, s2);
+                launch_ls(ds, H, s2);
                 CK(cudaStreamEndCapture(s2, &body_ls));
             }
-            launch_gather(ds, G_ITER, H, s1);
+            enqueue_accept(H, s1);
             CK(cudaStreamEndCapture(s1, &body_it));
         }
         launch_commit(ds, st);
@@ -433,7 +457,7 @@ struct Sim final : SimBase {
 
     int step(int nsteps, hqn_step_stats *stats) override {
         if (nsteps < 0) return fail(HQN_ERR_ARG, "negative step count");
-        CK(cudaMemsetAsync(&ds.ctl->trials_total, 0, 4 * sizeof(int), st));
+        CK(cudaMemsetAsync(&ds.ctl->trials_total, 0, 5 * sizeof(int), st));
         for (int k = 0; k < nsteps; ++k) {
             if (graph_mode) {
                 CK(cudaGraphLaunch(gexec, st));
@@ -457,6 +481,7 @@ struct Sim final : SimBase {
                 stats->g[i] = c.iter_g[i];
             }
             stats->g0 = c.g0;
+            stats->ls_passes_total = c.passes_total;
         }
         if (nsteps > 0 && !std::isfinite(c.g_k)) return fail(HQN_ERR_NONFINITE, "objective is not finite");
         return c.worst_status;
@@ -467,8 +492,8 @@ struct Sim final : SimBase {
         if ((rc = put_vec(ds.xt, x, true, false))) return rc;
         if ((rc = put_vec(ds.y, y, true, false))) return rc;
         const CondHandles none{0, 0, 0};
-        launch_trial(ds, 0, st);
-        launch_tet(ds, TET_EVAL, none, st);
+        launch_inertia(ds, st);
+        launch_tet(ds, TET_EVAL, st);
         launch_gather(ds, G_EVAL, none, st);
         CK(cudaGetLastError());
         if ((rc = read_ctl())) return rc;
@@ -504,6 +529,36 @@ struct Sim final : SimBase {
         enqueue_direction(CondHandles{0, 0, 0}, 0, st);
         CK(cudaGetLastError());
         return get_vec(ds.d, d, false, true);
+    }
+
+    int time_stage(int stage, int reps, double *ms) override {
+        if (reps <= 0 || stage < HQN_STAGE_TET || stage > HQN_STAGE_TWO_LOOP)
+            return fail(HQN_ERR_ARG, "bad stage or repetition count");
+        const CondHandles none{0, 0, 0};
+        auto launch = [&]() {
+            switch (stage) {
+                case HQN_STAGE_TET: launch_tet(ds, TET_EVAL, st); break;
+                case HQN_STAGE_GATHER: launch_gather(ds, G_EVAL, none, st); break;
+                case HQN_STAGE_SOLVE: launch_solve(dsol, ds.q, ds.z, ds.d, st); break;
+                case HQN_STAGE_LS_PASS: launch_ls(ds, none, st); break;
+                default: enqueue_direction(none, 0, st); break;
+            }
+        };
+        launch();  // warm-up
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        CK(cudaEventRecord(e0, st));
+        for (int k = 0; k < reps; ++k) launch();
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        CK(cudaGetLastError());
+        *ms = (double)t / reps;
+        return HQN_OK;
     }
 
     void info(hqn_info *o) const override {
@@ -549,6 +604,7 @@ void hqn_default_params(hqn_params *p) {
     p->leaf_size = 64;
     p->use_graph = 1;
     p->tet_block = 128;
+    p->ls_batch = 8;
 }
 
 int sim_create(const hqn_mesh *mesh, const hqn_material *material, const hqn_params *params, void *stream,
@@ -617,6 +673,11 @@ int sim_direction(sim_handle *sim, const double *grad, int32_t npairs, const dou
                   double *d) {
     if (!sim || !grad || !d || (npairs > 0 && (!s || !t))) return fail(HQN_ERR_ARG, "null argument");
     try { return sim->impl->direction(grad, npairs, s, t, d); } catch (...) { return fail(HQN_ERR_NO_MEMORY, "exception"); }
+}
+
+int sim_time_stage(sim_handle *sim, int32_t stage, int32_t reps, double *ms) {
+    if (!sim || !ms) return fail(HQN_ERR_ARG, "null argument");
+    try { return sim->impl->time_stage(stage, reps, ms); } catch (...) { return fail(HQN_ERR_NO_MEMORY, "exception"); }
 }
 
 int sim_get_info(const sim_handle *sim, hqn_info *info) {

@@ -40,6 +40,7 @@ struct Ctl {
     double alpha;      // current step length
     double g0;         // g(x_1), x_1 = y
     double dot;        // scratch: last finalised inner product
+    double ls_a[3];    // inertia term along d: I(alpha) = a0 + a1 alpha + a2 alpha^2
     double zeta[HQN_MAX_HISTORY + 1];  // first-loop coefficients by age (0 = newest)
     double rho[HQN_MAX_HISTORY + 1];   // tr(t^T s) by ring slot
     double iter_g[HQN_MAX_ITERS];
@@ -56,11 +57,12 @@ struct Ctl {
     int iters_total;
     int steps;
     int worst_status;
+    int passes_total;  // line-search passes (each tests up to ls_batch step lengths)
     unsigned int ticket[8];  // arrival counters of the last-block reductions
 };
 
 // Ticket slots (one per kernel family so consecutive kernels never share one).
-enum { TK_TRIAL = 0, TK_TET = 1, TK_GATHER = 2, TK_VEC = 3, TK_PUSH = 4, TK_DOT = 5 };
+enum { TK_TRIAL = 0, TK_TET = 1, TK_GATHER = 2, TK_VEC = 3, TK_LS = 4, TK_DOT = 5 };
 
 // Graph conditional handles a kernel may set (0 = not inside a graph).
 struct CondHandles {
@@ -72,7 +74,7 @@ struct CondHandles {
 // Per-simulation constants passed by value.
 template <typename R>
 struct StepConst {
-    int n, nf, T, m, iters, ls_max;
+    int n, nf, T, m, iters, ls_max, ls_batch;
     R h2;              // h^2
     R gx, gy, gz;      // h^2 * gravity (the h^2 M^{-1} f_ext term of Eq. PD)
     double gamma, backtrack;

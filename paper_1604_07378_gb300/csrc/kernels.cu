@@ -50,25 +50,16 @@ __global__ void __launch_bounds__(VBS) k_predict(DevSim<R> s) {
     }
 }
 
-// ---------------------------------------------------------------- trial update
+// ---------------------------------------------------------------- inertia of a given x
 
-// x_t = x_k + alpha d (apply) and the block partial of the inertia term
-// 1/(2h^2) sum m_v |x_t - y|^2 of Eq. PD.
+// Block partial of the inertia term 1/(2h^2) sum m_v |x_t - y|^2 of Eq. PD at
+// the caller-given point x_t (the start of a step, or an evaluation request).
 template <typename R>
-__global__ void __launch_bounds__(VBS) k_trial(DevSim<R> s, int apply) {
+__global__ void __launch_bounds__(VBS) k_inertia(DevSim<R> s) {
     const int i = blockIdx.x * VBS + threadIdx.x;
     double e[1] = {0.0};
     if (i < s.c.n) {
-        V4<R> x;
-        if (apply) {
-            const R al = (R)s.ctl->alpha;
-            const V4<R> a = s.xk[i], b = s.d[i];
-            x.x = a.x + al * b.x; x.y = a.y + al * b.y; x.z = a.z + al * b.z; x.w = R(0);
-            s.xt[i] = x;
-        } else {
-            x = s.xt[i];
-        }
-        const V4<R> yy = s.y[i];
+        const V4<R> x = s.xt[i], yy = s.y[i];
         const R dx = x.x - yy.x, dy = x.y - yy.y, dz = x.z - yy.z;
         e[0] = (double)(R(0.5) * s.mh2[i] * (dx * dx + dy * dy + dz * dz));
     }
@@ -76,30 +67,65 @@ __global__ void __launch_bounds__(VBS) k_trial(DevSim<R> s, int apply) {
     if (threadIdx.x == 0) s.part_in[blockIdx.x] = e[0];
 }
 
+// x_k + alpha d, rounded the same way wherever the accepted point is formed.
+template <typename R>
+__device__ __forceinline__ V4<R> step_point(const V4<R> &a, const V4<R> &b, R al) {
+    V4<R> o;
+    o.x = fma_(al, b.x, a.x);
+    o.y = fma_(al, b.y, a.y);
+    o.z = fma_(al, b.z, a.z);
+    o.w = R(0);
+    return o;
+}
+
+template <typename R>
+__device__ __forceinline__ void load_dm(const DevSim<R> &s, int t, R Di[9]) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Di[k] = s.dminv[(size_t)k * s.c.T + t];
+}
+
+template <typename R>
+__device__ __forceinline__ void edge_diffs(const V4<R> &x0, const V4<R> &x1, const V4<R> &x2, const V4<R> &x3,
+                                           R du[3][3]) {
+    du[0][0] = x1.x - x0.x; du[0][1] = x1.y - x0.y; du[0][2] = x1.z - x0.z;
+    du[1][0] = x2.x - x0.x; du[1][1] = x2.y - x0.y; du[1][2] = x2.z - x0.z;
+    du[2][0] = x3.x - x0.x; du[2][1] = x3.y - x0.y; du[2][2] = x3.z - x0.z;
+}
+
 // ---------------------------------------------------------------- tet kernel
 
-// One thread per tet: energy V Psi and the four corner gradients, written to
-// corner[c * T + t].  The last block sums the energy partials with the
-// inertia partials in a fixed order (float64) and takes the decision of the
-// mode: TET_INIT sets g(x_1); TET_TRIAL runs the Armijo test of Alg. 1
-// (g(x) <= g_k + gamma alpha tr(grad^T d)) and halves alpha on rejection.
+// One thread per tet: the four corner gradients of V Psi, written to
+// corner[c * T + t].  TET_INIT / TET_EVAL: at the point x_t, and the energy
+// is reduced too (last block, fixed order, float64, plus the inertia
+// partials): TET_INIT sets g(x_1), TET_EVAL reports g.  TET_GRAD: at the
+// accepted point x_k + alpha d of the line search, corners only.
 template <typename R, int BS>
-__global__ void __launch_bounds__(BS) k_tet(DevSim<R> s, int mode, CondHandles h) {
+__global__ void __launch_bounds__(BS) k_tet(DevSim<R> s, int mode) {
+    const bool grad_mode = mode == TET_GRAD;
+    if (grad_mode && s.ctl->stop) return;
+    const R al = grad_mode ? (R)s.ctl->alpha : R(0);
     const int T = s.c.T;
     const int t = blockIdx.x * BS + threadIdx.x;
     double e[1] = {0.0};
     if (t < T) {
         const int4 v = s.tets[t];
-        const V4<R> x0 = s.xt[v.x], x1 = s.xt[v.y], x2 = s.xt[v.z], x3 = s.xt[v.w];
-        R du[3][3] = {{x1.x - x0.x, x1.y - x0.y, x1.z - x0.z},
-                      {x2.x - x0.x, x2.y - x0.y, x2.z - x0.z},
-                      {x3.x - x0.x, x3.y - x0.y, x3.z - x0.z}};
-        R Di[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Di[k] = s.dminv[(size_t)k * T + t];
+        V4<R> x0, x1, x2, x3;
+        if (grad_mode) {
+            x0 = step_point(s.xk[v.x], s.d[v.x], al);
+            x1 = step_point(s.xk[v.y], s.d[v.y], al);
+            x2 = step_point(s.xk[v.z], s.d[v.z], al);
+            x3 = step_point(s.xk[v.w], s.d[v.w], al);
+        } else {
+            x0 = s.xt[v.x]; x1 = s.xt[v.y]; x2 = s.xt[v.z]; x3 = s.xt[v.w];
+        }
+        R du[3][3], Di[9], G[3][3];
+        edge_diffs(x0, x1, x2, x3, du);
+        load_dm(s, t, Di);
+        def_grad(du, Di, G);
+        const R vol = s.vol[t];
         R g[4][3];
-        const R et = tet_energy_grad(s.mat, du, Di, s.vol[t], g);
-        e[0] = (double)et;
+        tet_grad(s.mat, G, Di, vol, g);
+        if (!grad_mode) e[0] = (double)(vol * tet_psi(s.mat, G));
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             V4<R> o;
@@ -107,6 +133,7 @@ __global__ void __launch_bounds__(BS) k_tet(DevSim<R> s, int mode, CondHandles h
             s.corner[(size_t)c * T + t] = o;
         }
     }
+    if (grad_mode) return;
     block_sum<BS, 1>(e);
     if (!publish_and_arrive<1>(e, s.part_el, 0, &s.ctl->ticket[TK_TET])) return;
     double tot[1];
@@ -127,20 +154,95 @@ __global__ void __launch_bounds__(BS) k_tet(DevSim<R> s, int mode, CondHandles h
         c->g_k = g;
         c->g0 = g;
         c->accepted = 1;
-    } else if (mode == TET_TRIAL) {
-        c->trials += 1;
-        if (g <= c->g_k + s.c.gamma * c->alpha * c->gd) {
-            c->accepted = 1;
-            set_cond<R>(h.ls, 0);
-        } else if (c->trials >= s.c.ls_max) {
-            c->accepted = 0;
-            c->stop = 1;
-            c->status = HQN_WARN_LS_EXHAUSTED;
-            set_cond<R>(h.ls, 0);
-        } else {
-            c->alpha *= s.c.backtrack;
+    }
+}
+
+// ---------------------------------------------------------------- line search
+
+// One pass of the backtracking line search of Alg. 1 that evaluates K trial
+// step lengths at once: alpha_j = alpha * backtrack^j, j < K.  Each thread
+// forms G_k = Du_k Dm^{-1} and G_d = Dd Dm^{-1} once and the energy V Psi of
+// G_k + alpha_j G_d for every j (no singular vectors: tet_psi).  The last
+// block adds the inertia term, a quadratic in alpha whose coefficients were
+// formed with the direction, and runs the Armijo tests in the order of Alg. 1:
+// the first alpha_j with g <= g_k + gamma alpha_j tr(grad^T d) is accepted
+// (the same choice as testing them one at a time).  Otherwise the next pass
+// continues from alpha_K, until ls_max trials in all.
+template <typename R, int BS, int K>
+__global__ void __launch_bounds__(BS) k_ls(DevSim<R> s, CondHandles h) {
+    Ctl *ctl = s.ctl;
+    const double a0 = ctl->alpha;
+    const double bt = s.c.backtrack;
+    const int T = s.c.T;
+    const int t = blockIdx.x * BS + threadIdx.x;
+    double e[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) e[j] = 0.0;
+    if (t < T) {
+        const int4 v = s.tets[t];
+        R Duk[3][3], Dd[3][3], Di[9], Gk[3][3], Gd[3][3];
+        edge_diffs(s.xk[v.x], s.xk[v.y], s.xk[v.z], s.xk[v.w], Duk);
+        edge_diffs(s.d[v.x], s.d[v.y], s.d[v.z], s.d[v.w], Dd);
+        load_dm(s, t, Di);
+        def_grad(Duk, Di, Gk);
+        def_grad(Dd, Di, Gd);
+        const R vol = s.vol[t];
+        double a = a0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const R al = (R)a;
+            R G[3][3];
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) G[p][q] = fma_(al, Gd[p][q], Gk[p][q]);
+            e[j] = (double)(vol * tet_psi(s.mat, G));
+            a *= bt;
         }
     }
+    block_sum<BS, K>(e);
+    if (!publish_and_arrive<K>(e, s.part_ls, gridDim.x, &ctl->ticket[TK_LS])) return;
+    double tot[K];
+    sum_partials<BS, K>(s.part_ls, gridDim.x, gridDim.x, tot, &ctl->ticket[TK_LS]);
+    if (threadIdx.x != 0) return;
+    double a = a0;
+    int tr = ctl->trials;
+    ctl->passes_total += 1;
+    const double gk = ctl->g_k, slope = s.c.gamma * ctl->gd;
+    const double c0 = ctl->ls_a[0], c1 = ctl->ls_a[1], c2 = ctl->ls_a[2];
+    bool done = false;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        if (done) break;
+        if (tr >= s.c.ls_max) {
+            ctl->accepted = 0;
+            ctl->stop = 1;
+            ctl->status = HQN_WARN_LS_EXHAUSTED;
+            done = true;
+            break;
+        }
+        tr += 1;
+        const double g = tot[j] + (c0 + a * (c1 + a * c2));
+        if (g <= gk + slope * a) {
+            ctl->accepted = 1;
+            ctl->alpha = a;
+            ctl->g_trial = g;
+            done = true;
+            break;
+        }
+        a *= bt;
+    }
+    ctl->trials = tr;
+    if (!done) {
+        ctl->alpha = a;
+        if (tr >= s.c.ls_max) {
+            ctl->accepted = 0;
+            ctl->stop = 1;
+            ctl->status = HQN_WARN_LS_EXHAUSTED;
+            done = true;
+        }
+    }
+    if (done) set_cond<R>(h.ls, 0u);
 }
 
 // ---------------------------------------------------------------- gather
@@ -157,6 +259,7 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
     const bool stop = mode == G_ITER && ctl->stop;
     const bool push = mode == G_ITER && m > 0;
     const int w = push ? (ctl->head + 1) % (m + 1) : 0;
+    const R al = mode == G_ITER ? (R)ctl->alpha : R(0);
     const int i = blockIdx.x * VBS + threadIdx.x;
     double dots[3] = {0.0, 0.0, 0.0};
     if (!stop && i < s.c.nf) {
@@ -166,7 +269,8 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
             const V4<R> cg = s.corner[s.vt_slot[k]];
             gx += cg.x; gy += cg.y; gz += cg.z;
         }
-        const V4<R> x = s.xt[i], yy = s.y[i];
+        const V4<R> x = mode == G_ITER ? step_point(s.xk[i], s.d[i], al) : s.xt[i];
+        const V4<R> yy = s.y[i];
         const R mh = s.mh2[i];
         V4<R> gn;
         gn.x = gx + mh * (x.x - yy.x);
@@ -302,21 +406,31 @@ __global__ void __launch_bounds__(VBS) k_second(DevSim<R> s, int j) {
 
 // gd = tr(grad_k^T d); with history and gd >= 0 the direction is not a
 // descent direction: flag it (and set the if-node) so the history is dropped.
+// Also the coefficients of the inertia term along the ray x_k + alpha d:
+// 1/(2h^2) sum m |x_k + alpha d - y|^2 = a0 + a1 alpha + a2 alpha^2.
 template <typename R>
 __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, int set_nd) {
     Ctl *ctl = s.ctl;
     const int i = blockIdx.x * VBS + threadIdx.x;
-    double d1[1] = {0.0};
+    double d4[4] = {0.0, 0.0, 0.0, 0.0};
     if (i < s.c.nf) {
-        const V4<R> g = s.gk[i], dd = s.d[i];
-        d1[0] = (double)g.x * dd.x + (double)g.y * dd.y + (double)g.z * dd.z;
+        const V4<R> g = s.gk[i], dd = s.d[i], x = s.xk[i], yy = s.y[i];
+        const double mh = (double)s.mh2[i];
+        const double rx = (double)x.x - yy.x, ry = (double)x.y - yy.y, rz = (double)x.z - yy.z;
+        d4[0] = (double)g.x * dd.x + (double)g.y * dd.y + (double)g.z * dd.z;
+        d4[1] = 0.5 * mh * (rx * rx + ry * ry + rz * rz);
+        d4[2] = mh * (rx * dd.x + ry * dd.y + rz * dd.z);
+        d4[3] = 0.5 * mh * ((double)dd.x * dd.x + (double)dd.y * dd.y + (double)dd.z * dd.z);
     }
-    block_sum<VBS, 1>(d1);
-    if (!publish_and_arrive<1>(d1, s.part_v, 0, &ctl->ticket[TK_VEC])) return;
-    double tot[1];
-    sum_partials<VBS, 1>(s.part_v, 0, gridDim.x, tot, &ctl->ticket[TK_VEC]);
+    block_sum<VBS, 4>(d4);
+    if (!publish_and_arrive<4>(d4, s.part_v, gridDim.x, &ctl->ticket[TK_VEC])) return;
+    double tot[4];
+    sum_partials<VBS, 4>(s.part_v, gridDim.x, gridDim.x, tot, &ctl->ticket[TK_VEC]);
     if (threadIdx.x != 0) return;
     ctl->gd = tot[0];
+    ctl->ls_a[0] = tot[1];
+    ctl->ls_a[1] = tot[2];
+    ctl->ls_a[2] = tot[3];
     const int nd = (tot[0] >= 0.0 && ctl->count > 0) ? 1 : 0;
     ctl->nondescent = nd;
     if (set_nd) set_cond<R>(h.nd, (unsigned)nd);
@@ -376,15 +490,25 @@ inline int nblk(int n) { return (n + VBS - 1) / VBS; }
 template <typename R> void launch_predict(const DevSim<R> &s, cudaStream_t st) {
     k_predict<R><<<nblk(s.c.n), VBS, 0, st>>>(s);
 }
-template <typename R> void launch_trial(const DevSim<R> &s, int apply, cudaStream_t st) {
-    k_trial<R><<<nblk(s.c.n), VBS, 0, st>>>(s, apply);
+template <typename R> void launch_inertia(const DevSim<R> &s, cudaStream_t st) {
+    k_inertia<R><<<nblk(s.c.n), VBS, 0, st>>>(s);
 }
-template <typename R> void launch_tet(const DevSim<R> &s, int mode, CondHandles h, cudaStream_t st) {
+template <typename R> void launch_tet(const DevSim<R> &s, int mode, cudaStream_t st) {
     const int T = s.c.T;
     switch (s.tet_bs) {
-        case 64: k_tet<R, 64><<<(T + 63) / 64, 64, 0, st>>>(s, mode, h); break;
-        case 256: k_tet<R, 256><<<(T + 255) / 256, 256, 0, st>>>(s, mode, h); break;
-        default: k_tet<R, 128><<<(T + 127) / 128, 128, 0, st>>>(s, mode, h); break;
+        case 64: k_tet<R, 64><<<(T + 63) / 64, 64, 0, st>>>(s, mode); break;
+        case 256: k_tet<R, 256><<<(T + 255) / 256, 256, 0, st>>>(s, mode); break;
+        default: k_tet<R, 128><<<(T + 127) / 128, 128, 0, st>>>(s, mode); break;
+    }
+}
+template <typename R> void launch_ls(const DevSim<R> &s, CondHandles h, cudaStream_t st) {
+    const int T = s.c.T, nb = (T + 127) / 128;
+    switch (s.c.ls_batch) {
+        case 1: k_ls<R, 128, 1><<<nb, 128, 0, st>>>(s, h); break;
+        case 2: k_ls<R, 128, 2><<<nb, 128, 0, st>>>(s, h); break;
+        case 4: k_ls<R, 128, 4><<<nb, 128, 0, st>>>(s, h); break;
+        case 16: k_ls<R, 128, 16><<<nb, 128, 0, st>>>(s, h); break;
+        default: k_ls<R, 128, 8><<<nb, 128, 0, st>>>(s, h); break;
     }
 }
 template <typename R> void launch_gather(const DevSim<R> &s, int mode, CondHandles h, cudaStream_t st) {
@@ -415,8 +539,9 @@ template <typename R> void launch_pair_rho(const DevSim<R> &s, int slot, cudaStr
 
 #define HQN_INST(R)                                                                  \
     template void launch_predict<R>(const DevSim<R> &, cudaStream_t);                \
-    template void launch_trial<R>(const DevSim<R> &, int, cudaStream_t);             \
-    template void launch_tet<R>(const DevSim<R> &, int, CondHandles, cudaStream_t);  \
+    template void launch_inertia<R>(const DevSim<R> &, cudaStream_t);                \
+    template void launch_tet<R>(const DevSim<R> &, int, cudaStream_t);               \
+    template void launch_ls<R>(const DevSim<R> &, CondHandles, cudaStream_t);        \
     template void launch_gather<R>(const DevSim<R> &, int, CondHandles, cudaStream_t); \
     template void launch_first_loop<R>(const DevSim<R> &, int, cudaStream_t);        \
     template void launch_second_loop<R>(const DevSim<R> &, int, cudaStream_t);       \

@@ -26,16 +26,19 @@ struct DevSim {
     V4<R> *u_cur, *u_prev, *y, *xk, *xt, *gk, *d, *q, *z;
     V4<R> *S, *Tt;              // (m + 1) x n history ring
     V4<R> *corner;              // 4 x T corner gradients
-    double *part_in, *part_el, *part_g, *part_v;
+    double *part_in, *part_el, *part_g, *part_v, *part_ls;
     Ctl *ctl;
 };
 
-enum TetMode { TET_INIT = 0, TET_TRIAL = 1, TET_EVAL = 2 };
+enum TetMode { TET_INIT = 0, TET_GRAD = 1, TET_EVAL = 2 };
 enum GatherMode { G_INIT = 0, G_ITER = 1, G_EVAL = 2 };
 
 template <typename R> void launch_predict(const DevSim<R> &s, cudaStream_t st);
-template <typename R> void launch_trial(const DevSim<R> &s, int apply, cudaStream_t st);
-template <typename R> void launch_tet(const DevSim<R> &s, int mode, CondHandles h, cudaStream_t st);
+// Inertia partials of the caller-given point x_t.
+template <typename R> void launch_inertia(const DevSim<R> &s, cudaStream_t st);
+template <typename R> void launch_tet(const DevSim<R> &s, int mode, cudaStream_t st);
+// One multi-trial line-search pass (K = ls_batch step lengths).
+template <typename R> void launch_ls(const DevSim<R> &s, CondHandles h, cudaStream_t st);
 template <typename R> void launch_gather(const DevSim<R> &s, int mode, CondHandles h, cudaStream_t st);
 // Alg. 2 first loop: p = -1 starts it (q = -grad), p = 0..m-1 applies pair p.
 template <typename R> void launch_first_loop(const DevSim<R> &s, int p, cudaStream_t st);
@@ -50,19 +53,24 @@ template <typename R> void launch_commit(const DevSim<R> &s, cudaStream_t st);
 template <typename R> void launch_pair_rho(const DevSim<R> &s, int slot, cudaStream_t st);
 
 // ---- triangular solves (solve.cu)
+constexpr int SOLVE_MAX_SMEM = 220 * 1024;  // dynamic shared memory of one sweep block
+
 template <typename R>
 struct DevSolve {
     int nf, n_levels;
-    const R *Q;                 // concatenated Q_s, row-major
+    const R *QF;                // per supernode: Q_s row-major, rows padded to ldc (16 B)
+    const R *QB;                // per supernode: Q_s^T row-major, rows padded to ldr (16 B)
     const int4 *sn;             // (col, ncol, nrow, roff)
-    const long long *sn_q;      // offset of Q_s
+    const long long *sn_qf, *sn_qb;  // offsets of the two copies
+    const int2 *sn_ld;          // (ldc, ldr)
     const int *sn_u;            // offset of the supernode's update entries
     const int *rows;            // row structures
-    const int *fg_ptr, *fg_idx; // per column: child update entries to subtract
-    const int *ug_ptr, *ug_idx; // per update entry: child update entries to add
-    const int4 *fwd_items, *bwd_items;
-    const int *fwd_lvl_ptr, *bwd_lvl_ptr;  // host copies (launch sizes)
-    const int *fwd_lvl_cols;    // host: max ncol of the level (shared memory of the forward sweep)
+    const int2 *fg2;            // per column: the (<= 2) child update entries to subtract
+    const int2 *ug2;            // per update entry: the (<= 2) child update entries to add
+    const int4 *fwd_items;      // (s, row0, row1, G)
+    const int4 *bwd_items;      // (s, col0, col1, G)
+    const int *fwd_lvl_ptr, *bwd_lvl_ptr;  // host: items of level l in [ptr[l], ptr[l+1])
+    const int *fwd_lvl_ld, *bwd_lvl_ld;    // host: max ldc / ldr of the level (shared memory)
     V4<R> *u;                   // update vectors
 };
 

@@ -594,45 +594,99 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
         for (int u = 0; u < utot; ++u) S.ug_idx.insert(S.ug_idx.end(), ug[u].begin(), ug[u].end());
     }
 
-    // ---- level work lists
+    // ---- pair form of the extend-add maps (a binary tree: <= 2 sources per entry)
+    S.fg2.assign(2 * (size_t)nf, -1);
+    S.ug2.assign(2 * (size_t)utot, -1);
+    for (int j = 0; j < nf; ++j) {
+        const int c = S.fg_ptr[j + 1] - S.fg_ptr[j];
+        if (c > 2) {
+            err = "a column receives updates from more than two children";
+            return HQN_ERR_ARG;
+        }
+        for (int k = 0; k < c; ++k) S.fg2[2 * (size_t)j + k] = S.fg_idx[S.fg_ptr[j] + k];
+    }
+    for (int u = 0; u < utot; ++u) {
+        const int c = S.ug_ptr[u + 1] - S.ug_ptr[u];
+        if (c > 2) {
+            err = "an update entry receives from more than two children";
+            return HQN_ERR_ARG;
+        }
+        for (int k = 0; k < c; ++k) S.ug2[2 * (size_t)u + k] = S.ug_idx[S.ug_ptr[u] + k];
+    }
+
+    // ---- padded device layout and level work lists
+    // VN = entries per 16-byte vector in the device precision; rows of both
+    // copies are padded to a multiple of 4 entries (16 bytes in float, 32 in
+    // double), so every row starts 16-byte aligned.
+    const int VN = prm.precision == HQN_FP64_PLAIN ? 2 : 4;
+    S.qf_total = S.qb_total = 0;
+    S.max_ld = 0;
+    for (auto &sn : S.sn) {
+        sn.ldc = (sn.ncol + 3) / 4 * 4;
+        sn.ldr = (sn.ncol + sn.nrow + 3) / 4 * 4;
+        sn.qf = S.qf_total;
+        sn.qb = S.qb_total;
+        S.qf_total += (int64_t)(sn.ncol + sn.nrow) * sn.ldc;
+        S.qb_total += (int64_t)sn.ncol * sn.ldr;
+        S.max_ld = std::max(S.max_ld, std::max(sn.ldc, sn.ldr));
+    }
+    // lanes per output row: enough that each lane streams a few 16-byte vectors
+    auto lanes_for = [&](int len) {
+        const int nv = (len + VN - 1) / VN;
+        int G = 1;
+        while (G < 32 && G * 4 < nv) G *= 2;
+        return G;
+    };
+    constexpr int kBS = 256;                   // threads per block of the sweeps
+    const int kEntries = VN == 4 ? 16384 : 8192;  // target matrix entries per work item
     int L = 0;
     for (auto &sn : S.sn) L = std::max(L, sn.level + 1);
     S.n_levels = L;
     S.fwd_lvl_ptr.assign(L + 1, 0);
     S.bwd_lvl_ptr.assign(L + 1, 0);
+    S.fwd_lvl_ld.assign(L, 0);
+    S.bwd_lvl_ld.assign(L, 0);
     S.fwd_items.clear();
     S.bwd_items.clear();
-    constexpr int kFwdEntries = 8192;  // target matrix entries per forward work item
-    constexpr int kBwdEntries = 8192;  // target matrix entries per backward work item
     for (int l = 0; l < L; ++l) {
         S.fwd_lvl_ptr[l] = (int)S.fwd_items.size();
         for (int s = 0; s < ns; ++s) {
             const SupernodeHost &sn = S.sn[s];
             if (sn.level != l || sn.ncol == 0) continue;
+            S.fwd_lvl_ld[l] = std::max(S.fwd_lvl_ld[l], sn.ldc);
             const int rows = sn.ncol + sn.nrow;
-            int chunk = std::max(8, kFwdEntries / std::max(1, sn.ncol));
-            chunk = (chunk + 7) / 8 * 8;
-            for (int r0 = 0; r0 < rows; r0 += chunk)
-                S.fwd_items.push_back({s, r0, std::min(rows, r0 + chunk), 0});
+            // triangle rows (short, growing) and rectangle rows (length ncol)
+            // get separate items so one G fits every row of an item
+            const int G = lanes_for(sn.ncol);
+            const int ng = kBS / G;
+            int chunk = std::max(1, kEntries / std::max(1, sn.ncol));
+            chunk = (chunk + ng - 1) / ng * ng;
+            for (int r0 = 0; r0 < sn.ncol; r0 += chunk) {
+                const int r1 = std::min(sn.ncol, r0 + chunk);
+                S.fwd_items.push_back({s, r0, r1, lanes_for(r1)});
+            }
+            for (int r0 = sn.ncol; r0 < rows; r0 += chunk)
+                S.fwd_items.push_back({s, r0, std::min(rows, r0 + chunk), G});
         }
     }
     S.fwd_lvl_ptr[L] = (int)S.fwd_items.size();
-    // backward: levels from the root down; level index l here means tree level l
+    // backward: tree level l (launched from the root level down)
     for (int l = 0; l < L; ++l) {
         S.bwd_lvl_ptr[l] = (int)S.bwd_items.size();
         for (int s = 0; s < ns; ++s) {
             const SupernodeHost &sn = S.sn[s];
             if (sn.level != l || sn.ncol == 0) continue;
+            S.bwd_lvl_ld[l] = std::max(S.bwd_lvl_ld[l], sn.ldr);
             const int rows = sn.ncol + sn.nrow;
-            for (int c0 = 0; c0 < sn.ncol; c0 += 32) {
-                // rows [c0, rows): split into chunks so one item reads ~kBwdEntries
-                const int span = rows - c0;
-                int chunk = std::max(64, kBwdEntries / 32);
-                if (span <= chunk) {
-                    S.bwd_items.push_back({s, c0, c0, 0});
-                } else {
-                    S.bwd_items.push_back({s, c0, c0, 0});  // one item per column block
-                }
+            for (int c0 = 0; c0 < sn.ncol;) {
+                const int len = rows - c0;  // entries of Q_s^T row c0 from the diagonal on
+                const int G = lanes_for(len);
+                const int ng = kBS / G;
+                int chunk = std::max(1, kEntries / std::max(1, len));
+                chunk = (chunk + ng - 1) / ng * ng;
+                const int c1 = std::min(sn.ncol, c0 + chunk);
+                S.bwd_items.push_back({s, c0, c1, G});
+                c0 = c1;
             }
         }
     }

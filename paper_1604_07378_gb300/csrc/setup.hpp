@@ -28,11 +28,16 @@ struct SupernodeHost {
     int64_t qoff = 0;                 // offset of Q_s = [L_ss^{-1}; L_Rs L_ss^{-1}] (rows x ncol)
     int uoff = 0;                     // offset of its update vector (nrow entries)
     int roff = 0;                     // offset of R in the row-index array
+    // device layout: Q_s row-major with rows padded to ldc entries (forward
+    // sweep) and Q_s^T row-major with rows padded to ldr entries (backward)
+    int ldc = 0, ldr = 0;
+    int64_t qf = 0, qb = 0;           // offsets of the two padded copies
     std::vector<int> children;
 };
 
-struct FwdItem { int s, row0, row1, pad; };
-struct BwdItem { int s, col0, row0, pad; };
+// Work items of the device sweeps.  G = lanes that share one output row.
+struct FwdItem { int s, row0, row1, G; };  // rows [row0, row1) of Q_s f
+struct BwdItem { int s, col0, col1, G; };  // entries [col0, col1) of Q_s^T w
 
 struct Setup {
     int n = 0, T = 0, n_free = 0;
@@ -53,11 +58,16 @@ struct Setup {
     std::vector<double> Q;           // concatenated Q_s, row-major
     std::vector<int> fg_ptr, fg_idx; // per free column: child update entries to subtract
     std::vector<int> ug_ptr, ug_idx; // per update entry: child update entries to add
+    std::vector<int> fg2, ug2;       // the same maps as pairs (-1 = none): at most two
+                                     // children (a binary dissection tree) feed an entry
     int n_upd = 0, n_levels = 0;
     std::vector<int> fwd_lvl_ptr, bwd_lvl_ptr;  // items of level l: [ptr[l], ptr[l+1])
+    std::vector<int> fwd_lvl_ld, bwd_lvl_ld;    // max ldc / ldr over the level's supernodes
     std::vector<FwdItem> fwd_items;
     std::vector<BwdItem> bwd_items;
-    int max_front_cols = 0;          // max ncol (shared-memory size of the forward sweep)
+    int64_t qf_total = 0, qb_total = 0;  // entries of the two padded copies
+    int max_ld = 0;                  // max(ldc, ldr): shared-memory size of a sweep block
+    int max_front_cols = 0;          // max ncol
     int64_t factor_nnz = 0;
     double setup_seconds = 0.0;
 };

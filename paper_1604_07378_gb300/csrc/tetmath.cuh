@@ -46,8 +46,8 @@ __device__ __forceinline__ R x_minus_log1p(R x) {
 
 // One Jacobi rotation zeroing A[p][q] of the symmetric 3x3 A (Golub & Van Loan,
 // "Matrix Computations", the symmetric Schur decomposition of Sec. 8.5), with
-// the rotation accumulated into the columns of V.
-template <typename R, int p, int q>
+// the rotation accumulated into the columns of V when WithV.
+template <typename R, int p, int q, bool WithV>
 __device__ __forceinline__ void jacobi_rotate(R A[3][3], R V[3][3]) {
     const R apq = A[p][q];
     if (apq == R(0)) return;
@@ -64,12 +64,37 @@ __device__ __forceinline__ void jacobi_rotate(R A[3][3], R V[3][3]) {
     const R arp = A[r][p], arq = A[r][q];
     A[r][p] = A[p][r] = c * arp - s * arq;
     A[r][q] = A[q][r] = s * arp + c * arq;
+    if (WithV) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const R vp = V[i][p], vq = V[i][q];
-        V[i][p] = c * vp - s * vq;
-        V[i][q] = s * vp + c * vq;
+        for (int i = 0; i < 3; ++i) {
+            const R vp = V[i][p], vq = V[i][q];
+            V[i][p] = c * vp - s * vq;
+            V[i][q] = s * vp + c * vq;
+        }
     }
+}
+
+// Cyclic Jacobi sweeps until the off-diagonal part is at round-off level.
+template <typename R, bool WithV>
+__device__ __forceinline__ void jacobi_sweeps(R A[3][3], R V[3][3]) {
+    for (int sweep = 0; sweep < 8; ++sweep) {
+        const R off = abs_(A[0][1]) + abs_(A[0][2]) + abs_(A[1][2]);
+        const R dia = abs_(A[0][0]) + abs_(A[1][1]) + abs_(A[2][2]);
+        if (!(off > R(0.25) * Eps<R>::v * dia)) break;
+        jacobi_rotate<R, 0, 1, WithV>(A, V);
+        jacobi_rotate<R, 0, 2, WithV>(A, V);
+        jacobi_rotate<R, 1, 2, WithV>(A, V);
+    }
+}
+
+// S = F^T F - I = G + G^T + G^T G for F = I + G.
+template <typename R>
+__device__ __forceinline__ void strain2(const R G[3][3], R A[3][3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            A[a][b] = G[a][b] + G[b][a] + G[0][a] * G[0][b] + G[1][a] * G[1][b] + G[2][a] * G[2][b];
 }
 
 template <typename R>
@@ -90,23 +115,12 @@ __device__ __forceinline__ void swap_cols(R l[3], R V[3][3], int a, int b) {
 template <typename R>
 __device__ __forceinline__ void signed_svd(const R G[3][3], R U[3][3], R s[3], R l[3], R V[3][3]) {
     R A[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b)
-            A[a][b] = G[a][b] + G[b][a] + G[0][a] * G[0][b] + G[1][a] * G[1][b] + G[2][a] * G[2][b];
+    strain2(G, A);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) V[a][b] = a == b ? R(1) : R(0);
-    for (int sweep = 0; sweep < 8; ++sweep) {
-        const R off = abs_(A[0][1]) + abs_(A[0][2]) + abs_(A[1][2]);
-        const R dia = abs_(A[0][0]) + abs_(A[1][1]) + abs_(A[2][2]);
-        if (!(off > R(0.25) * Eps<R>::v * dia)) break;
-        jacobi_rotate<R, 0, 1>(A, V);
-        jacobi_rotate<R, 0, 2>(A, V);
-        jacobi_rotate<R, 1, 2>(A, V);
-    }
+    jacobi_sweeps<R, true>(A, V);
     l[0] = A[0][0]; l[1] = A[1][1]; l[2] = A[2][2];
     if (l[0] < l[1]) swap_cols(l, V, 0, 1);
     if (l[0] < l[2]) swap_cols(l, V, 0, 2);
@@ -264,23 +278,89 @@ __device__ __forceinline__ R material_tau(const MatDev<R> &M, const R s[3], cons
     }
 }
 
-// Energy V*Psi of one tet and its gradients with respect to the four corner
-// positions.  du[j] = u_{j} - u_0 (j = 1..3 as 0..2), Di = Dm^{-1} row-major.
-// First Piola P = U diag(tau) V^T; corners 1..3 get the columns of V P Dm^{-T},
-// corner 0 minus their sum.
+// Psi(F) alone, F = I + G, for the line-search trials (no singular vectors).
+// Neo-Hookean and StVK use the invariants, written so that no first-order
+// term is cancelled against another:
+//   NH:   I1 - 3 - 2 ln J = |G|^2 - 2 (m2 + det G) + 2 (d - log1p d),
+//         d = det F - 1 = tr G + m2 + det G, m2 = sum of principal 2x2 minors of G;
+//   StVK: mu |E|^2 + lam/2 tr^2 E with E = S / 2.
+// The other materials take the stretches from the eigenvalues of S (Jacobi
+// without vectors); s3 carries the sign of det F.
 template <typename R>
-__device__ __forceinline__ R tet_energy_grad(const MatDev<R> &M, const R du[3][3], const R Di[9], R vol,
-                                             R g[4][3]) {
-    R G[3][3];
+__device__ __forceinline__ R tet_psi(const MatDev<R> &M, const R G[3][3]) {
+    if (M.kind == HQN_NEOHOOKEAN) {
+        const R tr = G[0][0] + G[1][1] + G[2][2];
+        R n2 = R(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) n2 += G[a][b] * G[a][b];
+        const R m2 = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) + (G[0][0] * G[2][2] - G[0][2] * G[2][0]) +
+                     (G[1][1] * G[2][2] - G[1][2] * G[2][1]);
+        const R dg = G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) -
+                     G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
+                     G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
+        const R d = tr + m2 + dg;
+        const R J = R(1) + d;
+        if (J >= M.J0) {
+            const R lnJ = log1p_(d);
+            return R(0.5) * M.mu * (n2 - R(2) * (m2 + dg) + R(2) * x_minus_log1p(d)) + R(0.5) * M.lam * lnJ * lnJ;
+        }
+        const R dJ = J - M.J0;
+        return R(0.5) * M.mu * (R(2) * tr + n2) + M.c0 + dJ * (M.c1 + R(0.5) * M.c2 * dJ);
+    }
+    R A[3][3];
+    strain2(G, A);
+    if (M.kind == HQN_STVK) {
+        const R tr = R(0.5) * (A[0][0] + A[1][1] + A[2][2]);
+        R n2 = R(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) n2 += A[a][b] * A[a][b];
+        return R(0.25) * M.mu * n2 + R(0.5) * M.lam * tr * tr;
+    }
+    R Vd[3][3];
+    jacobi_sweeps<R, false>(A, Vd);
+    R l[3] = {A[0][0], A[1][1], A[2][2]};
+    if (l[0] < l[1]) { R t = l[0]; l[0] = l[1]; l[1] = t; }
+    if (l[0] < l[2]) { R t = l[0]; l[0] = l[2]; l[2] = t; }
+    if (l[1] < l[2]) { R t = l[1]; l[1] = l[2]; l[2] = t; }
+    const R dg = G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) -
+                 G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
+                 G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
+    const R d = (G[0][0] + G[1][1] + G[2][2]) +
+                (G[0][0] * G[1][1] - G[0][1] * G[1][0]) + (G[0][0] * G[2][2] - G[0][2] * G[2][0]) +
+                (G[1][1] * G[2][2] - G[1][2] * G[2][1]) + dg;
+    R s[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) s[i] = sqrt_(R(1) + l[i] > R(0) ? R(1) + l[i] : R(0));
+    if (d < R(-1)) s[2] = -s[2];
+    R tau[3];
+    return material_tau(M, s, l, tau);
+}
+
+template <typename R> __device__ __forceinline__ R fma_(R a, R b, R c) { return fma(a, b, c); }
+
+// G = Du Dm^{-1}: du[j] = u_{j+1} - u_0 (rows), Di = Dm^{-1} row-major.
+template <typename R>
+__device__ __forceinline__ void def_grad(const R du[3][3], const R Di[9], R G[3][3]) {
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b)
             G[a][b] = du[0][a] * Di[0 * 3 + b] + du[1][a] * Di[1 * 3 + b] + du[2][a] * Di[2 * 3 + b];
+}
+
+// Gradients of V*Psi with respect to the four corner positions, F = I + G.
+// First Piola P = U diag(tau) V^T; corners 1..3 get the columns of V P Dm^{-T},
+// corner 0 minus their sum.
+template <typename R>
+__device__ __forceinline__ void tet_grad(const MatDev<R> &M, const R G[3][3], const R Di[9], R vol, R g[4][3]) {
     R U[3][3], s[3], l[3], V[3][3];
     signed_svd(G, U, s, l, V);
     R tau[3];
-    const R psi = material_tau(M, s, l, tau);
+    material_tau(M, s, l, tau);
     R P[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -294,7 +374,6 @@ __device__ __forceinline__ R tet_energy_grad(const MatDev<R> &M, const R du[3][3
             g[j + 1][a] = P[a][0] * Di[j * 3 + 0] + P[a][1] * Di[j * 3 + 1] + P[a][2] * Di[j * 3 + 2];
 #pragma unroll
     for (int a = 0; a < 3; ++a) g[0][a] = -(g[1][a] + g[2][a] + g[3][a]);
-    return vol * psi;
 }
 
 }  // namespace hqn

@@ -25,6 +25,7 @@ HQN_ERR_NO_MEMORY = -6
 HQN_ERR_UNSUPPORTED = -7
 
 NEOHOOKEAN, STVK, SPLINE_VL, COROTATED, POLY4 = 0, 1, 2, 3, 4
+STAGE_TET, STAGE_GATHER, STAGE_SOLVE, STAGE_LS_PASS, STAGE_TWO_LOOP = 0, 1, 2, 3, 4
 FP64_PLAIN, FP32_MIXED = 0, 1
 MAX_HISTORY, MAX_ITERS = 16, 64
 
@@ -48,14 +49,14 @@ class Params(C.Structure):
                 ("x_start", C.c_double), ("x_end", C.c_double), ("gravity", C.c_double * 3),
                 ("iters", C.c_int32), ("history_m", C.c_int32), ("ls_max", C.c_int32),
                 ("precision", C.c_int32), ("leaf_size", C.c_int32), ("use_graph", C.c_int32),
-                ("tet_block", C.c_int32)]
+                ("tet_block", C.c_int32), ("ls_batch", C.c_int32)]
 
 
 class StepStats(C.Structure):
     _fields_ = [("steps", C.c_int32), ("iters", C.c_int32), ("status", C.c_int32),
                 ("trials_total", C.c_int32), ("iters_total", C.c_int32),
                 ("trials", C.c_int32 * MAX_ITERS), ("g0", C.c_double),
-                ("g", C.c_double * MAX_ITERS)]
+                ("g", C.c_double * MAX_ITERS), ("ls_passes_total", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -92,6 +93,7 @@ def library(path: str | None = None):
     lib.sim_solve_A0.argtypes = [C.c_void_p, _dp, _dp]
     lib.sim_direction.argtypes = [C.c_void_p, _dp, C.c_int32, _dp, _dp, _dp]
     lib.sim_get_info.argtypes = [C.c_void_p, C.POINTER(Info)]
+    lib.sim_time_stage.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _dp]
     lib.sim_destroy.argtypes = [C.c_void_p]
     lib.sim_destroy.restype = None
     lib.sim_strerror.argtypes = [C.c_int]
@@ -99,7 +101,7 @@ def library(path: str | None = None):
     lib.hqn_last_error.argtypes = []
     lib.hqn_last_error.restype = C.c_char_p
     for f in ("sim_set_state", "sim_get_state", "sim_step", "sim_energy_grad", "sim_solve_A0",
-              "sim_direction", "sim_get_info"):
+              "sim_direction", "sim_get_info", "sim_time_stage"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -209,7 +211,8 @@ class Sim:
         k = st.iters
         return rc, {"steps": st.steps, "iters": k, "status": st.status,
                     "trials_total": st.trials_total, "iters_total": st.iters_total,
-                    "trials": list(st.trials[:k]), "g0": st.g0, "g": list(st.g[:k])}
+                    "trials": list(st.trials[:k]), "g0": st.g0, "g": list(st.g[:k]),
+                    "ls_passes_total": st.ls_passes_total}
 
     def energy_grad(self, x, y):
         x, y = self._vec(x), self._vec(y)
@@ -238,6 +241,13 @@ class Sim:
         _check(library().sim_direction(self._h, _ptr(grad), npairs, sp, tp, _ptr(d)),
                "sim_direction")
         return d
+
+    def time_stage(self, stage, reps=20):
+        """Mean device milliseconds of one launch of a stage (CUDA events on the
+        handle's stream)."""
+        ms = C.c_double()
+        _check(library().sim_time_stage(self._h, stage, reps, C.byref(ms)), "sim_time_stage")
+        return ms.value
 
     def info(self) -> dict:
         i = Info()
