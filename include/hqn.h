@@ -205,6 +205,56 @@ const char *sim_strerror(int code);
 /* Message of the last error raised on the calling thread ("" if none). */
 const char *hqn_last_error(void);
 
+/* ---- allocation-free evaluation ------------------------------------------
+ * The paper has no counterpart of this entry point; it exists for callers
+ * that cannot allocate device memory: code running inside a memory pool or
+ * budget owned by someone else, plug-ins that must not call the CUDA
+ * allocator, and drivers that forbid cudaMalloc once they are running.
+ *
+ * hqn_energy_grad_static computes g(x) = 1/(2h^2) sum_v m_v |x_v - y_v|^2 +
+ * sum_t V_t Psi(F_t) and grad g(x) -- the quantities sim_energy_grad returns
+ * -- in float64 without a handle and without allocating anything.  Its
+ * scratch (per-tet corner gradients, per-block partial sums) is one
+ * fixed-size array of about 8.4 MB that the library places in each GPU's
+ * memory when it is loaded there and keeps until the process exits.
+ *
+ * Arguments (device pointers unless stated; all caller-owned, caller order):
+ *   n_verts, n_tets   1 <= n_tets <= HQN_STATIC_MAX_TETS,
+ *                     1 <= n_verts <= HQN_STATIC_MAX_VERTS; larger meshes
+ *                     are rejected with HQN_ERR_ARG before any device work
+ *   rest_pos          n_verts x 3 doubles, rest positions X
+ *   tets              n_tets x 4 int32, det[X1-X0, X2-X0, X3-X0] > 0 (a tet
+ *                     that breaks this makes *g_out NaN)
+ *   clamped           n_verts bytes, nonzero = gradient row set to zero; may be NULL
+ *   vt_ptr, vt_slot   incident-corner CSR: the corners of vertex v are
+ *                     vt_slot[vt_ptr[v] .. vt_ptr[v+1]), each encoded as
+ *                     4 * tet + corner (vt_ptr has n_verts + 1 entries); the
+ *                     gradient sums them in this order (no atomics)
+ *   material          HOST pointer; density gives the lumped mass
+ *                     m_v = density * sum of incident V_t / 4
+ *   h                 time step (> 0)
+ *   x, y              n_verts x 3 doubles: positions and inertial target
+ *   g_out             one double (device)
+ *   grad_out          n_verts x 3 doubles (device)
+ *   stream            cudaStream_t (NULL = legacy default stream)
+ * Work is enqueued on `stream`; the call returns without synchronising.
+ *
+ * The first call made with a given device current looks up the scratch's
+ * device address on that device (once per device), so make that first call
+ * before any stream capture.  Every call on a device shares the one scratch
+ * array, which keeps the last call's contents; the call clears what must
+ * start at zero itself.  Calls whose device work overlaps (different streams
+ * or threads without ordering between them) race on the scratch and give
+ * wrong results: order them on one stream.
+ * Errors: HQN_ERR_ARG (sizes, null pointers, h, material), HQN_ERR_CUDA. */
+#define HQN_STATIC_MAX_TETS  65536
+#define HQN_STATIC_MAX_VERTS 262144
+int hqn_energy_grad_static(int32_t n_verts, int32_t n_tets, const double *rest_pos,
+                           const int32_t *tets, const uint8_t *clamped, const int32_t *vt_ptr,
+                           const int32_t *vt_slot, const hqn_material *material, double h,
+                           const double *x, const double *y, double *g_out, double *grad_out,
+                           void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 
 CXX_SOURCES = ["setup.cpp", "dense.cpp"]
-CU_SOURCES = ["kernels.cu", "solve.cu", "api.cu"]
+CU_SOURCES = ["kernels.cu", "solve.cu", "api.cu", "noalloc.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

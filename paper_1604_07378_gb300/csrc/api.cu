@@ -580,6 +580,11 @@ struct Sim final : SimBase {
 
 }  // namespace
 
+namespace hqn {
+// Sets the message hqn_last_error() reports (for entry points in other files).
+void set_last_error(const char *msg) { g_last_error = msg; }
+}  // namespace hqn
+
 struct sim_handle {
     std::unique_ptr<SimBase> impl;
 };

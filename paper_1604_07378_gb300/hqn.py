@@ -23,6 +23,7 @@ HQN_ERR_NOT_SPD = -4
 HQN_ERR_CUDA = -5
 HQN_ERR_NO_MEMORY = -6
 HQN_ERR_UNSUPPORTED = -7
+STATIC_MAX_TETS, STATIC_MAX_VERTS = 65536, 262144
 
 NEOHOOKEAN, STVK, SPLINE_VL, COROTATED, POLY4 = 0, 1, 2, 3, 4
 STAGE_TET, STAGE_GATHER, STAGE_SOLVE, STAGE_LS_PASS, STAGE_TWO_LOOP = 0, 1, 2, 3, 4
@@ -100,6 +101,10 @@ def library(path: str | None = None):
     lib.sim_strerror.restype = C.c_char_p
     lib.hqn_last_error.argtypes = []
     lib.hqn_last_error.restype = C.c_char_p
+    lib.hqn_energy_grad_static.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.POINTER(Material), C.c_double,
+                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.hqn_energy_grad_static.restype = C.c_int
     for f in ("sim_set_state", "sim_get_state", "sim_step", "sim_energy_grad", "sim_solve_A0",
               "sim_direction", "sim_get_info", "sim_time_stage"):
         getattr(lib, f).restype = C.c_int
