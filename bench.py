@@ -177,10 +177,12 @@ def run_ours(args, rank, world, dist):
     stage_ms = {name: sim.time_stage(code, 20) for name, code in (
         ("tet", hqn.STAGE_TET), ("gather", hqn.STAGE_GATHER), ("solve", hqn.STAGE_SOLVE),
         ("ls_pass", hqn.STAGE_LS_PASS), ("two_loop_with_solve", hqn.STAGE_TWO_LOOP))}
+    # line-search passes: the fused first trial (a tet pass with the gradient)
+    # of every iteration plus the multi-trial passes after a rejection
     passes = stats["ls_passes_total"] / args.steps
     per_step = {"tet": stage_ms["tet"] * (iters + 1), "solve": stage_ms["solve"] * iters,
                 "gather": stage_ms["gather"] * (iters + 1),
-                "ls_pass": stage_ms["ls_pass"] * passes,
+                "ls_pass": stage_ms["ls_pass"] * max(passes - iters, 0.0),
                 "two_loop": max(stage_ms["two_loop_with_solve"] - stage_ms["solve"], 0.0) * iters}
     dominant = max(per_step, key=per_step.get)
 
@@ -258,6 +260,8 @@ def run_ours(args, rank, world, dist):
         "config": {"workload": WORKLOAD, "lattice": "40x40x40 Kuhn cubes", "tets": T,
                    "vertices": n, "material": "Neo-Hookean E=5e5 nu=0.4", "iters": w.iters,
                    "history_m": w.history, "h": w.h, "parallelism": f"replicas{world}",
+                   "initial_velocity": "one seeded body velocity, U[-0.5, 0.5]^3 m/s",
+                   "chained_sweeps": bool(info.get("chained_sweeps", 0)),
                    "l2": "working set %.0f MB > 129 MB L2 (factor alone %.0f MB)" % (
                        info["device_bytes"] / 1e6, info["factor_entries"] * 4 / 1e6)},
         "tet_grad_evals_per_s": world * tet_evals_step * args.steps / (ms / 1e3),
@@ -272,12 +276,12 @@ def run_ours(args, rank, world, dist):
         "gpu_launches": None,
         "status": rc,
     }
-    # kernels per step: start (predictor, inertia, tet, gather) + commit, and per
-    # iteration: both loops of Alg. 2 (2m + 2), the sweeps (2 per tree level),
-    # direction final, line-search begin, tet gradient, gather; plus every
-    # line-search pass
+    # kernels per step: start (predictor, inertia, tet, gather) + commit; per
+    # iteration: q, the sweeps (2 per tree level), t^T r0 products (m > 0),
+    # direction final, tet gradient (returns at once after an accepted first
+    # trial), gather; plus every line-search pass (fused first trial included)
     m = w.history
-    per_iter = 2 * (m + 1) + 2 * info["n_levels"] + 4
+    per_iter = 1 + 2 * info["n_levels"] + (1 if m > 0 else 0) + 1 + 2
     launches = args.steps * 5 + stats["iters_total"] * per_iter + stats["ls_passes_total"]
     line["gpu_launches"] = launches
     if rank == 0 and not args.no_cpu_baseline:

@@ -103,9 +103,11 @@ typedef struct {
                              loops; 0 = host-driven launches (same kernels)        */
     int32_t tet_block;    /* threads per block of the tet kernel: 64, 128 or 256
                              (0 = default 128)                                     */
-    int32_t ls_batch;     /* line-search step lengths tested per tet pass: 1, 2, 4,
-                             8 or 16 (0 = default 8); the accepted alpha is the
-                             one Alg. 1's sequential backtracking would accept    */
+    int32_t ls_batch;     /* line search: the first trial (alpha = 1) is one tet pass
+                             fused with the gradient; after a rejection each pass
+                             tests ls_batch step lengths (1, 2, 4, 8 or 16; 0 =
+                             default 8).  The accepted alpha is the one Alg. 1's
+                             sequential backtracking would accept                  */
 } hqn_params;
 
 #define HQN_MAX_HISTORY 16
@@ -135,6 +137,8 @@ typedef struct {
     int32_t precision;          /* hqn_precision in use                               */
     int32_t graph_mode;         /* 1 if steps run as a CUDA graph                     */
     int64_t n_update_entries;   /* entries of the forward-sweep update vectors        */
+    int32_t chained_sweeps;     /* 1 if the sweep levels use programmatic dependent
+                                   launch (a level starts while the previous finishes) */
 } hqn_info;
 
 typedef struct sim_handle sim_handle;

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "layout.hpp"
 #include "setup.hpp"
 
 using namespace hqn;
@@ -186,25 +187,32 @@ struct Sim final : SimBase {
         const int nbv = (n + VBS - 1) / VBS, nbf = (nf + VBS - 1) / VBS, nbt = (T + 63) / 64;
         if ((rc = alloc(ds.part_in, nbv))) return rc;
         if ((rc = alloc(ds.part_el, nbt))) return rc;
-        if ((rc = alloc(ds.part_g, (size_t)3 * nbf))) return rc;
-        if ((rc = alloc(ds.part_v, (size_t)4 * nbf))) return rc;
+        // per-block partials: up to 3 + 3 (m + 1) sums (gather with a history
+        // push), m + 2 (caller-given history rows), m + 1 or 4 (direction)
+        if ((rc = alloc(ds.part_g, (size_t)(3 + 3 * (HQN_MAX_HISTORY + 1)) * nbf))) return rc;
+        if ((rc = alloc(ds.part_v, (size_t)(HQN_MAX_HISTORY + 1) * nbf))) return rc;
         if ((rc = alloc(ds.part_ls, (size_t)16 * ((T + 127) / 128)))) return rc;
         if ((rc = alloc(ds.ctl, 1))) return rc;
         CK(cudaMallocHost(&h_ctl, sizeof(Ctl)));
         // solve operators
         dsol.nf = nf;
         dsol.n_levels = S.n_levels;
-        // the two padded copies of every Q_s (forward: row-major, backward: transposed)
+        // the two packed copies of every Q_s (layout.hpp): forward row-major,
+        // backward transposed
         std::vector<R> QF((size_t)S.qf_total, R(0)), QB((size_t)S.qb_total, R(0));
         for (const SupernodeHost &sn : S.sn) {
             const double *Qs = S.Q.data() + sn.qoff;
             const int nc = sn.ncol, rows = sn.ncol + sn.nrow;
-            for (int i = 0; i < rows; ++i)
-                for (int j = 0; j < nc; ++j) {
-                    const R v = (R)Qs[(size_t)i * nc + j];
-                    QF[(size_t)sn.qf + (size_t)i * sn.ldc + j] = v;
-                    QB[(size_t)sn.qb + (size_t)j * sn.ldr + i] = v;
-                }
+            for (int i = 0; i < rows; ++i) {
+                R *dst = QF.data() + sn.qf + fwd_row_off(i, nc, sn.ldc);
+                const int len = std::min(fwd_row_len(i, nc, sn.ldc), nc);
+                for (int j = 0; j < len; ++j) dst[j] = (R)Qs[(size_t)i * nc + j];
+            }
+            for (int j = 0; j < nc; ++j) {
+                R *dst = QB.data() + sn.qb + bwd_row_off(j, sn.ldr);
+                const int i0 = bwd_row_start(j);
+                for (int i = i0; i < rows; ++i) dst[i - i0] = (R)Qs[(size_t)i * nc + j];
+            }
         }
         const R *p_QF, *p_QB;
         if ((rc = upload(p_QF, QF.data(), QF.size()))) return rc;
@@ -213,40 +221,31 @@ struct Sim final : SimBase {
         std::vector<R>().swap(QB);
         dsol.QF = p_QF;
         dsol.QB = p_QB;
-        const size_t ns = S.sn.size();
-        std::vector<int4> sn(ns);
-        std::vector<long long> snqf(ns), snqb(ns);
-        std::vector<int2> snld(ns);
-        std::vector<int> snu(ns);
-        for (size_t s = 0; s < ns; ++s) {
-            sn[s] = make_int4(S.sn[s].col, S.sn[s].ncol, S.sn[s].nrow, S.sn[s].roff);
-            snqf[s] = S.sn[s].qf;
-            snqb[s] = S.sn[s].qb;
-            snld[s] = make_int2(S.sn[s].ldc, S.sn[s].ldr);
-            snu[s] = S.sn[s].uoff;
-        }
-        const int4 *p_sn;
-        const long long *p_snqf, *p_snqb;
-        const int2 *p_snld, *p_fg2, *p_ug2;
-        const int *p_snu, *p_rows;
-        if ((rc = upload(p_sn, sn.data(), ns))) return rc;
-        if ((rc = upload(p_snqf, snqf.data(), ns))) return rc;
-        if ((rc = upload(p_snqb, snqb.data(), ns))) return rc;
-        if ((rc = upload(p_snld, snld.data(), ns))) return rc;
-        if ((rc = upload(p_snu, snu.data(), ns))) return rc;
+        const int *p_rows;
+        const int2 *p_fg2, *p_ug2;
         if ((rc = upload(p_rows, S.rows.data(), S.rows.size()))) return rc;
         if ((rc = upload(p_fg2, reinterpret_cast<const int2 *>(S.fg2.data()), S.fg2.size() / 2))) return rc;
         if ((rc = upload(p_ug2, reinterpret_cast<const int2 *>(S.ug2.data()), S.ug2.size() / 2))) return rc;
-        dsol.sn = p_sn; dsol.sn_qf = p_snqf; dsol.sn_qb = p_snqb; dsol.sn_ld = p_snld;
-        dsol.sn_u = p_snu; dsol.rows = p_rows; dsol.fg2 = p_fg2; dsol.ug2 = p_ug2;
-        std::vector<int4> fi(S.fwd_items.size()), bi(S.bwd_items.size());
-        for (size_t k = 0; k < fi.size(); ++k) {
+        dsol.rows = p_rows; dsol.fg2 = p_fg2; dsol.ug2 = p_ug2;
+        // work-item records (kernels.cuh): everything a block needs in one place
+        std::vector<int4> fi(3 * S.fwd_items.size()), bi(3 * S.bwd_items.size());
+        for (size_t k = 0; k < S.fwd_items.size(); ++k) {
             const FwdItem &f = S.fwd_items[k];
-            fi[k] = make_int4(f.s, f.row0, f.row1, f.G);
+            const SupernodeHost &sn = S.sn[f.s];
+            const int64_t o0 = fwd_row_off(f.row0, sn.ncol, sn.ldc), o1 = fwd_row_off(f.row1, sn.ncol, sn.ldc);
+            const int64_t q0 = sn.qf + o0;
+            fi[3 * k] = make_int4((int)(q0 & 0xffffffffLL), (int)(q0 >> 32), (int)((o1 - o0) * sizeof(R)), f.G);
+            fi[3 * k + 1] = make_int4(sn.col, sn.ncol, sn.ldc, sn.uoff);
+            fi[3 * k + 2] = make_int4(f.row0, f.row1, fwd_row_len(f.row1 - 1, sn.ncol, sn.ldc), (int)o0);
         }
-        for (size_t k = 0; k < bi.size(); ++k) {
+        for (size_t k = 0; k < S.bwd_items.size(); ++k) {
             const BwdItem &b = S.bwd_items[k];
-            bi[k] = make_int4(b.s, b.col0, b.col1, b.G);
+            const SupernodeHost &sn = S.sn[b.s];
+            const int64_t o0 = bwd_row_off(b.col0, sn.ldr), o1 = bwd_row_off(b.col1, sn.ldr);
+            const int64_t q0 = sn.qb + o0;
+            bi[3 * k] = make_int4((int)(q0 & 0xffffffffLL), (int)(q0 >> 32), (int)((o1 - o0) * sizeof(R)), b.G);
+            bi[3 * k + 1] = make_int4(sn.col, sn.ncol, sn.nrow, sn.roff);
+            bi[3 * k + 2] = make_int4(b.col0, b.col1, sn.ldr, (int)o0);
         }
         const int4 *p_fi, *p_bi;
         if ((rc = upload(p_fi, fi.data(), fi.size()))) return rc;
@@ -256,21 +255,54 @@ struct Sim final : SimBase {
         dsol.bwd_lvl_ptr = S.bwd_lvl_ptr.data();
         dsol.fwd_lvl_ld = S.fwd_lvl_ld.data();
         dsol.bwd_lvl_ld = S.bwd_lvl_ld.data();
+        dsol.fwd_lvl_q = S.fwd_lvl_q.data();
+        dsol.bwd_lvl_q = S.bwd_lvl_q.data();
+        dsol.err = &ds.ctl->solve_err;
         if ((rc = alloc(dsol.u, (size_t)S.n_upd))) return rc;
         hbuf.resize(n);
         CK(cudaStreamSynchronize(st));
         // graph
+        // Chain the sweep levels with programmatic dependent launch when the
+        // device and the runtime accept it (one probe solve on zero vectors),
+        // and keep it in the graph only if the graph builds with it.
+        dsol.pdl = 1;
+        launch_solve(dsol, ds.q, ds.z, ds.d, st);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+            cudaGetLastError();
+            dsol.pdl = 0;
+        }
         graph_mode = false;
         if (p.use_graph) {
             rc = build_graph();
-            if (rc == HQN_OK) graph_mode = true;
-            else {
-                cudaGetLastError();
-                if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
+            if (rc != HQN_OK && dsol.pdl) {
+                abort_graph();
+                dsol.pdl = 0;
+                rc = build_graph();
+            }
+            if (rc != HQN_OK) {
+                abort_graph();
                 return rc;
             }
+            graph_mode = true;
         }
         return HQN_OK;
+    }
+
+    // Ends any capture a failed build_graph left open and drops the graph.
+    void abort_graph() {
+        std::vector<cudaStream_t> ss = cap_streams;
+        ss.push_back(st);
+        for (cudaStream_t s : ss) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(s, &g);
+                if (g && g != graph) cudaGraphDestroy(g);
+            }
+        }
+        cudaGetLastError();
+        if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+        if (graph) { cudaGraphDestroy(graph); graph = nullptr; }
     }
 
     // ---- state transfer (caller order, absolute positions <-> internal displacements)
@@ -327,33 +359,34 @@ struct Sim final : SimBase {
     int read_ctl() {
         CK(cudaMemcpyAsync(h_ctl, ds.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        if (h_ctl->solve_err) return fail(HQN_ERR_CUDA, "a triangular sweep's bulk copy did not complete in time");
         return HQN_OK;
     }
 
     // ---- pieces of the step
     void enqueue_direction(CondHandles h, int set_nd, cudaStream_t s) {
-        const int m = prm.history_m;
-        for (int p = -1; p < m; ++p) launch_first_loop(ds, p, s);
+        launch_q(ds, s);
         launch_solve(dsol, ds.q, ds.z, ds.d, s);
-        for (int j = -1; j < m; ++j) launch_second_loop(ds, j, s);
+        launch_r0_dots(ds, s);
         launch_direction_final(ds, h, set_nd, s);
     }
     void enqueue_reset_direction(cudaStream_t s) {
         launch_reset_history(ds, s);
-        launch_first_loop(ds, -1, s);
+        launch_q(ds, s);
         launch_solve(dsol, ds.q, ds.z, ds.d, s);
         launch_direction_final(ds, CondHandles{0, 0, 0}, 0, s);
     }
     void enqueue_start(CondHandles h, cudaStream_t s) {
         launch_predict(ds, s);
         launch_inertia(ds, s);
-        launch_tet(ds, TET_INIT, s);
+        launch_tet(ds, TET_INIT, CondHandles{0, 0, 0}, s);
         launch_gather(ds, G_INIT, h, s);
     }
-    // x_{k+1} = x_k + alpha d: its gradient (corners, then the gather with the
-    // history push) once the line search has accepted alpha.
+    // x_{k+1} = x_k + alpha d: its gradient (corners, unless the fused first
+    // trial already left them, then the gather with the history push) once the
+    // line search has accepted alpha.
     void enqueue_accept(CondHandles h, cudaStream_t s) {
-        launch_tet(ds, TET_GRAD, s);
+        launch_tet(ds, TET_GRAD, CondHandles{0, 0, 0}, s);
         launch_gather(ds, G_ITER, h, s);
     }
 
@@ -365,11 +398,11 @@ struct Sim final : SimBase {
             enqueue_direction(none, 0, st);
             if ((rc = read_ctl())) return rc;
             if (h_ctl->nondescent) enqueue_reset_direction(st);
-            launch_ls_begin(ds, none, st);
-            for (int tr = 0; tr < prm.ls_max; ++tr) {
+            launch_tet(ds, TET_TRIAL1, none, st);
+            if ((rc = read_ctl())) return rc;
+            for (int pass = 0; pass < prm.ls_max && !h_ctl->accepted && !h_ctl->stop; ++pass) {
                 launch_ls(ds, none, st);
                 if ((rc = read_ctl())) return rc;
-                if (h_ctl->accepted || h_ctl->stop) break;
             }
             enqueue_accept(none, st);
             if ((rc = read_ctl())) return rc;
@@ -434,7 +467,7 @@ struct Sim final : SimBase {
                 enqueue_reset_direction(s2);
                 CK(cudaStreamEndCapture(s2, &body_nd));
             }
-            launch_ls_begin(ds, H, s1);
+            launch_tet(ds, TET_TRIAL1, H, s1);
             cudaGraph_t body_ls;
             if ((rc = add_conditional(s1, h_ls, cudaGraphCondTypeWhile, &body_ls))) return rc;
             {
@@ -493,7 +526,7 @@ struct Sim final : SimBase {
         if ((rc = put_vec(ds.y, y, true, false))) return rc;
         const CondHandles none{0, 0, 0};
         launch_inertia(ds, st);
-        launch_tet(ds, TET_EVAL, st);
+        launch_tet(ds, TET_EVAL, none, st);
         launch_gather(ds, G_EVAL, none, st);
         CK(cudaGetLastError());
         if ((rc = read_ctl())) return rc;
@@ -510,6 +543,7 @@ struct Sim final : SimBase {
         if ((rc = put_vec(ds.q, q, false, true))) return rc;
         launch_solve(dsol, ds.q, ds.z, ds.d, st);
         CK(cudaGetLastError());
+        if ((rc = read_ctl())) return rc;
         return get_vec(ds.d, r, false, true);
     }
 
@@ -521,13 +555,14 @@ struct Sim final : SimBase {
         for (int i = 0; i < np; ++i) {
             if ((rc = put_vec(ds.S + (size_t)i * n, s + (size_t)i * 3 * n, false, true))) return rc;
             if ((rc = put_vec(ds.Tt + (size_t)i * n, t + (size_t)i * 3 * n, false, true))) return rc;
-            launch_pair_rho(ds, i, st);
         }
         int hc[2] = {np, np > 0 ? np - 1 : 0};
         CK(cudaMemcpyAsync(&ds.ctl->count, &hc[0], sizeof(int), cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(&ds.ctl->head, &hc[1], sizeof(int), cudaMemcpyHostToDevice, st));
+        for (int a = 0; a < np; ++a) launch_hist_row(ds, a, st);
         enqueue_direction(CondHandles{0, 0, 0}, 0, st);
         CK(cudaGetLastError());
+        if ((rc = read_ctl())) return rc;
         return get_vec(ds.d, d, false, true);
     }
 
@@ -537,7 +572,7 @@ struct Sim final : SimBase {
         const CondHandles none{0, 0, 0};
         auto launch = [&]() {
             switch (stage) {
-                case HQN_STAGE_TET: launch_tet(ds, TET_EVAL, st); break;
+                case HQN_STAGE_TET: launch_tet(ds, TET_EVAL, none, st); break;
                 case HQN_STAGE_GATHER: launch_gather(ds, G_EVAL, none, st); break;
                 case HQN_STAGE_SOLVE: launch_solve(dsol, ds.q, ds.z, ds.d, st); break;
                 case HQN_STAGE_LS_PASS: launch_ls(ds, none, st); break;
@@ -575,6 +610,7 @@ struct Sim final : SimBase {
         o->precision = (int)(sizeof(R) == 4 ? HQN_FP32_MIXED : HQN_FP64_PLAIN);
         o->graph_mode = graph_mode ? 1 : 0;
         o->n_update_entries = S.n_upd;
+        o->chained_sweeps = dsol.pdl;
     }
 };
 

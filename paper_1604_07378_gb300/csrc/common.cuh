@@ -39,10 +39,13 @@ struct Ctl {
     double gd;         // tr(grad_k^T d)
     double alpha;      // current step length
     double g0;         // g(x_1), x_1 = y
-    double dot;        // scratch: last finalised inner product
     double ls_a[3];    // inertia term along d: I(alpha) = a0 + a1 alpha + a2 alpha^2
     double zeta[HQN_MAX_HISTORY + 1];  // first-loop coefficients by age (0 = newest)
+    double coef[HQN_MAX_HISTORY + 1];  // second-loop coefficients zeta - eta by age
     double rho[HQN_MAX_HISTORY + 1];   // tr(t^T s) by ring slot
+    double sg[HQN_MAX_HISTORY + 1];    // s_a^T grad_k by ring slot
+    double tr0[HQN_MAX_HISTORY + 1];   // t_a^T r0 by ring slot (r0 = A0^{-1} q)
+    double gram[HQN_MAX_HISTORY + 1][HQN_MAX_HISTORY + 1];  // s_a^T t_b by ring slots
     double iter_g[HQN_MAX_ITERS];
     int iter_trials[HQN_MAX_ITERS];
     int k;             // 1-based iteration index of x_k
@@ -52,12 +55,14 @@ struct Ctl {
     int stop;          // the step's iterations have ended early
     int status;        // worst status of the step (HQN_OK or a warning)
     int accepted;      // the last trial passed the Armijo test
+    int grad_ready;    // the corner gradients already belong to the accepted point
     int nondescent;    // tr(grad^T d) >= 0 with history: reset and recompute
     int trials_total;  // over the steps since the host last cleared it
     int iters_total;
     int steps;
     int worst_status;
     int passes_total;  // line-search passes (each tests up to ls_batch step lengths)
+    unsigned int solve_err;  // nonzero: a sweep's bulk copy timed out (sticky)
     unsigned int ticket[8];  // arrival counters of the last-block reductions
 };
 

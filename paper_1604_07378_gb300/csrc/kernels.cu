@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(VBS) k_predict(DevSim<R> s) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         Ctl *c = s.ctl;
         c->k = 0; c->trials = 0; c->count = 0; c->head = 0; c->stop = 0;
-        c->status = HQN_OK; c->accepted = 0; c->nondescent = 0; c->alpha = 1.0;
+        c->status = HQN_OK; c->accepted = 0; c->nondescent = 0; c->alpha = 1.0; c->grad_ready = 0;
     }
 }
 
@@ -95,22 +95,30 @@ __device__ __forceinline__ void edge_diffs(const V4<R> &x0, const V4<R> &x1, con
 // ---------------------------------------------------------------- tet kernel
 
 // One thread per tet: the four corner gradients of V Psi, written to
-// corner[c * T + t].  TET_INIT / TET_EVAL: at the point x_t, and the energy
-// is reduced too (last block, fixed order, float64, plus the inertia
-// partials): TET_INIT sets g(x_1), TET_EVAL reports g.  TET_GRAD: at the
-// accepted point x_k + alpha d of the line search, corners only.
+// corner[c * T + t].
+//   TET_INIT / TET_EVAL: at the point x_t, with the energy reduced too (last
+//     block, fixed order, float64, plus the inertia partials): TET_INIT sets
+//     g(x_1), TET_EVAL reports g.
+//   TET_TRIAL1: the first trial of Alg. 1's line search, alpha = 1, at
+//     x_k + d; the last block adds the inertia term along the ray and runs the
+//     Armijo test.  Accepted: the corners are the gradient of x_{k+1} and the
+//     line-search loop is skipped.  Rejected: the loop continues at
+//     alpha = backtrack.
+//   TET_GRAD: at the accepted point x_k + alpha d, corners only; nothing to do
+//     if TET_TRIAL1 already left them there or the iterations stopped.
 template <typename R, int BS>
-__global__ void __launch_bounds__(BS) k_tet(DevSim<R> s, int mode) {
+__global__ void __launch_bounds__(BS) k_tet(DevSim<R> s, int mode, CondHandles h) {
     const bool grad_mode = mode == TET_GRAD;
-    if (grad_mode && s.ctl->stop) return;
-    const R al = grad_mode ? (R)s.ctl->alpha : R(0);
+    const bool ray_mode = mode == TET_GRAD || mode == TET_TRIAL1;
+    if (grad_mode && (s.ctl->stop || s.ctl->grad_ready)) return;
+    const R al = grad_mode ? (R)s.ctl->alpha : R(1);
     const int T = s.c.T;
     const int t = blockIdx.x * BS + threadIdx.x;
     double e[1] = {0.0};
     if (t < T) {
         const int4 v = s.tets[t];
         V4<R> x0, x1, x2, x3;
-        if (grad_mode) {
+        if (ray_mode) {
             x0 = step_point(s.xk[v.x], s.d[v.x], al);
             x1 = step_point(s.xk[v.y], s.d[v.y], al);
             x2 = step_point(s.xk[v.z], s.d[v.z], al);
@@ -138,6 +146,33 @@ __global__ void __launch_bounds__(BS) k_tet(DevSim<R> s, int mode) {
     if (!publish_and_arrive<1>(e, s.part_el, 0, &s.ctl->ticket[TK_TET])) return;
     double tot[1];
     sum_partials<BS, 1>(s.part_el, 0, gridDim.x, tot, &s.ctl->ticket[TK_TET]);
+    Ctl *c = s.ctl;
+    if (mode == TET_TRIAL1) {
+        if (threadIdx.x != 0) return;
+        // g(x_k + d) = elastic + I(1), I(alpha) = a0 + a1 alpha + a2 alpha^2
+        const double g = tot[0] + (c->ls_a[0] + c->ls_a[1] + c->ls_a[2]);
+        c->passes_total += 1;
+        c->trials = 1;
+        if (g <= c->g_k + s.c.gamma * c->gd) {
+            c->accepted = 1;
+            c->grad_ready = 1;
+            c->alpha = 1.0;
+            c->g_trial = g;
+            set_cond<R>(h.ls, 0u);
+        } else {
+            c->accepted = 0;
+            c->grad_ready = 0;
+            c->alpha = s.c.backtrack;
+            if (s.c.ls_max <= 1) {
+                c->stop = 1;
+                c->status = HQN_WARN_LS_EXHAUSTED;
+                set_cond<R>(h.ls, 0u);
+            } else {
+                set_cond<R>(h.ls, 1u);
+            }
+        }
+        return;
+    }
     double in[1];
     const int nbv = (s.c.n + VBS - 1) / VBS;
     {
@@ -147,7 +182,6 @@ __global__ void __launch_bounds__(BS) k_tet(DevSim<R> s, int mode) {
         block_sum<BS, 1>(in);
     }
     if (threadIdx.x != 0) return;
-    Ctl *c = s.ctl;
     const double g = tot[0] + in[0];
     c->g_trial = g;
     if (mode == TET_INIT) {
@@ -162,7 +196,7 @@ __global__ void __launch_bounds__(BS) k_tet(DevSim<R> s, int mode) {
 // One pass of the backtracking line search of Alg. 1 that evaluates K trial
 // step lengths at once: alpha_j = alpha * backtrack^j, j < K.  Each thread
 // forms G_k = Du_k Dm^{-1} and G_d = Dd Dm^{-1} once and the energy V Psi of
-// G_k + alpha_j G_d for every j (no singular vectors: tet_psi).  The last
+// G_k + alpha_j G_d for every j (no singular vectors: PsiRay).  The last
 // block adds the inertia term, a quadratic in alpha whose coefficients were
 // formed with the direction, and runs the Armijo tests in the order of Alg. 1:
 // the first alpha_j with g <= g_k + gamma alpha_j tr(grad^T d) is accepted
@@ -187,16 +221,12 @@ __global__ void __launch_bounds__(BS) k_ls(DevSim<R> s, CondHandles h) {
         def_grad(Duk, Di, Gk);
         def_grad(Dd, Di, Gd);
         const R vol = s.vol[t];
+        PsiRay<R> ray;
+        psi_ray_setup(s.mat, Gk, Gd, ray);
         double a = a0;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            const R al = (R)a;
-            R G[3][3];
-#pragma unroll
-            for (int p = 0; p < 3; ++p)
-#pragma unroll
-                for (int q = 0; q < 3; ++q) G[p][q] = fma_(al, Gd[p][q], Gk[p][q]);
-            e[j] = (double)(vol * tet_psi(s.mat, G));
+            e[j] = (double)(vol * psi_ray_eval(s.mat, ray, (R)a));
             a *= bt;
         }
     }
@@ -245,14 +275,57 @@ __global__ void __launch_bounds__(BS) k_ls(DevSim<R> s, CondHandles h) {
     if (done) set_cond<R>(h.ls, 0u);
 }
 
+// ---------------------------------------------------------------- Alg. 2 in dot-product form
+//
+// The two loops of Alg. 2 touch the vectors only through inner products with
+// the history pairs.  With q_p the value of q when pair p (age p, 0 = newest)
+// is reached in the first loop, and r_p the value of r in the second loop,
+//   s_p^T q_p = -s_p^T g - sum_{p' < p} zeta_p' (s_p^T t_p'),
+//   t_p^T r_p =  t_p^T r0 + sum_{p' > p} c_p' (t_p^T s_p'),   c_p = zeta_p - eta_p,
+// where r0 = A0^{-1} q_final, q_final = -g - sum_p zeta_p t_p and
+// d = r0 + sum_p c_p s_p.  So the recursion runs on scalars once the Gram
+// matrix s_a^T t_b of the ring slots and the products s_a^T g and t_a^T r0 are
+// known: the gather that pushes a pair forms its row and column of the Gram
+// matrix and s_a^T g for the new gradient, the vector passes are q_final, the
+// t_a^T r0 products and d.  The scalars are float64.
+
+__device__ __forceinline__ double dot3d(double ax, double ay, double az, double bx, double by, double bz) {
+    return ax * bx + ay * by + az * bz;
+}
+
+template <typename R>
+__device__ __forceinline__ double dotv(const V4<R> &a, const V4<R> &b) {
+    return (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z;
+}
+
+template <typename R>
+__device__ __forceinline__ R dotr(const V4<R> &a, const V4<R> &b) {
+    return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+
+// First loop on scalars: zeta_p for every held pair, newest first.
+__device__ __forceinline__ void zeta_recursion(Ctl *c, int m) {
+    const int count = c->count, head = c->head;
+    for (int p = 0; p < count; ++p) {
+        const int sl = ring_slot(head, p, m);
+        double sq = -c->sg[sl];
+        for (int pp = 0; pp < p; ++pp) sq -= c->zeta[pp] * c->gram[sl][ring_slot(head, pp, m)];
+        c->zeta[p] = sq / c->rho[sl];
+    }
+}
+
 // ---------------------------------------------------------------- gather
 
 // One thread per free vertex: grad g = m (x - y)/h^2 + sum of the vertex's
-// corner gradients in a fixed (ascending tet) order -- no atomics.  In
-// G_ITER mode the accepted trial becomes x_{k+1}: the pair
-// s = x_{k+1} - x_k, t = grad_{k+1} - grad_k is written to the free ring slot
-// and kept (last block) if tr(t^T s) > 1e-12 |s| |t|.
-template <typename R>
+// corner gradients in a fixed (ascending tet) order -- no atomics.  In G_ITER
+// mode the accepted trial becomes x_{k+1}: the pair s = x_{k+1} - x_k,
+// t = grad_{k+1} - grad_k goes to the free ring slot w, and the block partials
+// of rho = tr(t^T s), |s|^2, |t|^2 (float64 terms) and of s_a^T t_w, s_w^T t_a
+// and s_a^T grad_{k+1} for every ring slot a (R-precision terms and warp sums,
+// float64 beyond) are reduced.  The last block keeps the pair if
+// rho > 1e-12 |s| |t|, updates the Gram matrix and runs the first loop of
+// Alg. 2 on scalars.
+template <typename R, int MP1>
 __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandles h) {
     Ctl *ctl = s.ctl;
     const int m = s.c.m;
@@ -260,8 +333,14 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
     const bool push = mode == G_ITER && m > 0;
     const int w = push ? (ctl->head + 1) % (m + 1) : 0;
     const R al = mode == G_ITER ? (R)ctl->alpha : R(0);
+    constexpr int NG = 3 * MP1;
+    constexpr int ND = 3 + NG;
+    double dd[3] = {0.0, 0.0, 0.0};
+    R dr[NG];
+#pragma unroll
+    for (int k = 0; k < NG; ++k) dr[k] = R(0);
+    const size_t n = (size_t)s.c.n;
     const int i = blockIdx.x * VBS + threadIdx.x;
-    double dots[3] = {0.0, 0.0, 0.0};
     if (!stop && i < s.c.nf) {
         const int b = s.vt_ptr[i], e = s.vt_ptr[i + 1];
         R gx = R(0), gy = R(0), gz = R(0);
@@ -278,26 +357,47 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
         gn.z = gz + mh * (x.z - yy.z);
         gn.w = R(0);
         if (mode == G_ITER) {
-            const V4<R> xo = s.xk[i], go = s.gk[i];
             if (push) {
+                const V4<R> xo = s.xk[i], go = s.gk[i];
                 V4<R> sv, tv;
                 sv.x = x.x - xo.x; sv.y = x.y - xo.y; sv.z = x.z - xo.z; sv.w = R(0);
                 tv.x = gn.x - go.x; tv.y = gn.y - go.y; tv.z = gn.z - go.z; tv.w = R(0);
-                s.S[(size_t)w * s.c.n + i] = sv;
-                s.Tt[(size_t)w * s.c.n + i] = tv;
-                dots[0] = (double)tv.x * sv.x + (double)tv.y * sv.y + (double)tv.z * sv.z;
-                dots[1] = (double)sv.x * sv.x + (double)sv.y * sv.y + (double)sv.z * sv.z;
-                dots[2] = (double)tv.x * tv.x + (double)tv.y * tv.y + (double)tv.z * tv.z;
+                s.S[(size_t)w * n + i] = sv;
+                s.Tt[(size_t)w * n + i] = tv;
+                dd[0] = dotv(tv, sv);
+                dd[1] = dotv(sv, sv);
+                dd[2] = dotv(tv, tv);
+#pragma unroll
+                for (int a = 0; a < MP1; ++a) {
+                    if (a > m) break;
+                    const V4<R> sa = a == w ? sv : s.S[(size_t)a * n + i];
+                    const V4<R> ta = a == w ? tv : s.Tt[(size_t)a * n + i];
+                    dr[a] = dotr(sa, tv);
+                    dr[MP1 + a] = dotr(sv, ta);
+                    dr[2 * MP1 + a] = dotr(sa, gn);
+                }
             }
             s.xk[i] = x;
         }
         s.gk[i] = gn;
     }
     if (mode == G_EVAL) return;
-    block_sum<VBS, 3>(dots);
-    if (!publish_and_arrive<3>(dots, s.part_g, gridDim.x, &ctl->ticket[TK_GATHER])) return;
-    double tot[3];
-    sum_partials<VBS, 3>(s.part_g, gridDim.x, gridDim.x, tot, &ctl->ticket[TK_GATHER]);
+    double dots[ND];
+    if (push) {
+        double mixed[NG];
+        block_sum<VBS, 3>(dd);
+        block_sum_mixed<VBS, NG, R>(dr, mixed);
+        dots[0] = dd[0]; dots[1] = dd[1]; dots[2] = dd[2];
+#pragma unroll
+        for (int k = 0; k < NG; ++k) dots[3 + k] = mixed[k];
+        if (!publish_and_arrive<ND>(dots, s.part_g, gridDim.x, &ctl->ticket[TK_GATHER])) return;
+        sum_partials<VBS, ND>(s.part_g, gridDim.x, gridDim.x, dots, &ctl->ticket[TK_GATHER]);
+    } else {
+        double none[1] = {0.0};
+        if (!publish_and_arrive<1>(none, s.part_g, gridDim.x, &ctl->ticket[TK_GATHER])) return;
+        __threadfence();
+        if (threadIdx.x == 0) ctl->ticket[TK_GATHER] = 0u;
+    }
     if (threadIdx.x != 0) return;
     if (mode == G_INIT) {
         ctl->k = 1;
@@ -317,10 +417,23 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
         set_cond<R>(h.it, 0u);
         return;
     }
-    if (push && tot[0] > 1e-12 * sqrt(tot[1] * tot[2])) {
-        ctl->head = w;
-        ctl->rho[w] = tot[0];
-        ctl->count = ctl->count < m ? ctl->count + 1 : m;
+    if (push) {
+        // (compile-time indices keep dots[] in registers)
+        if (dots[0] > 1e-12 * sqrt(dots[1] * dots[2])) {
+            ctl->head = w;
+            ctl->rho[w] = dots[0];
+            ctl->count = ctl->count < m ? ctl->count + 1 : m;
+#pragma unroll
+            for (int a = 0; a < MP1; ++a)
+                if (a <= m) {
+                    ctl->gram[a][w] = dots[3 + a];
+                    ctl->gram[w][a] = dots[3 + MP1 + a];
+                }
+        }
+#pragma unroll
+        for (int a = 0; a < MP1; ++a)
+            if (a <= m) ctl->sg[a] = dots[3 + 2 * MP1 + a];
+        zeta_recursion(ctl, m);
     }
     ctl->g_k = ctl->g_trial;
     ctl->iter_g[kk] = ctl->g_trial;
@@ -328,85 +441,65 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
     set_cond<R>(h.it, (k + 1 <= s.c.iters) ? 1u : 0u);
 }
 
-// ---------------------------------------------------------------- Alg. 2
-
-// First loop, newest pair first.  p = -1: q = -grad.  p >= 0 (if p < count):
-// q -= zeta_p t_p.  Then, if pair p + 1 exists, the partial of tr(s_{p+1}^T q)
-// whose final sum (last block) gives zeta_{p+1} = tr(s^T q) / rho.
+// q = -grad - sum_p zeta_p t_p (the first loop's result).
 template <typename R>
-__global__ void __launch_bounds__(VBS) k_first(DevSim<R> s, int p) {
-    Ctl *ctl = s.ctl;
-    const int count = ctl->count, m = s.c.m, head = ctl->head;
-    if (p >= count) return;
+__global__ void __launch_bounds__(VBS) k_q(DevSim<R> s) {
+    const Ctl *ctl = s.ctl;
     const int i = blockIdx.x * VBS + threadIdx.x;
-    const bool next = p + 1 < count;
-    const int sn = next ? ring_slot(head, p + 1, m) : 0;
-    double d1[1] = {0.0};
-    if (i < s.c.nf) {
-        V4<R> qq;
-        if (p < 0) {
-            const V4<R> g = s.gk[i];
-            qq.x = -g.x; qq.y = -g.y; qq.z = -g.z; qq.w = R(0);
-        } else {
-            const R zeta = (R)ctl->zeta[p];
-            const V4<R> tv = s.Tt[(size_t)ring_slot(head, p, m) * s.c.n + i];
-            qq = s.q[i];
-            qq.x -= zeta * tv.x; qq.y -= zeta * tv.y; qq.z -= zeta * tv.z;
-        }
-        s.q[i] = qq;
-        if (next) {
-            const V4<R> sv = s.S[(size_t)sn * s.c.n + i];
-            d1[0] = (double)sv.x * qq.x + (double)sv.y * qq.y + (double)sv.z * qq.z;
-        }
+    if (i >= s.c.nf) return;
+    const int count = ctl->count, head = ctl->head, m = s.c.m;
+    const V4<R> g = s.gk[i];
+    V4<R> q;
+    q.x = -g.x; q.y = -g.y; q.z = -g.z; q.w = R(0);
+    for (int p = 0; p < count; ++p) {
+        const R z = (R)ctl->zeta[p];
+        const V4<R> t = s.Tt[(size_t)ring_slot(head, p, m) * s.c.n + i];
+        q.x -= z * t.x; q.y -= z * t.y; q.z -= z * t.z;
     }
-    if (!next) return;
-    block_sum<VBS, 1>(d1);
-    if (!publish_and_arrive<1>(d1, s.part_v, 0, &ctl->ticket[TK_VEC])) return;
-    double tot[1];
-    sum_partials<VBS, 1>(s.part_v, 0, gridDim.x, tot, &ctl->ticket[TK_VEC]);
-    if (threadIdx.x == 0) ctl->zeta[p + 1] = tot[0] / ctl->rho[sn];
+    s.q[i] = q;
 }
 
-// Second loop, oldest pair first, on r (held in d).  j = -1: the partial of
-// tr(t^T r) for the oldest pair.  j >= 0: pair age p = count - 1 - j:
-// r += s_p (zeta_p - eta_p), eta_p = tr(t_p^T r) / rho_p; then the partial
-// of tr(t_{p-1}^T r) for the next pair.
-template <typename R>
-__global__ void __launch_bounds__(VBS) k_second(DevSim<R> s, int j) {
+// t_a^T r0 for every ring slot a (r0 = A0^{-1} q, held in d); the last block
+// runs the second loop of Alg. 2 on scalars: c_p = zeta_p - eta_p, oldest first.
+template <typename R, int MP1>
+__global__ void __launch_bounds__(VBS) k_r0_dots(DevSim<R> s) {
     Ctl *ctl = s.ctl;
-    const int count = ctl->count, m = s.c.m, head = ctl->head;
-    const int p = j < 0 ? count : count - 1 - j;  // pair applied now (count = none)
-    if (p < 0 || (j < 0 && count == 0)) return;
-    const int pn = p - 1;  // pair whose inner product is formed next
-    const bool next = pn >= 0;
-    const int sn = next ? ring_slot(head, pn, m) : 0;
+    const int count = ctl->count, m = s.c.m;
+    if (count == 0) return;
+    R dr[MP1];
+#pragma unroll
+    for (int a = 0; a < MP1; ++a) dr[a] = R(0);
+    const size_t n = (size_t)s.c.n;
     const int i = blockIdx.x * VBS + threadIdx.x;
-    double d1[1] = {0.0};
     if (i < s.c.nf) {
-        V4<R> r = s.d[i];
-        if (j >= 0) {
-            const int sp = ring_slot(head, p, m);
-            const R coef = (R)(ctl->zeta[p] - ctl->dot / ctl->rho[sp]);
-            const V4<R> sv = s.S[(size_t)sp * s.c.n + i];
-            r.x += coef * sv.x; r.y += coef * sv.y; r.z += coef * sv.z;
-            s.d[i] = r;
-        }
-        if (next) {
-            const V4<R> tv = s.Tt[(size_t)sn * s.c.n + i];
-            d1[0] = (double)tv.x * r.x + (double)tv.y * r.y + (double)tv.z * r.z;
+        const V4<R> r = s.d[i];
+#pragma unroll
+        for (int a = 0; a < MP1; ++a) {
+            if (a > m) break;
+            dr[a] = dotr(s.Tt[(size_t)a * n + i], r);
         }
     }
-    if (!next) return;
-    block_sum<VBS, 1>(d1);
-    if (!publish_and_arrive<1>(d1, s.part_v, 0, &ctl->ticket[TK_VEC])) return;
-    double tot[1];
-    sum_partials<VBS, 1>(s.part_v, 0, gridDim.x, tot, &ctl->ticket[TK_VEC]);
-    if (threadIdx.x == 0) ctl->dot = tot[0];
+    double dots[MP1];
+    block_sum_mixed<VBS, MP1, R>(dr, dots);
+    if (!publish_and_arrive<MP1>(dots, s.part_v, gridDim.x, &ctl->ticket[TK_VEC])) return;
+    sum_partials<VBS, MP1>(s.part_v, gridDim.x, gridDim.x, dots, &ctl->ticket[TK_VEC]);
+    if (threadIdx.x != 0) return;
+#pragma unroll
+    for (int a = 0; a < MP1; ++a)
+        if (a <= m) ctl->tr0[a] = dots[a];
+    const int head = ctl->head;
+    for (int p = count - 1; p >= 0; --p) {
+        const int sl = ring_slot(head, p, m);
+        double tr = ctl->tr0[sl];
+        for (int pp = p + 1; pp < count; ++pp) tr += ctl->coef[pp] * ctl->gram[ring_slot(head, pp, m)][sl];
+        ctl->coef[p] = ctl->zeta[p] - tr / ctl->rho[sl];
+    }
 }
 
-// gd = tr(grad_k^T d); with history and gd >= 0 the direction is not a
-// descent direction: flag it (and set the if-node) so the history is dropped.
-// Also the coefficients of the inertia term along the ray x_k + alpha d:
+// d = r0 + sum_p c_p s_p; then gd = tr(grad_k^T d) -- with history and
+// gd >= 0 the direction is not a descent direction: flag it (and set the
+// if-node) so the history is dropped -- and the coefficients of the inertia
+// term along the ray x_k + alpha d:
 // 1/(2h^2) sum m |x_k + alpha d - y|^2 = a0 + a1 alpha + a2 alpha^2.
 template <typename R>
 __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, int set_nd) {
@@ -414,13 +507,21 @@ __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, i
     const int i = blockIdx.x * VBS + threadIdx.x;
     double d4[4] = {0.0, 0.0, 0.0, 0.0};
     if (i < s.c.nf) {
-        const V4<R> g = s.gk[i], dd = s.d[i], x = s.xk[i], yy = s.y[i];
+        V4<R> dd = s.d[i];
+        const int count = ctl->count, head = ctl->head, m = s.c.m;
+        for (int p = 0; p < count; ++p) {
+            const R c = (R)ctl->coef[p];
+            const V4<R> sv = s.S[(size_t)ring_slot(head, p, m) * s.c.n + i];
+            dd.x += c * sv.x; dd.y += c * sv.y; dd.z += c * sv.z;
+        }
+        if (count > 0) s.d[i] = dd;
+        const V4<R> g = s.gk[i], x = s.xk[i], yy = s.y[i];
         const double mh = (double)s.mh2[i];
         const double rx = (double)x.x - yy.x, ry = (double)x.y - yy.y, rz = (double)x.z - yy.z;
-        d4[0] = (double)g.x * dd.x + (double)g.y * dd.y + (double)g.z * dd.z;
+        d4[0] = dotv(g, dd);
         d4[1] = 0.5 * mh * (rx * rx + ry * ry + rz * rz);
-        d4[2] = mh * (rx * dd.x + ry * dd.y + rz * dd.z);
-        d4[3] = 0.5 * mh * ((double)dd.x * dd.x + (double)dd.y * dd.y + (double)dd.z * dd.z);
+        d4[2] = mh * dot3d(rx, ry, rz, dd.x, dd.y, dd.z);
+        d4[3] = 0.5 * mh * dotv(dd, dd);
     }
     block_sum<VBS, 4>(d4);
     if (!publish_and_arrive<4>(d4, s.part_v, gridDim.x, &ctl->ticket[TK_VEC])) return;
@@ -434,15 +535,6 @@ __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, i
     const int nd = (tot[0] >= 0.0 && ctl->count > 0) ? 1 : 0;
     ctl->nondescent = nd;
     if (set_nd) set_cond<R>(h.nd, (unsigned)nd);
-}
-
-template <typename R>
-__global__ void k_ls_begin(DevSim<R> s, CondHandles h) {
-    Ctl *ctl = s.ctl;
-    ctl->alpha = 1.0;
-    ctl->trials = 0;
-    ctl->accepted = 0;
-    set_cond<R>(h.ls, 1u);
 }
 
 template <typename R>
@@ -466,19 +558,36 @@ __global__ void __launch_bounds__(VBS) k_commit(DevSim<R> s) {
     }
 }
 
+// Caller-given history (sim_direction): row `a` of the Gram matrix, s_a^T t_b
+// for the slots b < count, rho_a = s_a^T t_a and s_a^T grad.  With
+// a == count - 1 the last block also runs the first loop on scalars.
 template <typename R>
-__global__ void __launch_bounds__(VBS) k_pair_rho(DevSim<R> s, int slot) {
+__global__ void __launch_bounds__(VBS) k_hist_row(DevSim<R> s, int a) {
+    Ctl *ctl = s.ctl;
+    constexpr int NB = HQN_MAX_HISTORY + 2;
+    double dots[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) dots[b] = 0.0;
+    const int count = ctl->count;
+    const size_t n = (size_t)s.c.n;
     const int i = blockIdx.x * VBS + threadIdx.x;
-    double d1[1] = {0.0};
     if (i < s.c.nf) {
-        const V4<R> sv = s.S[(size_t)slot * s.c.n + i], tv = s.Tt[(size_t)slot * s.c.n + i];
-        d1[0] = (double)tv.x * sv.x + (double)tv.y * sv.y + (double)tv.z * sv.z;
+        const V4<R> sa = s.S[(size_t)a * n + i];
+#pragma unroll
+        for (int b = 0; b < NB - 1; ++b)
+            if (b < count) dots[b] = dotv(sa, s.Tt[(size_t)b * n + i]);
+        dots[NB - 1] = dotv(sa, s.gk[i]);
     }
-    block_sum<VBS, 1>(d1);
-    if (!publish_and_arrive<1>(d1, s.part_v, 0, &s.ctl->ticket[TK_VEC])) return;
-    double tot[1];
-    sum_partials<VBS, 1>(s.part_v, 0, gridDim.x, tot, &s.ctl->ticket[TK_VEC]);
-    if (threadIdx.x == 0) s.ctl->rho[slot] = tot[0];
+    block_sum<VBS, NB>(dots);
+    if (!publish_and_arrive<NB>(dots, s.part_g, gridDim.x, &ctl->ticket[TK_GATHER])) return;
+    sum_partials<VBS, NB>(s.part_g, gridDim.x, gridDim.x, dots, &ctl->ticket[TK_GATHER]);
+    if (threadIdx.x != 0) return;
+#pragma unroll
+    for (int b = 0; b < NB - 1; ++b)
+        if (b < count) ctl->gram[a][b] = dots[b];
+    ctl->rho[a] = ctl->gram[a][a];
+    ctl->sg[a] = dots[NB - 1];
+    if (a == count - 1) zeta_recursion(ctl, s.c.m);
 }
 
 inline int nblk(int n) { return (n + VBS - 1) / VBS; }
@@ -493,12 +602,12 @@ template <typename R> void launch_predict(const DevSim<R> &s, cudaStream_t st) {
 template <typename R> void launch_inertia(const DevSim<R> &s, cudaStream_t st) {
     k_inertia<R><<<nblk(s.c.n), VBS, 0, st>>>(s);
 }
-template <typename R> void launch_tet(const DevSim<R> &s, int mode, cudaStream_t st) {
+template <typename R> void launch_tet(const DevSim<R> &s, int mode, CondHandles h, cudaStream_t st) {
     const int T = s.c.T;
     switch (s.tet_bs) {
-        case 64: k_tet<R, 64><<<(T + 63) / 64, 64, 0, st>>>(s, mode); break;
-        case 256: k_tet<R, 256><<<(T + 255) / 256, 256, 0, st>>>(s, mode); break;
-        default: k_tet<R, 128><<<(T + 127) / 128, 128, 0, st>>>(s, mode); break;
+        case 64: k_tet<R, 64><<<(T + 63) / 64, 64, 0, st>>>(s, mode, h); break;
+        case 256: k_tet<R, 256><<<(T + 255) / 256, 256, 0, st>>>(s, mode, h); break;
+        default: k_tet<R, 128><<<(T + 127) / 128, 128, 0, st>>>(s, mode, h); break;
     }
 }
 template <typename R> void launch_ls(const DevSim<R> &s, CondHandles h, cudaStream_t st) {
@@ -512,20 +621,29 @@ template <typename R> void launch_ls(const DevSim<R> &s, CondHandles h, cudaStre
     }
 }
 template <typename R> void launch_gather(const DevSim<R> &s, int mode, CondHandles h, cudaStream_t st) {
-    k_gather<R><<<nblk(s.c.nf), VBS, 0, st>>>(s, mode, h);
+    const int m = s.c.m;
+    const int nb = nblk(s.c.nf);
+    if (m <= 0) k_gather<R, 1><<<nb, VBS, 0, st>>>(s, mode, h);
+    else if (m <= 3) k_gather<R, 4><<<nb, VBS, 0, st>>>(s, mode, h);
+    else if (m <= 5) k_gather<R, 6><<<nb, VBS, 0, st>>>(s, mode, h);
+    else if (m <= 8) k_gather<R, 9><<<nb, VBS, 0, st>>>(s, mode, h);
+    else k_gather<R, HQN_MAX_HISTORY + 1><<<nb, VBS, 0, st>>>(s, mode, h);
 }
-template <typename R> void launch_first_loop(const DevSim<R> &s, int p, cudaStream_t st) {
-    k_first<R><<<nblk(s.c.nf), VBS, 0, st>>>(s, p);
+template <typename R> void launch_q(const DevSim<R> &s, cudaStream_t st) {
+    k_q<R><<<nblk(s.c.nf), VBS, 0, st>>>(s);
 }
-template <typename R> void launch_second_loop(const DevSim<R> &s, int j, cudaStream_t st) {
-    k_second<R><<<nblk(s.c.nf), VBS, 0, st>>>(s, j);
+template <typename R> void launch_r0_dots(const DevSim<R> &s, cudaStream_t st) {
+    const int m = s.c.m;
+    const int nb = nblk(s.c.nf);
+    if (m <= 0) return;
+    if (m <= 3) k_r0_dots<R, 4><<<nb, VBS, 0, st>>>(s);
+    else if (m <= 5) k_r0_dots<R, 6><<<nb, VBS, 0, st>>>(s);
+    else if (m <= 8) k_r0_dots<R, 9><<<nb, VBS, 0, st>>>(s);
+    else k_r0_dots<R, HQN_MAX_HISTORY + 1><<<nb, VBS, 0, st>>>(s);
 }
 template <typename R>
 void launch_direction_final(const DevSim<R> &s, CondHandles h, int set_nd, cudaStream_t st) {
     k_dir_final<R><<<nblk(s.c.nf), VBS, 0, st>>>(s, h, set_nd);
-}
-template <typename R> void launch_ls_begin(const DevSim<R> &s, CondHandles h, cudaStream_t st) {
-    k_ls_begin<R><<<1, 1, 0, st>>>(s, h);
 }
 template <typename R> void launch_reset_history(const DevSim<R> &s, cudaStream_t st) {
     k_reset_history<R><<<1, 1, 0, st>>>(s);
@@ -533,23 +651,22 @@ template <typename R> void launch_reset_history(const DevSim<R> &s, cudaStream_t
 template <typename R> void launch_commit(const DevSim<R> &s, cudaStream_t st) {
     k_commit<R><<<nblk(s.c.n), VBS, 0, st>>>(s);
 }
-template <typename R> void launch_pair_rho(const DevSim<R> &s, int slot, cudaStream_t st) {
-    k_pair_rho<R><<<nblk(s.c.nf), VBS, 0, st>>>(s, slot);
+template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream_t st) {
+    k_hist_row<R><<<nblk(s.c.nf), VBS, 0, st>>>(s, a);
 }
 
 #define HQN_INST(R)                                                                  \
     template void launch_predict<R>(const DevSim<R> &, cudaStream_t);                \
     template void launch_inertia<R>(const DevSim<R> &, cudaStream_t);                \
-    template void launch_tet<R>(const DevSim<R> &, int, cudaStream_t);               \
+    template void launch_tet<R>(const DevSim<R> &, int, CondHandles, cudaStream_t);  \
     template void launch_ls<R>(const DevSim<R> &, CondHandles, cudaStream_t);        \
     template void launch_gather<R>(const DevSim<R> &, int, CondHandles, cudaStream_t); \
-    template void launch_first_loop<R>(const DevSim<R> &, int, cudaStream_t);        \
-    template void launch_second_loop<R>(const DevSim<R> &, int, cudaStream_t);       \
+    template void launch_q<R>(const DevSim<R> &, cudaStream_t);                      \
+    template void launch_r0_dots<R>(const DevSim<R> &, cudaStream_t);                \
     template void launch_direction_final<R>(const DevSim<R> &, CondHandles, int, cudaStream_t); \
-    template void launch_ls_begin<R>(const DevSim<R> &, CondHandles, cudaStream_t);  \
     template void launch_reset_history<R>(const DevSim<R> &, cudaStream_t);          \
     template void launch_commit<R>(const DevSim<R> &, cudaStream_t);                 \
-    template void launch_pair_rho<R>(const DevSim<R> &, int, cudaStream_t);
+    template void launch_hist_row<R>(const DevSim<R> &, int, cudaStream_t);
 
 HQN_INST(float)
 HQN_INST(double)

@@ -30,48 +30,55 @@ struct DevSim {
     Ctl *ctl;
 };
 
-enum TetMode { TET_INIT = 0, TET_GRAD = 1, TET_EVAL = 2 };
+enum TetMode { TET_INIT = 0, TET_GRAD = 1, TET_EVAL = 2, TET_TRIAL1 = 3 };
 enum GatherMode { G_INIT = 0, G_ITER = 1, G_EVAL = 2 };
 
 template <typename R> void launch_predict(const DevSim<R> &s, cudaStream_t st);
 // Inertia partials of the caller-given point x_t.
 template <typename R> void launch_inertia(const DevSim<R> &s, cudaStream_t st);
-template <typename R> void launch_tet(const DevSim<R> &s, int mode, cudaStream_t st);
+// TET_TRIAL1 is the first line-search trial (alpha = 1) fused with the
+// gradient: it runs the Armijo test and, on acceptance, leaves the corner
+// gradients of the new point in place (TET_GRAD then returns at once).
+template <typename R> void launch_tet(const DevSim<R> &s, int mode, CondHandles h, cudaStream_t st);
 // One multi-trial line-search pass (K = ls_batch step lengths).
 template <typename R> void launch_ls(const DevSim<R> &s, CondHandles h, cudaStream_t st);
 template <typename R> void launch_gather(const DevSim<R> &s, int mode, CondHandles h, cudaStream_t st);
-// Alg. 2 first loop: p = -1 starts it (q = -grad), p = 0..m-1 applies pair p.
-template <typename R> void launch_first_loop(const DevSim<R> &s, int p, cudaStream_t st);
-// Alg. 2 second loop: j = -1 starts it, j = 0..m-1 applies the j-th oldest pair.
-template <typename R> void launch_second_loop(const DevSim<R> &s, int j, cudaStream_t st);
-// gd = tr(grad^T d); flags a non-descent direction (sets h.nd when set_nd).
+// Alg. 2 in dot-product form (the Gram matrix of the history and the
+// products with grad are formed by the gather that pushes a pair):
+// q = -grad - sum zeta_p t_p; after the solve, t_a^T r0 and the second loop on
+// scalars; then d = r0 + sum c_p s_p with gd and the inertia coefficients
+// (sets h.nd on a non-descent direction when set_nd).
+template <typename R> void launch_q(const DevSim<R> &s, cudaStream_t st);
+template <typename R> void launch_r0_dots(const DevSim<R> &s, cudaStream_t st);
 template <typename R> void launch_direction_final(const DevSim<R> &s, CondHandles h, int set_nd, cudaStream_t st);
-template <typename R> void launch_ls_begin(const DevSim<R> &s, CondHandles h, cudaStream_t st);
 template <typename R> void launch_reset_history(const DevSim<R> &s, cudaStream_t st);
 template <typename R> void launch_commit(const DevSim<R> &s, cudaStream_t st);
-// rho of ring slot `slot` = tr(Tt[slot]^T S[slot]) (history given by the caller).
-template <typename R> void launch_pair_rho(const DevSim<R> &s, int slot, cudaStream_t st);
+// Caller-given history: Gram row a, rho_a and s_a^T grad (run for a = 0..count-1).
+template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream_t st);
 
 // ---- triangular solves (solve.cu)
-constexpr int SOLVE_MAX_SMEM = 220 * 1024;  // dynamic shared memory of one sweep block
+constexpr int SOLVE_MAX_SMEM = 200 * 1024;  // dynamic shared memory of one sweep block
 
 template <typename R>
 struct DevSolve {
     int nf, n_levels;
-    const R *QF;                // per supernode: Q_s row-major, rows padded to ldc (16 B)
-    const R *QB;                // per supernode: Q_s^T row-major, rows padded to ldr (16 B)
-    const int4 *sn;             // (col, ncol, nrow, roff)
-    const long long *sn_qf, *sn_qb;  // offsets of the two copies
-    const int2 *sn_ld;          // (ldc, ldr)
-    const int *sn_u;            // offset of the supernode's update entries
-    const int *rows;            // row structures
+    int pdl;                    // host: launch the sweeps with programmatic dependent launch
+    const R *QF;                // per supernode: packed Q_s, row-major (layout.hpp)
+    const R *QB;                // per supernode: packed Q_s^T, row-major (layout.hpp)
+    const int *rows;            // row structures R of the supernodes
     const int2 *fg2;            // per column: the (<= 2) child update entries to subtract
     const int2 *ug2;            // per update entry: the (<= 2) child update entries to add
-    const int4 *fwd_items;      // (s, row0, row1, G)
-    const int4 *bwd_items;      // (s, col0, col1, G)
+    // Work items, 3 int4 each:
+    //   forward  {q0 lo, q0 hi, bytes, G} {col, nc, ldc, uoff} {r0, r1, ldf, off0}
+    //   backward {q0 lo, q0 hi, bytes, G} {col, nc, nrow, roff} {c0, c1, ldr, off0}
+    // q0 = entry offset of the item's first row in QF / QB, bytes = size of its
+    // rows, off0 = offset of that row inside its supernode's block.
+    const int4 *fwd_items, *bwd_items;
     const int *fwd_lvl_ptr, *bwd_lvl_ptr;  // host: items of level l in [ptr[l], ptr[l+1])
     const int *fwd_lvl_ld, *bwd_lvl_ld;    // host: max ldc / ldr of the level (shared memory)
+    const int *fwd_lvl_q, *bwd_lvl_q;      // host: max factor entries of one item of the level
     V4<R> *u;                   // update vectors
+    unsigned int *err;          // set nonzero if a bulk copy did not arrive in time
 };
 
 // r = A0^{-1} q on the first nf entries (q, r: V4 arrays, may not alias).

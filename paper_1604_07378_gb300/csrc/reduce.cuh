@@ -42,6 +42,27 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     __syncthreads();
 }
 
+// Sum of NV values over the block, first within each warp in the working
+// precision R, then across the warps in float64; the result (float64) is
+// valid in thread 0.  Used for the two-loop's inner products, whose terms are
+// R-precision products anyway; with R = double it equals block_sum.
+template <int BS, int NV, typename R>
+__device__ __forceinline__ void block_sum_mixed(const R (&v)[NV], double (&out)[NV]) {
+    __shared__ double sh[NV][BS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const R t = warp_sum_r(v[k]);
+        if (lane == 0) sh[k][warp] = (double)t;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = warp_sum(lane < BS / 32 ? sh[k][lane] : 0.0);
+    }
+    __syncthreads();
+}
+
 // Thread 0 publishes the block's partials (part[k * stride + blockIdx.x]) and
 // takes an arrival ticket.  Returns true in every thread of the last block.
 template <int NV>

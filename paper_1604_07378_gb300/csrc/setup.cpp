@@ -11,6 +11,7 @@
 #include <numeric>
 
 #include "dense.hpp"
+#include "layout.hpp"
 
 namespace hqn {
 
@@ -614,78 +615,89 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
         for (int k = 0; k < c; ++k) S.ug2[2 * (size_t)u + k] = S.ug_idx[S.ug_ptr[u] + k];
     }
 
-    // ---- padded device layout and level work lists
-    // VN = entries per 16-byte vector in the device precision; rows of both
-    // copies are padded to a multiple of 4 entries (16 bytes in float, 32 in
-    // double), so every row starts 16-byte aligned.
+    // ---- packed device layout (layout.hpp) and level work lists
+    // VN = entries per 16-byte vector in the device precision.
     const int VN = prm.precision == HQN_FP64_PLAIN ? 2 : 4;
+    const int esize = prm.precision == HQN_FP64_PLAIN ? 8 : 4;
     S.qf_total = S.qb_total = 0;
     S.max_ld = 0;
     for (auto &sn : S.sn) {
-        sn.ldc = (sn.ncol + 3) / 4 * 4;
-        sn.ldr = (sn.ncol + sn.nrow + 3) / 4 * 4;
+        sn.ldc = pad4(sn.ncol);
+        sn.ldr = pad4(sn.ncol + sn.nrow);
         sn.qf = S.qf_total;
         sn.qb = S.qb_total;
-        S.qf_total += (int64_t)(sn.ncol + sn.nrow) * sn.ldc;
-        S.qb_total += (int64_t)sn.ncol * sn.ldr;
+        S.qf_total += fwd_row_off(sn.ncol + sn.nrow, sn.ncol, sn.ldc);
+        S.qb_total += bwd_row_off(sn.ncol, sn.ldr);
         S.max_ld = std::max(S.max_ld, std::max(sn.ldc, sn.ldr));
     }
-    // lanes per output row: enough that each lane streams a few 16-byte vectors
+    // lanes per output row: enough that each lane reads a few 16-byte vectors
     auto lanes_for = [&](int len) {
         const int nv = (len + VN - 1) / VN;
         int G = 1;
         while (G < 32 && G * 4 < nv) G *= 2;
         return G;
     };
-    constexpr int kBS = 256;                   // threads per block of the sweeps
-    const int kEntries = VN == 4 ? 16384 : 8192;  // target matrix entries per work item
+    // Entries per work item: a level's entries spread over ~400 items (a few
+    // blocks per SM), within [kMin, kMax] so that one item's rows fit the
+    // shared-memory buffer its bulk copy fills (kMax entries = 64 KB).
+    const int kMax = 65536 / esize, kMin = kMax / 4;
     int L = 0;
     for (auto &sn : S.sn) L = std::max(L, sn.level + 1);
     S.n_levels = L;
+    std::vector<int64_t> lvl_entries(L, 0);
+    for (auto &sn : S.sn) lvl_entries[sn.level] += fwd_row_off(sn.ncol + sn.nrow, sn.ncol, sn.ldc);
     S.fwd_lvl_ptr.assign(L + 1, 0);
     S.bwd_lvl_ptr.assign(L + 1, 0);
     S.fwd_lvl_ld.assign(L, 0);
     S.bwd_lvl_ld.assign(L, 0);
+    S.fwd_lvl_q.assign(L, 0);
+    S.bwd_lvl_q.assign(L, 0);
     S.fwd_items.clear();
     S.bwd_items.clear();
     for (int l = 0; l < L; ++l) {
+        const int target = (int)std::min<int64_t>(kMax, std::max<int64_t>(kMin, lvl_entries[l] / 400));
         S.fwd_lvl_ptr[l] = (int)S.fwd_items.size();
         for (int s = 0; s < ns; ++s) {
             const SupernodeHost &sn = S.sn[s];
             if (sn.level != l || sn.ncol == 0) continue;
+            const int nc = sn.ncol, rows = nc + sn.nrow;
             S.fwd_lvl_ld[l] = std::max(S.fwd_lvl_ld[l], sn.ldc);
-            const int rows = sn.ncol + sn.nrow;
-            // triangle rows (short, growing) and rectangle rows (length ncol)
-            // get separate items so one G fits every row of an item
-            const int G = lanes_for(sn.ncol);
-            const int ng = kBS / G;
-            int chunk = std::max(1, kEntries / std::max(1, sn.ncol));
-            chunk = (chunk + ng - 1) / ng * ng;
-            for (int r0 = 0; r0 < sn.ncol; r0 += chunk) {
-                const int r1 = std::min(sn.ncol, r0 + chunk);
-                S.fwd_items.push_back({s, r0, r1, lanes_for(r1)});
+            // consecutive rows up to `target` entries; the triangle (rows < nc)
+            // and the rectangle get separate items
+            for (int r0 = 0; r0 < rows;) {
+                const int lim = r0 < nc ? nc : rows;
+                int r1 = r0 + 1;
+                while (r1 < lim && fwd_row_off(r1 + 1, nc, sn.ldc) - fwd_row_off(r0, nc, sn.ldc) <= target) ++r1;
+                const int entries = (int)(fwd_row_off(r1, nc, sn.ldc) - fwd_row_off(r0, nc, sn.ldc));
+                if (entries > kMax) {
+                    err = "a factor row does not fit the sweeps' shared-memory buffer";
+                    return HQN_ERR_UNSUPPORTED;
+                }
+                S.fwd_lvl_q[l] = std::max(S.fwd_lvl_q[l], entries);
+                S.fwd_items.push_back({s, r0, r1, lanes_for(fwd_row_len(r1 - 1, nc, sn.ldc))});
+                r0 = r1;
             }
-            for (int r0 = sn.ncol; r0 < rows; r0 += chunk)
-                S.fwd_items.push_back({s, r0, std::min(rows, r0 + chunk), G});
         }
     }
     S.fwd_lvl_ptr[L] = (int)S.fwd_items.size();
     // backward: tree level l (launched from the root level down)
     for (int l = 0; l < L; ++l) {
+        const int target = (int)std::min<int64_t>(kMax, std::max<int64_t>(kMin, lvl_entries[l] / 400));
         S.bwd_lvl_ptr[l] = (int)S.bwd_items.size();
         for (int s = 0; s < ns; ++s) {
             const SupernodeHost &sn = S.sn[s];
             if (sn.level != l || sn.ncol == 0) continue;
             S.bwd_lvl_ld[l] = std::max(S.bwd_lvl_ld[l], sn.ldr);
-            const int rows = sn.ncol + sn.nrow;
             for (int c0 = 0; c0 < sn.ncol;) {
-                const int len = rows - c0;  // entries of Q_s^T row c0 from the diagonal on
-                const int G = lanes_for(len);
-                const int ng = kBS / G;
-                int chunk = std::max(1, kEntries / std::max(1, len));
-                chunk = (chunk + ng - 1) / ng * ng;
-                const int c1 = std::min(sn.ncol, c0 + chunk);
-                S.bwd_items.push_back({s, c0, c1, G});
+                int c1 = c0 + 1;
+                while (c1 < sn.ncol && bwd_row_off(c1 + 1, sn.ldr) - bwd_row_off(c0, sn.ldr) <= target) ++c1;
+                const int entries = (int)(bwd_row_off(c1, sn.ldr) - bwd_row_off(c0, sn.ldr));
+                if (entries > kMax) {
+                    err = "a factor row does not fit the sweeps' shared-memory buffer";
+                    return HQN_ERR_UNSUPPORTED;
+                }
+                S.bwd_lvl_q[l] = std::max(S.bwd_lvl_q[l], entries);
+                S.bwd_items.push_back({s, c0, c1, lanes_for(sn.ldr - bwd_row_start(c0))});
                 c0 = c1;
             }
         }

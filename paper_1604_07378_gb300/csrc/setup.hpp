@@ -28,10 +28,10 @@ struct SupernodeHost {
     int64_t qoff = 0;                 // offset of Q_s = [L_ss^{-1}; L_Rs L_ss^{-1}] (rows x ncol)
     int uoff = 0;                     // offset of its update vector (nrow entries)
     int roff = 0;                     // offset of R in the row-index array
-    // device layout: Q_s row-major with rows padded to ldc entries (forward
-    // sweep) and Q_s^T row-major with rows padded to ldr entries (backward)
+    // device layout (layout.hpp): packed forward copy of Q_s and packed
+    // backward copy of Q_s^T; ldc = pad4(ncol), ldr = pad4(ncol + nrow)
     int ldc = 0, ldr = 0;
-    int64_t qf = 0, qb = 0;           // offsets of the two padded copies
+    int64_t qf = 0, qb = 0;           // offsets of the two copies
     std::vector<int> children;
 };
 
@@ -63,9 +63,10 @@ struct Setup {
     int n_upd = 0, n_levels = 0;
     std::vector<int> fwd_lvl_ptr, bwd_lvl_ptr;  // items of level l: [ptr[l], ptr[l+1])
     std::vector<int> fwd_lvl_ld, bwd_lvl_ld;    // max ldc / ldr over the level's supernodes
+    std::vector<int> fwd_lvl_q, bwd_lvl_q;      // max factor entries of one work item of the level
     std::vector<FwdItem> fwd_items;
     std::vector<BwdItem> bwd_items;
-    int64_t qf_total = 0, qb_total = 0;  // entries of the two padded copies
+    int64_t qf_total = 0, qb_total = 0;  // entries of the two packed copies
     int max_ld = 0;                  // max(ldc, ldr): shared-memory size of a sweep block
     int max_front_cols = 0;          // max ncol
     int64_t factor_nnz = 0;

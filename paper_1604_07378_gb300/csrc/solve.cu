@@ -8,31 +8,45 @@
 //   forward (leaves first):  f = q_C - (child updates landing on C);
 //                            z_C = L_CC^{-1} f;  u_R = L_RC z_C + (child updates on R)
 //   backward (root first):   r_C = Q_s^T [z_C; -r_R]
-// The forward sweep reads Q_s row-major (rows padded to 16 bytes), the
-// backward sweep a transposed copy, so every output is a dot of a contiguous
-// row with a vector staged in shared memory, read with 16-byte loads by a group
-// of G lanes (G sized to the row length).  A tree level is one launch; within
-// a level every supernode is independent, and updates pass up the tree through
-// index tables (each entry receives from at most two children; no atomics).
+// A tree level is one launch; within a level every supernode is independent,
+// and updates pass up the tree through index tables (each entry receives from
+// at most two children; no atomics).
+//
+// One block runs one work item: a run of consecutive rows of the packed
+// forward copy of Q_s, or of the packed backward copy of Q_s^T (layout.hpp),
+// which is one contiguous block of memory.  Thread 0 starts a single bulk
+// copy (cp.async.bulk, completion counted on an mbarrier) of those rows into
+// shared memory; meanwhile the block gathers the vector the rows multiply
+// (f, or w = [z_C; -r_R]) into shared memory.  Each output is then the dot of
+// a row with that vector, computed by a group of G lanes with 16-byte
+// shared-memory loads, two rows per group at a time.
+//
+// Consecutive levels are chained by programmatic dependent launch: a level's
+// blocks may start while the previous level still runs.  Before
+// griddepcontrol.wait a block touches only data that no sweep writes (its
+// item record, the factor rows, the index tables); the vectors produced by
+// earlier levels and by the kernels before the solve are read after it.
 #include "kernels.cuh"
+#include "layout.hpp"
 #include "reduce.cuh"
 
 namespace hqn {
 
 namespace {
 
-constexpr int SBS = 256;  // threads per block of the sweeps
+constexpr int SBS = 256;                  // threads per block of the sweeps
+constexpr long long kWaitPolls = 1 << 20;  // bound on the bulk-copy wait (polls)
 
 template <typename R> struct Vec16;
 template <> struct Vec16<float> {
     using T = float4;
     static constexpr int N = 4;
-    __device__ static float at(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+    __device__ static float dot3(const float4 &q, const float4 &a) { return q.x * a.x + q.y * a.y + q.z * a.z + q.w * a.w; }
 };
 template <> struct Vec16<double> {
     using T = double2;
     static constexpr int N = 2;
-    __device__ static double at(const double2 &v, int e) { return e == 0 ? v.x : v.y; }
+    __device__ static double dot3(const double2 &q, const double2 &a) { return q.x * a.x + q.y * a.y; }
 };
 
 template <typename R, int G>
@@ -42,168 +56,290 @@ __device__ __forceinline__ R group_sum(R v) {
     return v;
 }
 
-// acc += sum_k row[k] . (fx, fy, fz)[k] over 16-byte vectors k = k0 + lane, step G.
-template <typename R, int G>
-__device__ __forceinline__ void row_dot(const R *__restrict__ row, const R *fx, const R *fy, const R *fz, int k0,
-                                        int nv, int lane, R &ax, R &ay, R &az) {
-    using VT = typename Vec16<R>::T;
-    constexpr int VN = Vec16<R>::N;
-    const VT *rv = reinterpret_cast<const VT *>(row);
-    const VT *vx = reinterpret_cast<const VT *>(fx);
-    const VT *vy = reinterpret_cast<const VT *>(fy);
-    const VT *vz = reinterpret_cast<const VT *>(fz);
-#pragma unroll 4
-    for (int k = k0 + lane; k < nv; k += G) {
-        const VT q = __ldg(rv + k);
-        const VT a = vx[k], b = vy[k], c = vz[k];
-#pragma unroll
-        for (int e = 0; e < VN; ++e) {
-            const R qe = Vec16<R>::at(q, e);
-            ax += qe * Vec16<R>::at(a, e);
-            ay += qe * Vec16<R>::at(b, e);
-            az += qe * Vec16<R>::at(c, e);
-        }
-    }
+// ---- bulk copy global -> shared with an mbarrier (PTX ISA: cp.async.bulk, mbarrier)
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Forward item (s, row0, row1, G).
+__device__ __forceinline__ void bulk_load_start(uint64_t *bar, void *dst, const void *src, uint32_t bytes) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool bulk_load_wait(uint64_t *bar) {
+    for (long long it = 0; it < kWaitPolls; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_addr(bar))
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Every thread waits for the block's bulk copy.  Returns false (after
+// flagging the error) if it did not complete within the poll bound; the
+// block must then leave without reading the buffer.
+__device__ __forceinline__ bool bulk_load_finish(uint64_t *bar, unsigned int *err) {
+    __shared__ int timed_out;
+    if (threadIdx.x == 0) timed_out = 0;
+    __syncthreads();
+    if (!bulk_load_wait(bar)) timed_out = 1;
+    __syncthreads();
+    if (timed_out) {
+        if (threadIdx.x == 0) {
+            atomicOr(err, 1u);
+            bulk_load_wait(bar);  // give the copy in flight one more bounded chance to land
+        }
+        return false;
+    }
+    return true;
+}
+
+// ---- programmatic dependent launch (PTX ISA: griddepcontrol)
+
+// Waits until the grids this one depends on have completed and their memory
+// is visible (returns at once when the launch had no such dependency).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next grid in the stream start launching its blocks.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+__device__ __forceinline__ const void *item_src(const void *base, int4 a, int esize) {
+    const long long q0 = (long long)(unsigned)a.x | ((long long)a.y << 32);
+    return static_cast<const char *>(base) + q0 * esize;
+}
+
+// ---- forward sweep
+
+// Rows [r0, r1) of Q_s (in shared memory at qs, first row at offset off0 of
+// the supernode's block) times f: z_C for rows < nc, update entries (plus the
+// <= 2 child entries) for rows >= nc.
 template <typename R, int G>
-__device__ __forceinline__ void fwd_rows(const DevSolve<R> &S, int s, int r0, int r1, const R *f, int ldc,
-                                         V4<R> *z) {
-    const int4 sn = S.sn[s];
-    const int col = sn.x, nc = sn.y;
-    const R *Qs = S.QF + S.sn_qf[s];
-    const int uoff = S.sn_u[s];
+__device__ __forceinline__ void fwd_rows(const DevSolve<R> &S, int col, int nc, int ldc, int uoff, int r0, int r1,
+                                         int off0, const R *qs, const R *f, int ldf, V4<R> *z) {
+    using VT = typename Vec16<R>::T;
+    constexpr int VN = Vec16<R>::N;
     constexpr int NG = SBS / G;
     const int lane = threadIdx.x % G, grp = threadIdx.x / G;
-    constexpr int VN = Vec16<R>::N;
-    for (int base = r0; base < r1; base += NG) {
-        const int i = base + grp;
-        const bool valid = i < r1;
-        R ax = R(0), ay = R(0), az = R(0);
-        if (valid) {
-            const int len = i < nc ? i + 1 : nc;
-            row_dot<R, G>(Qs + (size_t)i * ldc, f, f + ldc, f + 2 * ldc, 0, (len + VN - 1) / VN, lane, ax, ay, az);
-            if (i >= nc) {
-                const int2 c = S.ug2[uoff + i - nc];
-                for (int k = lane; k < 2; k += G) {
-                    const int e = k == 0 ? c.x : c.y;
-                    if (e >= 0) {
-                        const V4<R> v = S.u[e];
-                        ax += v.x; ay += v.y; az += v.z;
-                    }
+    const VT *fx = reinterpret_cast<const VT *>(f);
+    const VT *fy = reinterpret_cast<const VT *>(f + ldf);
+    const VT *fz = reinterpret_cast<const VT *>(f + 2 * ldf);
+    for (int base = r0; base < r1; base += 2 * NG) {
+        const int i0 = base + 2 * grp, i1 = i0 + 1;
+        const bool v0 = i0 < r1, v1 = i1 < r1;
+        const int n0 = v0 ? fwd_row_len(i0, nc, ldc) / VN : 0;
+        const int n1 = v1 ? fwd_row_len(i1, nc, ldc) / VN : 0;
+        const VT *q0 = reinterpret_cast<const VT *>(qs + (v0 ? fwd_row_off(i0, nc, ldc) - off0 : 0));
+        const VT *q1 = reinterpret_cast<const VT *>(qs + (v1 ? fwd_row_off(i1, nc, ldc) - off0 : 0));
+        R a0x = R(0), a0y = R(0), a0z = R(0), a1x = R(0), a1y = R(0), a1z = R(0);
+        const int nmax = n0 > n1 ? n0 : n1;
+        for (int k = lane; k < nmax; k += G) {
+            const VT x = fx[k], y = fy[k], w = fz[k];
+            if (k < n0) {
+                const VT q = q0[k];
+                a0x += Vec16<R>::dot3(q, x); a0y += Vec16<R>::dot3(q, y); a0z += Vec16<R>::dot3(q, w);
+            }
+            if (k < n1) {
+                const VT q = q1[k];
+                a1x += Vec16<R>::dot3(q, x); a1y += Vec16<R>::dot3(q, y); a1z += Vec16<R>::dot3(q, w);
+            }
+        }
+        a0x = group_sum<R, G>(a0x); a0y = group_sum<R, G>(a0y); a0z = group_sum<R, G>(a0z);
+        a1x = group_sum<R, G>(a1x); a1y = group_sum<R, G>(a1y); a1z = group_sum<R, G>(a1z);
+        if (lane == 0) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = h ? i1 : i0;
+                if (!(h ? v1 : v0)) continue;
+                V4<R> o;
+                o.x = h ? a1x : a0x; o.y = h ? a1y : a0y; o.z = h ? a1z : a0z; o.w = R(0);
+                if (i < nc) {
+                    z[col + i] = o;
+                } else {
+                    const int2 c = S.ug2[uoff + i - nc];
+                    if (c.x >= 0) { const V4<R> a = S.u[c.x]; o.x += a.x; o.y += a.y; o.z += a.z; }
+                    if (c.y >= 0) { const V4<R> a = S.u[c.y]; o.x += a.x; o.y += a.y; o.z += a.z; }
+                    S.u[uoff + i - nc] = o;
                 }
             }
         }
-        ax = group_sum<R, G>(ax);
-        ay = group_sum<R, G>(ay);
-        az = group_sum<R, G>(az);
-        if (valid && lane == 0) {
-            V4<R> o;
-            o.x = ax; o.y = ay; o.z = az; o.w = R(0);
-            if (i < nc) z[col + i] = o;
-            else S.u[uoff + i - nc] = o;
-        }
     }
 }
 
+// Dynamic shared memory: [Q rows: qcap entries][f: 3 x ldf entries][child
+// update entries of the columns: ldf int2].
 template <typename R>
-__global__ void __launch_bounds__(SBS) k_fwd(DevSolve<R> S, int item0, const V4<R> *rhs, V4<R> *z) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *f = reinterpret_cast<R *>(smem_raw);
-    const int4 it = S.fwd_items[item0 + blockIdx.x];
-    const int s = it.x;
-    const int4 sn = S.sn[s];
-    const int col = sn.x, nc = sn.y;
-    const int ldc = S.sn_ld[s].x;
-    for (int j = threadIdx.x; j < ldc; j += SBS) {
+__global__ void __launch_bounds__(SBS) k_fwd(DevSolve<R> S, int item0, int qcap, const V4<R> *rhs, V4<R> *z) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    R *qs = reinterpret_cast<R *>(smem_raw);
+    const int4 *rec = S.fwd_items + 3 * (size_t)(item0 + blockIdx.x);
+    const int4 a = rec[0];
+    if (threadIdx.x == 0) bulk_load_start(&bar, qs, item_src(S.QF, a, sizeof(R)), (uint32_t)a.z);
+    const int4 b = rec[1], c = rec[2];
+    const int col = b.x, nc = b.y, ldc = b.z, uoff = b.w;
+    const int r0 = c.x, r1 = c.y, ldf = c.z, off0 = c.w;
+    R *f = qs + qcap;
+    int2 *cidx = reinterpret_cast<int2 *>(f + 3 * ldf);
+    const int nf = ldf < nc ? ldf : nc;
+    for (int j = threadIdx.x; j < nf; j += SBS) cidx[j] = S.fg2[col + j];
+    pdl_wait();
+    pdl_trigger();
+    // f = q_C - (child updates on C), entries [0, ldf); zero beyond nc
+    for (int j = threadIdx.x; j < ldf; j += SBS) {
         R vx = R(0), vy = R(0), vz = R(0);
         if (j < nc) {
             const V4<R> v = rhs[col + j];
-            const int2 c = S.fg2[col + j];
+            const int2 ci = cidx[j];
             vx = v.x; vy = v.y; vz = v.z;
-            if (c.x >= 0) { const V4<R> a = S.u[c.x]; vx -= a.x; vy -= a.y; vz -= a.z; }
-            if (c.y >= 0) { const V4<R> a = S.u[c.y]; vx -= a.x; vy -= a.y; vz -= a.z; }
+            if (ci.x >= 0) { const V4<R> u = S.u[ci.x]; vx -= u.x; vy -= u.y; vz -= u.z; }
+            if (ci.y >= 0) { const V4<R> u = S.u[ci.y]; vx -= u.x; vy -= u.y; vz -= u.z; }
         }
-        f[j] = vx; f[ldc + j] = vy; f[2 * ldc + j] = vz;
+        f[j] = vx; f[ldf + j] = vy; f[2 * ldf + j] = vz;
     }
-    __syncthreads();
-    const int r0 = it.y, r1 = it.z;
-    switch (it.w) {
-        case 1: fwd_rows<R, 1>(S, s, r0, r1, f, ldc, z); break;
-        case 2: fwd_rows<R, 2>(S, s, r0, r1, f, ldc, z); break;
-        case 4: fwd_rows<R, 4>(S, s, r0, r1, f, ldc, z); break;
-        case 8: fwd_rows<R, 8>(S, s, r0, r1, f, ldc, z); break;
-        case 16: fwd_rows<R, 16>(S, s, r0, r1, f, ldc, z); break;
-        default: fwd_rows<R, 32>(S, s, r0, r1, f, ldc, z); break;
+    if (!bulk_load_finish(&bar, S.err)) return;
+    switch (a.w) {
+        case 1: fwd_rows<R, 1>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z); break;
+        case 2: fwd_rows<R, 2>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z); break;
+        case 4: fwd_rows<R, 4>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z); break;
+        case 8: fwd_rows<R, 8>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z); break;
+        case 16: fwd_rows<R, 16>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z); break;
+        default: fwd_rows<R, 32>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z); break;
     }
 }
 
-// Backward item (s, col0, col1, G): r_j = (row j of Q_s^T) . [z_C; -r_R].
+// ---- backward sweep
+
+// Rows [c0, c1) of Q_s^T (in shared memory at qs, first row at offset off0)
+// times w, where w holds entries [w0, ldr) of [z_C; -r_R]: r_j for the
+// columns j of the supernode.
 template <typename R, int G>
-__device__ __forceinline__ void bwd_cols(const DevSolve<R> &S, int s, int c0, int c1, const R *w, int ldr,
-                                         V4<R> *r) {
-    const int col = S.sn[s].x;
-    const R *Qb = S.QB + S.sn_qb[s];
-    constexpr int NG = SBS / G;
+__device__ __forceinline__ void bwd_rows(int col, int ldr, int c0, int c1, int off0, const R *qs, const R *w,
+                                         int lw, int w0, V4<R> *r) {
+    using VT = typename Vec16<R>::T;
     constexpr int VN = Vec16<R>::N;
+    constexpr int NG = SBS / G;
     const int lane = threadIdx.x % G, grp = threadIdx.x / G;
-    const int nv = ldr / VN;
-    for (int base = c0; base < c1; base += NG) {
-        const int j = base + grp;
-        const bool valid = j < c1;
-        R ax = R(0), ay = R(0), az = R(0);
-        if (valid) row_dot<R, G>(Qb + (size_t)j * ldr, w, w + ldr, w + 2 * ldr, j / VN, nv, lane, ax, ay, az);
-        ax = group_sum<R, G>(ax);
-        ay = group_sum<R, G>(ay);
-        az = group_sum<R, G>(az);
-        if (valid && lane == 0) {
-            V4<R> o;
-            o.x = ax; o.y = ay; o.z = az; o.w = R(0);
-            r[col + j] = o;
+    const VT *wx = reinterpret_cast<const VT *>(w);
+    const VT *wy = reinterpret_cast<const VT *>(w + lw);
+    const VT *wz = reinterpret_cast<const VT *>(w + 2 * lw);
+    const int kend = (ldr - w0) / VN;
+    for (int base = c0; base < c1; base += 2 * NG) {
+        const int j0 = base + 2 * grp, j1 = j0 + 1;
+        const bool v0 = j0 < c1, v1 = j1 < c1;
+        // row j covers w vectors [k_j, kend)
+        const int k0 = v0 ? (bwd_row_start(j0) - w0) / VN : kend;
+        const int k1 = v1 ? (bwd_row_start(j1) - w0) / VN : kend;
+        const VT *q0 = reinterpret_cast<const VT *>(qs + (v0 ? bwd_row_off(j0, ldr) - off0 : 0)) - k0;
+        const VT *q1 = reinterpret_cast<const VT *>(qs + (v1 ? bwd_row_off(j1, ldr) - off0 : 0)) - k1;
+        R a0x = R(0), a0y = R(0), a0z = R(0), a1x = R(0), a1y = R(0), a1z = R(0);
+        const int kmin = k0 < k1 ? k0 : k1;
+        for (int k = kmin + lane; k < kend; k += G) {
+            const VT x = wx[k], y = wy[k], v = wz[k];
+            if (k >= k0) {
+                const VT q = q0[k];
+                a0x += Vec16<R>::dot3(q, x); a0y += Vec16<R>::dot3(q, y); a0z += Vec16<R>::dot3(q, v);
+            }
+            if (k >= k1) {
+                const VT q = q1[k];
+                a1x += Vec16<R>::dot3(q, x); a1y += Vec16<R>::dot3(q, y); a1z += Vec16<R>::dot3(q, v);
+            }
+        }
+        a0x = group_sum<R, G>(a0x); a0y = group_sum<R, G>(a0y); a0z = group_sum<R, G>(a0z);
+        a1x = group_sum<R, G>(a1x); a1y = group_sum<R, G>(a1y); a1z = group_sum<R, G>(a1z);
+        if (lane == 0) {
+            if (v0) { V4<R> o; o.x = a0x; o.y = a0y; o.z = a0z; o.w = R(0); r[col + j0] = o; }
+            if (v1) { V4<R> o; o.x = a1x; o.y = a1y; o.z = a1z; o.w = R(0); r[col + j1] = o; }
         }
     }
 }
 
+// Dynamic shared memory: [Q^T rows: qcap entries][w: 3 x lw entries][row
+// indices of the entries of w past nc: lw int].
 template <typename R>
-__global__ void __launch_bounds__(SBS) k_bwd(DevSolve<R> S, int item0, const V4<R> *z, V4<R> *r) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R *w = reinterpret_cast<R *>(smem_raw);
-    const int4 it = S.bwd_items[item0 + blockIdx.x];
-    const int s = it.x;
-    const int4 sn = S.sn[s];
-    const int col = sn.x, nc = sn.y, nr = sn.z, roff = sn.w;
+__global__ void __launch_bounds__(SBS) k_bwd(DevSolve<R> S, int item0, int qcap, const V4<R> *z, V4<R> *r) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    R *qs = reinterpret_cast<R *>(smem_raw);
+    const int4 *rec = S.bwd_items + 3 * (size_t)(item0 + blockIdx.x);
+    const int4 a = rec[0];
+    if (threadIdx.x == 0) bulk_load_start(&bar, qs, item_src(S.QB, a, sizeof(R)), (uint32_t)a.z);
+    const int4 b = rec[1], c = rec[2];
+    const int col = b.x, nc = b.y, nr = b.z, roff = b.w;
+    const int c0 = c.x, c1 = c.y, ldr = c.z, off0 = c.w;
     const int rows = nc + nr;
-    const int ldr = S.sn_ld[s].y;
-    constexpr int VN = Vec16<R>::N;
-    const int c0 = it.y;
-    const int i0 = (c0 / VN) * VN;  // entries of w below i0 meet only zeros of Q_s^T
-    for (int i = i0 + threadIdx.x; i < ldr; i += SBS) {
+    // w = [z_C; -r_R] from entry w0 on (entries below w0 meet no stored row entry)
+    const int w0 = bwd_row_start(c0);
+    const int lw = ldr - w0;
+    R *w = qs + qcap;
+    int *ridx = reinterpret_cast<int *>(w + 3 * lw);
+    for (int k = threadIdx.x; k < lw; k += SBS) {
+        const int i = w0 + k;
+        ridx[k] = (i >= nc && i < rows) ? S.rows[roff + i - nc] : -1;
+    }
+    pdl_wait();
+    pdl_trigger();
+    for (int k = threadIdx.x; k < lw; k += SBS) {
+        const int i = w0 + k;
         R vx = R(0), vy = R(0), vz = R(0);
         if (i < nc) {
             const V4<R> v = z[col + i];
             vx = v.x; vy = v.y; vz = v.z;
-        } else if (i < rows) {
-            const V4<R> v = r[S.rows[roff + i - nc]];
+        } else if (ridx[k] >= 0) {
+            const V4<R> v = r[ridx[k]];
             vx = -v.x; vy = -v.y; vz = -v.z;
         }
-        w[i] = vx; w[ldr + i] = vy; w[2 * ldr + i] = vz;
+        w[k] = vx; w[lw + k] = vy; w[2 * lw + k] = vz;
     }
-    __syncthreads();
-    switch (it.w) {
-        case 1: bwd_cols<R, 1>(S, s, c0, it.z, w, ldr, r); break;
-        case 2: bwd_cols<R, 2>(S, s, c0, it.z, w, ldr, r); break;
-        case 4: bwd_cols<R, 4>(S, s, c0, it.z, w, ldr, r); break;
-        case 8: bwd_cols<R, 8>(S, s, c0, it.z, w, ldr, r); break;
-        case 16: bwd_cols<R, 16>(S, s, c0, it.z, w, ldr, r); break;
-        default: bwd_cols<R, 32>(S, s, c0, it.z, w, ldr, r); break;
+    if (!bulk_load_finish(&bar, S.err)) return;
+    switch (a.w) {
+        case 1: bwd_rows<R, 1>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
+        case 2: bwd_rows<R, 2>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
+        case 4: bwd_rows<R, 4>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
+        case 8: bwd_rows<R, 8>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
+        case 16: bwd_rows<R, 16>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
+        default: bwd_rows<R, 32>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
     }
+}
+
+// Dynamic shared memory of a sweep block: qcap factor entries, 3 x ld vector
+// entries and ld 8-byte index slots.
+template <typename R>
+size_t sweep_smem(int qcap, int ld) {
+    return ((size_t)qcap + 3 * (size_t)ld) * sizeof(R) + 8 * (size_t)ld;
+}
+
+// One level's launch, with the programmatic-serialisation attribute when
+// the handle chains levels.
+template <typename R, typename... Args>
+void launch_level(bool pdl, void (*kernel)(DevSolve<R>, int, int, Args...), int grid, size_t smem, cudaStream_t st,
+                  const DevSolve<R> &s, int item0, int qcap, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(SBS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, s, item0, qcap, args...);
 }
 
 }  // namespace
 
 template <typename R> int solve_smem_limit_ok(int max_ld) {
-    return (size_t)3 * max_ld * sizeof(R) <= (size_t)SOLVE_MAX_SMEM;
+    return sweep_smem<R>(65536 / (int)sizeof(R), max_ld) <= (size_t)SOLVE_MAX_SMEM;
 }
 
 template <typename R> cudaError_t solve_prepare() {
@@ -216,11 +352,17 @@ template <typename R>
 void launch_solve(const DevSolve<R> &s, const V4<R> *q, V4<R> *z, V4<R> *r, cudaStream_t st) {
     for (int l = 0; l < s.n_levels; ++l) {
         const int a = s.fwd_lvl_ptr[l], b = s.fwd_lvl_ptr[l + 1];
-        if (b > a) k_fwd<R><<<b - a, SBS, (size_t)3 * s.fwd_lvl_ld[l] * sizeof(R), st>>>(s, a, q, z);
+        if (b > a)
+            launch_level<R, const V4<R> *, V4<R> *>(s.pdl != 0, k_fwd<R>, b - a,
+                                                     sweep_smem<R>(s.fwd_lvl_q[l], s.fwd_lvl_ld[l]), st, s, a,
+                                                     s.fwd_lvl_q[l], q, z);
     }
     for (int l = s.n_levels - 1; l >= 0; --l) {
         const int a = s.bwd_lvl_ptr[l], b = s.bwd_lvl_ptr[l + 1];
-        if (b > a) k_bwd<R><<<b - a, SBS, (size_t)3 * s.bwd_lvl_ld[l] * sizeof(R), st>>>(s, a, z, r);
+        if (b > a)
+            launch_level<R, const V4<R> *, V4<R> *>(s.pdl != 0, k_bwd<R>, b - a,
+                                                     sweep_smem<R>(s.bwd_lvl_q[l], s.bwd_lvl_ld[l]), st, s, a,
+                                                     s.bwd_lvl_q[l], (const V4<R> *)z, r);
     }
 }
 

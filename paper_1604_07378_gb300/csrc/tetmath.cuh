@@ -27,19 +27,22 @@ template <typename R> struct Eps;
 template <> struct Eps<float> { static constexpr float v = 1.1920929e-7f; };
 template <> struct Eps<double> { static constexpr double v = 2.220446049250313e-16; };
 
-// x - log(1 + x) without cancellation: its Taylor series sum_{k>=2} (-1)^k x^k / k
-// for |x| < 0.1 (truncation below 1e-11 relative), the direct form elsewhere.
+// x - log(1 + x) without cancellation: for |x| < 0.1 its Taylor series
+// sum_{k>=2} (-1)^k x^k / k in Horner form, x^2 (1/2 - x (1/3 - x (1/4 - ...))),
+// truncated where the next term is below the precision of R (k <= 9 in float,
+// k <= 18 in double); the direct form elsewhere.
+template <typename R> struct LogSeries;
+template <> struct LogSeries<float> { static constexpr int K = 9; };
+template <> struct LogSeries<double> { static constexpr int K = 18; };
+
 template <typename R>
 __device__ __forceinline__ R x_minus_log1p(R x) {
     if (abs_(x) < R(0.1)) {
-        R s = R(0);
-        R pk = x * x;  // x^k, k = 2
+        constexpr int K = LogSeries<R>::K;
+        R p = R(1.0 / K);
 #pragma unroll
-        for (int k = 2; k <= 12; ++k) {
-            s += ((k & 1) ? -pk : pk) / R(k);
-            pk *= x;
-        }
-        return s;
+        for (int k = K - 1; k >= 2; --k) p = R(1.0 / k) - x * p;
+        return x * x * p;
     }
     return x - log1p_(x);
 }
@@ -341,6 +344,163 @@ __device__ __forceinline__ R tet_psi(const MatDev<R> &M, const R G[3][3]) {
 }
 
 template <typename R> __device__ __forceinline__ R fma_(R a, R b, R c) { return fma(a, b, c); }
+
+// Psi(I + Gk + alpha Gd) for many step lengths alpha of one line search.
+// Neo-Hookean and StVK are polynomials in alpha once the tet's Gk and Gd are
+// known, so their coefficients are formed once and each alpha costs a few
+// fused multiply-adds plus, for Neo-Hookean, log1p and the series above:
+//   NH:   with d = det F - 1 = tr G + m2(G) + det G (cubic in alpha),
+//         I1 - 3 - 2 ln J = |G|^2 - 2 (m2 + det G) + 2 (d - log1p d),
+//         so |G|^2 - 2 (m2 + det G) is a cubic P(alpha) and d a cubic D(alpha);
+//         below J0 the quadratic continuation uses |G|^2 + 2 tr G (quadratic).
+//   StVK: E = (G + G^T + G^T G) / 2 = E0 + alpha E1 + alpha^2 E2, so |E|^2 is a
+//         quartic and tr E a quadratic.
+// The other materials evaluate tet_psi at G = Gk + alpha Gd.
+template <typename R>
+struct PsiRay {
+    R c[11];      // polynomial coefficients (material-specific)
+    R Gk[3][3], Gd[3][3];
+};
+
+template <typename R>
+__device__ __forceinline__ R det3g(const R G[3][3]) {
+    return G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) - G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
+           G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
+}
+
+// Cofactor matrix: C[a][b] = d det(G) / d G[a][b].
+template <typename R>
+__device__ __forceinline__ void cofactor3(const R G[3][3], R C[3][3]) {
+    C[0][0] = G[1][1] * G[2][2] - G[1][2] * G[2][1];
+    C[0][1] = G[1][2] * G[2][0] - G[1][0] * G[2][2];
+    C[0][2] = G[1][0] * G[2][1] - G[1][1] * G[2][0];
+    C[1][0] = G[0][2] * G[2][1] - G[0][1] * G[2][2];
+    C[1][1] = G[0][0] * G[2][2] - G[0][2] * G[2][0];
+    C[1][2] = G[0][1] * G[2][0] - G[0][0] * G[2][1];
+    C[2][0] = G[0][1] * G[1][2] - G[0][2] * G[1][1];
+    C[2][1] = G[0][2] * G[1][0] - G[0][0] * G[1][2];
+    C[2][2] = G[0][0] * G[1][1] - G[0][1] * G[1][0];
+}
+
+template <typename R>
+__device__ __forceinline__ void psi_ray_setup(const MatDev<R> &M, const R Gk[3][3], const R Gd[3][3], PsiRay<R> &r) {
+    if (M.kind == HQN_NEOHOOKEAN) {
+        // tr G, |G|^2, m2(G) (sum of principal 2x2 minors) and det G along the ray
+        const R t0 = Gk[0][0] + Gk[1][1] + Gk[2][2], t1 = Gd[0][0] + Gd[1][1] + Gd[2][2];
+        R n0 = R(0), n1 = R(0), n2 = R(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                n0 += Gk[a][b] * Gk[a][b];
+                n1 += Gk[a][b] * Gd[a][b];
+                n2 += Gd[a][b] * Gd[a][b];
+            }
+        n1 *= R(2);
+        // m2(A + alpha B) = m2(A) + alpha (tr A tr B - tr(AB)) + alpha^2 m2(B)
+        R trAB = R(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) trAB += Gk[a][b] * Gd[b][a];
+        const R m2k = (Gk[0][0] * Gk[1][1] - Gk[0][1] * Gk[1][0]) + (Gk[0][0] * Gk[2][2] - Gk[0][2] * Gk[2][0]) +
+                      (Gk[1][1] * Gk[2][2] - Gk[1][2] * Gk[2][1]);
+        const R m2d = (Gd[0][0] * Gd[1][1] - Gd[0][1] * Gd[1][0]) + (Gd[0][0] * Gd[2][2] - Gd[0][2] * Gd[2][0]) +
+                      (Gd[1][1] * Gd[2][2] - Gd[1][2] * Gd[2][1]);
+        const R m1 = t0 * t1 - trAB;
+        // det(A + alpha B) = det A + alpha <cof A, B> + alpha^2 <A, cof B> + alpha^3 det B
+        R Ck[3][3], Cd[3][3];
+        cofactor3(Gk, Ck);
+        cofactor3(Gd, Cd);
+        R e1 = R(0), e2 = R(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                e1 += Ck[a][b] * Gd[a][b];
+                e2 += Gk[a][b] * Cd[a][b];
+            }
+        const R e0 = det3g(Gk), e3 = det3g(Gd);
+        // D = tr + m2 + det; P = |G|^2 - 2 (m2 + det); Q = |G|^2 + 2 tr (below J0)
+        r.c[0] = t0 + m2k + e0; r.c[1] = t1 + m1 + e1; r.c[2] = m2d + e2; r.c[3] = e3;
+        r.c[4] = n0 - R(2) * (m2k + e0); r.c[5] = n1 - R(2) * (m1 + e1);
+        r.c[6] = n2 - R(2) * (m2d + e2); r.c[7] = -R(2) * e3;
+        r.c[8] = n0 + R(2) * t0; r.c[9] = n1 + R(2) * t1; r.c[10] = n2;
+        return;
+    }
+    if (M.kind == HQN_STVK) {
+        // E0 = (Gk + Gk^T + Gk^T Gk)/2, E1 = (Gd + Gd^T + Gk^T Gd + Gd^T Gk)/2, E2 = Gd^T Gd / 2
+        R E0[3][3], E1[3][3], E2[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                R kk = R(0), kd = R(0), dk = R(0), dd = R(0);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    kk += Gk[i][a] * Gk[i][b];
+                    kd += Gk[i][a] * Gd[i][b];
+                    dk += Gd[i][a] * Gk[i][b];
+                    dd += Gd[i][a] * Gd[i][b];
+                }
+                E0[a][b] = R(0.5) * (Gk[a][b] + Gk[b][a] + kk);
+                E1[a][b] = R(0.5) * (Gd[a][b] + Gd[b][a] + kd + dk);
+                E2[a][b] = R(0.5) * dd;
+            }
+        R p00 = R(0), p01 = R(0), p02 = R(0), p11 = R(0), p12 = R(0), p22 = R(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                p00 += E0[a][b] * E0[a][b];
+                p01 += E0[a][b] * E1[a][b];
+                p02 += E0[a][b] * E2[a][b];
+                p11 += E1[a][b] * E1[a][b];
+                p12 += E1[a][b] * E2[a][b];
+                p22 += E2[a][b] * E2[a][b];
+            }
+        // |E|^2 = p00 + 2 p01 a + (p11 + 2 p02) a^2 + 2 p12 a^3 + p22 a^4
+        r.c[0] = p00; r.c[1] = R(2) * p01; r.c[2] = p11 + R(2) * p02; r.c[3] = R(2) * p12; r.c[4] = p22;
+        r.c[5] = E0[0][0] + E0[1][1] + E0[2][2];
+        r.c[6] = E1[0][0] + E1[1][1] + E1[2][2];
+        r.c[7] = E2[0][0] + E2[1][1] + E2[2][2];
+        return;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            r.Gk[a][b] = Gk[a][b];
+            r.Gd[a][b] = Gd[a][b];
+        }
+}
+
+template <typename R>
+__device__ __forceinline__ R psi_ray_eval(const MatDev<R> &M, const PsiRay<R> &r, R al) {
+    if (M.kind == HQN_NEOHOOKEAN) {
+        const R d = r.c[0] + al * (r.c[1] + al * (r.c[2] + al * r.c[3]));
+        const R J = R(1) + d;
+        if (J >= M.J0) {
+            const R P = r.c[4] + al * (r.c[5] + al * (r.c[6] + al * r.c[7]));
+            const R lnJ = log1p_(d);
+            return R(0.5) * M.mu * (P + R(2) * x_minus_log1p(d)) + R(0.5) * M.lam * lnJ * lnJ;
+        }
+        const R Q = r.c[8] + al * (r.c[9] + al * r.c[10]);
+        const R dJ = J - M.J0;
+        return R(0.5) * M.mu * Q + M.c0 + dJ * (M.c1 + R(0.5) * M.c2 * dJ);
+    }
+    if (M.kind == HQN_STVK) {
+        const R n2 = r.c[0] + al * (r.c[1] + al * (r.c[2] + al * (r.c[3] + al * r.c[4])));
+        const R tr = r.c[5] + al * (r.c[6] + al * r.c[7]);
+        return M.mu * n2 + R(0.5) * M.lam * tr * tr;
+    }
+    R G[3][3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) G[p][q] = fma_(al, r.Gd[p][q], r.Gk[p][q]);
+    return tet_psi(M, G);
+}
 
 // G = Du Dm^{-1}: du[j] = u_{j+1} - u_0 (rows), Di = Dm^{-1} row-major.
 template <typename R>

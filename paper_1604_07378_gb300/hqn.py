@@ -66,7 +66,8 @@ class Info(C.Structure):
                 ("factor_entries", C.c_int64), ("factor_nnz", C.c_int64),
                 ("stiffness_k", C.c_double), ("setup_seconds", C.c_double),
                 ("device_bytes", C.c_int64), ("precision", C.c_int32),
-                ("graph_mode", C.c_int32), ("n_update_entries", C.c_int64)]
+                ("graph_mode", C.c_int32), ("n_update_entries", C.c_int64),
+                ("chained_sweeps", C.c_int32)]
 
 
 _lib = None
