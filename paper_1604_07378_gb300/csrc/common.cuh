@@ -36,6 +36,8 @@ struct MatDev {
 struct Ctl {
     double g_k;        // g(x_k)
     double g_trial;    // g at the current line-search trial
+    double e_k;        // elastic energy E(x_k) (the Armijo test compares differences)
+    double e_trial;    // E at the accepted trial
     double gd;         // tr(grad_k^T d)
     double alpha;      // current step length
     double g0;         // g(x_1), x_1 = y

@@ -56,15 +56,17 @@ __global__ void __launch_bounds__(VBS) k_predict(DevSim<R> s) {
 // the caller-given point x_t (the start of a step, or an evaluation request).
 template <typename R>
 __global__ void __launch_bounds__(VBS) k_inertia(DevSim<R> s) {
+    using A = ExactAcc<R>;
     const int i = blockIdx.x * VBS + threadIdx.x;
-    double e[1] = {0.0};
+    typename A::T e[1] = {A::zero()};
     if (i < s.c.n) {
         const V4<R> x = s.xt[i], yy = s.y[i];
         const R dx = x.x - yy.x, dy = x.y - yy.y, dz = x.z - yy.z;
-        e[0] = (double)(R(0.5) * s.mh2[i] * (dx * dx + dy * dy + dz * dz));
+        e[0] = A::add(e[0], R(0.5) * s.mh2[i] * (dx * dx + dy * dy + dz * dz));
     }
-    block_sum<VBS, 1>(e);
-    if (threadIdx.x == 0) s.part_in[blockIdx.x] = e[0];
+    double tot[1];
+    block_sum_exact<VBS, 1, R>(e, tot);
+    if (threadIdx.x == 0) s.part_in[blockIdx.x] = tot[0];
 }
 
 // x_k + alpha d, rounded the same way wherever the accepted point is formed.
@@ -107,14 +109,15 @@ __device__ __forceinline__ void edge_diffs(const V4<R> &x0, const V4<R> &x1, con
 //   TET_GRAD: at the accepted point x_k + alpha d, corners only; nothing to do
 //     if TET_TRIAL1 already left them there or the iterations stopped.
 template <typename R, int BS>
-__global__ void __launch_bounds__(BS) k_tet(DevSim<R> s, int mode, CondHandles h) {
+__global__ void __launch_bounds__(BS, 1024 / BS) k_tet(DevSim<R> s, int mode, CondHandles h) {
     const bool grad_mode = mode == TET_GRAD;
     const bool ray_mode = mode == TET_GRAD || mode == TET_TRIAL1;
     if (grad_mode && (s.ctl->stop || s.ctl->grad_ready)) return;
     const R al = grad_mode ? (R)s.ctl->alpha : R(1);
+    using A = ExactAcc<R>;
     const int T = s.c.T;
     const int t = blockIdx.x * BS + threadIdx.x;
-    double e[1] = {0.0};
+    typename A::T e[1] = {A::zero()};
     if (t < T) {
         const int4 v = s.tets[t];
         V4<R> x0, x1, x2, x3;
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(BS) k_tet(DevSim<R> s, int mode, CondHandles h
         const R vol = s.vol[t];
         R g[4][3];
         tet_grad(s.mat, G, Di, vol, g);
-        if (!grad_mode) e[0] = (double)(vol * tet_psi(s.mat, G));
+        if (!grad_mode) e[0] = A::add(e[0], vol * tet_psi(s.mat, G));
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             V4<R> o;
@@ -142,22 +145,25 @@ __global__ void __launch_bounds__(BS) k_tet(DevSim<R> s, int mode, CondHandles h
         }
     }
     if (grad_mode) return;
-    block_sum<BS, 1>(e);
-    if (!publish_and_arrive<1>(e, s.part_el, 0, &s.ctl->ticket[TK_TET])) return;
     double tot[1];
+    block_sum_exact<BS, 1, R>(e, tot);
+    if (!publish_and_arrive<1>(tot, s.part_el, 0, &s.ctl->ticket[TK_TET])) return;
     sum_partials<BS, 1>(s.part_el, 0, gridDim.x, tot, &s.ctl->ticket[TK_TET]);
     Ctl *c = s.ctl;
     if (mode == TET_TRIAL1) {
         if (threadIdx.x != 0) return;
-        // g(x_k + d) = elastic + I(1), I(alpha) = a0 + a1 alpha + a2 alpha^2
-        const double g = tot[0] + (c->ls_a[0] + c->ls_a[1] + c->ls_a[2]);
+        // g(x_k + d) - g(x_k) = E(x_k + d) - E(x_k) + I(1) - I(0) with the
+        // inertia term I(alpha) = a0 + a1 alpha + a2 alpha^2 along the ray
+        const double e = tot[0];
+        const double dI = c->ls_a[1] + c->ls_a[2];
         c->passes_total += 1;
         c->trials = 1;
-        if (g <= c->g_k + s.c.gamma * c->gd) {
+        if ((e - c->e_k) + dI <= s.c.gamma * c->gd) {
             c->accepted = 1;
             c->grad_ready = 1;
             c->alpha = 1.0;
-            c->g_trial = g;
+            c->e_trial = e;
+            c->g_trial = e + c->ls_a[0] + dI;
             set_cond<R>(h.ls, 0u);
         } else {
             c->accepted = 0;
@@ -186,6 +192,7 @@ __global__ void __launch_bounds__(BS) k_tet(DevSim<R> s, int mode, CondHandles h
     c->g_trial = g;
     if (mode == TET_INIT) {
         c->g_k = g;
+        c->e_k = tot[0];
         c->g0 = g;
         c->accepted = 1;
     }
@@ -198,20 +205,23 @@ __global__ void __launch_bounds__(BS) k_tet(DevSim<R> s, int mode, CondHandles h
 // forms G_k = Du_k Dm^{-1} and G_d = Dd Dm^{-1} once and the energy V Psi of
 // G_k + alpha_j G_d for every j (no singular vectors: PsiRay).  The last
 // block adds the inertia term, a quadratic in alpha whose coefficients were
-// formed with the direction, and runs the Armijo tests in the order of Alg. 1:
-// the first alpha_j with g <= g_k + gamma alpha_j tr(grad^T d) is accepted
-// (the same choice as testing them one at a time).  Otherwise the next pass
+// formed with the direction, and runs the Armijo tests in the order of Alg. 1
+// (written on differences, g(x_k + a d) - g(x_k) <= gamma a tr(grad^T d), so
+// the inertia term's constant part never enters a comparison): the first
+// alpha_j that passes is accepted (the same choice as testing them one at a
+// time).  Otherwise the next pass
 // continues from alpha_K, until ls_max trials in all.
 template <typename R, int BS, int K>
 __global__ void __launch_bounds__(BS) k_ls(DevSim<R> s, CondHandles h) {
     Ctl *ctl = s.ctl;
     const double a0 = ctl->alpha;
     const double bt = s.c.backtrack;
+    using A = ExactAcc<R>;
     const int T = s.c.T;
     const int t = blockIdx.x * BS + threadIdx.x;
-    double e[K];
+    typename A::T e[K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) e[j] = 0.0;
+    for (int j = 0; j < K; ++j) e[j] = A::zero();
     if (t < T) {
         const int4 v = s.tets[t];
         R Duk[3][3], Dd[3][3], Di[9], Gk[3][3], Gd[3][3];
@@ -226,19 +236,19 @@ __global__ void __launch_bounds__(BS) k_ls(DevSim<R> s, CondHandles h) {
         double a = a0;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            e[j] = (double)(vol * psi_ray_eval(s.mat, ray, (R)a));
+            e[j] = A::add(e[j], vol * psi_ray_eval(s.mat, ray, (R)a));
             a *= bt;
         }
     }
-    block_sum<BS, K>(e);
-    if (!publish_and_arrive<K>(e, s.part_ls, gridDim.x, &ctl->ticket[TK_LS])) return;
     double tot[K];
+    block_sum_exact<BS, K, R>(e, tot);
+    if (!publish_and_arrive<K>(tot, s.part_ls, gridDim.x, &ctl->ticket[TK_LS])) return;
     sum_partials<BS, K>(s.part_ls, gridDim.x, gridDim.x, tot, &ctl->ticket[TK_LS]);
     if (threadIdx.x != 0) return;
     double a = a0;
     int tr = ctl->trials;
     ctl->passes_total += 1;
-    const double gk = ctl->g_k, slope = s.c.gamma * ctl->gd;
+    const double ek = ctl->e_k, slope = s.c.gamma * ctl->gd;
     const double c0 = ctl->ls_a[0], c1 = ctl->ls_a[1], c2 = ctl->ls_a[2];
     bool done = false;
 #pragma unroll
@@ -252,11 +262,13 @@ __global__ void __launch_bounds__(BS) k_ls(DevSim<R> s, CondHandles h) {
             break;
         }
         tr += 1;
-        const double g = tot[j] + (c0 + a * (c1 + a * c2));
-        if (g <= gk + slope * a) {
+        // Armijo on differences: E(x_k + a d) - E(x_k) + I(a) - I(0) <= gamma a gd
+        const double dI = a * (c1 + a * c2);
+        if ((tot[j] - ek) + dI <= slope * a) {
             ctl->accepted = 1;
             ctl->alpha = a;
-            ctl->g_trial = g;
+            ctl->e_trial = tot[j];
+            ctl->g_trial = tot[j] + c0 + dI;
             done = true;
             break;
         }
@@ -303,14 +315,49 @@ __device__ __forceinline__ R dotr(const V4<R> &a, const V4<R> &b) {
     return a.x * b.x + a.y * b.y + a.z * b.z;
 }
 
+// The history scalars the recursions need, staged in shared memory by the
+// last block of a kernel: the control block lives in global memory, and a
+// recursion run on it directly would pay a memory round trip per step.
+constexpr int MH = HQN_MAX_HISTORY + 1;
+struct HistSmem {
+    double gram[MH][MH];  // s_a^T t_b by ring slots
+    double rho[MH], sg[MH], tr0[MH], zeta[MH], coef[MH];
+    int count, head;
+};
+
+// All threads: load the Gram matrix (rows and columns <= m), rho, zeta,
+// count and head into shared memory.
+__device__ __forceinline__ void hist_load(const Ctl *c, HistSmem &h, int m) {
+    const int m1 = m + 1;
+    for (int e = threadIdx.x; e < m1 * m1; e += blockDim.x) h.gram[e / m1][e % m1] = c->gram[e / m1][e % m1];
+    for (int a = threadIdx.x; a < m1; a += blockDim.x) {
+        h.rho[a] = c->rho[a];
+        h.zeta[a] = c->zeta[a];
+    }
+    if (threadIdx.x == 0) {
+        h.count = c->count;
+        h.head = c->head;
+    }
+    __syncthreads();
+}
+
 // First loop on scalars: zeta_p for every held pair, newest first.
-__device__ __forceinline__ void zeta_recursion(Ctl *c, int m) {
-    const int count = c->count, head = c->head;
-    for (int p = 0; p < count; ++p) {
-        const int sl = ring_slot(head, p, m);
-        double sq = -c->sg[sl];
-        for (int pp = 0; pp < p; ++pp) sq -= c->zeta[pp] * c->gram[sl][ring_slot(head, pp, m)];
-        c->zeta[p] = sq / c->rho[sl];
+__device__ __forceinline__ void zeta_recursion(HistSmem &h, int m) {
+    for (int p = 0; p < h.count; ++p) {
+        const int sl = ring_slot(h.head, p, m);
+        double sq = -h.sg[sl];
+        for (int pp = 0; pp < p; ++pp) sq -= h.zeta[pp] * h.gram[sl][ring_slot(h.head, pp, m)];
+        h.zeta[p] = sq / h.rho[sl];
+    }
+}
+
+// Second loop on scalars: c_p = zeta_p - eta_p, oldest first.
+__device__ __forceinline__ void coef_recursion(HistSmem &h, int m) {
+    for (int p = h.count - 1; p >= 0; --p) {
+        const int sl = ring_slot(h.head, p, m);
+        double tr = h.tr0[sl];
+        for (int pp = p + 1; pp < h.count; ++pp) tr += h.coef[pp] * h.gram[ring_slot(h.head, pp, m)][sl];
+        h.coef[p] = h.zeta[p] - tr / h.rho[sl];
     }
 }
 
@@ -320,7 +367,7 @@ __device__ __forceinline__ void zeta_recursion(Ctl *c, int m) {
 // corner gradients in a fixed (ascending tet) order -- no atomics.  In G_ITER
 // mode the accepted trial becomes x_{k+1}: the pair s = x_{k+1} - x_k,
 // t = grad_{k+1} - grad_k goes to the free ring slot w, and the block partials
-// of rho = tr(t^T s), |s|^2, |t|^2 (float64 terms) and of s_a^T t_w, s_w^T t_a
+// of rho = tr(t^T s) (float64 terms) and of |s|^2, |t|^2, s_a^T t_w, s_w^T t_a
 // and s_a^T grad_{k+1} for every ring slot a (R-precision terms and warp sums,
 // float64 beyond) are reduced.  The last block keeps the pair if
 // rho > 1e-12 |s| |t|, updates the Gram matrix and runs the first loop of
@@ -333,9 +380,10 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
     const bool push = mode == G_ITER && m > 0;
     const int w = push ? (ctl->head + 1) % (m + 1) : 0;
     const R al = mode == G_ITER ? (R)ctl->alpha : R(0);
-    constexpr int NG = 3 * MP1;
-    constexpr int ND = 3 + NG;
-    double dd[3] = {0.0, 0.0, 0.0};
+    constexpr int NG = 2 + 3 * MP1;  // |s|^2, |t|^2, then three products per slot
+    constexpr int ND = 1 + NG;
+    using A = ExactAcc<R>;
+    typename A::T dd[1] = {A::zero()};
     R dr[NG];
 #pragma unroll
     for (int k = 0; k < NG; ++k) dr[k] = R(0);
@@ -364,17 +412,17 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
                 tv.x = gn.x - go.x; tv.y = gn.y - go.y; tv.z = gn.z - go.z; tv.w = R(0);
                 s.S[(size_t)w * n + i] = sv;
                 s.Tt[(size_t)w * n + i] = tv;
-                dd[0] = dotv(tv, sv);
-                dd[1] = dotv(sv, sv);
-                dd[2] = dotv(tv, tv);
+                dd[0] = A::add_prod(A::add_prod(A::add_prod(dd[0], tv.x, sv.x), tv.y, sv.y), tv.z, sv.z);
+                dr[0] = dotr(sv, sv);
+                dr[1] = dotr(tv, tv);
 #pragma unroll
                 for (int a = 0; a < MP1; ++a) {
                     if (a > m) break;
                     const V4<R> sa = a == w ? sv : s.S[(size_t)a * n + i];
                     const V4<R> ta = a == w ? tv : s.Tt[(size_t)a * n + i];
-                    dr[a] = dotr(sa, tv);
-                    dr[MP1 + a] = dotr(sv, ta);
-                    dr[2 * MP1 + a] = dotr(sa, gn);
+                    dr[2 + a] = dotr(sa, tv);
+                    dr[2 + MP1 + a] = dotr(sv, ta);
+                    dr[2 + 2 * MP1 + a] = dotr(sa, gn);
                 }
             }
             s.xk[i] = x;
@@ -384,12 +432,12 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
     if (mode == G_EVAL) return;
     double dots[ND];
     if (push) {
-        double mixed[NG];
-        block_sum<VBS, 3>(dd);
-        block_sum_mixed<VBS, NG, R>(dr, mixed);
-        dots[0] = dd[0]; dots[1] = dd[1]; dots[2] = dd[2];
+        double mixed[NG], rho[1];
+        block_sum_exact<VBS, 1, R>(dd, rho);
+        block_sum_r<VBS, NG, R>(dr, mixed);
+        dots[0] = rho[0];
 #pragma unroll
-        for (int k = 0; k < NG; ++k) dots[3 + k] = mixed[k];
+        for (int k = 0; k < NG; ++k) dots[1 + k] = mixed[k];
         if (!publish_and_arrive<ND>(dots, s.part_g, gridDim.x, &ctl->ticket[TK_GATHER])) return;
         sum_partials<VBS, ND>(s.part_g, gridDim.x, gridDim.x, dots, &ctl->ticket[TK_GATHER]);
     } else {
@@ -398,8 +446,8 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
         __threadfence();
         if (threadIdx.x == 0) ctl->ticket[TK_GATHER] = 0u;
     }
-    if (threadIdx.x != 0) return;
     if (mode == G_INIT) {
+        if (threadIdx.x != 0) return;
         ctl->k = 1;
         ctl->count = 0;
         ctl->head = 0;
@@ -409,33 +457,58 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
     }
     const int k = ctl->k;
     const int kk = k - 1 < HQN_MAX_ITERS ? k - 1 : HQN_MAX_ITERS - 1;
-    ctl->iter_trials[kk] = ctl->trials;
-    ctl->trials_total += ctl->trials;
-    ctl->iters_total += 1;
     if (stop) {
+        if (threadIdx.x != 0) return;
+        ctl->iter_trials[kk] = ctl->trials;
+        ctl->trials_total += ctl->trials;
+        ctl->iters_total += 1;
         ctl->iter_g[kk] = ctl->g_k;
         set_cond<R>(h.it, 0u);
         return;
     }
     if (push) {
-        // (compile-time indices keep dots[] in registers)
-        if (dots[0] > 1e-12 * sqrt(dots[1] * dots[2])) {
-            ctl->head = w;
-            ctl->rho[w] = dots[0];
-            ctl->count = ctl->count < m ? ctl->count + 1 : m;
+        // dots (thread 0): rho, |s|^2, |t|^2, s_a^T t_w, s_w^T t_a, s_a^T grad
+        __shared__ HistSmem hs;
+        __shared__ int keep;
+        hist_load(ctl, hs, m);
+        if (threadIdx.x == 0) {
+            keep = dots[0] > 1e-12 * sqrt(dots[1] * dots[2]);
+            if (keep) {
+                hs.head = w;
+                hs.rho[w] = dots[0];
+                hs.count = hs.count < m ? hs.count + 1 : m;
+#pragma unroll
+                for (int a = 0; a < MP1; ++a)
+                    if (a <= m) {
+                        hs.gram[a][w] = dots[3 + a];
+                        hs.gram[w][a] = dots[3 + MP1 + a];
+                    }
+            }
 #pragma unroll
             for (int a = 0; a < MP1; ++a)
-                if (a <= m) {
-                    ctl->gram[a][w] = dots[3 + a];
-                    ctl->gram[w][a] = dots[3 + MP1 + a];
-                }
+                if (a <= m) hs.sg[a] = dots[3 + 2 * MP1 + a];
+            zeta_recursion(hs, m);
         }
-#pragma unroll
-        for (int a = 0; a < MP1; ++a)
-            if (a <= m) ctl->sg[a] = dots[3 + 2 * MP1 + a];
-        zeta_recursion(ctl, m);
+        __syncthreads();
+        for (int a = threadIdx.x; a <= m; a += VBS) {
+            ctl->zeta[a] = hs.zeta[a];
+            if (keep) {
+                ctl->gram[a][w] = hs.gram[a][w];
+                ctl->gram[w][a] = hs.gram[w][a];
+            }
+        }
+        if (threadIdx.x == 0 && keep) {
+            ctl->rho[w] = hs.rho[w];
+            ctl->head = hs.head;
+            ctl->count = hs.count;
+        }
     }
+    if (threadIdx.x != 0) return;
+    ctl->iter_trials[kk] = ctl->trials;
+    ctl->trials_total += ctl->trials;
+    ctl->iters_total += 1;
     ctl->g_k = ctl->g_trial;
+    ctl->e_k = ctl->e_trial;
     ctl->iter_g[kk] = ctl->g_trial;
     ctl->k = k + 1;
     set_cond<R>(h.it, (k + 1 <= s.c.iters) ? 1u : 0u);
@@ -480,20 +553,19 @@ __global__ void __launch_bounds__(VBS) k_r0_dots(DevSim<R> s) {
         }
     }
     double dots[MP1];
-    block_sum_mixed<VBS, MP1, R>(dr, dots);
+    block_sum_r<VBS, MP1, R>(dr, dots);
     if (!publish_and_arrive<MP1>(dots, s.part_v, gridDim.x, &ctl->ticket[TK_VEC])) return;
     sum_partials<VBS, MP1>(s.part_v, gridDim.x, gridDim.x, dots, &ctl->ticket[TK_VEC]);
-    if (threadIdx.x != 0) return;
+    __shared__ HistSmem hs;
+    hist_load(ctl, hs, m);
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int a = 0; a < MP1; ++a)
-        if (a <= m) ctl->tr0[a] = dots[a];
-    const int head = ctl->head;
-    for (int p = count - 1; p >= 0; --p) {
-        const int sl = ring_slot(head, p, m);
-        double tr = ctl->tr0[sl];
-        for (int pp = p + 1; pp < count; ++pp) tr += ctl->coef[pp] * ctl->gram[ring_slot(head, pp, m)][sl];
-        ctl->coef[p] = ctl->zeta[p] - tr / ctl->rho[sl];
+        for (int a = 0; a < MP1; ++a)
+            if (a <= m) hs.tr0[a] = dots[a];
+        coef_recursion(hs, m);
     }
+    __syncthreads();
+    for (int p = threadIdx.x; p < count; p += VBS) ctl->coef[p] = hs.coef[p];
 }
 
 // d = r0 + sum_p c_p s_p; then gd = tr(grad_k^T d) -- with history and
@@ -505,7 +577,7 @@ template <typename R>
 __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, int set_nd) {
     Ctl *ctl = s.ctl;
     const int i = blockIdx.x * VBS + threadIdx.x;
-    double d4[4] = {0.0, 0.0, 0.0, 0.0};
+    R d4[4] = {R(0), R(0), R(0), R(0)};
     if (i < s.c.nf) {
         V4<R> dd = s.d[i];
         const int count = ctl->count, head = ctl->head, m = s.c.m;
@@ -516,16 +588,16 @@ __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, i
         }
         if (count > 0) s.d[i] = dd;
         const V4<R> g = s.gk[i], x = s.xk[i], yy = s.y[i];
-        const double mh = (double)s.mh2[i];
-        const double rx = (double)x.x - yy.x, ry = (double)x.y - yy.y, rz = (double)x.z - yy.z;
-        d4[0] = dotv(g, dd);
-        d4[1] = 0.5 * mh * (rx * rx + ry * ry + rz * rz);
-        d4[2] = mh * dot3d(rx, ry, rz, dd.x, dd.y, dd.z);
-        d4[3] = 0.5 * mh * dotv(dd, dd);
+        const R mh = s.mh2[i];
+        const R rx = x.x - yy.x, ry = x.y - yy.y, rz = x.z - yy.z;
+        d4[0] = dotr(g, dd);
+        d4[1] = R(0.5) * mh * (rx * rx + ry * ry + rz * rz);
+        d4[2] = mh * (rx * dd.x + ry * dd.y + rz * dd.z);
+        d4[3] = R(0.5) * mh * dotr(dd, dd);
     }
-    block_sum<VBS, 4>(d4);
-    if (!publish_and_arrive<4>(d4, s.part_v, gridDim.x, &ctl->ticket[TK_VEC])) return;
     double tot[4];
+    block_sum_r<VBS, 4, R>(d4, tot);
+    if (!publish_and_arrive<4>(tot, s.part_v, gridDim.x, &ctl->ticket[TK_VEC])) return;
     sum_partials<VBS, 4>(s.part_v, gridDim.x, gridDim.x, tot, &ctl->ticket[TK_VEC]);
     if (threadIdx.x != 0) return;
     ctl->gd = tot[0];
@@ -581,13 +653,26 @@ __global__ void __launch_bounds__(VBS) k_hist_row(DevSim<R> s, int a) {
     block_sum<VBS, NB>(dots);
     if (!publish_and_arrive<NB>(dots, s.part_g, gridDim.x, &ctl->ticket[TK_GATHER])) return;
     sum_partials<VBS, NB>(s.part_g, gridDim.x, gridDim.x, dots, &ctl->ticket[TK_GATHER]);
-    if (threadIdx.x != 0) return;
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int b = 0; b < NB - 1; ++b)
-        if (b < count) ctl->gram[a][b] = dots[b];
-    ctl->rho[a] = ctl->gram[a][a];
-    ctl->sg[a] = dots[NB - 1];
-    if (a == count - 1) zeta_recursion(ctl, s.c.m);
+        for (int b = 0; b < NB - 1; ++b) {
+            if (b < count) ctl->gram[a][b] = dots[b];
+            if (b == a) ctl->rho[a] = dots[b];
+        }
+        ctl->sg[a] = dots[NB - 1];
+    }
+    if (a != count - 1) return;
+    // all rows are in place: the first loop on scalars
+    __threadfence();
+    __syncthreads();
+    __shared__ HistSmem hs;
+    hist_load(ctl, hs, s.c.m);
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < count; ++b) hs.sg[b] = ctl->sg[b];
+        zeta_recursion(hs, s.c.m);
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < count; p += VBS) ctl->zeta[p] = hs.zeta[p];
 }
 
 inline int nblk(int n) { return (n + VBS - 1) / VBS; }

@@ -2,6 +2,14 @@
 // partial per block; the last block to arrive (an arrival ticket, the only
 // atomic used) sums the partials in a fixed order, so results do not depend
 // on block scheduling.
+//
+// GB300 issues float64 arithmetic at a small fraction of its float32 rate, so
+// sums that must be float64-accurate (energies, rho = s^T t) accumulate in
+// float-float pairs inside warps and blocks -- a float hi plus a float lo
+// carrying its rounding error (Knuth's TwoSum; exact products by FMA, Dekker)
+// -- and become doubles only for the per-block partials.  Sums that may be
+// float32 (the other inner products of Alg. 2) use float32 up to the block
+// partial.  The final sum over the partials is float64, one warp per value.
 #pragma once
 
 #include "common.cuh"
@@ -21,7 +29,62 @@ __device__ __forceinline__ R warp_sum_r(R v) {
     return v;
 }
 
-// Sum of NV doubles over the block; the result is valid in thread 0.
+// ---- float-float accumulators
+
+struct FF {
+    float hi, lo;
+};
+
+// s + e = a + b exactly (Knuth's TwoSum, no ordering condition).
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return FF{s, e};
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const FF s = ff_two_sum(a.hi, b.hi);
+    const float e = s.lo + (a.lo + b.lo);
+    const float h = s.hi + e;
+    return FF{h, e - (h - s.hi)};
+}
+
+// a * b exactly as hi + lo (the FMA computes the rounding error of the product).
+__device__ __forceinline__ FF ff_prod(float a, float b) {
+    const float p = a * b;
+    return FF{p, fmaf(a, b, -p)};
+}
+
+__device__ __forceinline__ double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+
+// Accumulator of float64-accurate sums in working precision R: float-float
+// for float, double for double.
+template <typename R> struct ExactAcc;
+template <> struct ExactAcc<float> {
+    using T = FF;
+    __device__ static T zero() { return FF{0.f, 0.f}; }
+    __device__ static T add(T a, float x) { return ff_add(a, FF{x, 0.f}); }
+    __device__ static T add_prod(T a, float x, float y) { return ff_add(a, ff_prod(x, y)); }
+    __device__ static T combine(T a, T b) { return ff_add(a, b); }
+    __device__ static T shfl_xor(T a, int o) {
+        return FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+    }
+    __device__ static double to_double(T a) { return ff_to_double(a); }
+};
+template <> struct ExactAcc<double> {
+    using T = double;
+    __device__ static T zero() { return 0.0; }
+    __device__ static T add(T a, double x) { return a + x; }
+    __device__ static T add_prod(T a, double x, double y) { return fma(x, y, a); }
+    __device__ static T combine(T a, T b) { return a + b; }
+    __device__ static T shfl_xor(T a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+    __device__ static double to_double(T a) { return a; }
+};
+
+// ---- block sums (results valid in thread 0)
+
+// NV float64 values, float64 throughout.
 template <int BS, int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     __shared__ double sh[NV][BS / 32];
@@ -42,26 +105,52 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     __syncthreads();
 }
 
-// Sum of NV values over the block, first within each warp in the working
-// precision R, then across the warps in float64; the result (float64) is
-// valid in thread 0.  Used for the two-loop's inner products, whose terms are
-// R-precision products anyway; with R = double it equals block_sum.
+// NV float64-accurate sums accumulated in ExactAcc<R>.
 template <int BS, int NV, typename R>
-__device__ __forceinline__ void block_sum_mixed(const R (&v)[NV], double (&out)[NV]) {
-    __shared__ double sh[NV][BS / 32];
+__device__ __forceinline__ void block_sum_exact(typename ExactAcc<R>::T (&v)[NV], double (&out)[NV]) {
+    using A = ExactAcc<R>;
+    using T = typename A::T;
+    __shared__ T sh[NV][BS / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        const R t = warp_sum_r(v[k]);
-        if (lane == 0) sh[k][warp] = (double)t;
+        T t = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t = A::combine(t, A::shfl_xor(t, o));
+        if (lane == 0) sh[k][warp] = t;
     }
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) out[k] = warp_sum(lane < BS / 32 ? sh[k][lane] : 0.0);
+        for (int k = 0; k < NV; ++k) {
+            T t = lane < BS / 32 ? sh[k][lane] : A::zero();
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t = A::combine(t, A::shfl_xor(t, o));
+            out[k] = A::to_double(t);
+        }
     }
     __syncthreads();
 }
+
+// NV sums in working precision R up to the block partial (R = double: float64).
+template <int BS, int NV, typename R>
+__device__ __forceinline__ void block_sum_r(const R (&v)[NV], double (&out)[NV]) {
+    __shared__ R sh[NV][BS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const R t = warp_sum_r(v[k]);
+        if (lane == 0) sh[k][warp] = t;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = (double)warp_sum_r(lane < BS / 32 ? sh[k][lane] : R(0));
+    }
+    __syncthreads();
+}
+
+// ---- grid level
 
 // Thread 0 publishes the block's partials (part[k * stride + blockIdx.x]) and
 // takes an arrival ticket.  Returns true in every thread of the last block.
@@ -80,20 +169,27 @@ __device__ __forceinline__ bool publish_and_arrive(const double (&v)[NV], double
     return last;
 }
 
-// In the last block: fixed-order sums of NV partial arrays of length n.
-// Result valid in thread 0; thread 0 also re-arms the ticket.
+// In the last block: fixed-order float64 sums of NV partial arrays of length
+// n, one warp per value.  Result valid in thread 0; thread 0 also re-arms the
+// ticket.
 template <int BS, int NV>
 __device__ __forceinline__ void sum_partials(const double *part, int stride, int n, double (&out)[NV],
                                              unsigned int *ticket) {
+    __shared__ double sh[NV];
     __threadfence();
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = warp; k < NV; k += BS / 32) {
         double acc = 0.0;
-        for (int i = threadIdx.x; i < n; i += BS) acc += __ldcg(part + k * stride + i);
-        out[k] = acc;
+        for (int i = lane; i < n; i += 32) acc += __ldcg(part + k * stride + i);
+        acc = warp_sum(acc);
+        if (lane == 0) sh[k] = acc;
     }
-    block_sum<BS, NV>(out);
-    if (threadIdx.x == 0) *ticket = 0u;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = sh[k];
+        *ticket = 0u;
+    }
 }
 
 }  // namespace hqn
