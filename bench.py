@@ -245,8 +245,11 @@ def run_ours(args, rank, world, dist):
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                 "algorithmic_bytes_per_launch": bytes_launch}
     else:
-        bytes_launch = T * 56 + n * 16 + T * 48
-        achieved = bytes_launch / (stage_ms[dominant] * 1e-3) / 1e9
+        # the tet pass (energy + corner gradients): idx 16 + Dm^-1 36 + V 4 B
+        # and 4 corner gradients of 16 B per tet, x_k and d of every vertex
+        dominant = "tet"
+        bytes_launch = T * (56 + 64) + n * 32
+        achieved = bytes_launch / (stage_ms["tet"] * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                 "algorithmic_bytes_per_launch": bytes_launch}
@@ -284,12 +287,61 @@ def run_ours(args, rank, world, dist):
     per_iter = 1 + 2 * info["n_levels"] + (1 if m > 0 else 0) + 1 + 2
     launches = args.steps * 5 + stats["iters_total"] * per_iter + stats["ls_passes_total"]
     line["gpu_launches"] = launches
+    if not args.no_batch:
+        line["batched"] = run_batched(args, stream)
     if rank == 0 and not args.no_cpu_baseline:
         v, te, desc, cores = oracle_sample(w, budget_s=args.cpu_budget, counts=(trials, iters))
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": desc, "tet_grad_evals_per_s": te}
     sim.close()
     return line
+
+
+def run_batched(args, stream):
+    """The batched form: 512 independent simulations (lattices of random
+    dims 4-24 per axis, Neo-Hookean / StVK / spline materials, E log-uniform
+    1e4-1e6, nu U[0.3, 0.48]) advanced together, one launch per kernel stage,
+    one CUDA graph per step; FP32-mixed with the FP64-plain batch beside it."""
+    import torch
+
+    from paper_1604_07378_gb300 import hqn
+    from paper_1604_07378_gb300 import workloads as W
+
+    ws = W.batch_512()
+    T = sum(w.n_tets for w in ws)
+    out = {"workload": "batch512_lattices_4to24", "sims": len(ws), "tets_total": T,
+           "vertices_total": sum(w.n_verts for w in ws)}
+    for prec, key, steps in ((hqn.FP32_MIXED, "fp32_mixed", args.batch_steps),
+                             (hqn.FP64_PLAIN, "fp64_plain", max(2, args.batch_steps // 4))):
+        t0 = time.perf_counter()
+        b = hqn.Batch(ws, precision=prec, stream=stream.cuda_stream)
+        create_s = time.perf_counter() - t0
+        for i, w in enumerate(ws):
+            b.set_state(i, w.q_cur, w.q_prev)
+        b.step(args.warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        rc, tot = b.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        info = b.info()
+        solve_ms = b.time_stage(hqn.STAGE_SOLVE, 10)
+        b.close()
+        # tet evaluations per batch step: every simulation's start-of-step pass
+        # and line-search passes (ls_passes_total is summed over the batch;
+        # the simulations' sizes weight them equally here)
+        evals = T * (tot["ls_passes_total"] / (steps * len(ws)) + 1)
+        solve_bytes = 2 * info["factor_nnz"] * (4 if prec == hqn.FP32_MIXED else 8)
+        peaks, _ = _peaks()
+        out[key] = {"batch_steps_per_s": 1e3 / ms, "sim_steps_per_s": len(ws) * 1e3 / ms, "ms_per_step": ms,
+                    "tet_grad_evals_per_s": evals * 1e3 / ms, "steps": steps, "status": rc,
+                    "ls_trials_per_iter": tot["trials_total"] / max(tot["iters_total"], 1),
+                    "create_s": create_s, "device_bytes": info["device_bytes"],
+                    "solve_ms": solve_ms, "solve_hbm_frac_of_measured": solve_bytes / (solve_ms * 1e-3) / 1e9
+                    / peaks["hbm_gbs"]}
+    return out
 
 
 def run_reference(args, rank):
@@ -334,6 +386,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched 512-simulation measurement")
+    ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--no-graph", action="store_true",
                     help="issue the step's kernels one by one (same kernels; for profilers that "
                          "cannot see inside graphs with conditional nodes)")

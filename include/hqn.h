@@ -101,13 +101,18 @@ typedef struct {
     int32_t use_graph;    /* 1 = run each step as one CUDA graph with conditional
                              (while / if) nodes for the iteration and line-search
                              loops; 0 = host-driven launches (same kernels)        */
-    int32_t tet_block;    /* threads per block of the tet kernel: 64, 128 or 256
-                             (0 = default 128)                                     */
+    int32_t tet_block;    /* threads per block of the tet kernels: 0 or 128 (other
+                             values are rejected with HQN_ERR_UNSUPPORTED)         */
     int32_t ls_batch;     /* line search: the first trial (alpha = 1) is one tet pass
                              fused with the gradient; after a rejection each pass
                              tests ls_batch step lengths (1, 2, 4, 8 or 16; 0 =
                              default 8).  The accepted alpha is the one Alg. 1's
                              sequential backtracking would accept                  */
+    int32_t dyn_sweeps;   /* triangular sweeps: 0 = one launch per tree level,
+                             chained by programmatic dependent launch (default);
+                             1 = dependency-driven (one persistent launch per
+                             sweep; a work item waits only for the supernodes it
+                             reads).  Same arithmetic, bit-identical results      */
 } hqn_params;
 
 #define HQN_MAX_HISTORY 16
@@ -137,8 +142,10 @@ typedef struct {
     int32_t precision;          /* hqn_precision in use                               */
     int32_t graph_mode;         /* 1 if steps run as a CUDA graph                     */
     int64_t n_update_entries;   /* entries of the forward-sweep update vectors        */
-    int32_t chained_sweeps;     /* 1 if the sweep levels use programmatic dependent
+    int32_t chained_sweeps;     /* 1 if the per-level sweeps use programmatic dependent
                                    launch (a level starts while the previous finishes) */
+    int32_t sweep_schedule;     /* 1 = dependency-driven sweeps, 0 = one launch per level */
+    int32_t n_sims;             /* simulations in the handle (1 for sim_create)        */
 } hqn_info;
 
 typedef struct sim_handle sim_handle;
@@ -158,6 +165,35 @@ void hqn_default_params(hqn_params *p);
  * HQN_ERR_NOT_SPD, HQN_ERR_CUDA, HQN_ERR_NO_MEMORY.  *out is NULL on error. */
 int sim_create(const hqn_mesh *mesh, const hqn_material *material,
                const hqn_params *params, void *stream, sim_handle **out);
+
+/* ---- batches -------------------------------------------------------------
+ * The paper simulates one object at a time; a batch advances `count`
+ * independent simulations (each its own mesh, material, factor and state; the
+ * parameters are shared) in lockstep, every kernel stage of a step launched
+ * once for the whole batch and the step captured as one CUDA graph.  Each
+ * simulation takes exactly the iterations and line-search trials it would
+ * take alone (a finished simulation idles while others continue), so its
+ * results equal those of a handle made by sim_create for it alone.
+ * meshes and materials are arrays of `count`.  Errors as sim_create; a
+ * failing simulation is named in hqn_last_error().
+ * For a batch handle, sim_set_state, sim_get_state, sim_energy_grad,
+ * sim_solve_A0 and sim_direction act on simulation 0; sim_step advances all
+ * simulations and its stats carry simulation 0's per-iteration record with
+ * trials_total, iters_total and ls_passes_total summed over the batch and
+ * status the worst over the batch. */
+int sim_batch_create(int32_t count, const hqn_mesh *meshes, const hqn_material *materials,
+                     const hqn_params *params, void *stream, sim_handle **out);
+
+/* Simulations in the handle (0 for NULL). */
+int32_t sim_batch_count(const sim_handle *sim);
+
+/* sim_set_state / sim_get_state for simulation `index` of a batch. */
+int sim_batch_set_state(sim_handle *sim, int32_t index, const double *q_cur, const double *q_prev);
+int sim_batch_get_state(sim_handle *sim, int32_t index, double *q_cur, double *q_prev);
+
+/* The step record of simulation `index` (its own totals since the last
+ * sim_step call began).  Synchronises the stream. */
+int sim_batch_get_stats(sim_handle *sim, int32_t index, hqn_step_stats *stats);
 
 /* Sets the state (q_l, q_{l-1}); each n_verts x 3 host doubles.  Clamped
  * vertices are held at their q_l.  q_prev may be NULL (= q_cur, zero velocity). */

@@ -66,7 +66,7 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
                      os.path.join(CSRC, f), "-o", o])
     for f in CU_SOURCES:
         o = os.path.join(objdir, f + ".o")
-        jobs.append([nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+        jobs.append([nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp",
                      "-Xptxas", "-v" if verbose else "-O3", "-I" + INCLUDE, "-c",
                      os.path.join(CSRC, f), "-o", o])
     with ThreadPoolExecutor(max_workers=len(jobs)) as ex:

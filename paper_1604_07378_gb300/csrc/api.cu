@@ -3,13 +3,19 @@
 // iterations with backtracking Armijo line search) driving the L-BFGS
 // direction of Alg. 2 with the prefactored A0 = M/h^2 + L.
 //
+// A handle holds a batch of independent simulations (sim_create makes a
+// batch of one).  Their meshes, factors and states sit back to back in device
+// memory, and every kernel stage runs once over the whole batch.
+//
 // A step runs entirely on the device.  In graph mode it is one CUDA graph:
 // a while node over the iterations whose body holds the two-loop recursion,
 // the triangular sweeps, an if node for the (rare) non-descent reset and a
-// while node over the line-search trials.  Every decision is taken by a
-// kernel that sets the conditional handles, so the host launches one graph
-// per step and never waits inside it.  Eager mode issues the same kernels
-// and reads the control block between them (debugging, graph-less drivers).
+// while node over the line-search passes.  Each simulation's decisions are
+// taken by kernels on the device, and the last simulation to decide sets the
+// conditional handles, so the host launches one graph per step and never
+// waits inside it.  Eager mode issues the same kernels and reads the control
+// blocks between them (debugging, graph-less drivers).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -58,9 +64,11 @@ void spline_coeffs(const MaterialHost &m, int f, MatDev<R> &d) {
 
 struct SimBase {
     virtual ~SimBase() {}
-    virtual int set_state(const double *qc, const double *qp) = 0;
-    virtual int get_state(double *qc, double *qp) = 0;
+    virtual int count() const = 0;
+    virtual int set_state(int idx, const double *qc, const double *qp) = 0;
+    virtual int get_state(int idx, double *qc, double *qp) = 0;
     virtual int step(int nsteps, hqn_step_stats *stats) = 0;
+    virtual int stats_of(int idx, hqn_step_stats *stats) = 0;
     virtual int energy_grad(const double *x, const double *y, double *g, double *grad) = 0;
     virtual int solve_A0(const double *q, double *r) = 0;
     virtual int direction(const double *grad, int np, const double *s, const double *t, double *d) = 0;
@@ -70,20 +78,27 @@ struct SimBase {
 
 template <typename R>
 struct Sim final : SimBase {
-    Setup S;
+    std::vector<Setup> S;  // one set-up per simulation
+    int ns = 0;            // simulations in the batch
     hqn_params prm{};
     cudaStream_t st = nullptr;
     DevSim<R> ds{};
     DevSolve<R> dsol{};
+    std::vector<SimDesc<R>> hdesc;
     std::vector<void *> allocs;
     int64_t dev_bytes = 0;
-    Ctl *h_ctl = nullptr;  // pinned
+    Ctl *d_ctl = nullptr;  // ns control blocks (device)
+    Ctl *h_ctl = nullptr;  // ns control blocks (pinned host copy)
+    std::vector<int> fwd_ptr, fwd_ld, fwd_q, bwd_start, bwd_cnt, bwd_ld, bwd_q;  // per tree level
     std::vector<V4<R>> hbuf;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     bool graph_mode = false;
     std::vector<cudaStream_t> cap_streams;
     cudaStream_t own_stream = nullptr;
+    int64_t n_tot = 0, T_tot = 0, nf_tot = 0, sn_tot = 0, q_entries = 0, nnz_tot = 0, upd_tot = 0;
+    int n_levels = 0;
+    double setup_seconds = 0.0;
 
     ~Sim() override {
         if (st) cudaStreamSynchronize(st);
@@ -94,6 +109,8 @@ struct Sim final : SimBase {
         if (h_ctl) cudaFreeHost(h_ctl);
         if (own_stream) cudaStreamDestroy(own_stream);
     }
+
+    int count() const override { return ns; }
 
     template <typename X>
     int alloc(X *&p, size_t count) {
@@ -121,147 +138,138 @@ struct Sim final : SimBase {
     int init(const hqn_params &p, cudaStream_t stream) {
         prm = p;
         st = stream;
-        const int n = S.n, T = S.T, nf = S.n_free, m = p.history_m;
-        if (!solve_smem_limit_ok<R>(S.max_ld))
+        ns = (int)S.size();
+        const int m = p.history_m;
+        int max_ld = 0;
+        for (const Setup &s : S) max_ld = std::max(max_ld, s.max_ld);
+        if (!solve_smem_limit_ok<R>(max_ld))
             return fail(HQN_ERR_UNSUPPORTED, "a separator is too large for the sweeps' shared memory");
         CK(solve_prepare<R>());
         if (st == nullptr) {  // the legacy default stream cannot be captured: use an own stream
             CK(cudaStreamCreateWithFlags(&own_stream, cudaStreamNonBlocking));
             st = own_stream;
         }
-        StepConst<R> &c = ds.c;
-        c.n = n; c.nf = nf; c.T = T; c.m = m; c.iters = p.iters; c.ls_max = p.ls_max;
-        c.ls_batch = (p.ls_batch == 1 || p.ls_batch == 2 || p.ls_batch == 4 || p.ls_batch == 16) ? p.ls_batch : 8;
-        c.h2 = (R)(p.h * p.h);
-        c.gx = (R)(p.h * p.h * p.gravity[0]);
-        c.gy = (R)(p.h * p.h * p.gravity[1]);
-        c.gz = (R)(p.h * p.h * p.gravity[2]);
-        c.gamma = p.gamma;
-        c.backtrack = p.backtrack;
-        ds.tet_bs = (p.tet_block == 64 || p.tet_block == 256) ? p.tet_block : 128;
-        // material
-        MatDev<R> &M = ds.mat;
-        std::memset(&M, 0, sizeof(M));
-        M.kind = S.mat.kind;
-        M.mu = (R)S.mat.mu; M.lam = (R)S.mat.lam;
-        M.J0 = (R)S.mat.J0; M.c0 = (R)S.mat.c0; M.c1 = (R)S.mat.c1; M.c2 = (R)S.mat.c2;
-        if (S.mat.kind == HQN_SPLINE_VL)
-            for (int f = 0; f < 3; ++f) spline_coeffs(S.mat, f, M);
         int rc;
-        // mesh data
-        std::vector<int4> tets(T);
-        for (int t = 0; t < T; ++t) tets[t] = make_int4(S.tets[4 * t], S.tets[4 * t + 1], S.tets[4 * t + 2], S.tets[4 * t + 3]);
-        const int4 *dt;
-        if ((rc = upload(dt, tets.data(), T))) return rc;
-        ds.tets = dt;
-        std::vector<R> dm((size_t)9 * T);
-        for (int t = 0; t < T; ++t)
-            for (int e = 0; e < 9; ++e) dm[(size_t)e * T + t] = (R)S.dminv[(size_t)9 * t + e];
-        const R *p_dm;
-        if ((rc = upload(p_dm, dm.data(), dm.size()))) return rc;
-        ds.dminv = p_dm;
-        std::vector<R> vol(T), mh2(n);
-        for (int t = 0; t < T; ++t) vol[t] = (R)S.vol[t];
-        for (int i = 0; i < n; ++i) mh2[i] = (R)(S.mass[i] / (p.h * p.h));
-        const R *p_vol, *p_mh2;
-        if ((rc = upload(p_vol, vol.data(), T))) return rc;
-        if ((rc = upload(p_mh2, mh2.data(), n))) return rc;
-        ds.vol = p_vol; ds.mh2 = p_mh2;
-        std::vector<int> slot(S.vt_slot.size());
-        for (size_t k = 0; k < slot.size(); ++k) {
-            const int sv = S.vt_slot[k];
-            slot[k] = (sv & 3) * T + (sv >> 2);
+        // ---- batch layout: offsets of every simulation
+        std::vector<int> v0(ns), t0(ns), vb0(ns), tb0(ns), u0(ns), sn0(ns);
+        std::vector<int64_t> qf0(ns), qb0(ns);
+        int nvb = 0, ntb = 0;
+        n_tot = T_tot = nf_tot = sn_tot = q_entries = nnz_tot = upd_tot = 0;
+        int64_t qf_tot = 0, qb_tot = 0;
+        n_levels = 0;
+        setup_seconds = 0.0;
+        for (int k = 0; k < ns; ++k) {
+            const Setup &s = S[k];
+            v0[k] = (int)n_tot; t0[k] = (int)T_tot; vb0[k] = nvb; tb0[k] = ntb;
+            u0[k] = (int)upd_tot; sn0[k] = (int)sn_tot; qf0[k] = qf_tot; qb0[k] = qb_tot;
+            n_tot += s.n; T_tot += s.T; nf_tot += s.n_free; sn_tot += (int64_t)s.sn.size();
+            upd_tot += s.n_upd; qf_tot += s.qf_total; qb_tot += s.qb_total;
+            q_entries += (int64_t)s.Q.size(); nnz_tot += s.factor_nnz;
+            nvb += (s.n + VBS - 1) / VBS;
+            ntb += (s.T + TBS - 1) / TBS;
+            n_levels = std::max(n_levels, s.n_levels);
+            setup_seconds += s.setup_seconds;
         }
-        const int *p_ptr, *p_slot;
-        if ((rc = upload(p_ptr, S.vt_ptr.data(), S.vt_ptr.size()))) return rc;
-        if ((rc = upload(p_slot, slot.data(), slot.size()))) return rc;
-        ds.vt_ptr = p_ptr; ds.vt_slot = p_slot;
-        // vectors
+        if (n_tot > 0x7fffffffLL / 4 || T_tot > 0x7fffffffLL / 4 || upd_tot > 0x7fffffffLL)
+            return fail(HQN_ERR_UNSUPPORTED, "the batch is too large for 32-bit indices");
+        const int n = (int)n_tot, T = (int)T_tot;
+        ds.nsims = ns; ds.m = m; ds.nvb = nvb; ds.ntb = ntb; ds.Tn = T;
+        ds.ls_batch = (p.ls_batch == 1 || p.ls_batch == 2 || p.ls_batch == 4 || p.ls_batch == 16) ? p.ls_batch : 8;
+        // ---- mesh data
+        {
+            std::vector<int4> tets(T);
+            std::vector<R> dm((size_t)9 * T), vol(T), mh2(n);
+            std::vector<int> vptr(n + 1, 0), slot;
+            slot.reserve((size_t)4 * T);
+            for (int k = 0; k < ns; ++k) {
+                const Setup &s = S[k];
+                for (int t = 0; t < s.T; ++t) {
+                    const int *tv = &s.tets[4 * (size_t)t];
+                    tets[t0[k] + t] = make_int4(v0[k] + tv[0], v0[k] + tv[1], v0[k] + tv[2], v0[k] + tv[3]);
+                    for (int e = 0; e < 9; ++e) dm[(size_t)e * T + t0[k] + t] = (R)s.dminv[(size_t)9 * t + e];
+                    vol[t0[k] + t] = (R)s.vol[t];
+                }
+                for (int i = 0; i < s.n; ++i) {
+                    mh2[v0[k] + i] = (R)(s.mass[i] / (p.h * p.h));
+                    for (int e = s.vt_ptr[i]; e < s.vt_ptr[i + 1]; ++e) {
+                        const int sv = s.vt_slot[e];
+                        slot.push_back((sv & 3) * T + t0[k] + (sv >> 2));
+                    }
+                    vptr[v0[k] + i + 1] = (int)slot.size();
+                }
+            }
+            const int4 *p_t;
+            const R *p_dm, *p_vol, *p_mh2;
+            const int *p_ptr, *p_slot;
+            if ((rc = upload(p_t, tets.data(), tets.size()))) return rc;
+            if ((rc = upload(p_dm, dm.data(), dm.size()))) return rc;
+            if ((rc = upload(p_vol, vol.data(), vol.size()))) return rc;
+            if ((rc = upload(p_mh2, mh2.data(), mh2.size()))) return rc;
+            if ((rc = upload(p_ptr, vptr.data(), vptr.size()))) return rc;
+            if ((rc = upload(p_slot, slot.data(), slot.size()))) return rc;
+            ds.tets = p_t; ds.dminv = p_dm; ds.vol = p_vol; ds.mh2 = p_mh2; ds.vt_ptr = p_ptr; ds.vt_slot = p_slot;
+        }
+        // ---- vectors, rings, partials, control blocks
         V4<R> **vecs[] = {&ds.u_cur, &ds.u_prev, &ds.y, &ds.xk, &ds.xt, &ds.gk, &ds.d, &ds.q, &ds.z};
         for (auto v : vecs)
             if ((rc = alloc(*v, n))) return rc;
-        const size_t ring = (size_t)(m + 1) * n;
-        if ((rc = alloc(ds.S, m > 0 ? ring : 1))) return rc;
-        if ((rc = alloc(ds.Tt, m > 0 ? ring : 1))) return rc;
+        const size_t ring = m > 0 ? (size_t)(m + 1) * n : 1;
+        if ((rc = alloc(ds.S, ring))) return rc;
+        if ((rc = alloc(ds.Tt, ring))) return rc;
         if ((rc = alloc(ds.corner, (size_t)4 * T))) return rc;
-        const int nbv = (n + VBS - 1) / VBS, nbf = (nf + VBS - 1) / VBS, nbt = (T + 63) / 64;
-        if ((rc = alloc(ds.part_in, nbv))) return rc;
-        if ((rc = alloc(ds.part_el, nbt))) return rc;
+        if ((rc = alloc(ds.part_in, nvb))) return rc;
+        if ((rc = alloc(ds.part_el, ntb))) return rc;
         // per-block partials: up to 3 + 3 (m + 1) sums (gather with a history
-        // push), m + 2 (caller-given history rows), m + 1 or 4 (direction)
-        if ((rc = alloc(ds.part_g, (size_t)(3 + 3 * (HQN_MAX_HISTORY + 1)) * nbf))) return rc;
-        if ((rc = alloc(ds.part_v, (size_t)(HQN_MAX_HISTORY + 1) * nbf))) return rc;
-        if ((rc = alloc(ds.part_ls, (size_t)16 * ((T + 127) / 128)))) return rc;
-        if ((rc = alloc(ds.ctl, 1))) return rc;
-        CK(cudaMallocHost(&h_ctl, sizeof(Ctl)));
-        // solve operators
-        dsol.nf = nf;
-        dsol.n_levels = S.n_levels;
-        // the two packed copies of every Q_s (layout.hpp): forward row-major,
-        // backward transposed
-        std::vector<R> QF((size_t)S.qf_total, R(0)), QB((size_t)S.qb_total, R(0));
-        for (const SupernodeHost &sn : S.sn) {
-            const double *Qs = S.Q.data() + sn.qoff;
-            const int nc = sn.ncol, rows = sn.ncol + sn.nrow;
-            for (int i = 0; i < rows; ++i) {
-                R *dst = QF.data() + sn.qf + fwd_row_off(i, nc, sn.ldc);
-                const int len = std::min(fwd_row_len(i, nc, sn.ldc), nc);
-                for (int j = 0; j < len; ++j) dst[j] = (R)Qs[(size_t)i * nc + j];
-            }
-            for (int j = 0; j < nc; ++j) {
-                R *dst = QB.data() + sn.qb + bwd_row_off(j, sn.ldr);
-                const int i0 = bwd_row_start(j);
-                for (int i = i0; i < rows; ++i) dst[i - i0] = (R)Qs[(size_t)i * nc + j];
-            }
+        // push), m + 2 (caller-given history rows), m + 1 or 4 (direction),
+        // 16 (line-search pass)
+        if ((rc = alloc(ds.part_g, (size_t)(3 + 3 * (HQN_MAX_HISTORY + 1)) * nvb))) return rc;
+        if ((rc = alloc(ds.part_v, (size_t)(HQN_MAX_HISTORY + 1) * nvb))) return rc;
+        if ((rc = alloc(ds.part_ls, (size_t)16 * ntb))) return rc;
+        if ((rc = alloc(ds.batch_ticket, 4))) return rc;
+        if ((rc = alloc(d_ctl, ns))) return rc;
+        CK(cudaMallocHost(&h_ctl, sizeof(Ctl) * (size_t)ns));
+        // ---- descriptors and block tables
+        hdesc.assign(ns, SimDesc<R>{});
+        std::vector<int> vblk(nvb), tblk(ntb);
+        for (int k = 0; k < ns; ++k) {
+            const Setup &s = S[k];
+            SimDesc<R> &D = hdesc[k];
+            std::memset(&D, 0, sizeof(D));
+            StepConst<R> &c = D.c;
+            c.n = s.n; c.nf = s.n_free; c.T = s.T; c.m = m; c.iters = p.iters; c.ls_max = p.ls_max;
+            c.ls_batch = ds.ls_batch;
+            c.h2 = (R)(p.h * p.h);
+            c.gx = (R)(p.h * p.h * p.gravity[0]);
+            c.gy = (R)(p.h * p.h * p.gravity[1]);
+            c.gz = (R)(p.h * p.h * p.gravity[2]);
+            c.gamma = p.gamma;
+            c.backtrack = p.backtrack;
+            MatDev<R> &M = D.mat;
+            M.kind = s.mat.kind;
+            M.mu = (R)s.mat.mu; M.lam = (R)s.mat.lam;
+            M.J0 = (R)s.mat.J0; M.c0 = (R)s.mat.c0; M.c1 = (R)s.mat.c1; M.c2 = (R)s.mat.c2;
+            if (s.mat.kind == HQN_SPLINE_VL)
+                for (int f = 0; f < 3; ++f) spline_coeffs(s.mat, f, M);
+            D.v0 = v0[k]; D.t0 = t0[k];
+            D.vb0 = vb0[k]; D.nvb = (s.n + VBS - 1) / VBS;
+            D.tb0 = tb0[k]; D.ntb = (s.T + TBS - 1) / TBS;
+            D.ring0 = (long long)(m + 1) * v0[k];
+            D.ctl = d_ctl + k;
+            for (int b = 0; b < D.nvb; ++b) vblk[D.vb0 + b] = k;
+            for (int b = 0; b < D.ntb; ++b) tblk[D.tb0 + b] = k;
         }
-        const R *p_QF, *p_QB;
-        if ((rc = upload(p_QF, QF.data(), QF.size()))) return rc;
-        if ((rc = upload(p_QB, QB.data(), QB.size()))) return rc;
-        std::vector<R>().swap(QF);
-        std::vector<R>().swap(QB);
-        dsol.QF = p_QF;
-        dsol.QB = p_QB;
-        const int *p_rows;
-        const int2 *p_fg2, *p_ug2;
-        if ((rc = upload(p_rows, S.rows.data(), S.rows.size()))) return rc;
-        if ((rc = upload(p_fg2, reinterpret_cast<const int2 *>(S.fg2.data()), S.fg2.size() / 2))) return rc;
-        if ((rc = upload(p_ug2, reinterpret_cast<const int2 *>(S.ug2.data()), S.ug2.size() / 2))) return rc;
-        dsol.rows = p_rows; dsol.fg2 = p_fg2; dsol.ug2 = p_ug2;
-        // work-item records (kernels.cuh): everything a block needs in one place
-        std::vector<int4> fi(3 * S.fwd_items.size()), bi(3 * S.bwd_items.size());
-        for (size_t k = 0; k < S.fwd_items.size(); ++k) {
-            const FwdItem &f = S.fwd_items[k];
-            const SupernodeHost &sn = S.sn[f.s];
-            const int64_t o0 = fwd_row_off(f.row0, sn.ncol, sn.ldc), o1 = fwd_row_off(f.row1, sn.ncol, sn.ldc);
-            const int64_t q0 = sn.qf + o0;
-            fi[3 * k] = make_int4((int)(q0 & 0xffffffffLL), (int)(q0 >> 32), (int)((o1 - o0) * sizeof(R)), f.G);
-            fi[3 * k + 1] = make_int4(sn.col, sn.ncol, sn.ldc, sn.uoff);
-            fi[3 * k + 2] = make_int4(f.row0, f.row1, fwd_row_len(f.row1 - 1, sn.ncol, sn.ldc), (int)o0);
+        {
+            const SimDesc<R> *p_desc;
+            const int *p_vb, *p_tb;
+            if ((rc = upload(p_desc, hdesc.data(), hdesc.size()))) return rc;
+            if ((rc = upload(p_vb, vblk.data(), vblk.size()))) return rc;
+            if ((rc = upload(p_tb, tblk.data(), tblk.size()))) return rc;
+            ds.desc = p_desc; ds.vblk_sim = p_vb; ds.tblk_sim = p_tb;
+            ds.desc0 = hdesc[0];
         }
-        for (size_t k = 0; k < S.bwd_items.size(); ++k) {
-            const BwdItem &b = S.bwd_items[k];
-            const SupernodeHost &sn = S.sn[b.s];
-            const int64_t o0 = bwd_row_off(b.col0, sn.ldr), o1 = bwd_row_off(b.col1, sn.ldr);
-            const int64_t q0 = sn.qb + o0;
-            bi[3 * k] = make_int4((int)(q0 & 0xffffffffLL), (int)(q0 >> 32), (int)((o1 - o0) * sizeof(R)), b.G);
-            bi[3 * k + 1] = make_int4(sn.col, sn.ncol, sn.nrow, sn.roff);
-            bi[3 * k + 2] = make_int4(b.col0, b.col1, sn.ldr, (int)o0);
-        }
-        const int4 *p_fi, *p_bi;
-        if ((rc = upload(p_fi, fi.data(), fi.size()))) return rc;
-        if ((rc = upload(p_bi, bi.data(), bi.size()))) return rc;
-        dsol.fwd_items = p_fi; dsol.bwd_items = p_bi;
-        dsol.fwd_lvl_ptr = S.fwd_lvl_ptr.data();
-        dsol.bwd_lvl_ptr = S.bwd_lvl_ptr.data();
-        dsol.fwd_lvl_ld = S.fwd_lvl_ld.data();
-        dsol.bwd_lvl_ld = S.bwd_lvl_ld.data();
-        dsol.fwd_lvl_q = S.fwd_lvl_q.data();
-        dsol.bwd_lvl_q = S.bwd_lvl_q.data();
-        dsol.err = &ds.ctl->solve_err;
-        if ((rc = alloc(dsol.u, (size_t)S.n_upd))) return rc;
+        if ((rc = init_solve(v0, u0, sn0, qf0, qb0, qf_tot, qb_tot))) return rc;
         hbuf.resize(n);
         CK(cudaStreamSynchronize(st));
-        // graph
         // Chain the sweep levels with programmatic dependent launch when the
         // device and the runtime accept it (one probe solve on zero vectors),
         // and keep it in the graph only if the graph builds with it.
@@ -288,6 +296,165 @@ struct Sim final : SimBase {
         return HQN_OK;
     }
 
+    // The solve operators of every simulation, back to back, with batch
+    // offsets baked into the work-item records (kernels.cuh) and the index
+    // tables.  Level l of the sweeps holds level l of every simulation's tree.
+    // Backward items are stored root level first (the dependency-driven queue
+    // order); bwd_start[l] is where tree level l begins.
+    int init_solve(const std::vector<int> &v0, const std::vector<int> &u0, const std::vector<int> &sn0,
+                   const std::vector<int64_t> &qf0, const std::vector<int64_t> &qb0, int64_t qf_tot, int64_t qb_tot) {
+        int rc;
+        const int L = n_levels;
+        dsol.n_levels = L;
+        // the two packed copies of every Q_s (layout.hpp): forward row-major,
+        // backward transposed
+        {
+            std::vector<R> QF((size_t)qf_tot, R(0)), QB((size_t)qb_tot, R(0));
+            for (int k = 0; k < ns; ++k)
+                for (const SupernodeHost &sn : S[k].sn) {
+                    const double *Qs = S[k].Q.data() + sn.qoff;
+                    const int nc = sn.ncol, rows = sn.ncol + sn.nrow;
+                    for (int i = 0; i < rows; ++i) {
+                        R *dst = QF.data() + qf0[k] + sn.qf + fwd_row_off(i, nc, sn.ldc);
+                        const int len = std::min(fwd_row_len(i, nc, sn.ldc), nc);
+                        for (int j = 0; j < len; ++j) dst[j] = (R)Qs[(size_t)i * nc + j];
+                    }
+                    for (int j = 0; j < nc; ++j) {
+                        R *dst = QB.data() + qb0[k] + sn.qb + bwd_row_off(j, sn.ldr);
+                        const int i0 = bwd_row_start(j);
+                        for (int i = i0; i < rows; ++i) dst[i - i0] = (R)Qs[(size_t)i * nc + j];
+                    }
+                }
+            const R *p_QF, *p_QB;
+            if ((rc = upload(p_QF, QF.data(), QF.size()))) return rc;
+            if ((rc = upload(p_QB, QB.data(), QB.size()))) return rc;
+            dsol.QF = p_QF;
+            dsol.QB = p_QB;
+        }
+        // the double copies are no longer needed on the host
+        for (Setup &s : S) std::vector<double>().swap(s.Q);
+        {
+            std::vector<int> rows;
+            std::vector<int2> fg2, ug2;
+            for (int k = 0; k < ns; ++k) {
+                const Setup &s = S[k];
+                for (int r : s.rows) rows.push_back(v0[k] + r);
+                for (size_t e = 0; e < s.fg2.size(); e += 2)
+                    fg2.push_back(make_int2(s.fg2[e] >= 0 ? u0[k] + s.fg2[e] : -1,
+                                            s.fg2[e + 1] >= 0 ? u0[k] + s.fg2[e + 1] : -1));
+                for (size_t e = 0; e < s.ug2.size(); e += 2)
+                    ug2.push_back(make_int2(s.ug2[e] >= 0 ? u0[k] + s.ug2[e] : -1,
+                                            s.ug2[e + 1] >= 0 ? u0[k] + s.ug2[e + 1] : -1));
+            }
+            // fg2 is indexed by batch vertex (free vertices of each simulation
+            // come first in its range); pad each simulation to its n vertices
+            std::vector<int2> fgv((size_t)n_tot, make_int2(-1, -1));
+            size_t e = 0;
+            for (int k = 0; k < ns; ++k)
+                for (int j = 0; j < S[k].n_free; ++j) fgv[v0[k] + j] = fg2[e++];
+            const int *p_rows;
+            const int2 *p_fg2, *p_ug2;
+            if ((rc = upload(p_rows, rows.data(), rows.size()))) return rc;
+            if ((rc = upload(p_fg2, fgv.data(), fgv.size()))) return rc;
+            if ((rc = upload(p_ug2, ug2.data(), ug2.size()))) return rc;
+            dsol.rows = p_rows; dsol.fg2 = p_fg2; dsol.ug2 = p_ug2;
+        }
+        // work items by level, every simulation's items of a level together
+        std::vector<std::vector<int4>> frec(L), brec(L);
+        fwd_ld.assign(L, 0); fwd_q.assign(L, 0); bwd_ld.assign(L, 0); bwd_q.assign(L, 0);
+        std::vector<int> nit_f((size_t)sn_tot, 0), nit_b((size_t)sn_tot, 0);
+        for (int k = 0; k < ns; ++k) {
+            const Setup &s = S[k];
+            int roff0 = 0;
+            for (int kk = 0; kk < k; ++kk) roff0 += (int)S[kk].rows.size();
+            for (const SupernodeHost &sn : s.sn)
+                if (sn.children.size() > 2) return fail(HQN_ERR_UNSUPPORTED, "a supernode has more than two children");
+            for (int l = 0; l < s.n_levels; ++l) {
+                fwd_ld[l] = std::max(fwd_ld[l], s.fwd_lvl_ld[l]);
+                fwd_q[l] = std::max(fwd_q[l], s.fwd_lvl_q[l]);
+                bwd_ld[l] = std::max(bwd_ld[l], s.bwd_lvl_ld[l]);
+                bwd_q[l] = std::max(bwd_q[l], s.bwd_lvl_q[l]);
+                for (int e = s.fwd_lvl_ptr[l]; e < s.fwd_lvl_ptr[l + 1]; ++e) {
+                    const FwdItem &f = s.fwd_items[e];
+                    const SupernodeHost &sn = s.sn[f.s];
+                    const int64_t o0 = fwd_row_off(f.row0, sn.ncol, sn.ldc), o1 = fwd_row_off(f.row1, sn.ncol, sn.ldc);
+                    const int64_t q0 = qf0[k] + sn.qf + o0;
+                    auto &v = frec[l];
+                    v.push_back(make_int4((int)(q0 & 0xffffffffLL), (int)(q0 >> 32), (int)((o1 - o0) * sizeof(R)), f.G));
+                    v.push_back(make_int4(v0[k] + sn.col, sn.ncol, sn.ldc, u0[k] + sn.uoff));
+                    v.push_back(make_int4(f.row0, f.row1, fwd_row_len(f.row1 - 1, sn.ncol, sn.ldc), (int)o0));
+                    v.push_back(make_int4(sn.children.size() > 0 ? sn0[k] + sn.children[0] : -1,
+                                          sn.children.size() > 1 ? sn0[k] + sn.children[1] : -1, sn0[k] + f.s, 0));
+                    nit_f[sn0[k] + f.s]++;
+                }
+                for (int e = s.bwd_lvl_ptr[l]; e < s.bwd_lvl_ptr[l + 1]; ++e) {
+                    const BwdItem &b = s.bwd_items[e];
+                    const SupernodeHost &sn = s.sn[b.s];
+                    const int64_t o0 = bwd_row_off(b.col0, sn.ldr), o1 = bwd_row_off(b.col1, sn.ldr);
+                    const int64_t q0 = qb0[k] + sn.qb + o0;
+                    auto &v = brec[l];
+                    v.push_back(make_int4((int)(q0 & 0xffffffffLL), (int)(q0 >> 32), (int)((o1 - o0) * sizeof(R)), b.G));
+                    v.push_back(make_int4(v0[k] + sn.col, sn.ncol, sn.nrow, roff0 + sn.roff));
+                    v.push_back(make_int4(b.col0, b.col1, sn.ldr, (int)o0));
+                    v.push_back(make_int4(sn.parent >= 0 ? sn0[k] + sn.parent : -1, sn0[k] + b.s, 0, 0));
+                    nit_b[sn0[k] + b.s]++;
+                }
+            }
+        }
+        std::vector<int4> fi, bi;
+        fwd_ptr.assign(L + 1, 0);
+        for (int l = 0; l < L; ++l) {
+            fwd_ptr[l] = (int)(fi.size() / 4);
+            fi.insert(fi.end(), frec[l].begin(), frec[l].end());
+        }
+        fwd_ptr[L] = (int)(fi.size() / 4);
+        bwd_start.assign(L, 0);
+        bwd_cnt.assign(L, 0);
+        for (int l = L - 1; l >= 0; --l) {
+            bwd_start[l] = (int)(bi.size() / 4);
+            bwd_cnt[l] = (int)(brec[l].size() / 4);
+            bi.insert(bi.end(), brec[l].begin(), brec[l].end());
+        }
+        const int4 *p_fi, *p_bi;
+        const int *p_nf, *p_nb;
+        if ((rc = upload(p_fi, fi.data(), fi.size()))) return rc;
+        if ((rc = upload(p_bi, bi.data(), bi.size()))) return rc;
+        if ((rc = upload(p_nf, nit_f.data(), nit_f.size()))) return rc;
+        if ((rc = upload(p_nb, nit_b.data(), nit_b.size()))) return rc;
+        dsol.fwd_items = p_fi; dsol.bwd_items = p_bi;
+        dsol.fwd_nitems = p_nf; dsol.bwd_nitems = p_nb;
+        if ((rc = alloc(dsol.fwd_done, (size_t)sn_tot))) return rc;
+        if ((rc = alloc(dsol.bwd_done, (size_t)sn_tot))) return rc;
+        if ((rc = alloc(dsol.queue, 2))) return rc;
+        dsol.n_sn = (int)sn_tot;
+        dsol.nf = (int)nf_tot;
+        dsol.n_fwd_items = (int)(fi.size() / 4);
+        dsol.n_bwd_items = (int)(bi.size() / 4);
+        dsol.fwd_lvl_ptr = fwd_ptr.data();
+        dsol.bwd_lvl_start = bwd_start.data();
+        dsol.bwd_lvl_cnt = bwd_cnt.data();
+        dsol.fwd_lvl_ld = fwd_ld.data();
+        dsol.bwd_lvl_ld = bwd_ld.data();
+        dsol.fwd_lvl_q = fwd_q.data();
+        dsol.bwd_lvl_q = bwd_q.data();
+        dsol.fwd_qmax = dsol.fwd_ldmax = dsol.bwd_qmax = dsol.bwd_ldmax = 0;
+        for (int l = 0; l < L; ++l) {
+            dsol.fwd_qmax = std::max(dsol.fwd_qmax, fwd_q[l]);
+            dsol.fwd_ldmax = std::max(dsol.fwd_ldmax, fwd_ld[l]);
+            dsol.bwd_qmax = std::max(dsol.bwd_qmax, bwd_q[l]);
+            dsol.bwd_ldmax = std::max(dsol.bwd_ldmax, bwd_ld[l]);
+        }
+        dsol.dyn = 0;
+        dsol.dyn_grid = 0;
+        if (prm.dyn_sweeps) {
+            dsol.dyn_grid = solve_dyn_grid<R>(dsol);
+            dsol.dyn = dsol.dyn_grid > 0 ? 1 : 0;
+        }
+        dsol.err = &d_ctl[0].solve_err;
+        if ((rc = alloc(dsol.u, (size_t)std::max<int64_t>(upd_tot, 1)))) return rc;
+        return HQN_OK;
+    }
+
     // Ends any capture a failed build_graph left open and drops the graph.
     void abort_graph() {
         std::vector<cudaStream_t> ss = cap_streams;
@@ -306,61 +473,70 @@ struct Sim final : SimBase {
     }
 
     // ---- state transfer (caller order, absolute positions <-> internal displacements)
-    int put_vec(V4<R> *dst, const double *src, bool displacement, bool free_only) {
-        const int n = S.n;
+    int put_vec(int idx, V4<R> *dst, const double *src, bool displacement, bool free_only) {
+        const Setup &s = S[idx];
+        const int n = s.n;
         for (int i = 0; i < n; ++i) {
-            const int v = S.perm[i];
+            const int v = s.perm[i];
             V4<R> o;
             o.w = R(0);
-            if (free_only && i >= S.n_free) {
+            if (free_only && i >= s.n_free) {
                 o.x = o.y = o.z = R(0);
             } else {
                 double a[3];
                 for (int k = 0; k < 3; ++k) {
                     a[k] = src[3 * (size_t)v + k];
                     if (!std::isfinite(a[k])) return fail(HQN_ERR_NONFINITE, "non-finite input");
-                    if (displacement) a[k] -= S.X[3 * (size_t)i + k];
+                    if (displacement) a[k] -= s.X[3 * (size_t)i + k];
                 }
                 o.x = (R)a[0]; o.y = (R)a[1]; o.z = (R)a[2];
             }
             hbuf[i] = o;
         }
-        CK(cudaMemcpyAsync(dst, hbuf.data(), (size_t)n * sizeof(V4<R>), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dst + hdesc[idx].v0, hbuf.data(), (size_t)n * sizeof(V4<R>), cudaMemcpyHostToDevice, st));
         CK(cudaStreamSynchronize(st));
         return HQN_OK;
     }
-    int get_vec(const V4<R> *src, double *dst, bool displacement, bool free_only) {
-        const int n = S.n;
-        CK(cudaMemcpyAsync(hbuf.data(), src, (size_t)n * sizeof(V4<R>), cudaMemcpyDeviceToHost, st));
+    int get_vec(int idx, const V4<R> *src, double *dst, bool displacement, bool free_only) {
+        const Setup &s = S[idx];
+        const int n = s.n;
+        CK(cudaMemcpyAsync(hbuf.data(), src + hdesc[idx].v0, (size_t)n * sizeof(V4<R>), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         for (int i = 0; i < n; ++i) {
-            const int v = S.perm[i];
+            const int v = s.perm[i];
             const V4<R> o = hbuf[i];
             double a[3] = {(double)o.x, (double)o.y, (double)o.z};
-            if (free_only && i >= S.n_free) a[0] = a[1] = a[2] = 0.0;
+            if (free_only && i >= s.n_free) a[0] = a[1] = a[2] = 0.0;
             for (int k = 0; k < 3; ++k)
-                dst[3 * (size_t)v + k] = a[k] + (displacement ? S.X[3 * (size_t)i + k] : 0.0);
+                dst[3 * (size_t)v + k] = a[k] + (displacement ? s.X[3 * (size_t)i + k] : 0.0);
         }
         return HQN_OK;
     }
 
-    int set_state(const double *qc, const double *qp) override {
-        int rc = put_vec(ds.u_cur, qc, true, false);
+    int set_state(int idx, const double *qc, const double *qp) override {
+        if (idx < 0 || idx >= ns) return fail(HQN_ERR_ARG, "simulation index out of range");
+        int rc = put_vec(idx, ds.u_cur, qc, true, false);
         if (rc) return rc;
-        return put_vec(ds.u_prev, qp ? qp : qc, true, false);
+        return put_vec(idx, ds.u_prev, qp ? qp : qc, true, false);
     }
-    int get_state(double *qc, double *qp) override {
+    int get_state(int idx, double *qc, double *qp) override {
+        if (idx < 0 || idx >= ns) return fail(HQN_ERR_ARG, "simulation index out of range");
         int rc = HQN_OK;
-        if (qc && (rc = get_vec(ds.u_cur, qc, true, false))) return rc;
-        if (qp && (rc = get_vec(ds.u_prev, qp, true, false))) return rc;
+        if (qc && (rc = get_vec(idx, ds.u_cur, qc, true, false))) return rc;
+        if (qp && (rc = get_vec(idx, ds.u_prev, qp, true, false))) return rc;
         return HQN_OK;
     }
 
     int read_ctl() {
-        CK(cudaMemcpyAsync(h_ctl, ds.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h_ctl, d_ctl, sizeof(Ctl) * (size_t)ns, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        if (h_ctl->solve_err) return fail(HQN_ERR_CUDA, "a triangular sweep's bulk copy did not complete in time");
+        if (h_ctl[0].solve_err) return fail(HQN_ERR_CUDA, "a triangular sweep's device wait did not complete in time");
         return HQN_OK;
+    }
+    bool any_ctl(bool (*pred)(const Ctl &)) const {
+        for (int k = 0; k < ns; ++k)
+            if (pred(h_ctl[k])) return true;
+        return false;
     }
 
     // ---- pieces of the step
@@ -374,6 +550,7 @@ struct Sim final : SimBase {
         launch_reset_history(ds, s);
         launch_q(ds, s);
         launch_solve(dsol, ds.q, ds.z, ds.d, s);
+        launch_r0_dots(ds, s);
         launch_direction_final(ds, CondHandles{0, 0, 0}, 0, s);
     }
     void enqueue_start(CondHandles h, cudaStream_t s) {
@@ -394,19 +571,21 @@ struct Sim final : SimBase {
         const CondHandles none{0, 0, 0};
         int rc;
         enqueue_start(none, st);
-        for (int it = 0; it < prm.iters; ++it) {
+        if ((rc = read_ctl())) return rc;
+        for (int it = 0; it < prm.iters && any_ctl([](const Ctl &c) { return c.active != 0; }); ++it) {
             enqueue_direction(none, 0, st);
             if ((rc = read_ctl())) return rc;
-            if (h_ctl->nondescent) enqueue_reset_direction(st);
+            if (any_ctl([](const Ctl &c) { return c.nondescent != 0; })) enqueue_reset_direction(st);
             launch_tet(ds, TET_TRIAL1, none, st);
             if ((rc = read_ctl())) return rc;
-            for (int pass = 0; pass < prm.ls_max && !h_ctl->accepted && !h_ctl->stop; ++pass) {
+            for (int pass = 0; pass < prm.ls_max &&
+                               any_ctl([](const Ctl &c) { return c.active && !c.accepted && !c.stop; });
+                 ++pass) {
                 launch_ls(ds, none, st);
                 if ((rc = read_ctl())) return rc;
             }
             enqueue_accept(none, st);
             if ((rc = read_ctl())) return rc;
-            if (h_ctl->stop) break;
         }
         launch_commit(ds, st);
         CK(cudaGetLastError());
@@ -490,7 +669,7 @@ struct Sim final : SimBase {
 
     int step(int nsteps, hqn_step_stats *stats) override {
         if (nsteps < 0) return fail(HQN_ERR_ARG, "negative step count");
-        CK(cudaMemsetAsync(&ds.ctl->trials_total, 0, 5 * sizeof(int), st));
+        for (int k = 0; k < ns; ++k) CK(cudaMemsetAsync(&d_ctl[k].trials_total, 0, 5 * sizeof(int), st));
         for (int k = 0; k < nsteps; ++k) {
             if (graph_mode) {
                 CK(cudaGraphLaunch(gexec, st));
@@ -501,69 +680,101 @@ struct Sim final : SimBase {
         }
         int rc = read_ctl();
         if (rc) return rc;
-        const Ctl &c = *h_ctl;
+        int worst = HQN_OK;
+        for (int k = 0; k < ns; ++k) worst = std::max(worst, h_ctl[k].worst_status);
         if (stats) {
-            std::memset(stats, 0, sizeof(*stats));
-            stats->steps = c.steps;
-            stats->iters = c.stop ? c.k : c.k - 1;
-            stats->status = c.worst_status;
-            stats->trials_total = c.trials_total;
-            stats->iters_total = c.iters_total;
-            for (int i = 0; i < HQN_MAX_ITERS; ++i) {
-                stats->trials[i] = c.iter_trials[i];
-                stats->g[i] = c.iter_g[i];
+            fill_stats(0, stats);
+            stats->status = worst;
+            stats->trials_total = stats->iters_total = stats->ls_passes_total = 0;
+            for (int k = 0; k < ns; ++k) {
+                stats->trials_total += h_ctl[k].trials_total;
+                stats->iters_total += h_ctl[k].iters_total;
+                stats->ls_passes_total += h_ctl[k].passes_total;
             }
-            stats->g0 = c.g0;
-            stats->ls_passes_total = c.passes_total;
         }
-        if (nsteps > 0 && !std::isfinite(c.g_k)) return fail(HQN_ERR_NONFINITE, "objective is not finite");
-        return c.worst_status;
+        if (nsteps > 0)
+            for (int k = 0; k < ns; ++k)
+                if (!std::isfinite(h_ctl[k].g_k))
+                    return fail(HQN_ERR_NONFINITE, "objective of simulation " + std::to_string(k) + " is not finite");
+        return worst;
     }
 
+    void fill_stats(int idx, hqn_step_stats *stats) const {
+        const Ctl &c = h_ctl[idx];
+        std::memset(stats, 0, sizeof(*stats));
+        stats->steps = c.steps;
+        stats->iters = c.stop ? c.k : c.k - 1;
+        stats->status = c.worst_status;
+        stats->trials_total = c.trials_total;
+        stats->iters_total = c.iters_total;
+        for (int i = 0; i < HQN_MAX_ITERS; ++i) {
+            stats->trials[i] = c.iter_trials[i];
+            stats->g[i] = c.iter_g[i];
+        }
+        stats->g0 = c.g0;
+        stats->ls_passes_total = c.passes_total;
+    }
+
+    int stats_of(int idx, hqn_step_stats *stats) override {
+        if (idx < 0 || idx >= ns) return fail(HQN_ERR_ARG, "simulation index out of range");
+        int rc = read_ctl();
+        if (rc) return rc;
+        fill_stats(idx, stats);
+        return HQN_OK;
+    }
+
+    // The evaluation entry points act on simulation 0 (the kernels run over
+    // the batch; the other simulations' results are not used).
     int energy_grad(const double *x, const double *y, double *g, double *grad) override {
         int rc;
-        if ((rc = put_vec(ds.xt, x, true, false))) return rc;
-        if ((rc = put_vec(ds.y, y, true, false))) return rc;
+        if ((rc = put_vec(0, ds.xt, x, true, false))) return rc;
+        if ((rc = put_vec(0, ds.y, y, true, false))) return rc;
         const CondHandles none{0, 0, 0};
         launch_inertia(ds, st);
         launch_tet(ds, TET_EVAL, none, st);
         launch_gather(ds, G_EVAL, none, st);
         CK(cudaGetLastError());
         if ((rc = read_ctl())) return rc;
-        if (g) *g = h_ctl->g_trial;
+        if (g) *g = h_ctl[0].g_trial;
         if (grad) {
             // clamped rows of gk are never written: they stay zero
-            if ((rc = get_vec(ds.gk, grad, false, true))) return rc;
+            if ((rc = get_vec(0, ds.gk, grad, false, true))) return rc;
         }
         return HQN_OK;
     }
 
     int solve_A0(const double *q, double *r) override {
         int rc;
-        if ((rc = put_vec(ds.q, q, false, true))) return rc;
+        if ((rc = put_vec(0, ds.q, q, false, true))) return rc;
         launch_solve(dsol, ds.q, ds.z, ds.d, st);
         CK(cudaGetLastError());
         if ((rc = read_ctl())) return rc;
-        return get_vec(ds.d, r, false, true);
+        return get_vec(0, ds.d, r, false, true);
     }
 
     int direction(const double *grad, int np, const double *s, const double *t, double *d) override {
-        const int m = prm.history_m, n = S.n;
+        const int m = prm.history_m, n = S[0].n;
         if (np < 0 || np > m) return fail(HQN_ERR_ARG, "npairs out of range");
         int rc;
-        if ((rc = put_vec(ds.gk, grad, false, true))) return rc;
+        if ((rc = put_vec(0, ds.gk, grad, false, true))) return rc;
+        V4<R> *S0 = ds.S + hdesc[0].ring0, *T0 = ds.Tt + hdesc[0].ring0;
         for (int i = 0; i < np; ++i) {
-            if ((rc = put_vec(ds.S + (size_t)i * n, s + (size_t)i * 3 * n, false, true))) return rc;
-            if ((rc = put_vec(ds.Tt + (size_t)i * n, t + (size_t)i * 3 * n, false, true))) return rc;
+            if ((rc = put_vec(0, S0 + (size_t)i * n, s + (size_t)i * 3 * n, false, true))) return rc;
+            if ((rc = put_vec(0, T0 + (size_t)i * n, t + (size_t)i * 3 * n, false, true))) return rc;
         }
-        int hc[2] = {np, np > 0 ? np - 1 : 0};
-        CK(cudaMemcpyAsync(&ds.ctl->count, &hc[0], sizeof(int), cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(&ds.ctl->head, &hc[1], sizeof(int), cudaMemcpyHostToDevice, st));
-        for (int a = 0; a < np; ++a) launch_hist_row(ds, a, st);
+        // simulation 0 alone iterates, with the caller's pairs: count, head, active
+        for (int k = 0; k < ns; ++k) {
+            const int v[3] = {k == 0 ? np : 0, k == 0 && np > 0 ? np - 1 : 0, k == 0 ? 1 : 0};
+            CK(cudaMemcpyAsync(&d_ctl[k].count, &v[0], sizeof(int), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(&d_ctl[k].head, &v[1], sizeof(int), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(&d_ctl[k].active, &v[2], sizeof(int), cudaMemcpyHostToDevice, st));
+            CK(cudaStreamSynchronize(st));
+        }
+        for (int a = 0; a < np; ++a) launch_hist_row(ds, a, st, hdesc[0].nvb);
         enqueue_direction(CondHandles{0, 0, 0}, 0, st);
         CK(cudaGetLastError());
         if ((rc = read_ctl())) return rc;
-        return get_vec(ds.d, d, false, true);
+        return get_vec(0, ds.d, d, false, true);
     }
 
     int time_stage(int stage, int reps, double *ms) override {
@@ -597,22 +808,45 @@ struct Sim final : SimBase {
     }
 
     void info(hqn_info *o) const override {
-        o->n_verts = S.n;
-        o->n_tets = S.T;
-        o->n_free = S.n_free;
-        o->n_supernodes = (int)S.sn.size();
-        o->n_levels = S.n_levels;
-        o->factor_entries = (int64_t)S.Q.size();
-        o->factor_nnz = S.factor_nnz;
-        o->stiffness_k = S.k;
-        o->setup_seconds = S.setup_seconds;
+        o->n_verts = (int32_t)n_tot;
+        o->n_tets = (int32_t)T_tot;
+        o->n_free = (int32_t)nf_tot;
+        o->n_supernodes = (int32_t)sn_tot;
+        o->n_levels = n_levels;
+        o->factor_entries = q_entries;
+        o->factor_nnz = nnz_tot;
+        o->stiffness_k = S.empty() ? 0.0 : S[0].k;
+        o->setup_seconds = setup_seconds;
         o->device_bytes = dev_bytes;
         o->precision = (int)(sizeof(R) == 4 ? HQN_FP32_MIXED : HQN_FP64_PLAIN);
         o->graph_mode = graph_mode ? 1 : 0;
-        o->n_update_entries = S.n_upd;
+        o->n_update_entries = upd_tot;
         o->chained_sweeps = dsol.pdl;
+        o->sweep_schedule = dsol.dyn;
+        o->n_sims = ns;
     }
 };
+
+template <typename R>
+int make_batch(int count, const hqn_mesh *meshes, const hqn_material *materials, const hqn_params &prm,
+               cudaStream_t st, std::unique_ptr<SimBase> &out) {
+    std::unique_ptr<Sim<R>> b(new Sim<R>());
+    b->S.resize(count);
+    std::vector<int> rcs(count, HQN_OK);
+    std::vector<std::string> errs(count);
+#pragma omp parallel for schedule(dynamic, 1) if (count > 1)
+    for (int k = 0; k < count; ++k) rcs[k] = build_setup(meshes[k], materials[k], prm, b->S[k], errs[k]);
+    for (int k = 0; k < count; ++k)
+        if (rcs[k] != HQN_OK)
+            return fail(rcs[k], count > 1 ? "simulation " + std::to_string(k) + ": " + errs[k] : errs[k]);
+    const int rc = b->init(prm, st);
+    if (rc != HQN_OK) return rc;
+    out = std::move(b);
+    return HQN_OK;
+}
+
+int create_any(int count, const hqn_mesh *meshes, const hqn_material *materials, const hqn_params *params,
+               void *stream, sim_handle **out);
 
 }  // namespace
 
@@ -624,6 +858,37 @@ void set_last_error(const char *msg) { g_last_error = msg; }
 struct sim_handle {
     std::unique_ptr<SimBase> impl;
 };
+
+namespace {
+
+int create_any(int count, const hqn_mesh *meshes, const hqn_material *materials, const hqn_params *params,
+               void *stream, sim_handle **out) {
+    if (!out) return fail(HQN_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    if (count <= 0 || !meshes || !materials || !params) return fail(HQN_ERR_ARG, "null argument or empty batch");
+    if (params->precision != HQN_FP32_MIXED && params->precision != HQN_FP64_PLAIN)
+        return fail(HQN_ERR_ARG, "unknown precision");
+    if (params->tet_block != 0 && params->tet_block != TBS)
+        return fail(HQN_ERR_UNSUPPORTED, "tet_block must be 0 or 128");
+    try {
+        std::unique_ptr<SimBase> impl;
+        const cudaStream_t st = (cudaStream_t)stream;
+        const int rc = params->precision == HQN_FP32_MIXED
+                           ? make_batch<float>(count, meshes, materials, *params, st, impl)
+                           : make_batch<double>(count, meshes, materials, *params, st, impl);
+        if (rc != HQN_OK) return rc;
+        auto *h = new sim_handle;
+        h->impl = std::move(impl);
+        *out = h;
+        return HQN_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(HQN_ERR_NO_MEMORY, "host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(HQN_ERR_ARG, e.what());
+    }
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -644,55 +909,46 @@ void hqn_default_params(hqn_params *p) {
     p->precision = HQN_FP32_MIXED;
     p->leaf_size = 64;
     p->use_graph = 1;
-    p->tet_block = 128;
+    p->tet_block = TBS;
     p->ls_batch = 8;
+    p->dyn_sweeps = 0;
 }
 
 int sim_create(const hqn_mesh *mesh, const hqn_material *material, const hqn_params *params, void *stream,
                sim_handle **out) {
-    if (!out) return fail(HQN_ERR_ARG, "null output pointer");
-    *out = nullptr;
-    if (!mesh || !material || !params) return fail(HQN_ERR_ARG, "null argument");
-    if (params->precision != HQN_FP32_MIXED && params->precision != HQN_FP64_PLAIN)
-        return fail(HQN_ERR_ARG, "unknown precision");
-    try {
-        std::unique_ptr<SimBase> impl;
-        Setup *S = nullptr;
-        if (params->precision == HQN_FP32_MIXED) {
-            auto *p = new Sim<float>();
-            impl.reset(p);
-            S = &p->S;
-        } else {
-            auto *p = new Sim<double>();
-            impl.reset(p);
-            S = &p->S;
-        }
-        std::string err;
-        int rc = build_setup(*mesh, *material, *params, *S, err);
-        if (rc != HQN_OK) return fail(rc, err);
-        cudaStream_t st = (cudaStream_t)stream;
-        if (params->precision == HQN_FP32_MIXED) rc = static_cast<Sim<float> *>(impl.get())->init(*params, st);
-        else rc = static_cast<Sim<double> *>(impl.get())->init(*params, st);
-        if (rc != HQN_OK) return rc;
-        auto *h = new sim_handle;
-        h->impl = std::move(impl);
-        *out = h;
-        return HQN_OK;
-    } catch (const std::bad_alloc &) {
-        return fail(HQN_ERR_NO_MEMORY, "host allocation failed");
-    } catch (const std::exception &e) {
-        return fail(HQN_ERR_ARG, e.what());
-    }
+    return create_any(1, mesh, material, params, stream, out);
 }
+
+int sim_batch_create(int32_t count, const hqn_mesh *meshes, const hqn_material *materials,
+                     const hqn_params *params, void *stream, sim_handle **out) {
+    return create_any(count, meshes, materials, params, stream, out);
+}
+
+int32_t sim_batch_count(const sim_handle *sim) { return sim ? sim->impl->count() : 0; }
 
 int sim_set_state(sim_handle *sim, const double *q_cur, const double *q_prev) {
     if (!sim || !q_cur) return fail(HQN_ERR_ARG, "null argument");
-    try { return sim->impl->set_state(q_cur, q_prev); } catch (...) { return fail(HQN_ERR_NO_MEMORY, "exception"); }
+    try { return sim->impl->set_state(0, q_cur, q_prev); } catch (...) { return fail(HQN_ERR_NO_MEMORY, "exception"); }
 }
 
 int sim_get_state(sim_handle *sim, double *q_cur, double *q_prev) {
     if (!sim) return fail(HQN_ERR_ARG, "null handle");
-    try { return sim->impl->get_state(q_cur, q_prev); } catch (...) { return fail(HQN_ERR_NO_MEMORY, "exception"); }
+    try { return sim->impl->get_state(0, q_cur, q_prev); } catch (...) { return fail(HQN_ERR_NO_MEMORY, "exception"); }
+}
+
+int sim_batch_set_state(sim_handle *sim, int32_t index, const double *q_cur, const double *q_prev) {
+    if (!sim || !q_cur) return fail(HQN_ERR_ARG, "null argument");
+    try { return sim->impl->set_state(index, q_cur, q_prev); } catch (...) { return fail(HQN_ERR_NO_MEMORY, "exception"); }
+}
+
+int sim_batch_get_state(sim_handle *sim, int32_t index, double *q_cur, double *q_prev) {
+    if (!sim) return fail(HQN_ERR_ARG, "null handle");
+    try { return sim->impl->get_state(index, q_cur, q_prev); } catch (...) { return fail(HQN_ERR_NO_MEMORY, "exception"); }
+}
+
+int sim_batch_get_stats(sim_handle *sim, int32_t index, hqn_step_stats *stats) {
+    if (!sim || !stats) return fail(HQN_ERR_ARG, "null argument");
+    try { return sim->impl->stats_of(index, stats); } catch (...) { return fail(HQN_ERR_NO_MEMORY, "exception"); }
 }
 
 int sim_step(sim_handle *sim, int32_t nsteps, hqn_step_stats *stats) {

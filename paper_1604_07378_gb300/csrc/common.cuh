@@ -58,6 +58,7 @@ struct Ctl {
     int status;        // worst status of the step (HQN_OK or a warning)
     int accepted;      // the last trial passed the Armijo test
     int grad_ready;    // the corner gradients already belong to the accepted point
+    int active;        // this simulation is still iterating in the current step
     int nondescent;    // tr(grad^T d) >= 0 with history: reset and recompute
     int trials_total;  // over the steps since the host last cleared it
     int iters_total;

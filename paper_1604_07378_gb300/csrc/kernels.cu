@@ -1,7 +1,15 @@
 // Step kernels of the quasi-Newton implicit-Euler solver: predictor (Eq. PD),
-// line-search trial update and Armijo test (Alg. 1), per-tet energy and
-// corner gradients (Eq. valanis-landel), the atomic-free vertex gather of
-// grad g (Eq. PD), the history push and the two loops of Alg. 2.
+// per-tet energy and corner gradients (Eq. valanis-landel), the line-search
+// trials and Armijo tests (Alg. 1), the atomic-free vertex gather of grad g
+// (Eq. PD), the history push and the two loops of Alg. 2.
+//
+// Every kernel runs over a batch of independent simulations.  Each block
+// belongs to one simulation (the block tables map blocks to simulations) and
+// stages that simulation's descriptor in shared memory.  Reductions are per
+// simulation: each block publishes a partial, and the simulation's last block
+// (an arrival ticket in its control block) sums its partials in a fixed order
+// and takes its decisions.  The last simulation to decide sets the graph's
+// conditional handles from every simulation's state.
 #include "kernels.cuh"
 #include "reduce.cuh"
 #include "tetmath.cuh"
@@ -9,9 +17,6 @@
 namespace hqn {
 
 namespace {
-
-template <typename R>
-__device__ __forceinline__ V4<R> ld(const V4<R> *p, int i) { return p[i]; }
 
 template <typename R>
 __device__ __forceinline__ void set_cond(unsigned long long h, unsigned int v) {
@@ -23,30 +28,99 @@ __device__ __forceinline__ int ring_slot(int head, int age, int m) {
     return s < 0 ? s + m + 1 : s;
 }
 
+// The descriptor of the simulation that owns this block: the kernel
+// parameter for a single simulation, else a copy in shared memory made by the
+// block's threads (a block-uniform structure of a few hundred bytes that
+// every thread reads).
+template <typename R>
+__device__ __forceinline__ const SimDesc<R> &stage_desc_batch(const SimDesc<R> *all, int sim) {
+    __shared__ __align__(16) unsigned char raw[sizeof(SimDesc<R>)];
+    static_assert(sizeof(SimDesc<R>) % 4 == 0, "descriptor size");
+    const unsigned int *src = reinterpret_cast<const unsigned int *>(all + sim);
+    unsigned int *dst = reinterpret_cast<unsigned int *>(raw);
+    for (int k = threadIdx.x; k < (int)(sizeof(SimDesc<R>) / 4); k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    return *reinterpret_cast<const SimDesc<R> *>(raw);
+}
+
+template <typename R>
+__device__ __forceinline__ const SimDesc<R> &sim_desc(const DevSim<R> &s, const int *blk_sim) {
+    if (s.nsims == 1) return s.desc0;
+    return stage_desc_batch(s.desc, blk_sim[blockIdx.x]);
+}
+
+// Last block of a simulation, after its thread 0 wrote that simulation's
+// decision: the last simulation to get here sets the graph condition `handle`
+// to whether any simulation satisfies `pred` (called by every thread of the
+// block).  The arrival counter re-arms itself.
+template <typename R, typename Pred>
+__device__ __forceinline__ void batch_condition(const DevSim<R> &s, int slot, unsigned long long handle, Pred pred) {
+    if (s.nsims == 1) {  // thread 0 wrote the decision itself
+        if (threadIdx.x == 0) set_cond<R>(handle, pred((const volatile Ctl *)s.desc0.ctl) ? 1u : 0u);
+        return;
+    }
+    __shared__ int last_sim;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last_sim = atomicAdd(&s.batch_ticket[slot], 1u) == (unsigned)s.nsims - 1u;
+    }
+    __syncthreads();
+    if (!last_sim) return;
+    __threadfence();
+    int any = 0;
+    for (int k = threadIdx.x; k < s.nsims; k += blockDim.x) any |= pred((const volatile Ctl *)s.desc[k].ctl) ? 1 : 0;
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        s.batch_ticket[slot] = 0u;
+        set_cond<R>(handle, any ? 1u : 0u);
+    }
+}
+
+// Per-simulation grid reduction: the block's partials at
+// part[k * stride + block]; true in every thread of the simulation's last block.
+template <int NV>
+__device__ __forceinline__ bool sim_arrive(const double (&v)[NV], double *part, int stride, int nblocks,
+                                           unsigned int *ticket) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) part[k * stride + blockIdx.x] = v[k];
+        __threadfence();
+        const unsigned int t = atomicAdd(ticket, 1u);
+        last = (t == (unsigned)nblocks - 1u);
+    }
+    __syncthreads();
+    return last;
+}
+
 // ---------------------------------------------------------------- predictor
 
 // y = 2 q_l - q_{l-1} + h^2 g on free vertices, y = q_l on clamped ones;
-// x_1 = y.  Thread 0 of block 0 also clears the step's control block.
+// x_1 = y.  The simulation's first block also clears its control block.
 template <typename R>
 __global__ void __launch_bounds__(VBS) k_predict(DevSim<R> s) {
-    const int i = blockIdx.x * VBS + threadIdx.x;
-    if (i < s.c.n) {
-        const V4<R> a = s.u_cur[i], b = s.u_prev[i];
+    const SimDesc<R> &D = sim_desc(s, s.vblk_sim);
+    const int i = (blockIdx.x - D.vb0) * VBS + threadIdx.x;
+    if (i < D.c.n) {
+        const int g = D.v0 + i;
+        const V4<R> a = s.u_cur[g], b = s.u_prev[g];
         V4<R> yy = a;
-        if (i < s.c.nf) {
-            yy.x = R(2) * a.x - b.x + s.c.gx;
-            yy.y = R(2) * a.y - b.y + s.c.gy;
-            yy.z = R(2) * a.z - b.z + s.c.gz;
+        if (i < D.c.nf) {
+            yy.x = R(2) * a.x - b.x + D.c.gx;
+            yy.y = R(2) * a.y - b.y + D.c.gy;
+            yy.z = R(2) * a.z - b.z + D.c.gz;
         }
         yy.w = R(0);
-        s.y[i] = yy;
-        s.xk[i] = yy;
-        s.xt[i] = yy;
+        s.y[g] = yy;
+        s.xk[g] = yy;
+        s.xt[g] = yy;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        Ctl *c = s.ctl;
+    if (blockIdx.x == D.vb0 && threadIdx.x == 0) {
+        Ctl *c = D.ctl;
         c->k = 0; c->trials = 0; c->count = 0; c->head = 0; c->stop = 0;
         c->status = HQN_OK; c->accepted = 0; c->nondescent = 0; c->alpha = 1.0; c->grad_ready = 0;
+        c->active = 0;
     }
 }
 
@@ -57,12 +131,14 @@ __global__ void __launch_bounds__(VBS) k_predict(DevSim<R> s) {
 template <typename R>
 __global__ void __launch_bounds__(VBS) k_inertia(DevSim<R> s) {
     using A = ExactAcc<R>;
-    const int i = blockIdx.x * VBS + threadIdx.x;
+    const SimDesc<R> &D = sim_desc(s, s.vblk_sim);
+    const int i = (blockIdx.x - D.vb0) * VBS + threadIdx.x;
     typename A::T e[1] = {A::zero()};
-    if (i < s.c.n) {
-        const V4<R> x = s.xt[i], yy = s.y[i];
+    if (i < D.c.n) {
+        const int g = D.v0 + i;
+        const V4<R> x = s.xt[g], yy = s.y[g];
         const R dx = x.x - yy.x, dy = x.y - yy.y, dz = x.z - yy.z;
-        e[0] = A::add(e[0], R(0.5) * s.mh2[i] * (dx * dx + dy * dy + dz * dz));
+        e[0] = A::add(e[0], R(0.5) * s.mh2[g] * (dx * dx + dy * dy + dz * dz));
     }
     double tot[1];
     block_sum_exact<VBS, 1, R>(e, tot);
@@ -83,7 +159,7 @@ __device__ __forceinline__ V4<R> step_point(const V4<R> &a, const V4<R> &b, R al
 template <typename R>
 __device__ __forceinline__ void load_dm(const DevSim<R> &s, int t, R Di[9]) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Di[k] = s.dminv[(size_t)k * s.c.T + t];
+    for (int k = 0; k < 9; ++k) Di[k] = s.dminv[(size_t)k * s.Tn + t];
 }
 
 template <typename R>
@@ -94,31 +170,44 @@ __device__ __forceinline__ void edge_diffs(const V4<R> &x0, const V4<R> &x1, con
     du[2][0] = x3.x - x0.x; du[2][1] = x3.y - x0.y; du[2][2] = x3.z - x0.z;
 }
 
+// Sum of the simulation's per-block partials part[b], b in [b0, b0 + nb), by
+// its last block (fixed order, float64); result valid in thread 0.
+template <int BS>
+__device__ __forceinline__ double sum_block_range(const double *part, int b0, int nb) {
+    double acc[1] = {0.0};
+    for (int b = threadIdx.x; b < nb; b += BS) acc[0] += __ldcg(part + b0 + b);
+    block_sum<BS, 1>(acc);
+    return acc[0];
+}
+
 // ---------------------------------------------------------------- tet kernel
 
 // One thread per tet: the four corner gradients of V Psi, written to
-// corner[c * T + t].
-//   TET_INIT / TET_EVAL: at the point x_t, with the energy reduced too (last
-//     block, fixed order, float64, plus the inertia partials): TET_INIT sets
-//     g(x_1), TET_EVAL reports g.
+// corner[c * Tn + t].
+//   TET_INIT / TET_EVAL: at the point x_t, with the energy reduced too (the
+//     simulation's last block, fixed order, plus the inertia partials):
+//     TET_INIT sets g(x_1), TET_EVAL reports g.
 //   TET_TRIAL1: the first trial of Alg. 1's line search, alpha = 1, at
 //     x_k + d; the last block adds the inertia term along the ray and runs the
 //     Armijo test.  Accepted: the corners are the gradient of x_{k+1} and the
-//     line-search loop is skipped.  Rejected: the loop continues at
+//     simulation skips the line-search loop.  Rejected: the loop continues at
 //     alpha = backtrack.
 //   TET_GRAD: at the accepted point x_k + alpha d, corners only; nothing to do
-//     if TET_TRIAL1 already left them there or the iterations stopped.
-template <typename R, int BS>
-__global__ void __launch_bounds__(BS, 1024 / BS) k_tet(DevSim<R> s, int mode, CondHandles h) {
+//     if TET_TRIAL1 already left them there or the simulation stopped.
+template <typename R>
+__global__ void __launch_bounds__(TBS, 8) k_tet(DevSim<R> s, int mode, CondHandles h) {
+    using A = ExactAcc<R>;
+    const SimDesc<R> &D = sim_desc(s, s.tblk_sim);
+    Ctl *c = D.ctl;
     const bool grad_mode = mode == TET_GRAD;
     const bool ray_mode = mode == TET_GRAD || mode == TET_TRIAL1;
-    if (grad_mode && (s.ctl->stop || s.ctl->grad_ready)) return;
-    const R al = grad_mode ? (R)s.ctl->alpha : R(1);
-    using A = ExactAcc<R>;
-    const int T = s.c.T;
-    const int t = blockIdx.x * BS + threadIdx.x;
+    const bool inactive = ray_mode && !c->active;
+    if (grad_mode && (inactive || c->stop || c->grad_ready)) return;
+    const R al = grad_mode ? (R)c->alpha : R(1);
+    const int tl = (blockIdx.x - D.tb0) * TBS + threadIdx.x;
     typename A::T e[1] = {A::zero()};
-    if (t < T) {
+    if (tl < D.c.T && !inactive) {
+        const int t = D.t0 + tl;
         const int4 v = s.tets[t];
         V4<R> x0, x1, x2, x3;
         if (ray_mode) {
@@ -135,64 +224,58 @@ __global__ void __launch_bounds__(BS, 1024 / BS) k_tet(DevSim<R> s, int mode, Co
         def_grad(du, Di, G);
         const R vol = s.vol[t];
         R g[4][3];
-        tet_grad(s.mat, G, Di, vol, g);
-        if (!grad_mode) e[0] = A::add(e[0], vol * tet_psi(s.mat, G));
+        tet_grad(D.mat, G, Di, vol, g);
+        if (!grad_mode) e[0] = A::add(e[0], vol * tet_psi(D.mat, G));
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int k = 0; k < 4; ++k) {
             V4<R> o;
-            o.x = g[c][0]; o.y = g[c][1]; o.z = g[c][2]; o.w = R(0);
-            s.corner[(size_t)c * T + t] = o;
+            o.x = g[k][0]; o.y = g[k][1]; o.z = g[k][2]; o.w = R(0);
+            s.corner[(size_t)k * s.Tn + t] = o;
         }
     }
     if (grad_mode) return;
     double tot[1];
-    block_sum_exact<BS, 1, R>(e, tot);
-    if (!publish_and_arrive<1>(tot, s.part_el, 0, &s.ctl->ticket[TK_TET])) return;
-    sum_partials<BS, 1>(s.part_el, 0, gridDim.x, tot, &s.ctl->ticket[TK_TET]);
-    Ctl *c = s.ctl;
+    block_sum_exact<TBS, 1, R>(e, tot);
+    if (!sim_arrive<1>(tot, s.part_el, 0, D.ntb, &c->ticket[TK_TET])) return;
+    const double el = sum_block_range<TBS>(s.part_el, D.tb0, D.ntb);
     if (mode == TET_TRIAL1) {
-        if (threadIdx.x != 0) return;
-        // g(x_k + d) - g(x_k) = E(x_k + d) - E(x_k) + I(1) - I(0) with the
-        // inertia term I(alpha) = a0 + a1 alpha + a2 alpha^2 along the ray
-        const double e = tot[0];
-        const double dI = c->ls_a[1] + c->ls_a[2];
-        c->passes_total += 1;
-        c->trials = 1;
-        if ((e - c->e_k) + dI <= s.c.gamma * c->gd) {
-            c->accepted = 1;
-            c->grad_ready = 1;
-            c->alpha = 1.0;
-            c->e_trial = e;
-            c->g_trial = e + c->ls_a[0] + dI;
-            set_cond<R>(h.ls, 0u);
-        } else {
-            c->accepted = 0;
-            c->grad_ready = 0;
-            c->alpha = s.c.backtrack;
-            if (s.c.ls_max <= 1) {
-                c->stop = 1;
-                c->status = HQN_WARN_LS_EXHAUSTED;
-                set_cond<R>(h.ls, 0u);
-            } else {
-                set_cond<R>(h.ls, 1u);
+        if (threadIdx.x == 0) {
+            c->ticket[TK_TET] = 0u;
+            if (c->active) {
+                // g(x_k + d) - g(x_k) = E(x_k + d) - E(x_k) + I(1) - I(0) with the
+                // inertia term I(alpha) = a0 + a1 alpha + a2 alpha^2 along the ray
+                const double dI = c->ls_a[1] + c->ls_a[2];
+                c->passes_total += 1;
+                c->trials = 1;
+                if ((el - c->e_k) + dI <= D.c.gamma * c->gd) {
+                    c->accepted = 1;
+                    c->grad_ready = 1;
+                    c->alpha = 1.0;
+                    c->e_trial = el;
+                    c->g_trial = el + c->ls_a[0] + dI;
+                } else {
+                    c->accepted = 0;
+                    c->grad_ready = 0;
+                    c->alpha = D.c.backtrack;
+                    if (D.c.ls_max <= 1) {
+                        c->stop = 1;
+                        c->status = HQN_WARN_LS_EXHAUSTED;
+                    }
+                }
             }
         }
+        batch_condition(s, BT_LS, h.ls,
+                        [](const volatile Ctl *x) { return x->active && !x->accepted && !x->stop; });
         return;
     }
-    double in[1];
-    const int nbv = (s.c.n + VBS - 1) / VBS;
-    {
-        double acc = 0.0;
-        for (int i = threadIdx.x; i < nbv; i += BS) acc += __ldcg(s.part_in + i);
-        in[0] = acc;
-        block_sum<BS, 1>(in);
-    }
+    const double in = sum_block_range<TBS>(s.part_in, D.vb0, D.nvb);
     if (threadIdx.x != 0) return;
-    const double g = tot[0] + in[0];
+    c->ticket[TK_TET] = 0u;
+    const double g = el + in;
     c->g_trial = g;
     if (mode == TET_INIT) {
         c->g_k = g;
-        c->e_k = tot[0];
+        c->e_k = el;
         c->g0 = g;
         c->accepted = 1;
     }
@@ -209,20 +292,22 @@ __global__ void __launch_bounds__(BS, 1024 / BS) k_tet(DevSim<R> s, int mode, Co
 // (written on differences, g(x_k + a d) - g(x_k) <= gamma a tr(grad^T d), so
 // the inertia term's constant part never enters a comparison): the first
 // alpha_j that passes is accepted (the same choice as testing them one at a
-// time).  Otherwise the next pass
-// continues from alpha_K, until ls_max trials in all.
-template <typename R, int BS, int K>
-__global__ void __launch_bounds__(BS) k_ls(DevSim<R> s, CondHandles h) {
-    Ctl *ctl = s.ctl;
-    const double a0 = ctl->alpha;
-    const double bt = s.c.backtrack;
+// time).  Otherwise the next pass continues from alpha_K, until ls_max
+// trials in all.  Simulations that are not searching skip the pass.
+template <typename R, int K>
+__global__ void __launch_bounds__(TBS) k_ls(DevSim<R> s, CondHandles h) {
     using A = ExactAcc<R>;
-    const int T = s.c.T;
-    const int t = blockIdx.x * BS + threadIdx.x;
+    const SimDesc<R> &D = sim_desc(s, s.tblk_sim);
+    Ctl *ctl = D.ctl;
+    const bool searching = ctl->active && !ctl->accepted && !ctl->stop;
+    const double a0 = ctl->alpha;
+    const double bt = D.c.backtrack;
+    const int tl = (blockIdx.x - D.tb0) * TBS + threadIdx.x;
     typename A::T e[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) e[j] = A::zero();
-    if (t < T) {
+    if (tl < D.c.T && searching) {
+        const int t = D.t0 + tl;
         const int4 v = s.tets[t];
         R Duk[3][3], Dd[3][3], Di[9], Gk[3][3], Gd[3][3];
         edge_diffs(s.xk[v.x], s.xk[v.y], s.xk[v.z], s.xk[v.w], Duk);
@@ -232,59 +317,70 @@ __global__ void __launch_bounds__(BS) k_ls(DevSim<R> s, CondHandles h) {
         def_grad(Dd, Di, Gd);
         const R vol = s.vol[t];
         PsiRay<R> ray;
-        psi_ray_setup(s.mat, Gk, Gd, ray);
+        psi_ray_setup(D.mat, Gk, Gd, ray);
         double a = a0;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            e[j] = A::add(e[j], vol * psi_ray_eval(s.mat, ray, (R)a));
+            e[j] = A::add(e[j], vol * psi_ray_eval(D.mat, ray, (R)a));
             a *= bt;
         }
     }
     double tot[K];
-    block_sum_exact<BS, K, R>(e, tot);
-    if (!publish_and_arrive<K>(tot, s.part_ls, gridDim.x, &ctl->ticket[TK_LS])) return;
-    sum_partials<BS, K>(s.part_ls, gridDim.x, gridDim.x, tot, &ctl->ticket[TK_LS]);
-    if (threadIdx.x != 0) return;
-    double a = a0;
-    int tr = ctl->trials;
-    ctl->passes_total += 1;
-    const double ek = ctl->e_k, slope = s.c.gamma * ctl->gd;
-    const double c0 = ctl->ls_a[0], c1 = ctl->ls_a[1], c2 = ctl->ls_a[2];
-    bool done = false;
+    block_sum_exact<TBS, K, R>(e, tot);
+    if (!sim_arrive<K>(tot, s.part_ls, s.ntb, D.ntb, &ctl->ticket[TK_LS])) return;
+    {
+        // the simulation's partials, one warp per trial
+        __shared__ double sh[K];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        __threadfence();
+        for (int j = warp; j < K; j += TBS / 32) {
+            double acc = 0.0;
+            for (int b = lane; b < D.ntb; b += 32) acc += __ldcg(s.part_ls + (size_t)j * s.ntb + D.tb0 + b);
+            acc = warp_sum(acc);
+            if (lane == 0) sh[j] = acc;
+        }
+        __syncthreads();
 #pragma unroll
-    for (int j = 0; j < K; ++j) {
-        if (done) break;
-        if (tr >= s.c.ls_max) {
-            ctl->accepted = 0;
-            ctl->stop = 1;
-            ctl->status = HQN_WARN_LS_EXHAUSTED;
-            done = true;
-            break;
-        }
-        tr += 1;
-        // Armijo on differences: E(x_k + a d) - E(x_k) + I(a) - I(0) <= gamma a gd
-        const double dI = a * (c1 + a * c2);
-        if ((tot[j] - ek) + dI <= slope * a) {
-            ctl->accepted = 1;
-            ctl->alpha = a;
-            ctl->e_trial = tot[j];
-            ctl->g_trial = tot[j] + c0 + dI;
-            done = true;
-            break;
-        }
-        a *= bt;
+        for (int j = 0; j < K; ++j) tot[j] = sh[j];
     }
-    ctl->trials = tr;
-    if (!done) {
-        ctl->alpha = a;
-        if (tr >= s.c.ls_max) {
-            ctl->accepted = 0;
-            ctl->stop = 1;
-            ctl->status = HQN_WARN_LS_EXHAUSTED;
-            done = true;
+    if (threadIdx.x == 0) {
+        ctl->ticket[TK_LS] = 0u;
+        if (searching) {
+            double a = a0;
+            int tr = ctl->trials;
+            ctl->passes_total += 1;
+            const double ek = ctl->e_k, slope = D.c.gamma * ctl->gd;
+            const double c0 = ctl->ls_a[0], c1 = ctl->ls_a[1], c2 = ctl->ls_a[2];
+            bool done = false;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                if (done) break;
+                if (tr >= D.c.ls_max) break;
+                tr += 1;
+                // Armijo on differences: E(x_k + a d) - E(x_k) + I(a) - I(0) <= gamma a gd
+                const double dI = a * (c1 + a * c2);
+                if ((tot[j] - ek) + dI <= slope * a) {
+                    ctl->accepted = 1;
+                    ctl->alpha = a;
+                    ctl->e_trial = tot[j];
+                    ctl->g_trial = tot[j] + c0 + dI;
+                    done = true;
+                    break;
+                }
+                a *= bt;
+            }
+            ctl->trials = tr;
+            if (!done) {
+                ctl->alpha = a;
+                if (tr >= D.c.ls_max) {
+                    ctl->accepted = 0;
+                    ctl->stop = 1;
+                    ctl->status = HQN_WARN_LS_EXHAUSTED;
+                }
+            }
         }
     }
-    if (done) set_cond<R>(h.ls, 0u);
+    batch_condition(s, BT_LS, h.ls, [](const volatile Ctl *x) { return x->active && !x->accepted && !x->stop; });
 }
 
 // ---------------------------------------------------------------- Alg. 2 in dot-product form
@@ -301,10 +397,6 @@ __global__ void __launch_bounds__(BS) k_ls(DevSim<R> s, CondHandles h) {
 // matrix and s_a^T g for the new gradient, the vector passes are q_final, the
 // t_a^T r0 products and d.  The scalars are float64.
 
-__device__ __forceinline__ double dot3d(double ax, double ay, double az, double bx, double by, double bz) {
-    return ax * bx + ay * by + az * bz;
-}
-
 template <typename R>
 __device__ __forceinline__ double dotv(const V4<R> &a, const V4<R> &b) {
     return (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z;
@@ -316,7 +408,7 @@ __device__ __forceinline__ R dotr(const V4<R> &a, const V4<R> &b) {
 }
 
 // The history scalars the recursions need, staged in shared memory by the
-// last block of a kernel: the control block lives in global memory, and a
+// last block of a simulation: the control block lives in global memory, and a
 // recursion run on it directly would pay a memory round trip per step.
 constexpr int MH = HQN_MAX_HISTORY + 1;
 struct HistSmem {
@@ -367,19 +459,23 @@ __device__ __forceinline__ void coef_recursion(HistSmem &h, int m) {
 // corner gradients in a fixed (ascending tet) order -- no atomics.  In G_ITER
 // mode the accepted trial becomes x_{k+1}: the pair s = x_{k+1} - x_k,
 // t = grad_{k+1} - grad_k goes to the free ring slot w, and the block partials
-// of rho = tr(t^T s) (float64 terms) and of |s|^2, |t|^2, s_a^T t_w, s_w^T t_a
-// and s_a^T grad_{k+1} for every ring slot a (R-precision terms and warp sums,
-// float64 beyond) are reduced.  The last block keeps the pair if
-// rho > 1e-12 |s| |t|, updates the Gram matrix and runs the first loop of
-// Alg. 2 on scalars.
+// of rho = tr(t^T s) (float64-accurate terms) and of |s|^2, |t|^2, s_a^T t_w,
+// s_w^T t_a and s_a^T grad_{k+1} for every ring slot a (R-precision terms and
+// block sums, float64 beyond) are reduced.  The simulation's last block keeps
+// the pair if rho > 1e-12 |s| |t|, updates the Gram matrix, runs the first
+// loop of Alg. 2 on scalars and ends the simulation's iterations when its
+// count is reached or its line search gave up.
 template <typename R, int MP1>
 __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandles h) {
-    Ctl *ctl = s.ctl;
-    const int m = s.c.m;
-    const bool stop = mode == G_ITER && ctl->stop;
-    const bool push = mode == G_ITER && m > 0;
+    const SimDesc<R> &D = sim_desc(s, s.vblk_sim);
+    Ctl *ctl = D.ctl;
+    const int m = s.m;
+    const bool iter = mode == G_ITER;
+    const bool act = !iter || ctl->active;
+    const bool stop = iter && ctl->stop;
+    const bool push = iter && m > 0 && act && !stop;
     const int w = push ? (ctl->head + 1) % (m + 1) : 0;
-    const R al = mode == G_ITER ? (R)ctl->alpha : R(0);
+    const R al = iter ? (R)ctl->alpha : R(0);
     constexpr int NG = 2 + 3 * MP1;  // |s|^2, |t|^2, then three products per slot
     constexpr int ND = 1 + NG;
     using A = ExactAcc<R>;
@@ -387,89 +483,80 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
     R dr[NG];
 #pragma unroll
     for (int k = 0; k < NG; ++k) dr[k] = R(0);
-    const size_t n = (size_t)s.c.n;
-    const int i = blockIdx.x * VBS + threadIdx.x;
-    if (!stop && i < s.c.nf) {
-        const int b = s.vt_ptr[i], e = s.vt_ptr[i + 1];
+    const int i = (blockIdx.x - D.vb0) * VBS + threadIdx.x;
+    if (act && !stop && i < D.c.nf) {
+        const int gi = D.v0 + i;
+        const int b = s.vt_ptr[gi], e = s.vt_ptr[gi + 1];
         R gx = R(0), gy = R(0), gz = R(0);
         for (int k = b; k < e; ++k) {
             const V4<R> cg = s.corner[s.vt_slot[k]];
             gx += cg.x; gy += cg.y; gz += cg.z;
         }
-        const V4<R> x = mode == G_ITER ? step_point(s.xk[i], s.d[i], al) : s.xt[i];
-        const V4<R> yy = s.y[i];
-        const R mh = s.mh2[i];
+        const V4<R> x = iter ? step_point(s.xk[gi], s.d[gi], al) : s.xt[gi];
+        const V4<R> yy = s.y[gi];
+        const R mh = s.mh2[gi];
         V4<R> gn;
         gn.x = gx + mh * (x.x - yy.x);
         gn.y = gy + mh * (x.y - yy.y);
         gn.z = gz + mh * (x.z - yy.z);
         gn.w = R(0);
-        if (mode == G_ITER) {
+        if (iter) {
             if (push) {
-                const V4<R> xo = s.xk[i], go = s.gk[i];
+                const V4<R> xo = s.xk[gi], go = s.gk[gi];
                 V4<R> sv, tv;
                 sv.x = x.x - xo.x; sv.y = x.y - xo.y; sv.z = x.z - xo.z; sv.w = R(0);
                 tv.x = gn.x - go.x; tv.y = gn.y - go.y; tv.z = gn.z - go.z; tv.w = R(0);
-                s.S[(size_t)w * n + i] = sv;
-                s.Tt[(size_t)w * n + i] = tv;
+                V4<R> *S = s.S + D.ring0, *Tt = s.Tt + D.ring0;
+                const size_t n = (size_t)D.c.n;
+                S[(size_t)w * n + i] = sv;
+                Tt[(size_t)w * n + i] = tv;
                 dd[0] = A::add_prod(A::add_prod(A::add_prod(dd[0], tv.x, sv.x), tv.y, sv.y), tv.z, sv.z);
                 dr[0] = dotr(sv, sv);
                 dr[1] = dotr(tv, tv);
 #pragma unroll
                 for (int a = 0; a < MP1; ++a) {
                     if (a > m) break;
-                    const V4<R> sa = a == w ? sv : s.S[(size_t)a * n + i];
-                    const V4<R> ta = a == w ? tv : s.Tt[(size_t)a * n + i];
+                    const V4<R> sa = a == w ? sv : S[(size_t)a * n + i];
+                    const V4<R> ta = a == w ? tv : Tt[(size_t)a * n + i];
                     dr[2 + a] = dotr(sa, tv);
                     dr[2 + MP1 + a] = dotr(sv, ta);
                     dr[2 + 2 * MP1 + a] = dotr(sa, gn);
                 }
             }
-            s.xk[i] = x;
+            s.xk[gi] = x;
         }
-        s.gk[i] = gn;
+        s.gk[gi] = gn;
     }
     if (mode == G_EVAL) return;
     double dots[ND];
-    if (push) {
+    {
         double mixed[NG], rho[1];
         block_sum_exact<VBS, 1, R>(dd, rho);
         block_sum_r<VBS, NG, R>(dr, mixed);
         dots[0] = rho[0];
 #pragma unroll
         for (int k = 0; k < NG; ++k) dots[1 + k] = mixed[k];
-        if (!publish_and_arrive<ND>(dots, s.part_g, gridDim.x, &ctl->ticket[TK_GATHER])) return;
-        sum_partials<VBS, ND>(s.part_g, gridDim.x, gridDim.x, dots, &ctl->ticket[TK_GATHER]);
-    } else {
-        double none[1] = {0.0};
-        if (!publish_and_arrive<1>(none, s.part_g, gridDim.x, &ctl->ticket[TK_GATHER])) return;
-        __threadfence();
-        if (threadIdx.x == 0) ctl->ticket[TK_GATHER] = 0u;
     }
-    if (mode == G_INIT) {
-        if (threadIdx.x != 0) return;
-        ctl->k = 1;
-        ctl->count = 0;
-        ctl->head = 0;
-        ctl->g_k = ctl->g_trial;
-        set_cond<R>(h.it, s.c.iters > 0 ? 1u : 0u);
-        return;
-    }
-    const int k = ctl->k;
-    const int kk = k - 1 < HQN_MAX_ITERS ? k - 1 : HQN_MAX_ITERS - 1;
-    if (stop) {
-        if (threadIdx.x != 0) return;
-        ctl->iter_trials[kk] = ctl->trials;
-        ctl->trials_total += ctl->trials;
-        ctl->iters_total += 1;
-        ctl->iter_g[kk] = ctl->g_k;
-        set_cond<R>(h.it, 0u);
-        return;
-    }
+    if (!sim_arrive<ND>(dots, s.part_g, s.nvb, D.nvb, &ctl->ticket[TK_GATHER])) return;
+    __shared__ int keep;
     if (push) {
-        // dots (thread 0): rho, |s|^2, |t|^2, s_a^T t_w, s_w^T t_a, s_a^T grad
+        {
+            // the simulation's partials, one warp per value
+            __shared__ double sh[ND];
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            __threadfence();
+            for (int k = warp; k < ND; k += VBS / 32) {
+                double acc = 0.0;
+                for (int b = lane; b < D.nvb; b += 32) acc += __ldcg(s.part_g + (size_t)k * s.nvb + D.vb0 + b);
+                acc = warp_sum(acc);
+                if (lane == 0) sh[k] = acc;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < ND; ++k) dots[k] = sh[k];
+        }
+        // dots: rho, |s|^2, |t|^2, s_a^T t_w, s_w^T t_a, s_a^T grad
         __shared__ HistSmem hs;
-        __shared__ int keep;
         hist_load(ctl, hs, m);
         if (threadIdx.x == 0) {
             keep = dots[0] > 1e-12 * sqrt(dots[1] * dots[2]);
@@ -503,62 +590,98 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
             ctl->count = hs.count;
         }
     }
-    if (threadIdx.x != 0) return;
-    ctl->iter_trials[kk] = ctl->trials;
-    ctl->trials_total += ctl->trials;
-    ctl->iters_total += 1;
-    ctl->g_k = ctl->g_trial;
-    ctl->e_k = ctl->e_trial;
-    ctl->iter_g[kk] = ctl->g_trial;
-    ctl->k = k + 1;
-    set_cond<R>(h.it, (k + 1 <= s.c.iters) ? 1u : 0u);
+    if (threadIdx.x == 0) {
+        ctl->ticket[TK_GATHER] = 0u;
+        if (mode == G_INIT) {
+            ctl->k = 1;
+            ctl->count = 0;
+            ctl->head = 0;
+            ctl->g_k = ctl->g_trial;
+            ctl->active = D.c.iters > 0 ? 1 : 0;
+        } else if (act) {
+            const int k = ctl->k;
+            const int kk = k - 1 < HQN_MAX_ITERS ? k - 1 : HQN_MAX_ITERS - 1;
+            ctl->iter_trials[kk] = ctl->trials;
+            ctl->trials_total += ctl->trials;
+            ctl->iters_total += 1;
+            if (stop) {
+                ctl->iter_g[kk] = ctl->g_k;
+                ctl->active = 0;
+            } else {
+                ctl->g_k = ctl->g_trial;
+                ctl->e_k = ctl->e_trial;
+                ctl->iter_g[kk] = ctl->g_trial;
+                ctl->k = k + 1;
+                ctl->active = (k + 1 <= D.c.iters) ? 1 : 0;
+            }
+        }
+    }
+    batch_condition(s, BT_IT, h.it, [](const volatile Ctl *x) { return x->active != 0; });
 }
 
 // q = -grad - sum_p zeta_p t_p (the first loop's result).
 template <typename R>
 __global__ void __launch_bounds__(VBS) k_q(DevSim<R> s) {
-    const Ctl *ctl = s.ctl;
-    const int i = blockIdx.x * VBS + threadIdx.x;
-    if (i >= s.c.nf) return;
-    const int count = ctl->count, head = ctl->head, m = s.c.m;
-    const V4<R> g = s.gk[i];
+    const SimDesc<R> &D = sim_desc(s, s.vblk_sim);
+    const Ctl *ctl = D.ctl;
+    const int i = (blockIdx.x - D.vb0) * VBS + threadIdx.x;
+    if (i >= D.c.nf || !ctl->active) return;
+    const int count = ctl->count, head = ctl->head, m = s.m;
+    const int gi = D.v0 + i;
+    const V4<R> g = s.gk[gi];
     V4<R> q;
     q.x = -g.x; q.y = -g.y; q.z = -g.z; q.w = R(0);
+    const V4<R> *Tt = s.Tt + D.ring0;
     for (int p = 0; p < count; ++p) {
         const R z = (R)ctl->zeta[p];
-        const V4<R> t = s.Tt[(size_t)ring_slot(head, p, m) * s.c.n + i];
+        const V4<R> t = Tt[(size_t)ring_slot(head, p, m) * D.c.n + i];
         q.x -= z * t.x; q.y -= z * t.y; q.z -= z * t.z;
     }
-    s.q[i] = q;
+    s.q[gi] = q;
 }
 
 // t_a^T r0 for every ring slot a (r0 = A0^{-1} q, held in d); the last block
 // runs the second loop of Alg. 2 on scalars: c_p = zeta_p - eta_p, oldest first.
 template <typename R, int MP1>
 __global__ void __launch_bounds__(VBS) k_r0_dots(DevSim<R> s) {
-    Ctl *ctl = s.ctl;
-    const int count = ctl->count, m = s.c.m;
-    if (count == 0) return;
+    const SimDesc<R> &D = sim_desc(s, s.vblk_sim);
+    Ctl *ctl = D.ctl;
+    const int count = ctl->count, m = s.m;
+    if (count == 0 || !ctl->active) return;  // the whole simulation skips, tickets untouched
     R dr[MP1];
 #pragma unroll
     for (int a = 0; a < MP1; ++a) dr[a] = R(0);
-    const size_t n = (size_t)s.c.n;
-    const int i = blockIdx.x * VBS + threadIdx.x;
-    if (i < s.c.nf) {
-        const V4<R> r = s.d[i];
+    const int i = (blockIdx.x - D.vb0) * VBS + threadIdx.x;
+    if (i < D.c.nf) {
+        const V4<R> r = s.d[D.v0 + i];
+        const V4<R> *Tt = s.Tt + D.ring0;
 #pragma unroll
         for (int a = 0; a < MP1; ++a) {
             if (a > m) break;
-            dr[a] = dotr(s.Tt[(size_t)a * n + i], r);
+            dr[a] = dotr(Tt[(size_t)a * D.c.n + i], r);
         }
     }
     double dots[MP1];
     block_sum_r<VBS, MP1, R>(dr, dots);
-    if (!publish_and_arrive<MP1>(dots, s.part_v, gridDim.x, &ctl->ticket[TK_VEC])) return;
-    sum_partials<VBS, MP1>(s.part_v, gridDim.x, gridDim.x, dots, &ctl->ticket[TK_VEC]);
+    if (!sim_arrive<MP1>(dots, s.part_v, s.nvb, D.nvb, &ctl->ticket[TK_VEC])) return;
+    {
+        __shared__ double sh[MP1];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        __threadfence();
+        for (int k = warp; k < MP1; k += VBS / 32) {
+            double acc = 0.0;
+            for (int b = lane; b < D.nvb; b += 32) acc += __ldcg(s.part_v + (size_t)k * s.nvb + D.vb0 + b);
+            acc = warp_sum(acc);
+            if (lane == 0) sh[k] = acc;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < MP1; ++k) dots[k] = sh[k];
+    }
     __shared__ HistSmem hs;
     hist_load(ctl, hs, m);
     if (threadIdx.x == 0) {
+        ctl->ticket[TK_VEC] = 0u;
 #pragma unroll
         for (int a = 0; a < MP1; ++a)
             if (a <= m) hs.tr0[a] = dots[a];
@@ -569,26 +692,30 @@ __global__ void __launch_bounds__(VBS) k_r0_dots(DevSim<R> s) {
 }
 
 // d = r0 + sum_p c_p s_p; then gd = tr(grad_k^T d) -- with history and
-// gd >= 0 the direction is not a descent direction: flag it (and set the
-// if-node) so the history is dropped -- and the coefficients of the inertia
-// term along the ray x_k + alpha d:
+// gd >= 0 the direction is not a descent direction: flag it so the history is
+// dropped (h.nd: any simulation flagged) -- and the coefficients of the
+// inertia term along the ray x_k + alpha d:
 // 1/(2h^2) sum m |x_k + alpha d - y|^2 = a0 + a1 alpha + a2 alpha^2.
 template <typename R>
 __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, int set_nd) {
-    Ctl *ctl = s.ctl;
-    const int i = blockIdx.x * VBS + threadIdx.x;
+    const SimDesc<R> &D = sim_desc(s, s.vblk_sim);
+    Ctl *ctl = D.ctl;
+    const bool act = ctl->active;
+    const int i = (blockIdx.x - D.vb0) * VBS + threadIdx.x;
     R d4[4] = {R(0), R(0), R(0), R(0)};
-    if (i < s.c.nf) {
-        V4<R> dd = s.d[i];
-        const int count = ctl->count, head = ctl->head, m = s.c.m;
+    if (act && i < D.c.nf) {
+        const int gi = D.v0 + i;
+        V4<R> dd = s.d[gi];
+        const int count = ctl->count, head = ctl->head, m = s.m;
+        const V4<R> *S = s.S + D.ring0;
         for (int p = 0; p < count; ++p) {
             const R c = (R)ctl->coef[p];
-            const V4<R> sv = s.S[(size_t)ring_slot(head, p, m) * s.c.n + i];
+            const V4<R> sv = S[(size_t)ring_slot(head, p, m) * D.c.n + i];
             dd.x += c * sv.x; dd.y += c * sv.y; dd.z += c * sv.z;
         }
-        if (count > 0) s.d[i] = dd;
-        const V4<R> g = s.gk[i], x = s.xk[i], yy = s.y[i];
-        const R mh = s.mh2[i];
+        if (count > 0) s.d[gi] = dd;
+        const V4<R> g = s.gk[gi], x = s.xk[gi], yy = s.y[gi];
+        const R mh = s.mh2[gi];
         const R rx = x.x - yy.x, ry = x.y - yy.y, rz = x.z - yy.z;
         d4[0] = dotr(g, dd);
         d4[1] = R(0.5) * mh * (rx * rx + ry * ry + rz * rz);
@@ -597,58 +724,88 @@ __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, i
     }
     double tot[4];
     block_sum_r<VBS, 4, R>(d4, tot);
-    if (!publish_and_arrive<4>(tot, s.part_v, gridDim.x, &ctl->ticket[TK_VEC])) return;
-    sum_partials<VBS, 4>(s.part_v, gridDim.x, gridDim.x, tot, &ctl->ticket[TK_VEC]);
-    if (threadIdx.x != 0) return;
-    ctl->gd = tot[0];
-    ctl->ls_a[0] = tot[1];
-    ctl->ls_a[1] = tot[2];
-    ctl->ls_a[2] = tot[3];
-    const int nd = (tot[0] >= 0.0 && ctl->count > 0) ? 1 : 0;
-    ctl->nondescent = nd;
-    if (set_nd) set_cond<R>(h.nd, (unsigned)nd);
+    if (!sim_arrive<4>(tot, s.part_v, s.nvb, D.nvb, &ctl->ticket[TK_VEC])) return;
+    {
+        __shared__ double sh[4];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        __threadfence();
+        if (warp < 4) {
+            double acc = 0.0;
+            for (int b = lane; b < D.nvb; b += 32) acc += __ldcg(s.part_v + (size_t)warp * s.nvb + D.vb0 + b);
+            acc = warp_sum(acc);
+            if (lane == 0) sh[warp] = acc;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 4; ++k) tot[k] = sh[k];
+    }
+    if (threadIdx.x == 0) {
+        ctl->ticket[TK_VEC] = 0u;
+        if (act) {
+            ctl->gd = tot[0];
+            ctl->ls_a[0] = tot[1];
+            ctl->ls_a[1] = tot[2];
+            ctl->ls_a[2] = tot[3];
+            ctl->nondescent = (tot[0] >= 0.0 && ctl->count > 0) ? 1 : 0;
+        } else {
+            ctl->nondescent = 0;
+        }
+    }
+    if (set_nd) batch_condition(s, BT_ND, h.nd, [](const volatile Ctl *x) { return x->nondescent != 0; });
 }
 
+// Drops the history of the simulations whose direction was not a descent
+// direction (the others keep theirs and recompute the same direction).
 template <typename R>
 __global__ void k_reset_history(DevSim<R> s) {
-    s.ctl->count = 0;
-    s.ctl->nondescent = 0;
+    for (int k = threadIdx.x; k < s.nsims; k += blockDim.x) {
+        Ctl *c = s.desc[k].ctl;
+        if (c->nondescent) {
+            c->count = 0;
+            c->nondescent = 0;
+        }
+    }
 }
 
 // q_{l-1} := q_l, q_l := x (end of the time step, Eq. PD).
 template <typename R>
 __global__ void __launch_bounds__(VBS) k_commit(DevSim<R> s) {
-    const int i = blockIdx.x * VBS + threadIdx.x;
-    if (i < s.c.n) {
-        s.u_prev[i] = s.u_cur[i];
-        s.u_cur[i] = s.xk[i];
+    const SimDesc<R> &D = sim_desc(s, s.vblk_sim);
+    const int i = (blockIdx.x - D.vb0) * VBS + threadIdx.x;
+    if (i < D.c.n) {
+        const int g = D.v0 + i;
+        s.u_prev[g] = s.u_cur[g];
+        s.u_cur[g] = s.xk[g];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        Ctl *c = s.ctl;
+    if (blockIdx.x == D.vb0 && threadIdx.x == 0) {
+        Ctl *c = D.ctl;
         c->steps += 1;
         if (c->status > c->worst_status) c->worst_status = c->status;
     }
 }
 
-// Caller-given history (sim_direction): row `a` of the Gram matrix, s_a^T t_b
-// for the slots b < count, rho_a = s_a^T t_a and s_a^T grad.  With
-// a == count - 1 the last block also runs the first loop on scalars.
+// Caller-given history of simulation 0 (sim_direction): row `a` of the Gram
+// matrix, s_a^T t_b for the slots b < count, rho_a = s_a^T t_a and
+// s_a^T grad.  With a == count - 1 the last block also runs the first loop
+// on scalars.  Launched over simulation 0's vertex blocks.
 template <typename R>
 __global__ void __launch_bounds__(VBS) k_hist_row(DevSim<R> s, int a) {
-    Ctl *ctl = s.ctl;
+    const SimDesc<R> &D = s.desc0;
+    Ctl *ctl = D.ctl;
     constexpr int NB = HQN_MAX_HISTORY + 2;
     double dots[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) dots[b] = 0.0;
     const int count = ctl->count;
-    const size_t n = (size_t)s.c.n;
+    const size_t n = (size_t)D.c.n;
     const int i = blockIdx.x * VBS + threadIdx.x;
-    if (i < s.c.nf) {
-        const V4<R> sa = s.S[(size_t)a * n + i];
+    if (i < D.c.nf) {
+        const V4<R> *S = s.S + D.ring0, *Tt = s.Tt + D.ring0;
+        const V4<R> sa = S[(size_t)a * n + i];
 #pragma unroll
         for (int b = 0; b < NB - 1; ++b)
-            if (b < count) dots[b] = dotv(sa, s.Tt[(size_t)b * n + i]);
-        dots[NB - 1] = dotv(sa, s.gk[i]);
+            if (b < count) dots[b] = dotv(sa, Tt[(size_t)b * n + i]);
+        dots[NB - 1] = dotv(sa, s.gk[D.v0 + i]);
     }
     block_sum<VBS, NB>(dots);
     if (!publish_and_arrive<NB>(dots, s.part_g, gridDim.x, &ctl->ticket[TK_GATHER])) return;
@@ -666,78 +823,68 @@ __global__ void __launch_bounds__(VBS) k_hist_row(DevSim<R> s, int a) {
     __threadfence();
     __syncthreads();
     __shared__ HistSmem hs;
-    hist_load(ctl, hs, s.c.m);
+    hist_load(ctl, hs, s.m);
     if (threadIdx.x == 0) {
         for (int b = 0; b < count; ++b) hs.sg[b] = ctl->sg[b];
-        zeta_recursion(hs, s.c.m);
+        zeta_recursion(hs, s.m);
     }
     __syncthreads();
     for (int p = threadIdx.x; p < count; p += VBS) ctl->zeta[p] = hs.zeta[p];
 }
-
-inline int nblk(int n) { return (n + VBS - 1) / VBS; }
 
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
 
 template <typename R> void launch_predict(const DevSim<R> &s, cudaStream_t st) {
-    k_predict<R><<<nblk(s.c.n), VBS, 0, st>>>(s);
+    k_predict<R><<<s.nvb, VBS, 0, st>>>(s);
 }
 template <typename R> void launch_inertia(const DevSim<R> &s, cudaStream_t st) {
-    k_inertia<R><<<nblk(s.c.n), VBS, 0, st>>>(s);
+    k_inertia<R><<<s.nvb, VBS, 0, st>>>(s);
 }
 template <typename R> void launch_tet(const DevSim<R> &s, int mode, CondHandles h, cudaStream_t st) {
-    const int T = s.c.T;
-    switch (s.tet_bs) {
-        case 64: k_tet<R, 64><<<(T + 63) / 64, 64, 0, st>>>(s, mode, h); break;
-        case 256: k_tet<R, 256><<<(T + 255) / 256, 256, 0, st>>>(s, mode, h); break;
-        default: k_tet<R, 128><<<(T + 127) / 128, 128, 0, st>>>(s, mode, h); break;
-    }
+    k_tet<R><<<s.ntb, TBS, 0, st>>>(s, mode, h);
 }
 template <typename R> void launch_ls(const DevSim<R> &s, CondHandles h, cudaStream_t st) {
-    const int T = s.c.T, nb = (T + 127) / 128;
-    switch (s.c.ls_batch) {
-        case 1: k_ls<R, 128, 1><<<nb, 128, 0, st>>>(s, h); break;
-        case 2: k_ls<R, 128, 2><<<nb, 128, 0, st>>>(s, h); break;
-        case 4: k_ls<R, 128, 4><<<nb, 128, 0, st>>>(s, h); break;
-        case 16: k_ls<R, 128, 16><<<nb, 128, 0, st>>>(s, h); break;
-        default: k_ls<R, 128, 8><<<nb, 128, 0, st>>>(s, h); break;
+    switch (s.ls_batch) {
+        case 1: k_ls<R, 1><<<s.ntb, TBS, 0, st>>>(s, h); break;
+        case 2: k_ls<R, 2><<<s.ntb, TBS, 0, st>>>(s, h); break;
+        case 4: k_ls<R, 4><<<s.ntb, TBS, 0, st>>>(s, h); break;
+        case 16: k_ls<R, 16><<<s.ntb, TBS, 0, st>>>(s, h); break;
+        default: k_ls<R, 8><<<s.ntb, TBS, 0, st>>>(s, h); break;
     }
 }
 template <typename R> void launch_gather(const DevSim<R> &s, int mode, CondHandles h, cudaStream_t st) {
-    const int m = s.c.m;
-    const int nb = nblk(s.c.nf);
-    if (m <= 0) k_gather<R, 1><<<nb, VBS, 0, st>>>(s, mode, h);
-    else if (m <= 3) k_gather<R, 4><<<nb, VBS, 0, st>>>(s, mode, h);
-    else if (m <= 5) k_gather<R, 6><<<nb, VBS, 0, st>>>(s, mode, h);
-    else if (m <= 8) k_gather<R, 9><<<nb, VBS, 0, st>>>(s, mode, h);
-    else k_gather<R, HQN_MAX_HISTORY + 1><<<nb, VBS, 0, st>>>(s, mode, h);
+    const int m = s.m;
+    if (m <= 0) k_gather<R, 1><<<s.nvb, VBS, 0, st>>>(s, mode, h);
+    else if (m <= 3) k_gather<R, 4><<<s.nvb, VBS, 0, st>>>(s, mode, h);
+    else if (m <= 5) k_gather<R, 6><<<s.nvb, VBS, 0, st>>>(s, mode, h);
+    else if (m <= 8) k_gather<R, 9><<<s.nvb, VBS, 0, st>>>(s, mode, h);
+    else k_gather<R, HQN_MAX_HISTORY + 1><<<s.nvb, VBS, 0, st>>>(s, mode, h);
 }
 template <typename R> void launch_q(const DevSim<R> &s, cudaStream_t st) {
-    k_q<R><<<nblk(s.c.nf), VBS, 0, st>>>(s);
+    k_q<R><<<s.nvb, VBS, 0, st>>>(s);
 }
 template <typename R> void launch_r0_dots(const DevSim<R> &s, cudaStream_t st) {
-    const int m = s.c.m;
-    const int nb = nblk(s.c.nf);
+    const int m = s.m;
     if (m <= 0) return;
-    if (m <= 3) k_r0_dots<R, 4><<<nb, VBS, 0, st>>>(s);
-    else if (m <= 5) k_r0_dots<R, 6><<<nb, VBS, 0, st>>>(s);
-    else if (m <= 8) k_r0_dots<R, 9><<<nb, VBS, 0, st>>>(s);
-    else k_r0_dots<R, HQN_MAX_HISTORY + 1><<<nb, VBS, 0, st>>>(s);
+    if (m <= 3) k_r0_dots<R, 4><<<s.nvb, VBS, 0, st>>>(s);
+    else if (m <= 5) k_r0_dots<R, 6><<<s.nvb, VBS, 0, st>>>(s);
+    else if (m <= 8) k_r0_dots<R, 9><<<s.nvb, VBS, 0, st>>>(s);
+    else k_r0_dots<R, HQN_MAX_HISTORY + 1><<<s.nvb, VBS, 0, st>>>(s);
 }
 template <typename R>
 void launch_direction_final(const DevSim<R> &s, CondHandles h, int set_nd, cudaStream_t st) {
-    k_dir_final<R><<<nblk(s.c.nf), VBS, 0, st>>>(s, h, set_nd);
+    k_dir_final<R><<<s.nvb, VBS, 0, st>>>(s, h, set_nd);
 }
 template <typename R> void launch_reset_history(const DevSim<R> &s, cudaStream_t st) {
-    k_reset_history<R><<<1, 1, 0, st>>>(s);
+    k_reset_history<R><<<1, 256, 0, st>>>(s);
 }
 template <typename R> void launch_commit(const DevSim<R> &s, cudaStream_t st) {
-    k_commit<R><<<nblk(s.c.n), VBS, 0, st>>>(s);
+    k_commit<R><<<s.nvb, VBS, 0, st>>>(s);
 }
-template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream_t st) {
-    k_hist_row<R><<<nblk(s.c.nf), VBS, 0, st>>>(s, a);
+template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream_t st, int nblocks) {
+    k_hist_row<R><<<nblocks, VBS, 0, st>>>(s, a);
 }
 
 #define HQN_INST(R)                                                                  \
@@ -751,7 +898,7 @@ template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream
     template void launch_direction_final<R>(const DevSim<R> &, CondHandles, int, cudaStream_t); \
     template void launch_reset_history<R>(const DevSim<R> &, cudaStream_t);          \
     template void launch_commit<R>(const DevSim<R> &, cudaStream_t);                 \
-    template void launch_hist_row<R>(const DevSim<R> &, int, cudaStream_t);
+    template void launch_hist_row<R>(const DevSim<R> &, int, cudaStream_t, int);
 
 HQN_INST(float)
 HQN_INST(double)

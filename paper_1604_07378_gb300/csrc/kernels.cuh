@@ -8,37 +8,62 @@
 namespace hqn {
 
 constexpr int VBS = 256;  // threads per block of the vertex kernels
+constexpr int TBS = 128;  // threads per block of the tet kernels
 
-// Device view of one simulation's buffers.
+// One simulation of a batch, as the kernels see it (device-resident).  Every
+// block of a vertex or tet kernel belongs to exactly one simulation.
+template <typename R>
+struct SimDesc {
+    StepConst<R> c;             // n, nf, T, history m, iterations, ... of this simulation
+    MatDev<R> mat;
+    int v0, t0;                 // its first vertex / tet in the batch arrays
+    int vb0, nvb;               // its vertex-kernel blocks [vb0, vb0 + nvb), nvb = ceil(n / VBS)
+    int tb0, ntb;               // its tet-kernel blocks [tb0, tb0 + ntb), ntb = ceil(T / TBS)
+    long long ring0;            // its history ring: S / Tt entries [ring0, ring0 + (m + 1) n)
+    Ctl *ctl;                   // its control block
+};
+
+// Device view of a batch of simulations (a single simulation is a batch of
+// one).  Vertex and tet arrays are the simulations' arrays back to back.
 template <typename R>
 struct DevSim {
-    StepConst<R> c;
-    MatDev<R> mat;
-    int tet_bs;                 // threads per block of the tet kernel (64, 128 or 256)
+    int nsims, m, ls_batch;     // history window and line-search batch (shared)
+    int nvb, ntb;               // blocks of the vertex / tet kernels over the batch
+    int Tn;                     // tets of the batch (stride of the SoA arrays)
+    const SimDesc<R> *desc;     // nsims
+    SimDesc<R> desc0;           // simulation 0, by value (read from kernel parameters when nsims == 1)
+    const int *vblk_sim;        // nvb: the simulation of each vertex-kernel block
+    const int *tblk_sim;        // ntb: the simulation of each tet-kernel block
     // mesh
-    const int4 *tets;           // T
-    const R *dminv;             // 9 x T (SoA), Dm^{-1}[j][b] at (3j + b) * T + t
-    const R *vol;               // T
-    const R *mh2;               // n, m_v / h^2
-    const int *vt_ptr;          // n + 1
-    const int *vt_slot;         // corner slots c * T + t, ascending t per vertex
-    // state and work vectors (n entries each, internal vertex order)
+    const int4 *tets;           // Tn, batch vertex ids
+    const R *dminv;             // 9 x Tn (SoA), Dm^{-1}[j][b] at (3j + b) * Tn + t
+    const R *vol;               // Tn
+    const R *mh2;               // batch vertices: m_v / h^2
+    const int *vt_ptr;          // batch vertices + 1
+    const int *vt_slot;         // corner slots c * Tn + t, ascending t per vertex
+    // state and work vectors (batch vertices, internal order within each simulation)
     V4<R> *u_cur, *u_prev, *y, *xk, *xt, *gk, *d, *q, *z;
-    V4<R> *S, *Tt;              // (m + 1) x n history ring
-    V4<R> *corner;              // 4 x T corner gradients
+    V4<R> *S, *Tt;              // history rings
+    V4<R> *corner;              // 4 x Tn corner gradients
+    // per-block partial sums: part_x[k * (blocks of the kernel) + block]
     double *part_in, *part_el, *part_g, *part_v, *part_ls;
-    Ctl *ctl;
+    unsigned int *batch_ticket; // arrival counters of the simulations' last blocks (graph conditions)
 };
 
 enum TetMode { TET_INIT = 0, TET_GRAD = 1, TET_EVAL = 2, TET_TRIAL1 = 3 };
 enum GatherMode { G_INIT = 0, G_ITER = 1, G_EVAL = 2 };
+// Slots of batch_ticket (one per graph condition).
+enum { BT_IT = 0, BT_LS = 1, BT_ND = 2 };
 
+// Each simulation's decisions (Armijo, history, iteration count) are taken by
+// that simulation's last block; the last simulation to decide sets the graph's
+// conditional handles from all of them (h = 0: not inside a graph).
 template <typename R> void launch_predict(const DevSim<R> &s, cudaStream_t st);
 // Inertia partials of the caller-given point x_t.
 template <typename R> void launch_inertia(const DevSim<R> &s, cudaStream_t st);
 // TET_TRIAL1 is the first line-search trial (alpha = 1) fused with the
 // gradient: it runs the Armijo test and, on acceptance, leaves the corner
-// gradients of the new point in place (TET_GRAD then returns at once).
+// gradients of the new point in place (TET_GRAD then skips that simulation).
 template <typename R> void launch_tet(const DevSim<R> &s, int mode, CondHandles h, cudaStream_t st);
 // One multi-trial line-search pass (K = ls_batch step lengths).
 template <typename R> void launch_ls(const DevSim<R> &s, CondHandles h, cudaStream_t st);
@@ -47,34 +72,46 @@ template <typename R> void launch_gather(const DevSim<R> &s, int mode, CondHandl
 // products with grad are formed by the gather that pushes a pair):
 // q = -grad - sum zeta_p t_p; after the solve, t_a^T r0 and the second loop on
 // scalars; then d = r0 + sum c_p s_p with gd and the inertia coefficients
-// (sets h.nd on a non-descent direction when set_nd).
+// (sets h.nd if any simulation's direction is not a descent direction).
 template <typename R> void launch_q(const DevSim<R> &s, cudaStream_t st);
 template <typename R> void launch_r0_dots(const DevSim<R> &s, cudaStream_t st);
 template <typename R> void launch_direction_final(const DevSim<R> &s, CondHandles h, int set_nd, cudaStream_t st);
+// Drops the history of the simulations flagged non-descent.
 template <typename R> void launch_reset_history(const DevSim<R> &s, cudaStream_t st);
 template <typename R> void launch_commit(const DevSim<R> &s, cudaStream_t st);
-// Caller-given history: Gram row a, rho_a and s_a^T grad (run for a = 0..count-1).
-template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream_t st);
+// Caller-given history of simulation 0: Gram row a, rho_a and s_a^T grad
+// (run for a = 0..count-1).
+template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream_t st, int nblocks);
 
 // ---- triangular solves (solve.cu)
 constexpr int SOLVE_MAX_SMEM = 200 * 1024;  // dynamic shared memory of one sweep block
 
 template <typename R>
 struct DevSolve {
-    int nf, n_levels;
-    int pdl;                    // host: launch the sweeps with programmatic dependent launch
+    int nf, n_levels, n_sn;
+    int pdl;                    // host: launch the level sweeps with programmatic dependent launch
+    int dyn;                    // host: 1 = dependency-driven persistent sweeps, 0 = one launch per level
+    int dyn_grid;               // host: blocks of a persistent sweep
+    int fwd_qmax, fwd_ldmax, bwd_qmax, bwd_ldmax;  // host: shared-memory sizes of the persistent sweeps
+    int n_fwd_items, n_bwd_items;
     const R *QF;                // per supernode: packed Q_s, row-major (layout.hpp)
     const R *QB;                // per supernode: packed Q_s^T, row-major (layout.hpp)
     const int *rows;            // row structures R of the supernodes
     const int2 *fg2;            // per column: the (<= 2) child update entries to subtract
     const int2 *ug2;            // per update entry: the (<= 2) child update entries to add
-    // Work items, 3 int4 each:
-    //   forward  {q0 lo, q0 hi, bytes, G} {col, nc, ldc, uoff} {r0, r1, ldf, off0}
-    //   backward {q0 lo, q0 hi, bytes, G} {col, nc, nrow, roff} {c0, c1, ldr, off0}
+    // Work items, 4 int4 each:
+    //   forward  {q0 lo, q0 hi, bytes, G} {col, nc, ldc, uoff} {r0, r1, ldf, off0} {child0, child1, s, 0}
+    //   backward {q0 lo, q0 hi, bytes, G} {col, nc, nrow, roff} {c0, c1, ldr, off0} {parent, s, 0, 0}
     // q0 = entry offset of the item's first row in QF / QB, bytes = size of its
-    // rows, off0 = offset of that row inside its supernode's block.
+    // rows, off0 = offset of that row inside its supernode's block; -1 = no
+    // such supernode.  Forward items are in ascending, backward items in
+    // descending tree-level order (the dependency-driven queue order).
     const int4 *fwd_items, *bwd_items;
-    const int *fwd_lvl_ptr, *bwd_lvl_ptr;  // host: items of level l in [ptr[l], ptr[l+1])
+    const int *fwd_nitems, *bwd_nitems;    // items of each supernode
+    int *fwd_done, *bwd_done;              // completed items of each supernode (this solve)
+    unsigned int *queue;                   // [0]: forward ticket, [1]: backward ticket
+    const int *fwd_lvl_ptr;                // host: forward items of level l in [ptr[l], ptr[l+1])
+    const int *bwd_lvl_start, *bwd_lvl_cnt;  // host: backward items of level l: [start[l], start[l] + cnt[l])
     const int *fwd_lvl_ld, *bwd_lvl_ld;    // host: max ldc / ldr of the level (shared memory)
     const int *fwd_lvl_q, *bwd_lvl_q;      // host: max factor entries of one item of the level
     V4<R> *u;                   // update vectors
@@ -85,6 +122,8 @@ struct DevSolve {
 template <typename R>
 void launch_solve(const DevSolve<R> &s, const V4<R> *q, V4<R> *z, V4<R> *r, cudaStream_t st);
 template <typename R> int solve_smem_limit_ok(int max_cols);
+// Blocks of one persistent sweep (0 = cannot run the dependency-driven schedule).
+template <typename R> int solve_dyn_grid(const DevSolve<R> &s);
 // Raises the forward sweep's dynamic shared-memory limit (once per device).
 template <typename R> cudaError_t solve_prepare();
 

@@ -62,9 +62,14 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ void bulk_load_start(uint64_t *bar, void *dst, const void *src, uint32_t bytes) {
+// Thread 0, once per block: an mbarrier with one arrival per phase.
+__device__ __forceinline__ void bulk_bar_init(uint64_t *bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Thread 0: the phase's arrival with the byte count to expect, and the copy.
+__device__ __forceinline__ void bulk_load_issue(uint64_t *bar, void *dst, const void *src, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -73,32 +78,33 @@ __device__ __forceinline__ void bulk_load_start(uint64_t *bar, void *dst, const 
                  : "memory");
 }
 
-__device__ __forceinline__ bool bulk_load_wait(uint64_t *bar) {
+__device__ __forceinline__ bool bulk_load_wait(uint64_t *bar, uint32_t parity) {
     for (long long it = 0; it < kWaitPolls; ++it) {
         uint32_t done;
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(smem_addr(bar))
+            : "r"(smem_addr(bar)), "r"(parity)
             : "memory");
         if (done) return true;
     }
     return false;
 }
 
-// Every thread waits for the block's bulk copy.  Returns false (after
-// flagging the error) if it did not complete within the poll bound; the
-// block must then leave without reading the buffer.
-__device__ __forceinline__ bool bulk_load_finish(uint64_t *bar, unsigned int *err) {
+// Every thread waits for the phase `parity` of the block's bulk copy (the
+// barrier's init by thread 0 and this wait are separated by a __syncthreads
+// here).  Returns false (after flagging the error) if it did not complete
+// within the poll bound; the block must then leave without reading the buffer.
+__device__ __forceinline__ bool bulk_load_finish(uint64_t *bar, uint32_t parity, unsigned int *err) {
     __shared__ int timed_out;
     if (threadIdx.x == 0) timed_out = 0;
     __syncthreads();
-    if (!bulk_load_wait(bar)) timed_out = 1;
+    if (!bulk_load_wait(bar, parity)) timed_out = 1;
     __syncthreads();
     if (timed_out) {
         if (threadIdx.x == 0) {
             atomicOr(err, 1u);
-            bulk_load_wait(bar);  // give the copy in flight one more bounded chance to land
+            bulk_load_wait(bar, parity);  // give the copy in flight one more bounded chance to land
         }
         return false;
     }
@@ -116,6 +122,22 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 __device__ __forceinline__ const void *item_src(const void *base, int4 a, int esize) {
     const long long q0 = (long long)(unsigned)a.x | ((long long)a.y << 32);
     return static_cast<const char *>(base) + q0 * esize;
+}
+
+// Vector loads that bypass L1: the sweeps read vectors other blocks of the
+// same grid have just written.
+__device__ __forceinline__ V4<float> ld_cg(const V4<float> *p) {
+    const float4 v = __ldcg(reinterpret_cast<const float4 *>(p));
+    V4<float> o;
+    o.x = v.x; o.y = v.y; o.z = v.z; o.w = v.w;
+    return o;
+}
+__device__ __forceinline__ V4<double> ld_cg(const V4<double> *p) {
+    const double2 a = __ldcg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldcg(reinterpret_cast<const double2 *>(p) + 1);
+    V4<double> o;
+    o.x = a.x; o.y = a.y; o.z = b.x; o.w = b.y;
+    return o;
 }
 
 // ---- forward sweep
@@ -166,8 +188,8 @@ __device__ __forceinline__ void fwd_rows(const DevSolve<R> &S, int col, int nc, 
                     z[col + i] = o;
                 } else {
                     const int2 c = S.ug2[uoff + i - nc];
-                    if (c.x >= 0) { const V4<R> a = S.u[c.x]; o.x += a.x; o.y += a.y; o.z += a.z; }
-                    if (c.y >= 0) { const V4<R> a = S.u[c.y]; o.x += a.x; o.y += a.y; o.z += a.z; }
+                    if (c.x >= 0) { const V4<R> a = ld_cg(S.u + c.x); o.x += a.x; o.y += a.y; o.z += a.z; }
+                    if (c.y >= 0) { const V4<R> a = ld_cg(S.u + c.y); o.x += a.x; o.y += a.y; o.z += a.z; }
                     S.u[uoff + i - nc] = o;
                 }
             }
@@ -175,16 +197,15 @@ __device__ __forceinline__ void fwd_rows(const DevSolve<R> &S, int col, int nc, 
     }
 }
 
-// Dynamic shared memory: [Q rows: qcap entries][f: 3 x ldf entries][child
-// update entries of the columns: ldf int2].
-template <typename R>
-__global__ void __launch_bounds__(SBS) k_fwd(DevSolve<R> S, int item0, int qcap, const V4<R> *rhs, V4<R> *z) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
-    R *qs = reinterpret_cast<R *>(smem_raw);
-    const int4 *rec = S.fwd_items + 3 * (size_t)(item0 + blockIdx.x);
+// One forward work item (record `rec`, 4 int4).  Shared memory: qs = the
+// item's factor rows (qcap entries), then f (3 x ldf entries), then the
+// columns' child update entries (ldf int2).  `wait_inputs` runs between the
+// reads of static data and the reads of vectors other items produce.
+template <typename R, typename Wait>
+__device__ __forceinline__ void fwd_item(const DevSolve<R> &S, const int4 *rec, int qcap, R *qs, uint64_t *bar,
+                                         uint32_t parity, const V4<R> *rhs, V4<R> *z, Wait wait_inputs) {
     const int4 a = rec[0];
-    if (threadIdx.x == 0) bulk_load_start(&bar, qs, item_src(S.QF, a, sizeof(R)), (uint32_t)a.z);
+    if (threadIdx.x == 0) bulk_load_issue(bar, qs, item_src(S.QF, a, sizeof(R)), (uint32_t)a.z);
     const int4 b = rec[1], c = rec[2];
     const int col = b.x, nc = b.y, ldc = b.z, uoff = b.w;
     const int r0 = c.x, r1 = c.y, ldf = c.z, off0 = c.w;
@@ -192,21 +213,24 @@ __global__ void __launch_bounds__(SBS) k_fwd(DevSolve<R> S, int item0, int qcap,
     int2 *cidx = reinterpret_cast<int2 *>(f + 3 * ldf);
     const int nf = ldf < nc ? ldf : nc;
     for (int j = threadIdx.x; j < nf; j += SBS) cidx[j] = S.fg2[col + j];
-    pdl_wait();
-    pdl_trigger();
+    if (!wait_inputs()) {
+        if (threadIdx.x == 0) bulk_load_wait(bar, parity);  // let the copy in flight land first
+        return;
+    }
     // f = q_C - (child updates on C), entries [0, ldf); zero beyond nc
+#pragma unroll 4
     for (int j = threadIdx.x; j < ldf; j += SBS) {
         R vx = R(0), vy = R(0), vz = R(0);
         if (j < nc) {
-            const V4<R> v = rhs[col + j];
+            const V4<R> v = ld_cg(rhs + col + j);
             const int2 ci = cidx[j];
             vx = v.x; vy = v.y; vz = v.z;
-            if (ci.x >= 0) { const V4<R> u = S.u[ci.x]; vx -= u.x; vy -= u.y; vz -= u.z; }
-            if (ci.y >= 0) { const V4<R> u = S.u[ci.y]; vx -= u.x; vy -= u.y; vz -= u.z; }
+            if (ci.x >= 0) { const V4<R> u = ld_cg(S.u + ci.x); vx -= u.x; vy -= u.y; vz -= u.z; }
+            if (ci.y >= 0) { const V4<R> u = ld_cg(S.u + ci.y); vx -= u.x; vy -= u.y; vz -= u.z; }
         }
         f[j] = vx; f[ldf + j] = vy; f[2 * ldf + j] = vz;
     }
-    if (!bulk_load_finish(&bar, S.err)) return;
+    if (!bulk_load_finish(bar, parity, S.err)) return;
     switch (a.w) {
         case 1: fwd_rows<R, 1>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z); break;
         case 2: fwd_rows<R, 2>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z); break;
@@ -215,6 +239,20 @@ __global__ void __launch_bounds__(SBS) k_fwd(DevSolve<R> S, int item0, int qcap,
         case 16: fwd_rows<R, 16>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z); break;
         default: fwd_rows<R, 32>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z); break;
     }
+}
+
+// Level-synchronous schedule: one launch per tree level, one item per block.
+template <typename R>
+__global__ void __launch_bounds__(SBS) k_fwd(DevSolve<R> S, int item0, int qcap, const V4<R> *rhs, V4<R> *z) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) bulk_bar_init(&bar);
+    fwd_item<R>(S, S.fwd_items + 4 * (size_t)(item0 + blockIdx.x), qcap, reinterpret_cast<R *>(smem_raw), &bar, 0u,
+                rhs, z, []() {
+                    pdl_wait();
+                    pdl_trigger();
+                    return true;
+                });
 }
 
 // ---- backward sweep
@@ -263,16 +301,14 @@ __device__ __forceinline__ void bwd_rows(int col, int ldr, int c0, int c1, int o
     }
 }
 
-// Dynamic shared memory: [Q^T rows: qcap entries][w: 3 x lw entries][row
-// indices of the entries of w past nc: lw int].
-template <typename R>
-__global__ void __launch_bounds__(SBS) k_bwd(DevSolve<R> S, int item0, int qcap, const V4<R> *z, V4<R> *r) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
-    R *qs = reinterpret_cast<R *>(smem_raw);
-    const int4 *rec = S.bwd_items + 3 * (size_t)(item0 + blockIdx.x);
+// One backward work item (record `rec`, 4 int4).  Shared memory: qs = the
+// item's factor rows (qcap entries), then w (3 x lw entries), then the row
+// indices of the entries of w past nc (lw int).
+template <typename R, typename Wait>
+__device__ __forceinline__ void bwd_item(const DevSolve<R> &S, const int4 *rec, int qcap, R *qs, uint64_t *bar,
+                                         uint32_t parity, const V4<R> *z, V4<R> *r, Wait wait_inputs) {
     const int4 a = rec[0];
-    if (threadIdx.x == 0) bulk_load_start(&bar, qs, item_src(S.QB, a, sizeof(R)), (uint32_t)a.z);
+    if (threadIdx.x == 0) bulk_load_issue(bar, qs, item_src(S.QB, a, sizeof(R)), (uint32_t)a.z);
     const int4 b = rec[1], c = rec[2];
     const int col = b.x, nc = b.y, nr = b.z, roff = b.w;
     const int c0 = c.x, c1 = c.y, ldr = c.z, off0 = c.w;
@@ -286,21 +322,24 @@ __global__ void __launch_bounds__(SBS) k_bwd(DevSolve<R> S, int item0, int qcap,
         const int i = w0 + k;
         ridx[k] = (i >= nc && i < rows) ? S.rows[roff + i - nc] : -1;
     }
-    pdl_wait();
-    pdl_trigger();
+    if (!wait_inputs()) {
+        if (threadIdx.x == 0) bulk_load_wait(bar, parity);  // let the copy in flight land first
+        return;
+    }
+#pragma unroll 4
     for (int k = threadIdx.x; k < lw; k += SBS) {
         const int i = w0 + k;
         R vx = R(0), vy = R(0), vz = R(0);
         if (i < nc) {
-            const V4<R> v = z[col + i];
+            const V4<R> v = ld_cg(z + col + i);
             vx = v.x; vy = v.y; vz = v.z;
         } else if (ridx[k] >= 0) {
-            const V4<R> v = r[ridx[k]];
+            const V4<R> v = ld_cg(r + ridx[k]);
             vx = -v.x; vy = -v.y; vz = -v.z;
         }
         w[k] = vx; w[lw + k] = vy; w[2 * lw + k] = vz;
     }
-    if (!bulk_load_finish(&bar, S.err)) return;
+    if (!bulk_load_finish(bar, parity, S.err)) return;
     switch (a.w) {
         case 1: bwd_rows<R, 1>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
         case 2: bwd_rows<R, 2>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
@@ -308,6 +347,126 @@ __global__ void __launch_bounds__(SBS) k_bwd(DevSolve<R> S, int item0, int qcap,
         case 8: bwd_rows<R, 8>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
         case 16: bwd_rows<R, 16>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
         default: bwd_rows<R, 32>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(SBS) k_bwd(DevSolve<R> S, int item0, int qcap, const V4<R> *z, V4<R> *r) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) bulk_bar_init(&bar);
+    bwd_item<R>(S, S.bwd_items + 4 * (size_t)(item0 + blockIdx.x), qcap, reinterpret_cast<R *>(smem_raw), &bar, 0u,
+                z, r, []() {
+                    pdl_wait();
+                    pdl_trigger();
+                    return true;
+                });
+}
+
+// ---- dependency-driven schedule: one persistent launch per sweep
+//
+// Blocks take items from a queue (an atomic ticket) in topological order:
+// forward items leaf level first, backward items root level first.  An item
+// waits only for the items it reads from -- a forward item for every item of
+// its supernode's children, a backward item for every item of its parent
+// (whose own inputs were complete before it finished) -- by polling their
+// supernodes' completion counters.  Because items are taken in topological
+// order, every item waited on was taken earlier by a running block, so the
+// waits end.  Each wait is bounded all the same: past the bound the block sets
+// the error flag, and every later wait sees the flag and gives up at once.
+// Each sweep resets the other sweep's counters and queue for the next solve.
+
+constexpr long long kDepPolls = 1 << 22;
+
+// Thread 0 waits until counter[sn] >= need (sn < 0: nothing to wait for).
+__device__ __forceinline__ bool dep_wait(const int *counter, int sn, int need, unsigned int *err) {
+    if (sn < 0) return true;
+    const volatile int *c = counter + sn;
+    for (long long it = 0; it < kDepPolls; ++it) {
+        if (*c >= need) {
+            __threadfence();
+            return true;
+        }
+        if (*(volatile unsigned int *)err) return false;
+        __nanosleep(32);
+    }
+    atomicOr(err, 2u);
+    return false;
+}
+
+// Block-uniform: false once any block has flagged an error.
+__device__ __forceinline__ bool still_ok(const unsigned int *err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) ok = *(const volatile unsigned int *)err == 0u;
+    __syncthreads();
+    return ok != 0;
+}
+
+// After the block's outputs of an item are written: publish them.
+__device__ __forceinline__ void dep_signal(int *counter, int sn) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(counter + sn, 1);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(SBS) k_fwd_dyn(DevSolve<R> S, int qcap, const V4<R> *rhs, V4<R> *z) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int item_sh, ok_sh;
+    R *qs = reinterpret_cast<R *>(smem_raw);
+    for (int i = blockIdx.x * SBS + threadIdx.x; i < S.n_sn; i += gridDim.x * SBS) S.bwd_done[i] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) S.queue[1] = 0;
+    if (threadIdx.x == 0) bulk_bar_init(&bar);
+    uint32_t parity = 0;
+    for (;;) {
+        if (threadIdx.x == 0) item_sh = (int)atomicAdd(&S.queue[0], 1u);
+        __syncthreads();
+        const int item = item_sh;
+        if (item >= S.n_fwd_items) break;
+        const int4 *rec = S.fwd_items + 4 * (size_t)item;
+        const int4 dep = rec[3];  // children c0, c1 (-1: none), own supernode
+        fwd_item<R>(S, rec, qcap, qs, &bar, parity, rhs, z, [&]() {
+            if (threadIdx.x == 0)
+                ok_sh = dep_wait(S.fwd_done, dep.x, dep.x >= 0 ? S.fwd_nitems[dep.x] : 0, S.err) &&
+                        dep_wait(S.fwd_done, dep.y, dep.y >= 0 ? S.fwd_nitems[dep.y] : 0, S.err);
+            __syncthreads();
+            return ok_sh != 0;
+        });
+        if (!still_ok(S.err)) break;
+        dep_signal(S.fwd_done, dep.z);
+        parity ^= 1u;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(SBS) k_bwd_dyn(DevSolve<R> S, int qcap, const V4<R> *z, V4<R> *r) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int item_sh, ok_sh;
+    R *qs = reinterpret_cast<R *>(smem_raw);
+    for (int i = blockIdx.x * SBS + threadIdx.x; i < S.n_sn; i += gridDim.x * SBS) S.fwd_done[i] = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) S.queue[0] = 0;
+    if (threadIdx.x == 0) bulk_bar_init(&bar);
+    uint32_t parity = 0;
+    for (;;) {
+        if (threadIdx.x == 0) item_sh = (int)atomicAdd(&S.queue[1], 1u);
+        __syncthreads();
+        const int item = item_sh;
+        if (item >= S.n_bwd_items) break;
+        const int4 *rec = S.bwd_items + 4 * (size_t)item;
+        const int4 dep = rec[3];  // parent (-1: none), own supernode
+        bwd_item<R>(S, rec, qcap, qs, &bar, parity, z, r, [&]() {
+            if (threadIdx.x == 0) ok_sh = dep_wait(S.bwd_done, dep.x, dep.x >= 0 ? S.bwd_nitems[dep.x] : 0, S.err);
+            __syncthreads();
+            return ok_sh != 0;
+        });
+        if (!still_ok(S.err)) break;
+        dep_signal(S.bwd_done, dep.y);
+        parity ^= 1u;
     }
 }
 
@@ -344,12 +503,21 @@ template <typename R> int solve_smem_limit_ok(int max_ld) {
 
 template <typename R> cudaError_t solve_prepare() {
     cudaError_t e = cudaFuncSetAttribute(k_fwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_MAX_SMEM);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_bwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_MAX_SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_MAX_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fwd_dyn<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_MAX_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_bwd_dyn<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_MAX_SMEM);
+    return e;
 }
 
 template <typename R>
 void launch_solve(const DevSolve<R> &s, const V4<R> *q, V4<R> *z, V4<R> *r, cudaStream_t st) {
+    if (s.dyn) {
+        k_fwd_dyn<R><<<s.dyn_grid, SBS, sweep_smem<R>(s.fwd_qmax, s.fwd_ldmax), st>>>(s, s.fwd_qmax, q, z);
+        k_bwd_dyn<R><<<s.dyn_grid, SBS, sweep_smem<R>(s.bwd_qmax, s.bwd_ldmax), st>>>(s, s.bwd_qmax, z, r);
+        return;
+    }
     for (int l = 0; l < s.n_levels; ++l) {
         const int a = s.fwd_lvl_ptr[l], b = s.fwd_lvl_ptr[l + 1];
         if (b > a)
@@ -358,16 +526,35 @@ void launch_solve(const DevSolve<R> &s, const V4<R> *q, V4<R> *z, V4<R> *r, cuda
                                                      s.fwd_lvl_q[l], q, z);
     }
     for (int l = s.n_levels - 1; l >= 0; --l) {
-        const int a = s.bwd_lvl_ptr[l], b = s.bwd_lvl_ptr[l + 1];
-        if (b > a)
-            launch_level<R, const V4<R> *, V4<R> *>(s.pdl != 0, k_bwd<R>, b - a,
+        const int a = s.bwd_lvl_start[l], cnt = s.bwd_lvl_cnt[l];
+        if (cnt > 0)
+            launch_level<R, const V4<R> *, V4<R> *>(s.pdl != 0, k_bwd<R>, cnt,
                                                      sweep_smem<R>(s.bwd_lvl_q[l], s.bwd_lvl_ld[l]), st, s, a,
                                                      s.bwd_lvl_q[l], (const V4<R> *)z, r);
     }
 }
 
+// Blocks of the persistent sweeps that fit on the device at once (the grid of
+// the dependency-driven schedule must be co-resident only for speed, not for
+// progress: items are taken in topological order).
+template <typename R> int solve_dyn_grid(const DevSolve<R> &s) {
+    int dev = 0, sms = 0, per_sm_f = 0, per_sm_b = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_fwd_dyn<R>, SBS,
+                                                      sweep_smem<R>(s.fwd_qmax, s.fwd_ldmax)) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k_bwd_dyn<R>, SBS,
+                                                      sweep_smem<R>(s.bwd_qmax, s.bwd_ldmax)) != cudaSuccess)
+        return 0;
+    const int per_sm = per_sm_f < per_sm_b ? per_sm_f : per_sm_b;
+    return per_sm > 0 ? per_sm * sms : 0;
+}
+
 template void launch_solve<float>(const DevSolve<float> &, const V4<float> *, V4<float> *, V4<float> *, cudaStream_t);
 template void launch_solve<double>(const DevSolve<double> &, const V4<double> *, V4<double> *, V4<double> *, cudaStream_t);
+template int solve_dyn_grid<float>(const DevSolve<float> &);
+template int solve_dyn_grid<double>(const DevSolve<double> &);
 template int solve_smem_limit_ok<float>(int);
 template int solve_smem_limit_ok<double>(int);
 template cudaError_t solve_prepare<float>();

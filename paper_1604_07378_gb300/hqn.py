@@ -50,7 +50,7 @@ class Params(C.Structure):
                 ("x_start", C.c_double), ("x_end", C.c_double), ("gravity", C.c_double * 3),
                 ("iters", C.c_int32), ("history_m", C.c_int32), ("ls_max", C.c_int32),
                 ("precision", C.c_int32), ("leaf_size", C.c_int32), ("use_graph", C.c_int32),
-                ("tet_block", C.c_int32), ("ls_batch", C.c_int32)]
+                ("tet_block", C.c_int32), ("ls_batch", C.c_int32), ("dyn_sweeps", C.c_int32)]
 
 
 class StepStats(C.Structure):
@@ -67,7 +67,7 @@ class Info(C.Structure):
                 ("stiffness_k", C.c_double), ("setup_seconds", C.c_double),
                 ("device_bytes", C.c_int64), ("precision", C.c_int32),
                 ("graph_mode", C.c_int32), ("n_update_entries", C.c_int64),
-                ("chained_sweeps", C.c_int32)]
+                ("chained_sweeps", C.c_int32), ("sweep_schedule", C.c_int32), ("n_sims", C.c_int32)]
 
 
 _lib = None
@@ -88,6 +88,14 @@ def library(path: str | None = None):
     lib.sim_create.argtypes = [C.POINTER(Mesh), C.POINTER(Material), C.POINTER(Params), C.c_void_p,
                                C.POINTER(C.c_void_p)]
     lib.sim_create.restype = C.c_int
+    lib.sim_batch_create.argtypes = [C.c_int32, C.POINTER(Mesh), C.POINTER(Material), C.POINTER(Params),
+                                     C.c_void_p, C.POINTER(C.c_void_p)]
+    lib.sim_batch_create.restype = C.c_int
+    lib.sim_batch_count.argtypes = [C.c_void_p]
+    lib.sim_batch_count.restype = C.c_int32
+    lib.sim_batch_set_state.argtypes = [C.c_void_p, C.c_int32, _dp, _dp]
+    lib.sim_batch_get_state.argtypes = [C.c_void_p, C.c_int32, _dp, _dp]
+    lib.sim_batch_get_stats.argtypes = [C.c_void_p, C.c_int32, C.POINTER(StepStats)]
     lib.sim_set_state.argtypes = [C.c_void_p, _dp, _dp]
     lib.sim_get_state.argtypes = [C.c_void_p, _dp, _dp]
     lib.sim_step.argtypes = [C.c_void_p, C.c_int32, C.POINTER(StepStats)]
@@ -107,7 +115,8 @@ def library(path: str | None = None):
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.hqn_energy_grad_static.restype = C.c_int
     for f in ("sim_set_state", "sim_get_state", "sim_step", "sim_energy_grad", "sim_solve_A0",
-              "sim_direction", "sim_get_info", "sim_time_stage"):
+              "sim_direction", "sim_get_info", "sim_time_stage", "sim_batch_set_state",
+              "sim_batch_get_state", "sim_batch_get_stats"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -251,6 +260,106 @@ class Sim:
     def time_stage(self, stage, reps=20):
         """Mean device milliseconds of one launch of a stage (CUDA events on the
         handle's stream)."""
+        ms = C.c_double()
+        _check(library().sim_time_stage(self._h, stage, reps, C.byref(ms)), "sim_time_stage")
+        return ms.value
+
+    def info(self) -> dict:
+        i = Info()
+        _check(library().sim_get_info(self._h, C.byref(i)), "sim_get_info")
+        return {f: getattr(i, f) for f, _ in Info._fields_}
+
+
+class Batch:
+    """A batch of independent simulations advanced together (``sim_batch_create``).
+
+    ``workloads`` is a list of objects with the fields of ``workloads.Workload``
+    (mesh, clamps, material); the parameters (h, iterations, history window,
+    precision, ...) are shared and come from ``pkw`` / ``params``.
+    """
+
+    def __init__(self, workloads, *, params: Params | None = None, stream=None, **pkw):
+        lib = library()
+        ws = list(workloads)
+        if not ws:
+            raise ValueError("empty batch")
+        self._keep = []
+        meshes = (Mesh * len(ws))()
+        mats = (Material * len(ws))()
+        self.n = []
+        for k, w in enumerate(ws):
+            X = np.ascontiguousarray(w.rest_pos, dtype=np.float64)
+            tets = np.ascontiguousarray(w.tets, dtype=np.int32)
+            cl = None if w.clamped is None else np.ascontiguousarray(w.clamped, dtype=np.uint8)
+            m = w.material
+            sp = None if m.spline is None else np.ascontiguousarray(m.spline, dtype=np.float64)
+            self._keep += [X, tets, cl, sp]
+            meshes[k] = Mesh(X.shape[0], tets.shape[0], _ptr(X), _ptr(tets, _ip),
+                             None if cl is None else _ptr(cl, _up))
+            mats[k] = Material(m.kind, m.E, m.nu, m.density, None if sp is None else _ptr(sp))
+            self.n.append(X.shape[0])
+        w0 = ws[0]
+        pkw.setdefault("iters", w0.iters)
+        pkw.setdefault("history_m", w0.history)
+        pkw.setdefault("h", w0.h)
+        pkw.setdefault("gravity", w0.gravity)
+        self.params = params if params is not None else default_params(**pkw)
+        h = C.c_void_p()
+        _check(lib.sim_batch_create(len(ws), meshes, mats, C.byref(self.params), C.c_void_p(stream or 0),
+                                    C.byref(h)), "sim_batch_create")
+        self._h = h
+        self.count = len(ws)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            library().sim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _vec(self, i, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if a.shape != (self.n[i], 3):
+            raise ValueError(f"expected shape ({self.n[i]}, 3), got {a.shape}")
+        return a
+
+    def set_state(self, i, q_cur, q_prev=None):
+        qc = self._vec(i, q_cur)
+        qp = None if q_prev is None else self._vec(i, q_prev)
+        _check(library().sim_batch_set_state(self._h, i, _ptr(qc), None if qp is None else _ptr(qp)),
+               "sim_batch_set_state")
+
+    def get_state(self, i):
+        qc = np.empty((self.n[i], 3))
+        qp = np.empty((self.n[i], 3))
+        _check(library().sim_batch_get_state(self._h, i, _ptr(qc), _ptr(qp)), "sim_batch_get_state")
+        return qc, qp
+
+    def step(self, nsteps=1):
+        st = StepStats()
+        rc = _check(library().sim_step(self._h, nsteps, C.byref(st)), "sim_step")
+        return rc, {"trials_total": st.trials_total, "iters_total": st.iters_total,
+                    "ls_passes_total": st.ls_passes_total, "status": st.status}
+
+    def stats(self, i):
+        st = StepStats()
+        _check(library().sim_batch_get_stats(self._h, i, C.byref(st)), "sim_batch_get_stats")
+        k = st.iters
+        return {"steps": st.steps, "iters": k, "status": st.status, "trials_total": st.trials_total,
+                "iters_total": st.iters_total, "trials": list(st.trials[:k]), "g0": st.g0,
+                "g": list(st.g[:k]), "ls_passes_total": st.ls_passes_total}
+
+    def time_stage(self, stage, reps=20):
         ms = C.c_double()
         _check(library().sim_time_stage(self._h, stage, reps, C.byref(ms)), "sim_time_stage")
         return ms.value

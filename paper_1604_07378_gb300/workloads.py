@@ -110,28 +110,52 @@ def kuhn_lattice(nx: int, ny: int, nz: int, edge: float = 0.05):
     return pos, tets
 
 
+def _integrate_curvature(x, sig, one, v_one, d_one):
+    """Values and slopes at the knots x of the function whose second
+    derivative is linear between the knot values sig, with value v_one and
+    slope d_one at knot `one` (a C2 cubic spline; cubic Hermite interpolation
+    of the returned data reproduces it exactly)."""
+    v = np.zeros_like(x)
+    d = np.zeros_like(x)
+    v[one], d[one] = v_one, d_one
+    for i in range(one, x.size - 1):
+        h = x[i + 1] - x[i]
+        d[i + 1] = d[i] + h * (sig[i] + sig[i + 1]) / 2.0
+        v[i + 1] = v[i] + h * d[i] + h * h * (2.0 * sig[i] + sig[i + 1]) / 6.0
+    for i in range(one, 0, -1):
+        h = x[i] - x[i - 1]
+        d[i - 1] = d[i] - h * (sig[i - 1] + sig[i]) / 2.0
+        v[i - 1] = v[i] - h * d[i] + h * h * (sig[i - 1] + 2.0 * sig[i]) / 6.0
+    return v, d
+
+
 def spline_control_points(mu: float, lam: float, rng: np.random.Generator,
                           spread: float = 0.3) -> np.ndarray:
     """Control points of a synthetic spline Valanis-Landel material.
 
-    The base curves are the Neo-Hookean choice a(x) = mu/2 (x^2 - 1), b = 0,
-    c(J) = -mu ln J + lam/2 ln^2 J, sampled at the knots; every value and slope
-    is scaled by (1 + u) with u ~ U[-spread, spread].  The slope of c at J = 1
-    is then set so that a'(1) + 2 b'(1) + c'(1) = 0 (stress-free rest state).
+    The base is the Neo-Hookean choice a(x) = mu/2 (x^2 - 1), b = 0,
+    c(J) = -mu ln J + lam/2 ln^2 J.  At every knot the base curve's second
+    derivative (a'' = mu, c'' = (mu + lam - lam ln J) / J^2) is scaled by
+    (1 + u), u ~ U[-spread, spread]; values and slopes are the exact
+    integrals of that piecewise-linear curvature, anchored at 1 with the base
+    values a(1) = c(1) = 0, a'(1) = mu and c'(1) = -a'(1) - 2 b'(1) (a
+    stress-free rest state).  So each curve stays within a few tens of percent
+    of the Neo-Hookean one and is convex with positive curvature at the end
+    knots: the energy is bounded below, as a time step needs.  b stays 0.
     Returns (3, 8, 3): function (a, b, c) x knot x (knot, value, slope).
     """
     k = np.asarray(SPLINE_KNOTS, dtype=np.float64)
-    a_v, a_s = 0.5 * mu * (k * k - 1.0), mu * k
-    b_v, b_s = np.zeros_like(k), np.zeros_like(k)
-    lk = np.log(k)
-    c_v, c_s = -mu * lk + 0.5 * lam * lk * lk, (-mu + lam * lk) / k
-    out = np.zeros((3, k.size, 3))
-    for f, (v, s) in enumerate(((a_v, a_s), (b_v, b_s), (c_v, c_s))):
-        out[f, :, 0] = k
-        out[f, :, 1] = v * (1.0 + rng.uniform(-spread, spread, k.size))
-        out[f, :, 2] = s * (1.0 + rng.uniform(-spread, spread, k.size))
     one = int(np.argmin(np.abs(k - 1.0)))
-    out[2, one, 2] = -(out[0, one, 2] + 2.0 * out[1, one, 2])
+    lk = np.log(k)
+    sig_a = mu * (1.0 + rng.uniform(-spread, spread, k.size))
+    sig_c = (mu + lam - lam * lk) / (k * k) * (1.0 + rng.uniform(-spread, spread, k.size))
+    a_v, a_s = _integrate_curvature(k, sig_a, one, 0.0, mu)
+    c_v, c_s = _integrate_curvature(k, sig_c, one, 0.0, -mu)
+    out = np.zeros((3, k.size, 3))
+    for f, (v, s) in enumerate(((a_v, a_s), (np.zeros_like(k), np.zeros_like(k)), (c_v, c_s))):
+        out[f, :, 0] = k
+        out[f, :, 1] = v
+        out[f, :, 2] = s
     return out
 
 

@@ -82,11 +82,13 @@ def test_energy_gradient_other_materials(kind):
 
 @pytest.mark.parametrize("w", WORKLOADS[:3], ids=IDS[:3])
 @pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
-def test_solve_A0_parity(w, prec):
+@pytest.mark.parametrize("dyn_sweeps", [0, 1], ids=["levels", "dependency"])
+def test_solve_A0_parity(w, prec, dyn_sweeps):
     P = problem_for(w)
     rng = np.random.default_rng(4)
     q = rng.normal(size=(w.n_verts, 3))
-    with sim_for(w, prec, use_graph=0) as sim:
+    with sim_for(w, prec, use_graph=0, dyn_sweeps=dyn_sweeps) as sim:
+        assert sim.info()["sweep_schedule"] == dyn_sweeps
         r = sim.solve_A0(q)
     r_ref = O.solve_A(P, q)
     assert rel(r, r_ref) <= (1e-11 if prec == FP64 else 2e-5)
@@ -148,6 +150,21 @@ def test_step_parity_graph(w, prec):
     stats, st, qc, x_ref = _step_parity(w, prec, 1, 1e-9 if prec == FP64 else 1e-4)
     if prec == FP64:
         assert stats["trials"] == st.trials
+
+
+def test_sweep_schedules_agree_bitwise():
+    """The dependency-driven and the per-level sweeps do the same arithmetic
+    on every output, so whole steps agree bit for bit; repeated solves on one
+    handle (the counters reset between sweeps) too."""
+    w = WORKLOADS[1]
+    out = []
+    for dyn in (0, 1, 1):
+        with sim_for(w, FP32, use_graph=1, dyn_sweeps=dyn) as sim:
+            sim.set_state(w.q_cur, w.q_prev)
+            sim.step(3)
+            out.append(sim.get_state()[0])
+    np.testing.assert_array_equal(out[0], out[1])
+    np.testing.assert_array_equal(out[0], out[2])
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
