@@ -363,10 +363,12 @@ struct Sim final : SimBase {
         std::vector<std::vector<int4>> frec(L), brec(L);
         fwd_ld.assign(L, 0); fwd_q.assign(L, 0); bwd_ld.assign(L, 0); bwd_q.assign(L, 0);
         std::vector<int> nit_f((size_t)sn_tot, 0), nit_b((size_t)sn_tot, 0);
+        int cb0 = 0;
         for (int k = 0; k < ns; ++k) {
             const Setup &s = S[k];
             int roff0 = 0;
             for (int kk = 0; kk < k; ++kk) roff0 += (int)S[kk].rows.size();
+            if (k > 0) cb0 += S[k - 1].n_bwd_blocks;
             for (const SupernodeHost &sn : s.sn)
                 if (sn.children.size() > 2) return fail(HQN_ERR_UNSUPPORTED, "a supernode has more than two children");
             for (int l = 0; l < s.n_levels; ++l) {
@@ -390,13 +392,22 @@ struct Sim final : SimBase {
                 for (int e = s.bwd_lvl_ptr[l]; e < s.bwd_lvl_ptr[l + 1]; ++e) {
                     const BwdItem &b = s.bwd_items[e];
                     const SupernodeHost &sn = s.sn[b.s];
-                    const int64_t o0 = bwd_row_off(b.col0, sn.ldr), o1 = bwd_row_off(b.col1, sn.ldr);
-                    const int64_t q0 = qb0[k] + sn.qb + o0;
+                    int64_t o0 = bwd_row_off(b.col0, sn.ldr), q0, bytes;
+                    if (b.e0 < 0) {  // whole rows: one contiguous block from row col0 on
+                        q0 = qb0[k] + sn.qb + o0;
+                        bytes = (bwd_row_off(b.col1, sn.ldr) - o0) * (int64_t)sizeof(R);
+                    } else {  // a chunk: each row's piece [max(e0, start_j), e1)
+                        q0 = qb0[k] + sn.qb;
+                        bytes = 0;
+                        for (int j = b.col0; j < b.col1; ++j)
+                            bytes += std::max(0, b.e1 - std::max(b.e0, bwd_row_start(j))) * (int64_t)sizeof(R);
+                    }
                     auto &v = brec[l];
-                    v.push_back(make_int4((int)(q0 & 0xffffffffLL), (int)(q0 >> 32), (int)((o1 - o0) * sizeof(R)), b.G));
+                    v.push_back(make_int4((int)(q0 & 0xffffffffLL), (int)(q0 >> 32), (int)bytes, b.G));
                     v.push_back(make_int4(v0[k] + sn.col, sn.ncol, sn.nrow, roff0 + sn.roff));
                     v.push_back(make_int4(b.col0, b.col1, sn.ldr, (int)o0));
                     v.push_back(make_int4(sn.parent >= 0 ? sn0[k] + sn.parent : -1, sn0[k] + b.s, 0, 0));
+                    v.push_back(make_int4(b.e0, b.e1, b.cb >= 0 ? cb0 + b.cb : -1, (b.nch << 16) | b.k));
                     nit_b[sn0[k] + b.s]++;
                 }
             }
@@ -411,10 +422,12 @@ struct Sim final : SimBase {
         bwd_start.assign(L, 0);
         bwd_cnt.assign(L, 0);
         for (int l = L - 1; l >= 0; --l) {
-            bwd_start[l] = (int)(bi.size() / 4);
-            bwd_cnt[l] = (int)(brec[l].size() / 4);
+            bwd_start[l] = (int)(bi.size() / 5);
+            bwd_cnt[l] = (int)(brec[l].size() / 5);
             bi.insert(bi.end(), brec[l].begin(), brec[l].end());
         }
+        int n_cb = 0;
+        for (const Setup &s : S) n_cb += s.n_bwd_blocks;
         const int4 *p_fi, *p_bi;
         const int *p_nf, *p_nb;
         if ((rc = upload(p_fi, fi.data(), fi.size()))) return rc;
@@ -429,7 +442,9 @@ struct Sim final : SimBase {
         dsol.n_sn = (int)sn_tot;
         dsol.nf = (int)nf_tot;
         dsol.n_fwd_items = (int)(fi.size() / 4);
-        dsol.n_bwd_items = (int)(bi.size() / 4);
+        dsol.n_bwd_items = (int)(bi.size() / 5);
+        if ((rc = alloc(dsol.part_r, (size_t)std::max(1, dsol.n_bwd_items) * 32))) return rc;
+        if ((rc = alloc(dsol.cb_cnt, (size_t)std::max(1, n_cb)))) return rc;
         dsol.fwd_lvl_ptr = fwd_ptr.data();
         dsol.bwd_lvl_start = bwd_start.data();
         dsol.bwd_lvl_cnt = bwd_cnt.data();

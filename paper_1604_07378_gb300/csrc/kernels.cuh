@@ -99,9 +99,11 @@ struct DevSolve {
     const int *rows;            // row structures R of the supernodes
     const int2 *fg2;            // per column: the (<= 2) child update entries to subtract
     const int2 *ug2;            // per update entry: the (<= 2) child update entries to add
-    // Work items, 4 int4 each:
+    // Work items, 4 int4 each (backward: 5):
     //   forward  {q0 lo, q0 hi, bytes, G} {col, nc, ldc, uoff} {r0, r1, ldf, off0} {child0, child1, s, 0}
     //   backward {q0 lo, q0 hi, bytes, G} {col, nc, nrow, roff} {c0, c1, ldr, off0} {parent, s, 0, 0}
+    //            {e0, e1, column block, nch << 16 | chunk}  (e0 < 0: whole rows; chunk items
+    //            have q0 = their supernode's block, bytes = the sum of their rows' pieces)
     // q0 = entry offset of the item's first row in QF / QB, bytes = size of its
     // rows, off0 = offset of that row inside its supernode's block; -1 = no
     // such supernode.  Forward items are in ascending, backward items in
@@ -115,6 +117,8 @@ struct DevSolve {
     const int *fwd_lvl_ld, *bwd_lvl_ld;    // host: max ldc / ldr of the level (shared memory)
     const int *fwd_lvl_q, *bwd_lvl_q;      // host: max factor entries of one item of the level
     V4<R> *u;                   // update vectors
+    V4<R> *part_r;              // 32 partial sums per backward item (chunk items)
+    int *cb_cnt;                // chunks finished per backward column block (re-arms itself)
     unsigned int *err;          // set nonzero if a bulk copy did not arrive in time
 };
 

@@ -680,15 +680,40 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
         }
     }
     S.fwd_lvl_ptr[L] = (int)S.fwd_items.size();
-    // backward: tree level l (launched from the root level down)
+    // backward: tree level l (launched from the root level down).  Rows of
+    // Q_s^T longer than kLongRow entries are split into chunks of 32 rows x
+    // kChunk entries, so an item gathers a short piece of w instead of the
+    // whole vector (a few columns per item would otherwise each gather all of it).
+    constexpr int kBlockCols = 32;
+    const int kChunk = VN == 4 ? 256 : 128;
+    const int kLongRow = 4 * kChunk;
+    S.n_bwd_blocks = 0;
     for (int l = 0; l < L; ++l) {
         const int target = (int)std::min<int64_t>(kMax, std::max<int64_t>(kMin, lvl_entries[l] / 400));
         S.bwd_lvl_ptr[l] = (int)S.bwd_items.size();
         for (int s = 0; s < ns; ++s) {
             const SupernodeHost &sn = S.sn[s];
             if (sn.level != l || sn.ncol == 0) continue;
-            S.bwd_lvl_ld[l] = std::max(S.bwd_lvl_ld[l], sn.ldr);
             for (int c0 = 0; c0 < sn.ncol;) {
+                const int w0 = bwd_row_start(c0);
+                if (sn.ldr - w0 > kLongRow) {
+                    const int c1 = std::min(sn.ncol, c0 + kBlockCols);
+                    const int nch = (sn.ldr - w0 + kChunk - 1) / kChunk;
+                    for (int k = 0; k < nch; ++k) {
+                        BwdItem it{s, c0, c1, lanes_for(kChunk)};
+                        it.e0 = w0 + k * kChunk;
+                        it.e1 = std::min(sn.ldr, it.e0 + kChunk);
+                        it.cb = S.n_bwd_blocks;
+                        it.nch = nch;
+                        it.k = k;
+                        S.bwd_lvl_q[l] = std::max(S.bwd_lvl_q[l], (c1 - c0) * (it.e1 - it.e0));
+                        S.bwd_lvl_ld[l] = std::max(S.bwd_lvl_ld[l], it.e1 - it.e0);
+                        S.bwd_items.push_back(it);
+                    }
+                    ++S.n_bwd_blocks;
+                    c0 = c1;
+                    continue;
+                }
                 int c1 = c0 + 1;
                 while (c1 < sn.ncol && bwd_row_off(c1 + 1, sn.ldr) - bwd_row_off(c0, sn.ldr) <= target) ++c1;
                 const int entries = (int)(bwd_row_off(c1, sn.ldr) - bwd_row_off(c0, sn.ldr));
@@ -697,7 +722,8 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
                     return HQN_ERR_UNSUPPORTED;
                 }
                 S.bwd_lvl_q[l] = std::max(S.bwd_lvl_q[l], entries);
-                S.bwd_items.push_back({s, c0, c1, lanes_for(sn.ldr - bwd_row_start(c0))});
+                S.bwd_lvl_ld[l] = std::max(S.bwd_lvl_ld[l], sn.ldr - w0);
+                S.bwd_items.push_back({s, c0, c1, lanes_for(sn.ldr - w0)});
                 c0 = c1;
             }
         }

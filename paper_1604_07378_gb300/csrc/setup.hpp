@@ -37,7 +37,11 @@ struct SupernodeHost {
 
 // Work items of the device sweeps.  G = lanes that share one output row.
 struct FwdItem { int s, row0, row1, G; };  // rows [row0, row1) of Q_s f
-struct BwdItem { int s, col0, col1, G; };  // entries [col0, col1) of Q_s^T w
+// Backward item: rows [col0, col1) of Q_s^T times w.  A whole-row item
+// (e0 < 0) covers each row from its diagonal to the end; a chunk item covers
+// only the entries [e0, e1) of its rows and adds a partial sum, which the last
+// of the column block's nch chunks to finish (chunk k of block cb) combines.
+struct BwdItem { int s, col0, col1, G, e0 = -1, e1 = 0, cb = -1, nch = 1, k = 0; };
 
 struct Setup {
     int n = 0, T = 0, n_free = 0;
@@ -64,6 +68,7 @@ struct Setup {
     std::vector<int> fwd_lvl_ptr, bwd_lvl_ptr;  // items of level l: [ptr[l], ptr[l+1])
     std::vector<int> fwd_lvl_ld, bwd_lvl_ld;    // max ldc / ldr over the level's supernodes
     std::vector<int> fwd_lvl_q, bwd_lvl_q;      // max factor entries of one work item of the level
+    int n_bwd_blocks = 0;            // column blocks of the backward chunk items
     std::vector<FwdItem> fwd_items;
     std::vector<BwdItem> bwd_items;
     int64_t qf_total = 0, qb_total = 0;  // entries of the two packed copies

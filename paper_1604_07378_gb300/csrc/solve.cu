@@ -68,14 +68,24 @@ __device__ __forceinline__ void bulk_bar_init(uint64_t *bar) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Thread 0: the phase's arrival with the byte count to expect, and the copy.
-__device__ __forceinline__ void bulk_load_issue(uint64_t *bar, void *dst, const void *src, uint32_t bytes) {
+// Thread 0: the phase's single arrival, with the bytes its copies will bring.
+__device__ __forceinline__ void bulk_expect(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
+}
+
+// Any thread: one copy whose bytes count against the barrier's phase.
+__device__ __forceinline__ void bulk_copy(uint64_t *bar, void *dst, const void *src, uint32_t bytes) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_addr(dst)),
                  "l"(src), "r"(bytes), "r"(smem_addr(bar))
                  : "memory");
+}
+
+// Thread 0: the phase's arrival and one contiguous copy.
+__device__ __forceinline__ void bulk_load_issue(uint64_t *bar, void *dst, const void *src, uint32_t bytes) {
+    bulk_expect(bar, bytes);
+    bulk_copy(bar, dst, src, bytes);
 }
 
 __device__ __forceinline__ bool bulk_load_wait(uint64_t *bar, uint32_t parity) {
@@ -257,12 +267,15 @@ __global__ void __launch_bounds__(SBS) k_fwd(DevSolve<R> S, int item0, int qcap,
 
 // ---- backward sweep
 
-// Rows [c0, c1) of Q_s^T (in shared memory at qs, first row at offset off0)
-// times w, where w holds entries [w0, ldr) of [z_C; -r_R]: r_j for the
-// columns j of the supernode.
-template <typename R, int G>
+// Rows [c0, c1) of Q_s^T times w, where w holds entries [w0, w0 + lw) of
+// [z_C; -r_R].  Whole-row items (CHUNK false): the rows lie packed in shared
+// memory at qs (first row at offset off0 of the supernode's block), row j from
+// its diagonal start on.  Chunk items (CHUNK true): row j sits at
+// qs + (j - c0) lw, aligned with w, holding its entries of the chunk.
+// The sums go to r[col + j], or to out[j - c0] (a chunk's partial sums).
+template <typename R, int G, bool CHUNK>
 __device__ __forceinline__ void bwd_rows(int col, int ldr, int c0, int c1, int off0, const R *qs, const R *w,
-                                         int lw, int w0, V4<R> *r) {
+                                         int lw, int w0, V4<R> *r, V4<R> *out) {
     using VT = typename Vec16<R>::T;
     constexpr int VN = Vec16<R>::N;
     constexpr int NG = SBS / G;
@@ -270,15 +283,25 @@ __device__ __forceinline__ void bwd_rows(int col, int ldr, int c0, int c1, int o
     const VT *wx = reinterpret_cast<const VT *>(w);
     const VT *wy = reinterpret_cast<const VT *>(w + lw);
     const VT *wz = reinterpret_cast<const VT *>(w + 2 * lw);
-    const int kend = (ldr - w0) / VN;
+    const int kend = lw / VN;
     for (int base = c0; base < c1; base += 2 * NG) {
         const int j0 = base + 2 * grp, j1 = j0 + 1;
         const bool v0 = j0 < c1, v1 = j1 < c1;
         // row j covers w vectors [k_j, kend)
-        const int k0 = v0 ? (bwd_row_start(j0) - w0) / VN : kend;
-        const int k1 = v1 ? (bwd_row_start(j1) - w0) / VN : kend;
-        const VT *q0 = reinterpret_cast<const VT *>(qs + (v0 ? bwd_row_off(j0, ldr) - off0 : 0)) - k0;
-        const VT *q1 = reinterpret_cast<const VT *>(qs + (v1 ? bwd_row_off(j1, ldr) - off0 : 0)) - k1;
+        int k0 = kend, k1 = kend;
+        const VT *q0 = nullptr, *q1 = nullptr;
+        if (v0) {
+            const int st = bwd_row_start(j0);
+            k0 = st > w0 ? (st - w0) / VN : 0;
+            q0 = CHUNK ? reinterpret_cast<const VT *>(qs + (size_t)(j0 - c0) * lw)
+                       : reinterpret_cast<const VT *>(qs + (bwd_row_off(j0, ldr) - off0)) - k0;
+        }
+        if (v1) {
+            const int st = bwd_row_start(j1);
+            k1 = st > w0 ? (st - w0) / VN : 0;
+            q1 = CHUNK ? reinterpret_cast<const VT *>(qs + (size_t)(j1 - c0) * lw)
+                       : reinterpret_cast<const VT *>(qs + (bwd_row_off(j1, ldr) - off0)) - k1;
+        }
         R a0x = R(0), a0y = R(0), a0z = R(0), a1x = R(0), a1y = R(0), a1z = R(0);
         const int kmin = k0 < k1 ? k0 : k1;
         for (int k = kmin + lane; k < kend; k += G) {
@@ -295,27 +318,65 @@ __device__ __forceinline__ void bwd_rows(int col, int ldr, int c0, int c1, int o
         a0x = group_sum<R, G>(a0x); a0y = group_sum<R, G>(a0y); a0z = group_sum<R, G>(a0z);
         a1x = group_sum<R, G>(a1x); a1y = group_sum<R, G>(a1y); a1z = group_sum<R, G>(a1z);
         if (lane == 0) {
-            if (v0) { V4<R> o; o.x = a0x; o.y = a0y; o.z = a0z; o.w = R(0); r[col + j0] = o; }
-            if (v1) { V4<R> o; o.x = a1x; o.y = a1y; o.z = a1z; o.w = R(0); r[col + j1] = o; }
+            if (v0) {
+                V4<R> o; o.x = a0x; o.y = a0y; o.z = a0z; o.w = R(0);
+                if (out) out[j0 - c0] = o; else r[col + j0] = o;
+            }
+            if (v1) {
+                V4<R> o; o.x = a1x; o.y = a1y; o.z = a1z; o.w = R(0);
+                if (out) out[j1 - c0] = o; else r[col + j1] = o;
+            }
         }
     }
 }
 
-// One backward work item (record `rec`, 4 int4).  Shared memory: qs = the
-// item's factor rows (qcap entries), then w (3 x lw entries), then the row
-// indices of the entries of w past nc (lw int).
+template <typename R, bool CHUNK>
+__device__ __forceinline__ void bwd_rows_g(int G, int col, int ldr, int c0, int c1, int off0, const R *qs,
+                                           const R *w, int lw, int w0, V4<R> *r, V4<R> *out) {
+    switch (G) {
+        case 1: bwd_rows<R, 1, CHUNK>(col, ldr, c0, c1, off0, qs, w, lw, w0, r, out); break;
+        case 2: bwd_rows<R, 2, CHUNK>(col, ldr, c0, c1, off0, qs, w, lw, w0, r, out); break;
+        case 4: bwd_rows<R, 4, CHUNK>(col, ldr, c0, c1, off0, qs, w, lw, w0, r, out); break;
+        case 8: bwd_rows<R, 8, CHUNK>(col, ldr, c0, c1, off0, qs, w, lw, w0, r, out); break;
+        case 16: bwd_rows<R, 16, CHUNK>(col, ldr, c0, c1, off0, qs, w, lw, w0, r, out); break;
+        default: bwd_rows<R, 32, CHUNK>(col, ldr, c0, c1, off0, qs, w, lw, w0, r, out); break;
+    }
+}
+
+// One backward work item (record `rec`, 5 int4; index `item` in the record
+// array).  Shared memory: qs = the item's factor rows (qcap entries), then w
+// (3 x lw entries), then the row indices of the entries of w past nc (lw int).
+// A chunk item (rec[4].x >= 0) copies each of its rows' pieces separately and
+// writes partial sums; the last chunk of its column block to finish adds the
+// chunks' partials in chunk order and writes r.
 template <typename R, typename Wait>
-__device__ __forceinline__ void bwd_item(const DevSolve<R> &S, const int4 *rec, int qcap, R *qs, uint64_t *bar,
-                                         uint32_t parity, const V4<R> *z, V4<R> *r, Wait wait_inputs) {
-    const int4 a = rec[0];
-    if (threadIdx.x == 0) bulk_load_issue(bar, qs, item_src(S.QB, a, sizeof(R)), (uint32_t)a.z);
-    const int4 b = rec[1], c = rec[2];
+__device__ __forceinline__ void bwd_item(const DevSolve<R> &S, const int4 *rec, int item, int qcap, R *qs,
+                                         uint64_t *bar, uint32_t parity, const V4<R> *z, V4<R> *r,
+                                         Wait wait_inputs) {
+    const int4 a = rec[0], b = rec[1], c = rec[2], e = rec[4];
     const int col = b.x, nc = b.y, nr = b.z, roff = b.w;
     const int c0 = c.x, c1 = c.y, ldr = c.z, off0 = c.w;
     const int rows = nc + nr;
-    // w = [z_C; -r_R] from entry w0 on (entries below w0 meet no stored row entry)
-    const int w0 = bwd_row_start(c0);
-    const int lw = ldr - w0;
+    const bool chunk = e.x >= 0;
+    // w = [z_C; -r_R] over [w0, w0 + lw): from the first row's diagonal start
+    // to the end, or the chunk's entries
+    const int w0 = chunk ? e.x : bwd_row_start(c0);
+    const int lw = chunk ? e.y - e.x : ldr - w0;
+    if (!chunk) {
+        if (threadIdx.x == 0) bulk_load_issue(bar, qs, item_src(S.QB, a, sizeof(R)), (uint32_t)a.z);
+    } else {
+        if (threadIdx.x == 0) bulk_expect(bar, (uint32_t)a.z);
+        const int j = c0 + (int)threadIdx.x;
+        if (j < c1) {
+            const int st = bwd_row_start(j);
+            const int seg = st > w0 ? st : w0;
+            const int len = w0 + lw - seg;
+            if (len > 0) {
+                const R *src = static_cast<const R *>(item_src(S.QB, a, sizeof(R))) + bwd_row_off(j, ldr) + (seg - st);
+                bulk_copy(bar, qs + (size_t)(j - c0) * lw + (seg - w0), src, (uint32_t)(len * sizeof(R)));
+            }
+        }
+    }
     R *w = qs + qcap;
     int *ridx = reinterpret_cast<int *>(w + 3 * lw);
     for (int k = threadIdx.x; k < lw; k += SBS) {
@@ -323,7 +384,7 @@ __device__ __forceinline__ void bwd_item(const DevSolve<R> &S, const int4 *rec, 
         ridx[k] = (i >= nc && i < rows) ? S.rows[roff + i - nc] : -1;
     }
     if (!wait_inputs()) {
-        if (threadIdx.x == 0) bulk_load_wait(bar, parity);  // let the copy in flight land first
+        if (threadIdx.x == 0) bulk_load_wait(bar, parity);  // let the copies in flight land first
         return;
     }
 #pragma unroll 4
@@ -340,14 +401,39 @@ __device__ __forceinline__ void bwd_item(const DevSolve<R> &S, const int4 *rec, 
         w[k] = vx; w[lw + k] = vy; w[2 * lw + k] = vz;
     }
     if (!bulk_load_finish(bar, parity, S.err)) return;
-    switch (a.w) {
-        case 1: bwd_rows<R, 1>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
-        case 2: bwd_rows<R, 2>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
-        case 4: bwd_rows<R, 4>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
-        case 8: bwd_rows<R, 8>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
-        case 16: bwd_rows<R, 16>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
-        default: bwd_rows<R, 32>(col, ldr, c0, c1, off0, qs, w, lw, w0, r); break;
+    if (!chunk) {
+        bwd_rows_g<R, false>(a.w, col, ldr, c0, c1, off0, qs, w, lw, w0, r, nullptr);
+        return;
     }
+    const int nch = e.w >> 16, kch = e.w & 0xffff;
+    if (nch == 1) {
+        bwd_rows_g<R, true>(a.w, col, ldr, c0, c1, off0, qs, w, lw, w0, r, nullptr);
+        return;
+    }
+    V4<R> *mine = S.part_r + (size_t)item * 32;
+    bwd_rows_g<R, true>(a.w, col, ldr, c0, c1, off0, qs, w, lw, w0, r, mine);
+    // the last chunk of the column block to get here combines the partials
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(S.cb_cnt + e.z, 1) == nch - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const V4<R> *first = S.part_r + (size_t)(item - kch) * 32;
+    const int j = (int)threadIdx.x;
+    if (j < c1 - c0) {
+        R sx = R(0), sy = R(0), sz = R(0);
+        for (int q = 0; q < nch; ++q) {
+            const V4<R> p = ld_cg(first + (size_t)q * 32 + j);
+            sx += p.x; sy += p.y; sz += p.z;
+        }
+        V4<R> o; o.x = sx; o.y = sy; o.z = sz; o.w = R(0);
+        r[col + c0 + j] = o;
+    }
+    if (threadIdx.x == 0) S.cb_cnt[e.z] = 0;
 }
 
 template <typename R>
@@ -355,8 +441,9 @@ __global__ void __launch_bounds__(SBS) k_bwd(DevSolve<R> S, int item0, int qcap,
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) bulk_bar_init(&bar);
-    bwd_item<R>(S, S.bwd_items + 4 * (size_t)(item0 + blockIdx.x), qcap, reinterpret_cast<R *>(smem_raw), &bar, 0u,
-                z, r, []() {
+    const int item = item0 + blockIdx.x;
+    bwd_item<R>(S, S.bwd_items + 5 * (size_t)item, item, qcap, reinterpret_cast<R *>(smem_raw), &bar, 0u, z, r,
+                []() {
                     pdl_wait();
                     pdl_trigger();
                     return true;
@@ -457,9 +544,9 @@ __global__ void __launch_bounds__(SBS) k_bwd_dyn(DevSolve<R> S, int qcap, const 
         __syncthreads();
         const int item = item_sh;
         if (item >= S.n_bwd_items) break;
-        const int4 *rec = S.bwd_items + 4 * (size_t)item;
+        const int4 *rec = S.bwd_items + 5 * (size_t)item;
         const int4 dep = rec[3];  // parent (-1: none), own supernode
-        bwd_item<R>(S, rec, qcap, qs, &bar, parity, z, r, [&]() {
+        bwd_item<R>(S, rec, item, qcap, qs, &bar, parity, z, r, [&]() {
             if (threadIdx.x == 0) ok_sh = dep_wait(S.bwd_done, dep.x, dep.x >= 0 ? S.bwd_nitems[dep.x] : 0, S.err);
             __syncthreads();
             return ok_sh != 0;

@@ -80,7 +80,12 @@ def test_energy_gradient_other_materials(kind):
 
 # ---------------------------------------------------------------- A0 solve and two-loop
 
-@pytest.mark.parametrize("w", WORKLOADS[:3], ids=IDS[:3])
+# a lattice whose upper separators have backward rows long enough to be
+# split into chunk items (rows of Q^T longer than 1024 entries)
+LAT30 = W.lattice_workload((30, 30, 30), W.Material(W.NEOHOOKEAN, 5e5, 0.4), clamp_axis=2, seed=13, name="lat30")
+
+
+@pytest.mark.parametrize("w", WORKLOADS[:3] + [LAT30], ids=IDS[:3] + ["lat30"])
 @pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
 @pytest.mark.parametrize("dyn_sweeps", [0, 1], ids=["levels", "dependency"])
 def test_solve_A0_parity(w, prec, dyn_sweeps):
