@@ -26,6 +26,7 @@
 
 #include "kernels.cuh"
 #include "layout.hpp"
+#include "matdev_host.hpp"
 #include "setup.hpp"
 
 using namespace hqn;
@@ -45,22 +46,6 @@ int fail(int code, const std::string &msg) {
         if (e_ != cudaSuccess)                                                                \
             return fail(HQN_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
     } while (0)
-
-// Hermite segment coefficients p0 + u(p1 + u(p2 + u p3)) of one spline function.
-template <typename R>
-void spline_coeffs(const MaterialHost &m, int f, MatDev<R> &d) {
-    for (int i = 0; i < 8; ++i) d.kx[f][i] = (R)m.sx[f][i];
-    for (int i = 0; i < 7; ++i) {
-        const double h = m.sx[f][i + 1] - m.sx[f][i];
-        const double v0 = m.sv[f][i], v1 = m.sv[f][i + 1];
-        const double m0 = m.ss[f][i] * h, m1 = m.ss[f][i + 1] * h;
-        d.inv_h[f][i] = (R)(1.0 / h);
-        d.p[f][i][0] = (R)v0;
-        d.p[f][i][1] = (R)m0;
-        d.p[f][i][2] = (R)(3.0 * (v1 - v0) - 2.0 * m0 - m1);
-        d.p[f][i][3] = (R)(2.0 * (v0 - v1) + m0 + m1);
-    }
-}
 
 struct SimBase {
     virtual ~SimBase() {}
@@ -248,8 +233,7 @@ struct Sim final : SimBase {
             M.kind = s.mat.kind;
             M.mu = (R)s.mat.mu; M.lam = (R)s.mat.lam;
             M.J0 = (R)s.mat.J0; M.c0 = (R)s.mat.c0; M.c1 = (R)s.mat.c1; M.c2 = (R)s.mat.c2;
-            if (s.mat.kind == HQN_SPLINE_VL)
-                for (int f = 0; f < 3; ++f) spline_coeffs(s.mat, f, M);
+            if (s.mat.kind == HQN_SPLINE_VL) fill_spline(M, s.mat.sx, s.mat.sv, s.mat.ss);
             D.v0 = v0[k]; D.t0 = t0[k];
             D.vb0 = vb0[k]; D.nvb = (s.n + VBS - 1) / VBS;
             D.tb0 = tb0[k]; D.ntb = (s.T + TBS - 1) / TBS;

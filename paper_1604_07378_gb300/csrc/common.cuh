@@ -19,6 +19,11 @@ struct alignas(4 * sizeof(R)) V4 {
 // Material as the tet kernel consumes it (Eq. valanis-landel).  For the
 // spline material each of a, b, c is 7 cubic segments p0 + u(p1 + u(p2 + u p3)),
 // u = (t - x_i) * inv_h, over knots x_0..x_7, continued quadratically outside.
+// The spline energy is evaluated about the rest state (t = 1 for a, b, c):
+// f(t) = f(1) + f'(1) (t - 1) + df(t), with df taken inside segment i about
+// its point nearest 1 (u = ur[f][i]) using the constants
+// dD[f][i] = f'(ref) - f'(1) and dE[f][i] = f(ref) - f(1) - f'(1) (ref - 1),
+// so no first-order terms of size mu cancel in float32.
 template <typename R>
 struct MatDev {
     int kind;
@@ -27,6 +32,10 @@ struct MatDev {
     R kx[3][8];         // spline knots of a, b, c
     R inv_h[3][7];
     R p[3][7][4];
+    R ur[3][7], dD[3][7], dE[3][7];
+    R K0;               // a'(1) + 2 b'(1) + c'(1): the stress of the rest state
+    R B1C1, C1;         // b'(1) + c'(1) and c'(1)
+    R psi_rest;         // 3 a(1) + 3 b(1) + c(1)
 };
 
 // Control block of one simulation's step, resident on the device.  Every

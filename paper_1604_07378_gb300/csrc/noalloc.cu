@@ -18,6 +18,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "matdev_host.hpp"
 #include "reduce.cuh"
 #include "tetmath.cuh"
 
@@ -177,21 +178,15 @@ int material_dev(const hqn_material &m, MatDev<double> &d) {
         d.c2 = (d.mu + d.lam - d.lam * l0) / (d.J0 * d.J0);
     } else if (m.kind == HQN_SPLINE_VL) {
         if (!m.spline) return HQN_ERR_ARG;
-        for (int f = 0; f < 3; ++f) {
-            const double *k = m.spline + f * 24;  // 8 knots x (knot, value, slope)
-            for (int i = 0; i < 8; ++i) d.kx[f][i] = k[3 * i];
-            for (int i = 0; i < 7; ++i) {
-                const double h = k[3 * (i + 1)] - k[3 * i];
-                if (!(h > 0)) return HQN_ERR_ARG;
-                const double v0 = k[3 * i + 1], v1 = k[3 * (i + 1) + 1];
-                const double m0 = k[3 * i + 2] * h, m1 = k[3 * (i + 1) + 2] * h;
-                d.inv_h[f][i] = 1.0 / h;
-                d.p[f][i][0] = v0;
-                d.p[f][i][1] = m0;
-                d.p[f][i][2] = 3.0 * (v1 - v0) - 2.0 * m0 - m1;
-                d.p[f][i][3] = 2.0 * (v0 - v1) + m0 + m1;
+        double sx[3][8], sv[3][8], ss[3][8];
+        for (int f = 0; f < 3; ++f)
+            for (int i = 0; i < 8; ++i) {
+                sx[f][i] = m.spline[(f * 8 + i) * 3];
+                sv[f][i] = m.spline[(f * 8 + i) * 3 + 1];
+                ss[f][i] = m.spline[(f * 8 + i) * 3 + 2];
+                if (i > 0 && !(sx[f][i] > sx[f][i - 1])) return HQN_ERR_ARG;
             }
-        }
+        fill_spline(d, sx, sv, ss);
     } else if (m.kind != HQN_STVK && m.kind != HQN_COROTATED && m.kind != HQN_POLY4) {
         return HQN_ERR_ARG;
     }

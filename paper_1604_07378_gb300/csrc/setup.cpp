@@ -729,6 +729,9 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
         }
     }
     S.bwd_lvl_ptr[L] = (int)S.bwd_items.size();
+    // the longest vector a sweep block stages (what bounds its shared memory)
+    S.max_ld = 0;
+    for (int l = 0; l < L; ++l) S.max_ld = std::max(S.max_ld, std::max(S.fwd_lvl_ld[l], S.bwd_lvl_ld[l]));
 
     S.setup_seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();

@@ -72,7 +72,7 @@ struct Setup {
     std::vector<FwdItem> fwd_items;
     std::vector<BwdItem> bwd_items;
     int64_t qf_total = 0, qb_total = 0;  // entries of the two packed copies
-    int max_ld = 0;                  // max(ldc, ldr): shared-memory size of a sweep block
+    int max_ld = 0;                  // longest vector a sweep block stages (bounds its shared memory)
     int max_front_cols = 0;          // max ncol
     int64_t factor_nnz = 0;
     double setup_seconds = 0.0;

@@ -188,23 +188,32 @@ __device__ __forceinline__ R stretch_minus_one(R s, R l) {
     return s > R(0.5) ? l / (s + R(1)) : s - R(1);
 }
 
-// Cubic Hermite segment evaluation with quadratic continuation outside the knots.
+// Spline function f about its rest point, for the argument t = 1 + e (e
+// given, formed without cancellation): df = f(t) - f(1) - f'(1) e and
+// ddf = f'(t) - f'(1); cubic Hermite segments (knots stored as offsets
+// kx = x - 1) with quadratic continuation outside the knots.  Inside segment i
+// the cubic is expanded about u_r (its point nearest t = 1): with du = u - u_r,
+//   f'(u) - f'(u_r) = du (2 p2 + 3 p3 (u + u_r)) / h,
+//   f(u) - f(u_r) - f'(u_r) h du = du^2 (p2 + p3 (u + 2 u_r)),
+// whose terms do not cancel near t = 1.
 template <typename R>
-__device__ __forceinline__ void spline_eval(const MatDev<R> &M, int f, R t, R &val, R &der) {
+__device__ __forceinline__ void spline_delta(const MatDev<R> &M, int f, R e, R &df, R &ddf) {
     const R lo = M.kx[f][0], hi = M.kx[f][7];
-    const R tc = t < lo ? lo : (t > hi ? hi : t);
+    const R ec = e < lo ? lo : (e > hi ? hi : e);
     int i = 0;
 #pragma unroll
-    for (int k = 1; k < 7; ++k) i = tc >= M.kx[f][k] ? k : i;
+    for (int k = 1; k < 7; ++k) i = ec >= M.kx[f][k] ? k : i;
     const R ih = M.inv_h[f][i];
-    const R u = (tc - M.kx[f][i]) * ih;
+    const R u = (ec - M.kx[f][i]) * ih;
     const R *p = M.p[f][i];
-    const R v = p[0] + u * (p[1] + u * (p[2] + u * p[3]));
-    const R d = (p[1] + u * (R(2) * p[2] + R(3) * u * p[3])) * ih;
-    const R dd = (R(2) * p[2] + R(6) * u * p[3]) * ih * ih;
-    const R dt = t - tc;
-    val = v + dt * (d + R(0.5) * dd * dt);
-    der = d + dd * dt;
+    const R ur = M.ur[f][i];
+    const R du = u - ur;
+    const R dd1 = M.dD[f][i] + du * (R(2) * p[2] + R(3) * p[3] * (u + ur)) * ih;
+    const R dv = M.dE[f][i] + M.dD[f][i] * du / ih + du * du * (p[2] + p[3] * (u + R(2) * ur));
+    const R f2 = (R(2) * p[2] + R(6) * u * p[3]) * ih * ih;
+    const R dt = e - ec;
+    df = dv + dt * (dd1 + R(0.5) * f2 * dt);
+    ddf = dd1 + f2 * dt;
 }
 
 // Energy density Psi and tau_i = dPsi/ds_i from (s, l) for the material.
@@ -263,20 +272,25 @@ __device__ __forceinline__ R material_tau(const MatDev<R> &M, const R s[3], cons
             return psi;
         }
         default: {  // HQN_SPLINE_VL
-            R va0, da0, va1, da1, va2, da2;
-            spline_eval(M, 0, s[0], va0, da0);
-            spline_eval(M, 0, s[1], va1, da1);
-            spline_eval(M, 0, s[2], va2, da2);
-            R vb01, db01, vb02, db02, vb12, db12;
-            spline_eval(M, 1, s[0] * s[1], vb01, db01);
-            spline_eval(M, 1, s[0] * s[2], vb02, db02);
-            spline_eval(M, 1, s[1] * s[2], vb12, db12);
-            R vc, dc;
-            spline_eval(M, 2, J, vc, dc);
-            tau[0] = da0 + db01 * s[1] + db02 * s[2] + dc * s[1] * s[2];
-            tau[1] = da1 + db01 * s[0] + db12 * s[2] + dc * s[0] * s[2];
-            tau[2] = da2 + db02 * s[0] + db12 * s[1] + dc * s[0] * s[1];
-            return va0 + va1 + va2 + vb01 + vb02 + vb12 + vc;
+            // Psi = psi_rest + K0 sum d_i + (b'(1) + c'(1)) sum_{i<j} d_i d_j + c'(1) d1 d2 d3
+            //       + sum da(s_i) + sum db(s_i s_j) + dc(J),  d_i = s_i - 1
+            const R d0 = stretch_minus_one(s[0], l[0]), d1 = stretch_minus_one(s[1], l[1]),
+                    d2 = stretch_minus_one(s[2], l[2]);
+            R ea0, ga0, ea1, ga1, ea2, ga2;
+            spline_delta(M, 0, d0, ea0, ga0);
+            spline_delta(M, 0, d1, ea1, ga1);
+            spline_delta(M, 0, d2, ea2, ga2);
+            // b and c at products of stretches: their offsets from 1 without cancellation
+            R eb01, gb01, eb02, gb02, eb12, gb12, ec, gc;
+            spline_delta(M, 1, d0 + d1 + d0 * d1, eb01, gb01);
+            spline_delta(M, 1, d0 + d2 + d0 * d2, eb02, gb02);
+            spline_delta(M, 1, d1 + d2 + d1 * d2, eb12, gb12);
+            spline_delta(M, 2, (d0 + d1 + d2) + (d0 * d1 + d0 * d2 + d1 * d2) + d0 * d1 * d2, ec, gc);
+            tau[0] = M.K0 + M.B1C1 * (d1 + d2) + M.C1 * d1 * d2 + ga0 + gb01 * s[1] + gb02 * s[2] + gc * s[1] * s[2];
+            tau[1] = M.K0 + M.B1C1 * (d0 + d2) + M.C1 * d0 * d2 + ga1 + gb01 * s[0] + gb12 * s[2] + gc * s[0] * s[2];
+            tau[2] = M.K0 + M.B1C1 * (d0 + d1) + M.C1 * d0 * d1 + ga2 + gb02 * s[0] + gb12 * s[1] + gc * s[0] * s[1];
+            return M.psi_rest + M.K0 * (d0 + d1 + d2) + M.B1C1 * (d0 * d1 + d0 * d2 + d1 * d2) + M.C1 * d0 * d1 * d2 +
+                   (ea0 + ea1 + ea2) + (eb01 + eb02 + eb12) + ec;
         }
     }
 }
