@@ -133,6 +133,10 @@ def oracle_sample(w, budget_s=25.0, counts=None):
 
 # ---------------------------------------------------------------------------- GPU arm
 
+# schedules of the A0^-1 sweeps (hqn_params.dyn_sweeps)
+SWEEPS = {"levels": 0, "dependency": 1, "pipelined": 2}
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -145,7 +149,8 @@ def run_ours(args, rank, world, dist):
     w = W.cube40(W.NEOHOOKEAN)
     T = w.n_tets
     graph = 0 if args.no_graph else 1
-    sim = hqn.Sim.from_workload(w, precision=hqn.FP32_MIXED, stream=stream.cuda_stream, use_graph=graph)
+    sim = hqn.Sim.from_workload(w, precision=hqn.FP32_MIXED, stream=stream.cuda_stream, use_graph=graph,
+                                dyn_sweeps=SWEEPS[args.sweeps], leaf_size=args.leaf_size)
     info = sim.info()
     sim.set_state(w.q_cur, w.q_prev)
     sim.step(args.warmup)
@@ -218,7 +223,8 @@ def run_ours(args, rank, world, dist):
     d2h = n * vbytes + 1024  # state + control block (line-search statistics)
 
     # ---- FP64-plain GPU form beside it, and the accuracy of the FP32 form against it
-    sim64 = hqn.Sim.from_workload(w, precision=hqn.FP64_PLAIN, stream=stream.cuda_stream, use_graph=graph)
+    sim64 = hqn.Sim.from_workload(w, precision=hqn.FP64_PLAIN, stream=stream.cuda_stream, use_graph=graph,
+                                  dyn_sweeps=SWEEPS[args.sweeps], leaf_size=args.leaf_size)
     sim64.set_state(w.q_cur, w.q_prev)
     sim64.step(1)
     x64, _ = sim64.get_state()
@@ -318,7 +324,7 @@ def run_batched(args, stream):
     for prec, key, steps in ((hqn.FP32_MIXED, "fp32_mixed", args.batch_steps),
                              (hqn.FP64_PLAIN, "fp64_plain", max(2, args.batch_steps // 4))):
         t0 = time.perf_counter()
-        b = hqn.Batch(ws, precision=prec, stream=stream.cuda_stream)
+        b = hqn.Batch(ws, precision=prec, stream=stream.cuda_stream, dyn_sweeps=SWEEPS[args.sweeps])
         create_s = time.perf_counter() - t0
         for i, w in enumerate(ws):
             b.set_state(i, w.q_cur, w.q_prev)
@@ -392,6 +398,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 512-simulation measurement")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--leaf-size", type=int, default=0,
+                    help="max vertices of a nested-dissection leaf (0 = the library default)")
+    ap.add_argument("--sweeps", default="levels", choices=sorted(SWEEPS),
+                    help="schedule of the triangular sweeps")
     ap.add_argument("--no-graph", action="store_true",
                     help="issue the step's kernels one by one (same kernels; for profilers that "
                          "cannot see inside graphs with conditional nodes)")

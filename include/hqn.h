@@ -112,7 +112,14 @@ typedef struct {
                              chained by programmatic dependent launch (default);
                              1 = dependency-driven (one persistent launch per
                              sweep; a work item waits only for the supernodes it
-                             reads).  Same arithmetic, bit-identical results      */
+                             reads); 2 = pipelined (one persistent launch per
+                             sweep, one block per SM, each with a fixed list of
+                             items whose factor rows stream into shared memory
+                             ahead of the dependency chain; falls back to 0 when
+                             its shared memory does not fit).  0 and 1 give
+                             bit-identical results; 2 partitions the rows into
+                             other work items, so its results differ from them
+                             by rounding only                                      */
 } hqn_params;
 
 #define HQN_MAX_HISTORY 16
@@ -144,7 +151,8 @@ typedef struct {
     int64_t n_update_entries;   /* entries of the forward-sweep update vectors        */
     int32_t chained_sweeps;     /* 1 if the per-level sweeps use programmatic dependent
                                    launch (a level starts while the previous finishes) */
-    int32_t sweep_schedule;     /* 1 = dependency-driven sweeps, 0 = one launch per level */
+    int32_t sweep_schedule;     /* sweeps in use: 0 = one launch per level, 1 = dependency-
+                                   driven, 2 = pipelined (see hqn_params.dyn_sweeps)     */
     int32_t n_sims;             /* simulations in the handle (1 for sim_create)        */
 } hqn_info;
 

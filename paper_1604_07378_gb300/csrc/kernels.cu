@@ -174,16 +174,15 @@ __device__ __forceinline__ void edge_diffs(const V4<R> &x0, const V4<R> &x1, con
 // its last block (fixed order, float64); result valid in thread 0.
 template <int BS>
 __device__ __forceinline__ double sum_block_range(const double *part, int b0, int nb) {
-    double acc[1] = {0.0};
-    for (int b = threadIdx.x; b < nb; b += BS) acc[0] += __ldcg(part + b0 + b);
+    double acc[1] = {strided_sum(part + b0, threadIdx.x, nb, BS)};
     block_sum<BS, 1>(acc);
     return acc[0];
 }
 
 // ---------------------------------------------------------------- tet kernel
 
-// One thread per tet: the four corner gradients of V Psi, written to
-// corner[c * Tn + t].
+// One thread per tet: the four corner gradients of V Psi, written to their
+// places in the vertex-ordered corner array.
 //   TET_INIT / TET_EVAL: at the point x_t, with the energy reduced too (the
 //     simulation's last block, fixed order, plus the inertia partials):
 //     TET_INIT sets g(x_1), TET_EVAL reports g.
@@ -230,7 +229,7 @@ __global__ void __launch_bounds__(TBS, 8) k_tet(DevSim<R> s, int mode, CondHandl
         for (int k = 0; k < 4; ++k) {
             V4<R> o;
             o.x = g[k][0]; o.y = g[k][1]; o.z = g[k][2]; o.w = R(0);
-            s.corner[(size_t)k * s.Tn + t] = o;
+            s.corner[s.corner_pos[(size_t)k * s.Tn + t]] = o;
         }
     }
     if (grad_mode) return;
@@ -335,7 +334,7 @@ __global__ void __launch_bounds__(TBS) k_ls(DevSim<R> s, CondHandles h) {
         __threadfence();
         for (int j = warp; j < K; j += TBS / 32) {
             double acc = 0.0;
-            for (int b = lane; b < D.ntb; b += 32) acc += __ldcg(s.part_ls + (size_t)j * s.ntb + D.tb0 + b);
+            acc = strided_sum(s.part_ls + (size_t)j * s.ntb + D.tb0, lane, D.ntb, 32);
             acc = warp_sum(acc);
             if (lane == 0) sh[j] = acc;
         }
@@ -488,8 +487,9 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
         const int gi = D.v0 + i;
         const int b = s.vt_ptr[gi], e = s.vt_ptr[gi + 1];
         R gx = R(0), gy = R(0), gz = R(0);
+#pragma unroll 8
         for (int k = b; k < e; ++k) {
-            const V4<R> cg = s.corner[s.vt_slot[k]];
+            const V4<R> cg = s.corner[k];
             gx += cg.x; gy += cg.y; gz += cg.z;
         }
         const V4<R> x = iter ? step_point(s.xk[gi], s.d[gi], al) : s.xt[gi];
@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
             __threadfence();
             for (int k = warp; k < ND; k += VBS / 32) {
                 double acc = 0.0;
-                for (int b = lane; b < D.nvb; b += 32) acc += __ldcg(s.part_g + (size_t)k * s.nvb + D.vb0 + b);
+                acc = strided_sum(s.part_g + (size_t)k * s.nvb + D.vb0, lane, D.nvb, 32);
                 acc = warp_sum(acc);
                 if (lane == 0) sh[k] = acc;
             }
@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(VBS) k_r0_dots(DevSim<R> s) {
         __threadfence();
         for (int k = warp; k < MP1; k += VBS / 32) {
             double acc = 0.0;
-            for (int b = lane; b < D.nvb; b += 32) acc += __ldcg(s.part_v + (size_t)k * s.nvb + D.vb0 + b);
+            acc = strided_sum(s.part_v + (size_t)k * s.nvb + D.vb0, lane, D.nvb, 32);
             acc = warp_sum(acc);
             if (lane == 0) sh[k] = acc;
         }
@@ -731,7 +731,7 @@ __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, i
         __threadfence();
         if (warp < 4) {
             double acc = 0.0;
-            for (int b = lane; b < D.nvb; b += 32) acc += __ldcg(s.part_v + (size_t)warp * s.nvb + D.vb0 + b);
+            acc = strided_sum(s.part_v + (size_t)warp * s.nvb + D.vb0, lane, D.nvb, 32);
             acc = warp_sum(acc);
             if (lane == 0) sh[warp] = acc;
         }

@@ -40,11 +40,12 @@ struct DevSim {
     const R *vol;               // Tn
     const R *mh2;               // batch vertices: m_v / h^2
     const int *vt_ptr;          // batch vertices + 1
-    const int *vt_slot;         // corner slots c * Tn + t, ascending t per vertex
+    const int *corner_pos;      // position of corner c of tet t (index c * Tn + t) in `corner`,
+                                // which holds every vertex's incident corners together, ascending t
     // state and work vectors (batch vertices, internal order within each simulation)
     V4<R> *u_cur, *u_prev, *y, *xk, *xt, *gk, *d, *q, *z;
     V4<R> *S, *Tt;              // history rings
-    V4<R> *corner;              // 4 x Tn corner gradients
+    V4<R> *corner;              // 4 x Tn corner gradients in vertex order (vt_ptr ranges)
     // per-block partial sums: part_x[k * (blocks of the kernel) + block]
     double *part_in, *part_el, *part_g, *part_v, *part_ls;
     unsigned int *batch_ticket; // arrival counters of the simulations' last blocks (graph conditions)
@@ -85,6 +86,13 @@ template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream
 
 // ---- triangular solves (solve.cu)
 constexpr int SOLVE_MAX_SMEM = 200 * 1024;  // dynamic shared memory of one sweep block
+// Pipelined sweeps: dynamic shared memory of a block (ring slots + vector
+// area), and per-bundle bounds the host schedule respects.
+constexpr int PIPE_MAX_SMEM = 220 * 1024;
+constexpr int PIPE_NS_MAX = 8;    // ring slots
+constexpr int PIPE_CONS_WARPS = 16;  // consumer warps of a block (plus one producer warp)
+constexpr int PIPE_SEG_MAX = 64;  // gather segments (supernodes) per bundle
+constexpr int PIPE_CMB_MAX = 32;  // chunk column blocks per bundle
 
 template <typename R>
 struct DevSolve {
@@ -116,6 +124,37 @@ struct DevSolve {
     const int *bwd_lvl_start, *bwd_lvl_cnt;  // host: backward items of level l: [start[l], start[l] + cnt[l])
     const int *fwd_lvl_ld, *bwd_lvl_ld;    // host: max ldc / ldr of the level (shared memory)
     const int *fwd_lvl_q, *bwd_lvl_q;      // host: max factor entries of one item of the level
+    // Pipelined schedule (pipe = 1): one persistent launch per sweep, one block
+    // per SM.  Block b runs its own list of bundles; a bundle is consecutive
+    // items of one tree level (at most half the ring) sharing one wait for the
+    // items they read from in other blocks and one gather of the vectors
+    // their rows multiply (segments of the block's vector area, fcap entries
+    // per component).  A producer warp streams the block's items' factor rows
+    // into a ring of shared-memory slots ahead of the consumers, across levels.
+    //   items (in block order): forward  {q0 lo, q0 hi, bytes, G} {col, nc, ldc, uoff} {r0, r1, ldf, off0}
+    //                                    {foff, 0, w0, w1}
+    //                           backward {q0 lo, q0 hi, bytes, G} {col, nc, nrow, roff} {c0, c1, ldr, off0}
+    //                                    {woff, pslot0, w0, w1} {e0, e1, column block, nch << 16 | chunk}
+    //     foff / woff = vector-area offset of the item's first vector entry;
+    //     pslot0 = partial-sum slot of chunk 0 of the item's column block;
+    //     [w0, w1) = the consumer warps that run the item (a bundle's items
+    //     are resident together and run side by side)
+    //   bundles: {item0, item1, seg0, seg1} {dep0, dep1, sig0, sig1} {cmb0, cmb1, vector entries, 0}
+    //   segments: forward {col, filled entries, area offset, length};
+    //             backward {col, nc, nrow, roff} {w0, area offset, length, 0}
+    //   dep: (supernode, completed items to wait for); sig: (supernode, items completed)
+    //   cmb: {column block, chunks in the bundle, pslot0, nch} {first output vertex, columns, 0, 0}
+    int pipe;
+    int pipe_grid, pipe_ns, pipe_fcap;  // host: blocks, ring slots, vector-area entries
+    const int4 *pf_items, *pb_items;
+    const int4 *pf_bund, *pb_bund;
+    const int *pf_blk, *pb_blk;         // bundles of block b: [blk[b], blk[b + 1])
+    const int4 *pf_seg, *pb_seg;
+    const int2 *pf_dep, *pb_dep;
+    const int2 *pf_sig, *pb_sig;
+    const int4 *pb_cmb;
+    V4<R> *pb_part;                     // 32 partial sums per chunk slot
+    int *pb_cbc;                        // chunks finished per column block (re-arms itself)
     V4<R> *u;                   // update vectors
     V4<R> *part_r;              // 32 partial sums per backward item (chunk items)
     int *cb_cnt;                // chunks finished per backward column block (re-arms itself)
@@ -128,7 +167,10 @@ void launch_solve(const DevSolve<R> &s, const V4<R> *q, V4<R> *z, V4<R> *r, cuda
 template <typename R> int solve_smem_limit_ok(int max_cols);
 // Blocks of one persistent sweep (0 = cannot run the dependency-driven schedule).
 template <typename R> int solve_dyn_grid(const DevSolve<R> &s);
-// Raises the forward sweep's dynamic shared-memory limit (once per device).
+// Pipelined schedule: ring slots for a vector area of fcap entries and the
+// blocks of one launch (0 = cannot run it).
+template <typename R> int solve_pipe_grid(int fcap, int *ns);
+// Raises the sweeps' dynamic shared-memory limits (once per device).
 template <typename R> cudaError_t solve_prepare();
 
 }  // namespace hqn

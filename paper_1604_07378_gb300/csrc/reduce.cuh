@@ -152,6 +152,24 @@ __device__ __forceinline__ void block_sum_r(const R (&v)[NV], double (&out)[NV])
 
 // ---- grid level
 
+// part[j] + part[j + stride] + ... (indices < n), added in that order; eight
+// terms are loaded before any is added, so a thread's sum costs one memory
+// round trip per eight terms rather than one per term.
+__device__ __forceinline__ double strided_sum(const double *part, int j, int n, int stride) {
+    double acc = 0.0;
+    for (int b = j; b < n; b += 8 * stride) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int bb = b + u * stride;
+            v[u] = bb < n ? __ldcg(part + bb) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u];
+    }
+    return acc;
+}
+
 // Thread 0 publishes the block's partials (part[k * stride + blockIdx.x]) and
 // takes an arrival ticket.  Returns true in every thread of the last block.
 template <int NV>
@@ -179,8 +197,7 @@ __device__ __forceinline__ void sum_partials(const double *part, int stride, int
     __threadfence();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = warp; k < NV; k += BS / 32) {
-        double acc = 0.0;
-        for (int i = lane; i < n; i += 32) acc += __ldcg(part + k * stride + i);
+        double acc = strided_sum(part + k * stride, lane, n, 32);
         acc = warp_sum(acc);
         if (lane == 0) sh[k] = acc;
     }

@@ -203,6 +203,103 @@ int nd_recurse(NDState &st, std::vector<int> &V) {
     return id;
 }
 
+// Work items of both sweeps, level by level.  Items hold at most kMax factor
+// entries (one shared-memory buffer) and aim at a level's entries / per_level.
+// Forward: consecutive rows of Q_s.  Backward: consecutive rows of Q_s^T; rows longer than kLongRow
+// entries are split into chunks of 32 rows x kChunk entries, so an item
+// gathers a short piece of w instead of the whole vector (a few columns per
+// item would otherwise each gather all of it).
+int make_items(const Setup &S, int VN, int kMax, int64_t per_level, ItemLists &out, std::string &err) {
+    const int L = S.n_levels, ns = (int)S.sn.size();
+    const int kMin = kMax / 4;
+    // lanes per output row: enough that each lane reads a few 16-byte vectors
+    auto lanes_for = [&](int len) {
+        const int nv = (len + VN - 1) / VN;
+        int G = 1;
+        while (G < 32 && G * 4 < nv) G *= 2;
+        return G;
+    };
+    std::vector<int64_t> lvl_entries(L, 0);
+    for (auto &sn : S.sn) lvl_entries[sn.level] += fwd_row_off(sn.ncol + sn.nrow, sn.ncol, sn.ldc);
+    out = ItemLists{};
+    out.fwd_lvl_ptr.assign(L + 1, 0);
+    out.bwd_lvl_ptr.assign(L + 1, 0);
+    out.fwd_lvl_ld.assign(L, 0);
+    out.bwd_lvl_ld.assign(L, 0);
+    out.fwd_lvl_q.assign(L, 0);
+    out.bwd_lvl_q.assign(L, 0);
+    for (int l = 0; l < L; ++l) {
+        const int target = (int)std::min<int64_t>(kMax, std::max<int64_t>(kMin, lvl_entries[l] / per_level));
+        out.fwd_lvl_ptr[l] = (int)out.fwd_items.size();
+        for (int s = 0; s < ns; ++s) {
+            const SupernodeHost &sn = S.sn[s];
+            if (sn.level != l || sn.ncol == 0) continue;
+            const int nc = sn.ncol, rows = nc + sn.nrow;
+            for (int r0 = 0; r0 < rows;) {
+                int r1 = r0 + 1;
+                while (r1 < rows && fwd_row_off(r1 + 1, nc, sn.ldc) - fwd_row_off(r0, nc, sn.ldc) <= target) ++r1;
+                // staged vectors: f (ldc entries) and the rectangle rows' child updates
+                const int nrr = std::max(0, r1 - std::max(r0, nc));
+                out.fwd_lvl_ld[l] = std::max(out.fwd_lvl_ld[l], sn.ldc + pad4(nrr));
+                const int entries = (int)(fwd_row_off(r1, nc, sn.ldc) - fwd_row_off(r0, nc, sn.ldc));
+                if (entries > kMax) {
+                    err = "a factor row does not fit the sweeps' shared-memory buffer";
+                    return HQN_ERR_UNSUPPORTED;
+                }
+                out.fwd_lvl_q[l] = std::max(out.fwd_lvl_q[l], entries);
+                out.fwd_items.push_back({s, r0, r1, lanes_for(fwd_row_len(r1 - 1, nc, sn.ldc))});
+                r0 = r1;
+            }
+        }
+    }
+    out.fwd_lvl_ptr[L] = (int)out.fwd_items.size();
+    constexpr int kBlockCols = 32;
+    const int kChunk = VN == 4 ? 256 : 128;
+    const int kLongRow = 4 * kChunk;
+    for (int l = 0; l < L; ++l) {
+        const int target = (int)std::min<int64_t>(kMax, std::max<int64_t>(kMin, lvl_entries[l] / per_level));
+        out.bwd_lvl_ptr[l] = (int)out.bwd_items.size();
+        for (int s = 0; s < ns; ++s) {
+            const SupernodeHost &sn = S.sn[s];
+            if (sn.level != l || sn.ncol == 0) continue;
+            for (int c0 = 0; c0 < sn.ncol;) {
+                const int w0 = bwd_row_start(c0);
+                if (sn.ldr - w0 > kLongRow) {
+                    const int c1 = std::min(sn.ncol, c0 + kBlockCols);
+                    const int nch = (sn.ldr - w0 + kChunk - 1) / kChunk;
+                    for (int k = 0; k < nch; ++k) {
+                        BwdItem it{s, c0, c1, lanes_for(kChunk)};
+                        it.e0 = w0 + k * kChunk;
+                        it.e1 = std::min(sn.ldr, it.e0 + kChunk);
+                        it.cb = out.n_bwd_blocks;
+                        it.nch = nch;
+                        it.k = k;
+                        out.bwd_lvl_q[l] = std::max(out.bwd_lvl_q[l], (c1 - c0) * (it.e1 - it.e0));
+                        out.bwd_lvl_ld[l] = std::max(out.bwd_lvl_ld[l], it.e1 - it.e0);
+                        out.bwd_items.push_back(it);
+                    }
+                    ++out.n_bwd_blocks;
+                    c0 = c1;
+                    continue;
+                }
+                int c1 = c0 + 1;
+                while (c1 < sn.ncol && bwd_row_off(c1 + 1, sn.ldr) - bwd_row_off(c0, sn.ldr) <= target) ++c1;
+                const int entries = (int)(bwd_row_off(c1, sn.ldr) - bwd_row_off(c0, sn.ldr));
+                if (entries > kMax) {
+                    err = "a factor row does not fit the sweeps' shared-memory buffer";
+                    return HQN_ERR_UNSUPPORTED;
+                }
+                out.bwd_lvl_q[l] = std::max(out.bwd_lvl_q[l], entries);
+                out.bwd_lvl_ld[l] = std::max(out.bwd_lvl_ld[l], sn.ldr - w0);
+                out.bwd_items.push_back({s, c0, c1, lanes_for(sn.ldr - w0)});
+                c0 = c1;
+            }
+        }
+    }
+    out.bwd_lvl_ptr[L] = (int)out.bwd_items.size();
+    return HQN_OK;
+}
+
 }  // namespace
 
 double fit_stiffness(const MaterialHost &m, double x_start, double x_end) {
@@ -630,108 +727,18 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
         S.qb_total += bwd_row_off(sn.ncol, sn.ldr);
         S.max_ld = std::max(S.max_ld, std::max(sn.ldc, sn.ldr));
     }
-    // lanes per output row: enough that each lane reads a few 16-byte vectors
-    auto lanes_for = [&](int len) {
-        const int nv = (len + VN - 1) / VN;
-        int G = 1;
-        while (G < 32 && G * 4 < nv) G *= 2;
-        return G;
-    };
-    // Entries per work item: a level's entries spread over ~400 items (a few
-    // blocks per SM), within [kMin, kMax] so that one item's rows fit the
-    // shared-memory buffer its bulk copy fills (kMax entries = 64 KB).
-    const int kMax = 65536 / esize, kMin = kMax / 4;
-    int L = 0;
-    for (auto &sn : S.sn) L = std::max(L, sn.level + 1);
-    S.n_levels = L;
-    std::vector<int64_t> lvl_entries(L, 0);
-    for (auto &sn : S.sn) lvl_entries[sn.level] += fwd_row_off(sn.ncol + sn.nrow, sn.ncol, sn.ldc);
-    S.fwd_lvl_ptr.assign(L + 1, 0);
-    S.bwd_lvl_ptr.assign(L + 1, 0);
-    S.fwd_lvl_ld.assign(L, 0);
-    S.bwd_lvl_ld.assign(L, 0);
-    S.fwd_lvl_q.assign(L, 0);
-    S.bwd_lvl_q.assign(L, 0);
-    S.fwd_items.clear();
-    S.bwd_items.clear();
-    for (int l = 0; l < L; ++l) {
-        const int target = (int)std::min<int64_t>(kMax, std::max<int64_t>(kMin, lvl_entries[l] / 400));
-        S.fwd_lvl_ptr[l] = (int)S.fwd_items.size();
-        for (int s = 0; s < ns; ++s) {
-            const SupernodeHost &sn = S.sn[s];
-            if (sn.level != l || sn.ncol == 0) continue;
-            const int nc = sn.ncol, rows = nc + sn.nrow;
-            S.fwd_lvl_ld[l] = std::max(S.fwd_lvl_ld[l], sn.ldc);
-            // consecutive rows up to `target` entries; the triangle (rows < nc)
-            // and the rectangle get separate items
-            for (int r0 = 0; r0 < rows;) {
-                const int lim = r0 < nc ? nc : rows;
-                int r1 = r0 + 1;
-                while (r1 < lim && fwd_row_off(r1 + 1, nc, sn.ldc) - fwd_row_off(r0, nc, sn.ldc) <= target) ++r1;
-                const int entries = (int)(fwd_row_off(r1, nc, sn.ldc) - fwd_row_off(r0, nc, sn.ldc));
-                if (entries > kMax) {
-                    err = "a factor row does not fit the sweeps' shared-memory buffer";
-                    return HQN_ERR_UNSUPPORTED;
-                }
-                S.fwd_lvl_q[l] = std::max(S.fwd_lvl_q[l], entries);
-                S.fwd_items.push_back({s, r0, r1, lanes_for(fwd_row_len(r1 - 1, nc, sn.ldc))});
-                r0 = r1;
-            }
-        }
-    }
-    S.fwd_lvl_ptr[L] = (int)S.fwd_items.size();
-    // backward: tree level l (launched from the root level down).  Rows of
-    // Q_s^T longer than kLongRow entries are split into chunks of 32 rows x
-    // kChunk entries, so an item gathers a short piece of w instead of the
-    // whole vector (a few columns per item would otherwise each gather all of it).
-    constexpr int kBlockCols = 32;
-    const int kChunk = VN == 4 ? 256 : 128;
-    const int kLongRow = 4 * kChunk;
-    S.n_bwd_blocks = 0;
-    for (int l = 0; l < L; ++l) {
-        const int target = (int)std::min<int64_t>(kMax, std::max<int64_t>(kMin, lvl_entries[l] / 400));
-        S.bwd_lvl_ptr[l] = (int)S.bwd_items.size();
-        for (int s = 0; s < ns; ++s) {
-            const SupernodeHost &sn = S.sn[s];
-            if (sn.level != l || sn.ncol == 0) continue;
-            for (int c0 = 0; c0 < sn.ncol;) {
-                const int w0 = bwd_row_start(c0);
-                if (sn.ldr - w0 > kLongRow) {
-                    const int c1 = std::min(sn.ncol, c0 + kBlockCols);
-                    const int nch = (sn.ldr - w0 + kChunk - 1) / kChunk;
-                    for (int k = 0; k < nch; ++k) {
-                        BwdItem it{s, c0, c1, lanes_for(kChunk)};
-                        it.e0 = w0 + k * kChunk;
-                        it.e1 = std::min(sn.ldr, it.e0 + kChunk);
-                        it.cb = S.n_bwd_blocks;
-                        it.nch = nch;
-                        it.k = k;
-                        S.bwd_lvl_q[l] = std::max(S.bwd_lvl_q[l], (c1 - c0) * (it.e1 - it.e0));
-                        S.bwd_lvl_ld[l] = std::max(S.bwd_lvl_ld[l], it.e1 - it.e0);
-                        S.bwd_items.push_back(it);
-                    }
-                    ++S.n_bwd_blocks;
-                    c0 = c1;
-                    continue;
-                }
-                int c1 = c0 + 1;
-                while (c1 < sn.ncol && bwd_row_off(c1 + 1, sn.ldr) - bwd_row_off(c0, sn.ldr) <= target) ++c1;
-                const int entries = (int)(bwd_row_off(c1, sn.ldr) - bwd_row_off(c0, sn.ldr));
-                if (entries > kMax) {
-                    err = "a factor row does not fit the sweeps' shared-memory buffer";
-                    return HQN_ERR_UNSUPPORTED;
-                }
-                S.bwd_lvl_q[l] = std::max(S.bwd_lvl_q[l], entries);
-                S.bwd_lvl_ld[l] = std::max(S.bwd_lvl_ld[l], sn.ldr - w0);
-                S.bwd_items.push_back({s, c0, c1, lanes_for(sn.ldr - w0)});
-                c0 = c1;
-            }
-        }
-    }
-    S.bwd_lvl_ptr[L] = (int)S.bwd_items.size();
-    // the longest vector a sweep block stages (what bounds its shared memory)
+    S.n_levels = 0;
+    for (auto &sn : S.sn) S.n_levels = std::max(S.n_levels, sn.level + 1);
+    // level schedule: a level's entries spread over ~400 items (a few blocks
+    // per SM), each within [kMax/4, kMax] entries, kMax = 64 KB; pipelined
+    // schedule: items of at most one 32 KB ring slot, ~600 per level
+    int rc = make_items(S, VN, 65536 / esize, 400, S.lv, err);
+    if (rc == HQN_OK) rc = make_items(S, VN, kPipeSlotBytes / esize, 600, S.pp, err);
+    if (rc != HQN_OK) return rc;
+    // the longest vector a level-schedule block stages (what bounds its shared memory)
     S.max_ld = 0;
-    for (int l = 0; l < L; ++l) S.max_ld = std::max(S.max_ld, std::max(S.fwd_lvl_ld[l], S.bwd_lvl_ld[l]));
+    for (int l = 0; l < S.n_levels; ++l)
+        S.max_ld = std::max(S.max_ld, std::max(S.lv.fwd_lvl_ld[l], S.lv.bwd_lvl_ld[l]));
 
     S.setup_seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();

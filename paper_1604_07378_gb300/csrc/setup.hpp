@@ -43,6 +43,21 @@ struct FwdItem { int s, row0, row1, G; };  // rows [row0, row1) of Q_s f
 // of the column block's nch chunks to finish (chunk k of block cb) combines.
 struct BwdItem { int s, col0, col1, G, e0 = -1, e1 = 0, cb = -1, nch = 1, k = 0; };
 
+// Work items of both sweeps, grouped by tree level.
+struct ItemLists {
+    std::vector<int> fwd_lvl_ptr, bwd_lvl_ptr;  // items of level l: [ptr[l], ptr[l+1])
+    std::vector<int> fwd_lvl_ld, bwd_lvl_ld;    // longest vectors an item of the level stages (forward:
+                                                // f plus its rectangle rows' child updates)
+    std::vector<int> fwd_lvl_q, bwd_lvl_q;      // max factor entries of one item of the level
+    int n_bwd_blocks = 0;                       // column blocks of the backward chunk items
+    std::vector<FwdItem> fwd_items;
+    std::vector<BwdItem> bwd_items;
+};
+
+// Bytes of one shared-memory ring slot of the pipelined sweeps: the factor
+// rows of one work item.
+constexpr int kPipeSlotBytes = 32768;
+
 struct Setup {
     int n = 0, T = 0, n_free = 0;
     double h = 1.0 / 30.0, k = 0.0, density = 0.0;
@@ -65,12 +80,8 @@ struct Setup {
     std::vector<int> fg2, ug2;       // the same maps as pairs (-1 = none): at most two
                                      // children (a binary dissection tree) feed an entry
     int n_upd = 0, n_levels = 0;
-    std::vector<int> fwd_lvl_ptr, bwd_lvl_ptr;  // items of level l: [ptr[l], ptr[l+1])
-    std::vector<int> fwd_lvl_ld, bwd_lvl_ld;    // max ldc / ldr over the level's supernodes
-    std::vector<int> fwd_lvl_q, bwd_lvl_q;      // max factor entries of one work item of the level
-    int n_bwd_blocks = 0;            // column blocks of the backward chunk items
-    std::vector<FwdItem> fwd_items;
-    std::vector<BwdItem> bwd_items;
+    ItemLists lv;                    // items of the level-by-level schedules
+    ItemLists pp;                    // items of the pipelined schedule (one ring slot each)
     int64_t qf_total = 0, qb_total = 0;  // entries of the two packed copies
     int max_ld = 0;                  // longest vector a sweep block stages (bounds its shared memory)
     int max_front_cols = 0;          // max ncol

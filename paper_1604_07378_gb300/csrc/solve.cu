@@ -21,7 +21,8 @@
 // a row with that vector, computed by a group of G lanes with 16-byte
 // shared-memory loads, two rows per group at a time.
 //
-// Consecutive levels are chained by programmatic dependent launch: a level's
+// Consecutive levels are chained by programmatic dependent launch: every
+// block allows the next level to launch as soon as it starts, so a level's
 // blocks may start while the previous level still runs.  Before
 // griddepcontrol.wait a block touches only data that no sweep writes (its
 // item record, the factor rows, the index tables); the vectors produced by
@@ -155,16 +156,21 @@ __device__ __forceinline__ V4<double> ld_cg(const V4<double> *p) {
 // Rows [r0, r1) of Q_s (in shared memory at qs, first row at offset off0 of
 // the supernode's block) times f: z_C for rows < nc, update entries (plus the
 // <= 2 child entries) for rows >= nc.
+// nt threads (tid = 0..nt-1, nt a multiple of 32) share the rows; f's three
+// components lie fs entries apart.
+// ua (if not null): the child update entries of rows [rr0, ...) already
+// summed, three components ua_s entries apart.
 template <typename R, int G>
 __device__ __forceinline__ void fwd_rows(const DevSolve<R> &S, int col, int nc, int ldc, int uoff, int r0, int r1,
-                                         int off0, const R *qs, const R *f, int ldf, V4<R> *z) {
+                                         int off0, const R *qs, const R *f, int fs, V4<R> *z, int tid, int nt,
+                                         const R *ua, int ua_s, int rr0) {
     using VT = typename Vec16<R>::T;
     constexpr int VN = Vec16<R>::N;
-    constexpr int NG = SBS / G;
-    const int lane = threadIdx.x % G, grp = threadIdx.x / G;
+    const int NG = nt / G;
+    const int lane = tid % G, grp = tid / G;
     const VT *fx = reinterpret_cast<const VT *>(f);
-    const VT *fy = reinterpret_cast<const VT *>(f + ldf);
-    const VT *fz = reinterpret_cast<const VT *>(f + 2 * ldf);
+    const VT *fy = reinterpret_cast<const VT *>(f + fs);
+    const VT *fz = reinterpret_cast<const VT *>(f + 2 * fs);
     for (int base = r0; base < r1; base += 2 * NG) {
         const int i0 = base + 2 * grp, i1 = i0 + 1;
         const bool v0 = i0 < r1, v1 = i1 < r1;
@@ -197,9 +203,13 @@ __device__ __forceinline__ void fwd_rows(const DevSolve<R> &S, int col, int nc, 
                 if (i < nc) {
                     z[col + i] = o;
                 } else {
-                    const int2 c = S.ug2[uoff + i - nc];
-                    if (c.x >= 0) { const V4<R> a = ld_cg(S.u + c.x); o.x += a.x; o.y += a.y; o.z += a.z; }
-                    if (c.y >= 0) { const V4<R> a = ld_cg(S.u + c.y); o.x += a.x; o.y += a.y; o.z += a.z; }
+                    if (ua) {
+                        o.x += ua[i - rr0]; o.y += ua[ua_s + i - rr0]; o.z += ua[2 * ua_s + i - rr0];
+                    } else {
+                        const int2 c = S.ug2[uoff + i - nc];
+                        if (c.x >= 0) { const V4<R> a = ld_cg(S.u + c.x); o.x += a.x; o.y += a.y; o.z += a.z; }
+                        if (c.y >= 0) { const V4<R> a = ld_cg(S.u + c.y); o.x += a.x; o.y += a.y; o.z += a.z; }
+                    }
                     S.u[uoff + i - nc] = o;
                 }
             }
@@ -207,10 +217,26 @@ __device__ __forceinline__ void fwd_rows(const DevSolve<R> &S, int col, int nc, 
     }
 }
 
+template <typename R>
+__device__ __forceinline__ void fwd_rows_g(int G, const DevSolve<R> &S, int col, int nc, int ldc, int uoff, int r0,
+                                           int r1, int off0, const R *qs, const R *f, int fs, V4<R> *z, int tid,
+                                           int nt, const R *ua = nullptr, int ua_s = 0, int rr0 = 0) {
+    switch (G) {
+        case 1: fwd_rows<R, 1>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, fs, z, tid, nt, ua, ua_s, rr0); break;
+        case 2: fwd_rows<R, 2>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, fs, z, tid, nt, ua, ua_s, rr0); break;
+        case 4: fwd_rows<R, 4>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, fs, z, tid, nt, ua, ua_s, rr0); break;
+        case 8: fwd_rows<R, 8>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, fs, z, tid, nt, ua, ua_s, rr0); break;
+        case 16: fwd_rows<R, 16>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, fs, z, tid, nt, ua, ua_s, rr0); break;
+        default: fwd_rows<R, 32>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, fs, z, tid, nt, ua, ua_s, rr0); break;
+    }
+}
+
 // One forward work item (record `rec`, 4 int4).  Shared memory: qs = the
-// item's factor rows (qcap entries), then f (3 x ldf entries), then the
-// columns' child update entries (ldf int2).  `wait_inputs` runs between the
-// reads of static data and the reads of vectors other items produce.
+// item's factor rows (qcap entries), then f (3 x ldf entries), then the summed
+// child update entries of its rectangle rows (3 x pad4(nrr) entries), then
+// their index pairs (ldf int2 for the columns, nrr int2 for the rows).  Every
+// load of a vector another item produces is issued in one parallel pass
+// after `wait_inputs`, so the row products read only shared memory.
 template <typename R, typename Wait>
 __device__ __forceinline__ void fwd_item(const DevSolve<R> &S, const int4 *rec, int qcap, R *qs, uint64_t *bar,
                                          uint32_t parity, const V4<R> *rhs, V4<R> *z, Wait wait_inputs) {
@@ -219,36 +245,50 @@ __device__ __forceinline__ void fwd_item(const DevSolve<R> &S, const int4 *rec, 
     const int4 b = rec[1], c = rec[2];
     const int col = b.x, nc = b.y, ldc = b.z, uoff = b.w;
     const int r0 = c.x, r1 = c.y, ldf = c.z, off0 = c.w;
+    const int rr0 = r0 > nc ? r0 : nc, nrr = r1 > rr0 ? r1 - rr0 : 0, nrr4 = pad4(nrr);
     R *f = qs + qcap;
-    int2 *cidx = reinterpret_cast<int2 *>(f + 3 * ldf);
+    R *ua = f + 3 * ldf;
+    int2 *cidx = reinterpret_cast<int2 *>(ua + 3 * nrr4);
+    int2 *ridx = cidx + ldf;
     const int nf = ldf < nc ? ldf : nc;
     for (int j = threadIdx.x; j < nf; j += SBS) cidx[j] = S.fg2[col + j];
+    for (int j = threadIdx.x; j < nrr; j += SBS) ridx[j] = S.ug2[uoff + rr0 - nc + j];
     if (!wait_inputs()) {
         if (threadIdx.x == 0) bulk_load_wait(bar, parity);  // let the copy in flight land first
         return;
     }
-    // f = q_C - (child updates on C), entries [0, ldf); zero beyond nc
-#pragma unroll 4
-    for (int j = threadIdx.x; j < ldf; j += SBS) {
-        R vx = R(0), vy = R(0), vz = R(0);
+    // f = q_C - (child updates on C), entries [0, ldf), zero beyond nc; and
+    // the child updates landing on the rectangle rows
+    const int nj = ldf > nrr ? ldf : nrr;
+#pragma unroll 2
+    for (int j = threadIdx.x; j < nj; j += SBS) {
+        V4<R> v, u0, u1, w0, w1;
+        v.x = v.y = v.z = u0.x = u0.y = u0.z = u1.x = u1.y = u1.z = R(0);
+        w0 = u0; w1 = u0;
         if (j < nc) {
-            const V4<R> v = ld_cg(rhs + col + j);
             const int2 ci = cidx[j];
-            vx = v.x; vy = v.y; vz = v.z;
-            if (ci.x >= 0) { const V4<R> u = ld_cg(S.u + ci.x); vx -= u.x; vy -= u.y; vz -= u.z; }
-            if (ci.y >= 0) { const V4<R> u = ld_cg(S.u + ci.y); vx -= u.x; vy -= u.y; vz -= u.z; }
+            v = ld_cg(rhs + col + j);
+            if (ci.x >= 0) u0 = ld_cg(S.u + ci.x);
+            if (ci.y >= 0) u1 = ld_cg(S.u + ci.y);
         }
-        f[j] = vx; f[ldf + j] = vy; f[2 * ldf + j] = vz;
+        if (j < nrr) {
+            const int2 ri = ridx[j];
+            if (ri.x >= 0) w0 = ld_cg(S.u + ri.x);
+            if (ri.y >= 0) w1 = ld_cg(S.u + ri.y);
+        }
+        if (j < ldf) {
+            f[j] = v.x - u0.x - u1.x;
+            f[ldf + j] = v.y - u0.y - u1.y;
+            f[2 * ldf + j] = v.z - u0.z - u1.z;
+        }
+        if (j < nrr) {
+            ua[j] = w0.x + w1.x;
+            ua[nrr4 + j] = w0.y + w1.y;
+            ua[2 * nrr4 + j] = w0.z + w1.z;
+        }
     }
     if (!bulk_load_finish(bar, parity, S.err)) return;
-    switch (a.w) {
-        case 1: fwd_rows<R, 1>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z); break;
-        case 2: fwd_rows<R, 2>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z); break;
-        case 4: fwd_rows<R, 4>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z); break;
-        case 8: fwd_rows<R, 8>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z); break;
-        case 16: fwd_rows<R, 16>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z); break;
-        default: fwd_rows<R, 32>(S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z); break;
-    }
+    fwd_rows_g<R>(a.w, S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z, (int)threadIdx.x, SBS, ua, nrr4, rr0);
 }
 
 // Level-synchronous schedule: one launch per tree level, one item per block.
@@ -259,8 +299,8 @@ __global__ void __launch_bounds__(SBS) k_fwd(DevSolve<R> S, int item0, int qcap,
     if (threadIdx.x == 0) bulk_bar_init(&bar);
     fwd_item<R>(S, S.fwd_items + 4 * (size_t)(item0 + blockIdx.x), qcap, reinterpret_cast<R *>(smem_raw), &bar, 0u,
                 rhs, z, []() {
-                    pdl_wait();
                     pdl_trigger();
+                    pdl_wait();
                     return true;
                 });
 }
@@ -273,16 +313,18 @@ __global__ void __launch_bounds__(SBS) k_fwd(DevSolve<R> S, int item0, int qcap,
 // its diagonal start on.  Chunk items (CHUNK true): row j sits at
 // qs + (j - c0) lw, aligned with w, holding its entries of the chunk.
 // The sums go to r[col + j], or to out[j - c0] (a chunk's partial sums).
+// nt threads (tid = 0..nt-1, nt a multiple of 32) share the rows; w's three
+// components lie ws entries apart.
 template <typename R, int G, bool CHUNK>
 __device__ __forceinline__ void bwd_rows(int col, int ldr, int c0, int c1, int off0, const R *qs, const R *w,
-                                         int lw, int w0, V4<R> *r, V4<R> *out) {
+                                         int ws, int lw, int w0, V4<R> *r, V4<R> *out, int tid, int nt) {
     using VT = typename Vec16<R>::T;
     constexpr int VN = Vec16<R>::N;
-    constexpr int NG = SBS / G;
-    const int lane = threadIdx.x % G, grp = threadIdx.x / G;
+    const int NG = nt / G;
+    const int lane = tid % G, grp = tid / G;
     const VT *wx = reinterpret_cast<const VT *>(w);
-    const VT *wy = reinterpret_cast<const VT *>(w + lw);
-    const VT *wz = reinterpret_cast<const VT *>(w + 2 * lw);
+    const VT *wy = reinterpret_cast<const VT *>(w + ws);
+    const VT *wz = reinterpret_cast<const VT *>(w + 2 * ws);
     const int kend = lw / VN;
     for (int base = c0; base < c1; base += 2 * NG) {
         const int j0 = base + 2 * grp, j1 = j0 + 1;
@@ -332,14 +374,15 @@ __device__ __forceinline__ void bwd_rows(int col, int ldr, int c0, int c1, int o
 
 template <typename R, bool CHUNK>
 __device__ __forceinline__ void bwd_rows_g(int G, int col, int ldr, int c0, int c1, int off0, const R *qs,
-                                           const R *w, int lw, int w0, V4<R> *r, V4<R> *out) {
+                                           const R *w, int ws, int lw, int w0, V4<R> *r, V4<R> *out, int tid,
+                                           int nt) {
     switch (G) {
-        case 1: bwd_rows<R, 1, CHUNK>(col, ldr, c0, c1, off0, qs, w, lw, w0, r, out); break;
-        case 2: bwd_rows<R, 2, CHUNK>(col, ldr, c0, c1, off0, qs, w, lw, w0, r, out); break;
-        case 4: bwd_rows<R, 4, CHUNK>(col, ldr, c0, c1, off0, qs, w, lw, w0, r, out); break;
-        case 8: bwd_rows<R, 8, CHUNK>(col, ldr, c0, c1, off0, qs, w, lw, w0, r, out); break;
-        case 16: bwd_rows<R, 16, CHUNK>(col, ldr, c0, c1, off0, qs, w, lw, w0, r, out); break;
-        default: bwd_rows<R, 32, CHUNK>(col, ldr, c0, c1, off0, qs, w, lw, w0, r, out); break;
+        case 1: bwd_rows<R, 1, CHUNK>(col, ldr, c0, c1, off0, qs, w, ws, lw, w0, r, out, tid, nt); break;
+        case 2: bwd_rows<R, 2, CHUNK>(col, ldr, c0, c1, off0, qs, w, ws, lw, w0, r, out, tid, nt); break;
+        case 4: bwd_rows<R, 4, CHUNK>(col, ldr, c0, c1, off0, qs, w, ws, lw, w0, r, out, tid, nt); break;
+        case 8: bwd_rows<R, 8, CHUNK>(col, ldr, c0, c1, off0, qs, w, ws, lw, w0, r, out, tid, nt); break;
+        case 16: bwd_rows<R, 16, CHUNK>(col, ldr, c0, c1, off0, qs, w, ws, lw, w0, r, out, tid, nt); break;
+        default: bwd_rows<R, 32, CHUNK>(col, ldr, c0, c1, off0, qs, w, ws, lw, w0, r, out, tid, nt); break;
     }
 }
 
@@ -402,16 +445,16 @@ __device__ __forceinline__ void bwd_item(const DevSolve<R> &S, const int4 *rec, 
     }
     if (!bulk_load_finish(bar, parity, S.err)) return;
     if (!chunk) {
-        bwd_rows_g<R, false>(a.w, col, ldr, c0, c1, off0, qs, w, lw, w0, r, nullptr);
+        bwd_rows_g<R, false>(a.w, col, ldr, c0, c1, off0, qs, w, lw, lw, w0, r, nullptr, (int)threadIdx.x, SBS);
         return;
     }
     const int nch = e.w >> 16, kch = e.w & 0xffff;
     if (nch == 1) {
-        bwd_rows_g<R, true>(a.w, col, ldr, c0, c1, off0, qs, w, lw, w0, r, nullptr);
+        bwd_rows_g<R, true>(a.w, col, ldr, c0, c1, off0, qs, w, lw, lw, w0, r, nullptr, (int)threadIdx.x, SBS);
         return;
     }
     V4<R> *mine = S.part_r + (size_t)item * 32;
-    bwd_rows_g<R, true>(a.w, col, ldr, c0, c1, off0, qs, w, lw, w0, r, mine);
+    bwd_rows_g<R, true>(a.w, col, ldr, c0, c1, off0, qs, w, lw, lw, w0, r, mine, (int)threadIdx.x, SBS);
     // the last chunk of the column block to get here combines the partials
     __shared__ int last;
     __syncthreads();
@@ -444,8 +487,8 @@ __global__ void __launch_bounds__(SBS) k_bwd(DevSolve<R> S, int item0, int qcap,
     const int item = item0 + blockIdx.x;
     bwd_item<R>(S, S.bwd_items + 5 * (size_t)item, item, qcap, reinterpret_cast<R *>(smem_raw), &bar, 0u, z, r,
                 []() {
-                    pdl_wait();
                     pdl_trigger();
+                    pdl_wait();
                     return true;
                 });
 }
@@ -557,11 +600,404 @@ __global__ void __launch_bounds__(SBS) k_bwd_dyn(DevSolve<R> S, int qcap, const 
     }
 }
 
+// ---- pipelined schedule: one persistent launch per sweep, one block per SM
+//
+// Each block owns a fixed list of bundles (consecutive items of one tree
+// level), in level order: ascending for the forward sweep, descending for the
+// backward one.  Its last warp is a producer: it streams the factor rows of
+// the block's items, in order, into a ring of shared-memory slots (one bulk
+// copy per item, completion on the slot's `full` mbarrier) as soon as the
+// consumers release a slot (its `empty` mbarrier, one arrival per consumer
+// warp) -- the factor does not depend on the sweep, so the stream runs ahead
+// across levels while the consumers wait for other blocks.  The other warps
+// consume a bundle in four steps: wait until the items it reads from (other
+// blocks' or its own) have published, gather the vector its rows multiply
+// into the vector area (one segment per supernode), run its items' row dot
+// products from the ring, then publish (per-supernode completion counters).
+//
+// Progress: every block's waits are on items of earlier levels only, and the
+// grid is at most one block per SM with all blocks resident (the launch
+// asks for exactly the blocks that fit), so the lowest unfinished level
+// always advances.  Every wait is bounded; past the bound the block sets the
+// error flag, skips its remaining work and, before it exits, waits (bounded)
+// for the copies it has in flight.
+
+constexpr int PCONS = 32 * PIPE_CONS_WARPS;  // consumer threads of a pipelined sweep block
+constexpr int PTHREADS = PCONS + 32;        // plus one producer warp
+constexpr int PIPE_SLOT = 32768;            // bytes per ring slot (the host's item bound)
+constexpr long long kEmptyPolls = 1 << 22;  // bound on the producer's wait for a free slot
+
+struct PipeShared {
+    uint64_t full[PIPE_NS_MAX];   // slot holds its item's rows (bulk-copy bytes arrived)
+    uint64_t empty[PIPE_NS_MAX];  // slot released by every consumer warp
+    int abort;                    // set by a thread that gave up; ends the block's work
+    int k_issued;                 // items whose copies the producer has started
+    int seg_aoff[PIPE_SEG_MAX];   // vector-area offsets of the bundle's segments
+    int4 seg[2 * PIPE_SEG_MAX];
+    int mine[PIPE_CMB_MAX];       // this bundle completed the column block: it combines it
+};
+
+__device__ __forceinline__ void cons_sync() { asm volatile("bar.sync 1, %0;" ::"n"(PCONS) : "memory"); }
+// Consumer barrier that also returns, to every consumer, whether any of them
+// passed true.
+__device__ __forceinline__ bool cons_any(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(PCONS)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Producer warp: items [it0, it1) of the block, slot k % ns for the k-th.
+template <typename R, bool BWD>
+__device__ void pipe_produce(const DevSolve<R> &S, int it0, int it1, R *ring, PipeShared &sh, int ns) {
+    constexpr int SLOT_E = PIPE_SLOT / (int)sizeof(R);
+    const int lane = threadIdx.x & 31;
+    volatile int *abort = &sh.abort;
+    for (int it = it0; it < it1; ++it) {
+        const int k = it - it0, slot = k % ns, use = k / ns;
+        int ok = 1;
+        if (lane == 0) {
+            if (use > 0) {
+                ok = 0;
+                for (long long p = 0; p < kEmptyPolls && !*abort; ++p)
+                    if (mbar_test(&sh.empty[slot], (uint32_t)((use - 1) & 1))) {
+                        ok = 1;
+                        break;
+                    }
+                if (!ok && !*abort) {
+                    atomicOr(S.err, 8u);
+                    *abort = 1;
+                }
+            }
+            if (*abort) ok = 0;
+        }
+        if (!__shfl_sync(0xffffffffu, ok, 0)) break;  // lane 0 decides for the warp
+        R *dst = ring + (size_t)slot * SLOT_E;
+        if (!BWD) {
+            const int4 a = S.pf_items[4 * (size_t)it];
+            if (lane == 0) bulk_load_issue(&sh.full[slot], dst, item_src(S.QF, a, sizeof(R)), (uint32_t)a.z);
+        } else {
+            const int4 *rec = S.pb_items + 5 * (size_t)it;
+            const int4 a = rec[0], e = rec[4];
+            if (e.x < 0) {
+                if (lane == 0) bulk_load_issue(&sh.full[slot], dst, item_src(S.QB, a, sizeof(R)), (uint32_t)a.z);
+            } else {
+                // a chunk item: row j's piece [max(e0, start_j), e1) at dst + (j - c0) lw
+                const int4 c = rec[2];
+                const int c0 = c.x, c1 = c.y, ldr = c.z;
+                const int w0 = e.x, lw = e.y - e.x;
+                if (lane == 0) bulk_expect(&sh.full[slot], (uint32_t)a.z);
+                const int j = c0 + lane;
+                if (j < c1) {
+                    const int st = bwd_row_start(j);
+                    const int seg = st > w0 ? st : w0;
+                    const int len = w0 + lw - seg;
+                    if (len > 0) {
+                        const R *src =
+                            static_cast<const R *>(item_src(S.QB, a, sizeof(R))) + bwd_row_off(j, ldr) + (seg - st);
+                        bulk_copy(&sh.full[slot], dst + (size_t)(j - c0) * lw + (seg - w0), src,
+                                  (uint32_t)(len * sizeof(R)));
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) sh.k_issued = k + 1;
+    }
+}
+
+// Segment of vector-area entry e: the last one starting at or before it.
+__device__ __forceinline__ int pipe_seg_of(const PipeShared &sh, int nseg, int e) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sh.seg_aoff[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Gathers take PG entries per thread at a time: every load of a round is
+// issued before any result is used, so a round costs two dependent trips to
+// memory (index, then value) whatever PG is.
+constexpr int PG = 4;
+
+// Consumers, forward: f = q_C - (child updates on C) for every segment.
+template <typename R>
+__device__ __forceinline__ void pipe_gather_fwd(const DevSolve<R> &S, const PipeShared &sh, int nseg, int ftot, R *F,
+                                                int fcap, const V4<R> *rhs) {
+    for (int base = threadIdx.x; base < ftot; base += PG * PCONS) {
+        V4<R> v[PG];
+        int2 ci[PG];
+#pragma unroll
+        for (int g = 0; g < PG; ++g) {
+            const int e = base + g * PCONS;
+            v[g].x = v[g].y = v[g].z = v[g].w = R(0);
+            ci[g] = make_int2(-1, -1);
+            if (e < ftot) {
+                const int4 sg = sh.seg[pipe_seg_of(sh, nseg, e)];  // {col, filled, area offset, length}
+                const int j = e - sg.z;
+                if (j < sg.y) {
+                    v[g] = ld_cg(rhs + sg.x + j);
+                    ci[g] = __ldg(S.fg2 + sg.x + j);
+                }
+            }
+        }
+        V4<R> a[PG], b[PG];
+#pragma unroll
+        for (int g = 0; g < PG; ++g) {
+            a[g].x = a[g].y = a[g].z = R(0);
+            b[g].x = b[g].y = b[g].z = R(0);
+            if (ci[g].x >= 0) a[g] = ld_cg(S.u + ci[g].x);
+            if (ci[g].y >= 0) b[g] = ld_cg(S.u + ci[g].y);
+        }
+#pragma unroll
+        for (int g = 0; g < PG; ++g) {
+            const int e = base + g * PCONS;
+            if (e < ftot) {
+                F[e] = v[g].x - a[g].x - b[g].x;
+                F[fcap + e] = v[g].y - a[g].y - b[g].y;
+                F[2 * fcap + e] = v[g].z - a[g].z - b[g].z;
+            }
+        }
+    }
+}
+
+// Consumers, backward: w = [z_C; -r_R] over each segment's range.
+template <typename R>
+__device__ __forceinline__ void pipe_gather_bwd(const DevSolve<R> &S, const PipeShared &sh, int nseg, int ftot, R *F,
+                                                int fcap, const V4<R> *z, const V4<R> *r) {
+    for (int base = threadIdx.x; base < ftot; base += PG * PCONS) {
+        int src[PG];
+        R sgn[PG];
+#pragma unroll
+        for (int g = 0; g < PG; ++g) {
+            const int e = base + g * PCONS;
+            src[g] = -1;
+            sgn[g] = R(1);
+            if (e < ftot) {
+                const int q = pipe_seg_of(sh, nseg, e);
+                const int4 sa = sh.seg[2 * q], sb = sh.seg[2 * q + 1];  // {col, nc, nrow, roff} {w0, aoff, len, 0}
+                const int i = sb.x + (e - sb.y);
+                if (i < sa.y) {
+                    src[g] = sa.x + i;
+                } else if (i < sa.y + sa.z) {
+                    src[g] = __ldg(S.rows + sa.w + i - sa.y);
+                    sgn[g] = R(-1);
+                }
+            }
+        }
+        V4<R> v[PG];
+#pragma unroll
+        for (int g = 0; g < PG; ++g) {
+            v[g].x = v[g].y = v[g].z = R(0);
+            if (src[g] >= 0) v[g] = ld_cg((sgn[g] > R(0) ? z : r) + src[g]);
+        }
+#pragma unroll
+        for (int g = 0; g < PG; ++g) {
+            const int e = base + g * PCONS;
+            if (e < ftot) {
+                F[e] = sgn[g] * v[g].x;
+                F[fcap + e] = sgn[g] * v[g].y;
+                F[2 * fcap + e] = sgn[g] * v[g].z;
+            }
+        }
+    }
+}
+
+// Consumer warps: bundles [b0, b1) of the block, whose items start at it0.
+// Forward: in = q, out = z.  Backward: in = z, out = r.
+template <typename R, bool BWD>
+__device__ void pipe_consume(const DevSolve<R> &S, int b0, int b1, int it0, const R *ring, R *F, PipeShared &sh,
+                             const V4<R> *in, V4<R> *out) {
+    constexpr int SLOT_E = PIPE_SLOT / (int)sizeof(R);
+    const int tid = threadIdx.x;
+    const int ns = S.pipe_ns, fcap = S.pipe_fcap;
+    const int4 *bund = BWD ? S.pb_bund : S.pf_bund;
+    const int4 *segs = BWD ? S.pb_seg : S.pf_seg;
+    const int2 *dep = BWD ? S.pb_dep : S.pf_dep;
+    const int2 *sig = BWD ? S.pb_sig : S.pf_sig;
+    int *done = BWD ? S.bwd_done : S.fwd_done;
+    volatile int *abort = &sh.abort;
+    for (int b = b0; b < b1; ++b) {
+        const int4 B0 = bund[3 * (size_t)b], B1 = bund[3 * (size_t)b + 1], B2 = bund[3 * (size_t)b + 2];
+        // 1. the items this bundle reads from have published
+        if (tid < B1.y - B1.x) {
+            const int2 d = dep[B1.x + tid];
+            if (!dep_wait(done, d.x, d.y, S.err)) *abort = 1;
+        }
+        if (tid == 0 && *(volatile unsigned int *)S.err) *abort = 1;
+        const int nseg = B0.w - B0.z;
+        for (int i = tid; i < nseg; i += PCONS) {
+            if (BWD) {
+                const int4 sa = segs[2 * (size_t)(B0.z + i)], sb = segs[2 * (size_t)(B0.z + i) + 1];
+                sh.seg[2 * i] = sa;
+                sh.seg[2 * i + 1] = sb;
+                sh.seg_aoff[i] = sb.y;
+            } else {
+                const int4 sg = segs[B0.z + i];
+                sh.seg[i] = sg;
+                sh.seg_aoff[i] = sg.z;
+            }
+        }
+        if (cons_any(*abort)) break;
+        // 2. the vector the rows multiply
+        if (BWD) pipe_gather_bwd<R>(S, sh, nseg, B2.z, F, fcap, in, out);
+        else pipe_gather_fwd<R>(S, sh, nseg, B2.z, F, fcap, in);
+        cons_sync();
+        // 3. the items, from the ring: all of the bundle's items are resident
+        // at once (the host keeps a bundle within half the ring); each runs on
+        // its own range of consumer warps (item record: warps [w0, w1))
+        bool ready = true;
+        for (int it = B0.x; it < B0.y; ++it) {
+            const int k = it - it0;
+            ready = ready && bulk_load_wait(&sh.full[k % ns], (uint32_t)((k / ns) & 1));
+        }
+        if (!ready) *abort = 1;
+        if (cons_any(!ready || *abort)) break;
+        {
+            const int warp = tid >> 5;
+            int it = B0.x;
+            int4 d = BWD ? S.pb_items[5 * (size_t)it + 3] : S.pf_items[4 * (size_t)it + 3];
+            while (warp >= d.w && it + 1 < B0.y) {
+                ++it;
+                d = BWD ? S.pb_items[5 * (size_t)it + 3] : S.pf_items[4 * (size_t)it + 3];
+            }
+            const int k = it - it0;
+            const R *qs = ring + (size_t)(k % ns) * SLOT_E;
+            const int ltid = tid - 32 * d.z, lnt = 32 * (d.w - d.z);
+            if (!BWD) {
+                const int4 *rec = S.pf_items + 4 * (size_t)it;
+                const int4 a = rec[0], bb = rec[1], c = rec[2];
+                fwd_rows_g<R>(a.w, S, bb.x, bb.y, bb.z, bb.w, c.x, c.y, c.w, qs, F + d.x, fcap, out, ltid, lnt);
+            } else {
+                const int4 *rec = S.pb_items + 5 * (size_t)it;
+                const int4 a = rec[0], bb = rec[1], c = rec[2], e = rec[4];
+                const int c0 = c.x, c1 = c.y, ldr = c.z, off0 = c.w;
+                if (e.x < 0) {
+                    const int w0 = bwd_row_start(c0);
+                    bwd_rows_g<R, false>(a.w, bb.x, ldr, c0, c1, off0, qs, F + d.x, fcap, ldr - w0, w0, out, nullptr,
+                                         ltid, lnt);
+                } else {
+                    const int nch = e.w >> 16, kch = e.w & 0xffff;
+                    V4<R> *part = nch > 1 ? S.pb_part + (size_t)(d.y + kch) * 32 : nullptr;
+                    bwd_rows_g<R, true>(a.w, bb.x, ldr, c0, c1, off0, qs, F + d.x, fcap, e.y - e.x, e.x, out, part,
+                                        ltid, lnt);
+                }
+            }
+            __syncwarp();
+            if ((tid & 31) == 0)
+                for (int q = B0.x; q < B0.y; ++q) mbar_arrive(&sh.empty[(q - it0) % ns]);
+        }
+        if (cons_any(*abort)) break;
+        // 4. (backward) column blocks whose last chunks this bundle ran: add
+        // the chunks' partial sums in chunk order
+        if (BWD && B2.y > B2.x) {
+            const int ncmb = B2.y - B2.x;
+            if (tid < ncmb) {
+                const int4 c = S.pb_cmb[2 * (size_t)(B2.x + tid)];  // {column block, count, pslot0, nch}
+                __threadfence();
+                sh.mine[tid] = atomicAdd(S.pb_cbc + c.x, c.y) + c.y == c.w;
+            }
+            cons_sync();
+            for (int q = 0; q < ncmb; ++q) {
+                if (!sh.mine[q]) continue;
+                const int4 c = S.pb_cmb[2 * (size_t)(B2.x + q)], o = S.pb_cmb[2 * (size_t)(B2.x + q) + 1];
+                __threadfence();
+                if (tid < o.y) {
+                    R sx = R(0), sy = R(0), sz = R(0);
+                    for (int kk = 0; kk < c.w; ++kk) {
+                        const V4<R> p = ld_cg(S.pb_part + (size_t)(c.z + kk) * 32 + tid);
+                        sx += p.x; sy += p.y; sz += p.z;
+                    }
+                    V4<R> v; v.x = sx; v.y = sy; v.z = sz; v.w = R(0);
+                    out[o.x + tid] = v;
+                }
+                if (tid == 0) S.pb_cbc[c.x] = 0;
+            }
+            cons_sync();
+        }
+        // 5. publish
+        if (tid < B1.w - B1.z) {
+            const int2 g = sig[B1.z + tid];
+            __threadfence();
+            atomicAdd(done + g.x, g.y);
+        }
+    }
+}
+
+template <typename R, bool BWD>
+__global__ void __launch_bounds__(PTHREADS, 1) k_pipe(DevSolve<R> S, const V4<R> *in, V4<R> *out) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ PipeShared sh;
+    constexpr int SLOT_E = PIPE_SLOT / (int)sizeof(R);
+    const int ns = S.pipe_ns;
+    R *ring = reinterpret_cast<R *>(smem_raw);
+    R *F = ring + (size_t)ns * SLOT_E;
+    const int tid = threadIdx.x;
+    // the other sweep's counters start from zero in the next solve
+    int *other = BWD ? S.fwd_done : S.bwd_done;
+    for (int i = blockIdx.x * PTHREADS + tid; i < S.n_sn; i += gridDim.x * PTHREADS) other[i] = 0;
+    if (tid == 0) {
+        for (int q = 0; q < ns; ++q) {
+            mbar_init(&sh.full[q], 1);
+            mbar_init(&sh.empty[q], PCONS / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sh.abort = 0;
+        sh.k_issued = 0;
+    }
+    __syncthreads();
+    const int *blk = BWD ? S.pb_blk : S.pf_blk;
+    const int4 *bund = BWD ? S.pb_bund : S.pf_bund;
+    const int b0 = blk[blockIdx.x], b1 = blk[blockIdx.x + 1];
+    if (b1 > b0) {
+        const int it0 = bund[3 * (size_t)b0].x, it1 = bund[3 * (size_t)(b1 - 1)].y;
+        if (tid >= PCONS) pipe_produce<R, BWD>(S, it0, it1, ring, sh, ns);
+        else pipe_consume<R, BWD>(S, b0, b1, it0, ring, F, sh, in, out);
+    }
+    __syncthreads();
+    // copies still in flight land before the block exits (only after an error
+    // can the last use of a slot be unconsumed)
+    if (tid == 0 && sh.abort) {
+        const int n = sh.k_issued;
+        for (int q = 0; q < ns && q < n; ++q) {
+            const int last = q + ((n - 1 - q) / ns) * ns;
+            if (!bulk_load_wait(&sh.full[q], (uint32_t)((last / ns) & 1))) atomicOr(S.err, 4u);
+        }
+    }
+}
+
 // Dynamic shared memory of a sweep block: qcap factor entries, 3 x ld vector
 // entries and ld 8-byte index slots.
 template <typename R>
 size_t sweep_smem(int qcap, int ld) {
     return ((size_t)qcap + 3 * (size_t)ld) * sizeof(R) + 8 * (size_t)ld;
+}
+
+// Dynamic shared memory of a pipelined sweep block: ns ring slots and the
+// vector area (three components of fcap entries).
+template <typename R>
+size_t pipe_smem(int ns, int fcap) {
+    return (size_t)ns * PIPE_SLOT + 3 * (size_t)fcap * sizeof(R);
 }
 
 // One level's launch, with the programmatic-serialisation attribute when
@@ -595,11 +1031,42 @@ template <typename R> cudaError_t solve_prepare() {
         e = cudaFuncSetAttribute(k_fwd_dyn<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_MAX_SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_bwd_dyn<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_MAX_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pipe<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PIPE_MAX_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pipe<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PIPE_MAX_SMEM);
     return e;
+}
+
+// Ring slots for a vector area of fcap entries (as many as fit, at most
+// PIPE_NS_MAX, at least 2) and the blocks of one launch: one per SM, all
+// resident at once.
+template <typename R> int solve_pipe_grid(int fcap, int *ns_out) {
+    const size_t area = 3 * (size_t)fcap * sizeof(R);
+    if (area + 2 * (size_t)PIPE_SLOT > (size_t)PIPE_MAX_SMEM) return 0;
+    int ns = (int)((PIPE_MAX_SMEM - area) / PIPE_SLOT);
+    if (ns > PIPE_NS_MAX) ns = PIPE_NS_MAX;
+    int dev = 0, sms = 0, per_f = 0, per_b = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    const size_t smem = pipe_smem<R>(ns, fcap);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_f, k_pipe<R, false>, PTHREADS, smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_b, k_pipe<R, true>, PTHREADS, smem) != cudaSuccess)
+        return 0;
+    if (per_f < 1 || per_b < 1) return 0;
+    *ns_out = ns;
+    return sms;
 }
 
 template <typename R>
 void launch_solve(const DevSolve<R> &s, const V4<R> *q, V4<R> *z, V4<R> *r, cudaStream_t st) {
+    if (s.pipe) {
+        const size_t smem = pipe_smem<R>(s.pipe_ns, s.pipe_fcap);
+        k_pipe<R, false><<<s.pipe_grid, PTHREADS, smem, st>>>(s, q, z);
+        k_pipe<R, true><<<s.pipe_grid, PTHREADS, smem, st>>>(s, (const V4<R> *)z, r);
+        return;
+    }
     if (s.dyn) {
         k_fwd_dyn<R><<<s.dyn_grid, SBS, sweep_smem<R>(s.fwd_qmax, s.fwd_ldmax), st>>>(s, s.fwd_qmax, q, z);
         k_bwd_dyn<R><<<s.dyn_grid, SBS, sweep_smem<R>(s.bwd_qmax, s.bwd_ldmax), st>>>(s, s.bwd_qmax, z, r);
@@ -642,6 +1109,8 @@ template void launch_solve<float>(const DevSolve<float> &, const V4<float> *, V4
 template void launch_solve<double>(const DevSolve<double> &, const V4<double> *, V4<double> *, V4<double> *, cudaStream_t);
 template int solve_dyn_grid<float>(const DevSolve<float> &);
 template int solve_dyn_grid<double>(const DevSolve<double> &);
+template int solve_pipe_grid<float>(int, int *);
+template int solve_pipe_grid<double>(int, int *);
 template int solve_smem_limit_ok<float>(int);
 template int solve_smem_limit_ok<double>(int);
 template cudaError_t solve_prepare<float>();

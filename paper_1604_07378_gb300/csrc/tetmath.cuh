@@ -526,21 +526,97 @@ __device__ __forceinline__ void def_grad(const R du[3][3], const R Di[9], R G[3]
             G[a][b] = du[0][a] * Di[0 * 3 + b] + du[1][a] * Di[1 * 3 + b] + du[2][a] * Di[2 * 3 + b];
 }
 
-// Gradients of V*Psi with respect to the four corner positions, F = I + G.
-// First Piola P = U diag(tau) V^T; corners 1..3 get the columns of V P Dm^{-T},
-// corner 0 minus their sum.
+// First Piola stress of the Neo-Hookean and StVK materials from the
+// invariants of F = I + G (no singular vectors).  Both energies depend on the
+// stretches only through I1 = |F|^2 and J = det F (NH: a = mu/2 (x^2 - 1),
+// c(J) with its Taylor continuation below J0) or through E = (F^T F - I)/2
+// (StVK), so P = dPsi/dF equals U diag(tau) V^T of the stretch form:
+//   NH:   P = mu F + c'(J) cof F, written for J >= J0 as
+//         P = (mu (J F - cof F) + lam ln J cof F) / J with
+//         J F - cof F = (m2 + det G) I + J G + G^T - cof G and
+//         cof F = (1 + tr G) I - G^T + cof G  (cof is quadratic: cof(I + G) =
+//         I + (tr G) I - G^T + cof G), so no term of size mu cancels near rest;
+//         m2 = tr cof G, J - 1 = tr G + m2 + det G;
+//   StVK: P = F (mu A + lam/2 tr A I), A = F^T F - I = G + G^T + G^T G.
 template <typename R>
-__device__ __forceinline__ void tet_grad(const MatDev<R> &M, const R G[3][3], const R Di[9], R vol, R g[4][3]) {
-    R U[3][3], s[3], l[3], V[3][3];
-    signed_svd(G, U, s, l, V);
-    R tau[3];
-    material_tau(M, s, l, tau);
-    R P[3][3];
+__device__ __forceinline__ void invariant_stress(const MatDev<R> &M, const R G[3][3], R P[3][3]) {
+    if (M.kind == HQN_NEOHOOKEAN) {
+        R cg[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const int a1 = (a + 1) % 3, a2 = (a + 2) % 3, b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+                cg[a][b] = G[a1][b1] * G[a2][b2] - G[a1][b2] * G[a2][b1];
+            }
+        const R tr = G[0][0] + G[1][1] + G[2][2];
+        const R m2 = cg[0][0] + cg[1][1] + cg[2][2];
+        const R dg = G[0][0] * cg[0][0] + G[0][1] * cg[0][1] + G[0][2] * cg[0][2];
+        const R d = tr + m2 + dg;
+        const R J = R(1) + d;
+        if (J >= M.J0) {
+            const R lnJ = log1p_(d), inv = R(1) / J;
+            const R base = m2 + dg;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const R id = a == b ? R(1) : R(0);
+                    const R jf_cof = id * base + J * G[a][b] + G[b][a] - cg[a][b];
+                    const R cofF = id * (R(1) + tr) - G[b][a] + cg[a][b];
+                    P[a][b] = inv * (M.mu * jf_cof + M.lam * lnJ * cofF);
+                }
+        } else {
+            const R dc = M.c1 + M.c2 * (J - M.J0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const R id = a == b ? R(1) : R(0);
+                    P[a][b] = M.mu * (id + G[a][b]) + dc * (id * (R(1) + tr) - G[b][a] + cg[a][b]);
+                }
+        }
+        return;
+    }
+    // StVK
+    R A[3][3];
+    strain2(G, A);
+    const R htr = R(0.5) * M.lam * (A[0][0] + A[1][1] + A[2][2]);
+    R Sv[3][3];
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = 0; b < 3; ++b)
-            P[a][b] = vol * (U[a][0] * tau[0] * V[b][0] + U[a][1] * tau[1] * V[b][1] + U[a][2] * tau[2] * V[b][2]);
+        for (int b = 0; b < 3; ++b) Sv[a][b] = M.mu * A[a][b] + (a == b ? htr : R(0));
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) P[a][b] = Sv[a][b] + G[a][0] * Sv[0][b] + G[a][1] * Sv[1][b] + G[a][2] * Sv[2][b];
+}
+
+// Gradients of V*Psi with respect to the four corner positions, F = I + G.
+// First Piola P (invariant form for Neo-Hookean and StVK, otherwise
+// U diag(tau) V^T from the signed SVD); corners 1..3 get the columns of
+// V P Dm^{-T}, corner 0 minus their sum.
+template <typename R>
+__device__ __forceinline__ void tet_grad(const MatDev<R> &M, const R G[3][3], const R Di[9], R vol, R g[4][3]) {
+    R P[3][3];
+    if (M.kind == HQN_NEOHOOKEAN || M.kind == HQN_STVK) {
+        invariant_stress(M, G, P);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) P[a][b] *= vol;
+    } else {
+        R U[3][3], s[3], l[3], V[3][3];
+        signed_svd(G, U, s, l, V);
+        R tau[3];
+        material_tau(M, s, l, tau);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b)
+                P[a][b] = vol * (U[a][0] * tau[0] * V[b][0] + U[a][1] * tau[1] * V[b][1] + U[a][2] * tau[2] * V[b][2]);
+    }
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll

@@ -91,3 +91,28 @@ def test_batch_several_steps_bitwise_equal_to_single_handles():
             qc, qp = sim.get_state()
         np.testing.assert_array_equal(got[i][0], qc)
         np.testing.assert_array_equal(got[i][1], qp)
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_batch_pipelined_sweeps_bitwise_equal_to_single_handles(prec):
+    """With the pipelined sweeps a row's arithmetic does not depend on which
+    block runs its item, so the batch still agrees bit for bit with single
+    handles (and with the oracle)."""
+    from paper_1604_07378_gb300 import hqn
+    with hqn.Batch(WL, precision=prec, dyn_sweeps=2) as b:
+        assert b.info()["sweep_schedule"] == 2
+        for i, w in enumerate(WL):
+            b.set_state(i, w.q_cur, w.q_prev)
+        rc, _ = b.step(2)
+        assert rc >= 0
+        got = [b.get_state(i)[0] for i in range(len(WL))]
+    for i, w in enumerate(WL):
+        with hqn.Sim.from_workload(w, precision=prec, dyn_sweeps=2) as sim:
+            sim.set_state(w.q_cur, w.q_prev)
+            sim.step(2)
+            np.testing.assert_array_equal(got[i], sim.get_state()[0])
+    w = WL[0]
+    P = problem_for(w)
+    x1, _ = O.solve_step(P, w.q_cur, w.q_prev, iters=w.iters, m=w.history)
+    x2, _ = O.solve_step(P, x1, w.q_cur, iters=w.iters, m=w.history)
+    assert rel(got[0], x2) <= (1e-9 if prec == FP64 else 1e-4)

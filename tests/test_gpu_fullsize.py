@@ -41,11 +41,12 @@ def cube40():
     return w, problem_for(w)
 
 
-def test_cube40_three_iterations_match_oracle(cube40):
+@pytest.mark.parametrize("sweeps", [0, 2], ids=["levels", "pipelined"])
+def test_cube40_three_iterations_match_oracle(cube40, sweeps):
     """384,000 tets: the first three iterations of a step, element by element."""
     w, P = cube40
     x_ref, st = O.solve_step(P, w.q_cur, w.q_prev, iters=3, m=w.history)
-    with _sim(w, iters=3) as sim:
+    with _sim(w, iters=3, dyn_sweeps=sweeps) as sim:
         sim.set_state(w.q_cur, w.q_prev)
         rc, stats = sim.step(1, stats=True)
         x, _ = sim.get_state()
@@ -112,6 +113,10 @@ def test_large_bar_full_size():
     with _sim(w) as sim:
         g, grad = sim.energy_grad(x0, y)
         r = sim.solve_A0(q)
+    with _sim(w, dyn_sweeps=2) as simp:
+        assert simp.info()["sweep_schedule"] == 2
+        r_pipe = simp.solve_A0(q)
+    with _sim(w) as sim:
         sim.set_state(w.q_cur, w.q_prev)
         rc, st = sim.step(1, stats=True)
         x32, _ = sim.get_state()
@@ -125,6 +130,9 @@ def test_large_bar_full_size():
     a_inf = float(abs(A).sum(axis=1).max())
     eta = np.abs(A @ rf - qf).max() / (a_inf * np.abs(rf).max() + np.abs(qf).max())
     assert eta <= 1e-5, eta
+    rp = r_pipe[free]
+    eta_p = np.abs(A @ rp - qf).max() / (a_inf * np.abs(rp).max() + np.abs(qf).max())
+    assert eta_p <= 1e-5, eta_p
     assert rc >= 0 and st["iters"] == w.iters
     gs = [st["g0"]] + st["g"]
     assert all(b <= a * (1 + 1e-6) for a, b in zip(gs, gs[1:])), gs

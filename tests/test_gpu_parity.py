@@ -87,7 +87,7 @@ LAT30 = W.lattice_workload((30, 30, 30), W.Material(W.NEOHOOKEAN, 5e5, 0.4), cla
 
 @pytest.mark.parametrize("w", WORKLOADS[:3] + [LAT30], ids=IDS[:3] + ["lat30"])
 @pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
-@pytest.mark.parametrize("dyn_sweeps", [0, 1], ids=["levels", "dependency"])
+@pytest.mark.parametrize("dyn_sweeps", [0, 1, 2], ids=["levels", "dependency", "pipelined"])
 def test_solve_A0_parity(w, prec, dyn_sweeps):
     P = problem_for(w)
     rng = np.random.default_rng(4)
@@ -170,6 +170,48 @@ def test_sweep_schedules_agree_bitwise():
             out.append(sim.get_state()[0])
     np.testing.assert_array_equal(out[0], out[1])
     np.testing.assert_array_equal(out[0], out[2])
+
+
+@pytest.mark.parametrize("w", WORKLOADS, ids=IDS)
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_step_parity_pipelined_sweeps(w, prec):
+    """Whole steps with the pipelined sweeps (one persistent launch per sweep)
+    against the oracle; the same tolerances as the per-level sweeps."""
+    P = problem_for(w)
+    x_ref, st = O.solve_step(P, w.q_cur, w.q_prev, iters=w.iters, m=w.history)
+    with sim_for(w, prec, use_graph=1, dyn_sweeps=2) as sim:
+        assert sim.info()["sweep_schedule"] == 2
+        sim.set_state(w.q_cur, w.q_prev)
+        rc, stats = sim.step(1, stats=True)
+        qc, _ = sim.get_state()
+    assert rc >= 0
+    assert rel(qc, x_ref) <= (1e-9 if prec == FP64 else 1e-4), rel(qc, x_ref)
+    if prec == FP64:
+        assert stats["trials"] == st.trials
+
+
+def test_pipelined_sweeps_repeat_and_match_levels():
+    """Repeated solves on one handle (the counters of each sweep re-arm in
+    the other) give the same result every time; the pipelined sweeps
+    partition the rows into other work items than the per-level sweeps, so
+    the two agree to rounding."""
+    w = LAT30
+    rng = np.random.default_rng(12)
+    q = rng.normal(size=(w.n_verts, 3))
+    with sim_for(w, FP32, use_graph=0, dyn_sweeps=2) as sim:
+        r1 = sim.solve_A0(q)
+        r2 = sim.solve_A0(q)
+        sim.set_state(w.q_cur, w.q_prev)
+        sim.step(3)
+        x_pipe = sim.get_state()[0]
+    np.testing.assert_array_equal(r1, r2)
+    with sim_for(w, FP32, use_graph=0, dyn_sweeps=0) as sim:
+        r0 = sim.solve_A0(q)
+        sim.set_state(w.q_cur, w.q_prev)
+        sim.step(3)
+        x_lvl = sim.get_state()[0]
+    assert rel(r1, r0) <= 1e-5
+    assert rel(x_pipe, x_lvl) <= 1e-5
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
