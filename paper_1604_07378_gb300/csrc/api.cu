@@ -990,12 +990,15 @@ struct Sim final : SimBase {
         launch_tet(ds, TET_INIT, CondHandles{0, 0, 0}, s);
         launch_gather(ds, G_INIT, h, s);
     }
-    // x_{k+1} = x_k + alpha d: its gradient (corners, unless the fused first
-    // trial already left them, then the gather with the history push) once the
-    // line search has accepted alpha.
-    void enqueue_accept(CondHandles h, cudaStream_t s) {
+    // x_{k+1} = x_k + alpha d once the line search has accepted alpha: the
+    // gather of its gradient with the history push (the corners are left by
+    // the fused first trial or by the pass that accepted).
+    void enqueue_accept(CondHandles h, cudaStream_t s) { launch_gather(ds, G_ITER, h, s); }
+    // One pass of the line search, then the gradient at the accepted point of
+    // the simulations this pass accepted.
+    void enqueue_ls_pass(CondHandles h, cudaStream_t s) {
+        launch_ls(ds, h, s);
         launch_tet(ds, TET_GRAD, CondHandles{0, 0, 0}, s);
-        launch_gather(ds, G_ITER, h, s);
     }
 
     int step_eager() {
@@ -1012,7 +1015,7 @@ struct Sim final : SimBase {
             for (int pass = 0; pass < prm.ls_max &&
                                any_ctl([](const Ctl &c) { return c.active && !c.accepted && !c.stop; });
                  ++pass) {
-                launch_ls(ds, none, st);
+                enqueue_ls_pass(none, st);
                 if ((rc = read_ctl())) return rc;
             }
             enqueue_accept(none, st);
@@ -1083,7 +1086,7 @@ struct Sim final : SimBase {
             {
                 cudaStream_t s2 = cap_stream(1);
                 CK(cudaStreamBeginCaptureToGraph(s2, body_ls, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
-                launch_ls(ds, H, s2);
+                enqueue_ls_pass(H, s2);
                 CK(cudaStreamEndCapture(s2, &body_ls));
             }
             enqueue_accept(H, s1);

@@ -191,8 +191,9 @@ __device__ __forceinline__ double sum_block_range(const double *part, int b0, in
 //     Armijo test.  Accepted: the corners are the gradient of x_{k+1} and the
 //     simulation skips the line-search loop.  Rejected: the loop continues at
 //     alpha = backtrack.
-//   TET_GRAD: at the accepted point x_k + alpha d, corners only; nothing to do
-//     if TET_TRIAL1 already left them there or the simulation stopped.
+//   TET_GRAD: at the accepted point x_k + alpha d, corners only; runs after
+//     each line-search pass and does nothing for a simulation that has not
+//     accepted yet, whose TET_TRIAL1 already left the corners, or that stopped.
 template <typename R>
 __global__ void __launch_bounds__(TBS, 8) k_tet(DevSim<R> s, int mode, CondHandles h) {
     using A = ExactAcc<R>;
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(TBS, 8) k_tet(DevSim<R> s, int mode, CondHandl
     const bool grad_mode = mode == TET_GRAD;
     const bool ray_mode = mode == TET_GRAD || mode == TET_TRIAL1;
     const bool inactive = ray_mode && !c->active;
-    if (grad_mode && (inactive || c->stop || c->grad_ready)) return;
+    if (grad_mode && (inactive || c->stop || c->grad_ready || !c->accepted)) return;
     const R al = grad_mode ? (R)c->alpha : R(1);
     const int tl = (blockIdx.x - D.tb0) * TBS + threadIdx.x;
     typename A::T e[1] = {A::zero()};
@@ -485,16 +486,36 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
     const int i = (blockIdx.x - D.vb0) * VBS + threadIdx.x;
     if (act && !stop && i < D.c.nf) {
         const int gi = D.v0 + i;
+        // every load before any store: the vertex's corner range, its vectors
+        // and (history push) the ring slots; the ring slot being replaced is
+        // loaded too and not used
         const int b = s.vt_ptr[gi], e = s.vt_ptr[gi + 1];
+        const V4<R> xk = iter ? s.xk[gi] : s.xt[gi];
+        V4<R> dv;
+        dv.x = dv.y = dv.z = dv.w = R(0);
+        if (iter) dv = s.d[gi];
+        const V4<R> yy = s.y[gi];
+        const R mh = s.mh2[gi];
+        V4<R> go = dv;
+        V4<R> Sa[MP1], Ta[MP1];
+        V4<R> *S = s.S + D.ring0, *Tt = s.Tt + D.ring0;
+        const size_t n = (size_t)D.c.n;
+        if (push) {
+            go = s.gk[gi];
+#pragma unroll
+            for (int a = 0; a < MP1; ++a)
+                if (a <= m) {
+                    Sa[a] = S[(size_t)a * n + i];
+                    Ta[a] = Tt[(size_t)a * n + i];
+                }
+        }
         R gx = R(0), gy = R(0), gz = R(0);
 #pragma unroll 8
         for (int k = b; k < e; ++k) {
             const V4<R> cg = s.corner[k];
             gx += cg.x; gy += cg.y; gz += cg.z;
         }
-        const V4<R> x = iter ? step_point(s.xk[gi], s.d[gi], al) : s.xt[gi];
-        const V4<R> yy = s.y[gi];
-        const R mh = s.mh2[gi];
+        const V4<R> x = iter ? step_point(xk, dv, al) : xk;
         V4<R> gn;
         gn.x = gx + mh * (x.x - yy.x);
         gn.y = gy + mh * (x.y - yy.y);
@@ -502,12 +523,9 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
         gn.w = R(0);
         if (iter) {
             if (push) {
-                const V4<R> xo = s.xk[gi], go = s.gk[gi];
                 V4<R> sv, tv;
-                sv.x = x.x - xo.x; sv.y = x.y - xo.y; sv.z = x.z - xo.z; sv.w = R(0);
+                sv.x = x.x - xk.x; sv.y = x.y - xk.y; sv.z = x.z - xk.z; sv.w = R(0);
                 tv.x = gn.x - go.x; tv.y = gn.y - go.y; tv.z = gn.z - go.z; tv.w = R(0);
-                V4<R> *S = s.S + D.ring0, *Tt = s.Tt + D.ring0;
-                const size_t n = (size_t)D.c.n;
                 S[(size_t)w * n + i] = sv;
                 Tt[(size_t)w * n + i] = tv;
                 dd[0] = A::add_prod(A::add_prod(A::add_prod(dd[0], tv.x, sv.x), tv.y, sv.y), tv.z, sv.z);
@@ -516,8 +534,8 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
 #pragma unroll
                 for (int a = 0; a < MP1; ++a) {
                     if (a > m) break;
-                    const V4<R> sa = a == w ? sv : S[(size_t)a * n + i];
-                    const V4<R> ta = a == w ? tv : Tt[(size_t)a * n + i];
+                    const V4<R> sa = a == w ? sv : Sa[a];
+                    const V4<R> ta = a == w ? tv : Ta[a];
                     dr[2 + a] = dotr(sa, tv);
                     dr[2 + MP1 + a] = dotr(sv, ta);
                     dr[2 + 2 * MP1 + a] = dotr(sa, gn);
@@ -620,7 +638,7 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
 }
 
 // q = -grad - sum_p zeta_p t_p (the first loop's result).
-template <typename R>
+template <typename R, int MP1>
 __global__ void __launch_bounds__(VBS) k_q(DevSim<R> s) {
     const SimDesc<R> &D = sim_desc(s, s.vblk_sim);
     const Ctl *ctl = D.ctl;
@@ -628,15 +646,25 @@ __global__ void __launch_bounds__(VBS) k_q(DevSim<R> s) {
     if (i >= D.c.nf || !ctl->active) return;
     const int count = ctl->count, head = ctl->head, m = s.m;
     const int gi = D.v0 + i;
+    // every load first (history slots unrolled over the ring), then the sum in
+    // the order p = 0, 1, ...
     const V4<R> g = s.gk[gi];
+    const V4<R> *Tt = s.Tt + D.ring0;
+    R z[MP1];
+    V4<R> t[MP1];
+#pragma unroll
+    for (int p = 0; p < MP1; ++p)
+        if (p < count) {
+            z[p] = (R)ctl->zeta[p];
+            t[p] = Tt[(size_t)ring_slot(head, p, m) * D.c.n + i];
+        }
     V4<R> q;
     q.x = -g.x; q.y = -g.y; q.z = -g.z; q.w = R(0);
-    const V4<R> *Tt = s.Tt + D.ring0;
-    for (int p = 0; p < count; ++p) {
-        const R z = (R)ctl->zeta[p];
-        const V4<R> t = Tt[(size_t)ring_slot(head, p, m) * D.c.n + i];
-        q.x -= z * t.x; q.y -= z * t.y; q.z -= z * t.z;
-    }
+#pragma unroll
+    for (int p = 0; p < MP1; ++p)
+        if (p < count) {
+            q.x -= z[p] * t[p].x; q.y -= z[p] * t[p].y; q.z -= z[p] * t[p].z;
+        }
     s.q[gi] = q;
 }
 
@@ -696,7 +724,7 @@ __global__ void __launch_bounds__(VBS) k_r0_dots(DevSim<R> s) {
 // dropped (h.nd: any simulation flagged) -- and the coefficients of the
 // inertia term along the ray x_k + alpha d:
 // 1/(2h^2) sum m |x_k + alpha d - y|^2 = a0 + a1 alpha + a2 alpha^2.
-template <typename R>
+template <typename R, int MP1>
 __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, int set_nd) {
     const SimDesc<R> &D = sim_desc(s, s.vblk_sim);
     Ctl *ctl = D.ctl;
@@ -705,17 +733,27 @@ __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, i
     R d4[4] = {R(0), R(0), R(0), R(0)};
     if (act && i < D.c.nf) {
         const int gi = D.v0 + i;
-        V4<R> dd = s.d[gi];
         const int count = ctl->count, head = ctl->head, m = s.m;
         const V4<R> *S = s.S + D.ring0;
-        for (int p = 0; p < count; ++p) {
-            const R c = (R)ctl->coef[p];
-            const V4<R> sv = S[(size_t)ring_slot(head, p, m) * D.c.n + i];
-            dd.x += c * sv.x; dd.y += c * sv.y; dd.z += c * sv.z;
-        }
-        if (count > 0) s.d[gi] = dd;
+        // every load before the store of d (history slots unrolled over the
+        // ring); the sum runs in the order p = 0, 1, ...
+        V4<R> dd = s.d[gi];
         const V4<R> g = s.gk[gi], x = s.xk[gi], yy = s.y[gi];
         const R mh = s.mh2[gi];
+        R c[MP1];
+        V4<R> sv[MP1];
+#pragma unroll
+        for (int p = 0; p < MP1; ++p)
+            if (p < count) {
+                c[p] = (R)ctl->coef[p];
+                sv[p] = S[(size_t)ring_slot(head, p, m) * D.c.n + i];
+            }
+#pragma unroll
+        for (int p = 0; p < MP1; ++p)
+            if (p < count) {
+                dd.x += c[p] * sv[p].x; dd.y += c[p] * sv[p].y; dd.z += c[p] * sv[p].z;
+            }
+        if (count > 0) s.d[gi] = dd;
         const R rx = x.x - yy.x, ry = x.y - yy.y, rz = x.z - yy.z;
         d4[0] = dotr(g, dd);
         d4[1] = R(0.5) * mh * (rx * rx + ry * ry + rz * rz);
@@ -863,7 +901,12 @@ template <typename R> void launch_gather(const DevSim<R> &s, int mode, CondHandl
     else k_gather<R, HQN_MAX_HISTORY + 1><<<s.nvb, VBS, 0, st>>>(s, mode, h);
 }
 template <typename R> void launch_q(const DevSim<R> &s, cudaStream_t st) {
-    k_q<R><<<s.nvb, VBS, 0, st>>>(s);
+    const int m = s.m;
+    if (m <= 0) k_q<R, 1><<<s.nvb, VBS, 0, st>>>(s);
+    else if (m <= 3) k_q<R, 4><<<s.nvb, VBS, 0, st>>>(s);
+    else if (m <= 5) k_q<R, 6><<<s.nvb, VBS, 0, st>>>(s);
+    else if (m <= 8) k_q<R, 9><<<s.nvb, VBS, 0, st>>>(s);
+    else k_q<R, HQN_MAX_HISTORY + 1><<<s.nvb, VBS, 0, st>>>(s);
 }
 template <typename R> void launch_r0_dots(const DevSim<R> &s, cudaStream_t st) {
     const int m = s.m;
@@ -875,7 +918,12 @@ template <typename R> void launch_r0_dots(const DevSim<R> &s, cudaStream_t st) {
 }
 template <typename R>
 void launch_direction_final(const DevSim<R> &s, CondHandles h, int set_nd, cudaStream_t st) {
-    k_dir_final<R><<<s.nvb, VBS, 0, st>>>(s, h, set_nd);
+    const int m = s.m;
+    if (m <= 0) k_dir_final<R, 1><<<s.nvb, VBS, 0, st>>>(s, h, set_nd);
+    else if (m <= 3) k_dir_final<R, 4><<<s.nvb, VBS, 0, st>>>(s, h, set_nd);
+    else if (m <= 5) k_dir_final<R, 6><<<s.nvb, VBS, 0, st>>>(s, h, set_nd);
+    else if (m <= 8) k_dir_final<R, 9><<<s.nvb, VBS, 0, st>>>(s, h, set_nd);
+    else k_dir_final<R, HQN_MAX_HISTORY + 1><<<s.nvb, VBS, 0, st>>>(s, h, set_nd);
 }
 template <typename R> void launch_reset_history(const DevSim<R> &s, cudaStream_t st) {
     k_reset_history<R><<<1, 256, 0, st>>>(s);
