@@ -75,12 +75,18 @@ __device__ __forceinline__ void bulk_expect(uint64_t *bar, uint32_t bytes) {
                  : "memory");
 }
 
-// Any thread: one copy whose bytes count against the barrier's phase.
+// Any thread: one copy whose bytes count against the barrier's phase.  The
+// factor is streamed once per solve and does not fit in L2, so its lines are
+// marked evict-first: they do not push out the vectors and mesh data the
+// other kernels of an iteration reuse.
 __device__ __forceinline__ void bulk_copy(uint64_t *bar, void *dst, const void *src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+        : "memory");
 }
 
 // Thread 0: the phase's arrival and one contiguous copy.
