@@ -33,7 +33,7 @@ METRIC = "time-steps/s & tet grad-evals/s at 384k tets, FP32 vs FP64 GPU, pos er
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one cube40 FP32
 # solve, summed over its 22 sweep launches in an ncu capture of this script's
 # --no-graph run; to be set to None when the sweep kernels change.
-SOLVE_TRAFFIC_BYTES = 233.2e6
+SOLVE_TRAFFIC_BYTES = 233.14e6
 UNIT = "time-steps/s"
 WORKLOAD = "cube40_neohookean"
 
@@ -137,6 +137,25 @@ def oracle_sample(w, budget_s=25.0, counts=None):
 SWEEPS = {"levels": 0, "dependency": 1, "pipelined": 2}
 
 
+def max_over_ranks(x, dist, device=None):
+    """The maximum of x over the ranks of the process group (x itself without
+    one); every rank returns it.  The ranks first meet at a barrier."""
+    if not dist:
+        return float(x)
+    import torch
+
+    dist.barrier()
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, ms):
+    """Whole-job time-steps per second: every rank advances its own replica
+    `steps` steps, timed by the slowest rank (ms)."""
+    return world * steps / (ms / 1e3)
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -168,19 +187,13 @@ def run_ours(args, rank, world, dist):
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        if dist:
-            dist.barrier()
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     ms_step = ms / args.steps
     trials = stats["trials_total"] / args.steps
     iters = stats["iters_total"] / args.steps
     # energy evaluations per step: x_1 = y plus every line-search trial
     tet_evals_step = T * (stats["trials_total"] + args.steps) / args.steps
-    value = world * args.steps / (ms / 1e3)
+    value = job_throughput(world, args.steps, ms)
 
     # ---- per-stage device times (CUDA events on the handle's stream)
     stage_ms = {name: sim.time_stage(code, 20) for name, code in (
@@ -216,7 +229,7 @@ def run_ours(args, rank, world, dist):
     f1.record(stream)
     torch.cuda.synchronize()
     e2e_wall = time.perf_counter() - t0
-    e2e_ms = max(f0.elapsed_time(f1), e2e_wall * 1e3)
+    e2e_ms = max_over_ranks(max(f0.elapsed_time(f1), e2e_wall * 1e3), dist, dev)
     n = w.n_verts
     vbytes = 16  # FP32 vertex record
     h2d = 2 * n * vbytes
@@ -284,7 +297,7 @@ def run_ours(args, rank, world, dist):
         "pos_err_fp32_vs_fp64_gpu": ex,
         "stage_ms_per_launch": stage_ms, "stage_ms_per_step": per_step,
         "roofline": roof, "clocks": clocks,
-        "e2e": {"value": world * e2e_steps / (e2e_ms / 1e3), "unit": UNIT,
+        "e2e": {"value": job_throughput(world, e2e_steps, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": None,
         "status": rc,

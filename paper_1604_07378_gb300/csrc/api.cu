@@ -77,7 +77,7 @@ struct Sim final : SimBase {
     std::vector<int> fwd_ptr, fwd_ld, fwd_q, bwd_start, bwd_cnt, bwd_ld, bwd_q;  // per tree level
     int pipe_nbund[2] = {0, 0};  // bundles of the pipelined forward / backward sweeps
     int pipe_ndep[2] = {0, 0};   // cross-block waits of the pipelined forward / backward sweeps
-    std::vector<V4<R>> hbuf;
+    V4<R> *hbuf = nullptr;  // pinned staging buffer of the state transfers (largest simulation)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     bool graph_mode = false;
@@ -94,6 +94,7 @@ struct Sim final : SimBase {
         for (auto s : cap_streams) cudaStreamDestroy(s);
         for (void *p : allocs) cudaFree(p);
         if (h_ctl) cudaFreeHost(h_ctl);
+        if (hbuf) cudaFreeHost(hbuf);
         if (own_stream) cudaStreamDestroy(own_stream);
     }
 
@@ -256,7 +257,11 @@ struct Sim final : SimBase {
             ds.desc0 = hdesc[0];
         }
         if ((rc = init_solve(v0, u0, sn0, qf0, qb0, qf_tot, qb_tot))) return rc;
-        hbuf.resize(n);
+        {
+            int nmax = 1;
+            for (const Setup &q : S) nmax = std::max(nmax, q.n);
+            CK(cudaMallocHost(&hbuf, (size_t)nmax * sizeof(V4<R>)));
+        }
         CK(cudaStreamSynchronize(st));
         // Chain the sweep levels with programmatic dependent launch when the
         // device and the runtime accept it (one probe solve on zero vectors),
@@ -904,9 +909,14 @@ struct Sim final : SimBase {
     }
 
     // ---- state transfer (caller order, absolute positions <-> internal displacements)
+    // Host <-> device state transfers through the pinned staging buffer; the
+    // conversions (caller order and float64 <-> internal order and R) run on
+    // the host's cores for large meshes.
     int put_vec(int idx, V4<R> *dst, const double *src, bool displacement, bool free_only) {
         const Setup &s = S[idx];
         const int n = s.n;
+        int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad) if (n > 32768)
         for (int i = 0; i < n; ++i) {
             const int v = s.perm[i];
             V4<R> o;
@@ -917,22 +927,24 @@ struct Sim final : SimBase {
                 double a[3];
                 for (int k = 0; k < 3; ++k) {
                     a[k] = src[3 * (size_t)v + k];
-                    if (!std::isfinite(a[k])) return fail(HQN_ERR_NONFINITE, "non-finite input");
+                    if (!std::isfinite(a[k])) bad = 1;
                     if (displacement) a[k] -= s.X[3 * (size_t)i + k];
                 }
                 o.x = (R)a[0]; o.y = (R)a[1]; o.z = (R)a[2];
             }
             hbuf[i] = o;
         }
-        CK(cudaMemcpyAsync(dst + hdesc[idx].v0, hbuf.data(), (size_t)n * sizeof(V4<R>), cudaMemcpyHostToDevice, st));
+        if (bad) return fail(HQN_ERR_NONFINITE, "non-finite input");
+        CK(cudaMemcpyAsync(dst + hdesc[idx].v0, hbuf, (size_t)n * sizeof(V4<R>), cudaMemcpyHostToDevice, st));
         CK(cudaStreamSynchronize(st));
         return HQN_OK;
     }
     int get_vec(int idx, const V4<R> *src, double *dst, bool displacement, bool free_only) {
         const Setup &s = S[idx];
         const int n = s.n;
-        CK(cudaMemcpyAsync(hbuf.data(), src + hdesc[idx].v0, (size_t)n * sizeof(V4<R>), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hbuf, src + hdesc[idx].v0, (size_t)n * sizeof(V4<R>), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+#pragma omp parallel for schedule(static) if (n > 32768)
         for (int i = 0; i < n; ++i) {
             const int v = s.perm[i];
             const V4<R> o = hbuf[i];
