@@ -165,47 +165,57 @@ __device__ __forceinline__ V4<double> ld_cg(const V4<double> *p) {
 // nt threads (tid = 0..nt-1, nt a multiple of 32) share the rows; f's three
 // components lie fs entries apart.
 // ua (if not null): the child update entries of rows [rr0, ...) already
-// summed, three components ua_s entries apart.
+// summed, three components ua_s entries apart.  Each group of G lanes takes
+// RPG consecutive rows at a time, so every load of f serves RPG rows.
 template <typename R, int G>
 __device__ __forceinline__ void fwd_rows(const DevSolve<R> &S, int col, int nc, int ldc, int uoff, int r0, int r1,
                                          int off0, const R *qs, const R *f, int fs, V4<R> *z, int tid, int nt,
                                          const R *ua, int ua_s, int rr0) {
     using VT = typename Vec16<R>::T;
     constexpr int VN = Vec16<R>::N;
+    constexpr int RPG = 4;
     const int NG = nt / G;
     const int lane = tid % G, grp = tid / G;
     const VT *fx = reinterpret_cast<const VT *>(f);
     const VT *fy = reinterpret_cast<const VT *>(f + fs);
     const VT *fz = reinterpret_cast<const VT *>(f + 2 * fs);
-    for (int base = r0; base < r1; base += 2 * NG) {
-        const int i0 = base + 2 * grp, i1 = i0 + 1;
-        const bool v0 = i0 < r1, v1 = i1 < r1;
-        const int n0 = v0 ? fwd_row_len(i0, nc, ldc) / VN : 0;
-        const int n1 = v1 ? fwd_row_len(i1, nc, ldc) / VN : 0;
-        const VT *q0 = reinterpret_cast<const VT *>(qs + (v0 ? fwd_row_off(i0, nc, ldc) - off0 : 0));
-        const VT *q1 = reinterpret_cast<const VT *>(qs + (v1 ? fwd_row_off(i1, nc, ldc) - off0 : 0));
-        R a0x = R(0), a0y = R(0), a0z = R(0), a1x = R(0), a1y = R(0), a1z = R(0);
-        const int nmax = n0 > n1 ? n0 : n1;
+    for (int base = r0; base < r1; base += RPG * NG) {
+        int nv[RPG];
+        const VT *qv[RPG];
+        int nmax = 0;
+#pragma unroll
+        for (int h = 0; h < RPG; ++h) {
+            const int i = base + RPG * grp + h;
+            const bool v = i < r1;
+            nv[h] = v ? fwd_row_len(i, nc, ldc) / VN : 0;
+            qv[h] = reinterpret_cast<const VT *>(qs + (v ? fwd_row_off(i, nc, ldc) - off0 : 0));
+            nmax = nv[h] > nmax ? nv[h] : nmax;
+        }
+        R acc[RPG][3];
+#pragma unroll
+        for (int h = 0; h < RPG; ++h) acc[h][0] = acc[h][1] = acc[h][2] = R(0);
         for (int k = lane; k < nmax; k += G) {
             const VT x = fx[k], y = fy[k], w = fz[k];
-            if (k < n0) {
-                const VT q = q0[k];
-                a0x += Vec16<R>::dot3(q, x); a0y += Vec16<R>::dot3(q, y); a0z += Vec16<R>::dot3(q, w);
-            }
-            if (k < n1) {
-                const VT q = q1[k];
-                a1x += Vec16<R>::dot3(q, x); a1y += Vec16<R>::dot3(q, y); a1z += Vec16<R>::dot3(q, w);
-            }
+#pragma unroll
+            for (int h = 0; h < RPG; ++h)
+                if (k < nv[h]) {
+                    const VT q = qv[h][k];
+                    acc[h][0] += Vec16<R>::dot3(q, x); acc[h][1] += Vec16<R>::dot3(q, y); acc[h][2] += Vec16<R>::dot3(q, w);
+                }
         }
-        a0x = group_sum<R, G>(a0x); a0y = group_sum<R, G>(a0y); a0z = group_sum<R, G>(a0z);
-        a1x = group_sum<R, G>(a1x); a1y = group_sum<R, G>(a1y); a1z = group_sum<R, G>(a1z);
+#pragma unroll
+        for (int h = 0; h < RPG; ++h) {
+            acc[h][0] = group_sum<R, G>(acc[h][0]);
+            acc[h][1] = group_sum<R, G>(acc[h][1]);
+            acc[h][2] = group_sum<R, G>(acc[h][2]);
+        }
         if (lane == 0) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int i = h ? i1 : i0;
-                if (!(h ? v1 : v0)) continue;
+            for (int h = 0; h < RPG; ++h) {
+                const int i = base + RPG * grp + h;
+                if (i >= r1) continue;
                 V4<R> o;
-                o.x = h ? a1x : a0x; o.y = h ? a1y : a0y; o.z = h ? a1z : a0z; o.w = R(0);
+                o.x = acc[h][0]; o.y = acc[h][1]; o.z = acc[h][2]; o.w = R(0);
                 if (i < nc) {
                     z[col + i] = o;
                 } else {
@@ -299,7 +309,7 @@ __device__ __forceinline__ void fwd_item(const DevSolve<R> &S, const int4 *rec, 
 
 // Level-synchronous schedule: one launch per tree level, one item per block.
 template <typename R>
-__global__ void __launch_bounds__(SBS) k_fwd(DevSolve<R> S, int item0, int qcap, const V4<R> *rhs, V4<R> *z) {
+__global__ void __launch_bounds__(SBS, 4) k_fwd(DevSolve<R> S, int item0, int qcap, const V4<R> *rhs, V4<R> *z) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) bulk_bar_init(&bar);
@@ -320,59 +330,63 @@ __global__ void __launch_bounds__(SBS) k_fwd(DevSolve<R> S, int item0, int qcap,
 // qs + (j - c0) lw, aligned with w, holding its entries of the chunk.
 // The sums go to r[col + j], or to out[j - c0] (a chunk's partial sums).
 // nt threads (tid = 0..nt-1, nt a multiple of 32) share the rows; w's three
-// components lie ws entries apart.
+// components lie ws entries apart.  Each group of G lanes takes RPG
+// consecutive rows at a time, so every load of w serves RPG rows.
 template <typename R, int G, bool CHUNK>
 __device__ __forceinline__ void bwd_rows(int col, int ldr, int c0, int c1, int off0, const R *qs, const R *w,
                                          int ws, int lw, int w0, V4<R> *r, V4<R> *out, int tid, int nt) {
     using VT = typename Vec16<R>::T;
     constexpr int VN = Vec16<R>::N;
+    constexpr int RPG = 4;
     const int NG = nt / G;
     const int lane = tid % G, grp = tid / G;
     const VT *wx = reinterpret_cast<const VT *>(w);
     const VT *wy = reinterpret_cast<const VT *>(w + ws);
     const VT *wz = reinterpret_cast<const VT *>(w + 2 * ws);
     const int kend = lw / VN;
-    for (int base = c0; base < c1; base += 2 * NG) {
-        const int j0 = base + 2 * grp, j1 = j0 + 1;
-        const bool v0 = j0 < c1, v1 = j1 < c1;
+    for (int base = c0; base < c1; base += RPG * NG) {
         // row j covers w vectors [k_j, kend)
-        int k0 = kend, k1 = kend;
-        const VT *q0 = nullptr, *q1 = nullptr;
-        if (v0) {
-            const int st = bwd_row_start(j0);
-            k0 = st > w0 ? (st - w0) / VN : 0;
-            q0 = CHUNK ? reinterpret_cast<const VT *>(qs + (size_t)(j0 - c0) * lw)
-                       : reinterpret_cast<const VT *>(qs + (bwd_row_off(j0, ldr) - off0)) - k0;
+        int kb[RPG];
+        const VT *qv[RPG];
+        int kmin = kend;
+#pragma unroll
+        for (int h = 0; h < RPG; ++h) {
+            const int j = base + RPG * grp + h;
+            kb[h] = kend;
+            qv[h] = nullptr;
+            if (j < c1) {
+                const int st = bwd_row_start(j);
+                kb[h] = st > w0 ? (st - w0) / VN : 0;
+                qv[h] = CHUNK ? reinterpret_cast<const VT *>(qs + (size_t)(j - c0) * lw)
+                              : reinterpret_cast<const VT *>(qs + (bwd_row_off(j, ldr) - off0)) - kb[h];
+            }
+            kmin = kb[h] < kmin ? kb[h] : kmin;
         }
-        if (v1) {
-            const int st = bwd_row_start(j1);
-            k1 = st > w0 ? (st - w0) / VN : 0;
-            q1 = CHUNK ? reinterpret_cast<const VT *>(qs + (size_t)(j1 - c0) * lw)
-                       : reinterpret_cast<const VT *>(qs + (bwd_row_off(j1, ldr) - off0)) - k1;
-        }
-        R a0x = R(0), a0y = R(0), a0z = R(0), a1x = R(0), a1y = R(0), a1z = R(0);
-        const int kmin = k0 < k1 ? k0 : k1;
+        R acc[RPG][3];
+#pragma unroll
+        for (int h = 0; h < RPG; ++h) acc[h][0] = acc[h][1] = acc[h][2] = R(0);
         for (int k = kmin + lane; k < kend; k += G) {
             const VT x = wx[k], y = wy[k], v = wz[k];
-            if (k >= k0) {
-                const VT q = q0[k];
-                a0x += Vec16<R>::dot3(q, x); a0y += Vec16<R>::dot3(q, y); a0z += Vec16<R>::dot3(q, v);
-            }
-            if (k >= k1) {
-                const VT q = q1[k];
-                a1x += Vec16<R>::dot3(q, x); a1y += Vec16<R>::dot3(q, y); a1z += Vec16<R>::dot3(q, v);
-            }
+#pragma unroll
+            for (int h = 0; h < RPG; ++h)
+                if (k >= kb[h]) {
+                    const VT q = qv[h][k];
+                    acc[h][0] += Vec16<R>::dot3(q, x); acc[h][1] += Vec16<R>::dot3(q, y); acc[h][2] += Vec16<R>::dot3(q, v);
+                }
         }
-        a0x = group_sum<R, G>(a0x); a0y = group_sum<R, G>(a0y); a0z = group_sum<R, G>(a0z);
-        a1x = group_sum<R, G>(a1x); a1y = group_sum<R, G>(a1y); a1z = group_sum<R, G>(a1z);
+#pragma unroll
+        for (int h = 0; h < RPG; ++h) {
+            acc[h][0] = group_sum<R, G>(acc[h][0]);
+            acc[h][1] = group_sum<R, G>(acc[h][1]);
+            acc[h][2] = group_sum<R, G>(acc[h][2]);
+        }
         if (lane == 0) {
-            if (v0) {
-                V4<R> o; o.x = a0x; o.y = a0y; o.z = a0z; o.w = R(0);
-                if (out) out[j0 - c0] = o; else r[col + j0] = o;
-            }
-            if (v1) {
-                V4<R> o; o.x = a1x; o.y = a1y; o.z = a1z; o.w = R(0);
-                if (out) out[j1 - c0] = o; else r[col + j1] = o;
+#pragma unroll
+            for (int h = 0; h < RPG; ++h) {
+                const int j = base + RPG * grp + h;
+                if (j >= c1) continue;
+                V4<R> o; o.x = acc[h][0]; o.y = acc[h][1]; o.z = acc[h][2]; o.w = R(0);
+                if (out) out[j - c0] = o; else r[col + j] = o;
             }
         }
     }
@@ -486,7 +500,7 @@ __device__ __forceinline__ void bwd_item(const DevSolve<R> &S, const int4 *rec, 
 }
 
 template <typename R>
-__global__ void __launch_bounds__(SBS) k_bwd(DevSolve<R> S, int item0, int qcap, const V4<R> *z, V4<R> *r) {
+__global__ void __launch_bounds__(SBS, 4) k_bwd(DevSolve<R> S, int item0, int qcap, const V4<R> *z, V4<R> *r) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) bulk_bar_init(&bar);
