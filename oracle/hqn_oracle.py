@@ -23,7 +23,16 @@ taken by the CUDA path, written separately):
     only if rho = tr(t^T s) > 1e-12 ||s|| ||t||; if tr(grad^T d) >= 0 the
     history is dropped and d = -A0^{-1} grad;
   * the backtracking line search gives up after ls_max trials, keeping x_k and
-    ending the step's iterations.
+    ending the step's iterations;
+  * collisions (Sec. 4.3) against analytic colliders (a plane with its
+    normal, or a sphere the body stays outside of): at the start of every
+    iteration, before the gradient at x_k, each free vertex that penetrates a
+    collider (signed distance < 0) and does not move away from it (its
+    displacement over the step, x_k - q_l, has a non-positive normal
+    component) gets the term w_v ((x - t)^T n)^2 with t its projection on the
+    surface and n the surface normal there, both frozen for the iteration;
+    w_v = contact_scale * m_v / h^2 (the paper prints no weight).  The terms
+    enter the objective and its gradient but not A0.
 
 Parity pins: see tests/test_oracle_pins.py (finite differences, rest state,
 invariances, invariant-form materials, closed-form stiffness, SPD and residual
@@ -300,13 +309,15 @@ class Problem:
     free: np.ndarray = None
     A: sp.csc_matrix = None
     _solver: object = None
+    colliders: tuple = ()        # ("plane", point, normal) or ("sphere", centre, radius)
+    contact_scale: float = 100.0
 
     @property
     def n(self): return self.X.shape[0]
 
 
 def build_problem(X, tets, clamped, mat: VLMaterial, density, h, gravity,
-                  x_start=0.5, x_end=1.5) -> Problem:
+                  x_start=0.5, x_end=1.5, colliders=(), contact_scale=100.0) -> Problem:
     X = np.asarray(X, dtype=np.float64)
     tets = np.asarray(tets, dtype=np.int64)
     P = Problem(X=X, tets=tets, clamped=np.asarray(clamped).astype(bool), mat=mat,
@@ -327,6 +338,8 @@ def build_problem(X, tets, clamped, mat: VLMaterial, density, h, gravity,
     P.k = stiffness_k(mat, x_start, x_end)
     P.free = np.flatnonzero(~P.clamped)
     P.A = assemble_A(P)
+    P.colliders = tuple(colliders)
+    P.contact_scale = float(contact_scale)
     return P
 
 
@@ -392,20 +405,85 @@ def elastic_corner_gradients(P: Problem, x):
     return out
 
 
-def objective(P: Problem, x, y):
-    """g(x) = 1/(2h^2) tr((x-y)^T M (x-y)) + E(x), Eq. PD (free vertices)."""
+# ----------------------------------------------------------------------------
+# Collision terms (Sec. 4.3).
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Contacts:
+    """Active collision terms of one iteration: vertex ids, surface points t,
+    unit normals n and weights w (term w ((x_v - t)^T n)^2)."""
+    idx: np.ndarray
+    t: np.ndarray
+    n: np.ndarray
+    w: np.ndarray
+
+
+def contact_terms(P: Problem, x, q_ref):
+    """The terms active at the iterate x: free vertices with negative signed
+    distance to a collider whose displacement x - q_ref does not point away
+    from it (q_ref: the position at the start of the time step)."""
+    idx, ts, ns, ws = [], [], [], []
+    free = np.zeros(P.n, dtype=bool)
+    free[P.free] = True
+    for col in P.colliders:
+        if col[0] == "plane":
+            p, nrm = np.asarray(col[1], float), np.asarray(col[2], float)
+            nrm = nrm / np.linalg.norm(nrm)
+            phi = (x - p) @ nrm
+            n = np.broadcast_to(nrm, x.shape)
+        elif col[0] == "sphere":
+            c, r = np.asarray(col[1], float), float(col[2])
+            rel = x - c
+            dist = np.linalg.norm(rel, axis=1)
+            phi = dist - r
+            n = rel / np.maximum(dist, 1e-300)[:, None]
+        else:
+            raise ValueError(f"unknown collider {col[0]!r}")
+        vn = np.sum((x - q_ref) * n, axis=1)
+        act = np.flatnonzero(free & (phi < 0.0) & (vn <= 0.0))
+        idx.append(act)
+        ts.append(x[act] - phi[act, None] * n[act])
+        ns.append(n[act])
+        ws.append(P.contact_scale * P.mass[act] / P.h**2)
+    if not idx:
+        z = np.zeros(0, dtype=np.int64)
+        return Contacts(z, np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0))
+    return Contacts(np.concatenate(idx), np.concatenate(ts), np.concatenate(ns), np.concatenate(ws))
+
+
+def contact_energy(C: Contacts, x):
+    if C is None or C.idx.size == 0:
+        return 0.0
+    gap = np.sum((x[C.idx] - C.t) * C.n, axis=1)
+    return float(np.sum(C.w * gap * gap))
+
+
+def contact_gradient(C: Contacts, x, grad):
+    if C is None or C.idx.size == 0:
+        return grad
+    gap = np.sum((x[C.idx] - C.t) * C.n, axis=1)
+    np.add.at(grad, C.idx, (2.0 * C.w * gap)[:, None] * C.n)
+    return grad
+
+
+def objective(P: Problem, x, y, contacts: Contacts = None):
+    """g(x) = 1/(2h^2) tr((x-y)^T M (x-y)) + E(x), Eq. PD (free vertices),
+    plus the active collision terms (Sec. 4.3) if any."""
     dx = (x - y)[P.free]
     inertia = 0.5 / P.h**2 * np.sum(P.mass[P.free, None] * dx * dx)
-    return inertia + np.sum(elastic_energy_per_tet(P, x))
+    return inertia + np.sum(elastic_energy_per_tet(P, x)) + contact_energy(contacts, x)
 
 
-def gradient(P: Problem, x, y):
-    """grad g = M (x - y)/h^2 + grad E, zero on clamped vertices."""
+def gradient(P: Problem, x, y, contacts: Contacts = None):
+    """grad g = M (x - y)/h^2 + grad E (+ the collision terms), zero on
+    clamped vertices."""
     cg = elastic_corner_gradients(P, x)
     grad = np.zeros_like(x)
     for c in range(4):
         np.add.at(grad, P.tets[:, c], cg[:, c, :])
     grad += P.mass[:, None] * (x - y) / P.h**2
+    contact_gradient(contacts, x, grad)
     grad[P.clamped] = 0.0
     return grad
 
@@ -458,12 +536,17 @@ def solve_step(P: Problem, q_cur, q_prev, iters=10, m=5, gamma=0.3, backtrack=0.
     Returns (x_{iters+1}, stats[, iterates])."""
     y = predictor(P, q_cur, q_prev)
     x = y.copy()                                   # x_1 := y
-    gx = objective(P, x, y)
-    grad = gradient(P, x, y)
+    col = contact_terms(P, x, q_cur) if P.colliders else None
+    gx = objective(P, x, y, col)
+    grad = gradient(P, x, y, col)
     st = StepStats(g0=gx)
     history = []
     iterates = [x.copy()]
-    for _ in range(iters):
+    for it in range(iters):
+        if P.colliders and it > 0:
+            # the collision terms are updated at the start of the iteration,
+            # before the gradient at x_k (Sec. 4.3); g(x_k) is re-evaluated with them
+            gx = objective(P, x, y, col)
         d = lbfgs_direction(P, grad, history)
         gd = tr_dot(grad, d)
         if gd >= 0.0 and history:
@@ -476,7 +559,7 @@ def solve_step(P: Problem, q_cur, q_prev, iters=10, m=5, gamma=0.3, backtrack=0.
         for trial in range(ls_max):
             alpha *= backtrack
             x_new = x + alpha * d
-            g_new = objective(P, x_new, y)
+            g_new = objective(P, x_new, y, col)
             if g_new <= gx + gamma * alpha * gd:
                 accepted = True
                 break
@@ -485,7 +568,9 @@ def solve_step(P: Problem, q_cur, q_prev, iters=10, m=5, gamma=0.3, backtrack=0.
             st.exhausted = True
             st.g.append(gx)
             break
-        grad_new = gradient(P, x_new, y)
+        if P.colliders:
+            col = contact_terms(P, x_new, q_cur)
+        grad_new = gradient(P, x_new, y, col)
         s = x_new - x
         t = grad_new - grad
         rho = tr_dot(t, s)
@@ -551,5 +636,6 @@ def newton_minimise(P: Problem, q_cur, q_prev, tol=1e-11, max_iter=100, fd_eps=1
 def problem_from_workload(w, x_start=0.5, x_end=1.5) -> Problem:
     m = w.material
     mat = make_material(m.kind, m.E, m.nu, m.spline)
+    cols = tuple(c.as_tuple() for c in getattr(w, "colliders", ()))
     return build_problem(w.rest_pos, w.tets, w.clamped, mat, m.density, w.h, w.gravity,
-                         x_start, x_end)
+                         x_start, x_end, colliders=cols, contact_scale=getattr(w, "contact_scale", 100.0))

@@ -46,6 +46,21 @@ class Material:
 
 
 @dataclass
+class Collider:
+    """An analytic collider: a plane (point on it, normal pointing to the free
+    side) or a sphere the body stays outside of (centre, radius)."""
+    kind: str                     # "plane" or "sphere"
+    point: tuple                  # a point of the plane, or the sphere's centre
+    normal: tuple = (0.0, 0.0, 1.0)
+    radius: float = 0.0
+
+    def as_tuple(self):
+        if self.kind == "plane":
+            return ("plane", tuple(self.point), tuple(self.normal))
+        return ("sphere", tuple(self.point), float(self.radius))
+
+
+@dataclass
 class Workload:
     name: str
     rest_pos: np.ndarray          # (n, 3) float64, rest positions X
@@ -60,6 +75,8 @@ class Workload:
     history: int = 5
     dims: tuple = ()
     meta: dict = field(default_factory=dict)
+    colliders: tuple = ()         # Collider instances
+    contact_scale: float = 100.0  # collision weight w_v = contact_scale * m_v / h^2
 
     @property
     def n_verts(self) -> int:
@@ -171,7 +188,8 @@ def lattice_workload(dims, material: Material, *, clamp_axis: int = 2, seed: int
                      v_range: float = 0.0, v_mode: str = "iid", edge: float = 0.05, iters: int = 10,
                      history: int = 5, gravity=(0.0, 0.0, -9.81), h: float = 1.0 / 30.0,
                      twist_deg: float = 0.0, name: str = "lattice") -> Workload:
-    """A Kuhn lattice with its clamp_axis = 0 face clamped.
+    """A Kuhn lattice with its clamp_axis = 0 face clamped (clamp_axis < 0:
+    nothing clamped).
 
     v_range > 0 gives the free vertices an initial velocity with components
     drawn from U[-v_range, v_range]: v_mode "iid" draws every vertex's own
@@ -183,7 +201,10 @@ def lattice_workload(dims, material: Material, *, clamp_axis: int = 2, seed: int
     """
     nx, ny, nz = dims
     rest, tets = kuhn_lattice(nx, ny, nz, edge)
-    clamped = (np.abs(rest[:, clamp_axis]) < 1e-12 * edge).astype(np.uint8)
+    if clamp_axis < 0:  # nothing clamped
+        clamped = np.zeros(rest.shape[0], dtype=np.uint8)
+    else:
+        clamped = (np.abs(rest[:, clamp_axis]) < 1e-12 * edge).astype(np.uint8)
     rng = np.random.default_rng(seed)
     v0 = np.zeros_like(rest)
     if v_range > 0.0:
@@ -237,6 +258,28 @@ def spline_bar_80x40x40(scale: int = 1) -> Workload:
     mat.spline = spline_control_points(mat.mu, mat.lam, rng)
     return lattice_workload(dims, mat, clamp_axis=0, seed=1606, twist_deg=90.0,
                             name=f"splinebar{dims[0]}x{dims[1]}x{dims[2]}")
+
+
+def collision_drop(n: int = 8, drop: float = 0.02, speed: float = 2.0, sphere: bool = True,
+                   kind: int = NEOHOOKEAN, E: float = 2e5, name: str = "") -> Workload:
+    """An unclamped n^3 Neo-Hookean cube falling onto the ground plane z = 0
+    (Sec. 4.3's collision terms), its lowest face `drop` above it, every
+    vertex moving down at `speed` m/s; with `sphere`, a sphere of radius
+    n*edge/4 sits on the ground under one corner of the cube's footprint, so
+    part of the cube lands on it."""
+    edge = 0.05
+    w = lattice_workload((n, n, n), Material(kind, E, 0.4), clamp_axis=-1, seed=1609, name=name or f"drop{n}")
+    shift = np.array([-0.5 * n * edge, -0.5 * n * edge, drop])
+    v = np.array([0.0, 0.0, -speed])
+    w.q_cur = w.rest_pos + shift
+    w.q_prev = w.q_cur - w.h * v
+    cols = [Collider("plane", (0.0, 0.0, 0.0), (0.0, 0.0, 1.0))]
+    if sphere:
+        r = 0.25 * n * edge
+        cols.append(Collider("sphere", (-0.25 * n * edge, -0.25 * n * edge, 0.5 * r), radius=r))
+    w.colliders = tuple(cols)
+    w.meta.update({"drop": drop, "speed": speed})
+    return w
 
 
 def batch_512(count: int = 512, lo: int = 4, hi: int = 24, seed: int = 1607) -> list:

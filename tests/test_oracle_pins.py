@@ -360,3 +360,77 @@ def test_lbfgs_history_speeds_convergence():
     e0 = O.relative_error(st0.g[-1], st0.g0, g_star)
     e5 = O.relative_error(st5.g[-1], st5.g0, g_star)
     assert 0 <= e5 < e0 < 1
+
+
+# ---------------------------------------------------------------- collisions (Sec. 4.3)
+
+def _drop_problem(n=3, **kw):
+    w = W.collision_drop(n, **kw)
+    return w, O.problem_from_workload(w)
+
+
+def test_contact_gradient_matches_central_differences():
+    """The collision terms' gradient is the derivative of their energy (the
+    active set and the frozen t, n held fixed), on top of the elastic and
+    inertia terms."""
+    w, P = _drop_problem(3, drop=-0.01, speed=1.0)
+    y = O.predictor(P, w.q_cur, w.q_prev)
+    rng = np.random.default_rng(3)
+    x = y + 1e-3 * rng.normal(size=y.shape)
+    C = O.contact_terms(P, x, w.q_cur)
+    assert C.idx.size > 0
+    g = O.gradient(P, x, y, C)
+    eps = 1e-6
+    for v in C.idx[:4]:
+        for c in range(3):
+            xp = x.copy(); xp[v, c] += eps
+            xm = x.copy(); xm[v, c] -= eps
+            fd = (O.objective(P, xp, y, C) - O.objective(P, xm, y, C)) / (2 * eps)
+            assert abs(fd - g[v, c]) <= 1e-6 * max(1.0, abs(g[v, c])), (v, c, fd, g[v, c])
+
+
+def test_contact_set_penetrating_and_approaching_only():
+    """A vertex below the plane is active only if it is not moving away; a
+    vertex above the plane never is; the surface point is the vertex's
+    projection and the normal the plane's."""
+    w, P = _drop_problem(2, sphere=False)
+    x = w.rest_pos.copy()
+    q_ref = x.copy()
+    x[:, 2] += 0.01           # everything above z = 0 ...
+    x[0, 2] = -0.004          # ... but vertex 0 (moving down from 0)
+    x[1, 2] = -0.002          # and vertex 1, which moves up into the plane
+    q_ref[1, 2] = -0.003
+    C = O.contact_terms(P, x, q_ref)
+    assert list(C.idx) == [0]
+    np.testing.assert_allclose(C.t[0], [x[0, 0], x[0, 1], 0.0], atol=1e-15)
+    np.testing.assert_allclose(C.n[0], [0.0, 0.0, 1.0])
+    assert C.w[0] == pytest.approx(P.contact_scale * P.mass[0] / P.h**2)
+    assert O.contact_energy(C, x) == pytest.approx(C.w[0] * 0.004**2)
+
+
+def test_sphere_contact_projection():
+    w, P = _drop_problem(2)
+    cen, r = np.asarray(w.colliders[1].point), w.colliders[1].radius
+    x = w.rest_pos.copy() + 5.0  # far away ...
+    d = np.array([1.0, 2.0, 2.0]) / 3.0
+    x[3] = cen + 0.9 * r * d      # ... except vertex 3, inside the sphere
+    C = O.contact_terms(P, x, x + 0.01 * d)   # moved inwards over the step
+    assert list(C.idx) == [3]
+    np.testing.assert_allclose(C.n[0], d, atol=1e-14)
+    np.testing.assert_allclose(C.t[0], cen + r * d, atol=1e-14)
+
+
+def test_drop_onto_colliders_is_stopped():
+    """The falling cube is stopped by the ground: over 15 steps no vertex
+    sinks more than 1 cm below z = 0 and the centre of mass, falling at 2 m/s,
+    has stopped falling; every step keeps the objective below g(x_1)."""
+    w, P = _drop_problem(3, drop=0.005, speed=2.0)
+    qc, qp = w.q_cur.copy(), w.q_prev.copy()
+    for _ in range(15):
+        x, st = O.solve_step(P, qc, qp, iters=10, m=5)
+        assert not st.exhausted
+        assert min(st.g) < st.g0
+        assert x[:, 2].min() > -0.01
+        qp, qc = qc, x
+    vz = (qc[:, 2] - qp[:, 2]).mean() / P.h
+    assert vz > -0.3, vz
