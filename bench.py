@@ -312,12 +312,44 @@ def run_ours(args, rank, world, dist):
     line["gpu_launches"] = launches
     if not args.no_batch:
         line["batched"] = run_batched(args, stream)
+    if not args.no_collisions:
+        line["collisions"] = run_collisions(args, stream)
     if rank == 0 and not args.no_cpu_baseline:
         v, te, desc, cores = oracle_sample(w, budget_s=args.cpu_budget, counts=(trials, iters))
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": desc, "tet_grad_evals_per_s": te}
     sim.close()
     return line
+
+
+def run_collisions(args, stream):
+    """Collision terms (Sec. 4.3): an unclamped 40^3 Neo-Hookean cube
+    (384,000 tets) falling at 2 m/s onto a ground plane and a sphere, timed
+    over the impact; FP32-mixed, one graph per step."""
+    import torch
+
+    from paper_1604_07378_gb300 import hqn
+    from paper_1604_07378_gb300 import workloads as W
+
+    w = W.collision_drop(40, drop=0.01, speed=2.0)
+    sim = hqn.Sim.from_workload(w, precision=hqn.FP32_MIXED, stream=stream.cuda_stream,
+                                dyn_sweeps=SWEEPS[args.sweeps], leaf_size=args.leaf_size)
+    sim.set_state(w.q_cur, w.q_prev)
+    sim.step(2)  # warm-up: the fall before the impact
+    steps = 20
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc, st = sim.step(steps, stats=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    x, _ = sim.get_state()
+    sim.close()
+    return {"workload": "drop40_plane_sphere", "tets": w.n_tets, "colliders": ["plane", "sphere"],
+            "contact_scale": w.contact_scale, "steps_per_s": 1e3 / ms, "ms_per_step": ms, "steps": steps,
+            "status": rc, "ls_trials_per_iter": st["trials_total"] / max(1, st["iters_total"]),
+            "min_height_m": float(x[:, 2].min())}
 
 
 def run_batched(args, stream):
@@ -410,6 +442,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 512-simulation measurement")
+    ap.add_argument("--no-collisions", action="store_true", help="skip the collision measurement")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--leaf-size", type=int, default=0,
                     help="max vertices of a nested-dissection leaf (0 = the library default)")

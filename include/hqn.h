@@ -68,6 +68,20 @@ typedef enum {
                            float64 energy sums, Armijo test and inner products      */
 } hqn_precision;
 
+/* An analytic collider (see hqn_params.colliders). */
+#define HQN_MAX_COLLIDERS 4
+typedef enum {
+    HQN_COLLIDER_PLANE  = 1,  /* point[3] on the plane, normal[3] towards the free side
+                                 (normalised by the library)                         */
+    HQN_COLLIDER_SPHERE = 2   /* centre point[3], radius; the body stays outside      */
+} hqn_collider_kind;
+typedef struct {
+    int32_t kind;             /* hqn_collider_kind */
+    double  point[3];
+    double  normal[3];
+    double  radius;
+} hqn_collider;
+
 typedef struct {
     int32_t        n_verts;
     int32_t        n_tets;
@@ -120,6 +134,19 @@ typedef struct {
                              bit-identical results; 2 partitions the rows into
                              other work items, so its results differ from them
                              by rounding only                                      */
+    /* Collisions (Sec. 4.3) against analytic colliders, shared by every
+     * simulation of a handle.  At the start of each iteration (before the
+     * gradient at x_k) every free vertex that penetrates a collider and does
+     * not move away from it over the step (its displacement from the state
+     * q_l has a non-positive normal component) gets the energy term
+     * w_v ((x_v - t)^T n)^2, with t its projection on the collider and n the
+     * surface normal there, both frozen for the iteration, and
+     * w_v = contact_scale * m_v / h^2.  The terms enter the objective, its
+     * gradient and the line search but not A0 (no refactorisation).
+     * n_colliders = 0 (the default) disables them. */
+    int32_t n_colliders;  /* 0 .. HQN_MAX_COLLIDERS                                */
+    double  contact_scale;/* > 0 when n_colliders > 0 (default 100)                */
+    hqn_collider colliders[HQN_MAX_COLLIDERS];
 } hqn_params;
 
 #define HQN_MAX_HISTORY 16

@@ -436,7 +436,7 @@ def contact_terms(P: Problem, x, q_ref):
             c, r = np.asarray(col[1], float), float(col[2])
             rel = x - c
             dist = np.linalg.norm(rel, axis=1)
-            phi = dist - r
+            phi = np.where(dist > 0.0, dist - r, np.inf)  # at the centre: no normal, no term
             n = rel / np.maximum(dist, 1e-300)[:, None]
         else:
             raise ValueError(f"unknown collider {col[0]!r}")

@@ -167,6 +167,7 @@ struct Sim final : SimBase {
         {
             std::vector<int4> tets(T);
             std::vector<R> dm((size_t)9 * T), vol(T), mh2(n);
+            std::vector<V4<R>> rest(n);
             std::vector<int> vptr(n + 1, 0), cpos((size_t)4 * T, -1);
             int npos = 0;
             for (int k = 0; k < ns; ++k) {
@@ -179,6 +180,9 @@ struct Sim final : SimBase {
                 }
                 for (int i = 0; i < s.n; ++i) {
                     mh2[v0[k] + i] = (R)(s.mass[i] / (p.h * p.h));
+                    V4<R> &X = rest[v0[k] + i];
+                    X.x = (R)s.X[3 * (size_t)i]; X.y = (R)s.X[3 * (size_t)i + 1]; X.z = (R)s.X[3 * (size_t)i + 2];
+                    X.w = R(0);
                     for (int e = s.vt_ptr[i]; e < s.vt_ptr[i + 1]; ++e) {
                         const int sv = s.vt_slot[e];
                         cpos[(size_t)(sv & 3) * T + t0[k] + (sv >> 2)] = npos++;
@@ -197,6 +201,9 @@ struct Sim final : SimBase {
             if ((rc = upload(p_mh2, mh2.data(), mh2.size()))) return rc;
             if ((rc = upload(p_ptr, vptr.data(), vptr.size()))) return rc;
             if ((rc = upload(p_pos, cpos.data(), cpos.size()))) return rc;
+            const V4<R> *p_rest;
+            if ((rc = upload(p_rest, rest.data(), rest.size()))) return rc;
+            ds.rest = p_rest;
             ds.tets = p_t; ds.dminv = p_dm; ds.vol = p_vol; ds.mh2 = p_mh2; ds.vt_ptr = p_ptr; ds.corner_pos = p_pos;
         }
         // ---- vectors, rings, partials, control blocks
@@ -234,6 +241,21 @@ struct Sim final : SimBase {
             c.gz = (R)(p.h * p.h * p.gravity[2]);
             c.gamma = p.gamma;
             c.backtrack = p.backtrack;
+            c.ncol = p.n_colliders;
+            c.cscale = (R)p.contact_scale;
+            for (int q = 0; q < p.n_colliders; ++q) {
+                const hqn_collider &hc = p.colliders[q];
+                ColDev<R> &dc = c.col[q];
+                dc.kind = hc.kind;
+                dc.px = (R)hc.point[0]; dc.py = (R)hc.point[1]; dc.pz = (R)hc.point[2];
+                const double nn = std::sqrt(hc.normal[0] * hc.normal[0] + hc.normal[1] * hc.normal[1] +
+                                            hc.normal[2] * hc.normal[2]);
+                dc.nx = dc.ny = dc.nz = R(0);
+                if (hc.kind == HQN_COLLIDER_PLANE) {
+                    dc.nx = (R)(hc.normal[0] / nn); dc.ny = (R)(hc.normal[1] / nn); dc.nz = (R)(hc.normal[2] / nn);
+                }
+                dc.r = (R)hc.radius;
+            }
             MatDev<R> &M = D.mat;
             M.kind = s.mat.kind;
             M.mu = (R)s.mat.mu; M.lam = (R)s.mat.lam;
@@ -1314,6 +1336,21 @@ int create_any(int count, const hqn_mesh *meshes, const hqn_material *materials,
     if (count <= 0 || !meshes || !materials || !params) return fail(HQN_ERR_ARG, "null argument or empty batch");
     if (params->precision != HQN_FP32_MIXED && params->precision != HQN_FP64_PLAIN)
         return fail(HQN_ERR_ARG, "unknown precision");
+    if (params->n_colliders < 0 || params->n_colliders > HQN_MAX_COLLIDERS)
+        return fail(HQN_ERR_ARG, "n_colliders out of range");
+    if (params->n_colliders > 0 && !(params->contact_scale > 0.0 && std::isfinite(params->contact_scale)))
+        return fail(HQN_ERR_ARG, "contact_scale must be positive");
+    for (int k = 0; k < params->n_colliders; ++k) {
+        const hqn_collider &c = params->colliders[k];
+        if (c.kind == HQN_COLLIDER_PLANE) {
+            const double nn = c.normal[0] * c.normal[0] + c.normal[1] * c.normal[1] + c.normal[2] * c.normal[2];
+            if (!(nn > 0.0) || !std::isfinite(nn)) return fail(HQN_ERR_ARG, "a plane collider needs a nonzero normal");
+        } else if (c.kind == HQN_COLLIDER_SPHERE) {
+            if (!(c.radius > 0.0) || !std::isfinite(c.radius)) return fail(HQN_ERR_ARG, "a sphere collider needs a positive radius");
+        } else {
+            return fail(HQN_ERR_ARG, "unknown collider kind");
+        }
+    }
     if (params->tet_block != 0 && params->tet_block != TBS)
         return fail(HQN_ERR_UNSUPPORTED, "tet_block must be 0 or 128");
     try {
@@ -1358,6 +1395,8 @@ void hqn_default_params(hqn_params *p) {
     p->tet_block = TBS;
     p->ls_batch = 8;
     p->dyn_sweeps = 0;
+    p->n_colliders = 0;
+    p->contact_scale = 100.0;
 }
 
 int sim_create(const hqn_mesh *mesh, const hqn_material *material, const hqn_params *params, void *stream,

@@ -88,6 +88,14 @@ struct CondHandles {
     unsigned long long nd;   // if: non-descent reset of the direction
 };
 
+// An analytic collider (Sec. 4.3): plane (point p, unit normal n) or sphere
+// (centre p, radius r).
+template <typename R>
+struct ColDev {
+    int kind;
+    R px, py, pz, nx, ny, nz, r;
+};
+
 // Per-simulation constants passed by value.
 template <typename R>
 struct StepConst {
@@ -95,6 +103,9 @@ struct StepConst {
     R h2;              // h^2
     R gx, gy, gz;      // h^2 * gravity (the h^2 M^{-1} f_ext term of Eq. PD)
     double gamma, backtrack;
+    int ncol;          // colliders (0: no collision terms)
+    R cscale;          // collision weight w_v = cscale * m_v / h^2
+    ColDev<R> col[HQN_MAX_COLLIDERS];
 };
 
 }  // namespace hqn

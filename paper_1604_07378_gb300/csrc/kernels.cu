@@ -124,10 +124,43 @@ __global__ void __launch_bounds__(VBS) k_predict(DevSim<R> s) {
     }
 }
 
+// ---------------------------------------------------------------- collision terms (Sec. 4.3)
+
+// Calls f(gap, nx, ny, nz) for every collider that the vertex (rest position
+// X, displacement u, displacement u_l at the start of the step) penetrates
+// without moving away from it: gap = (x - t)^T n < 0, with t the projection of
+// x = X + u on the collider and n the surface normal there.  The terms are
+// w_v gap^2 (w_v = cscale m_v / h^2); with t and n frozen at the iteration's
+// start, along x + alpha d the gap is gap + alpha d^T n.
+template <typename R, typename F>
+__device__ __forceinline__ void for_contacts(const StepConst<R> &c, const V4<R> &X, const V4<R> &u, const V4<R> &ul,
+                                             F f) {
+    for (int k = 0; k < c.ncol; ++k) {
+        const ColDev<R> &q = c.col[k];
+        const R rx = (X.x - q.px) + u.x, ry = (X.y - q.py) + u.y, rz = (X.z - q.pz) + u.z;
+        R nx, ny, nz, gap;
+        if (q.kind == HQN_COLLIDER_PLANE) {
+            nx = q.nx; ny = q.ny; nz = q.nz;
+            gap = rx * nx + ry * ny + rz * nz;
+        } else {
+            const R dist = sqrt_(rx * rx + ry * ry + rz * rz);
+            if (!(dist > R(0))) continue;  // at the centre: no normal
+            const R inv = R(1) / dist;
+            nx = rx * inv; ny = ry * inv; nz = rz * inv;
+            gap = dist - q.r;
+        }
+        if (!(gap < R(0))) continue;
+        const R vn = (u.x - ul.x) * nx + (u.y - ul.y) * ny + (u.z - ul.z) * nz;
+        if (vn > R(0)) continue;
+        f(gap, nx, ny, nz);
+    }
+}
+
 // ---------------------------------------------------------------- inertia of a given x
 
 // Block partial of the inertia term 1/(2h^2) sum m_v |x_t - y|^2 of Eq. PD at
-// the caller-given point x_t (the start of a step, or an evaluation request).
+// the caller-given point x_t (the start of a step, or an evaluation request),
+// plus the collision terms active there.
 template <typename R>
 __global__ void __launch_bounds__(VBS) k_inertia(DevSim<R> s) {
     using A = ExactAcc<R>;
@@ -139,6 +172,10 @@ __global__ void __launch_bounds__(VBS) k_inertia(DevSim<R> s) {
         const V4<R> x = s.xt[g], yy = s.y[g];
         const R dx = x.x - yy.x, dy = x.y - yy.y, dz = x.z - yy.z;
         e[0] = A::add(e[0], R(0.5) * s.mh2[g] * (dx * dx + dy * dy + dz * dz));
+        if (D.c.ncol > 0 && i < D.c.nf) {
+            const R w = D.c.cscale * s.mh2[g];
+            for_contacts(D.c, s.rest[g], x, s.u_cur[g], [&](R gap, R, R, R) { e[0] = A::add(e[0], w * gap * gap); });
+        }
     }
     double tot[1];
     block_sum_exact<VBS, 1, R>(e, tot);
@@ -464,7 +501,8 @@ __device__ __forceinline__ void coef_recursion(HistSmem &h, int m) {
 // block sums, float64 beyond) are reduced.  The simulation's last block keeps
 // the pair if rho > 1e-12 |s| |t|, updates the Gram matrix, runs the first
 // loop of Alg. 2 on scalars and ends the simulation's iterations when its
-// count is reached or its line search gave up.
+// count is reached or its line search gave up.  The collision terms active
+// at the gathered point (Sec. 4.3) add 2 w_v gap n to its gradient.
 template <typename R, int MP1>
 __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandles h) {
     const SimDesc<R> &D = sim_desc(s, s.vblk_sim);
@@ -496,7 +534,11 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
         if (iter) dv = s.d[gi];
         const V4<R> yy = s.y[gi];
         const R mh = s.mh2[gi];
-        V4<R> go = dv;
+        V4<R> go = dv, Xr = dv, ul = dv;
+        if (D.c.ncol > 0) {
+            Xr = s.rest[gi];
+            ul = s.u_cur[gi];
+        }
         V4<R> Sa[MP1], Ta[MP1];
         V4<R> *S = s.S + D.ring0, *Tt = s.Tt + D.ring0;
         const size_t n = (size_t)D.c.n;
@@ -521,6 +563,12 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
         gn.y = gy + mh * (x.y - yy.y);
         gn.z = gz + mh * (x.z - yy.z);
         gn.w = R(0);
+        if (D.c.ncol > 0) {
+            const R w2 = R(2) * D.c.cscale * mh;
+            for_contacts(D.c, Xr, x, ul, [&](R gap, R nx, R ny, R nz) {
+                gn.x += w2 * gap * nx; gn.y += w2 * gap * ny; gn.z += w2 * gap * nz;
+            });
+        }
         if (iter) {
             if (push) {
                 V4<R> sv, tv;
@@ -723,7 +771,8 @@ __global__ void __launch_bounds__(VBS) k_r0_dots(DevSim<R> s) {
 // gd >= 0 the direction is not a descent direction: flag it so the history is
 // dropped (h.nd: any simulation flagged) -- and the coefficients of the
 // inertia term along the ray x_k + alpha d:
-// 1/(2h^2) sum m |x_k + alpha d - y|^2 = a0 + a1 alpha + a2 alpha^2.
+// 1/(2h^2) sum m |x_k + alpha d - y|^2 = a0 + a1 alpha + a2 alpha^2, with the
+// iteration's collision terms sum w (gap + alpha d^T n)^2 added to them.
 template <typename R, int MP1>
 __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, int set_nd) {
     const SimDesc<R> &D = sim_desc(s, s.vblk_sim);
@@ -753,12 +802,27 @@ __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, i
             if (p < count) {
                 dd.x += c[p] * sv[p].x; dd.y += c[p] * sv[p].y; dd.z += c[p] * sv[p].z;
             }
+        V4<R> Xr = dd, ul = dd;
+        if (D.c.ncol > 0) {
+            Xr = s.rest[gi];
+            ul = s.u_cur[gi];
+        }
         if (count > 0) s.d[gi] = dd;
         const R rx = x.x - yy.x, ry = x.y - yy.y, rz = x.z - yy.z;
         d4[0] = dotr(g, dd);
         d4[1] = R(0.5) * mh * (rx * rx + ry * ry + rz * rz);
         d4[2] = mh * (rx * dd.x + ry * dd.y + rz * dd.z);
         d4[3] = R(0.5) * mh * dotr(dd, dd);
+        if (D.c.ncol > 0) {
+            // the collision terms of this iteration (at x_k) along the ray
+            const R w = D.c.cscale * mh;
+            for_contacts(D.c, Xr, x, ul, [&](R gap, R nx, R ny, R nz) {
+                const R dn = dd.x * nx + dd.y * ny + dd.z * nz;
+                d4[1] += w * gap * gap;
+                d4[2] += R(2) * w * gap * dn;
+                d4[3] += w * dn * dn;
+            });
+        }
     }
     double tot[4];
     block_sum_r<VBS, 4, R>(d4, tot);

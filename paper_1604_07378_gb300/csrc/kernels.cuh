@@ -39,6 +39,7 @@ struct DevSim {
     const R *dminv;             // 9 x Tn (SoA), Dm^{-1}[j][b] at (3j + b) * Tn + t
     const R *vol;               // Tn
     const R *mh2;               // batch vertices: m_v / h^2
+    const V4<R> *rest;          // batch vertices: rest positions X (collision terms)
     const int *vt_ptr;          // batch vertices + 1
     const int *corner_pos;      // position of corner c of tet t (index c * Tn + t) in `corner`,
                                 // which holds every vertex's incident corners together, ascending t

@@ -45,12 +45,23 @@ class Material(C.Structure):
                 ("density", C.c_double), ("spline", _dp)]
 
 
+MAX_COLLIDERS = 4
+COLLIDER_PLANE, COLLIDER_SPHERE = 1, 2
+
+
+class Collider(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("point", C.c_double * 3), ("normal", C.c_double * 3),
+                ("radius", C.c_double)]
+
+
 class Params(C.Structure):
     _fields_ = [("h", C.c_double), ("gamma", C.c_double), ("backtrack", C.c_double),
                 ("x_start", C.c_double), ("x_end", C.c_double), ("gravity", C.c_double * 3),
                 ("iters", C.c_int32), ("history_m", C.c_int32), ("ls_max", C.c_int32),
                 ("precision", C.c_int32), ("leaf_size", C.c_int32), ("use_graph", C.c_int32),
-                ("tet_block", C.c_int32), ("ls_batch", C.c_int32), ("dyn_sweeps", C.c_int32)]
+                ("tet_block", C.c_int32), ("ls_batch", C.c_int32), ("dyn_sweeps", C.c_int32),
+                ("n_colliders", C.c_int32), ("contact_scale", C.c_double),
+                ("colliders", Collider * MAX_COLLIDERS)]
 
 
 class StepStats(C.Structure):
@@ -146,6 +157,24 @@ def default_params(**kw) -> Params:
     for k, v in kw.items():
         if k == "gravity":
             p.gravity[:] = list(v)
+        elif k == "colliders":
+            cols = list(v)
+            if len(cols) > MAX_COLLIDERS:
+                raise ValueError(f"at most {MAX_COLLIDERS} colliders")
+            p.n_colliders = len(cols)
+            for i, c in enumerate(cols):
+                # workloads.Collider or a ("plane", point, normal) / ("sphere", centre, radius) tuple
+                t = c.as_tuple() if hasattr(c, "as_tuple") else tuple(c)
+                cc = p.colliders[i]
+                cc.point[:] = list(t[1])
+                if t[0] == "plane":
+                    cc.kind = COLLIDER_PLANE
+                    cc.normal[:] = list(t[2])
+                elif t[0] == "sphere":
+                    cc.kind = COLLIDER_SPHERE
+                    cc.radius = float(t[2])
+                else:
+                    raise ValueError(f"unknown collider {t[0]!r}")
         else:
             setattr(p, k, v)
     return p
@@ -179,6 +208,9 @@ class Sim:
         pkw.setdefault("history_m", w.history)
         pkw.setdefault("h", w.h)
         pkw.setdefault("gravity", w.gravity)
+        if getattr(w, "colliders", ()):
+            pkw.setdefault("colliders", w.colliders)
+            pkw.setdefault("contact_scale", w.contact_scale)
         return cls(w.rest_pos, w.tets, w.clamped, kind=m.kind, E=m.E, nu=m.nu,
                    density=m.density, spline=m.spline, **pkw)
 
@@ -303,6 +335,9 @@ class Batch:
         pkw.setdefault("history_m", w0.history)
         pkw.setdefault("h", w0.h)
         pkw.setdefault("gravity", w0.gravity)
+        if getattr(w0, "colliders", ()):
+            pkw.setdefault("colliders", w0.colliders)
+            pkw.setdefault("contact_scale", w0.contact_scale)
         self.params = params if params is not None else default_params(**pkw)
         h = C.c_void_p()
         _check(lib.sim_batch_create(len(ws), meshes, mats, C.byref(self.params), C.c_void_p(stream or 0),

@@ -265,8 +265,9 @@ def collision_drop(n: int = 8, drop: float = 0.02, speed: float = 2.0, sphere: b
     """An unclamped n^3 Neo-Hookean cube falling onto the ground plane z = 0
     (Sec. 4.3's collision terms), its lowest face `drop` above it, every
     vertex moving down at `speed` m/s; with `sphere`, a sphere of radius
-    n*edge/4 sits on the ground under one corner of the cube's footprint, so
-    part of the cube lands on it."""
+    n*edge/4, sunk into the ground so that its top is just below the cube,
+    sits under one corner of the cube's footprint: that corner lands on it
+    first."""
     edge = 0.05
     w = lattice_workload((n, n, n), Material(kind, E, 0.4), clamp_axis=-1, seed=1609, name=name or f"drop{n}")
     shift = np.array([-0.5 * n * edge, -0.5 * n * edge, drop])
@@ -276,7 +277,8 @@ def collision_drop(n: int = 8, drop: float = 0.02, speed: float = 2.0, sphere: b
     cols = [Collider("plane", (0.0, 0.0, 0.0), (0.0, 0.0, 1.0))]
     if sphere:
         r = 0.25 * n * edge
-        cols.append(Collider("sphere", (-0.25 * n * edge, -0.25 * n * edge, 0.5 * r), radius=r))
+        top = 0.5 * drop  # the sphere's top, between the ground and the cube
+        cols.append(Collider("sphere", (-0.25 * n * edge, -0.25 * n * edge, top - r), radius=r))
     w.colliders = tuple(cols)
     w.meta.update({"drop": drop, "speed": speed})
     return w
