@@ -98,6 +98,12 @@ typedef struct {
     const double *spline;     /* HQN_SPLINE_VL only: 3 x 8 x 3 doubles, function
                                  (a, b, c) x knot x (knot, value, slope), knots
                                  strictly increasing; otherwise ignored (may be NULL) */
+    double        kappa;      /* anisotropic fibre term (Sec. 4.4): adds
+                                 kappa/2 (|F d| - 1)^2 per unit rest volume to any
+                                 base material; 0 = none.  A0 keeps the base
+                                 material's stiffness fit.                           */
+    double        fiber[3];   /* rest-pose fibre direction d (normalised by the
+                                 library; nonzero when kappa > 0)                   */
 } hqn_material;
 
 typedef struct {

@@ -24,6 +24,9 @@ taken by the CUDA path, written separately):
     history is dropped and d = -A0^{-1} grad;
   * the backtracking line search gives up after ls_max trials, keeping x_k and
     ending the step's iterations;
+  * the anisotropic fibre term kappa/2 (|F d| - 1)^2 of Sec. 4.4 is added to
+    the base material's energy density; A0 keeps the base material's
+    stiffness fit (Eq. stiffness is defined for Valanis-Landel energies only);
   * collisions (Sec. 4.3) against analytic colliders (a plane with its
     normal, or a sphere the body stays outside of): at the start of every
     iteration, before the gradient at x_k, each free vertex that penetrates a
@@ -58,6 +61,12 @@ J0_NEOHOOKEAN = 0.05
 # ----------------------------------------------------------------------------
 
 class VLMaterial:
+    # anisotropic fibre term kappa/2 (|F d| - 1)^2 (Sec. 4.4) on top of the
+    # stretch energy; kappa = 0: none.  It is not Valanis-Landel and does not
+    # enter the stiffness fit (A0 keeps the base material's).
+    kappa = 0.0
+    fiber = (0.0, 0.0, 0.0)
+
     def breakpoints(self): return ()
     def a(self, x): return np.zeros_like(x)
     def da(self, x): return np.zeros_like(x)
@@ -384,10 +393,23 @@ def deformation_gradients(P: Problem, x):
     return Ds @ P.Dm_inv
 
 
+def fiber_stretch(P: Problem, F):
+    """F d and |F d| for the material's fibre direction d (Sec. 4.4)."""
+    d = np.asarray(P.mat.fiber, dtype=np.float64)
+    Fd = F @ d
+    return Fd, np.linalg.norm(Fd, axis=1)
+
+
 def elastic_energy_per_tet(P: Problem, x):
+    """V (Psi(s) + kappa/2 (|F d| - 1)^2): the Valanis-Landel energy of the
+    stretches plus the anisotropic fibre term of Sec. 4.4 (kappa = 0: none)."""
     F = deformation_gradients(P, x)
     _, s, _ = signed_svd(F)
-    return P.vol * psi(P.mat, s)
+    e = psi(P.mat, s)
+    if P.mat.kappa:
+        _, nrm = fiber_stretch(P, F)
+        e = e + 0.5 * P.mat.kappa * (nrm - 1.0) ** 2
+    return P.vol * e
 
 
 def elastic_corner_gradients(P: Problem, x):
@@ -398,6 +420,11 @@ def elastic_corner_gradients(P: Problem, x):
     U, s, V = signed_svd(F)
     tau = dpsi(P.mat, s)
     Pk = U @ (tau[:, :, None] * np.swapaxes(V, -1, -2))
+    if P.mat.kappa:
+        # d/dF kappa/2 (|F d| - 1)^2 = kappa (|F d| - 1) (F d / |F d|) d^T
+        d = np.asarray(P.mat.fiber, dtype=np.float64)
+        Fd, nrm = fiber_stretch(P, F)
+        Pk = Pk + (P.mat.kappa * (nrm - 1.0) / nrm)[:, None, None] * (Fd[:, :, None] * d[None, None, :])
     H = P.vol[:, None, None] * (Pk @ np.swapaxes(P.Dm_inv, -1, -2))
     out = np.zeros((P.tets.shape[0], 4, 3))
     out[:, 1:, :] = np.swapaxes(H, -1, -2)
@@ -636,6 +663,10 @@ def newton_minimise(P: Problem, q_cur, q_prev, tol=1e-11, max_iter=100, fd_eps=1
 def problem_from_workload(w, x_start=0.5, x_end=1.5) -> Problem:
     m = w.material
     mat = make_material(m.kind, m.E, m.nu, m.spline)
+    kappa = float(getattr(m, "kappa", 0.0))
+    if kappa:
+        d = np.asarray(m.fiber, dtype=np.float64)
+        mat.fiber, mat.kappa = d / np.linalg.norm(d), kappa
     cols = tuple(c.as_tuple() for c in getattr(w, "colliders", ()))
     return build_problem(w.rest_pos, w.tets, w.clamped, mat, m.density, w.h, w.gravity,
                          x_start, x_end, colliders=cols, contact_scale=getattr(w, "contact_scale", 100.0))

@@ -42,7 +42,8 @@ class Mesh(C.Structure):
 
 class Material(C.Structure):
     _fields_ = [("kind", C.c_int32), ("E", C.c_double), ("nu", C.c_double),
-                ("density", C.c_double), ("spline", _dp)]
+                ("density", C.c_double), ("spline", _dp), ("kappa", C.c_double),
+                ("fiber", C.c_double * 3)]
 
 
 MAX_COLLIDERS = 4
@@ -184,7 +185,8 @@ class Sim:
     """One simulation handle (``sim_create`` ... ``sim_destroy``)."""
 
     def __init__(self, rest_pos, tets, clamped=None, *, kind=NEOHOOKEAN, E=1e5, nu=0.45,
-                 density=1000.0, spline=None, params: Params | None = None, stream=None, **pkw):
+                 density=1000.0, spline=None, kappa=0.0, fiber=(0.0, 0.0, 0.0),
+                 params: Params | None = None, stream=None, **pkw):
         lib = library()
         self._X = np.ascontiguousarray(rest_pos, dtype=np.float64)
         self._tets = np.ascontiguousarray(tets, dtype=np.int32)
@@ -193,7 +195,8 @@ class Sim:
         mesh = Mesh(self.n, self._tets.shape[0], _ptr(self._X), _ptr(self._tets, _ip),
                     None if self._cl is None else _ptr(self._cl, _up))
         self._spline = None if spline is None else np.ascontiguousarray(spline, dtype=np.float64)
-        mat = Material(kind, E, nu, density, None if self._spline is None else _ptr(self._spline))
+        mat = Material(kind, E, nu, density, None if self._spline is None else _ptr(self._spline),
+                       float(kappa), (C.c_double * 3)(*fiber))
         self.params = params if params is not None else default_params(**pkw)
         h = C.c_void_p()
         _check(lib.sim_create(C.byref(mesh), C.byref(mat), C.byref(self.params),
@@ -212,7 +215,8 @@ class Sim:
             pkw.setdefault("colliders", w.colliders)
             pkw.setdefault("contact_scale", w.contact_scale)
         return cls(w.rest_pos, w.tets, w.clamped, kind=m.kind, E=m.E, nu=m.nu,
-                   density=m.density, spline=m.spline, **pkw)
+                   density=m.density, spline=m.spline, kappa=getattr(m, "kappa", 0.0),
+                   fiber=getattr(m, "fiber", (0.0, 0.0, 0.0)), **pkw)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -328,7 +332,9 @@ class Batch:
             self._keep += [X, tets, cl, sp]
             meshes[k] = Mesh(X.shape[0], tets.shape[0], _ptr(X), _ptr(tets, _ip),
                              None if cl is None else _ptr(cl, _up))
-            mats[k] = Material(m.kind, m.E, m.nu, m.density, None if sp is None else _ptr(sp))
+            mats[k] = Material(m.kind, m.E, m.nu, m.density, None if sp is None else _ptr(sp),
+                               float(getattr(m, "kappa", 0.0)),
+                               (C.c_double * 3)(*getattr(m, "fiber", (0.0, 0.0, 0.0))))
             self.n.append(X.shape[0])
         w0 = ws[0]
         pkw.setdefault("iters", w0.iters)

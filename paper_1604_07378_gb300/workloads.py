@@ -35,6 +35,9 @@ class Material:
     density: float = 1000.0
     # spline control points, shape (3, 8, 3): function (a, b, c) x knot x (x, value, slope)
     spline: np.ndarray | None = None
+    # anisotropic fibre term kappa/2 (|F d| - 1)^2 (Sec. 4.4); kappa = 0: none
+    kappa: float = 0.0
+    fiber: tuple = (0.0, 0.0, 0.0)
 
     @property
     def mu(self) -> float:
@@ -258,6 +261,22 @@ def spline_bar_80x40x40(scale: int = 1) -> Workload:
     mat.spline = spline_control_points(mat.mu, mat.lam, rng)
     return lattice_workload(dims, mat, clamp_axis=0, seed=1606, twist_deg=90.0,
                             name=f"splinebar{dims[0]}x{dims[1]}x{dims[2]}")
+
+
+def fiber_cube(n: int = 8, kappa_scale: float = 5.0, fiber=(1.0, 1.0, 0.0), v: float = 0.5) -> Workload:
+    """Sec. 4.4's anisotropic example: an n^3 cube of corotated material
+    (mu : lambda = 1 : 10, as in the paper's mu = 10, lambda = 100) reinforced
+    along `fiber` with kappa = kappa_scale * mu (the paper's 50 = 5 mu),
+    z = 0 face clamped, the free vertices set moving with one seeded velocity
+    drawn from U[-v, v]^3 m/s."""
+    nu = 10.0 / 22.0                  # lambda / mu = 2 nu / (1 - 2 nu) = 10
+    E = 2.0 * (1.0 + nu) * 2e4        # mu = 2e4 Pa
+    mat = Material(COROTATED, E, nu)
+    d = np.asarray(fiber, dtype=np.float64)
+    mat.fiber = tuple(d / np.linalg.norm(d))
+    mat.kappa = kappa_scale * mat.mu
+    return lattice_workload((n, n, n), mat, clamp_axis=2, seed=1610, v_range=v, v_mode="body",
+                            name=f"fibercube{n}")
 
 
 def collision_drop(n: int = 8, drop: float = 0.02, speed: float = 2.0, sphere: bool = True,

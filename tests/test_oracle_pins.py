@@ -434,3 +434,50 @@ def test_drop_onto_colliders_is_stopped():
         qp, qc = qc, x
     vz = (qc[:, 2] - qp[:, 2]).mean() / P.h
     assert vz > -0.3, vz
+
+
+# ---------------------------------------------------------------- anisotropic fibre term (Sec. 4.4)
+
+def test_fiber_term_closed_form_and_invariances():
+    """kappa/2 (|F d| - 1)^2 per unit volume: a stretch s along d adds exactly
+    V kappa/2 (s - 1)^2 to the base energy, a stretch across d adds nothing,
+    the term vanishes at rest and is invariant under rotations of the
+    deformed state; the stiffness fit keeps the base material's k."""
+    w = W.fiber_cube(2, fiber=(1.0, 0.0, 0.0))
+    P = O.problem_from_workload(w)
+    base = O.problem_from_workload(W.lattice_workload((2, 2, 2), w.material.__class__(
+        w.material.kind, w.material.E, w.material.nu), clamp_axis=2))
+    assert P.k == base.k
+    X = w.rest_pos
+    assert np.allclose(O.elastic_energy_per_tet(P, X), 0.0)
+    for s, axis, extra in ((1.3, 0, True), (0.8, 0, True), (1.3, 1, False)):
+        x = X.copy()
+        x[:, axis] *= s
+        e = O.elastic_energy_per_tet(P, x) - O.elastic_energy_per_tet(base, x)
+        expect = P.vol * 0.5 * P.mat.kappa * (s - 1.0) ** 2 if extra else 0.0 * P.vol
+        np.testing.assert_allclose(e, expect, rtol=1e-12, atol=1e-9 * np.abs(expect).max() if extra else 1e-9)
+    rng = np.random.default_rng(2)
+    x = X + 0.01 * rng.normal(size=X.shape)
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    Q *= np.sign(np.linalg.det(Q))
+    np.testing.assert_allclose(O.elastic_energy_per_tet(P, x @ Q.T), O.elastic_energy_per_tet(P, x), rtol=1e-10)
+
+
+def test_fiber_gradient_matches_central_differences():
+    w = W.fiber_cube(2)
+    P = O.problem_from_workload(w)
+    rng = np.random.default_rng(12)
+    x = w.rest_pos + 0.01 * rng.normal(size=w.rest_pos.shape)
+    y = w.rest_pos + 0.01 * rng.normal(size=w.rest_pos.shape)
+    x[P.clamped] = w.rest_pos[P.clamped]
+    y[P.clamped] = w.rest_pos[P.clamped]
+    grad = O.gradient(P, x, y)
+    eps = 1e-7
+    fd = np.zeros_like(x)
+    for v in P.free:
+        for c in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[v, c] += eps
+            xm[v, c] -= eps
+            fd[v, c] = (O.objective(P, xp, y) - O.objective(P, xm, y)) / (2 * eps)
+    assert np.linalg.norm(fd - grad) / np.linalg.norm(grad) < 1e-6
