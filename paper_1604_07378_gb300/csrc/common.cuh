@@ -36,6 +36,8 @@ struct MatDev {
     R K0;               // a'(1) + 2 b'(1) + c'(1): the stress of the rest state
     R B1C1, C1;         // b'(1) + c'(1) and c'(1)
     R psi_rest;         // 3 a(1) + 3 b(1) + c(1)
+    R kappa;            // anisotropic fibre term kappa/2 (|F d| - 1)^2 (0: none)
+    R fd[3];            // its unit rest direction d
 };
 
 // Control block of one simulation's step, resident on the device.  Every

@@ -190,6 +190,12 @@ int material_dev(const hqn_material &m, MatDev<double> &d) {
     } else if (m.kind != HQN_STVK && m.kind != HQN_COROTATED && m.kind != HQN_POLY4) {
         return HQN_ERR_ARG;
     }
+    if (m.kappa != 0.0) {
+        const double nn = std::sqrt(m.fiber[0] * m.fiber[0] + m.fiber[1] * m.fiber[1] + m.fiber[2] * m.fiber[2]);
+        if (!(m.kappa > 0.0) || !std::isfinite(m.kappa) || !(nn > 0.0) || !std::isfinite(nn)) return HQN_ERR_ARG;
+        d.kappa = m.kappa;
+        for (int a = 0; a < 3; ++a) d.fd[a] = m.fiber[a] / nn;
+    }
     return HQN_OK;
 }
 

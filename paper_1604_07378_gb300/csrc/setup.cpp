@@ -389,6 +389,17 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
         err = "unknown material kind";
         return HQN_ERR_ARG;
     }
+    // anisotropic fibre term (Sec. 4.4); not part of the stiffness fit
+    if (matin.kappa != 0.0) {
+        const double nn = std::sqrt(matin.fiber[0] * matin.fiber[0] + matin.fiber[1] * matin.fiber[1] +
+                                    matin.fiber[2] * matin.fiber[2]);
+        if (!(matin.kappa > 0.0) || !std::isfinite(matin.kappa) || !(nn > 0.0) || !std::isfinite(nn)) {
+            err = "the fibre term needs kappa > 0 and a nonzero direction";
+            return HQN_ERR_ARG;
+        }
+        M.kappa = matin.kappa;
+        for (int a = 0; a < 3; ++a) M.fiber[a] = matin.fiber[a] / nn;
+    }
     S.k = fit_stiffness(M, prm.x_start, prm.x_end);
     if (!(S.k > 0) || !std::isfinite(S.k)) {
         err = "stiffness fit is not positive";

@@ -17,6 +17,7 @@ struct MaterialHost {
     int kind = HQN_NEOHOOKEAN;
     double mu = 0, lam = 0, J0 = 0.05, c0 = 0, c1 = 0, c2 = 0;
     double sx[3][8] = {}, sv[3][8] = {}, ss[3][8] = {};  // spline knots, values, slopes
+    double kappa = 0, fiber[3] = {};  // anisotropic fibre term kappa/2 (|F d| - 1)^2, unit d
 };
 
 // One supernode = one node of the nested-dissection tree: its columns are a

@@ -295,6 +295,25 @@ __device__ __forceinline__ R material_tau(const MatDev<R> &M, const R s[3], cons
     }
 }
 
+// Anisotropic fibre term of Sec. 4.4, kappa/2 (|F d| - 1)^2 for F = I + G:
+// with g = G d, |F d|^2 = 1 + 2 d.g + |g|^2, so |F d| - 1 =
+// (2 d.g + |g|^2) / (|F d| + 1) without cancellation near rest.  Returns the
+// energy density; w (if not null) gets F d and fac = kappa (|F d| - 1)/|F d|,
+// so that dPsi/dF = fac (F d) d^T.
+template <typename R>
+__device__ __forceinline__ R fiber_psi(const MatDev<R> &M, const R G[3][3], R Fd[3], R *fac) {
+    R g[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[a] = G[a][0] * M.fd[0] + G[a][1] * M.fd[1] + G[a][2] * M.fd[2];
+    const R s2 = R(2) * (M.fd[0] * g[0] + M.fd[1] * g[1] + M.fd[2] * g[2]) + (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    const R nrm = sqrt_(R(1) + s2);
+    const R e = s2 / (nrm + R(1));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Fd[a] = M.fd[a] + g[a];
+    if (fac) *fac = M.kappa * e / nrm;
+    return R(0.5) * M.kappa * e * e;
+}
+
 // Psi(F) alone, F = I + G, for the line-search trials (no singular vectors).
 // Neo-Hookean and StVK use the invariants, written so that no first-order
 // term is cancelled against another:
@@ -304,7 +323,7 @@ __device__ __forceinline__ R material_tau(const MatDev<R> &M, const R s[3], cons
 // The other materials take the stretches from the eigenvalues of S (Jacobi
 // without vectors); s3 carries the sign of det F.
 template <typename R>
-__device__ __forceinline__ R tet_psi(const MatDev<R> &M, const R G[3][3]) {
+__device__ __forceinline__ R tet_psi_base(const MatDev<R> &M, const R G[3][3]) {
     if (M.kind == HQN_NEOHOOKEAN) {
         const R tr = G[0][0] + G[1][1] + G[2][2];
         R n2 = R(0);
@@ -357,6 +376,17 @@ __device__ __forceinline__ R tet_psi(const MatDev<R> &M, const R G[3][3]) {
     return material_tau(M, s, l, tau);
 }
 
+// The energy density: the material's plus the fibre term, if any.
+template <typename R>
+__device__ __forceinline__ R tet_psi(const MatDev<R> &M, const R G[3][3]) {
+    R psi = tet_psi_base(M, G);
+    if (M.kappa > R(0)) {
+        R Fd[3];
+        psi += fiber_psi(M, G, Fd, (R *)nullptr);
+    }
+    return psi;
+}
+
 template <typename R> __device__ __forceinline__ R fma_(R a, R b, R c) { return fma(a, b, c); }
 
 // Psi(I + Gk + alpha Gd) for many step lengths alpha of one line search.
@@ -398,6 +428,14 @@ __device__ __forceinline__ void cofactor3(const R G[3][3], R C[3][3]) {
 
 template <typename R>
 __device__ __forceinline__ void psi_ray_setup(const MatDev<R> &M, const R Gk[3][3], const R Gd[3][3], PsiRay<R> &r) {
+    // G along the ray (the fibre term and the materials without a polynomial form)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            r.Gk[a][b] = Gk[a][b];
+            r.Gd[a][b] = Gd[a][b];
+        }
     if (M.kind == HQN_NEOHOOKEAN) {
         // tr G, |G|^2, m2(G) (sum of principal 2x2 minors) and det G along the ray
         const R t0 = Gk[0][0] + Gk[1][1] + Gk[2][2], t1 = Gd[0][0] + Gd[1][1] + Gd[2][2];
@@ -480,17 +518,11 @@ __device__ __forceinline__ void psi_ray_setup(const MatDev<R> &M, const R Gk[3][
         r.c[7] = E2[0][0] + E2[1][1] + E2[2][2];
         return;
     }
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-            r.Gk[a][b] = Gk[a][b];
-            r.Gd[a][b] = Gd[a][b];
-        }
 }
 
+// Neo-Hookean and StVK along the ray from the polynomial coefficients.
 template <typename R>
-__device__ __forceinline__ R psi_ray_eval(const MatDev<R> &M, const PsiRay<R> &r, R al) {
+__device__ __forceinline__ R psi_ray_poly(const MatDev<R> &M, const PsiRay<R> &r, R al) {
     if (M.kind == HQN_NEOHOOKEAN) {
         const R d = r.c[0] + al * (r.c[1] + al * (r.c[2] + al * r.c[3]));
         const R J = R(1) + d;
@@ -503,11 +535,25 @@ __device__ __forceinline__ R psi_ray_eval(const MatDev<R> &M, const PsiRay<R> &r
         const R dJ = J - M.J0;
         return R(0.5) * M.mu * Q + M.c0 + dJ * (M.c1 + R(0.5) * M.c2 * dJ);
     }
-    if (M.kind == HQN_STVK) {
-        const R n2 = r.c[0] + al * (r.c[1] + al * (r.c[2] + al * (r.c[3] + al * r.c[4])));
-        const R tr = r.c[5] + al * (r.c[6] + al * r.c[7]);
-        return M.mu * n2 + R(0.5) * M.lam * tr * tr;
-    }
+    const R n2 = r.c[0] + al * (r.c[1] + al * (r.c[2] + al * (r.c[3] + al * r.c[4])));
+    const R tr = r.c[5] + al * (r.c[6] + al * r.c[7]);
+    return M.mu * n2 + R(0.5) * M.lam * tr * tr;
+}
+
+template <typename R>
+__device__ __forceinline__ R psi_ray_fiber(const MatDev<R> &M, const PsiRay<R> &r, R al) {
+    if (!(M.kappa > R(0))) return R(0);
+    R G[3][3], Fd[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) G[p][q] = fma_(al, r.Gd[p][q], r.Gk[p][q]);
+    return fiber_psi(M, G, Fd, (R *)nullptr);
+}
+
+template <typename R>
+__device__ __forceinline__ R psi_ray_eval(const MatDev<R> &M, const PsiRay<R> &r, R al) {
+    if (M.kind == HQN_NEOHOOKEAN || M.kind == HQN_STVK) return psi_ray_poly(M, r, al) + psi_ray_fiber(M, r, al);
     R G[3][3];
 #pragma unroll
     for (int p = 0; p < 3; ++p)
@@ -515,6 +561,7 @@ __device__ __forceinline__ R psi_ray_eval(const MatDev<R> &M, const PsiRay<R> &r
         for (int q = 0; q < 3; ++q) G[p][q] = fma_(al, r.Gd[p][q], r.Gk[p][q]);
     return tet_psi(M, G);
 }
+
 
 // G = Du Dm^{-1}: du[j] = u_{j+1} - u_0 (rows), Di = Dm^{-1} row-major.
 template <typename R>
@@ -593,6 +640,18 @@ __device__ __forceinline__ void invariant_stress(const MatDev<R> &M, const R G[3
         for (int b = 0; b < 3; ++b) P[a][b] = Sv[a][b] + G[a][0] * Sv[0][b] + G[a][1] * Sv[1][b] + G[a][2] * Sv[2][b];
 }
 
+// P += d/dF of the fibre term: kappa (|F d| - 1) (F d / |F d|) d^T.
+template <typename R>
+__device__ __forceinline__ void add_fiber_stress(const MatDev<R> &M, const R G[3][3], R P[3][3]) {
+    if (!(M.kappa > R(0))) return;
+    R Fd[3], fac;
+    fiber_psi(M, G, Fd, &fac);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) P[a][b] += fac * Fd[a] * M.fd[b];
+}
+
 // Gradients of V*Psi with respect to the four corner positions, F = I + G.
 // First Piola P (invariant form for Neo-Hookean and StVK, otherwise
 // U diag(tau) V^T from the signed SVD); corners 1..3 get the columns of
@@ -602,6 +661,7 @@ __device__ __forceinline__ void tet_grad(const MatDev<R> &M, const R G[3][3], co
     R P[3][3];
     if (M.kind == HQN_NEOHOOKEAN || M.kind == HQN_STVK) {
         invariant_stress(M, G, P);
+        add_fiber_stress(M, G, P);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -615,7 +675,12 @@ __device__ __forceinline__ void tet_grad(const MatDev<R> &M, const R G[3][3], co
         for (int a = 0; a < 3; ++a)
 #pragma unroll
             for (int b = 0; b < 3; ++b)
-                P[a][b] = vol * (U[a][0] * tau[0] * V[b][0] + U[a][1] * tau[1] * V[b][1] + U[a][2] * tau[2] * V[b][2]);
+                P[a][b] = U[a][0] * tau[0] * V[b][0] + U[a][1] * tau[1] * V[b][1] + U[a][2] * tau[2] * V[b][2];
+        add_fiber_stress(M, G, P);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) P[a][b] *= vol;
     }
 #pragma unroll
     for (int j = 0; j < 3; ++j)

@@ -108,3 +108,34 @@ def test_batch_with_contacts_bitwise_equal_to_single_handles():
             sim.set_state(w.q_cur, w.q_prev)
             sim.step(4)
             np.testing.assert_array_equal(got[i], sim.get_state()[0])
+
+
+# ---------------------------------------------------------------- anisotropic fibre term (Sec. 4.4)
+
+def _fiber_workloads():
+    w_cor = W.fiber_cube(4)                                  # corotated base (signed-SVD path)
+    w_nh = W.fiber_cube(4, fiber=(0.0, 1.0, 1.0))
+    w_nh.material.kind = W.NEOHOOKEAN                        # invariant-form base
+    return [w_cor, w_nh]
+
+
+@pytest.mark.parametrize("idx", [0, 1], ids=["corotated", "neohookean"])
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_fiber_energy_gradient_and_step(idx, prec):
+    w = _fiber_workloads()[idx]
+    P = problem_for(w)
+    y = O.predictor(P, w.q_cur, w.q_prev)
+    rng = np.random.default_rng(21)
+    x = y + 3e-3 * rng.normal(size=y.shape) * (~w.clamped.astype(bool))[:, None]
+    x_ref, st = O.solve_step(P, w.q_cur, w.q_prev, iters=w.iters, m=w.history)
+    with sim_for(w, prec) as sim:
+        g, grad = sim.energy_grad(x, y)
+        sim.set_state(w.q_cur, w.q_prev)
+        rc, stats = sim.step(1, stats=True)
+        xs, _ = sim.get_state()
+    assert rel(grad, O.gradient(P, x, y)) <= (1e-10 if prec == FP64 else 1e-5)
+    assert abs(g - O.objective(P, x, y)) <= (1e-10 if prec == FP64 else 2e-6) * abs(O.objective(P, x, y))
+    assert rc >= 0
+    assert rel(xs, x_ref) <= (1e-9 if prec == FP64 else 1e-4), rel(xs, x_ref)
+    if prec == FP64:
+        assert stats["trials"] == st.trials
