@@ -27,6 +27,9 @@ taken by the CUDA path, written separately):
   * the anisotropic fibre term kappa/2 (|F d| - 1)^2 of Sec. 4.4 is added to
     the base material's energy density; A0 keeps the base material's
     stiffness fit (Eq. stiffness is defined for Valanis-Landel energies only);
+  * the iterative alternative to A0^{-1} (Sec. 8's comparison): Jacobi-
+    preconditioned CG from zero with a fixed number of iterations, the three
+    coordinate columns treated as one vector (one alpha, one beta);
   * collisions (Sec. 4.3) against analytic colliders (a plane with its
     normal, or a sphere the body stays outside of): at the start of every
     iteration, before the gradient at x_k, each free vertex that penetrates a
@@ -383,6 +386,40 @@ def solve_A(P: Problem, q):
     return out
 
 
+def jacobi_diagonal(P: Problem):
+    """diag(A0) on the free vertices (the Jacobi preconditioner)."""
+    return np.asarray(P.A.diagonal()).ravel()
+
+
+def solve_A_pcg(P: Problem, q, iters):
+    """An approximation of A0^{-1} q by `iters` iterations of Jacobi-
+    preconditioned conjugate gradients from zero (the paper's comparison
+    with iterative solvers, Sec. 8): the three right-hand sides form one
+    vector (inner products tr(a^T b)), so every iteration has one step
+    length alpha and one beta.  Stops early only if the residual vanishes."""
+    out = np.zeros_like(q)
+    b = np.ascontiguousarray(q[P.free])
+    dinv = 1.0 / jacobi_diagonal(P)
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = dinv[:, None] * r
+    p = z.copy()
+    rz = tr_dot(r, z)
+    for _ in range(iters):
+        if rz == 0.0:
+            break
+        Ap = P.A @ p
+        alpha = rz / tr_dot(p, Ap)
+        x = x + alpha * p
+        r = r - alpha * Ap
+        z = dinv[:, None] * r
+        rz_new = tr_dot(r, z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    out[P.free] = x
+    return out
+
+
 # ----------------------------------------------------------------------------
 # Objective g(x) of Eq. PD and its gradient.
 # ----------------------------------------------------------------------------
@@ -531,16 +568,17 @@ def tr_dot(a, b):
     return float(np.sum(a * b))
 
 
-def lbfgs_direction(P: Problem, grad, history):
+def lbfgs_direction(P: Problem, grad, history, pcg_iters=0):
     """Alg. 2: q := -grad; newest-to-oldest first loop; r := A0^{-1} q;
-    oldest-to-newest second loop; d := r.  history is oldest-first [(s, t, rho)]."""
+    oldest-to-newest second loop; d := r.  history is oldest-first [(s, t, rho)].
+    pcg_iters > 0 replaces A0^{-1} q by that many Jacobi-PCG iterations."""
     q = -grad
     zeta = [0.0] * len(history)
     for i in range(len(history) - 1, -1, -1):
         s, t, rho = history[i]
         zeta[i] = tr_dot(s, q) / rho
         q = q - zeta[i] * t
-    r = solve_A(P, q)
+    r = solve_A_pcg(P, q, pcg_iters) if pcg_iters > 0 else solve_A(P, q)
     for i in range(len(history)):
         s, t, rho = history[i]
         eta = tr_dot(t, r) / rho
@@ -558,8 +596,9 @@ class StepStats:
 
 
 def solve_step(P: Problem, q_cur, q_prev, iters=10, m=5, gamma=0.3, backtrack=0.5,
-               ls_max=30, return_iterates=False):
-    """One implicit-Euler step by Alg. 1 with the direction of Alg. 2.
+               ls_max=30, return_iterates=False, pcg_iters=0):
+    """One implicit-Euler step by Alg. 1 with the direction of Alg. 2
+    (pcg_iters > 0: A0^{-1} by that many Jacobi-PCG iterations).
     Returns (x_{iters+1}, stats[, iterates])."""
     y = predictor(P, q_cur, q_prev)
     x = y.copy()                                   # x_1 := y
@@ -574,12 +613,12 @@ def solve_step(P: Problem, q_cur, q_prev, iters=10, m=5, gamma=0.3, backtrack=0.
             # the collision terms are updated at the start of the iteration,
             # before the gradient at x_k (Sec. 4.3); g(x_k) is re-evaluated with them
             gx = objective(P, x, y, col)
-        d = lbfgs_direction(P, grad, history)
+        d = lbfgs_direction(P, grad, history, pcg_iters)
         gd = tr_dot(grad, d)
         if gd >= 0.0 and history:
             history = []
             st.resets += 1
-            d = lbfgs_direction(P, grad, history)
+            d = lbfgs_direction(P, grad, history, pcg_iters)
             gd = tr_dot(grad, d)
         alpha = 1.0 / backtrack
         accepted = False
