@@ -314,12 +314,51 @@ def run_ours(args, rank, world, dist):
         line["batched"] = run_batched(args, stream)
     if not args.no_collisions:
         line["collisions"] = run_collisions(args, stream)
+    if not args.no_pcg:
+        line["a0_pcg"] = run_pcg(args, stream, x32)
     if rank == 0 and not args.no_cpu_baseline:
         v, te, desc, cores = oracle_sample(w, budget_s=args.cpu_budget, counts=(trials, iters))
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": desc, "tet_grad_evals_per_s": te}
     sim.close()
     return line
+
+
+def run_pcg(args, stream, x_direct):
+    """The iterative alternative to the factorised A0^{-1} (the paper's
+    comparison with iterative solvers): cube40, FP32-mixed, Jacobi-PCG with
+    5 and 15 iterations in every L-BFGS direction; time-steps/s, the solve's
+    time and the position difference from the direct-solve step."""
+    import torch
+
+    from paper_1604_07378_gb300 import hqn
+    from paper_1604_07378_gb300 import workloads as W
+
+    w = W.cube40(W.NEOHOOKEAN)
+    out = {"workload": WORKLOAD}
+    for iters in (5, 15):
+        sim = hqn.Sim.from_workload(w, precision=hqn.FP32_MIXED, stream=stream.cuda_stream,
+                                    a0_solver=1, pcg_iters=iters)
+        sim.set_state(w.q_cur, w.q_prev)
+        sim.step(1)
+        x, _ = sim.get_state()
+        ex = float(np.linalg.norm(x - x_direct) / np.linalg.norm(x_direct))
+        sim.set_state(w.q_cur, w.q_prev)
+        sim.step(2)
+        steps = 20
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, st = sim.step(steps, stats=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        solve_ms = sim.time_stage(hqn.STAGE_SOLVE, 10)
+        sim.close()
+        out[f"pcg{iters}"] = {"steps_per_s": 1e3 / ms, "ms_per_step": ms, "solve_ms": solve_ms, "status": rc,
+                              "ls_trials_per_iter": st["trials_total"] / max(1, st["iters_total"]),
+                              "pos_err_vs_direct_one_step": ex}
+    return out
 
 
 def run_collisions(args, stream):
@@ -443,6 +482,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 512-simulation measurement")
     ap.add_argument("--no-collisions", action="store_true", help="skip the collision measurement")
+    ap.add_argument("--no-pcg", action="store_true", help="skip the Jacobi-PCG measurement")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--leaf-size", type=int, default=0,
                     help="max vertices of a nested-dissection leaf (0 = the library default)")

@@ -153,6 +153,13 @@ typedef struct {
     int32_t n_colliders;  /* 0 .. HQN_MAX_COLLIDERS                                */
     double  contact_scale;/* > 0 when n_colliders > 0 (default 100)                */
     hqn_collider colliders[HQN_MAX_COLLIDERS];
+    /* The initial Hessian's solve r = A0^{-1} q of Alg. 2: 0 = the factorised
+     * A0 (default); 1 = pcg_iters iterations of Jacobi-preconditioned
+     * conjugate gradients from zero, A0 applied matrix-free (the paper's
+     * comparison with iterative solvers; the three coordinate columns form one
+     * vector).  sim_solve_A0 then returns that approximation. */
+    int32_t a0_solver;
+    int32_t pcg_iters;    /* >= 1 when a0_solver = 1 (default 15)                  */
 } hqn_params;
 
 #define HQN_MAX_HISTORY 16

@@ -214,6 +214,17 @@ struct Sim final : SimBase {
         if ((rc = alloc(ds.S, ring))) return rc;
         if ((rc = alloc(ds.Tt, ring))) return rc;
         if ((rc = alloc(ds.corner, (size_t)4 * T))) return rc;
+        if (p.a0_solver == 1) {
+            V4<R> **pv[] = {&ds.pcg_r, &ds.pcg_z, &ds.pcg_p, &ds.pcg_ap};
+            for (auto v : pv)
+                if ((rc = alloc(*v, n))) return rc;
+            std::vector<R> dinv(n, R(0));
+            for (int k = 0; k < ns; ++k)
+                for (int j = 0; j < S[k].n_free; ++j) dinv[v0[k] + j] = (R)(1.0 / S[k].a0_diag[j]);
+            const R *p_dinv;
+            if ((rc = upload(p_dinv, dinv.data(), dinv.size()))) return rc;
+            ds.pcg_dinv = p_dinv;
+        }
         if ((rc = alloc(ds.part_in, nvb))) return rc;
         if ((rc = alloc(ds.part_el, ntb))) return rc;
         // per-block partials: up to 3 + 3 (m + 1) sums (gather with a history
@@ -241,6 +252,7 @@ struct Sim final : SimBase {
             c.gz = (R)(p.h * p.h * p.gravity[2]);
             c.gamma = p.gamma;
             c.backtrack = p.backtrack;
+            c.kstiff = (R)s.k;
             c.ncol = p.n_colliders;
             c.cscale = (R)p.contact_scale;
             for (int q = 0; q < p.n_colliders; ++q) {
@@ -1007,16 +1019,21 @@ struct Sim final : SimBase {
     }
 
     // ---- pieces of the step
+    // r = A0^{-1} q into d: the factorised solve, or the Jacobi-PCG approximation.
+    void enqueue_A0inv(cudaStream_t s) {
+        if (prm.a0_solver == 1) launch_pcg(ds, (const V4<R> *)ds.q, ds.d, prm.pcg_iters, s);
+        else launch_solve(dsol, ds.q, ds.z, ds.d, s);
+    }
     void enqueue_direction(CondHandles h, int set_nd, cudaStream_t s) {
         launch_q(ds, s);
-        launch_solve(dsol, ds.q, ds.z, ds.d, s);
+        enqueue_A0inv(s);
         launch_r0_dots(ds, s);
         launch_direction_final(ds, h, set_nd, s);
     }
     void enqueue_reset_direction(cudaStream_t s) {
         launch_reset_history(ds, s);
         launch_q(ds, s);
-        launch_solve(dsol, ds.q, ds.z, ds.d, s);
+        enqueue_A0inv(s);
         launch_r0_dots(ds, s);
         launch_direction_final(ds, CondHandles{0, 0, 0}, 0, s);
     }
@@ -1216,7 +1233,7 @@ struct Sim final : SimBase {
     int solve_A0(const double *q, double *r) override {
         int rc;
         if ((rc = put_vec(0, ds.q, q, false, true))) return rc;
-        launch_solve(dsol, ds.q, ds.z, ds.d, st);
+        enqueue_A0inv(st);
         CK(cudaGetLastError());
         if ((rc = read_ctl())) return rc;
         return get_vec(0, ds.d, r, false, true);
@@ -1255,7 +1272,7 @@ struct Sim final : SimBase {
             switch (stage) {
                 case HQN_STAGE_TET: launch_tet(ds, TET_EVAL, none, st); break;
                 case HQN_STAGE_GATHER: launch_gather(ds, G_EVAL, none, st); break;
-                case HQN_STAGE_SOLVE: launch_solve(dsol, ds.q, ds.z, ds.d, st); break;
+                case HQN_STAGE_SOLVE: enqueue_A0inv(st); break;
                 case HQN_STAGE_LS_PASS: launch_ls(ds, none, st); break;
                 default: enqueue_direction(none, 0, st); break;
             }
@@ -1338,6 +1355,9 @@ int create_any(int count, const hqn_mesh *meshes, const hqn_material *materials,
     if (count <= 0 || !meshes || !materials || !params) return fail(HQN_ERR_ARG, "null argument or empty batch");
     if (params->precision != HQN_FP32_MIXED && params->precision != HQN_FP64_PLAIN)
         return fail(HQN_ERR_ARG, "unknown precision");
+    if (params->a0_solver != 0 && params->a0_solver != 1) return fail(HQN_ERR_ARG, "unknown a0_solver");
+    if (params->a0_solver == 1 && (params->pcg_iters < 1 || params->pcg_iters > 1000))
+        return fail(HQN_ERR_ARG, "pcg_iters must be in [1, 1000]");
     if (params->n_colliders < 0 || params->n_colliders > HQN_MAX_COLLIDERS)
         return fail(HQN_ERR_ARG, "n_colliders out of range");
     if (params->n_colliders > 0 && !(params->contact_scale > 0.0 && std::isfinite(params->contact_scale)))
@@ -1399,6 +1419,8 @@ void hqn_default_params(hqn_params *p) {
     p->dyn_sweeps = 0;
     p->n_colliders = 0;
     p->contact_scale = 100.0;
+    p->a0_solver = 0;
+    p->pcg_iters = 15;
 }
 
 int sim_create(const hqn_mesh *mesh, const hqn_material *material, const hqn_params *params, void *stream,

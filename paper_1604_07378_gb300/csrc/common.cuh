@@ -53,6 +53,7 @@ struct Ctl {
     double alpha;      // current step length
     double g0;         // g(x_1), x_1 = y
     double ls_a[3];    // inertia term along d: I(alpha) = a0 + a1 alpha + a2 alpha^2
+    double pcg_rz, pcg_alpha, pcg_beta;  // Jacobi-PCG scalars (iterative A0^{-1})
     double zeta[HQN_MAX_HISTORY + 1];  // first-loop coefficients by age (0 = newest)
     double coef[HQN_MAX_HISTORY + 1];  // second-loop coefficients zeta - eta by age
     double rho[HQN_MAX_HISTORY + 1];   // tr(t^T s) by ring slot
@@ -81,7 +82,7 @@ struct Ctl {
 };
 
 // Ticket slots (one per kernel family so consecutive kernels never share one).
-enum { TK_TRIAL = 0, TK_TET = 1, TK_GATHER = 2, TK_VEC = 3, TK_LS = 4, TK_DOT = 5 };
+enum { TK_TRIAL = 0, TK_TET = 1, TK_GATHER = 2, TK_VEC = 3, TK_LS = 4, TK_DOT = 5, TK_PCG_A = 6, TK_PCG_B = 7 };
 
 // Graph conditional handles a kernel may set (0 = not inside a graph).
 struct CondHandles {
@@ -105,6 +106,7 @@ struct StepConst {
     R h2;              // h^2
     R gx, gy, gz;      // h^2 * gravity (the h^2 M^{-1} f_ext term of Eq. PD)
     double gamma, backtrack;
+    R kstiff;          // the stiffness k of Eq. stiffness (the matrix-free L of A0)
     int ncol;          // colliders (0: no collision terms)
     R cscale;          // collision weight w_v = cscale * m_v / h^2
     ColDev<R> col[HQN_MAX_COLLIDERS];

@@ -856,6 +856,163 @@ __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, i
     if (set_nd) batch_condition(s, BT_ND, h.nd, [](const volatile Ctl *x) { return x->nondescent != 0; });
 }
 
+// ---------------------------------------------------------------- Jacobi-PCG in lieu of A0^{-1}
+//
+// The paper's comparison with iterative solvers (Sec. 8): a fixed number of
+// Jacobi-preconditioned conjugate-gradient iterations from zero replaces the
+// factorised solve.  A0 = M/h^2 + L is applied matrix-free: L p is the
+// gradient of 1/2 sum_t V_t k |G_t p|^2, i.e. per tet the corner gradients of
+// the linear stress P = V k G(p) (G(p) = [p1 - p0, p2 - p0, p3 - p0] Dm^{-1}),
+// summed per vertex through the vertex-ordered corner array.  The three
+// coordinate columns form one vector: one alpha and one beta per iteration,
+// from fixed-order float64 grid sums.  Each iteration is three launches:
+//   tet:    corners of L p, p = z + beta p_old formed on the fly;
+//   gather: p (stored), A0 p, p^T A0 p -> alpha = r^T z / p^T A0 p;
+//   update: x += alpha p, r -= alpha A0 p, z = D^{-1} r, r^T z -> beta.
+
+template <typename R>
+__device__ __forceinline__ V4<R> pcg_p(const DevSim<R> &s, int g, R beta) {
+    const V4<R> z = s.pcg_z[g], p = s.pcg_p[g];
+    V4<R> o;
+    o.x = z.x + beta * p.x; o.y = z.y + beta * p.y; o.z = z.z + beta * p.z; o.w = R(0);
+    return o;
+}
+
+// x = 0 (out), r = q, z = D^{-1} q, p_old = 0, rz = r^T z, beta = 0.
+template <typename R>
+__global__ void __launch_bounds__(VBS) k_pcg_init(DevSim<R> s, const V4<R> *q, V4<R> *out) {
+    const SimDesc<R> &D = sim_desc(s, s.vblk_sim);
+    Ctl *ctl = D.ctl;
+    const int i = (blockIdx.x - D.vb0) * VBS + threadIdx.x;
+    R dr[1] = {R(0)};
+    if (i < D.c.n) {
+        const int g = D.v0 + i;
+        V4<R> r = q[g], z, zero;
+        zero.x = zero.y = zero.z = zero.w = R(0);
+        if (i >= D.c.nf) r = zero;
+        const R di = i < D.c.nf ? s.pcg_dinv[g] : R(0);
+        z.x = di * r.x; z.y = di * r.y; z.z = di * r.z; z.w = R(0);
+        s.pcg_r[g] = r;
+        s.pcg_z[g] = z;
+        s.pcg_p[g] = zero;
+        out[g] = zero;
+        dr[0] = dotr(r, z);
+    }
+    double tot[1];
+    block_sum_r<VBS, 1, R>(dr, tot);
+    if (!sim_arrive<1>(tot, s.part_v, s.nvb, D.nvb, &ctl->ticket[TK_PCG_B])) return;
+    __threadfence();
+    const double rz = sum_block_range<VBS>(s.part_v, D.vb0, D.nvb);
+    if (threadIdx.x == 0) {
+        ctl->ticket[TK_PCG_B] = 0u;
+        ctl->pcg_rz = rz;
+        ctl->pcg_beta = 0.0;
+    }
+}
+
+// Corners of L p (one thread per tet).
+template <typename R>
+__global__ void __launch_bounds__(TBS, 8) k_pcg_tet(DevSim<R> s) {
+    const SimDesc<R> &D = sim_desc(s, s.tblk_sim);
+    const int tl = (blockIdx.x - D.tb0) * TBS + threadIdx.x;
+    if (tl >= D.c.T) return;
+    const R beta = (R)D.ctl->pcg_beta;
+    const int t = D.t0 + tl;
+    const int4 v = s.tets[t];
+    const V4<R> p0 = pcg_p(s, v.x, beta), p1 = pcg_p(s, v.y, beta), p2 = pcg_p(s, v.z, beta),
+                p3 = pcg_p(s, v.w, beta);
+    R du[3][3], Di[9], G[3][3];
+    edge_diffs(p0, p1, p2, p3, du);
+    load_dm(s, t, Di);
+    def_grad(du, Di, G);
+    const R w = s.vol[t] * D.c.kstiff;
+    R g[4][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            g[j + 1][a] = w * (G[a][0] * Di[j * 3 + 0] + G[a][1] * Di[j * 3 + 1] + G[a][2] * Di[j * 3 + 2]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[0][a] = -(g[1][a] + g[2][a] + g[3][a]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        V4<R> o;
+        o.x = g[k][0]; o.y = g[k][1]; o.z = g[k][2]; o.w = R(0);
+        s.corner[s.corner_pos[(size_t)k * s.Tn + t]] = o;
+    }
+}
+
+// p = z + beta p_old (stored), A0 p = M/h^2 p + L p, and p^T A0 p; the last
+// block sets alpha = r^T z / p^T A0 p.
+template <typename R>
+__global__ void __launch_bounds__(VBS) k_pcg_gather(DevSim<R> s) {
+    const SimDesc<R> &D = sim_desc(s, s.vblk_sim);
+    Ctl *ctl = D.ctl;
+    const int i = (blockIdx.x - D.vb0) * VBS + threadIdx.x;
+    R dr[1] = {R(0)};
+    if (i < D.c.nf) {
+        const int g = D.v0 + i;
+        const R beta = (R)ctl->pcg_beta;
+        const int b = s.vt_ptr[g], e = s.vt_ptr[g + 1];
+        const V4<R> p = pcg_p(s, g, beta);
+        const R mh = s.mh2[g];
+        R ax = R(0), ay = R(0), az = R(0);
+#pragma unroll 8
+        for (int k = b; k < e; ++k) {
+            const V4<R> c = s.corner[k];
+            ax += c.x; ay += c.y; az += c.z;
+        }
+        V4<R> ap;
+        ap.x = ax + mh * p.x; ap.y = ay + mh * p.y; ap.z = az + mh * p.z; ap.w = R(0);
+        s.pcg_p[g] = p;
+        s.pcg_ap[g] = ap;
+        dr[0] = dotr(p, ap);
+    }
+    double tot[1];
+    block_sum_r<VBS, 1, R>(dr, tot);
+    if (!sim_arrive<1>(tot, s.part_v, s.nvb, D.nvb, &ctl->ticket[TK_PCG_A])) return;
+    __threadfence();
+    const double pap = sum_block_range<VBS>(s.part_v, D.vb0, D.nvb);
+    if (threadIdx.x == 0) {
+        ctl->ticket[TK_PCG_A] = 0u;
+        ctl->pcg_alpha = pap > 0.0 ? ctl->pcg_rz / pap : 0.0;
+    }
+}
+
+// x += alpha p, r -= alpha A0 p, z = D^{-1} r; the last block sets
+// beta = r^T z (new) / r^T z (old).
+template <typename R>
+__global__ void __launch_bounds__(VBS) k_pcg_update(DevSim<R> s, V4<R> *out) {
+    const SimDesc<R> &D = sim_desc(s, s.vblk_sim);
+    Ctl *ctl = D.ctl;
+    const int i = (blockIdx.x - D.vb0) * VBS + threadIdx.x;
+    R dr[1] = {R(0)};
+    if (i < D.c.nf) {
+        const int g = D.v0 + i;
+        const R alpha = (R)ctl->pcg_alpha;
+        const V4<R> p = s.pcg_p[g], ap = s.pcg_ap[g];
+        V4<R> x = out[g], r = s.pcg_r[g], z;
+        const R di = s.pcg_dinv[g];
+        x.x += alpha * p.x; x.y += alpha * p.y; x.z += alpha * p.z;
+        r.x -= alpha * ap.x; r.y -= alpha * ap.y; r.z -= alpha * ap.z;
+        z.x = di * r.x; z.y = di * r.y; z.z = di * r.z; z.w = R(0);
+        out[g] = x;
+        s.pcg_r[g] = r;
+        s.pcg_z[g] = z;
+        dr[0] = dotr(r, z);
+    }
+    double tot[1];
+    block_sum_r<VBS, 1, R>(dr, tot);
+    if (!sim_arrive<1>(tot, s.part_v, s.nvb, D.nvb, &ctl->ticket[TK_PCG_B])) return;
+    __threadfence();
+    const double rz = sum_block_range<VBS>(s.part_v, D.vb0, D.nvb);
+    if (threadIdx.x == 0) {
+        ctl->ticket[TK_PCG_B] = 0u;
+        ctl->pcg_beta = ctl->pcg_rz > 0.0 ? rz / ctl->pcg_rz : 0.0;
+        ctl->pcg_rz = rz;
+    }
+}
+
 // Drops the history of the simulations whose direction was not a descent
 // direction (the others keep theirs and recompute the same direction).
 template <typename R>
@@ -992,6 +1149,14 @@ void launch_direction_final(const DevSim<R> &s, CondHandles h, int set_nd, cudaS
 template <typename R> void launch_reset_history(const DevSim<R> &s, cudaStream_t st) {
     k_reset_history<R><<<1, 256, 0, st>>>(s);
 }
+template <typename R> void launch_pcg(const DevSim<R> &s, const V4<R> *q, V4<R> *out, int iters, cudaStream_t st) {
+    k_pcg_init<R><<<s.nvb, VBS, 0, st>>>(s, q, out);
+    for (int k = 0; k < iters; ++k) {
+        k_pcg_tet<R><<<s.ntb, TBS, 0, st>>>(s);
+        k_pcg_gather<R><<<s.nvb, VBS, 0, st>>>(s);
+        k_pcg_update<R><<<s.nvb, VBS, 0, st>>>(s, out);
+    }
+}
 template <typename R> void launch_commit(const DevSim<R> &s, cudaStream_t st) {
     k_commit<R><<<s.nvb, VBS, 0, st>>>(s);
 }
@@ -1010,6 +1175,7 @@ template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream
     template void launch_direction_final<R>(const DevSim<R> &, CondHandles, int, cudaStream_t); \
     template void launch_reset_history<R>(const DevSim<R> &, cudaStream_t);          \
     template void launch_commit<R>(const DevSim<R> &, cudaStream_t);                 \
+    template void launch_pcg<R>(const DevSim<R> &, const V4<R> *, V4<R> *, int, cudaStream_t); \
     template void launch_hist_row<R>(const DevSim<R> &, int, cudaStream_t, int);
 
 HQN_INST(float)

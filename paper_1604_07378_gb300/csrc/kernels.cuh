@@ -47,6 +47,10 @@ struct DevSim {
     V4<R> *u_cur, *u_prev, *y, *xk, *xt, *gk, *d, *q, *z;
     V4<R> *S, *Tt;              // history rings
     V4<R> *corner;              // 4 x Tn corner gradients in vertex order (vt_ptr ranges)
+    // Jacobi-PCG in lieu of A0^{-1} (iterative solver): residual, preconditioned
+    // residual, search direction, A0 p and the inverse diagonal of A0 (free vertices)
+    V4<R> *pcg_r, *pcg_z, *pcg_p, *pcg_ap;
+    const R *pcg_dinv;
     // per-block partial sums: part_x[k * (blocks of the kernel) + block]
     double *part_in, *part_el, *part_g, *part_v, *part_ls;
     unsigned int *batch_ticket; // arrival counters of the simulations' last blocks (graph conditions)
@@ -80,6 +84,9 @@ template <typename R> void launch_r0_dots(const DevSim<R> &s, cudaStream_t st);
 template <typename R> void launch_direction_final(const DevSim<R> &s, CondHandles h, int set_nd, cudaStream_t st);
 // Drops the history of the simulations flagged non-descent.
 template <typename R> void launch_reset_history(const DevSim<R> &s, cudaStream_t st);
+// out = approximation of A0^{-1} q by `iters` Jacobi-PCG iterations from zero
+// (matrix-free A0 = M/h^2 + sum_t V_t k G_t^T G_t; 1 + 3 iters launches).
+template <typename R> void launch_pcg(const DevSim<R> &s, const V4<R> *q, V4<R> *out, int iters, cudaStream_t st);
 template <typename R> void launch_commit(const DevSim<R> &s, cudaStream_t st);
 // Caller-given history of simulation 0: Gram row a, rho_a and s_a^T grad
 // (run for a = 0..count-1).

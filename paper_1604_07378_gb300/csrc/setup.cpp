@@ -564,6 +564,10 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
         }
         c.resize(w);
     }
+    S.a0_diag.assign(nf, 0.0);
+    for (int j = 0; j < nf; ++j)
+        for (const auto &e : Acol[j])
+            if (e.first == j) S.a0_diag[j] = e.second;
 
     // ---- symbolic: row structures R_s (postorder = node order)
     const int ns = (int)S.sn.size();

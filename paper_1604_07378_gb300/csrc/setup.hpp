@@ -71,6 +71,7 @@ struct Setup {
     std::vector<double> dminv;       // T x 9, Dm^{-1} row-major
     std::vector<double> vol;         // T
     std::vector<double> mass;        // n lumped masses
+    std::vector<double> a0_diag;     // n_free: diagonal of A0 (the Jacobi preconditioner)
     std::vector<int> vt_ptr, vt_slot;  // vertex -> (tet*4 + corner), ascending tet
     // factor and solve operators
     std::vector<SupernodeHost> sn;

@@ -62,7 +62,7 @@ class Params(C.Structure):
                 ("precision", C.c_int32), ("leaf_size", C.c_int32), ("use_graph", C.c_int32),
                 ("tet_block", C.c_int32), ("ls_batch", C.c_int32), ("dyn_sweeps", C.c_int32),
                 ("n_colliders", C.c_int32), ("contact_scale", C.c_double),
-                ("colliders", Collider * MAX_COLLIDERS)]
+                ("colliders", Collider * MAX_COLLIDERS), ("a0_solver", C.c_int32), ("pcg_iters", C.c_int32)]
 
 
 class StepStats(C.Structure):
