@@ -30,6 +30,8 @@ taken by the CUDA path, written separately):
   * the iterative alternative to A0^{-1} (Sec. 8's comparison): Jacobi-
     preconditioned CG from zero with a fixed number of iterations, the three
     coordinate columns treated as one vector (one alpha, one beta);
+  * Alg. 3 (the Chebyshev direction) reads x_0 := x_1 (its first S
+    directions have omega = 1, where x_{k-1} cancels) and keeps no history;
   * collisions (Sec. 4.3) against analytic colliders (a plane with its
     normal, or a sphere the body stays outside of): at the start of every
     iteration, before the gradient at x_k, each free vertex that penetrates a
@@ -595,10 +597,23 @@ class StepStats:
     resets: int = 0                                # non-descent history resets
 
 
+def chebyshev_omega(k, S, rho, omega_k):
+    """omega_{k+1} of Alg. 3: 1 for k < S, 2/(2 - rho^2) at k = S,
+    4/(4 - rho^2 omega_k) after."""
+    if k < S:
+        return 1.0
+    if k == S:
+        return 2.0 / (2.0 - rho * rho)
+    return 4.0 / (4.0 - rho * rho * omega_k)
+
+
 def solve_step(P: Problem, q_cur, q_prev, iters=10, m=5, gamma=0.3, backtrack=0.5,
-               ls_max=30, return_iterates=False, pcg_iters=0):
+               ls_max=30, return_iterates=False, pcg_iters=0, chebyshev=None):
     """One implicit-Euler step by Alg. 1 with the direction of Alg. 2
-    (pcg_iters > 0: A0^{-1} by that many Jacobi-PCG iterations).
+    (pcg_iters > 0: A0^{-1} by that many Jacobi-PCG iterations).  With
+    chebyshev = (S, rho) the direction is Alg. 3's instead (no history):
+    q = -A0^{-1} grad, x_hat = x_k + q, d = omega (x_hat - x_{k-1}) + x_{k-1} - x_k
+    (x_0 read as x_1: the first S directions have omega = 1).
     Returns (x_{iters+1}, stats[, iterates])."""
     y = predictor(P, q_cur, q_prev)
     x = y.copy()                                   # x_1 := y
@@ -608,12 +623,19 @@ def solve_step(P: Problem, q_cur, q_prev, iters=10, m=5, gamma=0.3, backtrack=0.
     st = StepStats(g0=gx)
     history = []
     iterates = [x.copy()]
+    x_prev, omega = x.copy(), 1.0
     for it in range(iters):
         if P.colliders and it > 0:
             # the collision terms are updated at the start of the iteration,
             # before the gradient at x_k (Sec. 4.3); g(x_k) is re-evaluated with them
             gx = objective(P, x, y, col)
-        d = lbfgs_direction(P, grad, history, pcg_iters)
+        if chebyshev is not None:
+            S_c, rho_c = chebyshev
+            omega = chebyshev_omega(it + 1, S_c, rho_c, omega)
+            q = lbfgs_direction(P, grad, [], pcg_iters)
+            d = omega * ((x + q) - x_prev) + x_prev - x
+        else:
+            d = lbfgs_direction(P, grad, history, pcg_iters)
         gd = tr_dot(grad, d)
         if gd >= 0.0 and history:
             history = []
@@ -637,10 +659,11 @@ def solve_step(P: Problem, q_cur, q_prev, iters=10, m=5, gamma=0.3, backtrack=0.
         if P.colliders:
             col = contact_terms(P, x_new, q_cur)
         grad_new = gradient(P, x_new, y, col)
+        x_prev = x
         s = x_new - x
         t = grad_new - grad
         rho = tr_dot(t, s)
-        if rho > 1e-12 * np.linalg.norm(s) * np.linalg.norm(t):
+        if chebyshev is None and rho > 1e-12 * np.linalg.norm(s) * np.linalg.norm(t):
             history.append((s, t, rho))
             if len(history) > m:
                 history.pop(0)

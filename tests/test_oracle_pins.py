@@ -527,3 +527,42 @@ def test_pcg_step_runs_and_decreases_objective():
     gs = [st_p.g0] + st_p.g
     assert all(b < a for a, b in zip(gs, gs[1:]))
     assert np.linalg.norm(x_p - x_d) / np.linalg.norm(x_d) < 1e-3
+
+
+# ---------------------------------------------------------------- Chebyshev direction (Alg. 3) and Eq. RelativeError
+
+def test_chebyshev_weights_and_pd_limit():
+    """omega_{k+1} follows Alg. 3 and tends to the Chebyshev fixed point
+    2 / (1 + sqrt(1 - rho^2)); while omega = 1 (k < S) the direction is the
+    projective-dynamics one, -A0^{-1} grad (L-BFGS with m = 0)."""
+    rho, S = 0.95, 10
+    om = 1.0
+    for k in range(1, 200):
+        om = O.chebyshev_omega(k, S, rho, om)
+        if k < S:
+            assert om == 1.0
+        if k == S:
+            assert om == pytest.approx(2.0 / (2.0 - rho * rho))
+    assert om == pytest.approx(2.0 / (1.0 + math.sqrt(1.0 - rho * rho)), rel=1e-12)
+    w = W.spline_bar_80x40x40(scale=10)
+    P = O.problem_from_workload(w)
+    x_c, st_c = O.solve_step(P, w.q_cur, w.q_prev, iters=8, chebyshev=(S, rho))
+    x_p, st_p = O.solve_step(P, w.q_cur, w.q_prev, iters=8, m=0)
+    np.testing.assert_allclose(x_c, x_p, rtol=0, atol=1e-12 * np.abs(x_p).max())
+    assert st_c.trials == st_p.trials
+
+
+def test_relative_error_ordering_on_twisted_bar():
+    """Eq. RelativeError on the twisting spline bar, x* from a long L-BFGS
+    run: after 40 iterations Chebyshev (S = 10, rho = 0.99) beats projective
+    dynamics (m = 0) and L-BFGS with m = 5 beats both -- the ordering of the
+    paper's comparison of methods."""
+    w = W.spline_bar_80x40x40(scale=10)
+    P = O.problem_from_workload(w)
+    _, st_star = O.solve_step(P, w.q_cur, w.q_prev, iters=300, m=8)
+    g_star = min(st_star.g)
+    err = {}
+    for name, kw in (("pd", dict(m=0)), ("cheb", dict(m=0, chebyshev=(10, 0.99))), ("lbfgs5", dict(m=5))):
+        _, st = O.solve_step(P, w.q_cur, w.q_prev, iters=40, **kw)
+        err[name] = O.relative_error(st.g[-1], st.g0, g_star)
+    assert 0.0 <= err["lbfgs5"] < err["cheb"] < err["pd"] < 1.0, err
