@@ -316,6 +316,8 @@ def run_ours(args, rank, world, dist):
         line["collisions"] = run_collisions(args, stream)
     if not args.no_pcg:
         line["a0_pcg"] = run_pcg(args, stream, x32)
+    if not args.no_convergence:
+        line["convergence"] = run_convergence(args, stream)
     if rank == 0 and not args.no_cpu_baseline:
         v, te, desc, cores = oracle_sample(w, budget_s=args.cpu_budget, counts=(trials, iters))
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -358,6 +360,48 @@ def run_pcg(args, stream, x_direct):
         out[f"pcg{iters}"] = {"steps_per_s": 1e3 / ms, "ms_per_step": ms, "solve_ms": solve_ms, "status": rc,
                               "ls_trials_per_iter": st["trials_total"] / max(1, st["iters_total"]),
                               "pos_err_vs_direct_one_step": ex}
+    return out
+
+
+def run_convergence(args, stream):
+    """Eq. RelativeError of one frame of the twisting spline bar (80x40x40 at
+    half resolution, 96,000 tets, FP64): (g(x_k) - g(x*)) / (g(x_0) - g(x*))
+    after 10, 30 and 60 iterations for projective dynamics (m = 0), L-BFGS
+    with m = 2, 5, 8, 16 and the Chebyshev direction (S = 10, rho = 0.99),
+    with the time per iteration; x* is a 500-iteration L-BFGS (m = 16) run
+    (the paper's Newton reference is not built on the GPU)."""
+    import torch
+
+    from paper_1604_07378_gb300 import hqn
+    from paper_1604_07378_gb300 import workloads as W
+
+    w = W.spline_bar_80x40x40(scale=2)
+
+    def run(iters, **kw):
+        sim = hqn.Sim.from_workload(w, precision=hqn.FP64_PLAIN, stream=stream.cuda_stream, iters=iters, **kw)
+        sim.set_state(w.q_cur, w.q_prev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st = sim.step(1, stats=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        sim.close()
+        return st, dt
+
+    st_star, _ = run(500, history_m=16)
+    gs = st_star["g"]  # the step ends early once the line search can no longer decrease g
+    g_star = min(gs)
+    out = {"workload": "splinebar40x20x20_twist90", "tets": w.n_tets, "precision": "f64",
+           "g_star_reference": "min g of an L-BFGS (m = 16) step of up to 500 iterations",
+           "g_star_iterations": len(gs), "g_star_status": st_star["status"], "methods": {}}
+    for name, kw in (("pd_m0", dict(history_m=0)), ("lbfgs_m2", dict(history_m=2)),
+                     ("lbfgs_m5", dict(history_m=5)), ("lbfgs_m8", dict(history_m=8)),
+                     ("chebyshev_S10_rho0.99", dict(direction=1, cheb_S=10, cheb_rho=0.99))):
+        st, dt = run(60, **kw)
+        g = st["g"][:60]
+        rel_err = {str(k): (g[k - 1] - g_star) / (st["g0"] - g_star) for k in (10, 30, 60)}
+        out["methods"][name] = {"relative_error": rel_err, "ms_per_iteration": 1e3 * dt / 60,
+                                "ls_trials_per_iter": st["trials_total"] / max(1, st["iters_total"])}
     return out
 
 
@@ -483,6 +527,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 512-simulation measurement")
     ap.add_argument("--no-collisions", action="store_true", help="skip the collision measurement")
     ap.add_argument("--no-pcg", action="store_true", help="skip the Jacobi-PCG measurement")
+    ap.add_argument("--no-convergence", action="store_true", help="skip the relative-error measurement")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--leaf-size", type=int, default=0,
                     help="max vertices of a nested-dissection leaf (0 = the library default)")

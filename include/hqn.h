@@ -160,10 +160,18 @@ typedef struct {
      * vector).  sim_solve_A0 then returns that approximation. */
     int32_t a0_solver;
     int32_t pcg_iters;    /* >= 1 when a0_solver = 1 (default 15)                  */
+    /* The descent direction: 0 = L-BFGS (Alg. 2, default); 1 = the Chebyshev
+     * semi-iterative direction of Alg. 3 with cheb_S and cheb_rho (no history;
+     * history_m is ignored): q = -A0^{-1} grad, d = omega (x_k + q - x_{k-1})
+     * + x_{k-1} - x_k, omega = 1 for k < S, 2/(2 - rho^2) at k = S,
+     * 4/(4 - rho^2 omega_k) after; x_0 is read as x_1. */
+    int32_t direction;
+    int32_t cheb_S;       /* default 10                                            */
+    double  cheb_rho;     /* spectral radius estimate in (0, 1) (default 0.99)     */
 } hqn_params;
 
 #define HQN_MAX_HISTORY 16
-#define HQN_MAX_ITERS   64
+#define HQN_MAX_ITERS   512
 
 /* Per-step record of the most recent step taken by sim_step. */
 typedef struct {

@@ -125,9 +125,10 @@ struct Sim final : SimBase {
 
     int init(const hqn_params &p, cudaStream_t stream) {
         prm = p;
+        if (prm.direction == 1) prm.history_m = 0;  // the Chebyshev direction keeps no history
         st = stream;
         ns = (int)S.size();
-        const int m = p.history_m;
+        const int m = prm.history_m;
         int max_ld = 0;
         for (const Setup &s : S) max_ld = std::max(max_ld, s.max_ld);
         if (!solve_smem_limit_ok<R>(max_ld))
@@ -214,6 +215,7 @@ struct Sim final : SimBase {
         if ((rc = alloc(ds.S, ring))) return rc;
         if ((rc = alloc(ds.Tt, ring))) return rc;
         if ((rc = alloc(ds.corner, (size_t)4 * T))) return rc;
+        if (p.direction == 1 && (rc = alloc(ds.xprev, n))) return rc;
         if (p.a0_solver == 1) {
             V4<R> **pv[] = {&ds.pcg_r, &ds.pcg_z, &ds.pcg_p, &ds.pcg_ap};
             for (auto v : pv)
@@ -253,6 +255,9 @@ struct Sim final : SimBase {
             c.gamma = p.gamma;
             c.backtrack = p.backtrack;
             c.kstiff = (R)s.k;
+            c.cheb = p.direction == 1 ? 1 : 0;
+            c.cheb_S = p.cheb_S;
+            c.cheb_rho2 = p.cheb_rho * p.cheb_rho;
             c.ncol = p.n_colliders;
             c.cscale = (R)p.contact_scale;
             for (int q = 0; q < p.n_colliders; ++q) {
@@ -1355,6 +1360,9 @@ int create_any(int count, const hqn_mesh *meshes, const hqn_material *materials,
     if (count <= 0 || !meshes || !materials || !params) return fail(HQN_ERR_ARG, "null argument or empty batch");
     if (params->precision != HQN_FP32_MIXED && params->precision != HQN_FP64_PLAIN)
         return fail(HQN_ERR_ARG, "unknown precision");
+    if (params->direction != 0 && params->direction != 1) return fail(HQN_ERR_ARG, "unknown direction");
+    if (params->direction == 1 && !(params->cheb_rho > 0.0 && params->cheb_rho < 1.0 && params->cheb_S >= 0))
+        return fail(HQN_ERR_ARG, "Chebyshev direction needs 0 < cheb_rho < 1 and cheb_S >= 0");
     if (params->a0_solver != 0 && params->a0_solver != 1) return fail(HQN_ERR_ARG, "unknown a0_solver");
     if (params->a0_solver == 1 && (params->pcg_iters < 1 || params->pcg_iters > 1000))
         return fail(HQN_ERR_ARG, "pcg_iters must be in [1, 1000]");
@@ -1421,6 +1429,9 @@ void hqn_default_params(hqn_params *p) {
     p->contact_scale = 100.0;
     p->a0_solver = 0;
     p->pcg_iters = 15;
+    p->direction = 0;
+    p->cheb_S = 10;
+    p->cheb_rho = 0.99;
 }
 
 int sim_create(const hqn_mesh *mesh, const hqn_material *material, const hqn_params *params, void *stream,

@@ -54,6 +54,7 @@ struct Ctl {
     double g0;         // g(x_1), x_1 = y
     double ls_a[3];    // inertia term along d: I(alpha) = a0 + a1 alpha + a2 alpha^2
     double pcg_rz, pcg_alpha, pcg_beta;  // Jacobi-PCG scalars (iterative A0^{-1})
+    double cheb_omega; // Chebyshev weight omega_k of Alg. 3
     double zeta[HQN_MAX_HISTORY + 1];  // first-loop coefficients by age (0 = newest)
     double coef[HQN_MAX_HISTORY + 1];  // second-loop coefficients zeta - eta by age
     double rho[HQN_MAX_HISTORY + 1];   // tr(t^T s) by ring slot
@@ -107,6 +108,8 @@ struct StepConst {
     R gx, gy, gz;      // h^2 * gravity (the h^2 M^{-1} f_ext term of Eq. PD)
     double gamma, backtrack;
     R kstiff;          // the stiffness k of Eq. stiffness (the matrix-free L of A0)
+    int cheb, cheb_S;  // the Chebyshev direction of Alg. 3 (cheb = 1) and its S
+    double cheb_rho2;  // rho^2
     int ncol;          // colliders (0: no collision terms)
     R cscale;          // collision weight w_v = cscale * m_v / h^2
     ColDev<R> col[HQN_MAX_COLLIDERS];

@@ -115,12 +115,14 @@ __global__ void __launch_bounds__(VBS) k_predict(DevSim<R> s) {
         s.y[g] = yy;
         s.xk[g] = yy;
         s.xt[g] = yy;
+        if (D.c.cheb) s.xprev[g] = yy;  // x_0 read as x_1 (Alg. 3)
     }
     if (blockIdx.x == D.vb0 && threadIdx.x == 0) {
         Ctl *c = D.ctl;
         c->k = 0; c->trials = 0; c->count = 0; c->head = 0; c->stop = 0;
         c->status = HQN_OK; c->accepted = 0; c->nondescent = 0; c->alpha = 1.0; c->grad_ready = 0;
         c->active = 0;
+        c->cheb_omega = 1.0;
     }
 }
 
@@ -589,6 +591,7 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
                     dr[2 + 2 * MP1 + a] = dotr(sa, gn);
                 }
             }
+            if (D.c.cheb) s.xprev[gi] = xk;  // x_{k-1} of the next direction (Alg. 3)
             s.xk[gi] = x;
         }
         s.gk[gi] = gn;
@@ -767,7 +770,15 @@ __global__ void __launch_bounds__(VBS) k_r0_dots(DevSim<R> s) {
     for (int p = threadIdx.x; p < count; p += VBS) ctl->coef[p] = hs.coef[p];
 }
 
-// d = r0 + sum_p c_p s_p; then gd = tr(grad_k^T d) -- with history and
+// omega_{k+1} of Alg. 3 from omega_k (k: the 1-based index of x_k).
+template <typename R>
+__device__ __forceinline__ double cheb_omega_next(const StepConst<R> &c, int k, double omega_k) {
+    if (k < c.cheb_S) return 1.0;
+    if (k == c.cheb_S) return 2.0 / (2.0 - c.cheb_rho2);
+    return 4.0 / (4.0 - c.cheb_rho2 * omega_k);
+}
+
+// d = r0 + sum_p c_p s_p (or Alg. 3's Chebyshev direction); then gd = tr(grad_k^T d) -- with history and
 // gd >= 0 the direction is not a descent direction: flag it so the history is
 // dropped (h.nd: any simulation flagged) -- and the coefficients of the
 // inertia term along the ray x_k + alpha d:
@@ -807,7 +818,15 @@ __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, i
             Xr = s.rest[gi];
             ul = s.u_cur[gi];
         }
-        if (count > 0) s.d[gi] = dd;
+        if (D.c.cheb) {
+            // Alg. 3: d = omega (x_k + q - x_{k-1}) + x_{k-1} - x_k with q = r0 (no history)
+            const R om = (R)cheb_omega_next(D.c, ctl->k, ctl->cheb_omega);
+            const V4<R> xp = s.xprev[gi];
+            dd.x = om * ((x.x + dd.x) - xp.x) + xp.x - x.x;
+            dd.y = om * ((x.y + dd.y) - xp.y) + xp.y - x.y;
+            dd.z = om * ((x.z + dd.z) - xp.z) + xp.z - x.z;
+        }
+        if (count > 0 || D.c.cheb) s.d[gi] = dd;
         const R rx = x.x - yy.x, ry = x.y - yy.y, rz = x.z - yy.z;
         d4[0] = dotr(g, dd);
         d4[1] = R(0.5) * mh * (rx * rx + ry * ry + rz * rz);
@@ -843,6 +862,7 @@ __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, i
     }
     if (threadIdx.x == 0) {
         ctl->ticket[TK_VEC] = 0u;
+        if (act && D.c.cheb) ctl->cheb_omega = cheb_omega_next(D.c, ctl->k, ctl->cheb_omega);
         if (act) {
             ctl->gd = tot[0];
             ctl->ls_a[0] = tot[1];

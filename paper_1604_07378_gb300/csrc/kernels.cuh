@@ -50,6 +50,7 @@ struct DevSim {
     // Jacobi-PCG in lieu of A0^{-1} (iterative solver): residual, preconditioned
     // residual, search direction, A0 p and the inverse diagonal of A0 (free vertices)
     V4<R> *pcg_r, *pcg_z, *pcg_p, *pcg_ap;
+    V4<R> *xprev;               // x_{k-1} (the Chebyshev direction of Alg. 3)
     const R *pcg_dinv;
     // per-block partial sums: part_x[k * (blocks of the kernel) + block]
     double *part_in, *part_el, *part_g, *part_v, *part_ls;

@@ -28,7 +28,7 @@ STATIC_MAX_TETS, STATIC_MAX_VERTS = 65536, 262144
 NEOHOOKEAN, STVK, SPLINE_VL, COROTATED, POLY4 = 0, 1, 2, 3, 4
 STAGE_TET, STAGE_GATHER, STAGE_SOLVE, STAGE_LS_PASS, STAGE_TWO_LOOP = 0, 1, 2, 3, 4
 FP64_PLAIN, FP32_MIXED = 0, 1
-MAX_HISTORY, MAX_ITERS = 16, 64
+MAX_HISTORY, MAX_ITERS = 16, 512
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -62,7 +62,8 @@ class Params(C.Structure):
                 ("precision", C.c_int32), ("leaf_size", C.c_int32), ("use_graph", C.c_int32),
                 ("tet_block", C.c_int32), ("ls_batch", C.c_int32), ("dyn_sweeps", C.c_int32),
                 ("n_colliders", C.c_int32), ("contact_scale", C.c_double),
-                ("colliders", Collider * MAX_COLLIDERS), ("a0_solver", C.c_int32), ("pcg_iters", C.c_int32)]
+                ("colliders", Collider * MAX_COLLIDERS), ("a0_solver", C.c_int32), ("pcg_iters", C.c_int32),
+                ("direction", C.c_int32), ("cheb_S", C.c_int32), ("cheb_rho", C.c_double)]
 
 
 class StepStats(C.Structure):

@@ -52,3 +52,23 @@ def test_step_with_pcg_matches_oracle(w, prec):
     assert rel(x, x_ref) <= (1e-9 if prec == FP64 else 1e-4), rel(x, x_ref)
     if prec == FP64:
         assert stats["trials"] == st.trials
+
+
+# ---------------------------------------------------------------- Chebyshev direction (Alg. 3)
+
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_chebyshev_step_matches_oracle(prec):
+    """30 iterations on the twisting spline bar with the Chebyshev direction
+    (S = 10, rho = 0.99): the acceleration is active for the last 20."""
+    w = W.spline_bar_80x40x40(scale=10)
+    P = problem_for(w)
+    x_ref, st = O.solve_step(P, w.q_cur, w.q_prev, iters=30, chebyshev=(10, 0.99))
+    with sim_for(w, prec, use_graph=1, iters=30, direction=1, cheb_S=10, cheb_rho=0.99) as sim:
+        sim.set_state(w.q_cur, w.q_prev)
+        rc, stats = sim.step(1, stats=True)
+        x, _ = sim.get_state()
+    assert rc >= 0
+    assert rel(x, x_ref) <= (1e-9 if prec == FP64 else 1e-4), rel(x, x_ref)
+    if prec == FP64:
+        assert stats["trials"][:30] == st.trials
+        np.testing.assert_allclose(stats["g"][:30], st.g, rtol=1e-10)
