@@ -311,7 +311,7 @@ def run_ours(args, rank, world, dist):
     launches = args.steps * 5 + stats["iters_total"] * per_iter + stats["ls_passes_total"]
     line["gpu_launches"] = launches
     if not args.no_batch:
-        line["batched"] = run_batched(args, stream)
+        line["batched"] = run_batched(args, stream, rank, world, dist)
     if not args.no_collisions:
         line["collisions"] = run_collisions(args, stream)
     if not args.no_pcg:
@@ -435,20 +435,31 @@ def run_collisions(args, stream):
             "min_height_m": float(x[:, 2].min())}
 
 
-def run_batched(args, stream):
+def shard_batch(items, rank, world):
+    """The simulations rank `rank` of `world` advances: a round-robin share,
+    so every rank gets the same mix of sizes and materials.  Independent
+    simulations need no data exchange between ranks."""
+    return list(items[rank::world])
+
+
+def run_batched(args, stream, rank=0, world=1, dist=None):
     """The batched form: 512 independent simulations (lattices of random
     dims 4-24 per axis, Neo-Hookean / StVK / spline materials, E log-uniform
     1e4-1e6, nu U[0.3, 0.48]) advanced together, one launch per kernel stage,
-    one CUDA graph per step; FP32-mixed with the FP64-plain batch beside it."""
+    one CUDA graph per step; FP32-mixed with the FP64-plain batch beside it.
+    With several ranks the 512 simulations are sharded across them (no
+    collective on the data path); simulation-steps/s counts all ranks'
+    simulations over the slowest rank's time."""
     import torch
 
     from paper_1604_07378_gb300 import hqn
     from paper_1604_07378_gb300 import workloads as W
 
-    ws = W.batch_512()
+    all_ws = W.batch_512()
+    ws = shard_batch(all_ws, rank, world)
     T = sum(w.n_tets for w in ws)
-    out = {"workload": "batch512_lattices_4to24", "sims": len(ws), "tets_total": T,
-           "vertices_total": sum(w.n_verts for w in ws)}
+    out = {"workload": "batch512_lattices_4to24", "sims": len(all_ws), "sims_per_rank": len(ws), "ranks": world,
+           "tets_total": sum(w.n_tets for w in all_ws), "vertices_total": sum(w.n_verts for w in all_ws)}
     for prec, key, steps in ((hqn.FP32_MIXED, "fp32_mixed", args.batch_steps),
                              (hqn.FP64_PLAIN, "fp64_plain", max(2, args.batch_steps // 4))):
         t0 = time.perf_counter()
@@ -463,7 +474,7 @@ def run_batched(args, stream):
         rc, tot = b.step(steps)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, torch.device("cuda", torch.cuda.current_device())) / steps
         info = b.info()
         solve_ms = b.time_stage(hqn.STAGE_SOLVE, 10)
         b.close()
@@ -473,7 +484,7 @@ def run_batched(args, stream):
         evals = T * (tot["ls_passes_total"] / (steps * len(ws)) + 1)
         solve_bytes = 2 * info["factor_nnz"] * (4 if prec == hqn.FP32_MIXED else 8)
         peaks, _ = _peaks()
-        out[key] = {"batch_steps_per_s": 1e3 / ms, "sim_steps_per_s": len(ws) * 1e3 / ms, "ms_per_step": ms,
+        out[key] = {"batch_steps_per_s": 1e3 / ms, "sim_steps_per_s": len(all_ws) * 1e3 / ms, "ms_per_step": ms,
                     "tet_grad_evals_per_s": evals * 1e3 / ms, "steps": steps, "status": rc,
                     "ls_trials_per_iter": tot["trials_total"] / max(tot["iters_total"], 1),
                     "create_s": create_s, "device_bytes": info["device_bytes"],

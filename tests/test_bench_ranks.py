@@ -48,3 +48,13 @@ def test_single_process_is_identity():
 
     assert bench.max_over_ranks(12.5, None) == 12.5
     assert bench.job_throughput(1, 100, 250.0) == pytest.approx(400.0)
+
+
+def test_batch_shards_cover_every_simulation_once():
+    import bench
+
+    items = list(range(512))
+    for world in (1, 2, 3, 8):
+        shards = [bench.shard_batch(items, r, world) for r in range(world)]
+        assert sorted(x for sh in shards for x in sh) == items
+        assert max(map(len, shards)) - min(map(len, shards)) <= 1
