@@ -318,6 +318,8 @@ def run_ours(args, rank, world, dist):
         line["a0_pcg"] = run_pcg(args, stream, x32)
     if not args.no_convergence:
         line["convergence"] = run_convergence(args, stream)
+    if not args.no_configs:
+        line["other_configs"] = run_other_configs(args, stream)
     if rank == 0 and not args.no_cpu_baseline:
         v, te, desc, cores = oracle_sample(w, budget_s=args.cpu_budget, counts=(trials, iters))
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -360,6 +362,60 @@ def run_pcg(args, stream, x_direct):
         out[f"pcg{iters}"] = {"steps_per_s": 1e3 / ms, "ms_per_step": ms, "solve_ms": solve_ms, "status": rc,
                               "ls_trials_per_iter": st["trials_total"] / max(1, st["iters_total"]),
                               "pos_err_vs_direct_one_step": ex}
+    return out
+
+
+def run_other_configs(args, stream):
+    """The other single-mesh workloads, FP32-mixed, one graph per step:
+    the twisting spline bar (80x40x40, 768,000 tets, 10 iterations, m = 5)
+    and the large bar (48x48x192, 2,654,208 tets, 20 iterations, m = 8) with
+    one FP64-plain step beside it for the position difference."""
+    import torch
+
+    from paper_1604_07378_gb300 import hqn
+    from paper_1604_07378_gb300 import workloads as W
+
+    out = {}
+    for key, w, steps in (("splinebar80x40x40", W.spline_bar_80x40x40(), 10),
+                          ("largebar48x48x192", W.large_48x48x192(), 5)):
+        t0 = time.perf_counter()
+        sim = hqn.Sim.from_workload(w, precision=hqn.FP32_MIXED, stream=stream.cuda_stream,
+                                    dyn_sweeps=SWEEPS[args.sweeps], leaf_size=args.leaf_size)
+        create_s = time.perf_counter() - t0
+        sim.set_state(w.q_cur, w.q_prev)
+        sim.step(1)
+        x32, _ = sim.get_state()
+        sim.set_state(w.q_cur, w.q_prev)
+        sim.step(2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, st = sim.step(steps, stats=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        solve_ms = sim.time_stage(hqn.STAGE_SOLVE, 5)
+        info = sim.info()
+        sim.close()
+        entry = {"tets": w.n_tets, "vertices": w.n_verts, "iters": w.iters, "history_m": w.history,
+                 "steps_per_s": 1e3 / ms, "ms_per_step": ms, "steps": steps, "status": rc,
+                 "tet_grad_evals_per_s": w.n_tets * (st["trials_total"] + steps) / steps * 1e3 / ms,
+                 "ls_trials_per_iter": st["trials_total"] / max(1, st["iters_total"]),
+                 "solve_ms": solve_ms, "factor_nnz": info["factor_nnz"], "create_s": create_s}
+        if key.startswith("large"):
+            sim64 = hqn.Sim.from_workload(w, precision=hqn.FP64_PLAIN, stream=stream.cuda_stream)
+            sim64.set_state(w.q_cur, w.q_prev)
+            torch.cuda.synchronize()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            sim64.step(1)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            x64, _ = sim64.get_state()
+            sim64.close()
+            entry["fp64_plain_steps_per_s"] = 1e3 / g0.elapsed_time(g1)
+            entry["pos_err_fp32_vs_fp64_gpu"] = float(np.linalg.norm(x32 - x64) / np.linalg.norm(x64))
+        out[key] = entry
     return out
 
 
@@ -539,6 +595,8 @@ def main():
     ap.add_argument("--no-collisions", action="store_true", help="skip the collision measurement")
     ap.add_argument("--no-pcg", action="store_true", help="skip the Jacobi-PCG measurement")
     ap.add_argument("--no-convergence", action="store_true", help="skip the relative-error measurement")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the spline-bar and large-bar measurements")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--leaf-size", type=int, default=0,
                     help="max vertices of a nested-dissection leaf (0 = the library default)")

@@ -64,10 +64,10 @@ __device__ __forceinline__ void batch_condition(const DevSim<R> &s, int slot, un
     if (threadIdx.x == 0) {
         __threadfence();
         last_sim = atomicAdd(&s.batch_ticket[slot], 1u) == (unsigned)s.nsims - 1u;
+        if (last_sim) __threadfence();  // acquire, ordered for the block by the barrier
     }
     __syncthreads();
     if (!last_sim) return;
-    __threadfence();
     int any = 0;
     for (int k = threadIdx.x; k < s.nsims; k += blockDim.x) any |= pred((const volatile Ctl *)s.desc[k].ctl) ? 1 : 0;
     any = __syncthreads_or(any);
@@ -79,16 +79,18 @@ __device__ __forceinline__ void batch_condition(const DevSim<R> &s, int slot, un
 
 // Per-simulation grid reduction: the block's partials at
 // part[k * stride + block]; true in every thread of the simulation's last block.
-template <int NV>
+template <typename R, int NV>
 __device__ __forceinline__ bool sim_arrive(const double (&v)[NV], double *part, int stride, int nblocks,
                                            unsigned int *ticket) {
     __shared__ bool last;
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k) part[k * stride + blockIdx.x] = v[k];
-        __threadfence();
+        for (int k = 0; k < NV; ++k) Part<R>::put(part + k * stride + blockIdx.x, v[k]);
+        __threadfence();  // release: the partials before the ticket
         const unsigned int t = atomicAdd(ticket, 1u);
         last = (t == (unsigned)nblocks - 1u);
+        if (last) __threadfence();  // acquire: every block's partials, ordered for the
+                                    // whole block by the barrier below
     }
     __syncthreads();
     return last;
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(VBS) k_inertia(DevSim<R> s) {
     }
     double tot[1];
     block_sum_exact<VBS, 1, R>(e, tot);
-    if (threadIdx.x == 0) s.part_in[blockIdx.x] = tot[0];
+    if (threadIdx.x == 0) Part<R>::put(s.part_in + blockIdx.x, tot[0]);
 }
 
 // x_k + alpha d, rounded the same way wherever the accepted point is formed.
@@ -209,13 +211,24 @@ __device__ __forceinline__ void edge_diffs(const V4<R> &x0, const V4<R> &x1, con
     du[2][0] = x3.x - x0.x; du[2][1] = x3.y - x0.y; du[2][2] = x3.z - x0.z;
 }
 
-// Sum of the simulation's per-block partials part[b], b in [b0, b0 + nb), by
-// its last block (fixed order, float64); result valid in thread 0.
-template <int BS>
+// Sum of the simulation's per-block partials part[b], b in [b0, b0 + nb)
+// (stored by Part<R>::put), by its last block in a fixed order; result valid
+// in thread 0.
+template <typename R, int BS>
 __device__ __forceinline__ double sum_block_range(const double *part, int b0, int nb) {
-    double acc[1] = {strided_sum(part + b0, threadIdx.x, nb, BS)};
-    block_sum<BS, 1>(acc);
-    return acc[0];
+    using P = Part<R>;
+    __shared__ typename P::T sh[BS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    typename P::T v = part_warp_sum<R>(part_strided_sum<R>(part + b0, threadIdx.x, nb, BS));
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double out = 0.0;
+    if (warp == 0) {
+        typename P::T t = lane < BS / 32 ? sh[lane] : P::zero();
+        out = P::to_double(part_warp_sum<R>(t));
+    }
+    __syncthreads();
+    return out;
 }
 
 // ---------------------------------------------------------------- tet kernel
@@ -275,8 +288,8 @@ __global__ void __launch_bounds__(TBS, 8) k_tet(DevSim<R> s, int mode, CondHandl
     if (grad_mode) return;
     double tot[1];
     block_sum_exact<TBS, 1, R>(e, tot);
-    if (!sim_arrive<1>(tot, s.part_el, 0, D.ntb, &c->ticket[TK_TET])) return;
-    const double el = sum_block_range<TBS>(s.part_el, D.tb0, D.ntb);
+    if (!sim_arrive<R, 1>(tot, s.part_el, 0, D.ntb, &c->ticket[TK_TET])) return;
+    const double el = sum_block_range<R, TBS>(s.part_el, D.tb0, D.ntb);
     if (mode == TET_TRIAL1) {
         if (threadIdx.x == 0) {
             c->ticket[TK_TET] = 0u;
@@ -307,7 +320,7 @@ __global__ void __launch_bounds__(TBS, 8) k_tet(DevSim<R> s, int mode, CondHandl
                         [](const volatile Ctl *x) { return x->active && !x->accepted && !x->stop; });
         return;
     }
-    const double in = sum_block_range<TBS>(s.part_in, D.vb0, D.nvb);
+    const double in = sum_block_range<R, TBS>(s.part_in, D.vb0, D.nvb);
     if (threadIdx.x != 0) return;
     c->ticket[TK_TET] = 0u;
     const double g = el + in;
@@ -366,18 +379,11 @@ __global__ void __launch_bounds__(TBS) k_ls(DevSim<R> s, CondHandles h) {
     }
     double tot[K];
     block_sum_exact<TBS, K, R>(e, tot);
-    if (!sim_arrive<K>(tot, s.part_ls, s.ntb, D.ntb, &ctl->ticket[TK_LS])) return;
+    if (!sim_arrive<R, K>(tot, s.part_ls, s.ntb, D.ntb, &ctl->ticket[TK_LS])) return;
     {
         // the simulation's partials, one warp per trial
         __shared__ double sh[K];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        __threadfence();
-        for (int j = warp; j < K; j += TBS / 32) {
-            double acc = 0.0;
-            acc = strided_sum(s.part_ls + (size_t)j * s.ntb + D.tb0, lane, D.ntb, 32);
-            acc = warp_sum(acc);
-            if (lane == 0) sh[j] = acc;
-        }
+        warp_value_sums<R, K, TBS / 32>(s.part_ls + D.tb0, (size_t)s.ntb, D.ntb, sh);
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < K; ++j) tot[j] = sh[j];
@@ -452,7 +458,7 @@ __device__ __forceinline__ R dotr(const V4<R> &a, const V4<R> &b) {
 constexpr int MH = HQN_MAX_HISTORY + 1;
 struct HistSmem {
     double gram[MH][MH];  // s_a^T t_b by ring slots
-    double rho[MH], sg[MH], tr0[MH], zeta[MH], coef[MH];
+    double rho[MH], rinv[MH], sg[MH], tr0[MH], zeta[MH], coef[MH];  // rinv = 1 / rho
     int count, head;
 };
 
@@ -463,6 +469,7 @@ __device__ __forceinline__ void hist_load(const Ctl *c, HistSmem &h, int m) {
     for (int e = threadIdx.x; e < m1 * m1; e += blockDim.x) h.gram[e / m1][e % m1] = c->gram[e / m1][e % m1];
     for (int a = threadIdx.x; a < m1; a += blockDim.x) {
         h.rho[a] = c->rho[a];
+        h.rinv[a] = 1.0 / c->rho[a];  // the recursions multiply (one division per slot, in parallel)
         h.zeta[a] = c->zeta[a];
     }
     if (threadIdx.x == 0) {
@@ -478,7 +485,7 @@ __device__ __forceinline__ void zeta_recursion(HistSmem &h, int m) {
         const int sl = ring_slot(h.head, p, m);
         double sq = -h.sg[sl];
         for (int pp = 0; pp < p; ++pp) sq -= h.zeta[pp] * h.gram[sl][ring_slot(h.head, pp, m)];
-        h.zeta[p] = sq / h.rho[sl];
+        h.zeta[p] = sq * h.rinv[sl];
     }
 }
 
@@ -488,7 +495,7 @@ __device__ __forceinline__ void coef_recursion(HistSmem &h, int m) {
         const int sl = ring_slot(h.head, p, m);
         double tr = h.tr0[sl];
         for (int pp = p + 1; pp < h.count; ++pp) tr += h.coef[pp] * h.gram[ring_slot(h.head, pp, m)][sl];
-        h.coef[p] = h.zeta[p] - tr / h.rho[sl];
+        h.coef[p] = h.zeta[p] - tr * h.rinv[sl];
     }
 }
 
@@ -606,20 +613,13 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
 #pragma unroll
         for (int k = 0; k < NG; ++k) dots[1 + k] = mixed[k];
     }
-    if (!sim_arrive<ND>(dots, s.part_g, s.nvb, D.nvb, &ctl->ticket[TK_GATHER])) return;
+    if (!sim_arrive<R, ND>(dots, s.part_g, s.nvb, D.nvb, &ctl->ticket[TK_GATHER])) return;
     __shared__ int keep;
     if (push) {
         {
             // the simulation's partials, one warp per value
             __shared__ double sh[ND];
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            __threadfence();
-            for (int k = warp; k < ND; k += VBS / 32) {
-                double acc = 0.0;
-                acc = strided_sum(s.part_g + (size_t)k * s.nvb + D.vb0, lane, D.nvb, 32);
-                acc = warp_sum(acc);
-                if (lane == 0) sh[k] = acc;
-            }
+            warp_value_sums<R, ND, VBS / 32>(s.part_g + D.vb0, (size_t)s.nvb, D.nvb, sh);
             __syncthreads();
 #pragma unroll
             for (int k = 0; k < ND; ++k) dots[k] = sh[k];
@@ -632,6 +632,7 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
             if (keep) {
                 hs.head = w;
                 hs.rho[w] = dots[0];
+                hs.rinv[w] = 1.0 / dots[0];
                 hs.count = hs.count < m ? hs.count + 1 : m;
 #pragma unroll
                 for (int a = 0; a < MP1; ++a)
@@ -742,17 +743,10 @@ __global__ void __launch_bounds__(VBS) k_r0_dots(DevSim<R> s) {
     }
     double dots[MP1];
     block_sum_r<VBS, MP1, R>(dr, dots);
-    if (!sim_arrive<MP1>(dots, s.part_v, s.nvb, D.nvb, &ctl->ticket[TK_VEC])) return;
+    if (!sim_arrive<R, MP1>(dots, s.part_v, s.nvb, D.nvb, &ctl->ticket[TK_VEC])) return;
     {
         __shared__ double sh[MP1];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        __threadfence();
-        for (int k = warp; k < MP1; k += VBS / 32) {
-            double acc = 0.0;
-            acc = strided_sum(s.part_v + (size_t)k * s.nvb + D.vb0, lane, D.nvb, 32);
-            acc = warp_sum(acc);
-            if (lane == 0) sh[k] = acc;
-        }
+        warp_value_sums<R, MP1, VBS / 32>(s.part_v + D.vb0, (size_t)s.nvb, D.nvb, sh);
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < MP1; ++k) dots[k] = sh[k];
@@ -845,17 +839,10 @@ __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, i
     }
     double tot[4];
     block_sum_r<VBS, 4, R>(d4, tot);
-    if (!sim_arrive<4>(tot, s.part_v, s.nvb, D.nvb, &ctl->ticket[TK_VEC])) return;
+    if (!sim_arrive<R, 4>(tot, s.part_v, s.nvb, D.nvb, &ctl->ticket[TK_VEC])) return;
     {
         __shared__ double sh[4];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        __threadfence();
-        if (warp < 4) {
-            double acc = 0.0;
-            acc = strided_sum(s.part_v + (size_t)warp * s.nvb + D.vb0, lane, D.nvb, 32);
-            acc = warp_sum(acc);
-            if (lane == 0) sh[warp] = acc;
-        }
+        warp_value_sums<R, 4, VBS / 32>(s.part_v + D.vb0, (size_t)s.nvb, D.nvb, sh);
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < 4; ++k) tot[k] = sh[k];
@@ -920,9 +907,8 @@ __global__ void __launch_bounds__(VBS) k_pcg_init(DevSim<R> s, const V4<R> *q, V
     }
     double tot[1];
     block_sum_r<VBS, 1, R>(dr, tot);
-    if (!sim_arrive<1>(tot, s.part_v, s.nvb, D.nvb, &ctl->ticket[TK_PCG_B])) return;
-    __threadfence();
-    const double rz = sum_block_range<VBS>(s.part_v, D.vb0, D.nvb);
+    if (!sim_arrive<R, 1>(tot, s.part_v, s.nvb, D.nvb, &ctl->ticket[TK_PCG_B])) return;
+    const double rz = sum_block_range<R, VBS>(s.part_v, D.vb0, D.nvb);
     if (threadIdx.x == 0) {
         ctl->ticket[TK_PCG_B] = 0u;
         ctl->pcg_rz = rz;
@@ -990,9 +976,8 @@ __global__ void __launch_bounds__(VBS) k_pcg_gather(DevSim<R> s) {
     }
     double tot[1];
     block_sum_r<VBS, 1, R>(dr, tot);
-    if (!sim_arrive<1>(tot, s.part_v, s.nvb, D.nvb, &ctl->ticket[TK_PCG_A])) return;
-    __threadfence();
-    const double pap = sum_block_range<VBS>(s.part_v, D.vb0, D.nvb);
+    if (!sim_arrive<R, 1>(tot, s.part_v, s.nvb, D.nvb, &ctl->ticket[TK_PCG_A])) return;
+    const double pap = sum_block_range<R, VBS>(s.part_v, D.vb0, D.nvb);
     if (threadIdx.x == 0) {
         ctl->ticket[TK_PCG_A] = 0u;
         ctl->pcg_alpha = pap > 0.0 ? ctl->pcg_rz / pap : 0.0;
@@ -1023,9 +1008,8 @@ __global__ void __launch_bounds__(VBS) k_pcg_update(DevSim<R> s, V4<R> *out) {
     }
     double tot[1];
     block_sum_r<VBS, 1, R>(dr, tot);
-    if (!sim_arrive<1>(tot, s.part_v, s.nvb, D.nvb, &ctl->ticket[TK_PCG_B])) return;
-    __threadfence();
-    const double rz = sum_block_range<VBS>(s.part_v, D.vb0, D.nvb);
+    if (!sim_arrive<R, 1>(tot, s.part_v, s.nvb, D.nvb, &ctl->ticket[TK_PCG_B])) return;
+    const double rz = sum_block_range<R, VBS>(s.part_v, D.vb0, D.nvb);
     if (threadIdx.x == 0) {
         ctl->ticket[TK_PCG_B] = 0u;
         ctl->pcg_beta = ctl->pcg_rz > 0.0 ? rz / ctl->pcg_rz : 0.0;

@@ -179,12 +179,117 @@ __device__ __forceinline__ bool publish_and_arrive(const double (&v)[NV], double
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) part[k * stride + blockIdx.x] = v[k];
-        __threadfence();
+        __threadfence();  // release: the partials before the ticket
         const unsigned int t = atomicAdd(ticket, 1u);
         last = (t == gridDim.x - 1);
+        if (last) __threadfence();  // acquire, ordered for the block by the barrier below
     }
     __syncthreads();
     return last;
+}
+
+// ---- block partials of float64-accurate sums
+//
+// A block partial occupies the 8 bytes of a double.  In float mode it is a
+// float-float pair and the simulation's last block adds the partials in
+// float-float arithmetic: GB300 issues float64 at a small fraction of the
+// float32 rate, and a chain of float64 additions on the one SM that finishes
+// a grid reduction was the tail of every reducing kernel.  In double mode
+// partials stay doubles.  The conversions are exact (a double that is the
+// sum of a float-float pair splits back into the same pair).
+template <typename R> struct Part;
+template <> struct Part<float> {
+    using T = FF;
+    __device__ static void put(double *slot, double v) {
+        const float hi = (float)v;
+        const float lo = (float)(v - (double)hi);
+        *reinterpret_cast<float2 *>(slot) = make_float2(hi, lo);
+    }
+    __device__ static T get(const double *slot) {
+        const float2 f = __ldcg(reinterpret_cast<const float2 *>(slot));
+        return FF{f.x, f.y};
+    }
+    __device__ static T zero() { return FF{0.f, 0.f}; }
+    __device__ static T add(T a, T b) { return ff_add(a, b); }
+    __device__ static T shfl_xor(T a, int o) {
+        return FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+    }
+    __device__ static double to_double(T a) { return ff_to_double(a); }
+};
+template <> struct Part<double> {
+    using T = double;
+    __device__ static void put(double *slot, double v) { *slot = v; }
+    __device__ static T get(const double *slot) { return __ldcg(slot); }
+    __device__ static T zero() { return 0.0; }
+    __device__ static T add(T a, T b) { return a + b; }
+    __device__ static T shfl_xor(T a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+    __device__ static double to_double(T a) { return a; }
+};
+
+template <typename R>
+__device__ __forceinline__ typename Part<R>::T part_warp_sum(typename Part<R>::T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = Part<R>::add(v, Part<R>::shfl_xor(v, o));
+    return v;
+}
+
+// part[j] + part[j + stride] + ... (indices < n) as Part<R> values, added in
+// that order, eight loads in flight per round.
+template <typename R>
+__device__ __forceinline__ typename Part<R>::T part_strided_sum(const double *part, int j, int n, int stride) {
+    using P = Part<R>;
+    typename P::T acc = P::zero();
+    for (int b = j; b < n; b += 8 * stride) {
+        typename P::T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int bb = b + u * stride;
+            v[u] = bb < n ? P::get(part + bb) : P::zero();
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = P::add(acc, v[u]);
+    }
+    return acc;
+}
+
+// Fixed-order sums of NV partial arrays (value k at part[k * stride + b],
+// b < n, stored by Part<R>::put) by the NW warps of a block: warp w takes the values k = w,
+// w + NW, ...; a lane adds the partials b = lane, lane + 32, ... in that order
+// (as strided_sum does) with the loads of all of the warp's values issued
+// together, so the whole sum costs one memory round trip per 256 partials.
+// Results in sh[k] (lane 0 writes them; the caller synchronises).
+template <typename R, int NV, int NW>
+__device__ __forceinline__ void warp_value_sums(const double *part, size_t stride, int n, double *sh) {
+    using P = Part<R>;
+    constexpr int PER = (NV + NW - 1) / NW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    typename P::T acc[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) acc[q] = P::zero();
+    for (int b0 = lane; b0 < n; b0 += 32 * 8) {
+        typename P::T v[PER][8];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int k = warp + q * NW;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int bb = b0 + u * 32;
+                v[q][u] = (k < NV && bb < n) ? P::get(part + (size_t)k * stride + bb) : P::zero();
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < PER; ++q)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[q] = P::add(acc[q], v[q][u]);
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int k = warp + q * NW;
+        if (k < NV) {
+            const typename P::T a = part_warp_sum<R>(acc[q]);
+            if (lane == 0) sh[k] = P::to_double(a);
+        }
+    }
 }
 
 // In the last block: fixed-order float64 sums of NV partial arrays of length
@@ -194,7 +299,6 @@ template <int BS, int NV>
 __device__ __forceinline__ void sum_partials(const double *part, int stride, int n, double (&out)[NV],
                                              unsigned int *ticket) {
     __shared__ double sh[NV];
-    __threadfence();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = warp; k < NV; k += BS / 32) {
         double acc = strided_sum(part + k * stride, lane, n, 32);

@@ -479,12 +479,12 @@ __device__ __forceinline__ void bwd_item(const DevSolve<R> &S, const int4 *rec, 
     __shared__ int last;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
+        __threadfence();  // release: the block's partial sums before the count
         last = atomicAdd(S.cb_cnt + e.z, 1) == nch - 1;
+        if (last) __threadfence();  // acquire, ordered for the block by the barrier below
     }
     __syncthreads();
     if (!last) return;
-    __threadfence();
     const V4<R> *first = S.part_r + (size_t)(item - kch) * 32;
     const int j = (int)threadIdx.x;
     if (j < c1 - c0) {
