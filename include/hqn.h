@@ -117,7 +117,8 @@ typedef struct {
     int32_t history_m;    /* L-BFGS window; paper: 5 (Sec. 4.2); 0 = Alg. 1 direction  */
     int32_t ls_max;       /* line-search trials before giving up (paper is silent)    */
     int32_t precision;    /* hqn_precision                                            */
-    int32_t leaf_size;    /* max vertices of a nested-dissection leaf (0 = default 64) */
+    int32_t leaf_size;    /* max vertices of a nested-dissection leaf (0 = default:
+                             128 in HQN_FP32_MIXED, 64 in HQN_FP64_PLAIN)        */
     int32_t use_graph;    /* 1 = run each step as one CUDA graph with conditional
                              (while / if) nodes for the iteration and line-search
                              loops; 0 = host-driven launches (same kernels)        */
@@ -168,6 +169,16 @@ typedef struct {
     int32_t direction;
     int32_t cheb_S;       /* default 10                                            */
     double  cheb_rho;     /* spectral radius estimate in (0, 1) (default 0.99)     */
+    /* Supernode amalgamation of the factored A0: a nested-dissection node at
+     * depth d (the root at 0) whose bit d is set merges with its children's
+     * separators into one supernode, which removes a level from each
+     * triangular sweep at the price of explicit zeros and some fill.  No two
+     * adjacent bits may be set (an update entry then has at most four
+     * sources); HQN_ERR_ARG otherwise.  A merge that would give a supernode
+     * more than 4096 columns is skipped.  Default 0 (the plain dissection
+     * tree): on a 40^3 lattice every mask tried made the solve slower, since
+     * each work item of a wide supernode gathers its whole right-hand side. */
+    int32_t merge_depths;
 } hqn_params;
 
 #define HQN_MAX_HISTORY 16

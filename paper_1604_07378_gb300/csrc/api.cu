@@ -369,29 +369,29 @@ struct Sim final : SimBase {
         for (Setup &s : S) std::vector<double>().swap(s.Q);
         {
             std::vector<int> rows;
-            std::vector<int2> fg2, ug2;
+            std::vector<int4> fg4, ug4;
+            auto quad = [](const std::vector<int> &m, size_t e, int off) {
+                auto at = [&](int k) { return m[e + k] >= 0 ? off + m[e + k] : -1; };
+                return make_int4(at(0), at(1), at(2), at(3));
+            };
             for (int k = 0; k < ns; ++k) {
                 const Setup &s = S[k];
                 for (int r : s.rows) rows.push_back(v0[k] + r);
-                for (size_t e = 0; e < s.fg2.size(); e += 2)
-                    fg2.push_back(make_int2(s.fg2[e] >= 0 ? u0[k] + s.fg2[e] : -1,
-                                            s.fg2[e + 1] >= 0 ? u0[k] + s.fg2[e + 1] : -1));
-                for (size_t e = 0; e < s.ug2.size(); e += 2)
-                    ug2.push_back(make_int2(s.ug2[e] >= 0 ? u0[k] + s.ug2[e] : -1,
-                                            s.ug2[e + 1] >= 0 ? u0[k] + s.ug2[e + 1] : -1));
+                for (size_t e = 0; e < s.fg4.size(); e += 4) fg4.push_back(quad(s.fg4, e, u0[k]));
+                for (size_t e = 0; e < s.ug4.size(); e += 4) ug4.push_back(quad(s.ug4, e, u0[k]));
             }
-            // fg2 is indexed by batch vertex (free vertices of each simulation
+            // fg4 is indexed by batch vertex (free vertices of each simulation
             // come first in its range); pad each simulation to its n vertices
-            std::vector<int2> fgv((size_t)n_tot, make_int2(-1, -1));
+            std::vector<int4> fgv((size_t)n_tot, make_int4(-1, -1, -1, -1));
             size_t e = 0;
             for (int k = 0; k < ns; ++k)
-                for (int j = 0; j < S[k].n_free; ++j) fgv[v0[k] + j] = fg2[e++];
+                for (int j = 0; j < S[k].n_free; ++j) fgv[v0[k] + j] = fg4[e++];
             const int *p_rows;
-            const int2 *p_fg2, *p_ug2;
+            const int4 *p_fg4, *p_ug4;
             if ((rc = upload(p_rows, rows.data(), rows.size()))) return rc;
-            if ((rc = upload(p_fg2, fgv.data(), fgv.size()))) return rc;
-            if ((rc = upload(p_ug2, ug2.data(), ug2.size()))) return rc;
-            dsol.rows = p_rows; dsol.fg2 = p_fg2; dsol.ug2 = p_ug2;
+            if ((rc = upload(p_fg4, fgv.data(), fgv.size()))) return rc;
+            if ((rc = upload(p_ug4, ug4.data(), ug4.size()))) return rc;
+            dsol.rows = p_rows; dsol.fg4 = p_fg4; dsol.ug4 = p_ug4;
         }
         // work items by level, every simulation's items of a level together
         std::vector<std::vector<int4>> frec(L), brec(L);
@@ -404,7 +404,7 @@ struct Sim final : SimBase {
             for (int kk = 0; kk < k; ++kk) roff0 += (int)S[kk].rows.size();
             if (k > 0) cb0 += S[k - 1].lv.n_bwd_blocks;
             for (const SupernodeHost &sn : s.sn)
-                if (sn.children.size() > 2) return fail(HQN_ERR_UNSUPPORTED, "a supernode has more than two children");
+                if (sn.children.size() > 4) return fail(HQN_ERR_UNSUPPORTED, "a supernode has more than four children");
             for (int l = 0; l < s.n_levels; ++l) {
                 fwd_ld[l] = std::max(fwd_ld[l], s.lv.fwd_lvl_ld[l]);
                 fwd_q[l] = std::max(fwd_q[l], s.lv.fwd_lvl_q[l]);
@@ -419,8 +419,9 @@ struct Sim final : SimBase {
                     v.push_back(make_int4((int)(q0 & 0xffffffffLL), (int)(q0 >> 32), (int)((o1 - o0) * sizeof(R)), f.G));
                     v.push_back(make_int4(v0[k] + sn.col, sn.ncol, sn.ldc, u0[k] + sn.uoff));
                     v.push_back(make_int4(f.row0, f.row1, fwd_row_len(f.row1 - 1, sn.ncol, sn.ldc), (int)o0));
-                    v.push_back(make_int4(sn.children.size() > 0 ? sn0[k] + sn.children[0] : -1,
-                                          sn.children.size() > 1 ? sn0[k] + sn.children[1] : -1, sn0[k] + f.s, 0));
+                    auto child = [&](size_t i) { return i < sn.children.size() ? sn0[k] + sn.children[i] : -1; };
+                    v.push_back(make_int4(child(0), child(1), child(2), child(3)));
+                    v.push_back(make_int4(sn0[k] + f.s, 0, 0, 0));
                     nit_f[sn0[k] + f.s]++;
                 }
                 for (int e = s.lv.bwd_lvl_ptr[l]; e < s.lv.bwd_lvl_ptr[l + 1]; ++e) {
@@ -449,10 +450,10 @@ struct Sim final : SimBase {
         std::vector<int4> fi, bi;
         fwd_ptr.assign(L + 1, 0);
         for (int l = 0; l < L; ++l) {
-            fwd_ptr[l] = (int)(fi.size() / 4);
+            fwd_ptr[l] = (int)(fi.size() / 5);
             fi.insert(fi.end(), frec[l].begin(), frec[l].end());
         }
-        fwd_ptr[L] = (int)(fi.size() / 4);
+        fwd_ptr[L] = (int)(fi.size() / 5);
         bwd_start.assign(L, 0);
         bwd_cnt.assign(L, 0);
         for (int l = L - 1; l >= 0; --l) {
@@ -475,7 +476,7 @@ struct Sim final : SimBase {
         if ((rc = alloc(dsol.queue, 2))) return rc;
         dsol.n_sn = (int)sn_tot;
         dsol.nf = (int)nf_tot;
-        dsol.n_fwd_items = (int)(fi.size() / 4);
+        dsol.n_fwd_items = (int)(fi.size() / 5);
         dsol.n_bwd_items = (int)(bi.size() / 5);
         if ((rc = alloc(dsol.part_r, (size_t)std::max(1, dsol.n_bwd_items) * 32))) return rc;
         if ((rc = alloc(dsol.cb_cnt, (size_t)std::max(1, n_cb)))) return rc;
@@ -1364,6 +1365,8 @@ int create_any(int count, const hqn_mesh *meshes, const hqn_material *materials,
     if (params->direction == 1 && !(params->cheb_rho > 0.0 && params->cheb_rho < 1.0 && params->cheb_S >= 0))
         return fail(HQN_ERR_ARG, "Chebyshev direction needs 0 < cheb_rho < 1 and cheb_S >= 0");
     if (params->a0_solver != 0 && params->a0_solver != 1) return fail(HQN_ERR_ARG, "unknown a0_solver");
+    if (params->merge_depths < 0 || (params->merge_depths & (params->merge_depths >> 1)))
+        return fail(HQN_ERR_ARG, "merge_depths must be a mask without two adjacent depths");
     if (params->a0_solver == 1 && (params->pcg_iters < 1 || params->pcg_iters > 1000))
         return fail(HQN_ERR_ARG, "pcg_iters must be in [1, 1000]");
     if (params->n_colliders < 0 || params->n_colliders > HQN_MAX_COLLIDERS)
@@ -1420,7 +1423,7 @@ void hqn_default_params(hqn_params *p) {
     p->history_m = 5;
     p->ls_max = 30;
     p->precision = HQN_FP32_MIXED;
-    p->leaf_size = 64;
+    p->leaf_size = 0;
     p->use_graph = 1;
     p->tet_block = TBS;
     p->ls_batch = 8;
@@ -1432,6 +1435,7 @@ void hqn_default_params(hqn_params *p) {
     p->direction = 0;
     p->cheb_S = 10;
     p->cheb_rho = 0.99;
+    p->merge_depths = 0;
 }
 
 int sim_create(const hqn_mesh *mesh, const hqn_material *material, const hqn_params *params, void *stream,

@@ -114,10 +114,11 @@ struct DevSolve {
     const R *QF;                // per supernode: packed Q_s, row-major (layout.hpp)
     const R *QB;                // per supernode: packed Q_s^T, row-major (layout.hpp)
     const int *rows;            // row structures R of the supernodes
-    const int2 *fg2;            // per column: the (<= 2) child update entries to subtract
-    const int2 *ug2;            // per update entry: the (<= 2) child update entries to add
-    // Work items, 4 int4 each (backward: 5):
-    //   forward  {q0 lo, q0 hi, bytes, G} {col, nc, ldc, uoff} {r0, r1, ldf, off0} {child0, child1, s, 0}
+    const int4 *fg4;            // per column: the (<= 4) child update entries to subtract
+    const int4 *ug4;            // per update entry: the (<= 4) child update entries to add
+    // Work items, 5 int4 each:
+    //   forward  {q0 lo, q0 hi, bytes, G} {col, nc, ldc, uoff} {r0, r1, ldf, off0}
+    //            {child0, child1, child2, child3} {s, 0, 0, 0}
     //   backward {q0 lo, q0 hi, bytes, G} {col, nc, nrow, roff} {c0, c1, ldr, off0} {parent, s, 0, 0}
     //            {e0, e1, column block, nch << 16 | chunk}  (e0 < 0: whole rows; chunk items
     //            have q0 = their supernode's block, bytes = the sum of their rows' pieces)

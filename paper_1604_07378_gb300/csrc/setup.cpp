@@ -125,17 +125,22 @@ struct NDState {
     int leaf = 64;
 };
 
+// A node of the dissection tree over vertex set V (its columns once ordered).
+int nd_node(NDState &st, const std::vector<int> &V, const std::vector<int> &children) {
+    SupernodeHost s;
+    s.children = children;
+    st.nodes.push_back(s);
+    st.node_verts.push_back(V);
+    const int id = (int)st.nodes.size() - 1;
+    for (int c : children) st.nodes[c].parent = id;
+    return id;
+}
+
 int nd_recurse(NDState &st, std::vector<int> &V) {
     const std::vector<double> &X = *st.X;
     if ((int)V.size() <= st.leaf) {
         std::sort(V.begin(), V.end());
-        SupernodeHost s;
-        s.col = (int)st.order.size();
-        s.ncol = (int)V.size();
-        for (int v : V) st.order.push_back(v);
-        st.nodes.push_back(s);
-        st.node_verts.push_back(V);
-        return (int)st.nodes.size() - 1;
+        return nd_node(st, V, {});
     }
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int v : V)
@@ -164,13 +169,7 @@ int nd_recurse(NDState &st, std::vector<int> &V) {
     }
     if (A.empty()) {  // cannot split geometrically: make it one leaf-like node
         std::sort(V.begin(), V.end());
-        SupernodeHost s;
-        s.col = (int)st.order.size();
-        s.ncol = (int)V.size();
-        for (int v : V) st.order.push_back(v);
-        st.nodes.push_back(s);
-        st.node_verts.push_back(V);
-        return (int)st.nodes.size() - 1;
+        return nd_node(st, V, {});
     }
     for (int v : A) st.side[v] = 1;
     for (int v : B) st.side[v] = 2;
@@ -191,15 +190,61 @@ int nd_recurse(NDState &st, std::vector<int> &V) {
     children.push_back(nd_recurse(st, A));
     if (!Bp.empty()) children.push_back(nd_recurse(st, Bp));
     std::sort(S.begin(), S.end());
+    return nd_node(st, S, children);
+}
+
+// The supernode tree and the elimination order, from the dissection tree.
+// A dissection node at depth d (the root at 0) whose bit d is set in `merge`
+// takes its children's vertices into its own supernode, and theirs in turn
+// when their bits are set; the supernode's children are the dissection nodes
+// below the merged group.  Merging a separator with the separators under it
+// gives up the zeros between them (the children's vertices are not coupled
+// to each other) and some fill in the rectangle, and removes a level from
+// each sweep's dependency chain.  Columns follow the tree in postorder: a
+// supernode's children first, then its group, children's vertices before
+// their parent's.
+// A merged supernode holds at most this many columns: a forward work item
+// stages its whole right-hand side in shared memory.
+constexpr int kMergeMaxCols = 4096;
+
+// Columns of the supernode that dissection node p (depth d) heads.
+int nd_group_cols(const NDState &st, int p, int d, uint32_t merge) {
+    int n = (int)st.node_verts[p].size();
+    if (d < 32 && ((merge >> d) & 1u)) {
+        int m = n;
+        for (int c : st.nodes[p].children) m += nd_group_cols(st, c, d + 1, merge);
+        if (m <= kMergeMaxCols) n = m;
+    }
+    return n;
+}
+
+void nd_collect(const NDState &st, int p, int d, uint32_t merge, std::vector<int> &group,
+                std::vector<std::pair<int, int>> &kids) {
+    const bool absorb = d < 32 && ((merge >> d) & 1u) &&
+                        nd_group_cols(st, p, d, merge) > (int)st.node_verts[p].size();
+    for (int c : st.nodes[p].children) {
+        if (absorb) nd_collect(st, c, d + 1, merge, group, kids);
+        else kids.push_back({c, d + 1});
+    }
+    group.push_back(p);
+}
+
+int nd_emit(const NDState &st, int p, int d, uint32_t merge, std::vector<SupernodeHost> &out,
+            std::vector<int> &order) {
+    std::vector<int> group;
+    std::vector<std::pair<int, int>> kids;
+    nd_collect(st, p, d, merge, group, kids);
+    std::vector<int> ch;
+    for (const auto &k : kids) ch.push_back(nd_emit(st, k.first, k.second, merge, out, order));
     SupernodeHost s;
-    s.col = (int)st.order.size();
-    s.ncol = (int)S.size();
-    s.children = children;
-    for (int v : S) st.order.push_back(v);
-    st.nodes.push_back(s);
-    st.node_verts.push_back(S);
-    const int id = (int)st.nodes.size() - 1;
-    for (int c : children) st.nodes[c].parent = id;
+    s.col = (int)order.size();
+    for (int g : group)
+        for (int v : st.node_verts[g]) order.push_back(v);
+    s.ncol = (int)order.size() - s.col;
+    s.children = ch;
+    out.push_back(s);
+    const int id = (int)out.size() - 1;
+    for (int c : ch) out[c].parent = id;
     return id;
 }
 
@@ -329,6 +374,15 @@ double fit_stiffness(const MaterialHost &m, double x_start, double x_end) {
     }
     const double len = x_end - x_start;
     return num / (len * len * len / 12.0);
+}
+
+// Leaf size 0: 128 vertices in the float32 form, whose sweeps are bound by
+// the chain of levels (one level fewer for ~5% more factor entries measured
+// faster on cube40), 64 in the float64 form, whose sweeps are bound by
+// float64 arithmetic on the factor's entries.
+static int leaf_size_of(const hqn_params &prm) {
+    if (prm.leaf_size > 0) return prm.leaf_size;
+    return prm.precision == HQN_FP64_PLAIN ? 64 : 128;
 }
 
 int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_params &prm,
@@ -470,7 +524,7 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
     st.adj_ptr = &adj_ptr;
     st.adj = &adj;
     st.side.assign(n, 0);
-    st.leaf = prm.leaf_size > 0 ? prm.leaf_size : 64;
+    st.leaf = leaf_size_of(prm);
     std::vector<int> freev;
     for (int v = 0; v < n; ++v)
         if (!clamped[v]) freev.push_back(v);
@@ -478,7 +532,10 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
         err = "every vertex is clamped";
         return HQN_ERR_ARG;
     }
-    nd_recurse(st, freev);
+    const int root = nd_recurse(st, freev);
+    S.sn.clear();
+    st.order.clear();
+    nd_emit(st, root, 0, (uint32_t)prm.merge_depths, S.sn, st.order);
     S.n = n;
     S.T = T;
     S.n_free = (int)st.order.size();
@@ -487,7 +544,6 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
         if (clamped[v]) S.perm.push_back(v);
     S.iperm.assign(n, 0);
     for (int i = 0; i < n; ++i) S.iperm[S.perm[i]] = i;
-    S.sn = std::move(st.nodes);
     const int nf = S.n_free;
 
     // ---- renumbered rest data, tets sorted by smallest vertex id
@@ -707,24 +763,26 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
         for (int u = 0; u < utot; ++u) S.ug_idx.insert(S.ug_idx.end(), ug[u].begin(), ug[u].end());
     }
 
-    // ---- pair form of the extend-add maps (a binary tree: <= 2 sources per entry)
-    S.fg2.assign(2 * (size_t)nf, -1);
-    S.ug2.assign(2 * (size_t)utot, -1);
+    // ---- quad form of the extend-add maps: each entry receives from at most
+    // the two children of a dissection node, or from the four below a merged
+    // pair of depths
+    S.fg4.assign(4 * (size_t)nf, -1);
+    S.ug4.assign(4 * (size_t)utot, -1);
     for (int j = 0; j < nf; ++j) {
         const int c = S.fg_ptr[j + 1] - S.fg_ptr[j];
-        if (c > 2) {
-            err = "a column receives updates from more than two children";
+        if (c > 4) {
+            err = "a column receives updates from more than four children";
             return HQN_ERR_ARG;
         }
-        for (int k = 0; k < c; ++k) S.fg2[2 * (size_t)j + k] = S.fg_idx[S.fg_ptr[j] + k];
+        for (int k = 0; k < c; ++k) S.fg4[4 * (size_t)j + k] = S.fg_idx[S.fg_ptr[j] + k];
     }
     for (int u = 0; u < utot; ++u) {
         const int c = S.ug_ptr[u + 1] - S.ug_ptr[u];
-        if (c > 2) {
-            err = "an update entry receives from more than two children";
+        if (c > 4) {
+            err = "an update entry receives from more than four children";
             return HQN_ERR_ARG;
         }
-        for (int k = 0; k < c; ++k) S.ug2[2 * (size_t)u + k] = S.ug_idx[S.ug_ptr[u] + k];
+        for (int k = 0; k < c; ++k) S.ug4[4 * (size_t)u + k] = S.ug_idx[S.ug_ptr[u] + k];
     }
 
     // ---- packed device layout (layout.hpp) and level work lists

@@ -79,8 +79,9 @@ struct Setup {
     std::vector<double> Q;           // concatenated Q_s, row-major
     std::vector<int> fg_ptr, fg_idx; // per free column: child update entries to subtract
     std::vector<int> ug_ptr, ug_idx; // per update entry: child update entries to add
-    std::vector<int> fg2, ug2;       // the same maps as pairs (-1 = none): at most two
-                                     // children (a binary dissection tree) feed an entry
+    std::vector<int> fg4, ug4;       // the same maps as quads (-1 = none): at most two
+                                     // children of a dissection node feed an entry, or
+                                     // four under a merged supernode
     int n_upd = 0, n_levels = 0;
     ItemLists lv;                    // items of the level-by-level schedules
     ItemLists pp;                    // items of the pipelined schedule (one ring slot each)

@@ -10,7 +10,7 @@
 //   backward (root first):   r_C = Q_s^T [z_C; -r_R]
 // A tree level is one launch; within a level every supernode is independent,
 // and updates pass up the tree through index tables (each entry receives from
-// at most two children; no atomics).
+// at most four children; no atomics).
 //
 // One block runs one work item: a run of consecutive rows of the packed
 // forward copy of Q_s, or of the packed backward copy of Q_s^T (layout.hpp),
@@ -222,9 +222,11 @@ __device__ __forceinline__ void fwd_rows(const DevSolve<R> &S, int col, int nc, 
                     if (ua) {
                         o.x += ua[i - rr0]; o.y += ua[ua_s + i - rr0]; o.z += ua[2 * ua_s + i - rr0];
                     } else {
-                        const int2 c = S.ug2[uoff + i - nc];
+                        const int4 c = S.ug4[uoff + i - nc];
                         if (c.x >= 0) { const V4<R> a = ld_cg(S.u + c.x); o.x += a.x; o.y += a.y; o.z += a.z; }
                         if (c.y >= 0) { const V4<R> a = ld_cg(S.u + c.y); o.x += a.x; o.y += a.y; o.z += a.z; }
+                        if (c.z >= 0) { const V4<R> a = ld_cg(S.u + c.z); o.x += a.x; o.y += a.y; o.z += a.z; }
+                        if (c.w >= 0) { const V4<R> a = ld_cg(S.u + c.w); o.x += a.x; o.y += a.y; o.z += a.z; }
                     }
                     S.u[uoff + i - nc] = o;
                 }
@@ -247,10 +249,11 @@ __device__ __forceinline__ void fwd_rows_g(int G, const DevSolve<R> &S, int col,
     }
 }
 
-// One forward work item (record `rec`, 4 int4).  Shared memory: qs = the
+// One forward work item (record `rec`, 5 int4).  Shared memory: qs = the
 // item's factor rows (qcap entries), then f (3 x ldf entries), then the summed
 // child update entries of its rectangle rows (3 x pad4(nrr) entries), then
-// their index pairs (ldf int2 for the columns, nrr int2 for the rows).  Every
+// their source indices (ldf int4 for the columns, nrr int4 for the rows; up
+// to four children feed an entry, -1 = none).  Every
 // load of a vector another item produces is issued in one parallel pass
 // after `wait_inputs`, so the row products read only shared memory.
 template <typename R, typename Wait>
@@ -264,11 +267,11 @@ __device__ __forceinline__ void fwd_item(const DevSolve<R> &S, const int4 *rec, 
     const int rr0 = r0 > nc ? r0 : nc, nrr = r1 > rr0 ? r1 - rr0 : 0, nrr4 = pad4(nrr);
     R *f = qs + qcap;
     R *ua = f + 3 * ldf;
-    int2 *cidx = reinterpret_cast<int2 *>(ua + 3 * nrr4);
-    int2 *ridx = cidx + ldf;
+    int4 *cidx = reinterpret_cast<int4 *>(ua + 3 * nrr4);
+    int4 *ridx = cidx + ldf;
     const int nf = ldf < nc ? ldf : nc;
-    for (int j = threadIdx.x; j < nf; j += SBS) cidx[j] = S.fg2[col + j];
-    for (int j = threadIdx.x; j < nrr; j += SBS) ridx[j] = S.ug2[uoff + rr0 - nc + j];
+    for (int j = threadIdx.x; j < nf; j += SBS) cidx[j] = __ldg(S.fg4 + col + j);
+    for (int j = threadIdx.x; j < nrr; j += SBS) ridx[j] = __ldg(S.ug4 + uoff + rr0 - nc + j);
     if (!wait_inputs()) {
         if (threadIdx.x == 0) bulk_load_wait(bar, parity);  // let the copy in flight land first
         return;
@@ -278,29 +281,34 @@ __device__ __forceinline__ void fwd_item(const DevSolve<R> &S, const int4 *rec, 
     const int nj = ldf > nrr ? ldf : nrr;
 #pragma unroll 2
     for (int j = threadIdx.x; j < nj; j += SBS) {
-        V4<R> v, u0, u1, w0, w1;
-        v.x = v.y = v.z = u0.x = u0.y = u0.z = u1.x = u1.y = u1.z = R(0);
-        w0 = u0; w1 = u0;
+        V4<R> v, u[4], w[4];
+        v.x = v.y = v.z = R(0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { u[k] = v; w[k] = v; }
         if (j < nc) {
-            const int2 ci = cidx[j];
+            const int4 ci = cidx[j];
             v = ld_cg(rhs + col + j);
-            if (ci.x >= 0) u0 = ld_cg(S.u + ci.x);
-            if (ci.y >= 0) u1 = ld_cg(S.u + ci.y);
+            if (ci.x >= 0) u[0] = ld_cg(S.u + ci.x);
+            if (ci.y >= 0) u[1] = ld_cg(S.u + ci.y);
+            if (ci.z >= 0) u[2] = ld_cg(S.u + ci.z);
+            if (ci.w >= 0) u[3] = ld_cg(S.u + ci.w);
         }
         if (j < nrr) {
-            const int2 ri = ridx[j];
-            if (ri.x >= 0) w0 = ld_cg(S.u + ri.x);
-            if (ri.y >= 0) w1 = ld_cg(S.u + ri.y);
+            const int4 ri = ridx[j];
+            if (ri.x >= 0) w[0] = ld_cg(S.u + ri.x);
+            if (ri.y >= 0) w[1] = ld_cg(S.u + ri.y);
+            if (ri.z >= 0) w[2] = ld_cg(S.u + ri.z);
+            if (ri.w >= 0) w[3] = ld_cg(S.u + ri.w);
         }
         if (j < ldf) {
-            f[j] = v.x - u0.x - u1.x;
-            f[ldf + j] = v.y - u0.y - u1.y;
-            f[2 * ldf + j] = v.z - u0.z - u1.z;
+            f[j] = v.x - u[0].x - u[1].x - u[2].x - u[3].x;
+            f[ldf + j] = v.y - u[0].y - u[1].y - u[2].y - u[3].y;
+            f[2 * ldf + j] = v.z - u[0].z - u[1].z - u[2].z - u[3].z;
         }
         if (j < nrr) {
-            ua[j] = w0.x + w1.x;
-            ua[nrr4 + j] = w0.y + w1.y;
-            ua[2 * nrr4 + j] = w0.z + w1.z;
+            ua[j] = w[0].x + w[1].x + w[2].x + w[3].x;
+            ua[nrr4 + j] = w[0].y + w[1].y + w[2].y + w[3].y;
+            ua[2 * nrr4 + j] = w[0].z + w[1].z + w[2].z + w[3].z;
         }
     }
     if (!bulk_load_finish(bar, parity, S.err)) return;
@@ -313,7 +321,7 @@ __global__ void __launch_bounds__(SBS, 4) k_fwd(DevSolve<R> S, int item0, int qc
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) bulk_bar_init(&bar);
-    fwd_item<R>(S, S.fwd_items + 4 * (size_t)(item0 + blockIdx.x), qcap, reinterpret_cast<R *>(smem_raw), &bar, 0u,
+    fwd_item<R>(S, S.fwd_items + 5 * (size_t)(item0 + blockIdx.x), qcap, reinterpret_cast<R *>(smem_raw), &bar, 0u,
                 rhs, z, []() {
                     pdl_trigger();
                     pdl_wait();
@@ -577,17 +585,20 @@ __global__ void __launch_bounds__(SBS) k_fwd_dyn(DevSolve<R> S, int qcap, const 
         __syncthreads();
         const int item = item_sh;
         if (item >= S.n_fwd_items) break;
-        const int4 *rec = S.fwd_items + 4 * (size_t)item;
-        const int4 dep = rec[3];  // children c0, c1 (-1: none), own supernode
+        const int4 *rec = S.fwd_items + 5 * (size_t)item;
+        const int4 dep = rec[3];  // children c0 .. c3 (-1: none)
+        const int own = rec[4].x;
         fwd_item<R>(S, rec, qcap, qs, &bar, parity, rhs, z, [&]() {
             if (threadIdx.x == 0)
                 ok_sh = dep_wait(S.fwd_done, dep.x, dep.x >= 0 ? S.fwd_nitems[dep.x] : 0, S.err) &&
-                        dep_wait(S.fwd_done, dep.y, dep.y >= 0 ? S.fwd_nitems[dep.y] : 0, S.err);
+                        dep_wait(S.fwd_done, dep.y, dep.y >= 0 ? S.fwd_nitems[dep.y] : 0, S.err) &&
+                        dep_wait(S.fwd_done, dep.z, dep.z >= 0 ? S.fwd_nitems[dep.z] : 0, S.err) &&
+                        dep_wait(S.fwd_done, dep.w, dep.w >= 0 ? S.fwd_nitems[dep.w] : 0, S.err);
             __syncthreads();
             return ok_sh != 0;
         });
         if (!still_ok(S.err)) break;
-        dep_signal(S.fwd_done, dep.z);
+        dep_signal(S.fwd_done, own);
         parity ^= 1u;
     }
 }
@@ -766,36 +777,38 @@ __device__ __forceinline__ void pipe_gather_fwd(const DevSolve<R> &S, const Pipe
                                                 int fcap, const V4<R> *rhs) {
     for (int base = threadIdx.x; base < ftot; base += PG * PCONS) {
         V4<R> v[PG];
-        int2 ci[PG];
+        int4 ci[PG];
 #pragma unroll
         for (int g = 0; g < PG; ++g) {
             const int e = base + g * PCONS;
             v[g].x = v[g].y = v[g].z = v[g].w = R(0);
-            ci[g] = make_int2(-1, -1);
+            ci[g] = make_int4(-1, -1, -1, -1);
             if (e < ftot) {
                 const int4 sg = sh.seg[pipe_seg_of(sh, nseg, e)];  // {col, filled, area offset, length}
                 const int j = e - sg.z;
                 if (j < sg.y) {
                     v[g] = ld_cg(rhs + sg.x + j);
-                    ci[g] = __ldg(S.fg2 + sg.x + j);
+                    ci[g] = __ldg(S.fg4 + sg.x + j);
                 }
             }
         }
-        V4<R> a[PG], b[PG];
+        V4<R> a[PG], b[PG], c[PG], d[PG];
 #pragma unroll
         for (int g = 0; g < PG; ++g) {
             a[g].x = a[g].y = a[g].z = R(0);
-            b[g].x = b[g].y = b[g].z = R(0);
+            b[g] = a[g]; c[g] = a[g]; d[g] = a[g];
             if (ci[g].x >= 0) a[g] = ld_cg(S.u + ci[g].x);
             if (ci[g].y >= 0) b[g] = ld_cg(S.u + ci[g].y);
+            if (ci[g].z >= 0) c[g] = ld_cg(S.u + ci[g].z);
+            if (ci[g].w >= 0) d[g] = ld_cg(S.u + ci[g].w);
         }
 #pragma unroll
         for (int g = 0; g < PG; ++g) {
             const int e = base + g * PCONS;
             if (e < ftot) {
-                F[e] = v[g].x - a[g].x - b[g].x;
-                F[fcap + e] = v[g].y - a[g].y - b[g].y;
-                F[2 * fcap + e] = v[g].z - a[g].z - b[g].z;
+                F[e] = v[g].x - a[g].x - b[g].x - c[g].x - d[g].x;
+                F[fcap + e] = v[g].y - a[g].y - b[g].y - c[g].y - d[g].y;
+                F[2 * fcap + e] = v[g].z - a[g].z - b[g].z - c[g].z - d[g].z;
             }
         }
     }
@@ -1007,10 +1020,10 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_pipe(DevSolve<R> S, const V4<R>
 }
 
 // Dynamic shared memory of a sweep block: qcap factor entries, 3 x ld vector
-// entries and ld 8-byte index slots.
+// entries and ld 16-byte index slots.
 template <typename R>
 size_t sweep_smem(int qcap, int ld) {
-    return ((size_t)qcap + 3 * (size_t)ld) * sizeof(R) + 8 * (size_t)ld;
+    return ((size_t)qcap + 3 * (size_t)ld) * sizeof(R) + 16 * (size_t)ld;
 }
 
 // Dynamic shared memory of a pipelined sweep block: ns ring slots and the

@@ -63,7 +63,8 @@ class Params(C.Structure):
                 ("tet_block", C.c_int32), ("ls_batch", C.c_int32), ("dyn_sweeps", C.c_int32),
                 ("n_colliders", C.c_int32), ("contact_scale", C.c_double),
                 ("colliders", Collider * MAX_COLLIDERS), ("a0_solver", C.c_int32), ("pcg_iters", C.c_int32),
-                ("direction", C.c_int32), ("cheb_S", C.c_int32), ("cheb_rho", C.c_double)]
+                ("direction", C.c_int32), ("cheb_S", C.c_int32), ("cheb_rho", C.c_double),
+                ("merge_depths", C.c_int32)]
 
 
 class StepStats(C.Structure):

@@ -240,3 +240,41 @@ def test_trajectory_30_steps_fp64():
             sim.step(1)
             gq, _ = sim.get_state()
             assert rel(gq, x_ref) <= 1e-8, k
+
+
+@pytest.fixture(scope="module")
+def lat30_solve_case():
+    rng = np.random.default_rng(21)
+    q = rng.normal(size=(LAT30.n_verts, 3))
+    return q, O.solve_A(problem_for(LAT30), q)
+
+
+@pytest.mark.parametrize("merge", [0, 1, 5, 0x55, 0x155], ids=lambda m: f"merge{m:#x}")
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("dyn_sweeps", [0, 1, 2], ids=["levels", "dependency", "pipelined"])
+def test_solve_A0_merged_supernodes(lat30_solve_case, merge, prec, dyn_sweeps):
+    """Supernodes that merge a separator with the separators under it (their
+    update entries fed by up to four children) solve A0 r = q to the same
+    tolerance as the plain dissection tree, in every sweep schedule."""
+    q, r_ref = lat30_solve_case
+    with sim_for(LAT30, prec, use_graph=0, dyn_sweeps=dyn_sweeps, merge_depths=merge) as sim:
+        r = sim.solve_A0(q)
+    assert rel(r, r_ref) <= (1e-11 if prec == FP64 else 2e-5)
+    assert np.all(r[LAT30.clamped.astype(bool)] == 0.0)
+
+
+def test_merged_supernodes_shorten_the_sweeps():
+    """Each merged depth removes one level from the sweeps' chain; the
+    default merges none; a mask with two adjacent depths is rejected."""
+    from paper_1604_07378_gb300 import hqn
+    levels = {}
+    for merge in (0, 1, 5, 0x55):
+        with sim_for(LAT30, FP32, merge_depths=merge) as sim:
+            levels[merge] = sim.info()["n_levels"]
+    assert levels[1] == levels[0] - 1 and levels[5] == levels[0] - 2
+    assert levels[0x55] < levels[5]
+    with sim_for(LAT30, FP32) as sim:
+        assert sim.info()["n_levels"] == levels[0]
+    with pytest.raises(hqn.HQNError) as e:
+        sim_for(LAT30, FP32, merge_depths=3)
+    assert e.value.code == hqn.HQN_ERR_ARG
