@@ -118,7 +118,8 @@ typedef struct {
     int32_t ls_max;       /* line-search trials before giving up (paper is silent)    */
     int32_t precision;    /* hqn_precision                                            */
     int32_t leaf_size;    /* max vertices of a nested-dissection leaf (0 = default:
-                             128 in HQN_FP32_MIXED, 64 in HQN_FP64_PLAIN)        */
+                             128 in HQN_FP32_MIXED up to 150,000 free vertices,
+                             64 otherwise)                                       */
     int32_t use_graph;    /* 1 = run each step as one CUDA graph with conditional
                              (while / if) nodes for the iteration and line-search
                              loops; 0 = host-driven launches (same kernels)        */
