@@ -31,9 +31,10 @@ if ROOT not in sys.path:
 
 METRIC = "time-steps/s & tet grad-evals/s at 384k tets, FP32 vs FP64 GPU, pos err ≤1e-4"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one cube40 FP32
-# solve, summed over its 20 sweep launches in an ncu capture of this script's
-# --no-graph run; to be set to None when the sweep kernels change.
-SOLVE_TRAFFIC_BYTES = None
+# solve (default leaf size and sweep schedule), summed over its 20 sweep
+# launches in an ncu capture of this script's --no-graph run; to be set to
+# None when the sweep kernels change.
+SOLVE_TRAFFIC_BYTES = 243.99e6
 UNIT = "time-steps/s"
 WORKLOAD = "cube40_neohookean"
 
@@ -265,7 +266,9 @@ def run_ours(args, rank, world, dist):
         achieved = bytes_launch / (stage_ms["solve"] * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": "A0^-1 solve: forward + backward sweeps (k_fwd, k_bwd), one solve",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": SOLVE_TRAFFIC_BYTES,
+                "frac": achieved / peaks["hbm_gbs"],
+                # the capture holds for the default tree and schedule only
+                "traffic": SOLVE_TRAFFIC_BYTES if args.leaf_size == 0 and SWEEPS[args.sweeps] == 0 else None,
                 "algorithmic_bytes_per_launch": bytes_launch}
     else:
         # the tet pass (energy + corner gradients): idx 16 + Dm^-1 36 + V 4 B
