@@ -219,9 +219,22 @@ typedef struct {
 typedef struct sim_handle sim_handle;
 
 /* Paper defaults: h = 1/30, gamma = 0.3, backtrack = 0.5, [0.5, 1.5], gravity
- * (0, 0, -9.81), 10 iterations, m = 5, ls_max = 30, FP32_MIXED, leaf 64,
- * graph mode on, tet block 128, 8 line-search trials per pass. */
+ * (0, 0, -9.81), 10 iterations, m = 5, ls_max = 30, FP32_MIXED, leaf size 0
+ * (the size-dependent default), no supernode merges, graph mode on, tet
+ * block 128, 8 line-search trials per pass. */
 void hqn_default_params(hqn_params *p);
+
+/* Host-only analysis: the set-up sim_create performs on the host (rest data,
+ * the stiffness k of Eq. stiffness, A0's nested-dissection ordering and
+ * float64 supernodal Cholesky factor, the sweeps' levels) for one mesh,
+ * without a GPU and without keeping anything.  Fills the fields of *info
+ * that the set-up determines: n_verts, n_tets, n_free, n_supernodes,
+ * n_levels, factor_entries, factor_nnz, stiffness_k, setup_seconds,
+ * n_update_entries, and precision, graph_mode and sweep_schedule as
+ * requested by *params (n_sims = 1); the device-dependent fields are 0.
+ * Errors: those of sim_create other than HQN_ERR_CUDA. */
+int hqn_analyse(const hqn_mesh *mesh, const hqn_material *material,
+                const hqn_params *params, hqn_info *info);
 
 /* Builds a simulation: rest data (Dm^-1, volumes, lumped mass), the stiffness k
  * of Eq. stiffness, A0 = M/h^2 + sum_t V_t k G_t^T G_t on the free vertices

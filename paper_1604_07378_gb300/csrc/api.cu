@@ -1354,11 +1354,9 @@ struct sim_handle {
 
 namespace {
 
-int create_any(int count, const hqn_mesh *meshes, const hqn_material *materials, const hqn_params *params,
-               void *stream, sim_handle **out) {
-    if (!out) return fail(HQN_ERR_ARG, "null output pointer");
-    *out = nullptr;
-    if (count <= 0 || !meshes || !materials || !params) return fail(HQN_ERR_ARG, "null argument or empty batch");
+// Checks of the parameters that do not depend on a mesh (HQN_OK or a status
+// set through fail()).
+int validate_params(const hqn_params *params) {
     if (params->precision != HQN_FP32_MIXED && params->precision != HQN_FP64_PLAIN)
         return fail(HQN_ERR_ARG, "unknown precision");
     if (params->direction != 0 && params->direction != 1) return fail(HQN_ERR_ARG, "unknown direction");
@@ -1386,6 +1384,15 @@ int create_any(int count, const hqn_mesh *meshes, const hqn_material *materials,
     }
     if (params->tet_block != 0 && params->tet_block != TBS)
         return fail(HQN_ERR_UNSUPPORTED, "tet_block must be 0 or 128");
+    return HQN_OK;
+}
+
+int create_any(int count, const hqn_mesh *meshes, const hqn_material *materials, const hqn_params *params,
+               void *stream, sim_handle **out) {
+    if (!out) return fail(HQN_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    if (count <= 0 || !meshes || !materials || !params) return fail(HQN_ERR_ARG, "null argument or empty batch");
+    if (const int rc = validate_params(params)) return rc;
     try {
         std::unique_ptr<SimBase> impl;
         const cudaStream_t st = (cudaStream_t)stream;
@@ -1499,6 +1506,37 @@ int sim_direction(sim_handle *sim, const double *grad, int32_t npairs, const dou
 int sim_time_stage(sim_handle *sim, int32_t stage, int32_t reps, double *ms) {
     if (!sim || !ms) return fail(HQN_ERR_ARG, "null argument");
     try { return sim->impl->time_stage(stage, reps, ms); } catch (...) { return fail(HQN_ERR_NO_MEMORY, "exception"); }
+}
+
+int hqn_analyse(const hqn_mesh *mesh, const hqn_material *material, const hqn_params *params, hqn_info *info) {
+    if (!mesh || !material || !params || !info) return fail(HQN_ERR_ARG, "null argument");
+    std::memset(info, 0, sizeof(*info));
+    if (const int rc = validate_params(params)) return rc;
+    try {
+        Setup S;
+        std::string err;
+        const int rc = build_setup(*mesh, *material, *params, S, err);
+        if (rc != HQN_OK) return fail(rc, err);
+        info->n_verts = S.n;
+        info->n_tets = S.T;
+        info->n_free = S.n_free;
+        info->n_supernodes = (int32_t)S.sn.size();
+        info->n_levels = S.n_levels;
+        info->factor_entries = (int64_t)S.Q.size();
+        info->factor_nnz = S.factor_nnz;
+        info->stiffness_k = S.k;
+        info->setup_seconds = S.setup_seconds;
+        info->precision = params->precision;
+        info->graph_mode = params->use_graph ? 1 : 0;
+        info->n_update_entries = S.n_upd;
+        info->sweep_schedule = params->dyn_sweeps;
+        info->n_sims = 1;
+        return HQN_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(HQN_ERR_NO_MEMORY, "host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(HQN_ERR_ARG, e.what());
+    }
 }
 
 int sim_get_info(const sim_handle *sim, hqn_info *info) {

@@ -117,6 +117,7 @@ def library(path: str | None = None):
     lib.sim_solve_A0.argtypes = [C.c_void_p, _dp, _dp]
     lib.sim_direction.argtypes = [C.c_void_p, _dp, C.c_int32, _dp, _dp, _dp]
     lib.sim_get_info.argtypes = [C.c_void_p, C.POINTER(Info)]
+    lib.hqn_analyse.argtypes = [C.POINTER(Mesh), C.POINTER(Material), C.POINTER(Params), C.POINTER(Info)]
     lib.sim_time_stage.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _dp]
     lib.sim_destroy.argtypes = [C.c_void_p]
     lib.sim_destroy.restype = None
@@ -183,6 +184,52 @@ def default_params(**kw) -> Params:
     return p
 
 
+class _MeshArgs:
+    """hqn_mesh and hqn_material views of caller arrays (kept alive here)."""
+
+    def __init__(self, rest_pos, tets, clamped, kind, E, nu, density, spline, kappa, fiber):
+        self.X = np.ascontiguousarray(rest_pos, dtype=np.float64)
+        self.tets = np.ascontiguousarray(tets, dtype=np.int32)
+        self.n = self.X.shape[0]
+        self.cl = None if clamped is None else np.ascontiguousarray(clamped, dtype=np.uint8)
+        self.mesh = Mesh(self.n, self.tets.shape[0], _ptr(self.X), _ptr(self.tets, _ip),
+                         None if self.cl is None else _ptr(self.cl, _up))
+        self.spline = None if spline is None else np.ascontiguousarray(spline, dtype=np.float64)
+        self.mat = Material(kind, E, nu, density, None if self.spline is None else _ptr(self.spline),
+                            float(kappa), (C.c_double * 3)(*fiber))
+
+
+def _workload_kwargs(w, pkw):
+    """Mesh, material and parameter keywords of a workloads.Workload."""
+    m = w.material
+    pkw.setdefault("iters", w.iters)
+    pkw.setdefault("history_m", w.history)
+    pkw.setdefault("h", w.h)
+    pkw.setdefault("gravity", w.gravity)
+    if getattr(w, "colliders", ()):
+        pkw.setdefault("colliders", w.colliders)
+        pkw.setdefault("contact_scale", w.contact_scale)
+    return (w.rest_pos, w.tets, w.clamped), dict(kind=m.kind, E=m.E, nu=m.nu, density=m.density,
+                                                 spline=m.spline, kappa=getattr(m, "kappa", 0.0),
+                                                 fiber=getattr(m, "fiber", (0.0, 0.0, 0.0)), **pkw)
+
+
+def analyse(rest_pos, tets, clamped=None, *, kind=NEOHOOKEAN, E=1e5, nu=0.45, density=1000.0,
+            spline=None, kappa=0.0, fiber=(0.0, 0.0, 0.0), params: Params | None = None, **pkw) -> dict:
+    """Host-only set-up statistics of one mesh (``hqn_analyse``; no GPU):
+    the factor's supernodes, levels and entries, the fitted stiffness."""
+    a = _MeshArgs(rest_pos, tets, clamped, kind, E, nu, density, spline, kappa, fiber)
+    p = params if params is not None else default_params(**pkw)
+    i = Info()
+    _check(library().hqn_analyse(C.byref(a.mesh), C.byref(a.mat), C.byref(p), C.byref(i)), "hqn_analyse")
+    return {f: getattr(i, f) for f, _ in Info._fields_}
+
+
+def analyse_workload(w, **pkw) -> dict:
+    args, kw = _workload_kwargs(w, pkw)
+    return analyse(*args, **kw)
+
+
 class Sim:
     """One simulation handle (``sim_create`` ... ``sim_destroy``)."""
 
@@ -190,35 +237,19 @@ class Sim:
                  density=1000.0, spline=None, kappa=0.0, fiber=(0.0, 0.0, 0.0),
                  params: Params | None = None, stream=None, **pkw):
         lib = library()
-        self._X = np.ascontiguousarray(rest_pos, dtype=np.float64)
-        self._tets = np.ascontiguousarray(tets, dtype=np.int32)
-        self.n = self._X.shape[0]
-        self._cl = None if clamped is None else np.ascontiguousarray(clamped, dtype=np.uint8)
-        mesh = Mesh(self.n, self._tets.shape[0], _ptr(self._X), _ptr(self._tets, _ip),
-                    None if self._cl is None else _ptr(self._cl, _up))
-        self._spline = None if spline is None else np.ascontiguousarray(spline, dtype=np.float64)
-        mat = Material(kind, E, nu, density, None if self._spline is None else _ptr(self._spline),
-                       float(kappa), (C.c_double * 3)(*fiber))
+        self._args = _MeshArgs(rest_pos, tets, clamped, kind, E, nu, density, spline, kappa, fiber)
+        self.n = self._args.n
         self.params = params if params is not None else default_params(**pkw)
         h = C.c_void_p()
-        _check(lib.sim_create(C.byref(mesh), C.byref(mat), C.byref(self.params),
+        _check(lib.sim_create(C.byref(self._args.mesh), C.byref(self._args.mat), C.byref(self.params),
                               C.c_void_p(stream or 0), C.byref(h)), "sim_create")
         self._h = h
         self.last_status = 0
 
     @classmethod
     def from_workload(cls, w, **pkw):
-        m = w.material
-        pkw.setdefault("iters", w.iters)
-        pkw.setdefault("history_m", w.history)
-        pkw.setdefault("h", w.h)
-        pkw.setdefault("gravity", w.gravity)
-        if getattr(w, "colliders", ()):
-            pkw.setdefault("colliders", w.colliders)
-            pkw.setdefault("contact_scale", w.contact_scale)
-        return cls(w.rest_pos, w.tets, w.clamped, kind=m.kind, E=m.E, nu=m.nu,
-                   density=m.density, spline=m.spline, kappa=getattr(m, "kappa", 0.0),
-                   fiber=getattr(m, "fiber", (0.0, 0.0, 0.0)), **pkw)
+        args, kw = _workload_kwargs(w, pkw)
+        return cls(*args, **kw)
 
     def close(self):
         if getattr(self, "_h", None):
