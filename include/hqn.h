@@ -287,6 +287,20 @@ int sim_get_state(sim_handle *sim, double *q_cur, double *q_prev);
  * NULL.  Returns the worst status over the steps (a warning keeps going). */
 int sim_step(sim_handle *sim, int32_t nsteps, hqn_step_stats *stats);
 
+/* Layouts of sim_positions_device (caller's vertex order, w = 0). */
+#define HQN_LAYOUT_F32X4 1  /* n_verts x {float x, y, z, w}  */
+#define HQN_LAYOUT_F64X4 2  /* n_verts x {double x, y, z, w} */
+
+/* Device copy of the current positions q_l (the state of Eq. PD) of
+ * simulation 0, for consumers that stay on the device (rendering, coupling).
+ * The buffer belongs to the handle (allocated on the first call) and is
+ * borrowed: it is complete when the call returns and valid until the next
+ * sim_positions_device, sim_step, sim_set_state or sim_destroy on the handle.
+ * *layout = HQN_LAYOUT_F32X4 in HQN_FP32_MIXED (rest position plus float32
+ * displacement, added in float32), HQN_LAYOUT_F64X4 in HQN_FP64_PLAIN.
+ * Errors: HQN_ERR_ARG (null argument), HQN_ERR_NO_MEMORY, HQN_ERR_CUDA. */
+int sim_positions_device(sim_handle *sim, void **dev_ptr, int32_t *layout);
+
 /* Evaluates g and grad g (Eq. PD) at positions x with inertial target y (both
  * n_verts x 3 host doubles).  grad is zero on clamped vertices.  g_out or
  * grad_out may be NULL.  Does not change the state. */

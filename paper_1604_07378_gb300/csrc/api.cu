@@ -59,6 +59,7 @@ struct SimBase {
     virtual int direction(const double *grad, int np, const double *s, const double *t, double *d) = 0;
     virtual void info(hqn_info *out) const = 0;
     virtual int time_stage(int stage, int reps, double *ms) = 0;
+    virtual int positions_device(void **ptr, int32_t *layout) = 0;
 };
 
 template <typename R>
@@ -78,6 +79,8 @@ struct Sim final : SimBase {
     int pipe_nbund[2] = {0, 0};  // bundles of the pipelined forward / backward sweeps
     int pipe_ndep[2] = {0, 0};   // cross-block waits of the pipelined forward / backward sweeps
     V4<R> *hbuf = nullptr;  // pinned staging buffer of the state transfers (largest simulation)
+    const int *d_perm0 = nullptr;  // simulation 0's caller ids by internal vertex (sim_positions_device)
+    V4<R> *d_pos0 = nullptr;       // its positions in caller order, borrowed by the caller
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     bool graph_mode = false;
@@ -1004,6 +1007,21 @@ struct Sim final : SimBase {
         if (rc) return rc;
         return put_vec(idx, ds.u_prev, qp ? qp : qc, true, false);
     }
+    int positions_device(void **ptr, int32_t *layout) override {
+        const Setup &s0 = S[0];
+        int rc = HQN_OK;
+        if (!d_pos0) {
+            if ((rc = upload(d_perm0, s0.perm.data(), (size_t)s0.n))) return rc;
+            if ((rc = alloc(d_pos0, (size_t)s0.n))) return rc;
+        }
+        launch_positions<R>(ds, d_perm0, hdesc[0].v0, s0.n, d_pos0, st);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(st));
+        *ptr = d_pos0;
+        *layout = sizeof(R) == 4 ? HQN_LAYOUT_F32X4 : HQN_LAYOUT_F64X4;
+        return HQN_OK;
+    }
+
     int get_state(int idx, double *qc, double *qp) override {
         if (idx < 0 || idx >= ns) return fail(HQN_ERR_ARG, "simulation index out of range");
         int rc = HQN_OK;
@@ -1465,6 +1483,13 @@ int sim_set_state(sim_handle *sim, const double *q_cur, const double *q_prev) {
 int sim_get_state(sim_handle *sim, double *q_cur, double *q_prev) {
     if (!sim) return fail(HQN_ERR_ARG, "null handle");
     try { return sim->impl->get_state(0, q_cur, q_prev); } catch (...) { return fail(HQN_ERR_NO_MEMORY, "exception"); }
+}
+
+int sim_positions_device(sim_handle *sim, void **dev_ptr, int32_t *layout) {
+    if (!sim || !dev_ptr || !layout) return fail(HQN_ERR_ARG, "null argument");
+    *dev_ptr = nullptr;
+    *layout = 0;
+    try { return sim->impl->positions_device(dev_ptr, layout); } catch (...) { return fail(HQN_ERR_NO_MEMORY, "exception"); }
 }
 
 int sim_batch_set_state(sim_handle *sim, int32_t index, const double *q_cur, const double *q_prev) {

@@ -1047,6 +1047,20 @@ __global__ void __launch_bounds__(VBS) k_commit(DevSim<R> s) {
     }
 }
 
+// Absolute positions x_v = X_v + u_v of n vertices starting at batch vertex
+// v0, written in the caller's vertex order (out[perm[i]], perm[i] < n).
+template <typename R>
+__global__ void __launch_bounds__(VBS) k_positions(const V4<R> *rest, const V4<R> *u, const int *perm, int v0, int n,
+                                                   V4<R> *out) {
+    const int i = blockIdx.x * VBS + threadIdx.x;
+    if (i < n) {
+        const V4<R> X = rest[v0 + i], d = u[v0 + i];
+        V4<R> o;
+        o.x = X.x + d.x; o.y = X.y + d.y; o.z = X.z + d.z; o.w = R(0);
+        out[perm[i]] = o;
+    }
+}
+
 // Caller-given history of simulation 0 (sim_direction): row `a` of the Gram
 // matrix, s_a^T t_b for the slots b < count, rho_a = s_a^T t_a and
 // s_a^T grad.  With a == count - 1 the last block also runs the first loop
@@ -1164,6 +1178,10 @@ template <typename R> void launch_pcg(const DevSim<R> &s, const V4<R> *q, V4<R> 
 template <typename R> void launch_commit(const DevSim<R> &s, cudaStream_t st) {
     k_commit<R><<<s.nvb, VBS, 0, st>>>(s);
 }
+template <typename R> void launch_positions(const DevSim<R> &s, const int *perm, int v0, int n, V4<R> *out,
+                                            cudaStream_t st) {
+    if (n > 0) k_positions<R><<<(n + VBS - 1) / VBS, VBS, 0, st>>>(s.rest, s.u_cur, perm, v0, n, out);
+}
 template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream_t st, int nblocks) {
     k_hist_row<R><<<nblocks, VBS, 0, st>>>(s, a);
 }
@@ -1180,7 +1198,8 @@ template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream
     template void launch_reset_history<R>(const DevSim<R> &, cudaStream_t);          \
     template void launch_commit<R>(const DevSim<R> &, cudaStream_t);                 \
     template void launch_pcg<R>(const DevSim<R> &, const V4<R> *, V4<R> *, int, cudaStream_t); \
-    template void launch_hist_row<R>(const DevSim<R> &, int, cudaStream_t, int);
+    template void launch_hist_row<R>(const DevSim<R> &, int, cudaStream_t, int);       \
+    template void launch_positions<R>(const DevSim<R> &, const int *, int, int, V4<R> *, cudaStream_t);
 
 HQN_INST(float)
 HQN_INST(double)

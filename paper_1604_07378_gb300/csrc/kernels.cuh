@@ -89,6 +89,9 @@ template <typename R> void launch_reset_history(const DevSim<R> &s, cudaStream_t
 // (matrix-free A0 = M/h^2 + sum_t V_t k G_t^T G_t; 1 + 3 iters launches).
 template <typename R> void launch_pcg(const DevSim<R> &s, const V4<R> *q, V4<R> *out, int iters, cudaStream_t st);
 template <typename R> void launch_commit(const DevSim<R> &s, cudaStream_t st);
+// out[perm[i]] = X + u_cur of the n vertices from batch vertex v0 (caller order).
+template <typename R> void launch_positions(const DevSim<R> &s, const int *perm, int v0, int n, V4<R> *out,
+                                            cudaStream_t st);
 // Caller-given history of simulation 0: Gram row a, rho_a and s_a^T grad
 // (run for a = 0..count-1).
 template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream_t st, int nblocks);

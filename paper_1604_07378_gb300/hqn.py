@@ -16,6 +16,7 @@ from . import build as _build
 HQN_OK = 0
 HQN_WARN_LS_EXHAUSTED = 1
 HQN_WARN_NONDESCENT = 2
+LAYOUT_F32X4, LAYOUT_F64X4 = 1, 2
 HQN_ERR_ARG = -1
 HQN_ERR_DEGENERATE_TET = -2
 HQN_ERR_NONFINITE = -3
@@ -118,6 +119,7 @@ def library(path: str | None = None):
     lib.sim_direction.argtypes = [C.c_void_p, _dp, C.c_int32, _dp, _dp, _dp]
     lib.sim_get_info.argtypes = [C.c_void_p, C.POINTER(Info)]
     lib.hqn_analyse.argtypes = [C.POINTER(Mesh), C.POINTER(Material), C.POINTER(Params), C.POINTER(Info)]
+    lib.sim_positions_device.argtypes = [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int32)]
     lib.sim_time_stage.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _dp]
     lib.sim_destroy.argtypes = [C.c_void_p]
     lib.sim_destroy.restype = None
@@ -337,6 +339,21 @@ class Sim:
         i = Info()
         _check(library().sim_get_info(self._h, C.byref(i)), "sim_get_info")
         return {f: getattr(i, f) for f, _ in Info._fields_}
+
+    def positions_device(self):
+        """``sim_positions_device``: a torch view (n x 4, float32 or float64,
+        caller's vertex order, w = 0) of the handle's device copy of q_l.
+        The view borrows the handle's buffer: it is valid until the next
+        positions_device, step, set_state or close."""
+        import torch
+        ptr, layout = C.c_void_p(), C.c_int32()
+        _check(library().sim_positions_device(self._h, C.byref(ptr), C.byref(layout)), "sim_positions_device")
+        typestr = {LAYOUT_F32X4: "<f4", LAYOUT_F64X4: "<f8"}[layout.value]
+
+        class _View:
+            __cuda_array_interface__ = {"shape": (self.n, 4), "typestr": typestr,
+                                        "data": (ptr.value, False), "version": 3, "strides": None}
+        return torch.as_tensor(_View(), device="cuda")
 
 
 class Batch:

@@ -278,3 +278,23 @@ def test_merged_supernodes_shorten_the_sweeps():
     with pytest.raises(hqn.HQNError) as e:
         sim_for(LAT30, FP32, merge_depths=3)
     assert e.value.code == hqn.HQN_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_positions_device_is_the_state(prec):
+    """sim_positions_device: the device copy of q_l in the caller's vertex
+    order equals the state sim_get_state downloads (FP64: bit for bit; FP32:
+    rest + displacement added in float32, within one float32 rounding of
+    the coordinates)."""
+    w = WORKLOADS[1]
+    with sim_for(w, prec) as sim:
+        sim.set_state(w.q_cur, w.q_prev)
+        sim.step(2)
+        x, _ = sim.get_state()
+        t = sim.positions_device()
+        p = t.double().cpu().numpy()
+    assert p.shape == (w.n_verts, 4) and np.all(p[:, 3] == 0.0)
+    if prec == FP64:
+        np.testing.assert_array_equal(p[:, :3], x)
+    else:
+        assert np.abs(p[:, :3] - x).max() <= 2 ** -23 * np.abs(x).max() * 2
