@@ -49,7 +49,7 @@ extern "C" {
 #define HQN_ERR_NOT_SPD          -4  /* A0 is not positive definite               */
 #define HQN_ERR_CUDA             -5  /* a CUDA runtime call failed                */
 #define HQN_ERR_NO_MEMORY        -6  /* host or device allocation failed          */
-#define HQN_ERR_UNSUPPORTED      -7  /* option not available in this build        */
+#define HQN_ERR_UNSUPPORTED      -7  /* option or size the library does not support */
 
 /* ---- materials (Eq. valanis-landel: Psi = sum a(s_i) + sum b(s_i s_j) + c(J)) */
 typedef enum {
