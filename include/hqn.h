@@ -73,13 +73,19 @@ typedef enum {
 typedef enum {
     HQN_COLLIDER_PLANE  = 1,  /* point[3] on the plane, normal[3] towards the free side
                                  (normalised by the library)                         */
-    HQN_COLLIDER_SPHERE = 2   /* centre point[3], radius; the body stays outside      */
+    HQN_COLLIDER_SPHERE = 2,  /* centre point[3], radius; the body stays outside      */
+    HQN_COLLIDER_TORUS  = 3   /* centre point[3], axis normal[3] (normalised by the
+                                 library), ring radius major_radius, tube radius
+                                 radius (0 < radius < major_radius); the body stays
+                                 outside the tube.  Vertices on the axis or on the
+                                 ring circle have no unique normal and get no term */
 } hqn_collider_kind;
 typedef struct {
     int32_t kind;             /* hqn_collider_kind */
     double  point[3];
     double  normal[3];
     double  radius;
+    double  major_radius;     /* HQN_COLLIDER_TORUS only */
 } hqn_collider;
 
 typedef struct {

@@ -33,7 +33,8 @@ taken by the CUDA path, written separately):
   * Alg. 3 (the Chebyshev direction) reads x_0 := x_1 (its first S
     directions have omega = 1, where x_{k-1} cancels) and keeps no history;
   * collisions (Sec. 4.3) against analytic colliders (a plane with its
-    normal, or a sphere the body stays outside of): at the start of every
+    normal, a sphere the body stays outside of, or a torus -- the paper's
+    examples are a ground plane and a torus): at the start of every
     iteration, before the gradient at x_k, each free vertex that penetrates a
     collider (signed distance < 0) and does not move away from it (its
     displacement over the step, x_k - q_l, has a non-positive normal
@@ -323,7 +324,8 @@ class Problem:
     free: np.ndarray = None
     A: sp.csc_matrix = None
     _solver: object = None
-    colliders: tuple = ()        # ("plane", point, normal) or ("sphere", centre, radius)
+    colliders: tuple = ()        # ("plane", point, normal), ("sphere", centre, radius) or
+                                 # ("torus", centre, axis, ring radius, tube radius)
     contact_scale: float = 100.0
 
     @property
@@ -504,6 +506,21 @@ def contact_terms(P: Problem, x, q_ref):
             dist = np.linalg.norm(rel, axis=1)
             phi = np.where(dist > 0.0, dist - r, np.inf)  # at the centre: no normal, no term
             n = rel / np.maximum(dist, 1e-300)[:, None]
+        elif col[0] == "torus":
+            # ring of radius R about the axis a through c, tube radius r: the
+            # nearest surface point lies on the segment from x to the nearest
+            # point of the ring circle, at distance r from that point
+            c, a = np.asarray(col[1], float), np.asarray(col[2], float)
+            R, r = float(col[3]), float(col[4])
+            a = a / np.linalg.norm(a)
+            rel = x - c
+            radial = rel - np.outer(rel @ a, a)
+            rho = np.linalg.norm(radial, axis=1)
+            v = rel - (R / np.maximum(rho, 1e-300))[:, None] * radial
+            dist = np.linalg.norm(v, axis=1)
+            # on the axis or on the ring circle: no unique normal, no term
+            phi = np.where((rho > 0.0) & (dist > 0.0), dist - r, np.inf)
+            n = v / np.maximum(dist, 1e-300)[:, None]
         else:
             raise ValueError(f"unknown collider {col[0]!r}")
         vn = np.sum((x - q_ref) * n, axis=1)

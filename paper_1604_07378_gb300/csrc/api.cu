@@ -271,10 +271,11 @@ struct Sim final : SimBase {
                 const double nn = std::sqrt(hc.normal[0] * hc.normal[0] + hc.normal[1] * hc.normal[1] +
                                             hc.normal[2] * hc.normal[2]);
                 dc.nx = dc.ny = dc.nz = R(0);
-                if (hc.kind == HQN_COLLIDER_PLANE) {
+                if (hc.kind == HQN_COLLIDER_PLANE || hc.kind == HQN_COLLIDER_TORUS) {
                     dc.nx = (R)(hc.normal[0] / nn); dc.ny = (R)(hc.normal[1] / nn); dc.nz = (R)(hc.normal[2] / nn);
                 }
                 dc.r = (R)hc.radius;
+                dc.ring = hc.kind == HQN_COLLIDER_TORUS ? (R)hc.major_radius : R(0);
             }
             MatDev<R> &M = D.mat;
             M.kind = s.mat.kind;
@@ -1396,6 +1397,11 @@ int validate_params(const hqn_params *params) {
             if (!(nn > 0.0) || !std::isfinite(nn)) return fail(HQN_ERR_ARG, "a plane collider needs a nonzero normal");
         } else if (c.kind == HQN_COLLIDER_SPHERE) {
             if (!(c.radius > 0.0) || !std::isfinite(c.radius)) return fail(HQN_ERR_ARG, "a sphere collider needs a positive radius");
+        } else if (c.kind == HQN_COLLIDER_TORUS) {
+            const double nn = c.normal[0] * c.normal[0] + c.normal[1] * c.normal[1] + c.normal[2] * c.normal[2];
+            if (!(nn > 0.0) || !std::isfinite(nn)) return fail(HQN_ERR_ARG, "a torus collider needs a nonzero axis");
+            if (!(c.radius > 0.0 && c.radius < c.major_radius) || !std::isfinite(c.major_radius))
+                return fail(HQN_ERR_ARG, "a torus collider needs 0 < radius < major_radius");
         } else {
             return fail(HQN_ERR_ARG, "unknown collider kind");
         }

@@ -97,7 +97,8 @@ struct CondHandles {
 template <typename R>
 struct ColDev {
     int kind;
-    R px, py, pz, nx, ny, nz, r;
+    R px, py, pz, nx, ny, nz, r;  // point / centre, unit normal / axis, radius (tube radius)
+    R ring;                       // torus ring radius
 };
 
 // Per-simulation constants passed by value.

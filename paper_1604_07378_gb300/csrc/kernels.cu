@@ -146,6 +146,20 @@ __device__ __forceinline__ void for_contacts(const StepConst<R> &c, const V4<R> 
         if (q.kind == HQN_COLLIDER_PLANE) {
             nx = q.nx; ny = q.ny; nz = q.nz;
             gap = rx * nx + ry * ny + rz * nz;
+        } else if (q.kind == HQN_COLLIDER_TORUS) {
+            // nearest point of the ring circle: the radial part of x - c
+            // scaled to the ring radius; the surface lies `r` from it
+            const R hgt = rx * q.nx + ry * q.ny + rz * q.nz;
+            const R ax = rx - hgt * q.nx, ay = ry - hgt * q.ny, az = rz - hgt * q.nz;
+            const R rho = sqrt_(ax * ax + ay * ay + az * az);
+            if (!(rho > R(0))) continue;  // on the axis: no nearest ring point
+            const R sc = q.ring / rho;
+            const R vx = rx - sc * ax, vy = ry - sc * ay, vz = rz - sc * az;
+            const R dist = sqrt_(vx * vx + vy * vy + vz * vz);
+            if (!(dist > R(0))) continue;  // on the ring circle: no normal
+            const R inv = R(1) / dist;
+            nx = vx * inv; ny = vy * inv; nz = vz * inv;
+            gap = dist - q.r;
         } else {
             const R dist = sqrt_(rx * rx + ry * ry + rz * rz);
             if (!(dist > R(0))) continue;  // at the centre: no normal

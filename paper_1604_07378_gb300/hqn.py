@@ -48,12 +48,12 @@ class Material(C.Structure):
 
 
 MAX_COLLIDERS = 4
-COLLIDER_PLANE, COLLIDER_SPHERE = 1, 2
+COLLIDER_PLANE, COLLIDER_SPHERE, COLLIDER_TORUS = 1, 2, 3
 
 
 class Collider(C.Structure):
     _fields_ = [("kind", C.c_int32), ("point", C.c_double * 3), ("normal", C.c_double * 3),
-                ("radius", C.c_double)]
+                ("radius", C.c_double), ("major_radius", C.c_double)]
 
 
 class Params(C.Structure):
@@ -169,7 +169,8 @@ def default_params(**kw) -> Params:
                 raise ValueError(f"at most {MAX_COLLIDERS} colliders")
             p.n_colliders = len(cols)
             for i, c in enumerate(cols):
-                # workloads.Collider or a ("plane", point, normal) / ("sphere", centre, radius) tuple
+                # workloads.Collider or a ("plane", point, normal) / ("sphere", centre, radius) /
+                # ("torus", centre, axis, ring radius, tube radius) tuple
                 t = c.as_tuple() if hasattr(c, "as_tuple") else tuple(c)
                 cc = p.colliders[i]
                 cc.point[:] = list(t[1])
@@ -179,6 +180,11 @@ def default_params(**kw) -> Params:
                 elif t[0] == "sphere":
                     cc.kind = COLLIDER_SPHERE
                     cc.radius = float(t[2])
+                elif t[0] == "torus":
+                    cc.kind = COLLIDER_TORUS
+                    cc.normal[:] = list(t[2])
+                    cc.major_radius = float(t[3])
+                    cc.radius = float(t[4])
                 else:
                     raise ValueError(f"unknown collider {t[0]!r}")
         else:

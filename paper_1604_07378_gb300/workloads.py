@@ -51,15 +51,19 @@ class Material:
 @dataclass
 class Collider:
     """An analytic collider: a plane (point on it, normal pointing to the free
-    side) or a sphere the body stays outside of (centre, radius)."""
-    kind: str                     # "plane" or "sphere"
-    point: tuple                  # a point of the plane, or the sphere's centre
+    side), a sphere the body stays outside of (centre, radius) or a torus
+    (centre, axis as `normal`, ring radius `major`, tube radius `radius`)."""
+    kind: str                     # "plane", "sphere" or "torus"
+    point: tuple                  # a point of the plane, or the sphere's / torus's centre
     normal: tuple = (0.0, 0.0, 1.0)
     radius: float = 0.0
+    major: float = 0.0
 
     def as_tuple(self):
         if self.kind == "plane":
             return ("plane", tuple(self.point), tuple(self.normal))
+        if self.kind == "torus":
+            return ("torus", tuple(self.point), tuple(self.normal), float(self.major), float(self.radius))
         return ("sphere", tuple(self.point), float(self.radius))
 
 
@@ -280,13 +284,16 @@ def fiber_cube(n: int = 8, kappa_scale: float = 5.0, fiber=(1.0, 1.0, 0.0), v: f
 
 
 def collision_drop(n: int = 8, drop: float = 0.02, speed: float = 2.0, sphere: bool = True,
-                   kind: int = NEOHOOKEAN, E: float = 2e5, name: str = "") -> Workload:
+                   kind: int = NEOHOOKEAN, E: float = 2e5, name: str = "", torus: bool = False) -> Workload:
     """An unclamped n^3 Neo-Hookean cube falling onto the ground plane z = 0
     (Sec. 4.3's collision terms), its lowest face `drop` above it, every
     vertex moving down at `speed` m/s; with `sphere`, a sphere of radius
     n*edge/4, sunk into the ground so that its top is just below the cube,
     sits under one corner of the cube's footprint: that corner lands on it
-    first."""
+    first.  With `torus`, a ring (axis z, centred under the cube, ring
+    radius n*edge/4, tube radius n*edge/8) lies sunk into the ground with
+    its top just below the cube, in place of the sphere: the vertices above
+    the ring land on its tube first."""
     edge = 0.05
     w = lattice_workload((n, n, n), Material(kind, E, 0.4), clamp_axis=-1, seed=1609, name=name or f"drop{n}")
     shift = np.array([-0.5 * n * edge, -0.5 * n * edge, drop])
@@ -294,7 +301,11 @@ def collision_drop(n: int = 8, drop: float = 0.02, speed: float = 2.0, sphere: b
     w.q_cur = w.rest_pos + shift
     w.q_prev = w.q_cur - w.h * v
     cols = [Collider("plane", (0.0, 0.0, 0.0), (0.0, 0.0, 1.0))]
-    if sphere:
+    if torus:
+        r = n * edge / 8.0
+        top = 0.5 * drop
+        cols.append(Collider("torus", (0.0, 0.0, top - r), (0.0, 0.0, 1.0), radius=r, major=n * edge / 4.0))
+    elif sphere:
         r = 0.25 * n * edge
         top = 0.5 * drop  # the sphere's top, between the ground and the cube
         cols.append(Collider("sphere", (-0.25 * n * edge, -0.25 * n * edge, top - r), radius=r))

@@ -93,3 +93,19 @@ def test_rejects_degenerate_and_bad_input(hqn, lat12):
     with pytest.raises(hqn.HQNError) as e:
         hqn.analyse(w.rest_pos, w.tets, np.ones(w.n_verts, np.uint8), kind=W.NEOHOOKEAN, E=5e5, nu=0.4)
     assert e.value.code == hqn.HQN_ERR_ARG
+
+
+def test_collider_parameters_are_checked(hqn):
+    """The parameter checks sim_create shares with the analysis: a torus
+    needs 0 < tube radius < ring radius and a nonzero axis; a sphere a
+    positive radius; a plane a nonzero normal."""
+    w = W.collision_drop(2, torus=True)
+    assert hqn.analyse_workload(w)["n_free"] == w.n_verts  # the drop is unclamped
+    bad = [W.Collider("torus", (0.0, 0.0, 0.0), (0.0, 0.0, 1.0), radius=0.2, major=0.1),
+           W.Collider("torus", (0.0, 0.0, 0.0), (0.0, 0.0, 0.0), radius=0.1, major=0.2),
+           W.Collider("sphere", (0.0, 0.0, 0.0), radius=0.0),
+           W.Collider("plane", (0.0, 0.0, 0.0), (0.0, 0.0, 0.0))]
+    for c in bad:
+        with pytest.raises(hqn.HQNError) as e:
+            hqn.analyse_workload(w, colliders=(c,))
+        assert e.value.code == hqn.HQN_ERR_ARG, c

@@ -1,5 +1,5 @@
 """Collision terms (Sec. 4.3) on the GPU against the oracle: a cube falling
-onto a ground plane and a sphere.  The active set is decided per vertex at
+onto a ground plane and a sphere, or a ground plane and a torus.  The active set is decided per vertex at
 the start of every iteration in both; FP64 is held to round-off, FP32 to the
 method's position tolerance."""
 import numpy as np
@@ -108,6 +108,52 @@ def test_batch_with_contacts_bitwise_equal_to_single_handles():
             sim.set_state(w.q_cur, w.q_prev)
             sim.step(4)
             np.testing.assert_array_equal(got[i], sim.get_state()[0])
+
+
+def _on_torus():
+    """The drop onto the ring (in place of the sphere), advanced by the oracle
+    until vertices press on the torus tube."""
+    w = W.collision_drop(4, drop=0.004, speed=2.0, torus=True)
+    P = problem_for(w)
+    qc, qp = w.q_cur.copy(), w.q_prev.copy()
+    for _ in range(2):
+        x, _ = O.solve_step(P, qc, qp, iters=10, m=5)
+        qp, qc = qc, x
+    return w, P, qc, qp
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_torus_contacts_energy_gradient_and_step(prec):
+    """Contacts with a torus (the ground plane and a ring, Sec. 4.3's
+    examples): g and its gradient at a point between the state and the
+    predictor, then one whole step, against the oracle."""
+    w, P, qc, qp = _on_torus()
+    y = O.predictor(P, qc, qp)
+    x = qc + 0.5 * (y - qc)
+    C = O.contact_terms(P, x, qc)
+    assert np.sum(np.abs(C.n[:, 2]) < 0.999) > 0  # some normals are the tube's
+    g_ref, grad_ref = O.objective(P, x, y, C), O.gradient(P, x, y, C)
+    x_ref, st = O.solve_step(P, qc, qp, iters=w.iters, m=w.history)
+    with sim_for(w, prec) as sim:
+        sim.set_state(qc, qp)
+        g, grad = sim.energy_grad(x, y)
+        rc, stats = sim.step(1, stats=True)
+        xs, _ = sim.get_state()
+    assert rel(grad, grad_ref) <= (1e-11 if prec == FP64 else 1e-5), rel(grad, grad_ref)
+    assert abs(g - g_ref) <= (1e-11 if prec == FP64 else 2e-6) * abs(g_ref)
+    assert rc >= 0
+    assert rel(xs, x_ref) <= (1e-9 if prec == FP64 else 1e-4), rel(xs, x_ref)
+    if prec == FP64:
+        assert stats["trials"] == st.trials
+
+
+def test_torus_parameters_are_checked():
+    from paper_1604_07378_gb300 import hqn
+    w = W.collision_drop(2, torus=True)
+    bad = W.Collider("torus", (0.0, 0.0, 0.0), (0.0, 0.0, 1.0), radius=0.2, major=0.1)  # tube wider than the ring
+    with pytest.raises(hqn.HQNError) as e:
+        sim_for(w, FP32, colliders=(bad,))
+    assert e.value.code == hqn.HQN_ERR_ARG
 
 
 # ---------------------------------------------------------------- anisotropic fibre term (Sec. 4.4)

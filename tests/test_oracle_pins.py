@@ -9,6 +9,8 @@ import json
 import math
 import os
 
+import types
+
 import numpy as np
 import pytest
 import scipy.linalg
@@ -566,3 +568,81 @@ def test_relative_error_ordering_on_twisted_bar():
         _, st = O.solve_step(P, w.q_cur, w.q_prev, iters=40, **kw)
         err[name] = O.relative_error(st.g[-1], st.g0, g_star)
     assert 0.0 <= err["lbfgs5"] < err["cheb"] < err["pd"] < 1.0, err
+
+
+def _torus_surface_distance(x, c, a, R, r, n_theta=720, n_phi=360):
+    """Brute force: the distance from x to a dense sampling of the torus
+    surface c + (R + r cos phi) e(theta) + r sin phi a."""
+    a = np.asarray(a, float) / np.linalg.norm(a)
+    e1 = np.cross(a, [1.0, 0.0, 0.0])
+    if np.linalg.norm(e1) < 1e-6:
+        e1 = np.cross(a, [0.0, 1.0, 0.0])
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(a, e1)
+    th = np.linspace(0.0, 2 * np.pi, n_theta, endpoint=False)
+    ph = np.linspace(0.0, 2 * np.pi, n_phi, endpoint=False)
+    T, Ph = np.meshgrid(th, ph, indexing="ij")
+    ring = np.cos(T)[..., None] * e1 + np.sin(T)[..., None] * e2
+    pts = c + (R + r * np.cos(Ph))[..., None] * ring + (r * np.sin(Ph))[..., None] * a
+    d = np.linalg.norm(pts.reshape(-1, 3) - x, axis=1)
+    k = int(np.argmin(d))
+    return d[k], pts.reshape(-1, 3)[k]
+
+
+def test_torus_contact_projection_against_brute_force():
+    """For points inside the tube of a tilted torus, the surface point t is
+    the nearest point of the surface (brute force over a dense (theta, phi)
+    grid), |x - t| = -phi, n is the unit vector from t towards the tube's
+    centre circle's outside, and points outside the tube, on the axis or in
+    the hole are not in contact."""
+    c, a, R, r = np.array([0.1, -0.2, 0.3]), np.array([1.0, 2.0, 2.0]) / 3.0, 0.5, 0.15
+    col = ("torus", tuple(c), tuple(a), R, r)
+    e1 = np.cross(a, [1.0, 0.0, 0.0]); e1 /= np.linalg.norm(e1)
+    e2 = np.cross(a, e1)
+    rng = np.random.default_rng(17)
+    pts = []
+    for _ in range(6):  # inside the tube at random angles and depths
+        th, ph, rr = rng.uniform(0, 2 * np.pi), rng.uniform(0, 2 * np.pi), rng.uniform(0.2, 0.9) * r
+        ring = np.cos(th) * e1 + np.sin(th) * e2
+        pts.append(c + (R + rr * np.cos(ph)) * ring + rr * np.sin(ph) * a)
+    pts.append(c + (R + 1.5 * r) * e1)      # outside the tube
+    pts.append(c + 0.3 * a)                  # on the axis (in the hole)
+    pts.append(c + 0.5 * (R - r) * e2)       # in the hole, off the axis
+    x = np.array(pts)
+    # contact_terms reads only these fields of a problem
+    P = types.SimpleNamespace(n=x.shape[0], free=np.arange(x.shape[0]), colliders=(col,),
+                              contact_scale=1.0, mass=np.ones(x.shape[0]), h=1.0)
+    C = O.contact_terms(P, x, x)   # not moving: vn = 0 keeps every penetrating vertex
+    assert list(C.idx) == list(range(6))
+    for k, v in enumerate(C.idx):
+        d_bf, p_bf = _torus_surface_distance(x[v], c, a, R, r)
+        depth = np.linalg.norm(x[v] - C.t[k])
+        assert abs(depth - d_bf) <= 2e-3 * r, (depth, d_bf)
+        assert np.linalg.norm(C.t[k] - p_bf) <= 0.02 * r
+        assert abs(np.linalg.norm(C.n[k]) - 1.0) <= 1e-14
+        # x lies on the inward side: x = t - depth n
+        np.testing.assert_allclose(x[v], C.t[k] - depth * C.n[k], atol=1e-14)
+
+
+def test_torus_contact_gradient_matches_central_differences():
+    """The cube dropped onto the ring, one step after the first contact: the
+    torus terms' gradient is the derivative of their energy."""
+    w = W.collision_drop(4, drop=0.004, speed=2.0, torus=True)
+    P = O.problem_from_workload(w)
+    qc, _ = O.solve_step(P, w.q_cur, w.q_prev, iters=10, m=5)
+    qp = w.q_cur
+    y = O.predictor(P, qc, qp)
+    rng = np.random.default_rng(5)
+    x = y + 1e-4 * rng.normal(size=y.shape)
+    C = O.contact_terms(P, x, qc)
+    tor = [k for k in range(C.idx.size) if abs(C.n[k, 2]) < 0.999]  # normals off the plane's
+    assert len(tor) > 0
+    g = O.gradient(P, x, y, C)
+    eps = 1e-6
+    for k in tor[:3]:
+        v = C.idx[k]
+        for cc in range(3):
+            xp = x.copy(); xp[v, cc] += eps
+            xm = x.copy(); xm[v, cc] -= eps
+            fd = (O.objective(P, xp, y, C) - O.objective(P, xm, y, C)) / (2 * eps)
+            assert abs(fd - g[v, cc]) <= 1e-6 * max(1.0, abs(g[v, cc])), (v, cc, fd, g[v, cc])
