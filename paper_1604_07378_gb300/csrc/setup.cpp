@@ -820,59 +820,4 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
     return HQN_OK;
 }
 
-void host_solve(const Setup &S, const double *q, double *r) {
-    const int nf = S.n_free;
-    std::vector<double> z(3 * (size_t)nf, 0.0), u(3 * (size_t)S.n_upd, 0.0);
-    // forward: level by level, children first
-    for (int l = 0; l < S.n_levels; ++l)
-        for (size_t s = 0; s < S.sn.size(); ++s) {
-            const SupernodeHost &sn = S.sn[s];
-            if (sn.level != l) continue;
-            const int nc = sn.ncol, rows = nc + sn.nrow;
-            std::vector<double> f(3 * (size_t)nc);
-            for (int p = 0; p < nc; ++p) {
-                const int j = sn.col + p;
-                for (int a = 0; a < 3; ++a) f[3 * p + a] = q[3 * (size_t)j + a];
-                for (int e = S.fg_ptr[j]; e < S.fg_ptr[j + 1]; ++e)
-                    for (int a = 0; a < 3; ++a) f[3 * p + a] -= u[3 * (size_t)S.fg_idx[e] + a];
-            }
-            const double *Qs = S.Q.data() + sn.qoff;
-            for (int i = 0; i < rows; ++i) {
-                double acc[3] = {0, 0, 0};
-                const int jn = i < nc ? i + 1 : nc;
-                for (int j = 0; j < jn; ++j)
-                    for (int a = 0; a < 3; ++a) acc[a] += Qs[(size_t)i * nc + j] * f[3 * j + a];
-                if (i < nc) {
-                    for (int a = 0; a < 3; ++a) z[3 * (size_t)(sn.col + i) + a] = acc[a];
-                } else {
-                    const int ui = sn.uoff + i - nc;
-                    for (int e = S.ug_ptr[ui]; e < S.ug_ptr[ui + 1]; ++e)
-                        for (int a = 0; a < 3; ++a) acc[a] += u[3 * (size_t)S.ug_idx[e] + a];
-                    for (int a = 0; a < 3; ++a) u[3 * (size_t)ui + a] = acc[a];
-                }
-            }
-        }
-    // backward: x_s = Q_s^T [z_s; -x_R], root first
-    for (int l = S.n_levels - 1; l >= 0; --l)
-        for (size_t s = 0; s < S.sn.size(); ++s) {
-            const SupernodeHost &sn = S.sn[s];
-            if (sn.level != l) continue;
-            const int nc = sn.ncol, rows = nc + sn.nrow;
-            const double *Qs = S.Q.data() + sn.qoff;
-            for (int j = 0; j < nc; ++j) {
-                double acc[3] = {0, 0, 0};
-                for (int i = j; i < rows; ++i) {
-                    const double qij = Qs[(size_t)i * nc + j];
-                    if (i < nc) {
-                        for (int a = 0; a < 3; ++a) acc[a] += qij * z[3 * (size_t)(sn.col + i) + a];
-                    } else {
-                        const int v = S.rows[sn.roff + i - nc];
-                        for (int a = 0; a < 3; ++a) acc[a] -= qij * r[3 * (size_t)v + a];
-                    }
-                }
-                for (int a = 0; a < 3; ++a) r[3 * (size_t)(sn.col + j) + a] = acc[a];
-            }
-        }
-}
-
 }  // namespace hqn

@@ -99,9 +99,5 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &mat, const hqn_params 
 // Fits the stiffness k of Eq. stiffness for a material (used by build_setup).
 double fit_stiffness(const MaterialHost &m, double x_start, double x_end);
 
-// Host float64 execution of the device solve algorithm (same operators, same
-// order of work): r = A0^{-1} q on the first n_free entries, 3 right-hand sides
-// stored as n_free x 3.
-void host_solve(const Setup &S, const double *q, double *r);
 
 }  // namespace hqn
