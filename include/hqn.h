@@ -99,7 +99,8 @@ typedef struct {
 
 typedef struct {
     int32_t       kind;       /* hqn_material_kind                                    */
-    double        E, nu;      /* Young's modulus [Pa], Poisson ratio -> mu, lambda    */
+    double        E, nu;      /* Young's modulus [Pa] > 0, Poisson ratio in (-1, 0.5)
+                                 -> mu, lambda (HQN_ERR_ARG otherwise)               */
     double        density;    /* [kg/m^3]; lumped mass m_v = density * sum V_t / 4    */
     const double *spline;     /* HQN_SPLINE_VL only: 3 x 8 x 3 doubles, function
                                  (a, b, c) x knot x (knot, value, slope), knots
@@ -134,8 +135,9 @@ typedef struct {
     int32_t ls_batch;     /* line search: the first trial (alpha = 1) is one tet pass
                              fused with the gradient; after a rejection each pass
                              tests ls_batch step lengths (1, 2, 4, 8 or 16; 0 =
-                             default 8).  The accepted alpha is the one Alg. 1's
-                             sequential backtracking would accept                  */
+                             default 8; other values HQN_ERR_ARG).  The accepted
+                             alpha is the one Alg. 1's sequential backtracking
+                             would accept                                          */
     int32_t dyn_sweeps;   /* triangular sweeps: 0 = one launch per tree level,
                              chained by programmatic dependent launch (default);
                              1 = dependency-driven (one persistent launch per

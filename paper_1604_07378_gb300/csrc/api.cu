@@ -1408,6 +1408,9 @@ int validate_params(const hqn_params *params) {
     }
     if (params->tet_block != 0 && params->tet_block != TBS)
         return fail(HQN_ERR_UNSUPPORTED, "tet_block must be 0 or 128");
+    const int lb = params->ls_batch;
+    if (lb != 0 && lb != 1 && lb != 2 && lb != 4 && lb != 8 && lb != 16)
+        return fail(HQN_ERR_ARG, "ls_batch must be 0, 1, 2, 4, 8 or 16");
     return HQN_OK;
 }
 

@@ -415,6 +415,10 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
         err = "material density must be positive and E, nu finite";
         return matin.density <= 0 ? HQN_ERR_NOT_SPD : HQN_ERR_NONFINITE;
     }
+    if (!(matin.E > 0) || !(matin.nu > -1.0 && matin.nu < 0.5)) {
+        err = "material needs E > 0 and -1 < nu < 0.5";
+        return HQN_ERR_ARG;
+    }
 
     // ---- material
     MaterialHost &M = S.mat;

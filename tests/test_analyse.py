@@ -85,6 +85,19 @@ def test_rejects_degenerate_and_bad_input(hqn, lat12):
     with pytest.raises(hqn.HQNError) as e:
         hqn.analyse_workload(w, precision=7)
     assert e.value.code == hqn.HQN_ERR_ARG
+    for kw in (dict(ls_batch=3), dict(history_m=hqn.MAX_HISTORY + 1), dict(h=0.0), dict(gamma=1.0)):
+        with pytest.raises(hqn.HQNError) as e:
+            hqn.analyse_workload(w, **kw)
+        assert e.value.code == hqn.HQN_ERR_ARG, kw
+    for E, nu in ((-1.0, 0.4), (5e5, 0.5), (5e5, -1.0)):
+        with pytest.raises(hqn.HQNError) as e:
+            hqn.analyse(w.rest_pos, w.tets, w.clamped, kind=W.NEOHOOKEAN, E=E, nu=nu)
+        assert e.value.code == hqn.HQN_ERR_ARG, (E, nu)
+    X = w.rest_pos.copy()
+    X[5, 1] = np.nan
+    with pytest.raises(hqn.HQNError) as e:
+        hqn.analyse(X, w.tets, w.clamped, kind=W.NEOHOOKEAN, E=5e5, nu=0.4)
+    assert e.value.code == hqn.HQN_ERR_NONFINITE
     tets = w.tets.copy()
     tets[0, 0] = w.n_verts  # vertex index out of range
     with pytest.raises(hqn.HQNError) as e:
