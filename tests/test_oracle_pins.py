@@ -646,3 +646,30 @@ def test_torus_contact_gradient_matches_central_differences():
             xm = x.copy(); xm[v, cc] -= eps
             fd = (O.objective(P, xp, y, C) - O.objective(P, xm, y, C)) / (2 * eps)
             assert abs(fd - g[v, cc]) <= 1e-6 * max(1.0, abs(g[v, cc])), (v, cc, fd, g[v, cc])
+
+
+def test_A0_quadratic_form_of_an_affine_displacement():
+    """Closed form of Eq. PDmatrixForm's quadratic form: for an affine
+    displacement u_v = B X_v every tet has F - I = B, so on an unclamped mesh
+    u^T A0 u = sum_v m_v |u_v|^2 / h^2 + k V_total |B|_F^2 (the three
+    coordinates summed); with the lumped masses m_v = rho sum_{t∋v} V_t / 4
+    counted by brute force over the tets.  A transposed gradient operator,
+    a missing volume or stiffness factor, or a wrong mass fails it."""
+    w = W.lattice_workload((3, 2, 4), W.Material(W.NEOHOOKEAN, 3e5, 0.35), clamp_axis=-1)
+    P = O.problem_from_workload(w)
+    A = O.assemble_A(P)
+    assert A.shape == (w.n_verts, w.n_verts)
+    rng = np.random.default_rng(23)
+    B = rng.normal(size=(3, 3))
+    u = w.rest_pos @ B.T
+    quad = sum(float(u[:, c] @ (A @ u[:, c])) for c in range(3))
+    vols = []
+    for t in w.tets:
+        X0, X1, X2, X3 = w.rest_pos[t]
+        vols.append(np.linalg.det(np.column_stack([X1 - X0, X2 - X0, X3 - X0])) / 6.0)
+    vols = np.array(vols)
+    m = np.zeros(w.n_verts)
+    for t, V in zip(w.tets, vols):
+        m[t] += w.material.density * V / 4.0
+    expect = float(np.sum(m * np.sum(u * u, axis=1))) / w.h**2 + P.k * vols.sum() * float(np.sum(B * B))
+    assert quad == pytest.approx(expect, rel=1e-12)
