@@ -673,3 +673,38 @@ def test_A0_quadratic_form_of_an_affine_displacement():
         m[t] += w.material.density * V / 4.0
     expect = float(np.sum(m * np.sum(u * u, axis=1))) / w.h**2 + P.k * vols.sum() * float(np.sum(B * B))
     assert quad == pytest.approx(expect, rel=1e-12)
+
+
+def test_two_loop_equals_dense_bfgs_with_full_memory():
+    """With every pair kept (memory at least the pairs, e.g. the paper's
+    m = 100 study), Alg. 2's two-loop recursion applies exactly the BFGS
+    inverse Hessian built by the textbook dense update, started from
+    H0 = A0^{-1} (the same on the x, y and z columns):
+    H <- (I - r s t^T) H (I - r t s^T) + r s s^T, r = 1 / t^T s, oldest pair
+    first (Nocedal-Wright eq. 6.17).  A pair applied in the wrong order or
+    with the wrong scaling fails it."""
+    w, P = _problem((2, 2, 3), seed=6)
+    rng = np.random.default_rng(31)
+    nf = P.free.size
+    Q = rng.normal(size=(3 * nf, 3 * nf))
+    Htrue = Q @ Q.T + 3 * nf * np.eye(3 * nf)
+    hist, pairs = [], []
+    for _ in range(7):
+        s = np.zeros((P.n, 3))
+        s[P.free] = rng.normal(size=(nf, 3))
+        t = np.zeros((P.n, 3))
+        t[P.free] = (Htrue @ s[P.free].ravel()).reshape(nf, 3)
+        hist.append((s, t, O.tr_dot(t, s)))
+        pairs.append((s[P.free].ravel(), t[P.free].ravel()))
+    A = O.assemble_A(P).toarray()
+    H = np.kron(np.linalg.inv(A), np.eye(3))  # free entries as (vertex, coordinate), row-major
+    I = np.eye(3 * nf)
+    for s, t in pairs:
+        r = 1.0 / (t @ s)
+        H = (I - r * np.outer(s, t)) @ H @ (I - r * np.outer(t, s)) + r * np.outer(s, s)
+    g = np.zeros((P.n, 3))
+    g[P.free] = rng.normal(size=(nf, 3))
+    d = O.lbfgs_direction(P, g, hist)
+    expect = -(H @ g[P.free].ravel())
+    np.testing.assert_allclose(d[P.free].ravel(), expect, rtol=1e-9, atol=1e-12 * np.abs(expect).max())
+    assert np.all(d[~np.isin(np.arange(P.n), P.free)] == 0.0)
