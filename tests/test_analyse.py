@@ -93,6 +93,10 @@ def test_rejects_degenerate_and_bad_input(hqn, lat12):
         with pytest.raises(hqn.HQNError) as e:
             hqn.analyse(w.rest_pos, w.tets, w.clamped, kind=W.NEOHOOKEAN, E=E, nu=nu)
         assert e.value.code == hqn.HQN_ERR_ARG, (E, nu)
+    for X0, T0 in ((np.zeros((0, 3)), np.zeros((0, 4), np.int32)), (w.rest_pos, np.zeros((0, 4), np.int32))):
+        with pytest.raises(hqn.HQNError) as e:  # no vertices, or no tets
+            hqn.analyse(X0, T0, kind=W.NEOHOOKEAN, E=5e5, nu=0.4)
+        assert e.value.code == hqn.HQN_ERR_ARG
     X = w.rest_pos.copy()
     X[5, 1] = np.nan
     with pytest.raises(hqn.HQNError) as e:
