@@ -708,3 +708,87 @@ def test_two_loop_equals_dense_bfgs_with_full_memory():
     expect = -(H @ g[P.free].ravel())
     np.testing.assert_allclose(d[P.free].ravel(), expect, rtol=1e-9, atol=1e-12 * np.abs(expect).max())
     assert np.all(d[~np.isin(np.arange(P.n), P.free)] == 0.0)
+
+
+# ---------------------------------------------------------------- Alg. 2's window, Alg. 1's trial cap
+
+def _iterate_gradients(P, w, iterates):
+    y = O.predictor(P, w.q_cur, w.q_prev)
+    return y, [O.gradient(P, x, y) for x in iterates]
+
+
+def test_history_window_keeps_the_newest_m_pairs():
+    """Alg. 2 (Sec. 4.2) builds the direction of iteration k from the newest
+    min(m, k - 1) accepted pairs (s, t).  With m = 2 over ten iterations the
+    window evicts from the fourth iteration on.  Rebuilding every pair from
+    the step's accepted iterates and their gradients, and each direction from
+    exactly the newest pairs, reproduces every step x_{k+1} - x_k = alpha_k d_k
+    the oracle took (alpha_k = 1/2^(trials - 1)).  A window that evicted the
+    newest pair, or never evicted, gives other steps: both are checked to
+    fail, so the pin is sensitive to the eviction rule."""
+    w = W.lattice_workload((3, 3, 3), W.Material(W.NEOHOOKEAN, 1e5, 0.45), seed=5, v_range=0.5)
+    P = O.problem_from_workload(w)
+    m, iters = 2, 10
+    _, st, its = O.solve_step(P, w.q_cur, w.q_prev, iters=iters, m=m, return_iterates=True)
+    assert st.resets == 0 and not st.exhausted and len(its) == iters + 1
+    y, grads = _iterate_gradients(P, w, its)
+    pairs = []
+    for k in range(iters):
+        s, t = its[k + 1] - its[k], grads[k + 1] - grads[k]
+        rho = O.tr_dot(t, s)
+        # every pair passes the curvature filter with room to spare, so the
+        # window is the plain "newest m" of the accepted pairs
+        assert rho > 1e-6 * np.linalg.norm(s) * np.linalg.norm(t)
+        pairs.append((s, t, rho))
+
+    def steps_with(window):
+        out = []
+        for k in range(iters):
+            d = O.lbfgs_direction(P, grads[k], window(k))
+            alpha = 0.5 ** (st.trials[k] - 1)
+            out.append(alpha * d)
+        return out
+
+    taken = [its[k + 1] - its[k] for k in range(iters)]
+    newest = steps_with(lambda k: pairs[max(0, k - m):k])
+    for k in range(iters):
+        assert np.linalg.norm(newest[k] - taken[k]) <= 1e-12 * np.linalg.norm(taken[k]), k
+    evict_newest = steps_with(lambda k: pairs[:min(k, m - 1)] + pairs[k - 1:k] if k > m else pairs[:k])
+    keep_all = steps_with(lambda k: pairs[:k])
+    for alt in (evict_newest, keep_all):
+        worst = max(np.linalg.norm(alt[k] - taken[k]) / np.linalg.norm(taken[k]) for k in range(m + 1, iters))
+        assert worst > 1e-6, worst
+
+
+def test_line_search_exhaustion_keeps_x_k_and_ends_the_step():
+    """Alg. 1 with a cap of ls_max trials (the paper gives none): when every
+    trial is rejected the step keeps x_k, reports the exhaustion and runs no
+    further iterations.  On the small twisted spline bar the ninth iteration
+    rejects alpha = 1 (checked here from Armijo's inequality itself:
+    g(x_k + d) > g(x_k) + 0.3 tr(grad^T d)) and accepts alpha = 1/2.  With
+    ls_max = 1 the step ends there at x_k; with ls_max = 2 it runs as
+    uncapped."""
+    w = W.spline_bar_80x40x40(scale=16)
+    P = O.problem_from_workload(w)
+    _, st_full, its_full = O.solve_step(P, w.q_cur, w.q_prev, iters=10, m=5, return_iterates=True)
+    assert max(st_full.trials) == 2
+    k0 = st_full.trials.index(2)
+    assert k0 >= 5  # the history window is full when the rejection happens
+    y, grads = _iterate_gradients(P, w, its_full[:k0 + 1])
+    d = (its_full[k0 + 1] - its_full[k0]) / 0.5
+    g_k = O.objective(P, its_full[k0], y)
+    gd = O.tr_dot(grads[k0], d)
+    assert gd < 0
+    assert O.objective(P, its_full[k0] + d, y) > g_k + 0.3 * gd
+    assert O.objective(P, its_full[k0] + 0.5 * d, y) <= g_k + 0.3 * 0.5 * gd
+
+    x1, st1, its1 = O.solve_step(P, w.q_cur, w.q_prev, iters=10, m=5, ls_max=1, return_iterates=True)
+    assert st1.exhausted
+    assert st1.trials == [1] * (k0 + 1)
+    assert len(its1) == k0 + 1
+    np.testing.assert_array_equal(x1, its_full[k0])
+    assert st1.g[-1] == pytest.approx(g_k, rel=1e-14)
+
+    x2, st2 = O.solve_step(P, w.q_cur, w.q_prev, iters=10, m=5, ls_max=2)
+    assert not st2.exhausted and st2.trials == st_full.trials
+    np.testing.assert_array_equal(x2, its_full[-1])
