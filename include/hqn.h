@@ -310,7 +310,9 @@ int sim_step(sim_handle *sim, int32_t nsteps, hqn_step_stats *stats);
 int sim_positions_device(sim_handle *sim, void **dev_ptr, int32_t *layout);
 
 /* Evaluates g and grad g (Eq. PD) at positions x with inertial target y (both
- * n_verts x 3 host doubles).  grad is zero on clamped vertices.  g_out or
+ * n_verts x 3 host doubles).  Clamped vertices are eliminated: the inertia
+ * term sums over the free vertices only and grad is zero on clamped rows (a
+ * clamped row of x still enters the elastic energy of its tets).  g_out or
  * grad_out may be NULL.  Does not change the state. */
 int sim_energy_grad(sim_handle *sim, const double *x, const double *y,
                     double *g_out, double *grad_out);
@@ -355,8 +357,9 @@ const char *hqn_last_error(void);
  * allocator, and drivers that forbid cudaMalloc once they are running.
  *
  * hqn_energy_grad_static computes g(x) = 1/(2h^2) sum_v m_v |x_v - y_v|^2 +
- * sum_t V_t Psi(F_t) and grad g(x) -- the quantities sim_energy_grad returns
- * -- in float64 without a handle and without allocating anything.  Its
+ * sum_t V_t Psi(F_t) (v over the free vertices) and grad g(x) -- the
+ * quantities sim_energy_grad returns -- in float64 without a handle and
+ * without allocating anything.  Its
  * scratch (per-tet corner gradients, per-block partial sums) is one
  * fixed-size array of about 8.4 MB that the library places in each GPU's
  * memory when it is loaded there and keeps until the process exits.
@@ -366,15 +369,21 @@ const char *hqn_last_error(void);
  *                     1 <= n_verts <= HQN_STATIC_MAX_VERTS; larger meshes
  *                     are rejected with HQN_ERR_ARG before any device work
  *   rest_pos          n_verts x 3 doubles, rest positions X
- *   tets              n_tets x 4 int32, det[X1-X0, X2-X0, X3-X0] > 0 (a tet
- *                     that breaks this makes *g_out NaN)
- *   clamped           n_verts bytes, nonzero = gradient row set to zero; may be NULL
+ *   tets              n_tets x 4 int32 in [0, n_verts), det[X1-X0, X2-X0,
+ *                     X3-X0] > 0 (a tet that breaks this makes *g_out NaN)
+ *   clamped           n_verts bytes, nonzero = eliminated vertex: no inertia
+ *                     term, gradient row set to zero; may be NULL
  *   vt_ptr, vt_slot   incident-corner CSR: the corners of vertex v are
  *                     vt_slot[vt_ptr[v] .. vt_ptr[v+1]), each encoded as
  *                     4 * tet + corner (vt_ptr has n_verts + 1 entries); the
  *                     gradient sums them in this order (no atomics)
- *   material          HOST pointer; density gives the lumped mass
- *                     m_v = density * sum of incident V_t / 4
+ *   material          HOST pointer, checked as in sim_create (E > 0,
+ *                     -1 < nu < 0.5, known kind, increasing spline knots,
+ *                     fibre term) plus density > 0, which gives the lumped
+ *                     mass m_v = density * sum of incident V_t / 4
+ * Indices are checked on the device before use: a tet vertex outside
+ * [0, n_verts), or a vt_ptr range or vt_slot entry outside [0, 4 n_tets), is
+ * never dereferenced; the affected gradient rows and *g_out are then NaN.
  *   h                 time step (> 0)
  *   x, y              n_verts x 3 doubles: positions and inertial target
  *   g_out             one double (device)

@@ -277,13 +277,7 @@ struct Sim final : SimBase {
                 dc.r = (R)hc.radius;
                 dc.ring = hc.kind == HQN_COLLIDER_TORUS ? (R)hc.major_radius : R(0);
             }
-            MatDev<R> &M = D.mat;
-            M.kind = s.mat.kind;
-            M.mu = (R)s.mat.mu; M.lam = (R)s.mat.lam;
-            M.J0 = (R)s.mat.J0; M.c0 = (R)s.mat.c0; M.c1 = (R)s.mat.c1; M.c2 = (R)s.mat.c2;
-            if (s.mat.kind == HQN_SPLINE_VL) fill_spline(M, s.mat.sx, s.mat.sv, s.mat.ss);
-            M.kappa = (R)s.mat.kappa;
-            for (int a = 0; a < 3; ++a) M.fd[a] = (R)s.mat.fiber[a];
+            matdev_from_host(s.mat, D.mat);
             D.v0 = v0[k]; D.t0 = t0[k];
             D.vb0 = vb0[k]; D.nvb = (s.n + VBS - 1) / VBS;
             D.tb0 = tb0[k]; D.ntb = (s.T + TBS - 1) / TBS;

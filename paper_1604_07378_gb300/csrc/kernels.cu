@@ -178,19 +178,21 @@ __device__ __forceinline__ void for_contacts(const StepConst<R> &c, const V4<R> 
 
 // Block partial of the inertia term 1/(2h^2) sum m_v |x_t - y|^2 of Eq. PD at
 // the caller-given point x_t (the start of a step, or an evaluation request),
-// plus the collision terms active there.
+// plus the collision terms active there.  The sum runs over the free
+// vertices: clamped ones are eliminated (their positions are prescribed), so
+// a caller's x != y on a clamped row adds nothing.
 template <typename R>
 __global__ void __launch_bounds__(VBS) k_inertia(DevSim<R> s) {
     using A = ExactAcc<R>;
     const SimDesc<R> &D = sim_desc(s, s.vblk_sim);
     const int i = (blockIdx.x - D.vb0) * VBS + threadIdx.x;
     typename A::T e[1] = {A::zero()};
-    if (i < D.c.n) {
+    if (i < D.c.nf) {
         const int g = D.v0 + i;
         const V4<R> x = s.xt[g], yy = s.y[g];
         const R dx = x.x - yy.x, dy = x.y - yy.y, dz = x.z - yy.z;
         e[0] = A::add(e[0], R(0.5) * s.mh2[g] * (dx * dx + dy * dy + dz * dz));
-        if (D.c.ncol > 0 && i < D.c.nf) {
+        if (D.c.ncol > 0) {
             const R w = D.c.cscale * s.mh2[g];
             for_contacts(D.c, s.rest[g], x, s.u_cur[g], [&](R gap, R, R, R) { e[0] = A::add(e[0], w * gap * gap); });
         }

@@ -1,11 +1,13 @@
-// Host-side set-up of the spline material's device form (MatDev, common.cuh):
-// cubic Hermite segment coefficients and the rest-state expansion constants.
+// Host-side set-up of a material's device form (MatDev, common.cuh): the
+// spline's cubic Hermite segment coefficients and rest-state expansion
+// constants, and the copy of a checked host material.
 #pragma once
 
 #include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
+#include "setup.hpp"
 
 namespace hqn {
 
@@ -57,6 +59,22 @@ void fill_spline(MatDev<R> &d, const double sx[3][8], const double sv[3][8], con
     d.B1C1 = (R)(F1[1] + F1[2]);
     d.C1 = (R)F1[2];
     d.psi_rest = (R)(3.0 * F0[0] + 3.0 * F0[1] + F0[2]);
+}
+
+// The kernel form of a checked host material (material_from_api).
+template <typename R>
+void matdev_from_host(const MaterialHost &m, MatDev<R> &M) {
+    M = MatDev<R>{};
+    M.kind = m.kind;
+    M.mu = (R)m.mu;
+    M.lam = (R)m.lam;
+    M.J0 = (R)m.J0;
+    M.c0 = (R)m.c0;
+    M.c1 = (R)m.c1;
+    M.c2 = (R)m.c2;
+    if (m.kind == HQN_SPLINE_VL) fill_spline(M, m.sx, m.sv, m.ss);
+    M.kappa = (R)m.kappa;
+    for (int a = 0; a < 3; ++a) M.fd[a] = (R)m.fiber[a];
 }
 
 }  // namespace hqn

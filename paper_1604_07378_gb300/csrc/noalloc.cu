@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <string>
 
 #include "matdev_host.hpp"
 #include "reduce.cuh"
@@ -39,12 +40,14 @@ constexpr int kVertBlocks = (kMaxVerts + kVB - 1) / kVB;
 
 // Scratch shared by every call on a device.  corner[c * T + t] holds tet t's
 // gradient with respect to its corner c (xyz) and, in w, the corner's share
-// of the lumped mass, density * V_t / 4.
+// of the lumped mass, density * V_t / 4.  bad is set by a kernel that met an
+// index outside its array (the call then reports a NaN objective).
 struct StaticScratch {
     V4<double> corner[4 * (size_t)kMaxTets];
     double part_el[kTetBlocks];
     double part_in[kVertBlocks];
     unsigned int ticket;
+    unsigned int bad;
 };
 
 static __device__ __align__(256) StaticScratch g_static_scratch;
@@ -74,16 +77,31 @@ cudaError_t scratch_address(StaticScratch **out) {
 // Per tet: Dm^{-1} and V from the rest positions, the corner gradients of
 // V Psi(F) at x (F = I + G, G from displacements u = x - X), the corners'
 // mass shares and the block partial of sum_t V_t Psi_t.  A tet with
-// det Dm <= 0 makes the energy NaN.
-__global__ void __launch_bounds__(kTB) k_static_tet(int T, const double *__restrict__ X, const int *__restrict__ tets,
-                                                   const double *__restrict__ x, MatDev<double> mat, double density,
-                                                   StaticScratch *sc) {
+// det Dm <= 0, or with a vertex index outside [0, n), makes the energy NaN.
+__global__ void __launch_bounds__(kTB) k_static_tet(int n, int T, const double *__restrict__ X,
+                                                   const int *__restrict__ tets, const double *__restrict__ x,
+                                                   MatDev<double> mat, double density, StaticScratch *sc) {
     const int t = blockIdx.x * kTB + threadIdx.x;
     double e[1] = {0.0};
+    bool in_range = true;
+    int v[4] = {0, 0, 0, 0};
     if (t < T) {
-        int v[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) v[c] = tets[4 * t + c];
+        for (int c = 0; c < 4; ++c) {
+            v[c] = tets[4 * t + c];
+            in_range = in_range && v[c] >= 0 && v[c] < n;
+        }
+    }
+    if (t < T && !in_range) {
+        // an index outside the vertex arrays is never dereferenced: the tet's
+        // corners and energy become NaN and the call reports it
+        V4<double> o;
+        o.x = o.y = o.z = o.w = NAN;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sc->corner[(size_t)c * T + t] = o;
+        e[0] = NAN;
+        atomicOr(&sc->bad, 1u);
+    } else if (t < T) {
         double Dm[3][3], du[3][3];
 #pragma unroll
         for (int j = 0; j < 3; ++j)
@@ -126,8 +144,10 @@ __global__ void __launch_bounds__(kTB) k_static_tet(int T, const double *__restr
 
 // Per vertex: grad g = m (x - y)/h^2 + sum of the incident corner gradients in
 // the CSR's order (zero on clamped vertices), and the block partial of the
-// inertia term m/(2h^2)|x - y|^2.  The last block adds every partial in a
-// fixed order and writes g.
+// inertia term m/(2h^2)|x - y|^2 over the free vertices.  A corner range or
+// slot outside [0, 4T) is not read: the vertex's gradient becomes NaN.  The
+// last block adds every partial in a fixed order and writes g (NaN if any
+// index was out of range).
 __global__ void __launch_bounds__(kVB) k_static_gather(int n, int T, int ntb, const double *__restrict__ x,
                                                       const double *__restrict__ y, const uint8_t *__restrict__ clamped,
                                                       const int *__restrict__ vt_ptr, const int *__restrict__ vt_slot,
@@ -137,15 +157,28 @@ __global__ void __launch_bounds__(kVB) k_static_gather(int n, int T, int ntb, co
     double e[1] = {0.0};
     if (i < n) {
         double gx = 0.0, gy = 0.0, gz = 0.0, m = 0.0;
-        for (int k = vt_ptr[i]; k < vt_ptr[i + 1]; ++k) {
-            const int s = vt_slot[k];  // 4 * t + c
-            const V4<double> cg = sc->corner[(size_t)(s & 3) * T + (s >> 2)];
-            gx += cg.x; gy += cg.y; gz += cg.z; m += cg.w;
+        const int k0 = vt_ptr[i], k1 = vt_ptr[i + 1];
+        if (k0 < 0 || k1 < k0 || k1 > 4 * T) {
+            gx = gy = gz = m = NAN;  // a corner range outside vt_slot is not read
+            atomicOr(&sc->bad, 2u);
+        } else {
+            for (int k = k0; k < k1; ++k) {
+                const int s = vt_slot[k];  // 4 * t + c
+                if (s < 0 || s >= 4 * T) {
+                    gx = gy = gz = m = NAN;
+                    atomicOr(&sc->bad, 2u);
+                    break;
+                }
+                const V4<double> cg = sc->corner[(size_t)(s & 3) * T + (s >> 2)];
+                gx += cg.x; gy += cg.y; gz += cg.z; m += cg.w;
+            }
         }
         const double dx = x[3 * i] - y[3 * i], dy = x[3 * i + 1] - y[3 * i + 1], dz = x[3 * i + 2] - y[3 * i + 2];
         const double mh = m * inv_h2;
-        e[0] = 0.5 * mh * (dx * dx + dy * dy + dz * dz);
         const bool fixed = clamped && clamped[i];
+        // the inertia term of Eq. PD sums over the free vertices (clamped
+        // ones are eliminated: their positions are prescribed)
+        e[0] = fixed ? 0.0 : 0.5 * mh * (dx * dx + dy * dy + dz * dz);
         grad_out[3 * i] = fixed ? 0.0 : gx + mh * dx;
         grad_out[3 * i + 1] = fixed ? 0.0 : gy + mh * dy;
         grad_out[3 * i + 2] = fixed ? 0.0 : gz + mh * dz;
@@ -160,43 +193,7 @@ __global__ void __launch_bounds__(kVB) k_static_gather(int n, int T, int ntb, co
         el[0] = acc;
         block_sum<kVB, 1>(el);
     }
-    if (threadIdx.x == 0) *g_out = el[0] + tot[0];
-}
-
-// Device form of a material (Eq. valanis-landel), as the other entry points build it.
-int material_dev(const hqn_material &m, MatDev<double> &d) {
-    std::memset(&d, 0, sizeof(d));
-    if (!std::isfinite(m.E) || !std::isfinite(m.nu) || !(m.density > 0)) return HQN_ERR_ARG;
-    d.kind = m.kind;
-    d.mu = m.E / (2.0 * (1.0 + m.nu));
-    d.lam = m.E * m.nu / ((1.0 + m.nu) * (1.0 - 2.0 * m.nu));
-    d.J0 = 0.05;
-    if (m.kind == HQN_NEOHOOKEAN) {
-        const double l0 = std::log(d.J0);
-        d.c0 = -d.mu * l0 + 0.5 * d.lam * l0 * l0;
-        d.c1 = (-d.mu + d.lam * l0) / d.J0;
-        d.c2 = (d.mu + d.lam - d.lam * l0) / (d.J0 * d.J0);
-    } else if (m.kind == HQN_SPLINE_VL) {
-        if (!m.spline) return HQN_ERR_ARG;
-        double sx[3][8], sv[3][8], ss[3][8];
-        for (int f = 0; f < 3; ++f)
-            for (int i = 0; i < 8; ++i) {
-                sx[f][i] = m.spline[(f * 8 + i) * 3];
-                sv[f][i] = m.spline[(f * 8 + i) * 3 + 1];
-                ss[f][i] = m.spline[(f * 8 + i) * 3 + 2];
-                if (i > 0 && !(sx[f][i] > sx[f][i - 1])) return HQN_ERR_ARG;
-            }
-        fill_spline(d, sx, sv, ss);
-    } else if (m.kind != HQN_STVK && m.kind != HQN_COROTATED && m.kind != HQN_POLY4) {
-        return HQN_ERR_ARG;
-    }
-    if (m.kappa != 0.0) {
-        const double nn = std::sqrt(m.fiber[0] * m.fiber[0] + m.fiber[1] * m.fiber[1] + m.fiber[2] * m.fiber[2]);
-        if (!(m.kappa > 0.0) || !std::isfinite(m.kappa) || !(nn > 0.0) || !std::isfinite(nn)) return HQN_ERR_ARG;
-        d.kappa = m.kappa;
-        for (int a = 0; a < 3; ++a) d.fd[a] = m.fiber[a] / nn;
-    }
-    return HQN_OK;
+    if (threadIdx.x == 0) *g_out = __ldcg(&sc->bad) ? NAN : el[0] + tot[0];
 }
 
 int fail(int code, const char *msg) {
@@ -222,17 +219,24 @@ extern "C" int hqn_energy_grad_static(int32_t n_verts, int32_t n_tets, const dou
     if (!rest_pos || !tets || !vt_ptr || !vt_slot || !material || !x || !y || !g_out || !grad_out)
         return fail(HQN_ERR_ARG, "hqn_energy_grad_static: null argument");
     if (!(h > 0)) return fail(HQN_ERR_ARG, "hqn_energy_grad_static: h must be positive");
+    if (!(material->density > 0) || !std::isfinite(material->density))
+        return fail(HQN_ERR_ARG, "hqn_energy_grad_static: density must be positive");
+    MaterialHost mh;
+    std::string merr;
+    if (material_from_api(*material, mh, merr) != HQN_OK)
+        return fail(HQN_ERR_ARG, ("hqn_energy_grad_static: " + merr).c_str());
     MatDev<double> mat;
-    if (material_dev(*material, mat) != HQN_OK) return fail(HQN_ERR_ARG, "hqn_energy_grad_static: bad material");
+    matdev_from_host(mh, mat);
     StaticScratch *sc = nullptr;
     cudaError_t e = scratch_address(&sc);
     if (e != cudaSuccess) return fail(HQN_ERR_CUDA, cudaGetErrorString(e));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    // the arrival ticket must start at zero (a previous call may have been cut short)
-    e = cudaMemsetAsync(&sc->ticket, 0, sizeof(unsigned int), st);
+    // the arrival ticket and the index flag start at zero (a previous call
+    // may have been cut short, or have met a bad index)
+    e = cudaMemsetAsync(&sc->ticket, 0, 2 * sizeof(unsigned int), st);
     if (e != cudaSuccess) return fail(HQN_ERR_CUDA, cudaGetErrorString(e));
     const int ntb = (n_tets + kTB - 1) / kTB, nvb = (n_verts + kVB - 1) / kVB;
-    k_static_tet<<<ntb, kTB, 0, st>>>(n_tets, rest_pos, tets, x, mat, material->density, sc);
+    k_static_tet<<<ntb, kTB, 0, st>>>(n_verts, n_tets, rest_pos, tets, x, mat, material->density, sc);
     k_static_gather<<<nvb, kVB, 0, st>>>(n_verts, n_tets, ntb, x, y, clamped, vt_ptr, vt_slot, 1.0 / (h * h), sc,
                                          g_out, grad_out);
     e = cudaGetLastError();

@@ -347,6 +347,58 @@ int make_items(const Setup &S, int VN, int kMax, int64_t per_level, ItemLists &o
 
 }  // namespace
 
+// Lame parameters and the kernel form of an API material (Eq. valanis-landel),
+// with its checks: E > 0 and -1 < nu < 0.5 (so that mu and lambda are finite
+// and positive where the materials need them), a known kind, strictly
+// increasing spline knots, and a positive fibre weight with a nonzero
+// direction.  The one mapping every entry point uses.
+int material_from_api(const hqn_material &in, MaterialHost &M, std::string &err) {
+    M = MaterialHost{};
+    if (!(in.E > 0) || !(in.nu > -1.0 && in.nu < 0.5)) {
+        err = "material needs E > 0 and -1 < nu < 0.5";
+        return HQN_ERR_ARG;
+    }
+    M.kind = in.kind;
+    M.mu = in.E / (2.0 * (1.0 + in.nu));
+    M.lam = in.E * in.nu / ((1.0 + in.nu) * (1.0 - 2.0 * in.nu));
+    if (M.kind == HQN_NEOHOOKEAN) {
+        const double J0 = M.J0, l0 = std::log(J0);
+        M.c0 = -M.mu * l0 + 0.5 * M.lam * l0 * l0;
+        M.c1 = (-M.mu + M.lam * l0) / J0;
+        M.c2 = (M.mu + M.lam - M.lam * l0) / (J0 * J0);
+    } else if (M.kind == HQN_SPLINE_VL) {
+        if (!in.spline) {
+            err = "spline material needs control points";
+            return HQN_ERR_ARG;
+        }
+        for (int f = 0; f < 3; ++f)
+            for (int i = 0; i < 8; ++i) {
+                M.sx[f][i] = in.spline[(f * 8 + i) * 3 + 0];
+                M.sv[f][i] = in.spline[(f * 8 + i) * 3 + 1];
+                M.ss[f][i] = in.spline[(f * 8 + i) * 3 + 2];
+                if (i > 0 && !(M.sx[f][i] > M.sx[f][i - 1])) {
+                    err = "spline knots must increase";
+                    return HQN_ERR_ARG;
+                }
+            }
+    } else if (M.kind != HQN_STVK && M.kind != HQN_COROTATED && M.kind != HQN_POLY4) {
+        err = "unknown material kind";
+        return HQN_ERR_ARG;
+    }
+    // anisotropic fibre term (Sec. 4.4); not part of the stiffness fit
+    if (in.kappa != 0.0) {
+        const double nn = std::sqrt(in.fiber[0] * in.fiber[0] + in.fiber[1] * in.fiber[1] +
+                                    in.fiber[2] * in.fiber[2]);
+        if (!(in.kappa > 0.0) || !std::isfinite(in.kappa) || !(nn > 0.0) || !std::isfinite(nn)) {
+            err = "the fibre term needs kappa > 0 and a nonzero direction";
+            return HQN_ERR_ARG;
+        }
+        M.kappa = in.kappa;
+        for (int a = 0; a < 3; ++a) M.fiber[a] = in.fiber[a] / nn;
+    }
+    return HQN_OK;
+}
+
 double fit_stiffness(const MaterialHost &m, double x_start, double x_end) {
     // k = int (s - sbar) f(s) ds / int (s - sbar)^2 ds on [x_start, x_end]
     // (continuous least-squares slope), integrated piecewise with 8-point
@@ -415,51 +467,8 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
         err = "material density must be positive and E, nu finite";
         return matin.density <= 0 ? HQN_ERR_NOT_SPD : HQN_ERR_NONFINITE;
     }
-    if (!(matin.E > 0) || !(matin.nu > -1.0 && matin.nu < 0.5)) {
-        err = "material needs E > 0 and -1 < nu < 0.5";
-        return HQN_ERR_ARG;
-    }
-
-    // ---- material
     MaterialHost &M = S.mat;
-    M.kind = matin.kind;
-    M.mu = matin.E / (2.0 * (1.0 + matin.nu));
-    M.lam = matin.E * matin.nu / ((1.0 + matin.nu) * (1.0 - 2.0 * matin.nu));
-    if (M.kind == HQN_NEOHOOKEAN) {
-        const double J0 = M.J0, l0 = std::log(J0);
-        M.c0 = -M.mu * l0 + 0.5 * M.lam * l0 * l0;
-        M.c1 = (-M.mu + M.lam * l0) / J0;
-        M.c2 = (M.mu + M.lam - M.lam * l0) / (J0 * J0);
-    } else if (M.kind == HQN_SPLINE_VL) {
-        if (!matin.spline) {
-            err = "spline material needs control points";
-            return HQN_ERR_ARG;
-        }
-        for (int f = 0; f < 3; ++f)
-            for (int i = 0; i < 8; ++i) {
-                M.sx[f][i] = matin.spline[(f * 8 + i) * 3 + 0];
-                M.sv[f][i] = matin.spline[(f * 8 + i) * 3 + 1];
-                M.ss[f][i] = matin.spline[(f * 8 + i) * 3 + 2];
-                if (i > 0 && !(M.sx[f][i] > M.sx[f][i - 1])) {
-                    err = "spline knots must increase";
-                    return HQN_ERR_ARG;
-                }
-            }
-    } else if (M.kind != HQN_STVK && M.kind != HQN_COROTATED && M.kind != HQN_POLY4) {
-        err = "unknown material kind";
-        return HQN_ERR_ARG;
-    }
-    // anisotropic fibre term (Sec. 4.4); not part of the stiffness fit
-    if (matin.kappa != 0.0) {
-        const double nn = std::sqrt(matin.fiber[0] * matin.fiber[0] + matin.fiber[1] * matin.fiber[1] +
-                                    matin.fiber[2] * matin.fiber[2]);
-        if (!(matin.kappa > 0.0) || !std::isfinite(matin.kappa) || !(nn > 0.0) || !std::isfinite(nn)) {
-            err = "the fibre term needs kappa > 0 and a nonzero direction";
-            return HQN_ERR_ARG;
-        }
-        M.kappa = matin.kappa;
-        for (int a = 0; a < 3; ++a) M.fiber[a] = matin.fiber[a] / nn;
-    }
+    if (int rc = material_from_api(matin, M, err)) return rc;
     S.k = fit_stiffness(M, prm.x_start, prm.x_end);
     if (!(S.k > 0) || !std::isfinite(S.k)) {
         err = "stiffness fit is not positive";

@@ -96,6 +96,10 @@ struct Setup {
 int build_setup(const hqn_mesh &mesh, const hqn_material &mat, const hqn_params &prm,
                 Setup &S, std::string &err);
 
+// Lame parameters and the kernel form of an API material, checked
+// (HQN_ERR_ARG with a message on a bad E, nu, kind, spline or fibre term).
+int material_from_api(const hqn_material &in, MaterialHost &out, std::string &err);
+
 // Fits the stiffness k of Eq. stiffness for a material (used by build_setup).
 double fit_stiffness(const MaterialHost &m, double x_start, double x_end);
 

@@ -50,6 +50,26 @@ def test_energy_gradient_parity(w, prec):
             assert np.all(grad[w.clamped.astype(bool)] == 0.0)
 
 
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_energy_gradient_clamped_rows_moved(prec):
+    """x != y on clamped rows: the clamped vertices are eliminated, so the
+    inertia term of Eq. PD skips them (their x still enters the elastic
+    energy of their tets) and their gradient rows are zero."""
+    w = WORKLOADS[1]
+    P = problem_for(w)
+    rng = np.random.default_rng(23)
+    x = w.q_cur + 3e-3 * rng.normal(size=w.q_cur.shape)  # every vertex moves
+    y = O.predictor(P, w.q_cur, w.q_prev)
+    cl = w.clamped.astype(bool)
+    assert np.abs(x[cl] - y[cl]).max() > 1e-4
+    with sim_for(w, prec, use_graph=0) as sim:
+        g, grad = sim.energy_grad(x, y)
+    g_ref = O.objective(P, x, y)
+    assert abs(g - g_ref) <= (1e-11 if prec == FP64 else 2e-6) * abs(g_ref), (g, g_ref)
+    assert rel(grad, O.gradient(P, x, y)) <= (1e-11 if prec == FP64 else 1e-5)
+    assert np.all(grad[cl] == 0.0)
+
+
 def test_energy_gradient_inverted_tets():
     """States with inverted elements exercise the Neo-Hookean continuation
     below J0 and the signed SVD (s3 < 0)."""
@@ -123,6 +143,17 @@ def test_direction_parity(npairs, prec):
 
 # ---------------------------------------------------------------- whole steps
 
+# The step's own motion is the stricter yardstick of position errors:
+# e_x' = ||x_GPU - x_oracle|| / ||x_oracle - q_l||.  FP64 agrees to rounding;
+# FP32 rounds the state and every sweep to 24 bits, and the ten iterations
+# of the (non-converged) step carry that rounding into x.
+STEP_TOL = {FP64: 1e-8, FP32: 1e-3}
+
+
+def rel_step(x, x_ref, q_l):
+    return float(np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref - q_l))
+
+
 def _step_parity(w, prec, use_graph, tol_x):
     P = problem_for(w)
     x_ref, st = O.solve_step(P, w.q_cur, w.q_prev, iters=w.iters, m=w.history)
@@ -134,6 +165,8 @@ def _step_parity(w, prec, use_graph, tol_x):
     np.testing.assert_allclose(qp, w.q_cur, rtol=0, atol=1e-6 if prec == FP32 else 1e-14)
     ex = rel(qc, x_ref)
     assert ex <= tol_x, (ex, stats["trials"], st.trials)
+    ex_step = rel_step(qc, x_ref, w.q_cur)
+    assert ex_step <= STEP_TOL[prec], (ex_step, stats["trials"], st.trials)
     return stats, st, qc, x_ref
 
 
@@ -298,3 +331,57 @@ def test_positions_device_is_the_state(prec):
         np.testing.assert_array_equal(p[:, :3], x)
     else:
         assert np.abs(p[:, :3] - x).max() <= 2 ** -23 * np.abs(x).max() * 2
+
+
+# ---------------------------------------------------------------- Alg. 1's trial cap, checkpoints
+
+@pytest.mark.parametrize("use_graph", [0, 1], ids=["eager", "graph"])
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_line_search_exhaustion_status_and_state(prec, use_graph):
+    """ls_max = 1 on the small twisted spline bar: the ninth iteration's
+    alpha = 1 is rejected (the oracle's pins check it from Armijo's
+    inequality), so the step ends at x_k with HQN_WARN_LS_EXHAUSTED -- on the
+    device exactly as in the oracle."""
+    from paper_1604_07378_gb300 import hqn
+    w = W.spline_bar_80x40x40(scale=16)
+    P = problem_for(w)
+    x_ref, st = O.solve_step(P, w.q_cur, w.q_prev, iters=w.iters, m=w.history, ls_max=1)
+    assert st.exhausted and len(st.trials) < w.iters
+    with sim_for(w, prec, use_graph=use_graph, ls_max=1) as sim:
+        sim.set_state(w.q_cur, w.q_prev)
+        rc, stats = sim.step(1, stats=True)
+        qc, _ = sim.get_state()
+    assert rc == hqn.HQN_WARN_LS_EXHAUSTED and stats["status"] == hqn.HQN_WARN_LS_EXHAUSTED
+    assert stats["iters"] == len(st.trials), (stats["iters"], st.trials)
+    assert rel(qc, x_ref) <= (1e-9 if prec == FP64 else 1e-4)
+    assert rel_step(qc, x_ref, w.q_cur) <= STEP_TOL[prec]
+    if prec == FP64:
+        np.testing.assert_allclose(stats["g"], st.g, rtol=1e-9)
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_checkpoint_resume(prec):
+    """The state (q_l, q_{l-1}) is the whole state between steps (the history
+    is reset every step): 15 steps, sim_get_state, a new handle,
+    sim_set_state and 15 more steps equal 30 straight steps.  FP32 holds the
+    float32 displacement, which survives the float64 round trip X + u - X,
+    so it is bit for bit; FP64's round trip rounds once in the sum."""
+    w = WORKLOADS[2]
+    with sim_for(w, prec) as sim:
+        sim.set_state(w.q_cur, w.q_prev)
+        sim.step(30)
+        straight, straight_prev = sim.get_state()
+    with sim_for(w, prec) as sim:
+        sim.set_state(w.q_cur, w.q_prev)
+        sim.step(15)
+        qc, qp = sim.get_state()
+    with sim_for(w, prec) as sim:
+        sim.set_state(qc, qp)
+        sim.step(15)
+        resumed, resumed_prev = sim.get_state()
+    if prec == FP32:
+        np.testing.assert_array_equal(resumed, straight)
+        np.testing.assert_array_equal(resumed_prev, straight_prev)
+    else:
+        assert rel(resumed, straight) <= 1e-12
+        assert rel(resumed_prev, straight_prev) <= 1e-12
