@@ -31,10 +31,10 @@ if ROOT not in sys.path:
 
 METRIC = "time-steps/s & tet grad-evals/s at 384k tets, FP32 vs FP64 GPU, pos err ≤1e-4"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one cube40 FP32
-# solve (default leaf size and sweep schedule), summed over its 20 sweep
-# launches in an ncu capture of this script's --no-graph run; to be set to
-# None when the sweep kernels change.
-SOLVE_TRAFFIC_BYTES = 243.99e6
+# solve (default shapes), summed over its 20 sweep launches in an ncu capture
+# of this script's --no-graph run; None until captured on the current sweep
+# kernels.
+SOLVE_TRAFFIC_BYTES = None
 UNIT = "time-steps/s"
 WORKLOAD = "cube40_neohookean"
 
@@ -97,48 +97,92 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------- oracle (CPU)
 
-def oracle_sample(w, budget_s=25.0, counts=None):
-    """Times the FP64 CPU oracle on a bounded sample of the workload: repeated
-    (objective, gradient, A0 solve) evaluations on the full mesh, scaled to
-    one time step by the step's counts (trial evaluations, gradients, solves).
-    Returns (steps_per_s, tet_evals_per_s, description, cores)."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
+def host_description():
+    """The host cores the CPU timings ran on: logical CPUs, those this
+    process may use, and the CPU model."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu model")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count()
+    return {"nproc": os.cpu_count(), "usable": usable, "model": model or "unknown"}
+
+
+def oracle_child(args):
+    """Runs in a child process (its thread count fixed by the environment
+    before numpy loads): whole FP64 oracle steps of cube40 (Alg. 1 with
+    Alg. 2, 10 iterations, m = 5, the workload's own state carried from step
+    to step), as many as fit in the budget (at least one); the oracle's A0
+    factorisation is set-up, not timed.  Prints one JSON line."""
     from oracle import hqn_oracle as O
+    from paper_1604_07378_gb300 import workloads as W
+    w = W.cube40(W.NEOHOOKEAN)
     P = O.problem_from_workload(w)
-    y = O.predictor(P, w.q_cur, w.q_prev)
-    x = y.copy()
-    O.solve_A(P, y)  # factorisation: set-up, not timed
-    t_obj, t_grad, t_solve, reps = 0.0, 0.0, 0.0, 0
-    start = time.perf_counter()
-    cpu0 = time.process_time()
-    while reps < 1 or (time.perf_counter() - start < budget_s and reps < 50):
-        t0 = time.perf_counter()
-        O.objective(P, x, y)
-        t1 = time.perf_counter()
-        g = O.gradient(P, x, y)
-        t2 = time.perf_counter()
-        O.solve_A(P, g)
-        t3 = time.perf_counter()
-        t_obj += t1 - t0
-        t_grad += t2 - t1
-        t_solve += t3 - t2
-        reps += 1
-    # threads the sample kept busy: process CPU time over wall time
-    cores = max(1, round((time.process_time() - cpu0) / (time.perf_counter() - start)))
-    t_obj, t_grad, t_solve = t_obj / reps, t_grad / reps, t_solve / reps
-    trials, iters = counts if counts else (1.07 * w.iters, w.iters)
-    step_s = (trials + 1) * t_obj + (iters + 1) * t_grad + iters * t_solve
-    tet_evals = w.n_tets * (trials + iters + 2)
-    desc = (f"{reps} x (objective + gradient + A0 solve) on the full {w.n_tets}-tet mesh "
-            f"({t_obj:.3f} s + {t_grad:.3f} s + {t_solve:.3f} s), scaled to one step of "
-            f"{trials:.1f} line-search trials and {iters:.0f} iterations")
-    return 1.0 / step_s, tet_evals / step_s, desc, cores
+    O.solve_A(P, np.zeros_like(w.q_cur))  # factorisation
+    qc, qp = w.q_cur.copy(), w.q_prev.copy()
+    steps = trials = iters = 0
+    wall0, cpu0 = time.perf_counter(), time.process_time()
+    while steps < args.oracle_max_steps:
+        x, st = O.solve_step(P, qc, qp, iters=w.iters, m=w.history)
+        qp, qc = qc, x
+        steps += 1
+        trials += sum(st.trials)
+        iters += len(st.trials)
+        el = time.perf_counter() - wall0
+        if el + el / steps > args.oracle_budget:
+            break
+    wall = time.perf_counter() - wall0
+    cpu = time.process_time() - cpu0
+    print(json.dumps({"steps": steps, "wall_s": wall, "cpu_s": cpu, "trials": trials, "iters": iters,
+                      "tets": w.n_tets}), flush=True)
+
+
+def oracle_steps(budget_s, threads, max_steps=1000):
+    """Whole oracle steps of cube40 timed in a child process allowed
+    `threads` threads (OpenMP / BLAS); returns the child's record with the
+    time-steps/s and the cores it kept busy (CPU time over wall time)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-child", "--oracle-budget", str(budget_s),
+           "--oracle-max-steps", str(max_steps)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=budget_s * 6 + 600)
+    if r.returncode != 0:
+        raise RuntimeError("oracle child failed:\n" + r.stderr[-2000:])
+    rec = json.loads(r.stdout.strip().splitlines()[-1])
+    rec["threads_allowed"] = threads
+    rec["cores"] = rec["cpu_s"] / rec["wall_s"]
+    rec["steps_per_s"] = rec["steps"] / rec["wall_s"]
+    rec["tet_grad_evals_per_s"] = rec["tets"] * (rec["trials"] + rec["steps"]) / rec["wall_s"]
+    rec["ls_trials_per_iter"] = rec["trials"] / max(rec["iters"], 1)
+    return rec
 
 
 # ---------------------------------------------------------------------------- GPU arm
 
-# schedules of the A0^-1 sweeps (hqn_params.dyn_sweeps)
-SWEEPS = {"levels": 0, "dependency": 1, "pipelined": 2}
+def solve_shapes(args):
+    """hqn_params.solve_* from the command line (0 = the library default)."""
+    return dict(solve_threads=args.solve_threads, solve_item_kb=args.solve_item_kb,
+                solve_items=args.solve_items, solve_prefetch=args.solve_prefetch)
 
 
 def max_over_ranks(x, dist, device=None):
@@ -173,7 +217,7 @@ def run_ours(args, rank, world, dist):
     T = w.n_tets
     graph = 0 if args.no_graph else 1
     sim = hqn.Sim.from_workload(w, precision=hqn.FP32_MIXED, stream=stream.cuda_stream, use_graph=graph,
-                                dyn_sweeps=SWEEPS[args.sweeps], leaf_size=args.leaf_size)
+                                leaf_size=args.leaf_size, **solve_shapes(args))
     info = sim.info()
     sim.set_state(w.q_cur, w.q_prev)
     sim.step(args.warmup)
@@ -241,7 +285,7 @@ def run_ours(args, rank, world, dist):
 
     # ---- FP64-plain GPU form beside it, and the accuracy of the FP32 form against it
     sim64 = hqn.Sim.from_workload(w, precision=hqn.FP64_PLAIN, stream=stream.cuda_stream, use_graph=graph,
-                                  dyn_sweeps=SWEEPS[args.sweeps], leaf_size=args.leaf_size)
+                                  leaf_size=args.leaf_size, **solve_shapes(args))
     sim64.set_state(w.q_cur, w.q_prev)
     sim64.step(1)
     x64, _ = sim64.get_state()
@@ -271,7 +315,7 @@ def run_ours(args, rank, world, dist):
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
                 # the capture holds for the default tree and schedule only
-                "traffic": SOLVE_TRAFFIC_BYTES if args.leaf_size == 0 and SWEEPS[args.sweeps] == 0 else None,
+                "traffic": SOLVE_TRAFFIC_BYTES if args.leaf_size == 0 else None,
                 "algorithmic_bytes_per_launch": bytes_launch}
     else:
         # the tet pass (energy + corner gradients): idx 16 + Dm^-1 36 + V 4 B
@@ -327,9 +371,19 @@ def run_ours(args, rank, world, dist):
     if not args.no_configs:
         line["other_configs"] = run_other_configs(args, stream)
     if rank == 0 and not args.no_cpu_baseline:
-        v, te, desc, cores = oracle_sample(w, budget_s=args.cpu_budget, counts=(trials, iters))
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": desc, "tet_grad_evals_per_s": te}
+        host = host_description()
+        one = oracle_steps(args.cpu_budget, 1, max_steps=2)
+        line["cpu_baseline"] = {
+            "value": one["steps_per_s"], "unit": UNIT, "cores": round(one["cores"], 2), "kind": "oracle",
+            "sample": f"{one['steps']} whole FP64 oracle step(s) of the same workload (10 iterations, m = 5, "
+                      f"{one['trials']} line-search trials), {one['wall_s']:.1f} s wall, one thread allowed",
+            "tet_grad_evals_per_s": one["tet_grad_evals_per_s"], "host": host}
+        if not args.no_threaded_oracle:
+            thr = oracle_steps(args.cpu_budget, host["usable"], max_steps=2)
+            line["cpu_baseline"]["threaded"] = {
+                "value": thr["steps_per_s"], "threads_allowed": thr["threads_allowed"],
+                "cores_busy": round(thr["cores"], 2), "steps": thr["steps"], "wall_s": thr["wall_s"],
+                "note": "the oracle is numpy/scipy: OpenMP/BLAS threads allowed, cores_busy measured"}
     sim.close()
     return line
 
@@ -386,7 +440,7 @@ def run_other_configs(args, stream):
                           ("largebar48x48x192", W.large_48x48x192(), 5)):
         t0 = time.perf_counter()
         sim = hqn.Sim.from_workload(w, precision=hqn.FP32_MIXED, stream=stream.cuda_stream,
-                                    dyn_sweeps=SWEEPS[args.sweeps], leaf_size=args.leaf_size)
+                                    leaf_size=args.leaf_size, **solve_shapes(args))
         create_s = time.perf_counter() - t0
         sim.set_state(w.q_cur, w.q_prev)
         sim.step(1)
@@ -478,7 +532,7 @@ def run_collisions(args, stream):
 
     w = W.collision_drop(40, drop=0.01, speed=2.0)
     sim = hqn.Sim.from_workload(w, precision=hqn.FP32_MIXED, stream=stream.cuda_stream,
-                                dyn_sweeps=SWEEPS[args.sweeps], leaf_size=args.leaf_size)
+                                leaf_size=args.leaf_size, **solve_shapes(args))
     sim.set_state(w.q_cur, w.q_prev)
     sim.step(2)  # warm-up: the fall before the impact
     steps = 20
@@ -525,7 +579,7 @@ def run_batched(args, stream, rank=0, world=1, dist=None):
     for prec, key, steps in ((hqn.FP32_MIXED, "fp32_mixed", args.batch_steps),
                              (hqn.FP64_PLAIN, "fp64_plain", max(2, args.batch_steps // 4))):
         t0 = time.perf_counter()
-        b = hqn.Batch(ws, precision=prec, stream=stream.cuda_stream, dyn_sweeps=SWEEPS[args.sweeps])
+        b = hqn.Batch(ws, precision=prec, stream=stream.cuda_stream, **solve_shapes(args))
         create_s = time.perf_counter() - t0
         for i, w in enumerate(ws):
             b.set_state(i, w.q_cur, w.q_prev)
@@ -556,38 +610,27 @@ def run_batched(args, stream, rank=0, world=1, dist=None):
 
 
 def run_reference(args, rank):
-    """The FP64 CPU oracle as the reference arm (rank 0 only)."""
+    """The reference arm: the FP64 CPU oracle itself (there is no reference
+    implementation; the reference is the paper), rank 0 only.  Whole oracle
+    time steps of the same workload, as many as fit in --ref-budget seconds
+    (at least one): `steps` reports the steps actually timed, not K.  The
+    oracle's A0 factorisation is set-up, not timed."""
     from paper_1604_07378_gb300 import workloads as W
     w = W.cube40(W.NEOHOOKEAN)
-    from oracle import hqn_oracle as O
-    P = O.problem_from_workload(w)
-    y = O.predictor(P, w.q_cur, w.q_prev)
-    O.solve_A(P, y)
-    trials, iters = 1.07 * w.iters, w.iters
-
-    def one():
-        t0 = time.perf_counter()
-        O.objective(P, y, y)
-        t1 = time.perf_counter()
-        g = O.gradient(P, y, y)
-        t2 = time.perf_counter()
-        O.solve_A(P, g)
-        t3 = time.perf_counter()
-        return (trials + 1) * (t1 - t0) + (iters + 1) * (t2 - t1) + iters * (t3 - t2)
-
-    for _ in range(args.warmup):
-        one()
-    wall0, cpu0 = time.perf_counter(), time.process_time()
-    total = sum(one() for _ in range(args.steps))
-    cores = max(1, round((time.process_time() - cpu0) / (time.perf_counter() - wall0)))
-    value = args.steps / total
-    desc = (f"per step: one objective + one gradient + one A0 solve on the full mesh, scaled to "
-            f"{trials:.1f} trials and {iters} iterations per step")
+    host = host_description()
+    rec = oracle_steps(args.ref_budget, host["usable"], max_steps=max(1, args.steps))
+    value = rec["steps_per_s"]
+    desc = (f"{rec['steps']} whole FP64 oracle step(s) of cube40 (10 iterations, m = 5, "
+            f"{rec['trials']} line-search trials) in {rec['wall_s']:.1f} s; {args.steps} requested, "
+            f"bounded by a {args.ref_budget:.0f} s budget")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+            "steps": rec["steps"], "requested_steps": args.steps, "warmup": 0, "ms_per_step": 1e3 / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "tets": w.n_tets, "vertices": w.n_verts},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "tets": w.n_tets, "vertices": w.n_verts,
+                                            "iters": w.iters, "history_m": w.history},
+            "tet_grad_evals_per_s": rec["tet_grad_evals_per_s"], "ls_trials_per_iter": rec["ls_trials_per_iter"],
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": round(rec["cores"], 2), "kind": "oracle",
+                             "sample": desc, "threads_allowed": rec["threads_allowed"], "host": host},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -598,7 +641,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-budget", type=float, default=20.0,
+                    help="seconds of whole oracle steps for cpu_baseline (at least one step)")
+    ap.add_argument("--no-threaded-oracle", action="store_true", help="skip the threaded oracle run")
+    ap.add_argument("--ref-budget", type=float, default=100.0,
+                    help="seconds of whole oracle steps for --impl reference (at least one step)")
+    ap.add_argument("--oracle-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-budget", type=float, default=20.0, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-max-steps", type=int, default=1, help=argparse.SUPPRESS)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 512-simulation measurement")
     ap.add_argument("--no-collisions", action="store_true", help="skip the collision measurement")
     ap.add_argument("--no-pcg", action="store_true", help="skip the Jacobi-PCG measurement")
@@ -608,12 +658,18 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--leaf-size", type=int, default=0,
                     help="max vertices of a nested-dissection leaf (0 = the library default)")
-    ap.add_argument("--sweeps", default="levels", choices=sorted(SWEEPS),
-                    help="schedule of the triangular sweeps")
+    ap.add_argument("--solve-threads", type=int, default=0, help="threads per sweep block (0 = default)")
+    ap.add_argument("--solve-item-kb", type=int, default=0, help="largest sweep work item in KB (0 = default)")
+    ap.add_argument("--solve-items", type=int, default=0, help="work items per tree level (0 = default)")
+    ap.add_argument("--solve-prefetch", type=int, default=0,
+                    help="L2 prefetch distance of the sweeps in launches (0 = default, -1 = none)")
     ap.add_argument("--no-graph", action="store_true",
                     help="issue the step's kernels one by one (same kernels; for profilers that "
                          "cannot see inside graphs with conditional nodes)")
     args = ap.parse_args()
+    if args.oracle_child:
+        oracle_child(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -50,6 +50,9 @@ extern "C" {
 #define HQN_ERR_CUDA             -5  /* a CUDA runtime call failed                */
 #define HQN_ERR_NO_MEMORY        -6  /* host or device allocation failed          */
 #define HQN_ERR_UNSUPPORTED      -7  /* option or size the library does not support */
+#define HQN_ERR_DEVICE_TIMEOUT   -8  /* a bounded wait on the device ran out (a sweep's
+                                        copy of its factor rows did not arrive); the
+                                        step was abandoned and the state is undefined */
 
 /* ---- materials (Eq. valanis-landel: Psi = sum a(s_i) + sum b(s_i s_j) + c(J)) */
 typedef enum {
@@ -138,18 +141,23 @@ typedef struct {
                              default 8; other values HQN_ERR_ARG).  The accepted
                              alpha is the one Alg. 1's sequential backtracking
                              would accept                                          */
-    int32_t dyn_sweeps;   /* triangular sweeps: 0 = one launch per tree level,
-                             chained by programmatic dependent launch (default);
-                             1 = dependency-driven (one persistent launch per
-                             sweep; a work item waits only for the supernodes it
-                             reads); 2 = pipelined (one persistent launch per
-                             sweep, one block per SM, each with a fixed list of
-                             items whose factor rows stream into shared memory
-                             ahead of the dependency chain; falls back to 0 when
-                             its shared memory does not fit).  0 and 1 give
-                             bit-identical results; 2 partitions the rows into
-                             other work items, so its results differ from them
-                             by rounding only                                      */
+    /* Shapes of the triangular sweeps of A0^{-1} (one launch per tree level;
+     * every level's factor rows split into work items of consecutive rows,
+     * one thread block each).  They change the speed, not the arithmetic of
+     * a row, except that a different split of the backward rows into chunk
+     * items sums some rows in another order (rounding-level differences).
+     * 0 selects the default; the autotuner (paper_1604_07378_gb300/autotune.py)
+     * picks them per mesh and GPU. */
+    int32_t solve_threads;  /* threads per sweep block: 256 or 512 (default 256)  */
+    int32_t solve_item_kb;  /* largest work item, KB of factor rows: 16..160
+                               (default 64)                                      */
+    int32_t solve_items;    /* work items a level's rows are spread over: 16..4096
+                               (default 400)                                     */
+    int32_t solve_prefetch; /* a level's blocks ask L2 to prefetch the factor rows
+                               of the level this many launches ahead: 1..8; 0 or
+                               -1 = no prefetch (default: on a 40^3 lattice the
+                               prefetch left the solve's time unchanged and cost
+                               the step 3% of L2 hits elsewhere)                 */
     /* Collisions (Sec. 4.3) against analytic colliders, shared by every
      * simulation of a handle.  At the start of each iteration (before the
      * gradient at x_k) every free vertex that penetrates a collider and does
@@ -188,6 +196,25 @@ typedef struct {
      * tree): on a 40^3 lattice every mask tried made the solve slower, since
      * each work item of a wide supernode gathers its whole right-hand side. */
     int32_t merge_depths;
+    /* Failure detection.  Every device wait of the sweeps is bounded: a block
+     * polls its bulk copy's barrier at most wait_polls times (0 = default
+     * 2^20), then flags the error, waits (bounded) for a copy still in
+     * flight and leaves; sim_step, sim_solve_A0 and sim_direction then
+     * return HQN_ERR_DEVICE_TIMEOUT.  fault_test is fault injection for
+     * tests of that path and stays 0 otherwise: 1 = the blocks of the first
+     * forward level of every solve issue no copy, so their waits run out with
+     * nothing in flight. */
+    int32_t wait_polls;
+    int32_t fault_test;
+    /* Path of an autotuner cache (see hqn_tune_lookup), or NULL.  When set,
+     * sim_create and sim_batch_create look up the mesh (hqn_mesh_key; for a
+     * batch, the keys of all meshes folded in order), the precision and the
+     * current device's name there, and, on a hit, replace leaf_size,
+     * solve_threads, solve_item_kb, solve_items, solve_prefetch (and
+     * ls_batch if the entry has it) by the tuned values.  A missing file
+     * or entry leaves the parameters as given; a malformed file is
+     * HQN_ERR_ARG. */
+    const char *tune_cache;
 } hqn_params;
 
 #define HQN_MAX_HISTORY 16
@@ -219,8 +246,10 @@ typedef struct {
     int64_t n_update_entries;   /* entries of the forward-sweep update vectors        */
     int32_t chained_sweeps;     /* 1 if the per-level sweeps use programmatic dependent
                                    launch (a level starts while the previous finishes) */
-    int32_t sweep_schedule;     /* sweeps in use: 0 = one launch per level, 1 = dependency-
-                                   driven, 2 = pipelined (see hqn_params.dyn_sweeps)     */
+    int32_t solve_threads;      /* sweep shapes in use (see hqn_params.solve_*)           */
+    int32_t solve_item_kb;
+    int32_t solve_items;
+    int32_t solve_prefetch;     /* 0 = no prefetch                                        */
     int32_t n_sims;             /* simulations in the handle (1 for sim_create)        */
 } hqn_info;
 
@@ -238,7 +267,7 @@ void hqn_default_params(hqn_params *p);
  * without a GPU and without keeping anything.  Fills the fields of *info
  * that the set-up determines: n_verts, n_tets, n_free, n_supernodes,
  * n_levels, factor_entries, factor_nnz, stiffness_k, setup_seconds,
- * n_update_entries, and precision, graph_mode and sweep_schedule as
+ * n_update_entries, and precision, graph_mode and the solve_* shapes as
  * requested by *params (n_sims = 1); the device-dependent fields are 0.
  * Errors: those of sim_create other than HQN_ERR_CUDA. */
 int hqn_analyse(const hqn_mesh *mesh, const hqn_material *material,
@@ -343,9 +372,48 @@ typedef enum {
  * leaves the state (q_l, q_{l-1}) unchanged.  Synchronises the stream. */
 int sim_time_stage(sim_handle *sim, int32_t stage, int32_t reps, double *ms);
 
+/* ---- autotuning ------------------------------------------------------------
+ * The paper has no counterpart: these entry points serve the project's
+ * autotuner (paper_1604_07378_gb300/autotune.py), which times the sweep
+ * shapes and the leaf size on the device and writes its choices to a cache
+ * file that sim_create reads (hqn_params.tune_cache). */
+
+/* New sweep shapes on an existing handle (hqn_params.solve_threads,
+ * solve_item_kb, solve_items, solve_prefetch; 0 = default): the work items
+ * are re-planned from the handle's own factor (no refactorisation) and the
+ * step graph is rebuilt.  Results change by rounding only (other row
+ * splits), or not at all (threads, prefetch).  Errors: HQN_ERR_ARG (a shape
+ * out of range), HQN_ERR_UNSUPPORTED (items that do not fit a block's shared
+ * memory), HQN_ERR_CUDA. */
+int sim_set_solve_shapes(sim_handle *sim, int32_t threads, int32_t item_kb, int32_t items, int32_t prefetch);
+
+/* 64-bit FNV-1a hash of a mesh (sizes, rest positions, tets, clamp flags):
+ * the key of its autotuner cache entries.  0 for a NULL or empty mesh.
+ * Host only. */
+uint64_t hqn_mesh_key(const hqn_mesh *mesh);
+
+/* Looks up (device, key, precision) in the autotuner cache file at `path`
+ * (host only; `device` is a CUDA device name).  The file holds one entry
+ * per line, later lines overriding earlier ones, '#' lines ignored:
+ *   hqn-tune 1 device=<name, spaces as '_'> precision=<0|1> key=<16 hex>
+ *     leaf_size=<n> solve_threads=<n> solve_item_kb=<n> solve_items=<n>
+ *     solve_prefetch=<n> [ls_batch=<n>] [other key=value pairs, ignored]
+ * Returns 1 and writes the entry's values into *params on a hit, 0 when the
+ * file or the entry does not exist (params unchanged), HQN_ERR_ARG for a
+ * malformed file or argument. */
+int hqn_tune_lookup(const char *path, const char *device, uint64_t key, int32_t precision, hqn_params *params);
+
 int  sim_get_info(const sim_handle *sim, hqn_info *info);
 void sim_destroy(sim_handle *sim);
 const char *sim_strerror(int code);
+
+/* Measures the current device's non-tensor fused multiply-add throughput in
+ * the precision's floating-point type (HQN_FP32_MIXED: float, HQN_FP64_PLAIN:
+ * double), in FLOP/s (an FMA counts 2): independent FMA chains on every SM,
+ * timed with CUDA events over a launch of at least 20 ms.  The FLOP roofline
+ * of the tet pass.  Allocates a few bytes of device memory and a stream for
+ * the call.  Errors: HQN_ERR_ARG, HQN_ERR_CUDA. */
+int hqn_measure_peak(int32_t precision, double *flops_per_s);
 
 /* Message of the last error raised on the calling thread ("" if none). */
 const char *hqn_last_error(void);

@@ -1,0 +1,128 @@
+"""The project's autotuner of the solver's launch shapes.
+
+The speed of the A0^{-1} sweeps, the heaviest stage of a step, depends on
+shapes the method leaves open: the nested-dissection leaf size (which sets
+the factor's levels and fill), the threads of a sweep block, the size and
+number of the work items a level's rows are split into, and how many
+launches ahead a level prefetches the factor into L2.  This module times
+them on the current GPU, on the mesh itself:
+
+1. for every leaf size, one handle (one factorisation); on it every sweep
+   shape of the grid is planned in turn (sim_set_solve_shapes re-plans the
+   work items without refactorising) and one solve is timed with CUDA
+   events on the device (sim_time_stage, best of three means);
+2. the best shape of each leaf size, and the library's defaults, are timed
+   as whole time steps (one CUDA graph each);
+3. the fastest is written to the cache file as one line, keyed by the
+   device name, the precision and the mesh's hash (hqn_mesh_key).
+
+sim_create reads the cache when hqn_params.tune_cache names it, so a tuned
+mesh needs no timing afterwards.  The choice is never slower than the
+defaults on the steps timed, since the defaults are among the candidates.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import time
+
+import numpy as np
+
+from . import hqn
+
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.txt")
+
+LEAF_SIZES = (64, 128, 256)
+# (threads, item KB, items per level, prefetch distance; -1 = none)
+SHAPE_GRID = tuple((t, kb, n, pf) for t in (256, 512)
+                   for kb, n in ((64, 400), (32, 800), (48, 304), (96, 152), (128, 152), (64, 152))
+                   for pf in (-1, 1, 2, 3))
+SHAPE_KEYS = ("solve_threads", "solve_item_kb", "solve_items", "solve_prefetch")
+
+
+def mesh_key(rest_pos, tets, clamped=None) -> int:
+    """The library's hash of a mesh (hqn_mesh_key)."""
+    X = np.ascontiguousarray(rest_pos, dtype=np.float64)
+    T = np.ascontiguousarray(tets, dtype=np.int32)
+    cl = None if clamped is None else np.ascontiguousarray(clamped, dtype=np.uint8)
+    m = hqn.Mesh(X.shape[0], T.shape[0], X.ctypes.data_as(C.POINTER(C.c_double)),
+                 T.ctypes.data_as(C.POINTER(C.c_int32)),
+                 None if cl is None else cl.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return int(hqn.library().hqn_mesh_key(C.byref(m)))
+
+
+def cache_line(device: str, precision: int, key: int, choice: dict, **extra) -> str:
+    """One cache entry in the format hqn_tune_lookup reads."""
+    fields = [f"device={device.replace(' ', '_')}", f"precision={int(precision)}", f"key={key:016x}",
+              f"leaf_size={int(choice['leaf_size'])}"]
+    fields += [f"{k}={int(choice[k])}" for k in SHAPE_KEYS]
+    fields += [f"{k}={v:.6g}" if isinstance(v, float) else f"{k}={v}" for k, v in extra.items()]
+    return "hqn-tune 1 " + " ".join(fields)
+
+
+def lookup(path: str, device: str, key: int, precision: int):
+    """The entry the library would apply (a dict of the tuned fields), or None."""
+    p = hqn.default_params()
+    rc = hqn.library().hqn_tune_lookup(os.fsencode(path), device.encode(), key, precision, C.byref(p))
+    if rc < 0:
+        raise hqn.HQNError(rc, f"malformed autotuner cache {path}")
+    if rc == 0:
+        return None
+    return {"leaf_size": p.leaf_size, **{k: getattr(p, k) for k in SHAPE_KEYS}, "ls_batch": p.ls_batch}
+
+
+def _device_name() -> str:
+    import torch
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+def _step_ms(sim, w, steps):
+    sim.set_state(w.q_cur, w.q_prev)
+    sim.step(2)
+    sim.set_state(w.q_cur, w.q_prev)
+    t0 = time.perf_counter()
+    sim.step(steps)  # ends with a synchronising read of the control blocks
+    return 1e3 * (time.perf_counter() - t0) / steps
+
+
+def tune_workload(w, precision=hqn.FP32_MIXED, stream=None, leaf_sizes=LEAF_SIZES, grid=SHAPE_GRID,
+                  reps=20, steps=10, cache: str | None = DEFAULT_CACHE) -> dict:
+    """Times the shapes on workload `w` (a workloads.Workload) and returns
+    the choice with its measurements; appends it to `cache` unless None."""
+    results = []
+    for leaf in leaf_sizes:
+        with hqn.Sim.from_workload(w, precision=precision, stream=stream, leaf_size=leaf) as sim:
+            sim.set_state(w.q_cur, w.q_prev)
+            sim.step(1)
+            timed = []
+            for shape in grid:
+                try:
+                    sim.set_solve_shapes(*shape)
+                except hqn.HQNError:
+                    continue  # items that do not fit a block's shared memory
+                t = min(sim.time_stage(hqn.STAGE_SOLVE, reps) for _ in range(3))
+                timed.append((t, shape))
+            if not timed:
+                continue
+            t_best, best = min(timed)
+            sim.set_solve_shapes(*best)
+            results.append({"leaf_size": leaf, **dict(zip(SHAPE_KEYS, best)), "solve_ms": t_best,
+                            "step_ms": _step_ms(sim, w, steps), "shapes_timed": len(timed)})
+    with hqn.Sim.from_workload(w, precision=precision, stream=stream) as sim:
+        info = sim.info()
+        default = {"leaf_size": 0, **{k: 0 for k in SHAPE_KEYS},
+                   "solve_ms": min(sim.time_stage(hqn.STAGE_SOLVE, reps) for _ in range(3)),
+                   "step_ms": _step_ms(sim, w, steps), "default_leaf": None, "levels": info["n_levels"]}
+    choice = min(results + [default], key=lambda r: r["step_ms"])
+    out = dict(choice)
+    out["default_step_ms"] = default["step_ms"]
+    out["default_solve_ms"] = default["solve_ms"]
+    out["candidates"] = results
+    if cache and choice is not default:
+        key = mesh_key(w.rest_pos, w.tets, w.clamped)
+        line = cache_line(_device_name(), precision, key, choice, step_ms=float(choice["step_ms"]),
+                          solve_ms=float(choice["solve_ms"]), workload=getattr(w, "name", "mesh"))
+        with open(cache, "a") as f:
+            f.write(line + "\n")
+        out["cache_line"] = line
+    return out

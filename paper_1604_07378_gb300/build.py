@@ -19,8 +19,8 @@ LIB = os.path.join(LIBDIR, "libhqn.so")
 ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 
-CXX_SOURCES = ["setup.cpp", "dense.cpp"]
-CU_SOURCES = ["kernels.cu", "solve.cu", "api.cu", "noalloc.cu"]
+CXX_SOURCES = ["setup.cpp", "dense.cpp", "tune.cpp"]
+CU_SOURCES = ["kernels.cu", "solve.cu", "api.cu", "noalloc.cu", "peak.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

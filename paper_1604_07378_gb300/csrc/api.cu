@@ -60,7 +60,10 @@ struct SimBase {
     virtual void info(hqn_info *out) const = 0;
     virtual int time_stage(int stage, int reps, double *ms) = 0;
     virtual int positions_device(void **ptr, int32_t *layout) = 0;
+    virtual int set_solve_shapes(int threads, int item_kb, int items, int prefetch) = 0;
 };
+
+int check_solve_shapes(const hqn_params &p);
 
 template <typename R>
 struct Sim final : SimBase {
@@ -72,12 +75,17 @@ struct Sim final : SimBase {
     DevSolve<R> dsol{};
     std::vector<SimDesc<R>> hdesc;
     std::vector<void *> allocs;
-    int64_t dev_bytes = 0;
+    std::vector<void *> plan_allocs;  // device memory of the current sweep plan (work items, prefetch spans)
+    std::vector<void *> *alloc_to = &allocs;
+    int64_t dev_bytes = 0, plan_bytes = 0;
+    // batch offsets of every simulation's vertices, update entries,
+    // supernodes and packed operators (kept to re-plan the sweeps)
+    std::vector<int> sv0, su0, ssn0;
+    std::vector<int64_t> sqf0, sqb0;
     Ctl *d_ctl = nullptr;  // ns control blocks (device)
     Ctl *h_ctl = nullptr;  // ns control blocks (pinned host copy)
     std::vector<int> fwd_ptr, fwd_ld, fwd_q, bwd_start, bwd_cnt, bwd_ld, bwd_q;  // per tree level
-    int pipe_nbund[2] = {0, 0};  // bundles of the pipelined forward / backward sweeps
-    int pipe_ndep[2] = {0, 0};   // cross-block waits of the pipelined forward / backward sweeps
+    std::vector<int> pf_ptr;  // L2 prefetch spans of each launch of a solve
     V4<R> *hbuf = nullptr;  // pinned staging buffer of the state transfers (largest simulation)
     const int *d_perm0 = nullptr;  // simulation 0's caller ids by internal vertex (sim_positions_device)
     V4<R> *d_pos0 = nullptr;       // its positions in caller order, borrowed by the caller
@@ -96,6 +104,7 @@ struct Sim final : SimBase {
         if (graph) cudaGraphDestroy(graph);
         for (auto s : cap_streams) cudaStreamDestroy(s);
         for (void *p : allocs) cudaFree(p);
+        for (void *p : plan_allocs) cudaFree(p);
         if (h_ctl) cudaFreeHost(h_ctl);
         if (hbuf) cudaFreeHost(hbuf);
         if (own_stream) cudaStreamDestroy(own_stream);
@@ -110,8 +119,9 @@ struct Sim final : SimBase {
         void *q = nullptr;
         cudaError_t e = cudaMalloc(&q, count * sizeof(X));
         if (e != cudaSuccess) return fail(HQN_ERR_NO_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-        allocs.push_back(q);
+        alloc_to->push_back(q);
         dev_bytes += (int64_t)(count * sizeof(X));
+        if (alloc_to == &plan_allocs) plan_bytes += (int64_t)(count * sizeof(X));
         p = (X *)q;
         CK(cudaMemsetAsync(q, 0, count * sizeof(X), st));
         return HQN_OK;
@@ -132,9 +142,10 @@ struct Sim final : SimBase {
         st = stream;
         ns = (int)S.size();
         const int m = prm.history_m;
+        const int item_kb = p.solve_item_kb > 0 ? p.solve_item_kb : 64;
         int max_ld = 0;
         for (const Setup &s : S) max_ld = std::max(max_ld, s.max_ld);
-        if (!solve_smem_limit_ok<R>(max_ld))
+        if (solve_block_smem<R>(item_kb * 1024 / (int)sizeof(R), max_ld) > (size_t)SOLVE_MAX_SMEM)
             return fail(HQN_ERR_UNSUPPORTED, "a separator is too large for the sweeps' shared memory");
         CK(solve_prepare<R>());
         if (st == nullptr) {  // the legacy default stream cannot be captured: use an own stream
@@ -331,8 +342,8 @@ struct Sim final : SimBase {
     // The solve operators of every simulation, back to back, with batch
     // offsets baked into the work-item records (kernels.cuh) and the index
     // tables.  Level l of the sweeps holds level l of every simulation's tree.
-    // Backward items are stored root level first (the dependency-driven queue
-    // order); bwd_start[l] is where tree level l begins.
+    // Backward items are stored root level first (launch order); bwd_start[l]
+    // is where tree level l begins.
     int init_solve(const std::vector<int> &v0, const std::vector<int> &u0, const std::vector<int> &sn0,
                    const std::vector<int64_t> &qf0, const std::vector<int64_t> &qb0, int64_t qf_tot, int64_t qb_tot) {
         int rc;
@@ -391,10 +402,34 @@ struct Sim final : SimBase {
             if ((rc = upload(p_ug4, ug4.data(), ug4.size()))) return rc;
             dsol.rows = p_rows; dsol.fg4 = p_fg4; dsol.ug4 = p_ug4;
         }
+        sv0 = v0; su0 = u0; ssn0 = sn0; sqf0 = qf0; sqb0 = qb0;
+        dsol.err = &d_ctl[0].solve_err;
+        if ((rc = alloc(dsol.u, (size_t)std::max<int64_t>(upd_tot, 1)))) return rc;
+        return plan_solve();
+    }
+
+    // The sweeps' work items and prefetch spans from every simulation's
+    // plan (Setup::lv), and the shapes of hqn_params.solve_*.  Runs again
+    // when the shapes change (set_solve_shapes); the factor stays.
+    int plan_solve() {
+        int rc;
+        const int L = n_levels;
+        const std::vector<int> &v0 = sv0, &u0 = su0, &sn0 = ssn0;
+        const std::vector<int64_t> &qf0 = sqf0, &qb0 = sqb0;
+        if (st) cudaStreamSynchronize(st);
+        for (void *q : plan_allocs) cudaFree(q);
+        plan_allocs.clear();
+        dev_bytes -= plan_bytes;
+        plan_bytes = 0;
+        alloc_to = &plan_allocs;
+        struct Restore {
+            std::vector<void *> *&a;
+            std::vector<void *> *v;
+            ~Restore() { a = v; }
+        } restore{alloc_to, &allocs};
         // work items by level, every simulation's items of a level together
         std::vector<std::vector<int4>> frec(L), brec(L);
         fwd_ld.assign(L, 0); fwd_q.assign(L, 0); bwd_ld.assign(L, 0); bwd_q.assign(L, 0);
-        std::vector<int> nit_f((size_t)sn_tot, 0), nit_b((size_t)sn_tot, 0);
         int cb0 = 0;
         for (int k = 0; k < ns; ++k) {
             const Setup &s = S[k];
@@ -420,7 +455,6 @@ struct Sim final : SimBase {
                     auto child = [&](size_t i) { return i < sn.children.size() ? sn0[k] + sn.children[i] : -1; };
                     v.push_back(make_int4(child(0), child(1), child(2), child(3)));
                     v.push_back(make_int4(sn0[k] + f.s, 0, 0, 0));
-                    nit_f[sn0[k] + f.s]++;
                 }
                 for (int e = s.lv.bwd_lvl_ptr[l]; e < s.lv.bwd_lvl_ptr[l + 1]; ++e) {
                     const BwdItem &b = s.lv.bwd_items[e];
@@ -441,7 +475,6 @@ struct Sim final : SimBase {
                     v.push_back(make_int4(b.col0, b.col1, sn.ldr, (int)o0));
                     v.push_back(make_int4(sn.parent >= 0 ? sn0[k] + sn.parent : -1, sn0[k] + b.s, 0, 0));
                     v.push_back(make_int4(b.e0, b.e1, b.cb >= 0 ? cb0 + b.cb : -1, (b.nch << 16) | b.k));
-                    nit_b[sn0[k] + b.s]++;
                 }
             }
         }
@@ -462,16 +495,9 @@ struct Sim final : SimBase {
         int n_cb = 0;
         for (const Setup &s : S) n_cb += s.lv.n_bwd_blocks;
         const int4 *p_fi, *p_bi;
-        const int *p_nf, *p_nb;
         if ((rc = upload(p_fi, fi.data(), fi.size()))) return rc;
         if ((rc = upload(p_bi, bi.data(), bi.size()))) return rc;
-        if ((rc = upload(p_nf, nit_f.data(), nit_f.size()))) return rc;
-        if ((rc = upload(p_nb, nit_b.data(), nit_b.size()))) return rc;
         dsol.fwd_items = p_fi; dsol.bwd_items = p_bi;
-        dsol.fwd_nitems = p_nf; dsol.bwd_nitems = p_nb;
-        if ((rc = alloc(dsol.fwd_done, (size_t)sn_tot))) return rc;
-        if ((rc = alloc(dsol.bwd_done, (size_t)sn_tot))) return rc;
-        if ((rc = alloc(dsol.queue, 2))) return rc;
         dsol.n_sn = (int)sn_tot;
         dsol.nf = (int)nf_tot;
         dsol.n_fwd_items = (int)(fi.size() / 5);
@@ -485,453 +511,98 @@ struct Sim final : SimBase {
         dsol.bwd_lvl_ld = bwd_ld.data();
         dsol.fwd_lvl_q = fwd_q.data();
         dsol.bwd_lvl_q = bwd_q.data();
-        dsol.fwd_qmax = dsol.fwd_ldmax = dsol.bwd_qmax = dsol.bwd_ldmax = 0;
-        for (int l = 0; l < L; ++l) {
-            dsol.fwd_qmax = std::max(dsol.fwd_qmax, fwd_q[l]);
-            dsol.fwd_ldmax = std::max(dsol.fwd_ldmax, fwd_ld[l]);
-            dsol.bwd_qmax = std::max(dsol.bwd_qmax, bwd_q[l]);
-            dsol.bwd_ldmax = std::max(dsol.bwd_ldmax, bwd_ld[l]);
-        }
-        dsol.dyn = 0;
-        dsol.dyn_grid = 0;
-        dsol.pipe = 0;
-        if (prm.dyn_sweeps == 1) {
-            dsol.dyn_grid = solve_dyn_grid<R>(dsol);
-            dsol.dyn = dsol.dyn_grid > 0 ? 1 : 0;
-        } else if (prm.dyn_sweeps == 2) {
-            if ((rc = init_pipe(v0, u0, sn0, qf0, qb0))) return rc;
-        }
-        dsol.err = &d_ctl[0].solve_err;
-        if ((rc = alloc(dsol.u, (size_t)std::max<int64_t>(upd_tot, 1)))) return rc;
-        return HQN_OK;
-    }
-
-    // ---- pipelined schedule (one persistent launch per sweep; solve.cu)
-    //
-    // Every tree level's items (all simulations) are split over the P blocks
-    // in contiguous runs of about equal weight (bytes plus a per-item cost),
-    // so a supernode's items stay together and a block's items of
-    // consecutive levels tend to be parent and child.  A block's consecutive
-    // items of one level form a bundle until it would hold more than half
-    // the ring, overflow its vector area (fcap entries), its segments or its
-    // chunk column blocks.  A supernode whose items all sit in one block
-    // ("owned") needs no completion counter for consumers in that block:
-    // the block's own order covers them; counters are kept only where a
-    // consumer sits elsewhere.
-
-    struct PipeSweep {  // host copy of one sweep's schedule
-        std::vector<int4> items, bund, seg, cmb;
-        std::vector<int2> dep, sig;
-        std::vector<int> bptr, seg_sn;  // seg_sn: supernode of each segment (checks only)
-    };
-
-    // Invariants the pipelined kernels rely on for in-bounds accesses and for
-    // progress, checked on the host before anything is uploaded: every item's
-    // rows fit one ring slot and its vector entries lie inside its bundle's
-    // area; a bundle holds at most half the ring, its items share one tree
-    // level and its warp ranges tile the consumer warps; a block's bundles
-    // come in sweep order; every producer a bundle reads from is either
-    // owned by the same block or waited for, and everything waited for
-    // publishes exactly its item count.
-    static bool pipe_schedule_ok(bool bwd, const PipeSweep &W, int fcap, int ns, const std::vector<int> &lev,
-                                 const std::vector<int> &nit, const std::vector<int> &owner,
-                                 const std::vector<int> &gparent, const std::vector<int> &ch_ptr,
-                                 const std::vector<int> &ch) {
-        const int RN = bwd ? 5 : 4, SN = bwd ? 2 : 1;
-        const std::vector<int4> &items = W.items, &bund = W.bund, &seg = W.seg, &cmb = W.cmb;
-        const std::vector<int2> &dep = W.dep, &sig = W.sig;
-        const std::vector<int> &bptr = W.bptr;
-        const int nitems = (int)(items.size() / RN), nb = (int)(bund.size() / 3), nseg = (int)(seg.size() / SN);
-        if ((int)W.seg_sn.size() != nseg) return false;
-        std::vector<int> published(nit.size(), 0);
-        std::vector<char> waited(nit.size(), 0);
-        int prev_item_end = 0;
-        for (size_t b = 0; b + 1 < bptr.size(); ++b) {
-            if (bptr[b] > bptr[b + 1] || bptr[b + 1] > nb) return false;
-            int prev_level = bwd ? INT32_MAX : -1;
-            for (int q = bptr[b]; q < bptr[b + 1]; ++q) {
-                const int4 B0 = bund[3 * (size_t)q], B1 = bund[3 * (size_t)q + 1], B2 = bund[3 * (size_t)q + 2];
-                if (B0.x != prev_item_end || B0.y <= B0.x || B0.y > nitems || B0.y - B0.x > ns / 2) return false;
-                prev_item_end = B0.y;
-                if (B0.z < 0 || B0.w > nseg || B0.w - B0.z < 1 || B0.w - B0.z > PIPE_SEG_MAX) return false;
-                if (B1.x < 0 || B1.y > (int)dep.size() || B1.y - B1.x > 512) return false;
-                if (B1.z < 0 || B1.w > (int)sig.size() || B1.w - B1.z > 512) return false;
-                if (B2.x < 0 || B2.y > (int)(cmb.size() / 2) || B2.y - B2.x > PIPE_CMB_MAX) return false;
-                if (B2.z < 1 || B2.z > fcap) return false;
-                // segments tile [0, ftot) and share the bundle's level
-                int off = 0, level = -1;
-                for (int g = B0.z; g < B0.w; ++g) {
-                    const int4 sg = bwd ? seg[2 * (size_t)g + 1] : seg[g];
-                    const int aoff = bwd ? sg.y : sg.z, len = bwd ? sg.z : sg.w;
-                    if (aoff != off || len < 1 || (len & 3) || (aoff & 3)) return false;
-                    off += len;
-                    const int sn = W.seg_sn[g];
-                    if (sn < 0 || sn >= (int)nit.size()) return false;
-                    if (level < 0) level = lev[sn];
-                    if (lev[sn] != level) return false;
-                    // every producer is owned by this block or waited for
-                    auto covered = [&](int p) {
-                        if (nit[p] == 0 || owner[p] == (int)b) return true;
-                        for (int d = B1.x; d < B1.y; ++d)
-                            if (dep[d].x == p) return true;
-                        return false;
-                    };
-                    if (bwd) {
-                        if (gparent[sn] >= 0 && !covered(gparent[sn])) return false;
-                    } else {
-                        for (int c = ch_ptr[sn]; c < ch_ptr[sn + 1]; ++c)
-                            if (!covered(ch[c])) return false;
-                    }
-                }
-                if (off != B2.z) return false;
-                if (bwd ? level > prev_level : level < prev_level) return false;
-                prev_level = level;
-                for (int g = B1.z; g < B1.w; ++g) {
-                    const int2 sgn = sig[g];
-                    if (sgn.x < 0 || sgn.x >= (int)nit.size() || sgn.y < 1 || lev[sgn.x] != level) return false;
-                    published[sgn.x] += sgn.y;
-                }
-                for (int g = B1.x; g < B1.y; ++g) {
-                    const int2 d = dep[g];
-                    if (d.x < 0 || d.x >= (int)nit.size() || d.y != nit[d.x]) return false;
-                    if (bwd ? lev[d.x] <= level : lev[d.x] >= level) return false;
-                    waited[d.x] = 1;
-                }
-                int wprev = 0;
-                for (int it = B0.x; it < B0.y; ++it) {
-                    const int4 a = items[(size_t)RN * it], c = items[(size_t)RN * it + 2], d = items[(size_t)RN * it + 3];
-                    if (a.z < 16 || a.z > 32768 || (a.z & 15)) return false;
-                    const int64_t q0 = (int64_t)(unsigned)a.x | ((int64_t)a.y << 32);
-                    if ((q0 * (int64_t)sizeof(R)) & 15) return false;
-                    if (d.z != wprev || d.w <= d.z) return false;
-                    wprev = d.w;
-                    if (!bwd) {
-                        if (d.x < 0 || (d.x & 3) || d.x + c.z > B2.z) return false;
-                    } else {
-                        const int4 e = items[(size_t)RN * it + 4];
-                        const int lw = e.x >= 0 ? e.y - e.x : c.z - bwd_row_start(c.x);
-                        if (d.x < 0 || (d.x & 3) || lw < 1 || d.x + lw > B2.z) return false;
-                        if (e.x >= 0 && (c.y - c.x) * lw * (int)sizeof(R) > 32768) return false;
-                    }
-                }
-                if (wprev != 16) return false;
-            }
-        }
-        if (prev_item_end != nitems) return false;
-        for (size_t q = 0; q < nit.size(); ++q)
-            if (waited[q] && published[q] != nit[q]) return false;
-        return true;
-    }
-
-    int init_pipe(const std::vector<int> &v0, const std::vector<int> &u0, const std::vector<int> &sn0,
-                  const std::vector<int64_t> &qf0, const std::vector<int64_t> &qb0) {
-        const int L = n_levels;
-        int need_max = 2048;
-        for (const Setup &s : S) {
-            for (const FwdItem &f : s.pp.fwd_items) {
-                const SupernodeHost &sn = s.sn[f.s];
-                need_max = std::max(need_max, fwd_row_len(f.row1 - 1, sn.ncol, sn.ldc));
-            }
-            for (const BwdItem &b : s.pp.bwd_items) {
-                const SupernodeHost &sn = s.sn[b.s];
-                need_max = std::max(need_max, b.e0 >= 0 ? b.e1 - b.e0 : sn.ldr - bwd_row_start(b.col0));
-            }
-        }
-        const int fcap = pad4(need_max);
-        int nslots = 0;
-        const int P = solve_pipe_grid<R>(fcap, &nslots);
-        if (P <= 0) return HQN_OK;  // does not fit: the level schedule stays
-        const int bmax = nslots / 2;
-        std::vector<int> roff0(ns, 0), cb_off(ns, 0);
-        for (int k = 1; k < ns; ++k) {
-            roff0[k] = roff0[k - 1] + (int)S[k - 1].rows.size();
-            cb_off[k] = cb_off[k - 1] + S[k - 1].pp.n_bwd_blocks;
-        }
-        const int n_cb = cb_off[ns - 1] + S[ns - 1].pp.n_bwd_blocks;
-        // global supernodes: level, parent, children; items per sweep; column blocks
-        std::vector<int> lev((size_t)sn_tot, 0), gparent((size_t)sn_tot, -1), ch_ptr((size_t)sn_tot + 1, 0), ch;
-        std::vector<int> nit_f((size_t)sn_tot, 0), nit_b((size_t)sn_tot, 0), cb_nch(std::max(1, n_cb), 0),
-            cb_slot(std::max(1, n_cb), 0);
-        for (int k = 0; k < ns; ++k) {
-            for (size_t q = 0; q < S[k].sn.size(); ++q) {
-                lev[sn0[k] + q] = S[k].sn[q].level;
-                gparent[sn0[k] + q] = S[k].sn[q].parent >= 0 ? sn0[k] + S[k].sn[q].parent : -1;
-            }
-            for (const FwdItem &f : S[k].pp.fwd_items) nit_f[sn0[k] + f.s]++;
-            for (const BwdItem &b : S[k].pp.bwd_items) {
-                nit_b[sn0[k] + b.s]++;
-                if (b.cb >= 0) cb_nch[cb_off[k] + b.cb] = b.nch;
-            }
-        }
-        for (int64_t q = 0; q < sn_tot; ++q)
-            if (gparent[q] >= 0) ch_ptr[gparent[q] + 1]++;
-        for (int64_t q = 0; q < sn_tot; ++q) ch_ptr[q + 1] += ch_ptr[q];
-        ch.assign((size_t)ch_ptr[sn_tot], 0);
+        // L2 prefetch spans of every launch, in launch order: the factor rows
+        // its items copy, as contiguous runs (a whole supernode's rows where
+        // its items follow each other) cut into pieces of at most 256 KB;
+        // a chunk item's rows are covered once, by chunk 0 of its column block
         {
-            std::vector<int> fill(ch_ptr.begin(), ch_ptr.end() - 1);
-            for (int64_t q = 0; q < sn_tot; ++q)
-                if (gparent[q] >= 0) ch[fill[gparent[q]]++] = (int)q;
+            std::vector<int4> spans;
+            pf_ptr.assign(2 * (size_t)L + 1, 0);
+            const int esz = (int)sizeof(R);
+            auto add_run = [&](const R *base, int64_t e0, int64_t e1, std::vector<std::pair<int64_t, int64_t>> &runs) {
+                if (e1 <= e0) return;
+                if (!runs.empty() && runs.back().second == e0) runs.back().second = e1;
+                else runs.push_back({e0, e1});
+                (void)base;
+            };
+            auto flush = [&](const R *base, std::vector<std::pair<int64_t, int64_t>> &runs) {
+                constexpr int64_t kPiece = 256 * 1024;
+                for (const auto &r : runs)
+                    for (int64_t b0 = r.first * esz; b0 < r.second * esz; b0 += kPiece) {
+                        const int64_t b1 = std::min<int64_t>(r.second * esz, b0 + kPiece);
+                        const unsigned long long a = (unsigned long long)(reinterpret_cast<uintptr_t>(base) + b0);
+                        spans.push_back(make_int4((int)(a & 0xffffffffULL), (int)(a >> 32), (int)(b1 - b0), 0));
+                    }
+                runs.clear();
+            };
+            std::vector<std::pair<int64_t, int64_t>> runs;
+            for (int k = 0; k < 2 * L; ++k) {
+                pf_ptr[k] = (int)spans.size();
+                if (k < L) {
+                    for (int it = fwd_ptr[k]; it < fwd_ptr[k + 1]; ++it) {
+                        const int4 a = fi[5 * (size_t)it];
+                        const int64_t q0 = (int64_t)(unsigned)a.x | ((int64_t)a.y << 32);
+                        add_run(dsol.QF, q0, q0 + a.z / esz, runs);
+                    }
+                    flush(dsol.QF, runs);
+                } else {
+                    const int l = 2 * L - 1 - k;
+                    for (int it = bwd_start[l]; it < bwd_start[l] + bwd_cnt[l]; ++it) {
+                        const int4 a = bi[5 * (size_t)it], c = bi[5 * (size_t)it + 2], e = bi[5 * (size_t)it + 4];
+                        const int64_t q0 = (int64_t)(unsigned)a.x | ((int64_t)a.y << 32);
+                        if (e.x < 0) {
+                            add_run(dsol.QB, q0, q0 + a.z / esz, runs);
+                        } else if ((e.w & 0xffff) == 0) {  // chunk 0: rows c0 .. c1 whole
+                            add_run(dsol.QB, q0 + bwd_row_off(c.x, c.z), q0 + bwd_row_off(c.y, c.z), runs);
+                        }
+                    }
+                    flush(dsol.QB, runs);
+                }
+            }
+            pf_ptr[2 * (size_t)L] = (int)spans.size();
+            const int4 *p_sp;
+            if ((rc = upload(p_sp, spans.data(), spans.size()))) return rc;
+            dsol.pf_spans = p_sp;
+            dsol.pf_ptr = pf_ptr.data();
         }
-        int n_slots_part = 0;
-        for (int c = 0; c < n_cb; ++c) {
-            cb_slot[c] = n_slots_part;
-            n_slots_part += cb_nch[c];
-        }
-        struct Ref {
-            int k, i;
-            double w;
-        };
-        auto assign = [&](bool bwd) {
-            std::vector<std::vector<Ref>> blk((size_t)P);
-            for (int li = 0; li < L; ++li) {
-                const int l = bwd ? L - 1 - li : li;
-                std::vector<Ref> lv;
-                double total = 0.0;
-                for (int k = 0; k < ns; ++k) {
-                    const ItemLists &it = S[k].pp;
-                    if (l >= S[k].n_levels) continue;
-                    const std::vector<int> &ptr = bwd ? it.bwd_lvl_ptr : it.fwd_lvl_ptr;
-                    for (int i = ptr[l]; i < ptr[l + 1]; ++i) {
-                        int64_t ent;
-                        if (!bwd) {
-                            const FwdItem &f = it.fwd_items[i];
-                            const SupernodeHost &sn = S[k].sn[f.s];
-                            ent = fwd_row_off(f.row1, sn.ncol, sn.ldc) - fwd_row_off(f.row0, sn.ncol, sn.ldc);
-                        } else {
-                            const BwdItem &b = it.bwd_items[i];
-                            const SupernodeHost &sn = S[k].sn[b.s];
-                            ent = b.e0 < 0 ? bwd_row_off(b.col1, sn.ldr) - bwd_row_off(b.col0, sn.ldr)
-                                           : (int64_t)(b.col1 - b.col0) * (b.e1 - b.e0);
-                        }
-                        const double w = (double)ent * sizeof(R) + 2048.0;
-                        lv.push_back({k, i, w});
-                        total += w;
-                    }
-                }
-                double cum = 0.0;
-                for (const Ref &r : lv) {
-                    int b = (int)((cum + 0.5 * r.w) / total * P);
-                    b = std::min(std::max(b, 0), P - 1);
-                    blk[b].push_back(r);
-                    cum += r.w;
-                }
-            }
-            return blk;
-        };
-        // owner[s]: the block holding every item of s (-1: split over blocks)
-        auto owners = [&](bool bwd, const std::vector<std::vector<Ref>> &blk) {
-            std::vector<int> own((size_t)sn_tot, -2);
-            for (int b = 0; b < P; ++b)
-                for (const Ref &r : blk[b]) {
-                    const int s = sn0[r.k] + (bwd ? S[r.k].pp.bwd_items[r.i].s : S[r.k].pp.fwd_items[r.i].s);
-                    own[s] = own[s] == -2 || own[s] == b ? b : -1;
-                }
-            for (int &o : own)
-                if (o == -2) o = -1;
-            return own;
-        };
-        // does s publish a completion counter (a consumer sits elsewhere)?
-        auto publishes = [&](bool bwd, int s, const std::vector<int> &own, const std::vector<int> &nit) {
-            if (own[s] < 0) return true;
-            if (!bwd) {
-                const int p = gparent[s];
-                return p >= 0 && nit[p] > 0 && own[p] != own[s];
-            }
-            for (int c = ch_ptr[s]; c < ch_ptr[s + 1]; ++c)
-                if (nit[ch[c]] > 0 && own[ch[c]] != own[s]) return true;
-            return false;
-        };
-        auto build = [&](bool bwd, PipeSweep &W, std::vector<int> &own) {
-            const std::vector<std::vector<Ref>> blk = assign(bwd);
-            own = owners(bwd, blk);
-            const std::vector<int> &nit = bwd ? nit_b : nit_f;
-            const int RN = bwd ? 5 : 4, SN = bwd ? 2 : 1;
-            W.bptr.assign((size_t)P + 1, 0);
-            for (int b = 0; b < P; ++b) {
-                W.bptr[b] = (int)(W.bund.size() / 3);
-                int cur_level = -1, ftot = 0, seg_sn = -1, item0 = 0, seg0 = 0, dep0 = 0, sig0 = 0, cmb0 = 0;
-                int last_cb = -1, sig_cur = -1;
-                bool open = false;
-                auto close = [&]() {
-                    if (!open) return;
-                    const int i1 = (int)(W.items.size() / RN), m = i1 - item0;
-                    // consumer warps per item, in proportion to its bytes (at least one)
-                    double tot = 0.0;
-                    for (int it = item0; it < i1; ++it) tot += W.items[(size_t)RN * it].z;
-                    double cum = 0.0;
-                    for (int it = item0; it < i1; ++it) {
-                        const int j = it - item0;
-                        int4 &d = W.items[(size_t)RN * it + 3];
-                        d.z = j + (int)((PIPE_CONS_WARPS - m) * cum / tot);
-                        cum += W.items[(size_t)RN * it].z;
-                        d.w = it + 1 < i1 ? j + 1 + (int)((PIPE_CONS_WARPS - m) * cum / tot) : PIPE_CONS_WARPS;
-                    }
-                    W.bund.push_back(make_int4(item0, i1, seg0, (int)(W.seg.size() / SN)));
-                    W.bund.push_back(make_int4(dep0, (int)W.dep.size(), sig0, (int)W.sig.size()));
-                    W.bund.push_back(make_int4(cmb0, (int)(W.cmb.size() / 2), ftot, 0));
-                    open = false;
-                };
-                for (const Ref &r : blk[b]) {
-                    const Setup &s = S[r.k];
-                    int gs, start, end, level, nc;
-                    const SupernodeHost *snp;
-                    const BwdItem *bi = nullptr;
-                    const FwdItem *fi = nullptr;
-                    if (!bwd) {
-                        fi = &s.pp.fwd_items[r.i];
-                        snp = &s.sn[fi->s];
-                        gs = sn0[r.k] + fi->s;
-                        start = 0;
-                        end = fwd_row_len(fi->row1 - 1, snp->ncol, snp->ldc);
-                    } else {
-                        bi = &s.pp.bwd_items[r.i];
-                        snp = &s.sn[bi->s];
-                        gs = sn0[r.k] + bi->s;
-                        start = bi->e0 >= 0 ? bi->e0 : bwd_row_start(bi->col0);
-                        end = bi->e0 >= 0 ? bi->e1 : snp->ldr;
-                    }
-                    const SupernodeHost &sn = *snp;
-                    level = sn.level;
-                    nc = sn.ncol;
-                    const bool chunk = bwd && bi->e0 >= 0 && bi->nch > 1;
-                    const int cbg = bwd && bi->cb >= 0 ? cb_off[r.k] + bi->cb : -1;
-                    // segment of this supernode: [w0, w0 + len) of its vector
-                    auto seg_w0 = [&]() { return bwd ? W.seg.back().x : 0; };
-                    auto seg_len = [&]() { return bwd ? W.seg.back().z : W.seg.back().w; };
-                    bool same = open && seg_sn == gs && start >= seg_w0();
-                    int grow = same ? std::max(0, end - (seg_w0() + seg_len())) : end - start;
-                    const bool new_cmb = chunk && !(open && last_cb == cbg);
-                    if (!open || level != cur_level || (int)(W.items.size() / RN) - item0 == bmax ||
-                        ftot + grow > fcap || (!same && (int)(W.seg.size() / SN) - seg0 == PIPE_SEG_MAX) ||
-                        (new_cmb && (int)(W.cmb.size() / 2) - cmb0 == PIPE_CMB_MAX)) {
-                        close();
-                        open = true;
-                        cur_level = level;
-                        ftot = 0;
-                        item0 = (int)(W.items.size() / RN);
-                        seg0 = (int)(W.seg.size() / SN);
-                        dep0 = (int)W.dep.size();
-                        sig0 = (int)W.sig.size();
-                        cmb0 = (int)(W.cmb.size() / 2);
-                        last_cb = -1;
-                        same = false;
-                        grow = end - start;
-                    }
-                    if (!same) {
-                        if (!bwd) {
-                            W.seg.push_back(make_int4(v0[r.k] + sn.col, std::min(end, nc), ftot, end));
-                        } else {
-                            W.seg.push_back(make_int4(v0[r.k] + sn.col, sn.ncol, sn.nrow, roff0[r.k] + sn.roff));
-                            W.seg.push_back(make_int4(start, ftot, end - start, 0));
-                        }
-                        W.seg_sn.push_back(gs);
-                        // producers this bundle must wait for (not owned by this block)
-                        auto add_dep = [&](int p) {
-                            if (nit[p] == 0 || own[p] == b) return;
-                            for (int d = dep0; d < (int)W.dep.size(); ++d)
-                                if (W.dep[d].x == p) return;
-                            W.dep.push_back(make_int2(p, nit[p]));
-                        };
-                        if (bwd) {
-                            if (gparent[gs] >= 0) add_dep(gparent[gs]);
-                        } else {
-                            for (int c = ch_ptr[gs]; c < ch_ptr[gs + 1]; ++c) add_dep(ch[c]);
-                        }
-                        sig_cur = -1;
-                        if (publishes(bwd, gs, own, nit)) {
-                            W.sig.push_back(make_int2(gs, 0));
-                            sig_cur = (int)W.sig.size() - 1;
-                        }
-                        ftot += end - start;
-                        seg_sn = gs;
-                    } else if (grow > 0) {
-                        if (!bwd) {
-                            W.seg.back().w += grow;
-                            W.seg.back().y = std::min(W.seg.back().w, nc);
-                        } else {
-                            W.seg.back().z += grow;
-                        }
-                        ftot += grow;
-                    }
-                    if (sig_cur >= 0) W.sig[sig_cur].y++;
-                    if (chunk) {
-                        if (last_cb != cbg) {
-                            W.cmb.push_back(make_int4(cbg, 0, cb_slot[cbg], bi->nch));
-                            W.cmb.push_back(make_int4(v0[r.k] + sn.col + bi->col0, bi->col1 - bi->col0, 0, 0));
-                            last_cb = cbg;
-                        }
-                        W.cmb[W.cmb.size() - 2].y++;
-                    }
-                    const int aoff = bwd ? W.seg.back().y + (start - W.seg.back().x) : W.seg.back().z;
-                    if (!bwd) {
-                        const int64_t o0 = fwd_row_off(fi->row0, nc, sn.ldc), o1 = fwd_row_off(fi->row1, nc, sn.ldc);
-                        const int64_t q0 = qf0[r.k] + sn.qf + o0;
-                        W.items.push_back(make_int4((int)(q0 & 0xffffffffLL), (int)(q0 >> 32),
-                                                    (int)((o1 - o0) * sizeof(R)), fi->G));
-                        W.items.push_back(make_int4(v0[r.k] + sn.col, nc, sn.ldc, u0[r.k] + sn.uoff));
-                        W.items.push_back(make_int4(fi->row0, fi->row1, end, (int)o0));
-                        W.items.push_back(make_int4(aoff, 0, 0, 0));
-                    } else {
-                        int64_t o0 = bwd_row_off(bi->col0, sn.ldr), q0, bytes;
-                        if (bi->e0 < 0) {
-                            q0 = qb0[r.k] + sn.qb + o0;
-                            bytes = (bwd_row_off(bi->col1, sn.ldr) - o0) * (int64_t)sizeof(R);
-                        } else {
-                            q0 = qb0[r.k] + sn.qb;
-                            bytes = 0;
-                            for (int j = bi->col0; j < bi->col1; ++j)
-                                bytes += std::max(0, bi->e1 - std::max(bi->e0, bwd_row_start(j))) * (int64_t)sizeof(R);
-                        }
-                        W.items.push_back(make_int4((int)(q0 & 0xffffffffLL), (int)(q0 >> 32), (int)bytes, bi->G));
-                        W.items.push_back(make_int4(v0[r.k] + sn.col, sn.ncol, sn.nrow, roff0[r.k] + sn.roff));
-                        W.items.push_back(make_int4(bi->col0, bi->col1, sn.ldr, (int)o0));
-                        W.items.push_back(make_int4(aoff, cbg >= 0 ? cb_slot[cbg] : 0, 0, 0));
-                        W.items.push_back(make_int4(bi->e0, bi->e1, cbg, (bi->nch << 16) | bi->k));
-                    }
-                }
-                close();
-            }
-            W.bptr[P] = (int)(W.bund.size() / 3);
-        };
-        int rc;
-        for (int dir = 0; dir < 2; ++dir) {
-            const bool bwd = dir == 1;
-            PipeSweep W;
-            std::vector<int> own;
-            build(bwd, W, own);
-            if (!pipe_schedule_ok(bwd, W, fcap, nslots, lev, bwd ? nit_b : nit_f, own, gparent, ch_ptr, ch))
-                return fail(HQN_ERR_UNSUPPORTED, bwd ? "pipelined backward schedule failed its consistency check"
-                                                     : "pipelined forward schedule failed its consistency check");
-            const int4 *p_items, *p_bund, *p_seg, *p_cmb = nullptr;
-            const int2 *p_dep, *p_sig;
-            const int *p_blk;
-            if ((rc = upload(p_items, W.items.data(), W.items.size()))) return rc;
-            if ((rc = upload(p_bund, W.bund.data(), W.bund.size()))) return rc;
-            if ((rc = upload(p_seg, W.seg.data(), W.seg.size()))) return rc;
-            if (bwd && (rc = upload(p_cmb, W.cmb.data(), W.cmb.size()))) return rc;
-            if ((rc = upload(p_dep, W.dep.data(), W.dep.size()))) return rc;
-            if ((rc = upload(p_sig, W.sig.data(), W.sig.size()))) return rc;
-            if ((rc = upload(p_blk, W.bptr.data(), W.bptr.size()))) return rc;
-            if (!bwd) {
-                dsol.pf_items = p_items; dsol.pf_bund = p_bund; dsol.pf_seg = p_seg;
-                dsol.pf_dep = p_dep; dsol.pf_sig = p_sig; dsol.pf_blk = p_blk;
-            } else {
-                dsol.pb_items = p_items; dsol.pb_bund = p_bund; dsol.pb_seg = p_seg; dsol.pb_cmb = p_cmb;
-                dsol.pb_dep = p_dep; dsol.pb_sig = p_sig; dsol.pb_blk = p_blk;
-            }
-            pipe_nbund[dir] = W.bptr[P];
-            pipe_ndep[dir] = (int)W.dep.size();
-        }
-        if ((rc = alloc(dsol.pb_part, (size_t)std::max(1, n_slots_part) * 32))) return rc;
-        if ((rc = alloc(dsol.pb_cbc, (size_t)std::max(1, n_cb)))) return rc;
-        dsol.pipe = 1;
-        dsol.pipe_grid = P;
-        dsol.pipe_ns = nslots;
-        dsol.pipe_fcap = fcap;
+        dsol.threads = prm.solve_threads == 512 ? 512 : 256;
+        dsol.prefetch = prm.solve_prefetch <= 0 ? 0 : prm.solve_prefetch;
+        dsol.wait_polls = prm.wait_polls > 0 ? prm.wait_polls : (1LL << 20);
+        dsol.fault_test = prm.fault_test;
         return HQN_OK;
     }
 
-    // Ends any capture a failed build_graph left open and drops the graph.
+    // New sweep shapes on an existing handle (the autotuner's entry): the
+    // work items are re-planned from the kept set-up, the graph rebuilt.
+    int set_solve_shapes(int threads, int item_kb, int items, int prefetch) override {
+        hqn_params p = prm;
+        p.solve_threads = threads;
+        p.solve_item_kb = item_kb;
+        p.solve_items = items;
+        p.solve_prefetch = prefetch;
+        if (const int rc = check_solve_shapes(p)) return rc;
+        int rc;
+        std::string err;
+        for (Setup &s : S)
+            if ((rc = plan_sweeps(s, p, err))) return fail(rc, err);
+        int max_ld = 0;
+        for (const Setup &s : S) max_ld = std::max(max_ld, s.max_ld);
+        const int kb = p.solve_item_kb > 0 ? p.solve_item_kb : 64;
+        if (solve_block_smem<R>(kb * 1024 / (int)sizeof(R), max_ld) > (size_t)SOLVE_MAX_SMEM)
+            return fail(HQN_ERR_UNSUPPORTED, "the work items do not fit the sweeps' shared memory");
+        prm = p;
+        if (graph_mode) abort_graph();
+        if ((rc = plan_solve())) return rc;
+        if (graph_mode) {
+            if ((rc = build_graph())) {
+                abort_graph();
+                graph_mode = false;
+                return rc;
+            }
+        }
+        return HQN_OK;
+    }
+
     void abort_graph() {
         std::vector<cudaStream_t> ss = cap_streams;
         ss.push_back(st);
@@ -1028,7 +699,9 @@ struct Sim final : SimBase {
     int read_ctl() {
         CK(cudaMemcpyAsync(h_ctl, d_ctl, sizeof(Ctl) * (size_t)ns, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        if (h_ctl[0].solve_err) return fail(HQN_ERR_CUDA, "a triangular sweep's device wait did not complete in time");
+        if (h_ctl[0].solve_err)
+            return fail(HQN_ERR_DEVICE_TIMEOUT, "a triangular sweep's wait for its factor rows ran out (flags " +
+                                                    std::to_string(h_ctl[0].solve_err) + ")");
         return HQN_OK;
     }
     bool any_ctl(bool (*pred)(const Ctl &)) const {
@@ -1328,7 +1001,10 @@ struct Sim final : SimBase {
         o->graph_mode = graph_mode ? 1 : 0;
         o->n_update_entries = upd_tot;
         o->chained_sweeps = dsol.pdl;
-        o->sweep_schedule = dsol.pipe ? 2 : dsol.dyn;
+        o->solve_threads = dsol.threads;
+        o->solve_item_kb = prm.solve_item_kb > 0 ? prm.solve_item_kb : 64;
+        o->solve_items = prm.solve_items > 0 ? prm.solve_items : 400;
+        o->solve_prefetch = dsol.prefetch;
         o->n_sims = ns;
     }
 };
@@ -1366,6 +1042,19 @@ struct sim_handle {
 };
 
 namespace {
+
+// Checks of the sweep shapes hqn_params.solve_*.
+int check_solve_shapes(const hqn_params &p) {
+    if (p.solve_threads != 0 && p.solve_threads != 256 && p.solve_threads != 512)
+        return fail(HQN_ERR_ARG, "solve_threads must be 0, 256 or 512");
+    if (p.solve_item_kb != 0 && (p.solve_item_kb < 16 || p.solve_item_kb > 160))
+        return fail(HQN_ERR_ARG, "solve_item_kb must be 0 or in [16, 160]");
+    if (p.solve_items != 0 && (p.solve_items < 16 || p.solve_items > 4096))
+        return fail(HQN_ERR_ARG, "solve_items must be 0 or in [16, 4096]");
+    if (p.solve_prefetch < -1 || p.solve_prefetch > 8)
+        return fail(HQN_ERR_ARG, "solve_prefetch must be -1 (none), 0 (default) or in [1, 8]");
+    return HQN_OK;
+}
 
 // Checks of the parameters that do not depend on a mesh (HQN_OK or a status
 // set through fail()).
@@ -1405,6 +1094,9 @@ int validate_params(const hqn_params *params) {
     const int lb = params->ls_batch;
     if (lb != 0 && lb != 1 && lb != 2 && lb != 4 && lb != 8 && lb != 16)
         return fail(HQN_ERR_ARG, "ls_batch must be 0, 1, 2, 4, 8 or 16");
+    if (const int rc = check_solve_shapes(*params)) return rc;
+    if (params->wait_polls < 0) return fail(HQN_ERR_ARG, "wait_polls must be >= 0");
+    if (params->fault_test != 0 && params->fault_test != 1) return fail(HQN_ERR_ARG, "fault_test must be 0 or 1");
     return HQN_OK;
 }
 
@@ -1413,6 +1105,28 @@ int create_any(int count, const hqn_mesh *meshes, const hqn_material *materials,
     if (!out) return fail(HQN_ERR_ARG, "null output pointer");
     *out = nullptr;
     if (count <= 0 || !meshes || !materials || !params) return fail(HQN_ERR_ARG, "null argument or empty batch");
+    hqn_params tuned = *params;
+    if (params->tune_cache) {
+        // the autotuner's choices for this mesh (or batch), precision and device
+        uint64_t key = hqn_mesh_key(&meshes[0]);
+        if (count > 1) {
+            key = 1469598103934665603ULL;
+            for (int k = 0; k < count; ++k) {
+                const uint64_t mk = hqn_mesh_key(&meshes[k]);
+                for (int b = 0; b < 8; ++b) {
+                    key ^= (mk >> (8 * b)) & 0xffULL;
+                    key *= 1099511628211ULL;
+                }
+            }
+        }
+        int dev = 0;
+        cudaDeviceProp prop;
+        CK(cudaGetDevice(&dev));
+        CK(cudaGetDeviceProperties(&prop, dev));
+        const int hit = hqn_tune_lookup(params->tune_cache, prop.name, key, params->precision, &tuned);
+        if (hit < 0) return fail(hit, std::string("malformed autotuner cache ") + params->tune_cache);
+    }
+    params = &tuned;
     if (const int rc = validate_params(params)) return rc;
     try {
         std::unique_ptr<SimBase> impl;
@@ -1455,7 +1169,6 @@ void hqn_default_params(hqn_params *p) {
     p->use_graph = 1;
     p->tet_block = TBS;
     p->ls_batch = 8;
-    p->dyn_sweeps = 0;
     p->n_colliders = 0;
     p->contact_scale = 100.0;
     p->a0_solver = 0;
@@ -1464,6 +1177,12 @@ void hqn_default_params(hqn_params *p) {
     p->cheb_S = 10;
     p->cheb_rho = 0.99;
     p->merge_depths = 0;
+    p->solve_threads = 256;
+    p->solve_item_kb = 64;
+    p->solve_items = 400;
+    p->solve_prefetch = 0;
+    p->wait_polls = 0;
+    p->fault_test = 0;
 }
 
 int sim_create(const hqn_mesh *mesh, const hqn_material *material, const hqn_params *params, void *stream,
@@ -1557,13 +1276,25 @@ int hqn_analyse(const hqn_mesh *mesh, const hqn_material *material, const hqn_pa
         info->precision = params->precision;
         info->graph_mode = params->use_graph ? 1 : 0;
         info->n_update_entries = S.n_upd;
-        info->sweep_schedule = params->dyn_sweeps;
+        info->solve_threads = params->solve_threads == 512 ? 512 : 256;
+        info->solve_item_kb = params->solve_item_kb > 0 ? params->solve_item_kb : 64;
+        info->solve_items = params->solve_items > 0 ? params->solve_items : 400;
+        info->solve_prefetch = params->solve_prefetch <= 0 ? 0 : params->solve_prefetch;
         info->n_sims = 1;
         return HQN_OK;
     } catch (const std::bad_alloc &) {
         return fail(HQN_ERR_NO_MEMORY, "host allocation failed");
     } catch (const std::exception &e) {
         return fail(HQN_ERR_ARG, e.what());
+    }
+}
+
+int sim_set_solve_shapes(sim_handle *sim, int32_t threads, int32_t item_kb, int32_t items, int32_t prefetch) {
+    if (!sim) return fail(HQN_ERR_ARG, "null handle");
+    try {
+        return sim->impl->set_solve_shapes(threads, item_kb, items, prefetch);
+    } catch (const std::bad_alloc &) {
+        return fail(HQN_ERR_NO_MEMORY, "host allocation failed");
     }
 }
 
@@ -1588,6 +1319,7 @@ const char *sim_strerror(int code) {
         case HQN_ERR_CUDA: return "CUDA error";
         case HQN_ERR_NO_MEMORY: return "out of memory";
         case HQN_ERR_UNSUPPORTED: return "unsupported option";
+        case HQN_ERR_DEVICE_TIMEOUT: return "device wait timed out";
         default: return "unknown status";
     }
 }

@@ -98,21 +98,15 @@ template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream
 
 // ---- triangular solves (solve.cu)
 constexpr int SOLVE_MAX_SMEM = 200 * 1024;  // dynamic shared memory of one sweep block
-// Pipelined sweeps: dynamic shared memory of a block (ring slots + vector
-// area), and per-bundle bounds the host schedule respects.
-constexpr int PIPE_MAX_SMEM = 220 * 1024;
-constexpr int PIPE_NS_MAX = 8;    // ring slots
-constexpr int PIPE_CONS_WARPS = 16;  // consumer warps of a block (plus one producer warp)
-constexpr int PIPE_SEG_MAX = 64;  // gather segments (supernodes) per bundle
-constexpr int PIPE_CMB_MAX = 32;  // chunk column blocks per bundle
 
 template <typename R>
 struct DevSolve {
     int nf, n_levels, n_sn;
     int pdl;                    // host: launch the level sweeps with programmatic dependent launch
-    int dyn;                    // host: 1 = dependency-driven persistent sweeps, 0 = one launch per level
-    int dyn_grid;               // host: blocks of a persistent sweep
-    int fwd_qmax, fwd_ldmax, bwd_qmax, bwd_ldmax;  // host: shared-memory sizes of the persistent sweeps
+    int threads;                // host: threads per sweep block (256 or 512)
+    int prefetch;               // host: launches ahead whose factor rows a level prefetches into L2 (0: none)
+    int fault_test;             // host: 1 = the first level's blocks issue no copy (tests of the bounded wait)
+    long long wait_polls;       // bound on a block's wait for its bulk copy, in polls
     int n_fwd_items, n_bwd_items;
     const R *QF;                // per supernode: packed Q_s, row-major (layout.hpp)
     const R *QB;                // per supernode: packed Q_s^T, row-major (layout.hpp)
@@ -128,46 +122,17 @@ struct DevSolve {
     // q0 = entry offset of the item's first row in QF / QB, bytes = size of its
     // rows, off0 = offset of that row inside its supernode's block; -1 = no
     // such supernode.  Forward items are in ascending, backward items in
-    // descending tree-level order (the dependency-driven queue order).
+    // descending tree-level order.
     const int4 *fwd_items, *bwd_items;
-    const int *fwd_nitems, *bwd_nitems;    // items of each supernode
-    int *fwd_done, *bwd_done;              // completed items of each supernode (this solve)
-    unsigned int *queue;                   // [0]: forward ticket, [1]: backward ticket
     const int *fwd_lvl_ptr;                // host: forward items of level l in [ptr[l], ptr[l+1])
     const int *bwd_lvl_start, *bwd_lvl_cnt;  // host: backward items of level l: [start[l], start[l] + cnt[l])
     const int *fwd_lvl_ld, *bwd_lvl_ld;    // host: max ldc / ldr of the level (shared memory)
     const int *fwd_lvl_q, *bwd_lvl_q;      // host: max factor entries of one item of the level
-    // Pipelined schedule (pipe = 1): one persistent launch per sweep, one block
-    // per SM.  Block b runs its own list of bundles; a bundle is consecutive
-    // items of one tree level (at most half the ring) sharing one wait for the
-    // items they read from in other blocks and one gather of the vectors
-    // their rows multiply (segments of the block's vector area, fcap entries
-    // per component).  A producer warp streams the block's items' factor rows
-    // into a ring of shared-memory slots ahead of the consumers, across levels.
-    //   items (in block order): forward  {q0 lo, q0 hi, bytes, G} {col, nc, ldc, uoff} {r0, r1, ldf, off0}
-    //                                    {foff, 0, w0, w1}
-    //                           backward {q0 lo, q0 hi, bytes, G} {col, nc, nrow, roff} {c0, c1, ldr, off0}
-    //                                    {woff, pslot0, w0, w1} {e0, e1, column block, nch << 16 | chunk}
-    //     foff / woff = vector-area offset of the item's first vector entry;
-    //     pslot0 = partial-sum slot of chunk 0 of the item's column block;
-    //     [w0, w1) = the consumer warps that run the item (a bundle's items
-    //     are resident together and run side by side)
-    //   bundles: {item0, item1, seg0, seg1} {dep0, dep1, sig0, sig1} {cmb0, cmb1, vector entries, 0}
-    //   segments: forward {col, filled entries, area offset, length};
-    //             backward {col, nc, nrow, roff} {w0, area offset, length, 0}
-    //   dep: (supernode, completed items to wait for); sig: (supernode, items completed)
-    //   cmb: {column block, chunks in the bundle, pslot0, nch} {first output vertex, columns, 0, 0}
-    int pipe;
-    int pipe_grid, pipe_ns, pipe_fcap;  // host: blocks, ring slots, vector-area entries
-    const int4 *pf_items, *pb_items;
-    const int4 *pf_bund, *pb_bund;
-    const int *pf_blk, *pb_blk;         // bundles of block b: [blk[b], blk[b + 1])
-    const int4 *pf_seg, *pb_seg;
-    const int2 *pf_dep, *pb_dep;
-    const int2 *pf_sig, *pb_sig;
-    const int4 *pb_cmb;
-    V4<R> *pb_part;                     // 32 partial sums per chunk slot
-    int *pb_cbc;                        // chunks finished per column block (re-arms itself)
+    // L2 prefetch spans {address lo, address hi, bytes, 0} of the factor rows
+    // each launch reads; launch k of a solve (forward level k for k < L, then
+    // backward level 2L - 1 - k) reads spans [pf_ptr[k], pf_ptr[k + 1]).
+    const int4 *pf_spans;
+    const int *pf_ptr;                     // host: 2 L + 1 entries
     V4<R> *u;                   // update vectors
     V4<R> *part_r;              // 32 partial sums per backward item (chunk items)
     int *cb_cnt;                // chunks finished per backward column block (re-arms itself)
@@ -177,12 +142,9 @@ struct DevSolve {
 // r = A0^{-1} q on the first nf entries (q, r: V4 arrays, may not alias).
 template <typename R>
 void launch_solve(const DevSolve<R> &s, const V4<R> *q, V4<R> *z, V4<R> *r, cudaStream_t st);
-template <typename R> int solve_smem_limit_ok(int max_cols);
-// Blocks of one persistent sweep (0 = cannot run the dependency-driven schedule).
-template <typename R> int solve_dyn_grid(const DevSolve<R> &s);
-// Pipelined schedule: ring slots for a vector area of fcap entries and the
-// blocks of one launch (0 = cannot run it).
-template <typename R> int solve_pipe_grid(int fcap, int *ns);
+// Dynamic shared memory of a sweep block staging qcap factor entries and
+// vectors of ld entries.
+template <typename R> size_t solve_block_smem(int qcap, int ld);
 // Raises the sweeps' dynamic shared-memory limits (once per device).
 template <typename R> cudaError_t solve_prepare();
 

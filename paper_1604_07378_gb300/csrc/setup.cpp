@@ -439,6 +439,23 @@ static int leaf_size_of(const hqn_params &prm, int n_free) {
     return prm.precision == HQN_FP32_MIXED && n_free <= 150000 ? 128 : 64;
 }
 
+int plan_sweeps(Setup &S, const hqn_params &prm, std::string &err) {
+    const int VN = prm.precision == HQN_FP64_PLAIN ? 2 : 4;
+    const int esize = prm.precision == HQN_FP64_PLAIN ? 8 : 4;
+    // a level's entries spread over solve_items items (default 400, a few
+    // blocks per SM), each within [kMax/4, kMax] entries, kMax =
+    // solve_item_kb KB (default 64)
+    const int item_kb = prm.solve_item_kb > 0 ? prm.solve_item_kb : 64;
+    const int per_level = prm.solve_items > 0 ? prm.solve_items : 400;
+    int rc = make_items(S, VN, item_kb * 1024 / esize, per_level, S.lv, err);
+    if (rc != HQN_OK) return rc;
+    // the longest vector a sweep block stages (what bounds its shared memory)
+    S.max_ld = 0;
+    for (int l = 0; l < S.n_levels; ++l)
+        S.max_ld = std::max(S.max_ld, std::max(S.lv.fwd_lvl_ld[l], S.lv.bwd_lvl_ld[l]));
+    return HQN_OK;
+}
+
 int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_params &prm,
                 Setup &S, std::string &err) {
     auto t_start = std::chrono::steady_clock::now();
@@ -801,11 +818,7 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
     }
 
     // ---- packed device layout (layout.hpp) and level work lists
-    // VN = entries per 16-byte vector in the device precision.
-    const int VN = prm.precision == HQN_FP64_PLAIN ? 2 : 4;
-    const int esize = prm.precision == HQN_FP64_PLAIN ? 8 : 4;
     S.qf_total = S.qb_total = 0;
-    S.max_ld = 0;
     for (auto &sn : S.sn) {
         sn.ldc = pad4(sn.ncol);
         sn.ldr = pad4(sn.ncol + sn.nrow);
@@ -813,20 +826,10 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
         sn.qb = S.qb_total;
         S.qf_total += fwd_row_off(sn.ncol + sn.nrow, sn.ncol, sn.ldc);
         S.qb_total += bwd_row_off(sn.ncol, sn.ldr);
-        S.max_ld = std::max(S.max_ld, std::max(sn.ldc, sn.ldr));
     }
     S.n_levels = 0;
     for (auto &sn : S.sn) S.n_levels = std::max(S.n_levels, sn.level + 1);
-    // level schedule: a level's entries spread over ~400 items (a few blocks
-    // per SM), each within [kMax/4, kMax] entries, kMax = 64 KB; pipelined
-    // schedule: items of at most one 32 KB ring slot, ~600 per level
-    int rc = make_items(S, VN, 65536 / esize, 400, S.lv, err);
-    if (rc == HQN_OK) rc = make_items(S, VN, kPipeSlotBytes / esize, 600, S.pp, err);
-    if (rc != HQN_OK) return rc;
-    // the longest vector a level-schedule block stages (what bounds its shared memory)
-    S.max_ld = 0;
-    for (int l = 0; l < S.n_levels; ++l)
-        S.max_ld = std::max(S.max_ld, std::max(S.lv.fwd_lvl_ld[l], S.lv.bwd_lvl_ld[l]));
+    if (int rc = plan_sweeps(S, prm, err)) return rc;
 
     S.setup_seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();

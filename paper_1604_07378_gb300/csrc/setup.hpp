@@ -55,10 +55,6 @@ struct ItemLists {
     std::vector<BwdItem> bwd_items;
 };
 
-// Bytes of one shared-memory ring slot of the pipelined sweeps: the factor
-// rows of one work item.
-constexpr int kPipeSlotBytes = 32768;
-
 struct Setup {
     int n = 0, T = 0, n_free = 0;
     double h = 1.0 / 30.0, k = 0.0, density = 0.0;
@@ -83,14 +79,17 @@ struct Setup {
                                      // children of a dissection node feed an entry, or
                                      // four under a merged supernode
     int n_upd = 0, n_levels = 0;
-    ItemLists lv;                    // items of the level-by-level schedules
-    ItemLists pp;                    // items of the pipelined schedule (one ring slot each)
+    ItemLists lv;                    // work items of the sweeps, level by level
     int64_t qf_total = 0, qb_total = 0;  // entries of the two packed copies
     int max_ld = 0;                  // longest vector a sweep block stages (bounds its shared memory)
     int max_front_cols = 0;          // max ncol
     int64_t factor_nnz = 0;
     double setup_seconds = 0.0;
 };
+
+// (Re)plans the sweeps' work items of a set-up for the shapes in prm
+// (solve_item_kb, solve_items, precision); cheap, no refactorisation.
+int plan_sweeps(Setup &S, const hqn_params &prm, std::string &err);
 
 // Builds everything; returns an HQN_* status and a message on failure.
 int build_setup(const hqn_mesh &mesh, const hqn_material &mat, const hqn_params &prm,

@@ -27,6 +27,19 @@
 // griddepcontrol.wait a block touches only data that no sweep writes (its
 // item record, the factor rows, the index tables); the vectors produced by
 // earlier levels and by the kernels before the solve are read after it.
+//
+// The factor does not depend on the solve's data, only the vectors do.  So
+// each level's blocks, as they start, also ask L2 to prefetch the factor rows
+// of the level `prefetch` launches ahead (cp.async.bulk.prefetch.L2, spans
+// listed by the host): the stream of the factor out of HBM runs ahead of the
+// chain of levels, and a level's own bulk copies then read L2.
+//
+// Every wait is bounded (wait_polls polls of the copy's mbarrier); past the
+// bound the block flags the error in the handle's control block and leaves
+// without reading its buffer, after its copy in flight, if any, has landed
+// (itself a bounded wait).  The host reports HQN_ERR_DEVICE_TIMEOUT.  For
+// tests of that path, fault_test = 1 makes the first level's blocks skip
+// their copies, so their waits run out with nothing in flight.
 #include "kernels.cuh"
 #include "layout.hpp"
 #include "reduce.cuh"
@@ -35,8 +48,7 @@ namespace hqn {
 
 namespace {
 
-constexpr int SBS = 256;                  // threads per block of the sweeps
-constexpr long long kWaitPolls = 1 << 20;  // bound on the bulk-copy wait (polls)
+constexpr long long kDrainPolls = 1LL << 26;  // bound on waiting for a copy in flight after a timeout
 
 template <typename R> struct Vec16;
 template <> struct Vec16<float> {
@@ -95,8 +107,9 @@ __device__ __forceinline__ void bulk_load_issue(uint64_t *bar, void *dst, const 
     bulk_copy(bar, dst, src, bytes);
 }
 
-__device__ __forceinline__ bool bulk_load_wait(uint64_t *bar, uint32_t parity) {
-    for (long long it = 0; it < kWaitPolls; ++it) {
+// Polls the barrier's phase `parity` at most `polls` times.
+__device__ __forceinline__ bool bulk_load_wait(uint64_t *bar, uint32_t parity, long long polls) {
+    for (long long it = 0; it < polls; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -111,21 +124,42 @@ __device__ __forceinline__ bool bulk_load_wait(uint64_t *bar, uint32_t parity) {
 // Every thread waits for the phase `parity` of the block's bulk copy (the
 // barrier's init by thread 0 and this wait are separated by a __syncthreads
 // here).  Returns false (after flagging the error) if it did not complete
-// within the poll bound; the block must then leave without reading the buffer.
-__device__ __forceinline__ bool bulk_load_finish(uint64_t *bar, uint32_t parity, unsigned int *err) {
+// within `polls` polls; the block must then leave without reading the buffer.
+// A block must not exit while a bulk copy into its shared memory is in
+// flight, so after a timeout thread 0 keeps waiting for an issued copy (up to
+// kDrainPolls polls, flagging bit 4 if even that runs out) before it returns;
+// the block ends only when thread 0 does.
+__device__ __forceinline__ bool bulk_load_finish(uint64_t *bar, uint32_t parity, unsigned int *err, long long polls,
+                                                 bool issued) {
     __shared__ int timed_out;
     if (threadIdx.x == 0) timed_out = 0;
     __syncthreads();
-    if (!bulk_load_wait(bar, parity)) timed_out = 1;
+    if (!bulk_load_wait(bar, parity, polls)) timed_out = 1;
     __syncthreads();
     if (timed_out) {
         if (threadIdx.x == 0) {
             atomicOr(err, 1u);
-            bulk_load_wait(bar, parity);  // give the copy in flight one more bounded chance to land
+            if (issued && !bulk_load_wait(bar, parity, kDrainPolls)) atomicOr(err, 4u);
         }
         return false;
     }
     return true;
+}
+
+// Asks L2 to fetch `bytes` (a multiple of 16) at the 16-byte aligned address p.
+__device__ __forceinline__ void l2_prefetch(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Thread 0 of every block of a level: its share of the prefetch spans
+// {address lo, address hi, bytes, 0} of the level `prefetch` launches ahead.
+__device__ __forceinline__ void prefetch_ahead(const int4 *pf, int pf_n) {
+    if (threadIdx.x != 0) return;
+    for (int j = blockIdx.x; j < pf_n; j += gridDim.x) {
+        const int4 a = pf[j];
+        const unsigned long long addr = (unsigned long long)(unsigned)a.x | ((unsigned long long)(unsigned)a.y << 32);
+        l2_prefetch(reinterpret_cast<const void *>(addr), (uint32_t)a.z);
+    }
 }
 
 // ---- programmatic dependent launch (PTX ISA: griddepcontrol)
@@ -255,12 +289,14 @@ __device__ __forceinline__ void fwd_rows_g(int G, const DevSolve<R> &S, int col,
 // their source indices (ldf int4 for the columns, nrr int4 for the rows; up
 // to four children feed an entry, -1 = none).  Every
 // load of a vector another item produces is issued in one parallel pass
-// after `wait_inputs`, so the row products read only shared memory.
-template <typename R, typename Wait>
+// after the wait on the previous level, so the row products read only
+// shared memory.  NT threads per block.
+template <typename R, int NT>
 __device__ __forceinline__ void fwd_item(const DevSolve<R> &S, const int4 *rec, int qcap, R *qs, uint64_t *bar,
-                                         uint32_t parity, const V4<R> *rhs, V4<R> *z, Wait wait_inputs) {
+                                         const V4<R> *rhs, V4<R> *z, bool issue, const int4 *pf, int pf_n) {
     const int4 a = rec[0];
-    if (threadIdx.x == 0) bulk_load_issue(bar, qs, item_src(S.QF, a, sizeof(R)), (uint32_t)a.z);
+    if (threadIdx.x == 0 && issue) bulk_load_issue(bar, qs, item_src(S.QF, a, sizeof(R)), (uint32_t)a.z);
+    prefetch_ahead(pf, pf_n);
     const int4 b = rec[1], c = rec[2];
     const int col = b.x, nc = b.y, ldc = b.z, uoff = b.w;
     const int r0 = c.x, r1 = c.y, ldf = c.z, off0 = c.w;
@@ -270,17 +306,15 @@ __device__ __forceinline__ void fwd_item(const DevSolve<R> &S, const int4 *rec, 
     int4 *cidx = reinterpret_cast<int4 *>(ua + 3 * nrr4);
     int4 *ridx = cidx + ldf;
     const int nf = ldf < nc ? ldf : nc;
-    for (int j = threadIdx.x; j < nf; j += SBS) cidx[j] = __ldg(S.fg4 + col + j);
-    for (int j = threadIdx.x; j < nrr; j += SBS) ridx[j] = __ldg(S.ug4 + uoff + rr0 - nc + j);
-    if (!wait_inputs()) {
-        if (threadIdx.x == 0) bulk_load_wait(bar, parity);  // let the copy in flight land first
-        return;
-    }
+    for (int j = threadIdx.x; j < nf; j += NT) cidx[j] = __ldg(S.fg4 + col + j);
+    for (int j = threadIdx.x; j < nrr; j += NT) ridx[j] = __ldg(S.ug4 + uoff + rr0 - nc + j);
+    pdl_trigger();
+    pdl_wait();
     // f = q_C - (child updates on C), entries [0, ldf), zero beyond nc; and
     // the child updates landing on the rectangle rows
     const int nj = ldf > nrr ? ldf : nrr;
 #pragma unroll 2
-    for (int j = threadIdx.x; j < nj; j += SBS) {
+    for (int j = threadIdx.x; j < nj; j += NT) {
         V4<R> v, u[4], w[4];
         v.x = v.y = v.z = R(0);
 #pragma unroll
@@ -311,22 +345,20 @@ __device__ __forceinline__ void fwd_item(const DevSolve<R> &S, const int4 *rec, 
             ua[2 * nrr4 + j] = w[0].z + w[1].z + w[2].z + w[3].z;
         }
     }
-    if (!bulk_load_finish(bar, parity, S.err)) return;
-    fwd_rows_g<R>(a.w, S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z, (int)threadIdx.x, SBS, ua, nrr4, rr0);
+    if (!bulk_load_finish(bar, 0u, S.err, S.wait_polls, issue)) return;
+    fwd_rows_g<R>(a.w, S, col, nc, ldc, uoff, r0, r1, off0, qs, f, ldf, z, (int)threadIdx.x, NT, ua, nrr4, rr0);
 }
 
-// Level-synchronous schedule: one launch per tree level, one item per block.
-template <typename R>
-__global__ void __launch_bounds__(SBS, 4) k_fwd(DevSolve<R> S, int item0, int qcap, const V4<R> *rhs, V4<R> *z) {
+// One launch per tree level, one item per block.  skip_copy (fault tests
+// only): the block issues no copy, so its wait runs out.
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_fwd(DevSolve<R> S, int item0, int qcap, const V4<R> *rhs,
+                                                       V4<R> *z, const int4 *pf, int pf_n, int skip_copy) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) bulk_bar_init(&bar);
-    fwd_item<R>(S, S.fwd_items + 5 * (size_t)(item0 + blockIdx.x), qcap, reinterpret_cast<R *>(smem_raw), &bar, 0u,
-                rhs, z, []() {
-                    pdl_trigger();
-                    pdl_wait();
-                    return true;
-                });
+    fwd_item<R, NT>(S, S.fwd_items + 5 * (size_t)(item0 + blockIdx.x), qcap, reinterpret_cast<R *>(smem_raw), &bar,
+                    rhs, z, skip_copy == 0, pf, pf_n);
 }
 
 // ---- backward sweep
@@ -420,10 +452,9 @@ __device__ __forceinline__ void bwd_rows_g(int G, int col, int ldr, int c0, int 
 // A chunk item (rec[4].x >= 0) copies each of its rows' pieces separately and
 // writes partial sums; the last chunk of its column block to finish adds the
 // chunks' partials in chunk order and writes r.
-template <typename R, typename Wait>
+template <typename R, int NT>
 __device__ __forceinline__ void bwd_item(const DevSolve<R> &S, const int4 *rec, int item, int qcap, R *qs,
-                                         uint64_t *bar, uint32_t parity, const V4<R> *z, V4<R> *r,
-                                         Wait wait_inputs) {
+                                         uint64_t *bar, const V4<R> *z, V4<R> *r, const int4 *pf, int pf_n) {
     const int4 a = rec[0], b = rec[1], c = rec[2], e = rec[4];
     const int col = b.x, nc = b.y, nr = b.z, roff = b.w;
     const int c0 = c.x, c1 = c.y, ldr = c.z, off0 = c.w;
@@ -448,18 +479,17 @@ __device__ __forceinline__ void bwd_item(const DevSolve<R> &S, const int4 *rec, 
             }
         }
     }
+    prefetch_ahead(pf, pf_n);
     R *w = qs + qcap;
     int *ridx = reinterpret_cast<int *>(w + 3 * lw);
-    for (int k = threadIdx.x; k < lw; k += SBS) {
+    for (int k = threadIdx.x; k < lw; k += NT) {
         const int i = w0 + k;
         ridx[k] = (i >= nc && i < rows) ? S.rows[roff + i - nc] : -1;
     }
-    if (!wait_inputs()) {
-        if (threadIdx.x == 0) bulk_load_wait(bar, parity);  // let the copies in flight land first
-        return;
-    }
+    pdl_trigger();
+    pdl_wait();
 #pragma unroll 4
-    for (int k = threadIdx.x; k < lw; k += SBS) {
+    for (int k = threadIdx.x; k < lw; k += NT) {
         const int i = w0 + k;
         R vx = R(0), vy = R(0), vz = R(0);
         if (i < nc) {
@@ -471,18 +501,18 @@ __device__ __forceinline__ void bwd_item(const DevSolve<R> &S, const int4 *rec, 
         }
         w[k] = vx; w[lw + k] = vy; w[2 * lw + k] = vz;
     }
-    if (!bulk_load_finish(bar, parity, S.err)) return;
+    if (!bulk_load_finish(bar, 0u, S.err, S.wait_polls, true)) return;
     if (!chunk) {
-        bwd_rows_g<R, false>(a.w, col, ldr, c0, c1, off0, qs, w, lw, lw, w0, r, nullptr, (int)threadIdx.x, SBS);
+        bwd_rows_g<R, false>(a.w, col, ldr, c0, c1, off0, qs, w, lw, lw, w0, r, nullptr, (int)threadIdx.x, NT);
         return;
     }
     const int nch = e.w >> 16, kch = e.w & 0xffff;
     if (nch == 1) {
-        bwd_rows_g<R, true>(a.w, col, ldr, c0, c1, off0, qs, w, lw, lw, w0, r, nullptr, (int)threadIdx.x, SBS);
+        bwd_rows_g<R, true>(a.w, col, ldr, c0, c1, off0, qs, w, lw, lw, w0, r, nullptr, (int)threadIdx.x, NT);
         return;
     }
     V4<R> *mine = S.part_r + (size_t)item * 32;
-    bwd_rows_g<R, true>(a.w, col, ldr, c0, c1, off0, qs, w, lw, lw, w0, r, mine, (int)threadIdx.x, SBS);
+    bwd_rows_g<R, true>(a.w, col, ldr, c0, c1, off0, qs, w, lw, lw, w0, r, mine, (int)threadIdx.x, NT);
     // the last chunk of the column block to get here combines the partials
     __shared__ int last;
     __syncthreads();
@@ -507,516 +537,15 @@ __device__ __forceinline__ void bwd_item(const DevSolve<R> &S, const int4 *rec, 
     if (threadIdx.x == 0) S.cb_cnt[e.z] = 0;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(SBS, 4) k_bwd(DevSolve<R> S, int item0, int qcap, const V4<R> *z, V4<R> *r) {
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_bwd(DevSolve<R> S, int item0, int qcap, const V4<R> *z, V4<R> *r,
+                                                       const int4 *pf, int pf_n) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) bulk_bar_init(&bar);
     const int item = item0 + blockIdx.x;
-    bwd_item<R>(S, S.bwd_items + 5 * (size_t)item, item, qcap, reinterpret_cast<R *>(smem_raw), &bar, 0u, z, r,
-                []() {
-                    pdl_trigger();
-                    pdl_wait();
-                    return true;
-                });
-}
-
-// ---- dependency-driven schedule: one persistent launch per sweep
-//
-// Blocks take items from a queue (an atomic ticket) in topological order:
-// forward items leaf level first, backward items root level first.  An item
-// waits only for the items it reads from -- a forward item for every item of
-// its supernode's children, a backward item for every item of its parent
-// (whose own inputs were complete before it finished) -- by polling their
-// supernodes' completion counters.  Because items are taken in topological
-// order, every item waited on was taken earlier by a running block, so the
-// waits end.  Each wait is bounded all the same: past the bound the block sets
-// the error flag, and every later wait sees the flag and gives up at once.
-// Each sweep resets the other sweep's counters and queue for the next solve.
-
-constexpr long long kDepPolls = 1 << 22;
-
-// Thread 0 waits until counter[sn] >= need (sn < 0: nothing to wait for).
-__device__ __forceinline__ bool dep_wait(const int *counter, int sn, int need, unsigned int *err) {
-    if (sn < 0) return true;
-    const volatile int *c = counter + sn;
-    for (long long it = 0; it < kDepPolls; ++it) {
-        if (*c >= need) {
-            __threadfence();
-            return true;
-        }
-        if (*(volatile unsigned int *)err) return false;
-        __nanosleep(32);
-    }
-    atomicOr(err, 2u);
-    return false;
-}
-
-// Block-uniform: false once any block has flagged an error.
-__device__ __forceinline__ bool still_ok(const unsigned int *err) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) ok = *(const volatile unsigned int *)err == 0u;
-    __syncthreads();
-    return ok != 0;
-}
-
-// After the block's outputs of an item are written: publish them.
-__device__ __forceinline__ void dep_signal(int *counter, int sn) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(counter + sn, 1);
-    }
-}
-
-template <typename R>
-__global__ void __launch_bounds__(SBS) k_fwd_dyn(DevSolve<R> S, int qcap, const V4<R> *rhs, V4<R> *z) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ int item_sh, ok_sh;
-    R *qs = reinterpret_cast<R *>(smem_raw);
-    for (int i = blockIdx.x * SBS + threadIdx.x; i < S.n_sn; i += gridDim.x * SBS) S.bwd_done[i] = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) S.queue[1] = 0;
-    if (threadIdx.x == 0) bulk_bar_init(&bar);
-    uint32_t parity = 0;
-    for (;;) {
-        if (threadIdx.x == 0) item_sh = (int)atomicAdd(&S.queue[0], 1u);
-        __syncthreads();
-        const int item = item_sh;
-        if (item >= S.n_fwd_items) break;
-        const int4 *rec = S.fwd_items + 5 * (size_t)item;
-        const int4 dep = rec[3];  // children c0 .. c3 (-1: none)
-        const int own = rec[4].x;
-        fwd_item<R>(S, rec, qcap, qs, &bar, parity, rhs, z, [&]() {
-            if (threadIdx.x == 0)
-                ok_sh = dep_wait(S.fwd_done, dep.x, dep.x >= 0 ? S.fwd_nitems[dep.x] : 0, S.err) &&
-                        dep_wait(S.fwd_done, dep.y, dep.y >= 0 ? S.fwd_nitems[dep.y] : 0, S.err) &&
-                        dep_wait(S.fwd_done, dep.z, dep.z >= 0 ? S.fwd_nitems[dep.z] : 0, S.err) &&
-                        dep_wait(S.fwd_done, dep.w, dep.w >= 0 ? S.fwd_nitems[dep.w] : 0, S.err);
-            __syncthreads();
-            return ok_sh != 0;
-        });
-        if (!still_ok(S.err)) break;
-        dep_signal(S.fwd_done, own);
-        parity ^= 1u;
-    }
-}
-
-template <typename R>
-__global__ void __launch_bounds__(SBS) k_bwd_dyn(DevSolve<R> S, int qcap, const V4<R> *z, V4<R> *r) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ int item_sh, ok_sh;
-    R *qs = reinterpret_cast<R *>(smem_raw);
-    for (int i = blockIdx.x * SBS + threadIdx.x; i < S.n_sn; i += gridDim.x * SBS) S.fwd_done[i] = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) S.queue[0] = 0;
-    if (threadIdx.x == 0) bulk_bar_init(&bar);
-    uint32_t parity = 0;
-    for (;;) {
-        if (threadIdx.x == 0) item_sh = (int)atomicAdd(&S.queue[1], 1u);
-        __syncthreads();
-        const int item = item_sh;
-        if (item >= S.n_bwd_items) break;
-        const int4 *rec = S.bwd_items + 5 * (size_t)item;
-        const int4 dep = rec[3];  // parent (-1: none), own supernode
-        bwd_item<R>(S, rec, item, qcap, qs, &bar, parity, z, r, [&]() {
-            if (threadIdx.x == 0) ok_sh = dep_wait(S.bwd_done, dep.x, dep.x >= 0 ? S.bwd_nitems[dep.x] : 0, S.err);
-            __syncthreads();
-            return ok_sh != 0;
-        });
-        if (!still_ok(S.err)) break;
-        dep_signal(S.bwd_done, dep.y);
-        parity ^= 1u;
-    }
-}
-
-// ---- pipelined schedule: one persistent launch per sweep, one block per SM
-//
-// Each block owns a fixed list of bundles (consecutive items of one tree
-// level), in level order: ascending for the forward sweep, descending for the
-// backward one.  Its last warp is a producer: it streams the factor rows of
-// the block's items, in order, into a ring of shared-memory slots (one bulk
-// copy per item, completion on the slot's `full` mbarrier) as soon as the
-// consumers release a slot (its `empty` mbarrier, one arrival per consumer
-// warp) -- the factor does not depend on the sweep, so the stream runs ahead
-// across levels while the consumers wait for other blocks.  The other warps
-// consume a bundle in four steps: wait until the items it reads from (other
-// blocks' or its own) have published, gather the vector its rows multiply
-// into the vector area (one segment per supernode), run its items' row dot
-// products from the ring, then publish (per-supernode completion counters).
-//
-// Progress: every block's waits are on items of earlier levels only, and the
-// grid is at most one block per SM with all blocks resident (the launch
-// asks for exactly the blocks that fit), so the lowest unfinished level
-// always advances.  Every wait is bounded; past the bound the block sets the
-// error flag, skips its remaining work and, before it exits, waits (bounded)
-// for the copies it has in flight.
-
-constexpr int PCONS = 32 * PIPE_CONS_WARPS;  // consumer threads of a pipelined sweep block
-constexpr int PTHREADS = PCONS + 32;        // plus one producer warp
-constexpr int PIPE_SLOT = 32768;            // bytes per ring slot (the host's item bound)
-constexpr long long kEmptyPolls = 1 << 22;  // bound on the producer's wait for a free slot
-
-struct PipeShared {
-    uint64_t full[PIPE_NS_MAX];   // slot holds its item's rows (bulk-copy bytes arrived)
-    uint64_t empty[PIPE_NS_MAX];  // slot released by every consumer warp
-    int abort;                    // set by a thread that gave up; ends the block's work
-    int k_issued;                 // items whose copies the producer has started
-    int seg_aoff[PIPE_SEG_MAX];   // vector-area offsets of the bundle's segments
-    int4 seg[2 * PIPE_SEG_MAX];
-    int mine[PIPE_CMB_MAX];       // this bundle completed the column block: it combines it
-};
-
-__device__ __forceinline__ void cons_sync() { asm volatile("bar.sync 1, %0;" ::"n"(PCONS) : "memory"); }
-// Consumer barrier that also returns, to every consumer, whether any of them
-// passed true.
-__device__ __forceinline__ bool cons_any(bool v) {
-    uint32_t r;
-    asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
-        : "=r"(r)
-        : "r"((uint32_t)v), "n"(PCONS)
-        : "memory");
-    return r != 0;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Producer warp: items [it0, it1) of the block, slot k % ns for the k-th.
-template <typename R, bool BWD>
-__device__ void pipe_produce(const DevSolve<R> &S, int it0, int it1, R *ring, PipeShared &sh, int ns) {
-    constexpr int SLOT_E = PIPE_SLOT / (int)sizeof(R);
-    const int lane = threadIdx.x & 31;
-    volatile int *abort = &sh.abort;
-    for (int it = it0; it < it1; ++it) {
-        const int k = it - it0, slot = k % ns, use = k / ns;
-        int ok = 1;
-        if (lane == 0) {
-            if (use > 0) {
-                ok = 0;
-                for (long long p = 0; p < kEmptyPolls && !*abort; ++p)
-                    if (mbar_test(&sh.empty[slot], (uint32_t)((use - 1) & 1))) {
-                        ok = 1;
-                        break;
-                    }
-                if (!ok && !*abort) {
-                    atomicOr(S.err, 8u);
-                    *abort = 1;
-                }
-            }
-            if (*abort) ok = 0;
-        }
-        if (!__shfl_sync(0xffffffffu, ok, 0)) break;  // lane 0 decides for the warp
-        R *dst = ring + (size_t)slot * SLOT_E;
-        if (!BWD) {
-            const int4 a = S.pf_items[4 * (size_t)it];
-            if (lane == 0) bulk_load_issue(&sh.full[slot], dst, item_src(S.QF, a, sizeof(R)), (uint32_t)a.z);
-        } else {
-            const int4 *rec = S.pb_items + 5 * (size_t)it;
-            const int4 a = rec[0], e = rec[4];
-            if (e.x < 0) {
-                if (lane == 0) bulk_load_issue(&sh.full[slot], dst, item_src(S.QB, a, sizeof(R)), (uint32_t)a.z);
-            } else {
-                // a chunk item: row j's piece [max(e0, start_j), e1) at dst + (j - c0) lw
-                const int4 c = rec[2];
-                const int c0 = c.x, c1 = c.y, ldr = c.z;
-                const int w0 = e.x, lw = e.y - e.x;
-                if (lane == 0) bulk_expect(&sh.full[slot], (uint32_t)a.z);
-                const int j = c0 + lane;
-                if (j < c1) {
-                    const int st = bwd_row_start(j);
-                    const int seg = st > w0 ? st : w0;
-                    const int len = w0 + lw - seg;
-                    if (len > 0) {
-                        const R *src =
-                            static_cast<const R *>(item_src(S.QB, a, sizeof(R))) + bwd_row_off(j, ldr) + (seg - st);
-                        bulk_copy(&sh.full[slot], dst + (size_t)(j - c0) * lw + (seg - w0), src,
-                                  (uint32_t)(len * sizeof(R)));
-                    }
-                }
-            }
-        }
-        __syncwarp();
-        if (lane == 0) sh.k_issued = k + 1;
-    }
-}
-
-// Segment of vector-area entry e: the last one starting at or before it.
-__device__ __forceinline__ int pipe_seg_of(const PipeShared &sh, int nseg, int e) {
-    int lo = 0, hi = nseg - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (sh.seg_aoff[mid] <= e) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Gathers take PG entries per thread at a time: every load of a round is
-// issued before any result is used, so a round costs two dependent trips to
-// memory (index, then value) whatever PG is.
-constexpr int PG = 4;
-
-// Consumers, forward: f = q_C - (child updates on C) for every segment.
-template <typename R>
-__device__ __forceinline__ void pipe_gather_fwd(const DevSolve<R> &S, const PipeShared &sh, int nseg, int ftot, R *F,
-                                                int fcap, const V4<R> *rhs) {
-    for (int base = threadIdx.x; base < ftot; base += PG * PCONS) {
-        V4<R> v[PG];
-        int4 ci[PG];
-#pragma unroll
-        for (int g = 0; g < PG; ++g) {
-            const int e = base + g * PCONS;
-            v[g].x = v[g].y = v[g].z = v[g].w = R(0);
-            ci[g] = make_int4(-1, -1, -1, -1);
-            if (e < ftot) {
-                const int4 sg = sh.seg[pipe_seg_of(sh, nseg, e)];  // {col, filled, area offset, length}
-                const int j = e - sg.z;
-                if (j < sg.y) {
-                    v[g] = ld_cg(rhs + sg.x + j);
-                    ci[g] = __ldg(S.fg4 + sg.x + j);
-                }
-            }
-        }
-        V4<R> a[PG], b[PG], c[PG], d[PG];
-#pragma unroll
-        for (int g = 0; g < PG; ++g) {
-            a[g].x = a[g].y = a[g].z = R(0);
-            b[g] = a[g]; c[g] = a[g]; d[g] = a[g];
-            if (ci[g].x >= 0) a[g] = ld_cg(S.u + ci[g].x);
-            if (ci[g].y >= 0) b[g] = ld_cg(S.u + ci[g].y);
-            if (ci[g].z >= 0) c[g] = ld_cg(S.u + ci[g].z);
-            if (ci[g].w >= 0) d[g] = ld_cg(S.u + ci[g].w);
-        }
-#pragma unroll
-        for (int g = 0; g < PG; ++g) {
-            const int e = base + g * PCONS;
-            if (e < ftot) {
-                F[e] = v[g].x - a[g].x - b[g].x - c[g].x - d[g].x;
-                F[fcap + e] = v[g].y - a[g].y - b[g].y - c[g].y - d[g].y;
-                F[2 * fcap + e] = v[g].z - a[g].z - b[g].z - c[g].z - d[g].z;
-            }
-        }
-    }
-}
-
-// Consumers, backward: w = [z_C; -r_R] over each segment's range.
-template <typename R>
-__device__ __forceinline__ void pipe_gather_bwd(const DevSolve<R> &S, const PipeShared &sh, int nseg, int ftot, R *F,
-                                                int fcap, const V4<R> *z, const V4<R> *r) {
-    for (int base = threadIdx.x; base < ftot; base += PG * PCONS) {
-        int src[PG];
-        R sgn[PG];
-#pragma unroll
-        for (int g = 0; g < PG; ++g) {
-            const int e = base + g * PCONS;
-            src[g] = -1;
-            sgn[g] = R(1);
-            if (e < ftot) {
-                const int q = pipe_seg_of(sh, nseg, e);
-                const int4 sa = sh.seg[2 * q], sb = sh.seg[2 * q + 1];  // {col, nc, nrow, roff} {w0, aoff, len, 0}
-                const int i = sb.x + (e - sb.y);
-                if (i < sa.y) {
-                    src[g] = sa.x + i;
-                } else if (i < sa.y + sa.z) {
-                    src[g] = __ldg(S.rows + sa.w + i - sa.y);
-                    sgn[g] = R(-1);
-                }
-            }
-        }
-        V4<R> v[PG];
-#pragma unroll
-        for (int g = 0; g < PG; ++g) {
-            v[g].x = v[g].y = v[g].z = R(0);
-            if (src[g] >= 0) v[g] = ld_cg((sgn[g] > R(0) ? z : r) + src[g]);
-        }
-#pragma unroll
-        for (int g = 0; g < PG; ++g) {
-            const int e = base + g * PCONS;
-            if (e < ftot) {
-                F[e] = sgn[g] * v[g].x;
-                F[fcap + e] = sgn[g] * v[g].y;
-                F[2 * fcap + e] = sgn[g] * v[g].z;
-            }
-        }
-    }
-}
-
-// Consumer warps: bundles [b0, b1) of the block, whose items start at it0.
-// Forward: in = q, out = z.  Backward: in = z, out = r.
-template <typename R, bool BWD>
-__device__ void pipe_consume(const DevSolve<R> &S, int b0, int b1, int it0, const R *ring, R *F, PipeShared &sh,
-                             const V4<R> *in, V4<R> *out) {
-    constexpr int SLOT_E = PIPE_SLOT / (int)sizeof(R);
-    const int tid = threadIdx.x;
-    const int ns = S.pipe_ns, fcap = S.pipe_fcap;
-    const int4 *bund = BWD ? S.pb_bund : S.pf_bund;
-    const int4 *segs = BWD ? S.pb_seg : S.pf_seg;
-    const int2 *dep = BWD ? S.pb_dep : S.pf_dep;
-    const int2 *sig = BWD ? S.pb_sig : S.pf_sig;
-    int *done = BWD ? S.bwd_done : S.fwd_done;
-    volatile int *abort = &sh.abort;
-    for (int b = b0; b < b1; ++b) {
-        const int4 B0 = bund[3 * (size_t)b], B1 = bund[3 * (size_t)b + 1], B2 = bund[3 * (size_t)b + 2];
-        // 1. the items this bundle reads from have published
-        if (tid < B1.y - B1.x) {
-            const int2 d = dep[B1.x + tid];
-            if (!dep_wait(done, d.x, d.y, S.err)) *abort = 1;
-        }
-        if (tid == 0 && *(volatile unsigned int *)S.err) *abort = 1;
-        const int nseg = B0.w - B0.z;
-        for (int i = tid; i < nseg; i += PCONS) {
-            if (BWD) {
-                const int4 sa = segs[2 * (size_t)(B0.z + i)], sb = segs[2 * (size_t)(B0.z + i) + 1];
-                sh.seg[2 * i] = sa;
-                sh.seg[2 * i + 1] = sb;
-                sh.seg_aoff[i] = sb.y;
-            } else {
-                const int4 sg = segs[B0.z + i];
-                sh.seg[i] = sg;
-                sh.seg_aoff[i] = sg.z;
-            }
-        }
-        if (cons_any(*abort)) break;
-        // 2. the vector the rows multiply
-        if (BWD) pipe_gather_bwd<R>(S, sh, nseg, B2.z, F, fcap, in, out);
-        else pipe_gather_fwd<R>(S, sh, nseg, B2.z, F, fcap, in);
-        cons_sync();
-        // 3. the items, from the ring: all of the bundle's items are resident
-        // at once (the host keeps a bundle within half the ring); each runs on
-        // its own range of consumer warps (item record: warps [w0, w1))
-        bool ready = true;
-        for (int it = B0.x; it < B0.y; ++it) {
-            const int k = it - it0;
-            ready = ready && bulk_load_wait(&sh.full[k % ns], (uint32_t)((k / ns) & 1));
-        }
-        if (!ready) *abort = 1;
-        if (cons_any(!ready || *abort)) break;
-        {
-            const int warp = tid >> 5;
-            int it = B0.x;
-            int4 d = BWD ? S.pb_items[5 * (size_t)it + 3] : S.pf_items[4 * (size_t)it + 3];
-            while (warp >= d.w && it + 1 < B0.y) {
-                ++it;
-                d = BWD ? S.pb_items[5 * (size_t)it + 3] : S.pf_items[4 * (size_t)it + 3];
-            }
-            const int k = it - it0;
-            const R *qs = ring + (size_t)(k % ns) * SLOT_E;
-            const int ltid = tid - 32 * d.z, lnt = 32 * (d.w - d.z);
-            if (!BWD) {
-                const int4 *rec = S.pf_items + 4 * (size_t)it;
-                const int4 a = rec[0], bb = rec[1], c = rec[2];
-                fwd_rows_g<R>(a.w, S, bb.x, bb.y, bb.z, bb.w, c.x, c.y, c.w, qs, F + d.x, fcap, out, ltid, lnt);
-            } else {
-                const int4 *rec = S.pb_items + 5 * (size_t)it;
-                const int4 a = rec[0], bb = rec[1], c = rec[2], e = rec[4];
-                const int c0 = c.x, c1 = c.y, ldr = c.z, off0 = c.w;
-                if (e.x < 0) {
-                    const int w0 = bwd_row_start(c0);
-                    bwd_rows_g<R, false>(a.w, bb.x, ldr, c0, c1, off0, qs, F + d.x, fcap, ldr - w0, w0, out, nullptr,
-                                         ltid, lnt);
-                } else {
-                    const int nch = e.w >> 16, kch = e.w & 0xffff;
-                    V4<R> *part = nch > 1 ? S.pb_part + (size_t)(d.y + kch) * 32 : nullptr;
-                    bwd_rows_g<R, true>(a.w, bb.x, ldr, c0, c1, off0, qs, F + d.x, fcap, e.y - e.x, e.x, out, part,
-                                        ltid, lnt);
-                }
-            }
-            __syncwarp();
-            if ((tid & 31) == 0)
-                for (int q = B0.x; q < B0.y; ++q) mbar_arrive(&sh.empty[(q - it0) % ns]);
-        }
-        if (cons_any(*abort)) break;
-        // 4. (backward) column blocks whose last chunks this bundle ran: add
-        // the chunks' partial sums in chunk order
-        if (BWD && B2.y > B2.x) {
-            const int ncmb = B2.y - B2.x;
-            if (tid < ncmb) {
-                const int4 c = S.pb_cmb[2 * (size_t)(B2.x + tid)];  // {column block, count, pslot0, nch}
-                __threadfence();
-                sh.mine[tid] = atomicAdd(S.pb_cbc + c.x, c.y) + c.y == c.w;
-            }
-            cons_sync();
-            for (int q = 0; q < ncmb; ++q) {
-                if (!sh.mine[q]) continue;
-                const int4 c = S.pb_cmb[2 * (size_t)(B2.x + q)], o = S.pb_cmb[2 * (size_t)(B2.x + q) + 1];
-                __threadfence();
-                if (tid < o.y) {
-                    R sx = R(0), sy = R(0), sz = R(0);
-                    for (int kk = 0; kk < c.w; ++kk) {
-                        const V4<R> p = ld_cg(S.pb_part + (size_t)(c.z + kk) * 32 + tid);
-                        sx += p.x; sy += p.y; sz += p.z;
-                    }
-                    V4<R> v; v.x = sx; v.y = sy; v.z = sz; v.w = R(0);
-                    out[o.x + tid] = v;
-                }
-                if (tid == 0) S.pb_cbc[c.x] = 0;
-            }
-            cons_sync();
-        }
-        // 5. publish
-        if (tid < B1.w - B1.z) {
-            const int2 g = sig[B1.z + tid];
-            __threadfence();
-            atomicAdd(done + g.x, g.y);
-        }
-    }
-}
-
-template <typename R, bool BWD>
-__global__ void __launch_bounds__(PTHREADS, 1) k_pipe(DevSolve<R> S, const V4<R> *in, V4<R> *out) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ PipeShared sh;
-    constexpr int SLOT_E = PIPE_SLOT / (int)sizeof(R);
-    const int ns = S.pipe_ns;
-    R *ring = reinterpret_cast<R *>(smem_raw);
-    R *F = ring + (size_t)ns * SLOT_E;
-    const int tid = threadIdx.x;
-    // the other sweep's counters start from zero in the next solve
-    int *other = BWD ? S.fwd_done : S.bwd_done;
-    for (int i = blockIdx.x * PTHREADS + tid; i < S.n_sn; i += gridDim.x * PTHREADS) other[i] = 0;
-    if (tid == 0) {
-        for (int q = 0; q < ns; ++q) {
-            mbar_init(&sh.full[q], 1);
-            mbar_init(&sh.empty[q], PCONS / 32);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        sh.abort = 0;
-        sh.k_issued = 0;
-    }
-    __syncthreads();
-    const int *blk = BWD ? S.pb_blk : S.pf_blk;
-    const int4 *bund = BWD ? S.pb_bund : S.pf_bund;
-    const int b0 = blk[blockIdx.x], b1 = blk[blockIdx.x + 1];
-    if (b1 > b0) {
-        const int it0 = bund[3 * (size_t)b0].x, it1 = bund[3 * (size_t)(b1 - 1)].y;
-        if (tid >= PCONS) pipe_produce<R, BWD>(S, it0, it1, ring, sh, ns);
-        else pipe_consume<R, BWD>(S, b0, b1, it0, ring, F, sh, in, out);
-    }
-    __syncthreads();
-    // copies still in flight land before the block exits (only after an error
-    // can the last use of a slot be unconsumed)
-    if (tid == 0 && sh.abort) {
-        const int n = sh.k_issued;
-        for (int q = 0; q < ns && q < n; ++q) {
-            const int last = q + ((n - 1 - q) / ns) * ns;
-            if (!bulk_load_wait(&sh.full[q], (uint32_t)((last / ns) & 1))) atomicOr(S.err, 4u);
-        }
-    }
+    bwd_item<R, NT>(S, S.bwd_items + 5 * (size_t)item, item, qcap, reinterpret_cast<R *>(smem_raw), &bar, z, r, pf,
+                    pf_n);
 }
 
 // Dynamic shared memory of a sweep block: qcap factor entries, 3 x ld vector
@@ -1026,21 +555,14 @@ size_t sweep_smem(int qcap, int ld) {
     return ((size_t)qcap + 3 * (size_t)ld) * sizeof(R) + 16 * (size_t)ld;
 }
 
-// Dynamic shared memory of a pipelined sweep block: ns ring slots and the
-// vector area (three components of fcap entries).
-template <typename R>
-size_t pipe_smem(int ns, int fcap) {
-    return (size_t)ns * PIPE_SLOT + 3 * (size_t)fcap * sizeof(R);
-}
-
 // One level's launch, with the programmatic-serialisation attribute when
 // the handle chains levels.
-template <typename R, typename... Args>
-void launch_level(bool pdl, void (*kernel)(DevSolve<R>, int, int, Args...), int grid, size_t smem, cudaStream_t st,
-                  const DevSolve<R> &s, int item0, int qcap, Args... args) {
+template <typename R, typename... KArgs, typename... Args>
+void launch_level(bool pdl, void (*kernel)(DevSolve<R>, int, int, KArgs...), int grid, int threads, size_t smem,
+                  cudaStream_t st, const DevSolve<R> &s, int item0, int qcap, Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(SBS);
+    cfg.blockDim = dim3((unsigned)threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -1051,101 +573,68 @@ void launch_level(bool pdl, void (*kernel)(DevSolve<R>, int, int, Args...), int 
     cudaLaunchKernelEx(&cfg, kernel, s, item0, qcap, args...);
 }
 
-}  // namespace
-
-template <typename R> int solve_smem_limit_ok(int max_ld) {
-    return sweep_smem<R>(65536 / (int)sizeof(R), max_ld) <= (size_t)SOLVE_MAX_SMEM;
+template <typename R, int NT>
+void launch_sweeps(const DevSolve<R> &s, const V4<R> *q, V4<R> *z, V4<R> *r, cudaStream_t st) {
+    const int L = s.n_levels;
+    // launch k of the solve: forward level k (k < L), then backward level 2L - 1 - k
+    auto pf_of = [&](int k, const int4 **p, int *n) {
+        const int t = k + s.prefetch;
+        *p = nullptr;
+        *n = 0;
+        if (s.prefetch <= 0 || t >= 2 * L) return;
+        *p = s.pf_spans + s.pf_ptr[t];
+        *n = s.pf_ptr[t + 1] - s.pf_ptr[t];
+    };
+    for (int l = 0; l < L; ++l) {
+        const int a = s.fwd_lvl_ptr[l], b = s.fwd_lvl_ptr[l + 1];
+        if (b <= a) continue;
+        const int4 *pf;
+        int pf_n;
+        pf_of(l, &pf, &pf_n);
+        launch_level<R, const V4<R> *, V4<R> *, const int4 *, int, int>(
+            s.pdl != 0, k_fwd<R, NT>, b - a, NT, sweep_smem<R>(s.fwd_lvl_q[l], s.fwd_lvl_ld[l]), st, s, a,
+            s.fwd_lvl_q[l], q, z, pf, pf_n, (s.fault_test == 1 && l == 0) ? 1 : 0);
+    }
+    for (int l = L - 1; l >= 0; --l) {
+        const int a = s.bwd_lvl_start[l], cnt = s.bwd_lvl_cnt[l];
+        if (cnt <= 0) continue;
+        const int4 *pf;
+        int pf_n;
+        pf_of(2 * L - 1 - l, &pf, &pf_n);
+        launch_level<R, const V4<R> *, V4<R> *, const int4 *, int>(
+            s.pdl != 0, k_bwd<R, NT>, cnt, NT, sweep_smem<R>(s.bwd_lvl_q[l], s.bwd_lvl_ld[l]), st, s, a,
+            s.bwd_lvl_q[l], (const V4<R> *)z, r, pf, pf_n);
+    }
 }
 
-template <typename R> cudaError_t solve_prepare() {
-    cudaError_t e = cudaFuncSetAttribute(k_fwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_MAX_SMEM);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bwd<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_MAX_SMEM);
+template <typename R, int NT>
+cudaError_t prepare_nt() {
+    cudaError_t e = cudaFuncSetAttribute(k_fwd<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_MAX_SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fwd_dyn<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_MAX_SMEM);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_bwd_dyn<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_MAX_SMEM);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pipe<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, PIPE_MAX_SMEM);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_pipe<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, PIPE_MAX_SMEM);
+        e = cudaFuncSetAttribute(k_bwd<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SOLVE_MAX_SMEM);
     return e;
 }
 
-// Ring slots for a vector area of fcap entries (as many as fit, at most
-// PIPE_NS_MAX, at least 2) and the blocks of one launch: one per SM, all
-// resident at once.
-template <typename R> int solve_pipe_grid(int fcap, int *ns_out) {
-    const size_t area = 3 * (size_t)fcap * sizeof(R);
-    if (area + 2 * (size_t)PIPE_SLOT > (size_t)PIPE_MAX_SMEM) return 0;
-    int ns = (int)((PIPE_MAX_SMEM - area) / PIPE_SLOT);
-    if (ns > PIPE_NS_MAX) ns = PIPE_NS_MAX;
-    int dev = 0, sms = 0, per_f = 0, per_b = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    const size_t smem = pipe_smem<R>(ns, fcap);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_f, k_pipe<R, false>, PTHREADS, smem) != cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_b, k_pipe<R, true>, PTHREADS, smem) != cudaSuccess)
-        return 0;
-    if (per_f < 1 || per_b < 1) return 0;
-    *ns_out = ns;
-    return sms;
+}  // namespace
+
+template <typename R> size_t solve_block_smem(int qcap, int ld) { return sweep_smem<R>(qcap, ld); }
+
+template <typename R> cudaError_t solve_prepare() {
+    cudaError_t e = prepare_nt<R, 256>();
+    if (e == cudaSuccess) e = prepare_nt<R, 512>();
+    return e;
 }
 
 template <typename R>
 void launch_solve(const DevSolve<R> &s, const V4<R> *q, V4<R> *z, V4<R> *r, cudaStream_t st) {
-    if (s.pipe) {
-        const size_t smem = pipe_smem<R>(s.pipe_ns, s.pipe_fcap);
-        k_pipe<R, false><<<s.pipe_grid, PTHREADS, smem, st>>>(s, q, z);
-        k_pipe<R, true><<<s.pipe_grid, PTHREADS, smem, st>>>(s, (const V4<R> *)z, r);
-        return;
-    }
-    if (s.dyn) {
-        k_fwd_dyn<R><<<s.dyn_grid, SBS, sweep_smem<R>(s.fwd_qmax, s.fwd_ldmax), st>>>(s, s.fwd_qmax, q, z);
-        k_bwd_dyn<R><<<s.dyn_grid, SBS, sweep_smem<R>(s.bwd_qmax, s.bwd_ldmax), st>>>(s, s.bwd_qmax, z, r);
-        return;
-    }
-    for (int l = 0; l < s.n_levels; ++l) {
-        const int a = s.fwd_lvl_ptr[l], b = s.fwd_lvl_ptr[l + 1];
-        if (b > a)
-            launch_level<R, const V4<R> *, V4<R> *>(s.pdl != 0, k_fwd<R>, b - a,
-                                                     sweep_smem<R>(s.fwd_lvl_q[l], s.fwd_lvl_ld[l]), st, s, a,
-                                                     s.fwd_lvl_q[l], q, z);
-    }
-    for (int l = s.n_levels - 1; l >= 0; --l) {
-        const int a = s.bwd_lvl_start[l], cnt = s.bwd_lvl_cnt[l];
-        if (cnt > 0)
-            launch_level<R, const V4<R> *, V4<R> *>(s.pdl != 0, k_bwd<R>, cnt,
-                                                     sweep_smem<R>(s.bwd_lvl_q[l], s.bwd_lvl_ld[l]), st, s, a,
-                                                     s.bwd_lvl_q[l], (const V4<R> *)z, r);
-    }
-}
-
-// Blocks of the persistent sweeps that fit on the device at once (the grid of
-// the dependency-driven schedule must be co-resident only for speed, not for
-// progress: items are taken in topological order).
-template <typename R> int solve_dyn_grid(const DevSolve<R> &s) {
-    int dev = 0, sms = 0, per_sm_f = 0, per_sm_b = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_fwd_dyn<R>, SBS,
-                                                      sweep_smem<R>(s.fwd_qmax, s.fwd_ldmax)) != cudaSuccess)
-        return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k_bwd_dyn<R>, SBS,
-                                                      sweep_smem<R>(s.bwd_qmax, s.bwd_ldmax)) != cudaSuccess)
-        return 0;
-    const int per_sm = per_sm_f < per_sm_b ? per_sm_f : per_sm_b;
-    return per_sm > 0 ? per_sm * sms : 0;
+    if (s.threads == 512) launch_sweeps<R, 512>(s, q, z, r, st);
+    else launch_sweeps<R, 256>(s, q, z, r, st);
 }
 
 template void launch_solve<float>(const DevSolve<float> &, const V4<float> *, V4<float> *, V4<float> *, cudaStream_t);
 template void launch_solve<double>(const DevSolve<double> &, const V4<double> *, V4<double> *, V4<double> *, cudaStream_t);
-template int solve_dyn_grid<float>(const DevSolve<float> &);
-template int solve_dyn_grid<double>(const DevSolve<double> &);
-template int solve_pipe_grid<float>(int, int *);
-template int solve_pipe_grid<double>(int, int *);
-template int solve_smem_limit_ok<float>(int);
-template int solve_smem_limit_ok<double>(int);
+template size_t solve_block_smem<float>(int, int);
+template size_t solve_block_smem<double>(int, int);
 template cudaError_t solve_prepare<float>();
 template cudaError_t solve_prepare<double>();
 

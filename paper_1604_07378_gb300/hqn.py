@@ -24,6 +24,7 @@ HQN_ERR_NOT_SPD = -4
 HQN_ERR_CUDA = -5
 HQN_ERR_NO_MEMORY = -6
 HQN_ERR_UNSUPPORTED = -7
+HQN_ERR_DEVICE_TIMEOUT = -8
 STATIC_MAX_TETS, STATIC_MAX_VERTS = 65536, 262144
 
 NEOHOOKEAN, STVK, SPLINE_VL, COROTATED, POLY4 = 0, 1, 2, 3, 4
@@ -61,11 +62,13 @@ class Params(C.Structure):
                 ("x_start", C.c_double), ("x_end", C.c_double), ("gravity", C.c_double * 3),
                 ("iters", C.c_int32), ("history_m", C.c_int32), ("ls_max", C.c_int32),
                 ("precision", C.c_int32), ("leaf_size", C.c_int32), ("use_graph", C.c_int32),
-                ("tet_block", C.c_int32), ("ls_batch", C.c_int32), ("dyn_sweeps", C.c_int32),
+                ("tet_block", C.c_int32), ("ls_batch", C.c_int32), ("solve_threads", C.c_int32),
+                ("solve_item_kb", C.c_int32), ("solve_items", C.c_int32), ("solve_prefetch", C.c_int32),
                 ("n_colliders", C.c_int32), ("contact_scale", C.c_double),
                 ("colliders", Collider * MAX_COLLIDERS), ("a0_solver", C.c_int32), ("pcg_iters", C.c_int32),
                 ("direction", C.c_int32), ("cheb_S", C.c_int32), ("cheb_rho", C.c_double),
-                ("merge_depths", C.c_int32)]
+                ("merge_depths", C.c_int32), ("wait_polls", C.c_int32), ("fault_test", C.c_int32),
+                ("tune_cache", C.c_char_p)]
 
 
 class StepStats(C.Structure):
@@ -82,7 +85,8 @@ class Info(C.Structure):
                 ("stiffness_k", C.c_double), ("setup_seconds", C.c_double),
                 ("device_bytes", C.c_int64), ("precision", C.c_int32),
                 ("graph_mode", C.c_int32), ("n_update_entries", C.c_int64),
-                ("chained_sweeps", C.c_int32), ("sweep_schedule", C.c_int32), ("n_sims", C.c_int32)]
+                ("chained_sweeps", C.c_int32), ("solve_threads", C.c_int32), ("solve_item_kb", C.c_int32),
+                ("solve_items", C.c_int32), ("solve_prefetch", C.c_int32), ("n_sims", C.c_int32)]
 
 
 _lib = None
@@ -118,6 +122,14 @@ def library(path: str | None = None):
     lib.sim_solve_A0.argtypes = [C.c_void_p, _dp, _dp]
     lib.sim_direction.argtypes = [C.c_void_p, _dp, C.c_int32, _dp, _dp, _dp]
     lib.sim_get_info.argtypes = [C.c_void_p, C.POINTER(Info)]
+    lib.hqn_measure_peak.argtypes = [C.c_int32, _dp]
+    lib.hqn_measure_peak.restype = C.c_int
+    lib.sim_set_solve_shapes.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+    lib.sim_set_solve_shapes.restype = C.c_int
+    lib.hqn_mesh_key.argtypes = [C.POINTER(Mesh)]
+    lib.hqn_mesh_key.restype = C.c_uint64
+    lib.hqn_tune_lookup.argtypes = [C.c_char_p, C.c_char_p, C.c_uint64, C.c_int32, C.POINTER(Params)]
+    lib.hqn_tune_lookup.restype = C.c_int
     lib.hqn_analyse.argtypes = [C.POINTER(Mesh), C.POINTER(Material), C.POINTER(Params), C.POINTER(Info)]
     lib.sim_positions_device.argtypes = [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int32)]
     lib.sim_time_stage.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _dp]
@@ -157,12 +169,21 @@ def _ptr(a, ctype=_dp):
     return a.ctypes.data_as(ctype)
 
 
+def measure_peak(precision=FP32_MIXED) -> float:
+    """``hqn_measure_peak``: the current device's non-tensor FMA FLOP/s."""
+    v = C.c_double()
+    _check(library().hqn_measure_peak(precision, C.byref(v)), "hqn_measure_peak")
+    return v.value
+
+
 def default_params(**kw) -> Params:
     p = Params()
     library().hqn_default_params(C.byref(p))
     for k, v in kw.items():
         if k == "gravity":
             p.gravity[:] = list(v)
+        elif k == "tune_cache":
+            p.tune_cache = None if v is None else os.fsencode(v)
         elif k == "colliders":
             cols = list(v)
             if len(cols) > MAX_COLLIDERS:
@@ -333,6 +354,11 @@ class Sim:
         _check(library().sim_direction(self._h, _ptr(grad), npairs, sp, tp, _ptr(d)),
                "sim_direction")
         return d
+
+    def set_solve_shapes(self, solve_threads=0, solve_item_kb=0, solve_items=0, solve_prefetch=0):
+        """``sim_set_solve_shapes``: re-plans the sweeps on this handle."""
+        _check(library().sim_set_solve_shapes(self._h, solve_threads, solve_item_kb, solve_items, solve_prefetch),
+               "sim_set_solve_shapes")
 
     def time_stage(self, stage, reps=20):
         """Mean device milliseconds of one launch of a stage (CUDA events on the

@@ -94,20 +94,23 @@ def test_batch_several_steps_bitwise_equal_to_single_handles():
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
-def test_batch_pipelined_sweeps_bitwise_equal_to_single_handles(prec):
-    """With the pipelined sweeps a row's arithmetic does not depend on which
-    block runs its item, so the batch still agrees bit for bit with single
-    handles (and with the oracle)."""
+def test_batch_other_sweep_shapes_bitwise_equal_to_single_handles(prec):
+    """With other sweep shapes (512-thread blocks, small work items, no L2
+    prefetch) each simulation's items are still its own, so the batch agrees
+    bit for bit with single handles of the same shapes (and with the
+    oracle)."""
     from paper_1604_07378_gb300 import hqn
-    with hqn.Batch(WL, precision=prec, dyn_sweeps=2) as b:
-        assert b.info()["sweep_schedule"] == 2
+    shapes = dict(solve_threads=512, solve_item_kb=16, solve_items=64, solve_prefetch=-1)
+    with hqn.Batch(WL, precision=prec, **shapes) as b:
+        info = b.info()
+        assert (info["solve_threads"], info["solve_item_kb"], info["solve_prefetch"]) == (512, 16, 0)
         for i, w in enumerate(WL):
             b.set_state(i, w.q_cur, w.q_prev)
         rc, _ = b.step(2)
         assert rc >= 0
         got = [b.get_state(i)[0] for i in range(len(WL))]
     for i, w in enumerate(WL):
-        with hqn.Sim.from_workload(w, precision=prec, dyn_sweeps=2) as sim:
+        with hqn.Sim.from_workload(w, precision=prec, **shapes) as sim:
             sim.set_state(w.q_cur, w.q_prev)
             sim.step(2)
             np.testing.assert_array_equal(got[i], sim.get_state()[0])

@@ -105,15 +105,25 @@ def test_energy_gradient_other_materials(kind):
 LAT30 = W.lattice_workload((30, 30, 30), W.Material(W.NEOHOOKEAN, 5e5, 0.4), clamp_axis=2, seed=13, name="lat30")
 
 
+# shapes of the sweeps (hqn_params.solve_*): block threads, work-item size
+# and count, L2 prefetch distance
+SHAPES = {"default": {}, "t512": dict(solve_threads=512),
+          "small_items": dict(solve_item_kb=16, solve_items=2000, solve_prefetch=1),
+          "big_items": dict(solve_item_kb=128, solve_items=152, solve_threads=512, solve_prefetch=4),
+          "no_prefetch": dict(solve_prefetch=-1)}
+
+
 @pytest.mark.parametrize("w", WORKLOADS[:3] + [LAT30], ids=IDS[:3] + ["lat30"])
 @pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
-@pytest.mark.parametrize("dyn_sweeps", [0, 1, 2], ids=["levels", "dependency", "pipelined"])
-def test_solve_A0_parity(w, prec, dyn_sweeps):
+@pytest.mark.parametrize("shape", sorted(SHAPES))
+def test_solve_A0_parity(w, prec, shape):
     P = problem_for(w)
     rng = np.random.default_rng(4)
     q = rng.normal(size=(w.n_verts, 3))
-    with sim_for(w, prec, use_graph=0, dyn_sweeps=dyn_sweeps) as sim:
-        assert sim.info()["sweep_schedule"] == dyn_sweeps
+    with sim_for(w, prec, use_graph=0, **SHAPES[shape]) as sim:
+        info = sim.info()
+        for k, v in SHAPES[shape].items():
+            assert info[k] == (0 if k == "solve_prefetch" and v < 0 else v), (k, info[k])
         r = sim.solve_A0(q)
     r_ref = O.solve_A(P, q)
     assert rel(r, r_ref) <= (1e-11 if prec == FP64 else 2e-5)
@@ -190,61 +200,45 @@ def test_step_parity_graph(w, prec):
         assert stats["trials"] == st.trials
 
 
-def test_sweep_schedules_agree_bitwise():
-    """The dependency-driven and the per-level sweeps do the same arithmetic
-    on every output, so whole steps agree bit for bit; repeated solves on one
-    handle (the counters reset between sweeps) too."""
+def test_sweep_shapes_agree_bitwise():
+    """The block's thread count and the L2 prefetch distance change neither
+    the work items nor any row's summation order, so whole steps agree bit
+    for bit; repeated solves on one handle (the chunk counters re-arm
+    themselves) give the same result every time."""
     w = WORKLOADS[1]
     out = []
-    for dyn in (0, 1, 1):
-        with sim_for(w, FP32, use_graph=1, dyn_sweeps=dyn) as sim:
+    for kw in ({}, dict(solve_threads=512), dict(solve_prefetch=-1), dict(solve_prefetch=6)):
+        with sim_for(w, FP32, use_graph=1, **kw) as sim:
             sim.set_state(w.q_cur, w.q_prev)
             sim.step(3)
             out.append(sim.get_state()[0])
-    np.testing.assert_array_equal(out[0], out[1])
-    np.testing.assert_array_equal(out[0], out[2])
+    for o in out[1:]:
+        np.testing.assert_array_equal(out[0], o)
+    rng = np.random.default_rng(12)
+    q = rng.normal(size=(LAT30.n_verts, 3))
+    with sim_for(LAT30, FP32, use_graph=0) as sim:
+        r1 = sim.solve_A0(q)
+        r2 = sim.solve_A0(q)
+    np.testing.assert_array_equal(r1, r2)
 
 
 @pytest.mark.parametrize("w", WORKLOADS, ids=IDS)
 @pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
-def test_step_parity_pipelined_sweeps(w, prec):
-    """Whole steps with the pipelined sweeps (one persistent launch per sweep)
-    against the oracle; the same tolerances as the per-level sweeps."""
+def test_step_parity_other_sweep_shapes(w, prec):
+    """Whole steps with small work items (other row splits, so other
+    summation orders) and 512-thread blocks against the oracle, at the
+    tolerances of the default shapes."""
     P = problem_for(w)
     x_ref, st = O.solve_step(P, w.q_cur, w.q_prev, iters=w.iters, m=w.history)
-    with sim_for(w, prec, use_graph=1, dyn_sweeps=2) as sim:
-        assert sim.info()["sweep_schedule"] == 2
+    with sim_for(w, prec, use_graph=1, solve_item_kb=16, solve_items=2000, solve_threads=512) as sim:
         sim.set_state(w.q_cur, w.q_prev)
         rc, stats = sim.step(1, stats=True)
         qc, _ = sim.get_state()
     assert rc >= 0
     assert rel(qc, x_ref) <= (1e-9 if prec == FP64 else 1e-4), rel(qc, x_ref)
+    assert rel_step(qc, x_ref, w.q_cur) <= STEP_TOL[prec]
     if prec == FP64:
         assert stats["trials"] == st.trials
-
-
-def test_pipelined_sweeps_repeat_and_match_levels():
-    """Repeated solves on one handle (the counters of each sweep re-arm in
-    the other) give the same result every time; the pipelined sweeps
-    partition the rows into other work items than the per-level sweeps, so
-    the two agree to rounding."""
-    w = LAT30
-    rng = np.random.default_rng(12)
-    q = rng.normal(size=(w.n_verts, 3))
-    with sim_for(w, FP32, use_graph=0, dyn_sweeps=2) as sim:
-        r1 = sim.solve_A0(q)
-        r2 = sim.solve_A0(q)
-        sim.set_state(w.q_cur, w.q_prev)
-        sim.step(3)
-        x_pipe = sim.get_state()[0]
-    np.testing.assert_array_equal(r1, r2)
-    with sim_for(w, FP32, use_graph=0, dyn_sweeps=0) as sim:
-        r0 = sim.solve_A0(q)
-        sim.set_state(w.q_cur, w.q_prev)
-        sim.step(3)
-        x_lvl = sim.get_state()[0]
-    assert rel(r1, r0) <= 1e-5
-    assert rel(x_pipe, x_lvl) <= 1e-5
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
@@ -284,13 +278,13 @@ def lat30_solve_case():
 
 @pytest.mark.parametrize("merge", [0, 1, 5, 0x55, 0x155], ids=lambda m: f"merge{m:#x}")
 @pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
-@pytest.mark.parametrize("dyn_sweeps", [0, 1, 2], ids=["levels", "dependency", "pipelined"])
-def test_solve_A0_merged_supernodes(lat30_solve_case, merge, prec, dyn_sweeps):
+@pytest.mark.parametrize("threads", [256, 512])
+def test_solve_A0_merged_supernodes(lat30_solve_case, merge, prec, threads):
     """Supernodes that merge a separator with the separators under it (their
     update entries fed by up to four children) solve A0 r = q to the same
-    tolerance as the plain dissection tree, in every sweep schedule."""
+    tolerance as the plain dissection tree."""
     q, r_ref = lat30_solve_case
-    with sim_for(LAT30, prec, use_graph=0, dyn_sweeps=dyn_sweeps, merge_depths=merge) as sim:
+    with sim_for(LAT30, prec, use_graph=0, merge_depths=merge, solve_threads=threads) as sim:
         r = sim.solve_A0(q)
     assert rel(r, r_ref) <= (1e-11 if prec == FP64 else 2e-5)
     assert np.all(r[LAT30.clamped.astype(bool)] == 0.0)
@@ -385,3 +379,31 @@ def test_checkpoint_resume(prec):
     else:
         assert rel(resumed, straight) <= 1e-12
         assert rel(resumed_prev, straight_prev) <= 1e-12
+
+
+# ---------------------------------------------------------------- bounded device waits
+
+@pytest.mark.parametrize("use_graph", [0, 1], ids=["eager", "graph"])
+def test_sweep_wait_timeout_is_reported(use_graph):
+    """Failure detection without a GPU fault: with fault_test = 1 the first
+    forward level's blocks issue no copy, so each block's wait on its copy
+    (bounded here to 2,000 polls) runs out with nothing in flight; the block
+    flags it and leaves, and the step returns HQN_ERR_DEVICE_TIMEOUT instead
+    of hanging.  The context stays usable: a new handle then steps as the
+    oracle does."""
+    from paper_1604_07378_gb300 import hqn
+    w = WORKLOADS[1]
+    with sim_for(w, FP32, use_graph=use_graph, fault_test=1, wait_polls=2000) as sim:
+        sim.set_state(w.q_cur, w.q_prev)
+        with pytest.raises(hqn.HQNError) as e:
+            sim.step(1)
+        assert e.value.code == hqn.HQN_ERR_DEVICE_TIMEOUT
+        with pytest.raises(hqn.HQNError) as e:
+            sim.solve_A0(np.ones((w.n_verts, 3)))
+        assert e.value.code == hqn.HQN_ERR_DEVICE_TIMEOUT
+    P = problem_for(w)
+    x_ref, _ = O.solve_step(P, w.q_cur, w.q_prev, iters=w.iters, m=w.history)
+    with sim_for(w, FP32, use_graph=use_graph) as sim:
+        sim.set_state(w.q_cur, w.q_prev)
+        assert sim.step(1) >= 0
+        assert rel(sim.get_state()[0], x_ref) <= 1e-4
