@@ -148,16 +148,34 @@ typedef struct {
      * items sums some rows in another order (rounding-level differences).
      * 0 selects the default; the autotuner (paper_1604_07378_gb300/autotune.py)
      * picks them per mesh and GPU. */
-    int32_t solve_threads;  /* threads per sweep block: 256 or 512 (default 256)  */
+    int32_t solve_threads;  /* threads per sweep block: 128, 256 or 512 (default 256) */
     int32_t solve_item_kb;  /* largest work item, KB of factor rows: 16..160
                                (default 64)                                      */
     int32_t solve_items;    /* work items a level's rows are spread over: 16..4096
                                (default 400)                                     */
-    int32_t solve_prefetch; /* a level's blocks ask L2 to prefetch the factor rows
-                               of the level this many launches ahead: 1..8; 0 or
-                               -1 = no prefetch (default: on a 40^3 lattice the
-                               prefetch left the solve's time unchanged and cost
-                               the step 3% of L2 hits elsewhere)                 */
+    int32_t solve_leaf_kb;  /* largest work item of the leaf level (level 0, whose
+                               items depend on no other level): 8..160, 0 = as
+                               solve_item_kb                                     */
+    int32_t solve_leaf_threads; /* threads per block of the leaf level: 128, 256 or
+                               512, 0 = as solve_threads                         */
+    int32_t solve_dense_top;/* the supernodes of the tree's top solve_dense_top levels
+                               (1..8) are solved together, r_T = S^{-1} f_T with
+                               the inverse of A0's Schur complement on their
+                               columns (formed once on the host in float64):
+                               one tiled dense product replaces 2 solve_dense_top
+                               launches of the sweeps.  0 (default) = automatic:
+                               the most levels, at most 3, whose block has at
+                               most 5,000 columns (the host's cost grows as the
+                               cube of the columns); -1 = none.  Set at
+                               sim_create (not by sim_set_solve_shapes)        */
+    int32_t solve_prefetch; /* L2 prefetches issued by the sweeps' levels: 1..8 =
+                               a level's blocks also prefetch the factor rows of
+                               the level this many launches ahead; 0 (default) =
+                               only the dense top block's matrix, streamed into
+                               L2 by the forward levels before it; -1 = none.
+                               (On a 40^3 lattice the factor-row prefetch left
+                               the solve's time unchanged and cost the step 3%
+                               of L2 hits elsewhere.)                            */
     /* Collisions (Sec. 4.3) against analytic colliders, shared by every
      * simulation of a handle.  At the start of each iteration (before the
      * gradient at x_k) every free vertex that penetrates a collider and does
@@ -202,8 +220,9 @@ typedef struct {
      * flight and leaves; sim_step, sim_solve_A0 and sim_direction then
      * return HQN_ERR_DEVICE_TIMEOUT.  fault_test is fault injection for
      * tests of that path and stays 0 otherwise: 1 = the blocks of the first
-     * forward level of every solve issue no copy, so their waits run out with
-     * nothing in flight. */
+     * forward sweep level (the leaves) of every solve issue no copy, so
+     * their waits run out with nothing in flight (a tree whose every level is
+     * in the dense top block has no such level). */
     int32_t wait_polls;
     int32_t fault_test;
     /* Path of an autotuner cache (see hqn_tune_lookup), or NULL.  When set,
@@ -211,7 +230,8 @@ typedef struct {
      * batch, the keys of all meshes folded in order), the precision and the
      * current device's name there, and, on a hit, replace leaf_size,
      * solve_threads, solve_item_kb, solve_items, solve_prefetch (and
-     * ls_batch if the entry has it) by the tuned values.  A missing file
+     * solve_leaf_kb, solve_leaf_threads, solve_dense_top and ls_batch if
+     * the entry has them) by the tuned values.  A missing file
      * or entry leaves the parameters as given; a malformed file is
      * HQN_ERR_ARG. */
     const char *tune_cache;
@@ -249,7 +269,12 @@ typedef struct {
     int32_t solve_threads;      /* sweep shapes in use (see hqn_params.solve_*)           */
     int32_t solve_item_kb;
     int32_t solve_items;
+    int32_t solve_leaf_kb;
+    int32_t solve_leaf_threads;
     int32_t solve_prefetch;     /* 0 = no prefetch                                        */
+    int32_t solve_dense_top;    /* top levels solved by the dense block (0 = none), of the
+                                   first simulation                                       */
+    int32_t dense_top_cols;     /* columns of that block (largest simulation)              */
     int32_t n_sims;             /* simulations in the handle (1 for sim_create)        */
 } hqn_info;
 
@@ -378,14 +403,16 @@ int sim_time_stage(sim_handle *sim, int32_t stage, int32_t reps, double *ms);
  * shapes and the leaf size on the device and writes its choices to a cache
  * file that sim_create reads (hqn_params.tune_cache). */
 
-/* New sweep shapes on an existing handle (hqn_params.solve_threads,
- * solve_item_kb, solve_items, solve_prefetch; 0 = default): the work items
- * are re-planned from the handle's own factor (no refactorisation) and the
- * step graph is rebuilt.  Results change by rounding only (other row
- * splits), or not at all (threads, prefetch).  Errors: HQN_ERR_ARG (a shape
- * out of range), HQN_ERR_UNSUPPORTED (items that do not fit a block's shared
+/* New sweep shapes on an existing handle: the fields solve_threads,
+ * solve_item_kb, solve_items, solve_leaf_kb, solve_leaf_threads and
+ * solve_prefetch of *shapes (0 = default; the other fields are ignored).  The
+ * work items are re-planned from the handle's own factor (no
+ * refactorisation) and the step graph is rebuilt.  Results change by
+ * rounding only (other row splits), or not at all (threads, prefetch).
+ * solve_dense_top stays as created.  Errors: HQN_ERR_ARG (a shape out of
+ * range), HQN_ERR_UNSUPPORTED (items that do not fit a block's shared
  * memory), HQN_ERR_CUDA. */
-int sim_set_solve_shapes(sim_handle *sim, int32_t threads, int32_t item_kb, int32_t items, int32_t prefetch);
+int sim_set_solve_shapes(sim_handle *sim, const hqn_params *shapes);
 
 /* 64-bit FNV-1a hash of a mesh (sizes, rest positions, tets, clamp flags):
  * the key of its autotuner cache entries.  0 for a NULL or empty mesh.
@@ -397,7 +424,8 @@ uint64_t hqn_mesh_key(const hqn_mesh *mesh);
  * per line, later lines overriding earlier ones, '#' lines ignored:
  *   hqn-tune 1 device=<name, spaces as '_'> precision=<0|1> key=<16 hex>
  *     leaf_size=<n> solve_threads=<n> solve_item_kb=<n> solve_items=<n>
- *     solve_prefetch=<n> [ls_batch=<n>] [other key=value pairs, ignored]
+ *     solve_prefetch=<n> [solve_leaf_kb=<n>] [solve_leaf_threads=<n>]
+ *     [solve_dense_top=<n>] [ls_batch=<n>] [other key=value pairs, ignored]
  * Returns 1 and writes the entry's values into *params on a hit, 0 when the
  * file or the entry does not exist (params unchanged), HQN_ERR_ARG for a
  * malformed file or argument. */

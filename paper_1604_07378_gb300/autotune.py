@@ -2,16 +2,18 @@
 
 The speed of the A0^{-1} sweeps, the heaviest stage of a step, depends on
 shapes the method leaves open: the nested-dissection leaf size (which sets
-the factor's levels and fill), the threads of a sweep block, the size and
-number of the work items a level's rows are split into, and how many
-launches ahead a level prefetches the factor into L2.  This module times
-them on the current GPU, on the mesh itself:
+the factor's levels and fill), how many top levels of the tree are solved
+by one dense block, the threads of a sweep block, the size and number of
+the work items a level's rows are split into (the leaf level's on their
+own), and what the levels prefetch into L2.  This module times them on the
+current GPU, on the mesh itself:
 
-1. for every leaf size, one handle (one factorisation); on it every sweep
-   shape of the grid is planned in turn (sim_set_solve_shapes re-plans the
-   work items without refactorising) and one solve is timed with CUDA
-   events on the device (sim_time_stage, best of three means);
-2. the best shape of each leaf size, and the library's defaults, are timed
+1. for every (leaf size, dense top levels), one handle (one
+   factorisation); on it every sweep shape of the grid is planned in turn
+   (sim_set_solve_shapes re-plans the work items without refactorising)
+   and one solve is timed with CUDA events on the device (sim_time_stage,
+   best of three means);
+2. the best shape of each handle, and the library's defaults, are timed
    as whole time steps (one CUDA graph each);
 3. the fastest is written to the cache file as one line, keyed by the
    device name, the precision and the mesh's hash (hqn_mesh_key).
@@ -32,12 +34,16 @@ from . import hqn
 
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.txt")
 
-LEAF_SIZES = (64, 128, 256)
-# (threads, item KB, items per level, prefetch distance; -1 = none)
-SHAPE_GRID = tuple((t, kb, n, pf) for t in (256, 512)
-                   for kb, n in ((64, 400), (32, 800), (48, 304), (96, 152), (128, 152), (64, 152))
-                   for pf in (-1, 1, 2, 3))
-SHAPE_KEYS = ("solve_threads", "solve_item_kb", "solve_items", "solve_prefetch")
+LEAF_SIZES = (64, 128)
+DENSE_TOPS = (-1, 2, 3)
+SHAPE_KEYS = ("solve_threads", "solve_item_kb", "solve_items", "solve_prefetch", "solve_leaf_kb",
+              "solve_leaf_threads")
+# the re-plannable sweep shapes (hqn_params.solve_*; 0 = default)
+SHAPE_GRID = tuple(dict(solve_threads=256, solve_item_kb=kb, solve_items=n, solve_prefetch=pf,
+                        solve_leaf_kb=lkb, solve_leaf_threads=lt)
+                   for kb, n in ((64, 400), (48, 304), (96, 304))
+                   for lkb, lt in ((0, 0), (24, 128), (32, 128), (48, 256))
+                   for pf in (0, -1))
 
 
 def mesh_key(rest_pos, tets, clamped=None) -> int:
@@ -54,8 +60,8 @@ def mesh_key(rest_pos, tets, clamped=None) -> int:
 def cache_line(device: str, precision: int, key: int, choice: dict, **extra) -> str:
     """One cache entry in the format hqn_tune_lookup reads."""
     fields = [f"device={device.replace(' ', '_')}", f"precision={int(precision)}", f"key={key:016x}",
-              f"leaf_size={int(choice['leaf_size'])}"]
-    fields += [f"{k}={int(choice[k])}" for k in SHAPE_KEYS]
+              f"leaf_size={int(choice['leaf_size'])}", f"solve_dense_top={int(choice.get('solve_dense_top', 0))}"]
+    fields += [f"{k}={int(choice.get(k, 0))}" for k in SHAPE_KEYS]
     fields += [f"{k}={v:.6g}" if isinstance(v, float) else f"{k}={v}" for k, v in extra.items()]
     return "hqn-tune 1 " + " ".join(fields)
 
@@ -68,7 +74,8 @@ def lookup(path: str, device: str, key: int, precision: int):
         raise hqn.HQNError(rc, f"malformed autotuner cache {path}")
     if rc == 0:
         return None
-    return {"leaf_size": p.leaf_size, **{k: getattr(p, k) for k in SHAPE_KEYS}, "ls_batch": p.ls_batch}
+    return {"leaf_size": p.leaf_size, "solve_dense_top": p.solve_dense_top, **{k: getattr(p, k) for k in SHAPE_KEYS},
+            "ls_batch": p.ls_batch}
 
 
 def _device_name() -> str:
@@ -85,34 +92,40 @@ def _step_ms(sim, w, steps):
     return 1e3 * (time.perf_counter() - t0) / steps
 
 
-def tune_workload(w, precision=hqn.FP32_MIXED, stream=None, leaf_sizes=LEAF_SIZES, grid=SHAPE_GRID,
-                  reps=20, steps=10, cache: str | None = DEFAULT_CACHE) -> dict:
+def tune_workload(w, precision=hqn.FP32_MIXED, stream=None, leaf_sizes=LEAF_SIZES, dense_tops=DENSE_TOPS,
+                  grid=SHAPE_GRID, reps=20, steps=10, cache: str | None = DEFAULT_CACHE) -> dict:
     """Times the shapes on workload `w` (a workloads.Workload) and returns
     the choice with its measurements; appends it to `cache` unless None."""
     results = []
     for leaf in leaf_sizes:
-        with hqn.Sim.from_workload(w, precision=precision, stream=stream, leaf_size=leaf) as sim:
-            sim.set_state(w.q_cur, w.q_prev)
-            sim.step(1)
-            timed = []
-            for shape in grid:
-                try:
-                    sim.set_solve_shapes(*shape)
-                except hqn.HQNError:
-                    continue  # items that do not fit a block's shared memory
-                t = min(sim.time_stage(hqn.STAGE_SOLVE, reps) for _ in range(3))
-                timed.append((t, shape))
-            if not timed:
-                continue
-            t_best, best = min(timed)
-            sim.set_solve_shapes(*best)
-            results.append({"leaf_size": leaf, **dict(zip(SHAPE_KEYS, best)), "solve_ms": t_best,
-                            "step_ms": _step_ms(sim, w, steps), "shapes_timed": len(timed)})
+        for top in dense_tops:
+            try:
+                sim = hqn.Sim.from_workload(w, precision=precision, stream=stream, leaf_size=leaf,
+                                            solve_dense_top=top)
+            except hqn.HQNError:
+                continue  # e.g. a dense top block too large for this mesh
+            with sim:
+                sim.set_state(w.q_cur, w.q_prev)
+                sim.step(1)
+                timed = []
+                for g, shape in enumerate(grid):
+                    try:
+                        sim.set_solve_shapes(**shape)
+                    except hqn.HQNError:
+                        continue  # items that do not fit a block's shared memory
+                    t = min(sim.time_stage(hqn.STAGE_SOLVE, reps) for _ in range(3))
+                    timed.append((t, g))
+                if not timed:
+                    continue
+                t_best, g_best = min(timed)
+                sim.set_solve_shapes(**grid[g_best])
+                results.append({"leaf_size": leaf, "solve_dense_top": top, **grid[g_best], "solve_ms": t_best,
+                                "step_ms": _step_ms(sim, w, steps), "shapes_timed": len(timed)})
     with hqn.Sim.from_workload(w, precision=precision, stream=stream) as sim:
         info = sim.info()
-        default = {"leaf_size": 0, **{k: 0 for k in SHAPE_KEYS},
+        default = {"leaf_size": 0, "solve_dense_top": 0, **{k: 0 for k in SHAPE_KEYS},
                    "solve_ms": min(sim.time_stage(hqn.STAGE_SOLVE, reps) for _ in range(3)),
-                   "step_ms": _step_ms(sim, w, steps), "default_leaf": None, "levels": info["n_levels"]}
+                   "step_ms": _step_ms(sim, w, steps), "levels": info["n_levels"]}
     choice = min(results + [default], key=lambda r: r["step_ms"])
     out = dict(choice)
     out["default_step_ms"] = default["step_ms"]

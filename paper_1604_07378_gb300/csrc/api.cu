@@ -60,7 +60,7 @@ struct SimBase {
     virtual void info(hqn_info *out) const = 0;
     virtual int time_stage(int stage, int reps, double *ms) = 0;
     virtual int positions_device(void **ptr, int32_t *layout) = 0;
-    virtual int set_solve_shapes(int threads, int item_kb, int items, int prefetch) = 0;
+    virtual int set_solve_shapes(const hqn_params &shapes) = 0;
 };
 
 int check_solve_shapes(const hqn_params &p);
@@ -96,6 +96,9 @@ struct Sim final : SimBase {
     cudaStream_t own_stream = nullptr;
     int64_t n_tot = 0, T_tot = 0, nf_tot = 0, sn_tot = 0, q_entries = 0, nnz_tot = 0, upd_tot = 0;
     int n_levels = 0;
+    int dense_cols = 0;   // columns of the largest dense top block
+    int64_t dense_bytes = 0;  // bytes of the dense top blocks' matrices
+    int spans_total = 0;  // L2 prefetch spans of one solve
     double setup_seconds = 0.0;
 
     ~Sim() override {
@@ -142,7 +145,7 @@ struct Sim final : SimBase {
         st = stream;
         ns = (int)S.size();
         const int m = prm.history_m;
-        const int item_kb = p.solve_item_kb > 0 ? p.solve_item_kb : 64;
+        const int item_kb = std::max(p.solve_item_kb > 0 ? p.solve_item_kb : 64, p.solve_leaf_kb);
         int max_ld = 0;
         for (const Setup &s : S) max_ld = std::max(max_ld, s.max_ld);
         if (solve_block_smem<R>(item_kb * 1024 / (int)sizeof(R), max_ld) > (size_t)SOLVE_MAX_SMEM)
@@ -402,10 +405,72 @@ struct Sim final : SimBase {
             if ((rc = upload(p_ug4, ug4.data(), ug4.size()))) return rc;
             dsol.rows = p_rows; dsol.fg4 = p_fg4; dsol.ug4 = p_ug4;
         }
+        if ((rc = init_dense_top(v0, u0))) return rc;
         sv0 = v0; su0 = u0; ssn0 = sn0; sqf0 = qf0; sqb0 = qb0;
         dsol.err = &d_ctl[0].solve_err;
         if ((rc = alloc(dsol.u, (size_t)std::max<int64_t>(upd_tot, 1)))) return rc;
         return plan_solve();
+    }
+
+    // The dense top block of every simulation that has one (Setup::n_top > 0):
+    // the lower block triangle of S^{-1} as TS x TS tiles (J <= I), each a
+    // contiguous row-major block zero-padded past the last column; the
+    // block's columns and its boundary update entries in batch numbering;
+    // one tile record per tile (solve.cu, k_dense).
+    int init_dense_top(const std::vector<int> &v0, const std::vector<int> &u0) {
+        int rc;
+        constexpr int TS = 128;  // the tile edge of k_dense (solve.cu)
+        std::vector<R> inv;
+        std::vector<int> col, bptr, bidx;
+        std::vector<int4> tiles;
+        int bands = 0, nb_max = 1;
+        dense_cols = 0;
+        for (int k = 0; k < ns; ++k) {
+            Setup &s = S[k];
+            const int n = s.n_top;
+            if (n == 0) continue;
+            dense_cols = std::max(dense_cols, n);
+            const int nb = (n + TS - 1) / TS;
+            nb_max = std::max(nb_max, nb);
+            const int tc0 = (int)col.size(), bp0 = (int)bptr.size();
+            for (int i = 0; i < n; ++i) col.push_back(v0[k] + s.top_col[i]);
+            const int b0 = (int)bidx.size();
+            for (int i = 0; i <= n; ++i) bptr.push_back(b0 + s.top_bptr[i]);
+            for (int e : s.top_bidx) bidx.push_back(u0[k] + e);
+            for (int I = 0; I < nb; ++I)
+                for (int J = 0; J <= I; ++J) {
+                    const int64_t off = (int64_t)inv.size();
+                    inv.resize(inv.size() + (size_t)TS * TS, R(0));
+                    for (int i = 0; i < TS && I * TS + i < n; ++i)
+                        for (int j = 0; j < TS && J * TS + j < n; ++j)
+                            inv[off + (size_t)i * TS + j] = (R)s.top_inv[(size_t)(I * TS + i) * n + J * TS + j];
+                    tiles.push_back(make_int4((int)(off & 0xffffffffLL), (int)(off >> 32), I, J));
+                    tiles.push_back(make_int4(n, bands, nb, tc0));
+                    tiles.push_back(make_int4(bp0, 0, 0, 0));
+                }
+            bands += nb;
+            std::vector<double>().swap(s.top_inv);  // the float64 copy is no longer needed
+        }
+        dsol.n_dense_tiles = (int)(tiles.size() / 3);
+        dsol.dense_nct_max = nb_max;
+        dense_bytes = (int64_t)inv.size() * (int64_t)sizeof(R);
+        if (dsol.n_dense_tiles == 0) return HQN_OK;
+        const int4 *p_t;
+        const R *p_inv;
+        const int *p_col, *p_bptr, *p_bidx;
+        if ((rc = upload(p_t, tiles.data(), tiles.size()))) return rc;
+        if ((rc = upload(p_inv, inv.data(), inv.size()))) return rc;
+        if ((rc = upload(p_col, col.data(), col.size()))) return rc;
+        if ((rc = upload(p_bptr, bptr.data(), bptr.size()))) return rc;
+        if ((rc = upload(p_bidx, bidx.data(), bidx.size()))) return rc;
+        dsol.dense_tiles = p_t;
+        dsol.dense_inv = p_inv;
+        dsol.dense_col = p_col;
+        dsol.dense_bptr = p_bptr;
+        dsol.dense_bidx = p_bidx;
+        if ((rc = alloc(dsol.dense_part, (size_t)bands * nb_max * TS))) return rc;
+        if ((rc = alloc(dsol.dense_cnt, (size_t)bands))) return rc;
+        return HQN_OK;
     }
 
     // The sweeps' work items and prefetch spans from every simulation's
@@ -511,12 +576,17 @@ struct Sim final : SimBase {
         dsol.bwd_lvl_ld = bwd_ld.data();
         dsol.fwd_lvl_q = fwd_q.data();
         dsol.bwd_lvl_q = bwd_q.data();
-        // L2 prefetch spans of every launch, in launch order: the factor rows
-        // its items copy, as contiguous runs (a whole supernode's rows where
-        // its items follow each other) cut into pieces of at most 256 KB;
-        // a chunk item's rows are covered once, by chunk 0 of its column block
+        // L2 prefetches of every launch, in launch order.  reads[k]: the factor
+        // rows launch k copies, as contiguous runs (a whole supernode's rows
+        // where its items follow each other) cut into pieces of at most
+        // 256 KB; a chunk item's rows are covered once, by chunk 0 of its
+        // column block.  Launch k issues reads[k + prefetch] (prefetch >= 1)
+        // and, when a dense top block exists (and prefetch is not -1), a share
+        // of the dense matrix: the forward launches before the last one, which
+        // leave HBM mostly idle, stream it into L2 for the dense launch.
         {
             std::vector<int4> spans;
+            std::vector<std::vector<int4>> reads(2 * (size_t)L);
             pf_ptr.assign(2 * (size_t)L + 1, 0);
             const int esz = (int)sizeof(R);
             auto add_run = [&](const R *base, int64_t e0, int64_t e1, std::vector<std::pair<int64_t, int64_t>> &runs) {
@@ -537,7 +607,7 @@ struct Sim final : SimBase {
             };
             std::vector<std::pair<int64_t, int64_t>> runs;
             for (int k = 0; k < 2 * L; ++k) {
-                pf_ptr[k] = (int)spans.size();
+                const size_t s0 = spans.size();
                 if (k < L) {
                     for (int it = fwd_ptr[k]; it < fwd_ptr[k + 1]; ++it) {
                         const int4 a = fi[5 * (size_t)it];
@@ -558,15 +628,44 @@ struct Sim final : SimBase {
                     }
                     flush(dsol.QB, runs);
                 }
+                reads[k].assign(spans.begin() + s0, spans.end());
+                spans.resize(s0);
+            }
+            const int dist = prm.solve_prefetch > 0 ? prm.solve_prefetch : 0;
+            std::vector<std::vector<int4>> issue(2 * (size_t)L);
+            for (int k = 0; k < 2 * L; ++k)
+                if (dist > 0 && k + dist < 2 * L) issue[k] = reads[k + dist];
+            // the dense matrix, over forward launches [1, last forward launch)
+            std::vector<int> fwd_launches;
+            for (int l = 0; l < L; ++l)
+                if (fwd_ptr[l + 1] > fwd_ptr[l]) fwd_launches.push_back(l);
+            if (dense_bytes > 0 && prm.solve_prefetch >= 0 && fwd_launches.size() >= 3) {
+                const int first = 1, last = (int)fwd_launches.size() - 2;  // inclusive
+                const int nl = last - first + 1;
+                constexpr int64_t kPiece = 256 * 1024;
+                const int64_t npieces = (dense_bytes + kPiece - 1) / kPiece;
+                for (int64_t p = 0; p < npieces; ++p) {
+                    const int64_t b0 = p * kPiece, b1 = std::min<int64_t>(dense_bytes, b0 + kPiece);
+                    const unsigned long long a = (unsigned long long)(reinterpret_cast<uintptr_t>(dsol.dense_inv) + b0);
+                    issue[fwd_launches[first + (int)(p * nl / npieces)]].push_back(
+                        make_int4((int)(a & 0xffffffffULL), (int)(a >> 32), (int)(b1 - b0), 0));
+                }
+            }
+            for (int k = 0; k < 2 * L; ++k) {
+                pf_ptr[k] = (int)spans.size();
+                spans.insert(spans.end(), issue[k].begin(), issue[k].end());
             }
             pf_ptr[2 * (size_t)L] = (int)spans.size();
+            spans_total = (int)spans.size();
             const int4 *p_sp;
             if ((rc = upload(p_sp, spans.data(), spans.size()))) return rc;
             dsol.pf_spans = p_sp;
             dsol.pf_ptr = pf_ptr.data();
         }
-        dsol.threads = prm.solve_threads == 512 ? 512 : 256;
+        dsol.threads = prm.solve_threads > 0 ? prm.solve_threads : 256;
+        dsol.leaf_threads = prm.solve_leaf_threads > 0 ? prm.solve_leaf_threads : dsol.threads;
         dsol.prefetch = prm.solve_prefetch <= 0 ? 0 : prm.solve_prefetch;
+        dsol.pf_any = spans_total > 0 ? 1 : 0;
         dsol.wait_polls = prm.wait_polls > 0 ? prm.wait_polls : (1LL << 20);
         dsol.fault_test = prm.fault_test;
         return HQN_OK;
@@ -574,12 +673,14 @@ struct Sim final : SimBase {
 
     // New sweep shapes on an existing handle (the autotuner's entry): the
     // work items are re-planned from the kept set-up, the graph rebuilt.
-    int set_solve_shapes(int threads, int item_kb, int items, int prefetch) override {
-        hqn_params p = prm;
-        p.solve_threads = threads;
-        p.solve_item_kb = item_kb;
-        p.solve_items = items;
-        p.solve_prefetch = prefetch;
+    int set_solve_shapes(const hqn_params &sh) override {
+        hqn_params p = prm;  // solve_dense_top stays as created (the top block is factor data)
+        p.solve_threads = sh.solve_threads;
+        p.solve_item_kb = sh.solve_item_kb;
+        p.solve_items = sh.solve_items;
+        p.solve_prefetch = sh.solve_prefetch;
+        p.solve_leaf_kb = sh.solve_leaf_kb;
+        p.solve_leaf_threads = sh.solve_leaf_threads;
         if (const int rc = check_solve_shapes(p)) return rc;
         int rc;
         std::string err;
@@ -587,7 +688,7 @@ struct Sim final : SimBase {
             if ((rc = plan_sweeps(s, p, err))) return fail(rc, err);
         int max_ld = 0;
         for (const Setup &s : S) max_ld = std::max(max_ld, s.max_ld);
-        const int kb = p.solve_item_kb > 0 ? p.solve_item_kb : 64;
+        const int kb = std::max(p.solve_item_kb > 0 ? p.solve_item_kb : 64, p.solve_leaf_kb);
         if (solve_block_smem<R>(kb * 1024 / (int)sizeof(R), max_ld) > (size_t)SOLVE_MAX_SMEM)
             return fail(HQN_ERR_UNSUPPORTED, "the work items do not fit the sweeps' shared memory");
         prm = p;
@@ -1004,7 +1105,11 @@ struct Sim final : SimBase {
         o->solve_threads = dsol.threads;
         o->solve_item_kb = prm.solve_item_kb > 0 ? prm.solve_item_kb : 64;
         o->solve_items = prm.solve_items > 0 ? prm.solve_items : 400;
+        o->solve_leaf_kb = prm.solve_leaf_kb > 0 ? prm.solve_leaf_kb : o->solve_item_kb;
+        o->solve_leaf_threads = dsol.leaf_threads;
         o->solve_prefetch = dsol.prefetch;
+        o->solve_dense_top = S.empty() ? 0 : S[0].top_levels;
+        o->dense_top_cols = dense_cols;
         o->n_sims = ns;
     }
 };
@@ -1045,12 +1150,19 @@ namespace {
 
 // Checks of the sweep shapes hqn_params.solve_*.
 int check_solve_shapes(const hqn_params &p) {
-    if (p.solve_threads != 0 && p.solve_threads != 256 && p.solve_threads != 512)
-        return fail(HQN_ERR_ARG, "solve_threads must be 0, 256 or 512");
+    if (p.solve_threads != 0 && p.solve_threads != 128 && p.solve_threads != 256 && p.solve_threads != 512)
+        return fail(HQN_ERR_ARG, "solve_threads must be 0, 128, 256 or 512");
+    if (p.solve_leaf_threads != 0 && p.solve_leaf_threads != 128 && p.solve_leaf_threads != 256 &&
+        p.solve_leaf_threads != 512)
+        return fail(HQN_ERR_ARG, "solve_leaf_threads must be 0, 128, 256 or 512");
+    if (p.solve_leaf_kb != 0 && (p.solve_leaf_kb < 8 || p.solve_leaf_kb > 160))
+        return fail(HQN_ERR_ARG, "solve_leaf_kb must be 0 or in [8, 160]");
     if (p.solve_item_kb != 0 && (p.solve_item_kb < 16 || p.solve_item_kb > 160))
         return fail(HQN_ERR_ARG, "solve_item_kb must be 0 or in [16, 160]");
     if (p.solve_items != 0 && (p.solve_items < 16 || p.solve_items > 4096))
         return fail(HQN_ERR_ARG, "solve_items must be 0 or in [16, 4096]");
+    if (p.solve_dense_top < -1 || p.solve_dense_top > 8)
+        return fail(HQN_ERR_ARG, "solve_dense_top must be -1 (none), 0 (automatic) or in [1, 8]");
     if (p.solve_prefetch < -1 || p.solve_prefetch > 8)
         return fail(HQN_ERR_ARG, "solve_prefetch must be -1 (none), 0 (default) or in [1, 8]");
     return HQN_OK;
@@ -1181,6 +1293,7 @@ void hqn_default_params(hqn_params *p) {
     p->solve_item_kb = 64;
     p->solve_items = 400;
     p->solve_prefetch = 0;
+    p->solve_dense_top = 0;
     p->wait_polls = 0;
     p->fault_test = 0;
 }
@@ -1276,10 +1389,14 @@ int hqn_analyse(const hqn_mesh *mesh, const hqn_material *material, const hqn_pa
         info->precision = params->precision;
         info->graph_mode = params->use_graph ? 1 : 0;
         info->n_update_entries = S.n_upd;
-        info->solve_threads = params->solve_threads == 512 ? 512 : 256;
+        info->solve_threads = params->solve_threads > 0 ? params->solve_threads : 256;
         info->solve_item_kb = params->solve_item_kb > 0 ? params->solve_item_kb : 64;
+        info->solve_leaf_kb = params->solve_leaf_kb > 0 ? params->solve_leaf_kb : info->solve_item_kb;
+        info->solve_leaf_threads = params->solve_leaf_threads > 0 ? params->solve_leaf_threads : info->solve_threads;
         info->solve_items = params->solve_items > 0 ? params->solve_items : 400;
         info->solve_prefetch = params->solve_prefetch <= 0 ? 0 : params->solve_prefetch;
+        info->solve_dense_top = S.top_levels;
+        info->dense_top_cols = S.n_top;
         info->n_sims = 1;
         return HQN_OK;
     } catch (const std::bad_alloc &) {
@@ -1289,10 +1406,10 @@ int hqn_analyse(const hqn_mesh *mesh, const hqn_material *material, const hqn_pa
     }
 }
 
-int sim_set_solve_shapes(sim_handle *sim, int32_t threads, int32_t item_kb, int32_t items, int32_t prefetch) {
-    if (!sim) return fail(HQN_ERR_ARG, "null handle");
+int sim_set_solve_shapes(sim_handle *sim, const hqn_params *shapes) {
+    if (!sim || !shapes) return fail(HQN_ERR_ARG, "null argument");
     try {
-        return sim->impl->set_solve_shapes(threads, item_kb, items, prefetch);
+        return sim->impl->set_solve_shapes(*shapes);
     } catch (const std::bad_alloc &) {
         return fail(HQN_ERR_NO_MEMORY, "host allocation failed");
     }

@@ -103,7 +103,8 @@ template <typename R>
 struct DevSolve {
     int nf, n_levels, n_sn;
     int pdl;                    // host: launch the level sweeps with programmatic dependent launch
-    int threads;                // host: threads per sweep block (256 or 512)
+    int threads;                // host: threads per sweep block (128, 256 or 512)
+    int leaf_threads;           // host: threads per block of the leaf level
     int prefetch;               // host: launches ahead whose factor rows a level prefetches into L2 (0: none)
     int fault_test;             // host: 1 = the first level's blocks issue no copy (tests of the bounded wait)
     long long wait_polls;       // bound on a block's wait for its bulk copy, in polls
@@ -128,15 +129,30 @@ struct DevSolve {
     const int *bwd_lvl_start, *bwd_lvl_cnt;  // host: backward items of level l: [start[l], start[l] + cnt[l])
     const int *fwd_lvl_ld, *bwd_lvl_ld;    // host: max ldc / ldr of the level (shared memory)
     const int *fwd_lvl_q, *bwd_lvl_q;      // host: max factor entries of one item of the level
-    // L2 prefetch spans {address lo, address hi, bytes, 0} of the factor rows
-    // each launch reads; launch k of a solve (forward level k for k < L, then
-    // backward level 2L - 1 - k) reads spans [pf_ptr[k], pf_ptr[k + 1]).
+    // L2 prefetch spans {address lo, address hi, bytes, 0}: launch k of a
+    // solve (forward level k for k < L, then backward level 2L - 1 - k) asks
+    // L2 to fetch spans [pf_ptr[k], pf_ptr[k + 1]) -- factor rows of a later
+    // launch and shares of the dense top block's matrix.
+    int pf_any;                            // host: some launch has spans
     const int4 *pf_spans;
     const int *pf_ptr;                     // host: 2 L + 1 entries
+    // Dense top block (solve_dense_top; solve.cu): its tiles (3 int4 each),
+    // per simulation the lower block triangle of S^{-1} as TS x TS tiles,
+    // the free columns of T, and the update entries below T that reach each
+    // column (CSR, n_top + 1 offsets per simulation); the partial products
+    // of every band (dense_nct_max slots of TS rows: one per block column)
+    // and the bands' arrival counters (re-armed by the last contribution).
+    int n_dense_tiles, dense_nct_max;
+    const int4 *dense_tiles;
+    const R *dense_inv;
+    const int *dense_col, *dense_bptr, *dense_bidx;
+    V4<R> *dense_part;
+    int *dense_cnt;
     V4<R> *u;                   // update vectors
     V4<R> *part_r;              // 32 partial sums per backward item (chunk items)
     int *cb_cnt;                // chunks finished per backward column block (re-arms itself)
     unsigned int *err;          // set nonzero if a bulk copy did not arrive in time
+    cudaStream_t stream;        // host: the stream of the launch in progress
 };
 
 // r = A0^{-1} q on the first nf entries (q, r: V4 arrays, may not alias).

@@ -254,9 +254,9 @@ int nd_emit(const NDState &st, int p, int d, uint32_t merge, std::vector<Superno
 // entries are split into chunks of 32 rows x kChunk entries, so an item
 // gathers a short piece of w instead of the whole vector (a few columns per
 // item would otherwise each gather all of it).
-int make_items(const Setup &S, int VN, int kMax, int64_t per_level, ItemLists &out, std::string &err) {
+int make_items(const Setup &S, int VN, int kMaxUpper, int kMaxLeaf, int64_t per_level, ItemLists &out,
+               std::string &err) {
     const int L = S.n_levels, ns = (int)S.sn.size();
-    const int kMin = kMax / 4;
     // lanes per output row: enough that each lane reads a few 16-byte vectors
     auto lanes_for = [&](int len) {
         const int nv = (len + VN - 1) / VN;
@@ -265,7 +265,8 @@ int make_items(const Setup &S, int VN, int kMax, int64_t per_level, ItemLists &o
         return G;
     };
     std::vector<int64_t> lvl_entries(L, 0);
-    for (auto &sn : S.sn) lvl_entries[sn.level] += fwd_row_off(sn.ncol + sn.nrow, sn.ncol, sn.ldc);
+    for (auto &sn : S.sn)
+        if (!sn.top) lvl_entries[sn.level] += fwd_row_off(sn.ncol + sn.nrow, sn.ncol, sn.ldc);
     out = ItemLists{};
     out.fwd_lvl_ptr.assign(L + 1, 0);
     out.bwd_lvl_ptr.assign(L + 1, 0);
@@ -274,11 +275,12 @@ int make_items(const Setup &S, int VN, int kMax, int64_t per_level, ItemLists &o
     out.fwd_lvl_q.assign(L, 0);
     out.bwd_lvl_q.assign(L, 0);
     for (int l = 0; l < L; ++l) {
+        const int kMax = l == 0 ? kMaxLeaf : kMaxUpper, kMin = kMax / 4;
         const int target = (int)std::min<int64_t>(kMax, std::max<int64_t>(kMin, lvl_entries[l] / per_level));
         out.fwd_lvl_ptr[l] = (int)out.fwd_items.size();
         for (int s = 0; s < ns; ++s) {
             const SupernodeHost &sn = S.sn[s];
-            if (sn.level != l || sn.ncol == 0) continue;
+            if (sn.level != l || sn.ncol == 0 || sn.top) continue;
             const int nc = sn.ncol, rows = nc + sn.nrow;
             for (int r0 = 0; r0 < rows;) {
                 int r1 = r0 + 1;
@@ -302,11 +304,12 @@ int make_items(const Setup &S, int VN, int kMax, int64_t per_level, ItemLists &o
     const int kChunk = VN == 4 ? 256 : 128;
     const int kLongRow = 4 * kChunk;
     for (int l = 0; l < L; ++l) {
+        const int kMax = l == 0 ? kMaxLeaf : kMaxUpper, kMin = kMax / 4;
         const int target = (int)std::min<int64_t>(kMax, std::max<int64_t>(kMin, lvl_entries[l] / per_level));
         out.bwd_lvl_ptr[l] = (int)out.bwd_items.size();
         for (int s = 0; s < ns; ++s) {
             const SupernodeHost &sn = S.sn[s];
-            if (sn.level != l || sn.ncol == 0) continue;
+            if (sn.level != l || sn.ncol == 0 || sn.top) continue;
             for (int c0 = 0; c0 < sn.ncol;) {
                 const int w0 = bwd_row_start(c0);
                 if (sn.ldr - w0 > kLongRow) {
@@ -439,15 +442,168 @@ static int leaf_size_of(const hqn_params &prm, int n_free) {
     return prm.precision == HQN_FP32_MIXED && n_free <= 150000 ? 128 : 64;
 }
 
+// The dense top block of hqn_params.solve_dense_top (D < 0: none; 0: the
+// automatic choice below): the subtree T of the top D levels, S^{-1} = (L_TT L_TT^T)^{-1} on its columns and the update
+// entries below T that reach each of its columns.  S^{-1} = L_TT^{-T} L_TT^{-1}
+// comes from the supernodal sweeps themselves, run on T alone with the
+// identity as n_top right-hand sides: forward X := L_TT^{-1} X (right-looking:
+// X_C := Q_ss X_C, X_R -= Q_Rs X_C), then backward X := L_TT^{-T} X
+// (X_C := Q_ss^T X_C - Q_Rs^T X_R, root first), every step one GEMM.
+static int build_dense_top(Setup &S, int D, std::string &err) {
+    const int ns = (int)S.sn.size(), nf = S.n_free;
+    S.top_levels = 0;
+    S.n_top = 0;
+    S.top_col.clear();
+    S.top_inv.clear();
+    S.top_bptr.assign(1, 0);
+    S.top_bidx.clear();
+    for (auto &sn : S.sn) sn.top = false;
+    if (D < 0) return HQN_OK;
+    if (D == 0) {
+        // automatic: the most top levels (at most 3) whose block has at most
+        // kAutoCols columns (the host's cost grows as the cube of the columns)
+        constexpr int kAutoCols = 5000;
+        for (int d = std::min(3, S.n_levels); d >= 1 && D == 0; --d) {
+            int64_t cols = 0;
+            for (const SupernodeHost &sn : S.sn)
+                if (sn.level >= S.n_levels - d) cols += sn.ncol;
+            if (cols <= kAutoCols) D = d;
+        }
+        if (D == 0) return HQN_OK;
+    }
+    D = std::min(D, S.n_levels);
+    std::vector<int> pos(nf, -1);  // free column -> T-local index
+    for (int s = 0; s < ns; ++s) {
+        SupernodeHost &sn = S.sn[s];
+        if (sn.level < S.n_levels - D || sn.ncol == 0) continue;
+        sn.top = true;
+    }
+    // columns of T in ascending order
+    for (int s = 0; s < ns; ++s)
+        if (S.sn[s].top)
+            for (int a = 0; a < S.sn[s].ncol; ++a) S.top_col.push_back(S.sn[s].col + a);
+    std::sort(S.top_col.begin(), S.top_col.end());
+    const int n = (int)S.top_col.size();
+    if (n == 0) return HQN_OK;
+    if (n > 16384) {
+        err = "the dense top block would hold more than 16384 columns";
+        return HQN_ERR_UNSUPPORTED;
+    }
+    for (int i = 0; i < n; ++i) pos[S.top_col[i]] = i;
+    // every T supernode's columns are consecutive in T-local order and its
+    // rows lie in T (an ancestor's columns)
+    for (int s = 0; s < ns; ++s) {
+        const SupernodeHost &sn = S.sn[s];
+        if (!sn.top) continue;
+        for (int a = 1; a < sn.ncol; ++a)
+            if (pos[sn.col + a] != pos[sn.col] + a) {
+                err = "dense top block: supernode columns not consecutive";
+                return HQN_ERR_ARG;
+            }
+        for (int b = 0; b < sn.nrow; ++b)
+            if (pos[S.rows[sn.roff + b]] < 0) {
+                err = "dense top block: a row lies outside the top subtree";
+                return HQN_ERR_ARG;
+            }
+        if (sn.parent >= 0 && !S.sn[sn.parent].top) {
+            err = "dense top block: not a subtree";
+            return HQN_ERR_ARG;
+        }
+    }
+    std::vector<double> X((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) X[(size_t)i * n + i] = 1.0;
+    std::vector<double> XcT, tmp, Qt;
+    // forward: X := L_TT^{-1} X (X stays lower triangular: columns >= cend of a
+    // supernode's rows are still zero when it is processed)
+    for (int s = 0; s < ns; ++s) {
+        const SupernodeHost &sn = S.sn[s];
+        if (!sn.top) continue;
+        const int nc = sn.ncol, nr = sn.nrow, c0 = pos[sn.col], cend = c0 + nc;
+        const double *Qs = S.Q.data() + sn.qoff;
+        XcT.assign((size_t)cend * nc, 0.0);  // X_C^T (cend x nc)
+        for (int a = 0; a < nc; ++a)
+            for (int j = 0; j < cend; ++j) XcT[(size_t)j * nc + a] = X[(size_t)(c0 + a) * n + j];
+        tmp.assign((size_t)nc * cend, 0.0);
+        gemm_nt(nc, cend, nc, 1.0, Qs, nc, XcT.data(), nc, 0.0, tmp.data(), cend, false);
+        for (int a = 0; a < nc; ++a)
+            std::copy(tmp.begin() + (size_t)a * cend, tmp.begin() + (size_t)(a + 1) * cend, X.begin() + (size_t)(c0 + a) * n);
+        if (nr > 0) {
+            tmp.assign((size_t)nr * cend, 0.0);
+            gemm_nt(nr, cend, nc, 1.0, Qs + (size_t)nc * nc, nc, XcT.data(), nc, 0.0, tmp.data(), cend, false);
+            for (int b = 0; b < nr; ++b) {
+                double *xr = X.data() + (size_t)pos[S.rows[sn.roff + b]] * n;
+                const double *t = tmp.data() + (size_t)b * cend;
+                for (int j = 0; j < cend; ++j) xr[j] -= t[j];
+            }
+        }
+    }
+    // backward, root first: X_C := Q_ss^T X_C - Q_Rs^T X_R (all n columns)
+    for (int s = ns - 1; s >= 0; --s) {
+        const SupernodeHost &sn = S.sn[s];
+        if (!sn.top) continue;
+        const int nc = sn.ncol, nr = sn.nrow, c0 = pos[sn.col], rows = nc + nr;
+        const double *Qs = S.Q.data() + sn.qoff;
+        // Qt = Q_s^T (nc x rows); W^T = [X_C; -X_R]^T (n x rows)
+        Qt.assign((size_t)nc * rows, 0.0);
+        for (int i = 0; i < rows; ++i)
+            for (int a = 0; a < nc; ++a) Qt[(size_t)a * rows + i] = Qs[(size_t)i * nc + a];
+        XcT.assign((size_t)n * rows, 0.0);
+        for (int i = 0; i < rows; ++i) {
+            const bool own = i < nc;
+            const double *xr = X.data() + (size_t)(own ? c0 + i : pos[S.rows[sn.roff + i - nc]]) * n;
+            for (int j = 0; j < n; ++j) XcT[(size_t)j * rows + i] = own ? xr[j] : -xr[j];
+        }
+        tmp.assign((size_t)nc * n, 0.0);
+        gemm_nt(nc, n, rows, 1.0, Qt.data(), rows, XcT.data(), rows, 0.0, tmp.data(), n, false);
+        std::copy(tmp.begin(), tmp.end(), X.begin() + (size_t)c0 * n);
+    }
+    // S^{-1} is symmetric; average the two triangles' rounding
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j) {
+            const double v = 0.5 * (X[(size_t)i * n + j] + X[(size_t)j * n + i]);
+            X[(size_t)i * n + j] = X[(size_t)j * n + i] = v;
+        }
+    S.top_inv.swap(X);
+    // update entries below T that reach each T column: the column's child
+    // entries, expanded through the update vectors of T's own supernodes
+    std::vector<int> owner(S.n_upd, -1);
+    for (int s = 0; s < ns; ++s)
+        for (int b = 0; b < S.sn[s].nrow; ++b) owner[S.sn[s].uoff + b] = s;
+    std::vector<int> stack;
+    for (int i = 0; i < n; ++i) {
+        const int j = S.top_col[i];
+        stack.assign(S.fg_idx.begin() + S.fg_ptr[j], S.fg_idx.begin() + S.fg_ptr[j + 1]);
+        while (!stack.empty()) {
+            const int e = stack.back();
+            stack.pop_back();
+            if (S.sn[owner[e]].top) {
+                for (int k = S.ug_ptr[e]; k < S.ug_ptr[e + 1]; ++k) stack.push_back(S.ug_idx[k]);
+            } else {
+                S.top_bidx.push_back(e);
+            }
+        }
+        std::sort(S.top_bidx.begin() + S.top_bptr.back(), S.top_bidx.end());
+        if ((int)S.top_bidx.size() - S.top_bptr.back() > 4) {
+            err = "dense top block: a column receives more than four update entries from below";
+            return HQN_ERR_UNSUPPORTED;
+        }
+        S.top_bptr.push_back((int)S.top_bidx.size());
+    }
+    S.top_levels = D;
+    S.n_top = n;
+    return HQN_OK;
+}
+
 int plan_sweeps(Setup &S, const hqn_params &prm, std::string &err) {
     const int VN = prm.precision == HQN_FP64_PLAIN ? 2 : 4;
     const int esize = prm.precision == HQN_FP64_PLAIN ? 8 : 4;
     // a level's entries spread over solve_items items (default 400, a few
     // blocks per SM), each within [kMax/4, kMax] entries, kMax =
-    // solve_item_kb KB (default 64)
+    // solve_item_kb KB (default 64), solve_leaf_kb on the leaf level
     const int item_kb = prm.solve_item_kb > 0 ? prm.solve_item_kb : 64;
+    const int leaf_kb = prm.solve_leaf_kb > 0 ? prm.solve_leaf_kb : item_kb;
     const int per_level = prm.solve_items > 0 ? prm.solve_items : 400;
-    int rc = make_items(S, VN, item_kb * 1024 / esize, per_level, S.lv, err);
+    int rc = make_items(S, VN, item_kb * 1024 / esize, leaf_kb * 1024 / esize, per_level, S.lv, err);
     if (rc != HQN_OK) return rc;
     // the longest vector a sweep block stages (what bounds its shared memory)
     S.max_ld = 0;
@@ -829,6 +985,7 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
     }
     S.n_levels = 0;
     for (auto &sn : S.sn) S.n_levels = std::max(S.n_levels, sn.level + 1);
+    if (int rc = build_dense_top(S, prm.solve_dense_top, err)) return rc;
     if (int rc = plan_sweeps(S, prm, err)) return rc;
 
     S.setup_seconds =

@@ -26,6 +26,7 @@ struct MaterialHost {
 struct SupernodeHost {
     int col = 0, ncol = 0, nrow = 0;  // first column, #columns, #rows in R
     int parent = -1, level = 0;
+    bool top = false;                 // solved by the dense top block instead of the sweeps
     int64_t qoff = 0;                 // offset of Q_s = [L_ss^{-1}; L_Rs L_ss^{-1}] (rows x ncol)
     int uoff = 0;                     // offset of its update vector (nrow entries)
     int roff = 0;                     // offset of R in the row-index array
@@ -80,6 +81,16 @@ struct Setup {
                                      // four under a merged supernode
     int n_upd = 0, n_levels = 0;
     ItemLists lv;                    // work items of the sweeps, level by level
+    // Dense top block (hqn_params.solve_dense_top = D > 0): the supernodes of
+    // the top D tree levels (level >= n_levels - D) form a subtree T whose
+    // n_top columns are solved together: r_T = S^{-1} f_T with S = L_TT L_TT^T,
+    // the Schur complement of A0 on T, and f_T = q_T minus the update entries
+    // of the supernodes below T that reach T's columns (directly or passed
+    // on through T's own update vectors).
+    int top_levels = 0, n_top = 0;
+    std::vector<int> top_col;        // n_top: free column of T-local index i (ascending)
+    std::vector<double> top_inv;     // n_top x n_top: S^{-1}, row-major
+    std::vector<int> top_bptr, top_bidx;  // per T-local column: update entries below T to subtract
     int64_t qf_total = 0, qb_total = 0;  // entries of the two packed copies
     int max_ld = 0;                  // longest vector a sweep block stages (bounds its shared memory)
     int max_front_cols = 0;          // max ncol

@@ -34,6 +34,9 @@
 // listed by the host): the stream of the factor out of HBM runs ahead of the
 // chain of levels, and a level's own bulk copies then read L2.
 //
+// When the top levels are solved by the dense block, the forward launches
+// before it also prefetch its matrix into L2 the same way.
+//
 // Every wait is bounded (wait_polls polls of the copy's mbarrier); past the
 // bound the block flags the error in the handle's control block and leaves
 // without reading its buffer, after its copy in flight, if any, has landed
@@ -548,12 +551,226 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_bwd(DevSolve<R> S, int item0,
                     pf_n);
 }
 
+// ---- dense top block
+//
+// The supernodes of the tree's top levels are solved together (solve_dense_top):
+// r_T = S^{-1} f_T, with S^{-1} (the inverse of A0's Schur complement on the
+// top subtree's columns T, computed on the host) and f_T = q_T minus the
+// update entries of the supernodes below T that reach T.  One launch
+// replaces both sweeps' top levels.
+//
+// S^{-1} is symmetric, so only its lower block triangle is stored: TS x TS
+// tiles (I, J), J <= I, each a contiguous row-major block, zero-padded past
+// the last column.  A block takes one tile: every row of the tile gives a
+// row product S_IJ f_J (for band I), and an off-diagonal tile also gives the
+// column products S_IJ^T f_I (for band J) from the same loaded rows.  Each
+// product lands in its band's partial slot (slot J for row products, slot I
+// for column products); the last of a band's nb contributions to arrive adds
+// the slots in order and writes r.
+//   tile record (3 int4): {tile offset lo, hi, I, J}
+//                         {n_top, first band of the simulation, nb, tcol offset}
+//                         {bptr offset, 0, 0, 0}
+constexpr int TS = 128;
+
+__device__ __forceinline__ float4 ld_stream(const float4 *p, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double2 ld_stream(const double2 *p, uint64_t pol) {
+    double2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+                 : "=d"(v.x), "=d"(v.y)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
+// f of Eq. PDsolution's right-hand side on TS columns of T from c0 (zero past
+// n): q minus the (<= 4) update entries from below T, entries e.
+template <typename R>
+__device__ __forceinline__ void dense_gather(const DevSolve<R> &S, const V4<R> *rhs, const int *colv, const int4 *bnd,
+                                             int n_valid, R *f, int tid, int nt) {
+    for (int j = tid; j < TS; j += nt) {
+        R fx = R(0), fy = R(0), fz = R(0);
+        if (j < n_valid) {
+            const int4 e = bnd[j];
+            const V4<R> v = ld_cg(rhs + colv[j]);
+            V4<R> u[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) u[k].x = u[k].y = u[k].z = R(0);
+            if (e.x >= 0) u[0] = ld_cg(S.u + e.x);
+            if (e.y >= 0) u[1] = ld_cg(S.u + e.y);
+            if (e.z >= 0) u[2] = ld_cg(S.u + e.z);
+            if (e.w >= 0) u[3] = ld_cg(S.u + e.w);
+            fx = v.x - u[0].x - u[1].x - u[2].x - u[3].x;
+            fy = v.y - u[0].y - u[1].y - u[2].y - u[3].y;
+            fz = v.z - u[0].z - u[1].z - u[2].z - u[3].z;
+        }
+        f[j] = fx; f[TS + j] = fy; f[2 * TS + j] = fz;
+    }
+}
+
+template <typename R, int NT>
+__global__ void __launch_bounds__(NT, 768 / NT) k_dense(DevSolve<R> S, const V4<R> *rhs, V4<R> *r) {
+    constexpr int NW = NT / 32;
+    constexpr int RPW = TS / NW;  // rows per warp
+    // one lane holds TS / 32 consecutive columns of a row: 4 floats (one
+    // 16-byte load) or 4 doubles (two)
+    __shared__ __align__(16) R fJ[3 * TS], fI[3 * TS];
+    __shared__ __align__(16) R colpart[NW][3][TS];
+    __shared__ int colvJ[TS], colvI[TS];
+    __shared__ int4 bndJ[TS], bndI[TS];
+    __shared__ int lastJ, lastI;
+    const int4 *rec = S.dense_tiles + 3 * (size_t)blockIdx.x;
+    const int4 a = rec[0], b = rec[1], c = rec[2];
+    const long long off = (long long)(unsigned)a.x | ((long long)a.y << 32);
+    const int I = a.z, J = a.w;
+    const int n = b.x, band0 = b.y, nb = b.z, tc0 = b.w;
+    const bool diag = I == J;
+    const int rI = I * TS, cJ = J * TS;
+    const int nI = min(TS, n - rI), nJ = min(TS, n - cJ);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    // before the wait: the index data of the gathers (nothing the solve writes)
+    const int *tcol = S.dense_col + tc0;
+    const int *bptr = S.dense_bptr + c.x;
+    for (int j = threadIdx.x; j < 2 * TS; j += NT) {
+        const bool jside = j < TS;
+        const int jj = jside ? j : j - TS, col = (jside ? cJ : rI) + jj;
+        if (!jside && diag) continue;
+        if (jj >= (jside ? nJ : nI)) continue;
+        const int k0 = bptr[col], k1 = bptr[col + 1];
+        const int4 e = make_int4(k1 > k0 ? S.dense_bidx[k0] : -1, k1 > k0 + 1 ? S.dense_bidx[k0 + 1] : -1,
+                                 k1 > k0 + 2 ? S.dense_bidx[k0 + 2] : -1, k1 > k0 + 3 ? S.dense_bidx[k0 + 3] : -1);
+        if (jside) { colvJ[jj] = tcol[col]; bndJ[jj] = e; }
+        else { colvI[jj] = tcol[col]; bndI[jj] = e; }
+    }
+    pdl_trigger();
+    pdl_wait();
+    __syncthreads();
+    dense_gather<R>(S, rhs, colvJ, bndJ, nJ, fJ, threadIdx.x, NT);
+    if (!diag) dense_gather<R>(S, rhs, colvI, bndI, nI, fI, threadIdx.x, NT);
+    __syncthreads();
+    const R *fi = diag ? fJ : fI;
+    // this lane's columns of f_J
+    R fj[3][4];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+        fj[0][cc] = fJ[4 * lane + cc];
+        fj[1][cc] = fJ[TS + 4 * lane + cc];
+        fj[2][cc] = fJ[2 * TS + 4 * lane + cc];
+    }
+    R ca[3][4];  // column products of this lane's columns over the warp's rows
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) ca[k][cc] = R(0);
+    const R *tile = S.dense_inv + off;
+    V4<R> *part = S.dense_part + (size_t)band0 * S.dense_nct_max * TS;
+    constexpr int BATCH = 4;  // rows whose loads are in flight together
+    for (int i0 = warp * RPW; i0 < warp * RPW + RPW; i0 += BATCH) {
+        R q[BATCH][4];
+#pragma unroll
+        for (int h = 0; h < BATCH; ++h) {
+            const R *row = tile + (size_t)(i0 + h) * TS + 4 * lane;
+            if (sizeof(R) == 4) {
+                const float4 v = ld_stream(reinterpret_cast<const float4 *>(row), pol);
+                q[h][0] = v.x; q[h][1] = v.y; q[h][2] = v.z; q[h][3] = v.w;
+            } else {
+                const double2 v0 = ld_stream(reinterpret_cast<const double2 *>(row), pol);
+                const double2 v1 = ld_stream(reinterpret_cast<const double2 *>(row) + 1, pol);
+                q[h][0] = v0.x; q[h][1] = v0.y; q[h][2] = v1.x; q[h][3] = v1.y;
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < BATCH; ++h) {
+            const int i = i0 + h;
+            R px = R(0), py = R(0), pz = R(0);
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                px += q[h][cc] * fj[0][cc];
+                py += q[h][cc] * fj[1][cc];
+                pz += q[h][cc] * fj[2][cc];
+            }
+            px = group_sum<R, 32>(px);
+            py = group_sum<R, 32>(py);
+            pz = group_sum<R, 32>(pz);
+            if (lane == 0 && i < nI) {
+                V4<R> o;
+                o.x = px; o.y = py; o.z = pz; o.w = R(0);
+                part[((size_t)I * S.dense_nct_max + J) * TS + i] = o;  // band I, slot J
+            }
+            if (!diag) {
+                const R gx = fi[i], gy = fi[TS + i], gz = fi[2 * TS + i];
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    ca[0][cc] += q[h][cc] * gx;
+                    ca[1][cc] += q[h][cc] * gy;
+                    ca[2][cc] += q[h][cc] * gz;
+                }
+            }
+        }
+    }
+    if (!diag) {
+        // the warps' column products, added in warp order: band J, slot I
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) colpart[warp][k][4 * lane + cc] = ca[k][cc];
+        __syncthreads();
+        for (int j = threadIdx.x; j < nJ; j += NT) {
+            R sx = R(0), sy = R(0), sz = R(0);
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                sx += colpart[w][0][j];
+                sy += colpart[w][1][j];
+                sz += colpart[w][2][j];
+            }
+            V4<R> o;
+            o.x = sx; o.y = sy; o.z = sz; o.w = R(0);
+            part[((size_t)J * S.dense_nct_max + I) * TS + j] = o;
+        }
+    }
+    // arrivals: band I (and band J); the nb-th contribution to a band adds
+    // its slots in order
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();  // release: this tile's partials before the counts
+        lastI = atomicAdd(S.dense_cnt + band0 + I, 1) == nb - 1;
+        lastJ = diag ? 0 : (atomicAdd(S.dense_cnt + band0 + J, 1) == nb - 1);
+        if (lastI || lastJ) __threadfence();  // acquire, ordered for the block by the barrier below
+    }
+    __syncthreads();
+    for (int side = 0; side < 2; ++side) {
+        const bool go = side == 0 ? lastI : lastJ;
+        if (!go) continue;
+        const int B = side == 0 ? I : J, nB = side == 0 ? nI : nJ;
+        const V4<R> *slots = part + (size_t)B * S.dense_nct_max * TS;
+        for (int i = threadIdx.x; i < nB; i += NT) {
+            R sx = R(0), sy = R(0), sz = R(0);
+            for (int t = 0; t < nb; ++t) {
+                const V4<R> p = ld_cg(slots + (size_t)t * TS + i);
+                sx += p.x; sy += p.y; sz += p.z;
+            }
+            V4<R> o;
+            o.x = sx; o.y = sy; o.z = sz; o.w = R(0);
+            r[tcol[B * TS + i]] = o;
+        }
+        if (threadIdx.x == 0) S.dense_cnt[band0 + B] = 0;
+    }
+}
+
 // Dynamic shared memory of a sweep block: qcap factor entries, 3 x ld vector
 // entries and ld 16-byte index slots.
 template <typename R>
 size_t sweep_smem(int qcap, int ld) {
     return ((size_t)qcap + 3 * (size_t)ld) * sizeof(R) + 16 * (size_t)ld;
 }
+
+template <typename R> cudaStream_t st_of(const DevSolve<R> &s) { return s.stream; }
 
 // One level's launch, with the programmatic-serialisation attribute when
 // the handle chains levels.
@@ -574,36 +791,69 @@ void launch_level(bool pdl, void (*kernel)(DevSolve<R>, int, int, KArgs...), int
 }
 
 template <typename R, int NT>
-void launch_sweeps(const DevSolve<R> &s, const V4<R> *q, V4<R> *z, V4<R> *r, cudaStream_t st) {
+void launch_fwd_level(const DevSolve<R> &s, int l, const V4<R> *q, V4<R> *z, const int4 *pf, int pf_n) {
+    const int a = s.fwd_lvl_ptr[l], b = s.fwd_lvl_ptr[l + 1];
+    launch_level<R, const V4<R> *, V4<R> *, const int4 *, int, int>(
+        s.pdl != 0, k_fwd<R, NT>, b - a, NT, sweep_smem<R>(s.fwd_lvl_q[l], s.fwd_lvl_ld[l]), st_of(s), s, a,
+        s.fwd_lvl_q[l], q, z, pf, pf_n, (s.fault_test == 1 && l == 0) ? 1 : 0);
+}
+
+template <typename R, int NT>
+void launch_bwd_level(const DevSolve<R> &s, int l, const V4<R> *z, V4<R> *r, const int4 *pf, int pf_n) {
+    const int a = s.bwd_lvl_start[l], cnt = s.bwd_lvl_cnt[l];
+    launch_level<R, const V4<R> *, V4<R> *, const int4 *, int>(
+        s.pdl != 0, k_bwd<R, NT>, cnt, NT, sweep_smem<R>(s.bwd_lvl_q[l], s.bwd_lvl_ld[l]), st_of(s), s, a,
+        s.bwd_lvl_q[l], z, r, pf, pf_n);
+}
+
+// One solve: the forward levels (leaves first), the dense top block if any,
+// the backward levels (root first).  The leaf level may run with its own
+// block size.
+template <typename R>
+void launch_sweeps(const DevSolve<R> &s, const V4<R> *q, V4<R> *z, V4<R> *r) {
     const int L = s.n_levels;
     // launch k of the solve: forward level k (k < L), then backward level 2L - 1 - k
     auto pf_of = [&](int k, const int4 **p, int *n) {
-        const int t = k + s.prefetch;
         *p = nullptr;
         *n = 0;
-        if (s.prefetch <= 0 || t >= 2 * L) return;
-        *p = s.pf_spans + s.pf_ptr[t];
-        *n = s.pf_ptr[t + 1] - s.pf_ptr[t];
+        if (!s.pf_any) return;
+        *p = s.pf_spans + s.pf_ptr[k];
+        *n = s.pf_ptr[k + 1] - s.pf_ptr[k];
     };
+    auto nt_of = [&](int l) { return l == 0 ? s.leaf_threads : s.threads; };
     for (int l = 0; l < L; ++l) {
-        const int a = s.fwd_lvl_ptr[l], b = s.fwd_lvl_ptr[l + 1];
-        if (b <= a) continue;
+        if (s.fwd_lvl_ptr[l + 1] <= s.fwd_lvl_ptr[l]) continue;
         const int4 *pf;
         int pf_n;
         pf_of(l, &pf, &pf_n);
-        launch_level<R, const V4<R> *, V4<R> *, const int4 *, int, int>(
-            s.pdl != 0, k_fwd<R, NT>, b - a, NT, sweep_smem<R>(s.fwd_lvl_q[l], s.fwd_lvl_ld[l]), st, s, a,
-            s.fwd_lvl_q[l], q, z, pf, pf_n, (s.fault_test == 1 && l == 0) ? 1 : 0);
+        switch (nt_of(l)) {
+            case 128: launch_fwd_level<R, 128>(s, l, q, z, pf, pf_n); break;
+            case 512: launch_fwd_level<R, 512>(s, l, q, z, pf, pf_n); break;
+            default: launch_fwd_level<R, 256>(s, l, q, z, pf, pf_n); break;
+        }
+    }
+    if (s.n_dense_tiles > 0) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)s.n_dense_tiles);
+        cfg.blockDim = dim3(256);
+        cfg.stream = st_of(s);
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = s.pdl ? 1 : 0;
+        cudaLaunchKernelEx(&cfg, k_dense<R, 256>, s, q, r);
     }
     for (int l = L - 1; l >= 0; --l) {
-        const int a = s.bwd_lvl_start[l], cnt = s.bwd_lvl_cnt[l];
-        if (cnt <= 0) continue;
+        if (s.bwd_lvl_cnt[l] <= 0) continue;
         const int4 *pf;
         int pf_n;
         pf_of(2 * L - 1 - l, &pf, &pf_n);
-        launch_level<R, const V4<R> *, V4<R> *, const int4 *, int>(
-            s.pdl != 0, k_bwd<R, NT>, cnt, NT, sweep_smem<R>(s.bwd_lvl_q[l], s.bwd_lvl_ld[l]), st, s, a,
-            s.bwd_lvl_q[l], (const V4<R> *)z, r, pf, pf_n);
+        switch (nt_of(l)) {
+            case 128: launch_bwd_level<R, 128>(s, l, (const V4<R> *)z, r, pf, pf_n); break;
+            case 512: launch_bwd_level<R, 512>(s, l, (const V4<R> *)z, r, pf, pf_n); break;
+            default: launch_bwd_level<R, 256>(s, l, (const V4<R> *)z, r, pf, pf_n); break;
+        }
     }
 }
 
@@ -620,15 +870,17 @@ cudaError_t prepare_nt() {
 template <typename R> size_t solve_block_smem(int qcap, int ld) { return sweep_smem<R>(qcap, ld); }
 
 template <typename R> cudaError_t solve_prepare() {
-    cudaError_t e = prepare_nt<R, 256>();
+    cudaError_t e = prepare_nt<R, 128>();
+    if (e == cudaSuccess) e = prepare_nt<R, 256>();
     if (e == cudaSuccess) e = prepare_nt<R, 512>();
     return e;
 }
 
 template <typename R>
 void launch_solve(const DevSolve<R> &s, const V4<R> *q, V4<R> *z, V4<R> *r, cudaStream_t st) {
-    if (s.threads == 512) launch_sweeps<R, 512>(s, q, z, r, st);
-    else launch_sweeps<R, 256>(s, q, z, r, st);
+    DevSolve<R> t = s;
+    t.stream = st;
+    launch_sweeps<R>(t, q, z, r);
 }
 
 template void launch_solve<float>(const DevSolve<float> &, const V4<float> *, V4<float> *, V4<float> *, cudaStream_t);

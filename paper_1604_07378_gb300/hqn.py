@@ -63,7 +63,8 @@ class Params(C.Structure):
                 ("iters", C.c_int32), ("history_m", C.c_int32), ("ls_max", C.c_int32),
                 ("precision", C.c_int32), ("leaf_size", C.c_int32), ("use_graph", C.c_int32),
                 ("tet_block", C.c_int32), ("ls_batch", C.c_int32), ("solve_threads", C.c_int32),
-                ("solve_item_kb", C.c_int32), ("solve_items", C.c_int32), ("solve_prefetch", C.c_int32),
+                ("solve_item_kb", C.c_int32), ("solve_items", C.c_int32), ("solve_leaf_kb", C.c_int32),
+                ("solve_leaf_threads", C.c_int32), ("solve_dense_top", C.c_int32), ("solve_prefetch", C.c_int32),
                 ("n_colliders", C.c_int32), ("contact_scale", C.c_double),
                 ("colliders", Collider * MAX_COLLIDERS), ("a0_solver", C.c_int32), ("pcg_iters", C.c_int32),
                 ("direction", C.c_int32), ("cheb_S", C.c_int32), ("cheb_rho", C.c_double),
@@ -86,7 +87,9 @@ class Info(C.Structure):
                 ("device_bytes", C.c_int64), ("precision", C.c_int32),
                 ("graph_mode", C.c_int32), ("n_update_entries", C.c_int64),
                 ("chained_sweeps", C.c_int32), ("solve_threads", C.c_int32), ("solve_item_kb", C.c_int32),
-                ("solve_items", C.c_int32), ("solve_prefetch", C.c_int32), ("n_sims", C.c_int32)]
+                ("solve_items", C.c_int32), ("solve_leaf_kb", C.c_int32), ("solve_leaf_threads", C.c_int32),
+                ("solve_prefetch", C.c_int32), ("solve_dense_top", C.c_int32),
+                ("dense_top_cols", C.c_int32), ("n_sims", C.c_int32)]
 
 
 _lib = None
@@ -124,7 +127,7 @@ def library(path: str | None = None):
     lib.sim_get_info.argtypes = [C.c_void_p, C.POINTER(Info)]
     lib.hqn_measure_peak.argtypes = [C.c_int32, _dp]
     lib.hqn_measure_peak.restype = C.c_int
-    lib.sim_set_solve_shapes.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+    lib.sim_set_solve_shapes.argtypes = [C.c_void_p, C.POINTER(Params)]
     lib.sim_set_solve_shapes.restype = C.c_int
     lib.hqn_mesh_key.argtypes = [C.POINTER(Mesh)]
     lib.hqn_mesh_key.restype = C.c_uint64
@@ -355,10 +358,15 @@ class Sim:
                "sim_direction")
         return d
 
-    def set_solve_shapes(self, solve_threads=0, solve_item_kb=0, solve_items=0, solve_prefetch=0):
-        """``sim_set_solve_shapes``: re-plans the sweeps on this handle."""
-        _check(library().sim_set_solve_shapes(self._h, solve_threads, solve_item_kb, solve_items, solve_prefetch),
-               "sim_set_solve_shapes")
+    def set_solve_shapes(self, **shapes):
+        """``sim_set_solve_shapes``: re-plans the sweeps on this handle with the
+        given solve_* fields (the others at their defaults)."""
+        p = Params()
+        for k, v in shapes.items():
+            if not k.startswith("solve_") or k == "solve_dense_top":
+                raise ValueError(f"not a re-plannable sweep shape: {k}")
+            setattr(p, k, v)
+        _check(library().sim_set_solve_shapes(self._h, C.byref(p)), "sim_set_solve_shapes")
 
     def time_stage(self, stage, reps=20):
         """Mean device milliseconds of one launch of a stage (CUDA events on the

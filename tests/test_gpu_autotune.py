@@ -39,13 +39,17 @@ def test_replanned_sweeps_solve_and_step(use_graph):
     r_ref = O.solve_A(P, q)
     x_ref, _ = O.solve_step(P, w.q_cur, w.q_prev, iters=w.iters, m=w.history)
     with hqn.Sim.from_workload(w, precision=FP32, use_graph=use_graph) as sim:
-        for shape in autotune.SHAPE_GRID[::5]:
-            sim.set_solve_shapes(*shape)
+        for shape in autotune.SHAPE_GRID[::5] + (dict(solve_threads=128, solve_leaf_threads=512),):
+            sim.set_solve_shapes(**shape)
             info = sim.info()
-            assert (info["solve_threads"], info["solve_item_kb"], info["solve_items"]) == shape[:3]
+            for k in ("solve_threads", "solve_item_kb", "solve_items"):
+                if shape.get(k):
+                    assert info[k] == shape[k], (k, shape)
+            if shape.get("solve_leaf_threads"):
+                assert info["solve_leaf_threads"] == shape["solve_leaf_threads"]
             assert rel(sim.solve_A0(q), r_ref) <= 2e-5, shape
         with pytest.raises(hqn.HQNError):
-            sim.set_solve_shapes(384, 0, 0, 0)
+            sim.set_solve_shapes(solve_threads=384)
         sim.set_state(w.q_cur, w.q_prev)
         assert sim.step(1) >= 0
         assert rel(sim.get_state()[0], x_ref) <= 1e-4
@@ -58,8 +62,9 @@ def test_tuning_writes_a_cache_that_sim_create_applies(tmp_path):
     from paper_1604_07378_gb300 import autotune, hqn
     w = W9
     cache = str(tmp_path / "cache.txt")
-    grid = ((256, 64, 400, -1), (256, 32, 800, 2), (512, 96, 152, 2), (512, 64, 152, 3))
-    res = autotune.tune_workload(w, leaf_sizes=(32, 64), grid=grid, reps=5, steps=3, cache=cache)
+    grid = (dict(solve_prefetch=-1), dict(solve_item_kb=32, solve_items=800, solve_leaf_kb=16, solve_leaf_threads=128),
+            dict(solve_threads=512, solve_item_kb=96, solve_items=152))
+    res = autotune.tune_workload(w, leaf_sizes=(32, 64), dense_tops=(0, 2), grid=grid, reps=5, steps=3, cache=cache)
     assert res["step_ms"] <= res["default_step_ms"]
     key = autotune.mesh_key(w.rest_pos, w.tets, w.clamped)
     dev = autotune._device_name()
@@ -68,6 +73,7 @@ def test_tuning_writes_a_cache_that_sim_create_applies(tmp_path):
         assert hit is None
         return
     assert hit["leaf_size"] == res["leaf_size"] and hit["solve_items"] == res["solve_items"]
+    assert hit["solve_dense_top"] == res["solve_dense_top"]
     x_ref, _ = O.solve_step(problem_for(w), w.q_cur, w.q_prev, iters=w.iters, m=w.history)
     with hqn.Sim.from_workload(w, precision=FP32, tune_cache=cache) as sim:
         info = sim.info()

@@ -96,14 +96,15 @@ def test_batch_several_steps_bitwise_equal_to_single_handles():
 @pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
 def test_batch_other_sweep_shapes_bitwise_equal_to_single_handles(prec):
     """With other sweep shapes (512-thread blocks, small work items, no L2
-    prefetch) each simulation's items are still its own, so the batch agrees
-    bit for bit with single handles of the same shapes (and with the
-    oracle)."""
+    prefetch, each simulation's top two levels in a dense block) each
+    simulation's items and tiles are still its own, so the batch agrees bit
+    for bit with single handles of the same shapes (and with the oracle)."""
     from paper_1604_07378_gb300 import hqn
-    shapes = dict(solve_threads=512, solve_item_kb=16, solve_items=64, solve_prefetch=-1)
+    shapes = dict(solve_threads=512, solve_item_kb=16, solve_items=64, solve_prefetch=-1, solve_dense_top=2)
     with hqn.Batch(WL, precision=prec, **shapes) as b:
         info = b.info()
         assert (info["solve_threads"], info["solve_item_kb"], info["solve_prefetch"]) == (512, 16, 0)
+        assert info["dense_top_cols"] > 0
         for i, w in enumerate(WL):
             b.set_state(i, w.q_cur, w.q_prev)
         rc, _ = b.step(2)

@@ -118,7 +118,8 @@ def test_large_bar_full_size():
     with _sim(w) as sim:
         g, grad = sim.energy_grad(x0, y)
         r = sim.solve_A0(q)
-    with _sim(w, solve_threads=512, solve_item_kb=128, solve_items=152, solve_prefetch=4) as simp:
+    with _sim(w, solve_threads=512, solve_item_kb=128, solve_items=152, solve_prefetch=4, solve_dense_top=2) as simp:
+        assert simp.info()["dense_top_cols"] > 2401  # the root separator and more
         r_big = simp.solve_A0(q)
     with _sim(w) as sim:
         sim.set_state(w.q_cur, w.q_prev)

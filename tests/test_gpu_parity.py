@@ -110,7 +110,10 @@ LAT30 = W.lattice_workload((30, 30, 30), W.Material(W.NEOHOOKEAN, 5e5, 0.4), cla
 SHAPES = {"default": {}, "t512": dict(solve_threads=512),
           "small_items": dict(solve_item_kb=16, solve_items=2000, solve_prefetch=1),
           "big_items": dict(solve_item_kb=128, solve_items=152, solve_threads=512, solve_prefetch=4),
-          "no_prefetch": dict(solve_prefetch=-1)}
+          "no_prefetch": dict(solve_prefetch=-1),
+          "dense_top1": dict(solve_dense_top=1), "dense_top3": dict(solve_dense_top=3, solve_prefetch=2),
+          "no_dense_top": dict(solve_dense_top=-1),
+          "leaf_items": dict(solve_leaf_kb=16, solve_leaf_threads=128, solve_threads=512)}
 
 
 @pytest.mark.parametrize("w", WORKLOADS[:3] + [LAT30], ids=IDS[:3] + ["lat30"])
@@ -123,7 +126,17 @@ def test_solve_A0_parity(w, prec, shape):
     with sim_for(w, prec, use_graph=0, **SHAPES[shape]) as sim:
         info = sim.info()
         for k, v in SHAPES[shape].items():
-            assert info[k] == (0 if k == "solve_prefetch" and v < 0 else v), (k, info[k])
+            if k in ("solve_prefetch", "solve_dense_top") and v < 0:
+                want = 0
+            elif k == "solve_dense_top":
+                want = min(v, info["n_levels"])
+            else:
+                want = v
+            assert info[k] == want, (k, info[k])
+        if SHAPES[shape].get("solve_dense_top", 0) > 0:
+            assert info["dense_top_cols"] > 0
+        elif SHAPES[shape].get("solve_dense_top", 0) < 0:
+            assert info["dense_top_cols"] == 0
         r = sim.solve_A0(q)
     r_ref = O.solve_A(P, q)
     assert rel(r, r_ref) <= (1e-11 if prec == FP64 else 2e-5)
@@ -222,15 +235,22 @@ def test_sweep_shapes_agree_bitwise():
     np.testing.assert_array_equal(r1, r2)
 
 
+STEP_SHAPES = {"small_items_t512": dict(solve_item_kb=16, solve_items=2000, solve_threads=512),
+               "dense_top2": dict(solve_dense_top=2), "no_dense_top": dict(solve_dense_top=-1)}
+
+
 @pytest.mark.parametrize("w", WORKLOADS, ids=IDS)
 @pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
-def test_step_parity_other_sweep_shapes(w, prec):
-    """Whole steps with small work items (other row splits, so other
-    summation orders) and 512-thread blocks against the oracle, at the
-    tolerances of the default shapes."""
+@pytest.mark.parametrize("shape", sorted(STEP_SHAPES))
+def test_step_parity_other_sweep_shapes(w, prec, shape):
+    """Whole steps with other sweep shapes against the oracle, at the
+    tolerances of the default shapes: small work items (other row splits,
+    so other summation orders) with 512-thread blocks, the dense top block
+    over the top two levels, and no dense top block at all (the default
+    chooses it automatically)."""
     P = problem_for(w)
     x_ref, st = O.solve_step(P, w.q_cur, w.q_prev, iters=w.iters, m=w.history)
-    with sim_for(w, prec, use_graph=1, solve_item_kb=16, solve_items=2000, solve_threads=512) as sim:
+    with sim_for(w, prec, use_graph=1, **STEP_SHAPES[shape]) as sim:
         sim.set_state(w.q_cur, w.q_prev)
         rc, stats = sim.step(1, stats=True)
         qc, _ = sim.get_state()
@@ -393,7 +413,9 @@ def test_sweep_wait_timeout_is_reported(use_graph):
     oracle does."""
     from paper_1604_07378_gb300 import hqn
     w = WORKLOADS[1]
-    with sim_for(w, FP32, use_graph=use_graph, fault_test=1, wait_polls=2000) as sim:
+    # no dense top block: on this small mesh it would take the whole tree,
+    # leaving no sweep level (and no copy wait) to make run out
+    with sim_for(w, FP32, use_graph=use_graph, fault_test=1, wait_polls=2000, solve_dense_top=-1) as sim:
         sim.set_state(w.q_cur, w.q_prev)
         with pytest.raises(hqn.HQNError) as e:
             sim.step(1)
