@@ -338,11 +338,18 @@ int sim_batch_get_state(sim_handle *sim, int32_t index, double *q_cur, double *q
  * sim_step call began).  Synchronises the stream. */
 int sim_batch_get_stats(sim_handle *sim, int32_t index, hqn_step_stats *stats);
 
-/* Sets the state (q_l, q_{l-1}); each n_verts x 3 host doubles.  Clamped
- * vertices are held at their q_l.  q_prev may be NULL (= q_cur, zero velocity). */
+/* Sets the state (q_l, q_{l-1}) of Eq. PD -- the positions of the current and
+ * the previous time step, from which the predictor y = 2 q_l - q_{l-1} +
+ * h^2 M^{-1} f_ext of the next step is formed (Sec. 3); each n_verts x 3 host
+ * doubles.  An initial velocity v enters as q_{l-1} = q_l - h v.  Clamped
+ * vertices are held at their q_l.  q_prev may be NULL (= q_cur, zero
+ * velocity).  The state is the whole state between steps (the L-BFGS history
+ * is reset every step), so sim_get_state / sim_set_state checkpoint and
+ * resume a simulation. */
 int sim_set_state(sim_handle *sim, const double *q_cur, const double *q_prev);
 
-/* Copies the state out (either pointer may be NULL).  Synchronises the stream. */
+/* Copies the state (q_l, q_{l-1}) of Eq. PD out (either pointer may be NULL).
+ * Synchronises the stream. */
 int sim_get_state(sim_handle *sim, double *q_cur, double *q_prev);
 
 /* Advances nsteps time steps (Alg. 1 with Alg. 2) on the device.  stats may be
@@ -370,6 +377,19 @@ int sim_positions_device(sim_handle *sim, void **dev_ptr, int32_t *layout);
  * grad_out may be NULL.  Does not change the state. */
 int sim_energy_grad(sim_handle *sim, const double *x, const double *y,
                     double *g_out, double *grad_out);
+
+/* sim_energy_grad on device arrays: x_dev and y_dev are n_verts x 3 doubles
+ * in the caller's vertex order in device memory (on the handle's device;
+ * read by kernels on the handle's stream, so they must be ready there), and
+ * grad_dev (n_verts x 3 doubles, device; may be NULL) receives grad g in the
+ * same order, zero on clamped rows.  *g_out (host; may be NULL) receives g.
+ * The positions are not checked for NaN/Inf (a non-finite input gives a
+ * non-finite g).  Returns after the work is done (the stream is
+ * synchronised).  The first call allocates the handle's copies of its
+ * float64 rest positions and vertex order on the device.
+ * Errors: HQN_ERR_ARG, HQN_ERR_NO_MEMORY, HQN_ERR_CUDA. */
+int sim_energy_grad_device(sim_handle *sim, const double *x_dev, const double *y_dev, double *g_out,
+                           double *grad_dev);
 
 /* r = A0^{-1} q on the free vertices by the device forward and backward
  * triangular solves (3 right-hand sides); rows of clamped vertices are ignored

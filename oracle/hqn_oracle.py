@@ -24,6 +24,9 @@ taken by the CUDA path, written separately):
     history is dropped and d = -A0^{-1} grad;
   * the backtracking line search gives up after ls_max trials, keeping x_k and
     ending the step's iterations;
+  * a mesh may give each tet its own material (the energy of Eq. PD is a sum
+    over elements): a tet's energy density, its mass share (density * V / 4)
+    and its weight V k in L use its own material, k fitted per material;
   * the anisotropic fibre term kappa/2 (|F d| - 1)^2 of Sec. 4.4 is added to
     the base material's energy density; A0 keeps the base material's
     stiffness fit (Eq. stiffness is defined for Valanis-Landel energies only);
@@ -327,17 +330,26 @@ class Problem:
     colliders: tuple = ()        # ("plane", point, normal), ("sphere", centre, radius) or
                                  # ("torus", centre, axis, ring radius, tube radius)
     contact_scale: float = 100.0
+    mats: tuple = ()             # the materials of a mesh with several (mats[0] is `mat`)
+    tmat: np.ndarray = None      # (T,) index of each tet's material in mats
+    k_tet: np.ndarray = None     # (T,) stiffness k of each tet's material
 
     @property
     def n(self): return self.X.shape[0]
 
 
-def build_problem(X, tets, clamped, mat: VLMaterial, density, h, gravity,
-                  x_start=0.5, x_end=1.5, colliders=(), contact_scale=100.0) -> Problem:
+def build_problem(X, tets, clamped, mat, density, h, gravity,
+                  x_start=0.5, x_end=1.5, colliders=(), contact_scale=100.0, tet_material=None) -> Problem:
+    """mat and density: one material and its density, or (with tet_material,
+    each tet's index into them) sequences of them."""
     X = np.asarray(X, dtype=np.float64)
     tets = np.asarray(tets, dtype=np.int64)
-    P = Problem(X=X, tets=tets, clamped=np.asarray(clamped).astype(bool), mat=mat,
-                density=float(density), h=float(h), gravity=np.asarray(gravity, dtype=np.float64))
+    mats = tuple(mat) if isinstance(mat, (list, tuple)) else (mat,)
+    dens = np.atleast_1d(np.asarray(density, dtype=np.float64))
+    tmat = np.zeros(tets.shape[0], dtype=np.int64) if tet_material is None else np.asarray(tet_material, np.int64)
+    P = Problem(X=X, tets=tets, clamped=np.asarray(clamped).astype(bool), mat=mats[0],
+                density=float(dens[0]), h=float(h), gravity=np.asarray(gravity, dtype=np.float64))
+    P.mats, P.tmat = mats, tmat
     # rest shape matrices Dm = [X1-X0, X2-X0, X3-X0] (columns), volume det(Dm)/6
     Dm = np.stack([X[tets[:, 1]] - X[tets[:, 0]], X[tets[:, 2]] - X[tets[:, 0]],
                    X[tets[:, 3]] - X[tets[:, 0]]], axis=-1)
@@ -349,9 +361,11 @@ def build_problem(X, tets, clamped, mat: VLMaterial, density, h, gravity,
     # lumped mass: a quarter of each incident tet's mass
     mass = np.zeros(P.n)
     for c in range(4):
-        np.add.at(mass, tets[:, c], 0.25 * density * P.vol)
+        np.add.at(mass, tets[:, c], 0.25 * dens[tmat] * P.vol)
     P.mass = mass
-    P.k = stiffness_k(mat, x_start, x_end)
+    ks = np.array([stiffness_k(m, x_start, x_end) for m in mats])
+    P.k = float(ks[0])
+    P.k_tet = ks[tmat]
     P.free = np.flatnonzero(~P.clamped)
     P.A = assemble_A(P)
     P.colliders = tuple(colliders)
@@ -360,9 +374,10 @@ def build_problem(X, tets, clamped, mat: VLMaterial, density, h, gravity,
 
 
 def laplacian(P: Problem, weights=None):
-    """L = sum_t w_t G_t^T G_t (n x n), w_t = V_t k (Eq. PDmatrixForm).
+    """L = sum_t w_t G_t^T G_t (n x n), w_t = V_t k_t (Eq. PDmatrixForm), k_t
+    the stiffness of tet t's material.
     G_t maps positions to Dm^{-T} [x1-x0; x2-x0; x3-x0]."""
-    w = P.vol * P.k if weights is None else weights
+    w = P.vol * P.k_tet if weights is None else weights
     B = np.array([[-1.0, 1.0, 0.0, 0.0], [-1.0, 0.0, 1.0, 0.0], [-1.0, 0.0, 0.0, 1.0]])
     # G_t = Dm^{-T} B  (3 x 4 on the tet's vertices)
     G = np.einsum("tji,jk->tik", P.Dm_inv, B)
@@ -434,22 +449,32 @@ def deformation_gradients(P: Problem, x):
     return Ds @ P.Dm_inv
 
 
-def fiber_stretch(P: Problem, F):
+def fiber_stretch(mat: VLMaterial, F):
     """F d and |F d| for the material's fibre direction d (Sec. 4.4)."""
-    d = np.asarray(P.mat.fiber, dtype=np.float64)
+    d = np.asarray(mat.fiber, dtype=np.float64)
     Fd = F @ d
     return Fd, np.linalg.norm(Fd, axis=1)
 
 
+def material_groups(P: Problem):
+    """(material, boolean mask of its tets) for every material of the mesh."""
+    if len(P.mats) <= 1:
+        return [(P.mat, slice(None))]
+    return [(m, P.tmat == i) for i, m in enumerate(P.mats)]
+
+
 def elastic_energy_per_tet(P: Problem, x):
     """V (Psi(s) + kappa/2 (|F d| - 1)^2): the Valanis-Landel energy of the
-    stretches plus the anisotropic fibre term of Sec. 4.4 (kappa = 0: none)."""
+    stretches plus the anisotropic fibre term of Sec. 4.4 (kappa = 0: none),
+    each tet with its own material."""
     F = deformation_gradients(P, x)
     _, s, _ = signed_svd(F)
-    e = psi(P.mat, s)
-    if P.mat.kappa:
-        _, nrm = fiber_stretch(P, F)
-        e = e + 0.5 * P.mat.kappa * (nrm - 1.0) ** 2
+    e = np.zeros(P.tets.shape[0])
+    for mat, sel in material_groups(P):
+        e[sel] = psi(mat, s[sel])
+        if mat.kappa:
+            _, nrm = fiber_stretch(mat, F[sel])
+            e[sel] = e[sel] + 0.5 * mat.kappa * (nrm - 1.0) ** 2
     return P.vol * e
 
 
@@ -459,13 +484,16 @@ def elastic_corner_gradients(P: Problem, x):
     corner 0 is minus their sum."""
     F = deformation_gradients(P, x)
     U, s, V = signed_svd(F)
-    tau = dpsi(P.mat, s)
+    tau = np.zeros_like(s)
+    for mat, sel in material_groups(P):
+        tau[sel] = dpsi(mat, s[sel])
     Pk = U @ (tau[:, :, None] * np.swapaxes(V, -1, -2))
-    if P.mat.kappa:
-        # d/dF kappa/2 (|F d| - 1)^2 = kappa (|F d| - 1) (F d / |F d|) d^T
-        d = np.asarray(P.mat.fiber, dtype=np.float64)
-        Fd, nrm = fiber_stretch(P, F)
-        Pk = Pk + (P.mat.kappa * (nrm - 1.0) / nrm)[:, None, None] * (Fd[:, :, None] * d[None, None, :])
+    for mat, sel in material_groups(P):
+        if mat.kappa:
+            # d/dF kappa/2 (|F d| - 1)^2 = kappa (|F d| - 1) (F d / |F d|) d^T
+            d = np.asarray(mat.fiber, dtype=np.float64)
+            Fd, nrm = fiber_stretch(mat, F[sel])
+            Pk[sel] = Pk[sel] + (mat.kappa * (nrm - 1.0) / nrm)[:, None, None] * (Fd[:, :, None] * d[None, None, :])
     H = P.vol[:, None, None] * (Pk @ np.swapaxes(P.Dm_inv, -1, -2))
     out = np.zeros((P.tets.shape[0], 4, 3))
     out[:, 1:, :] = np.swapaxes(H, -1, -2)
@@ -739,13 +767,22 @@ def newton_minimise(P: Problem, q_cur, q_prev, tol=1e-11, max_iter=100, fd_eps=1
 # Convenience: build from a workload-like object.
 # ----------------------------------------------------------------------------
 
-def problem_from_workload(w, x_start=0.5, x_end=1.5) -> Problem:
-    m = w.material
+def _material_of(m):
     mat = make_material(m.kind, m.E, m.nu, m.spline)
     kappa = float(getattr(m, "kappa", 0.0))
     if kappa:
         d = np.asarray(m.fiber, dtype=np.float64)
         mat.fiber, mat.kappa = d / np.linalg.norm(d), kappa
+    return mat
+
+
+def problem_from_workload(w, x_start=0.5, x_end=1.5) -> Problem:
     cols = tuple(c.as_tuple() for c in getattr(w, "colliders", ()))
-    return build_problem(w.rest_pos, w.tets, w.clamped, mat, m.density, w.h, w.gravity,
-                         x_start, x_end, colliders=cols, contact_scale=getattr(w, "contact_scale", 100.0))
+    extra = tuple(getattr(w, "extra_materials", ()))
+    ms = (w.material,) + extra
+    mats = [_material_of(m) for m in ms]
+    tmat = getattr(w, "tet_material", None) if extra else None
+    return build_problem(w.rest_pos, w.tets, w.clamped, mats if extra else mats[0],
+                         [m.density for m in ms] if extra else w.material.density, w.h, w.gravity,
+                         x_start, x_end, colliders=cols, contact_scale=getattr(w, "contact_scale", 100.0),
+                         tet_material=tmat)

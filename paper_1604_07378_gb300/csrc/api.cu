@@ -55,6 +55,7 @@ struct SimBase {
     virtual int step(int nsteps, hqn_step_stats *stats) = 0;
     virtual int stats_of(int idx, hqn_step_stats *stats) = 0;
     virtual int energy_grad(const double *x, const double *y, double *g, double *grad) = 0;
+    virtual int energy_grad_device(const double *x, const double *y, double *g, double *grad) = 0;
     virtual int solve_A0(const double *q, double *r) = 0;
     virtual int direction(const double *grad, int np, const double *s, const double *t, double *d) = 0;
     virtual void info(hqn_info *out) const = 0;
@@ -88,6 +89,7 @@ struct Sim final : SimBase {
     std::vector<int> pf_ptr;  // L2 prefetch spans of each launch of a solve
     V4<R> *hbuf = nullptr;  // pinned staging buffer of the state transfers (largest simulation)
     const int *d_perm0 = nullptr;  // simulation 0's caller ids by internal vertex (sim_positions_device)
+    const double *d_X0 = nullptr;  // simulation 0's float64 rest positions, internal order (device evaluation)
     V4<R> *d_pos0 = nullptr;       // its positions in caller order, borrowed by the caller
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -1023,6 +1025,26 @@ struct Sim final : SimBase {
         return HQN_OK;
     }
 
+    // g and grad g at caller-order device positions (simulation 0): the
+    // conversions to and from the internal order run on the device.
+    int energy_grad_device(const double *x, const double *y, double *g, double *grad) override {
+        const Setup &s0 = S[0];
+        int rc;
+        if (!d_perm0 && (rc = upload(d_perm0, s0.perm.data(), (size_t)s0.n))) return rc;
+        if (!d_X0 && (rc = upload(d_X0, s0.X.data(), s0.X.size()))) return rc;
+        launch_from_caller<R>(d_X0, x, d_perm0, hdesc[0].v0, s0.n, ds.xt, st);
+        launch_from_caller<R>(d_X0, y, d_perm0, hdesc[0].v0, s0.n, ds.y, st);
+        const CondHandles none{0, 0, 0};
+        launch_inertia(ds, st);
+        launch_tet(ds, TET_EVAL, none, st);
+        launch_gather(ds, G_EVAL, none, st);
+        if (grad) launch_to_caller<R>(ds.gk, d_perm0, hdesc[0].v0, s0.n, s0.n_free, grad, st);
+        CK(cudaGetLastError());
+        if ((rc = read_ctl())) return rc;
+        if (g) *g = h_ctl[0].g_trial;
+        return HQN_OK;
+    }
+
     int solve_A0(const double *q, double *r) override {
         int rc;
         if ((rc = put_vec(0, ds.q, q, false, true))) return rc;
@@ -1350,6 +1372,12 @@ int sim_step(sim_handle *sim, int32_t nsteps, hqn_step_stats *stats) {
 int sim_energy_grad(sim_handle *sim, const double *x, const double *y, double *g_out, double *grad_out) {
     if (!sim || !x || !y) return fail(HQN_ERR_ARG, "null argument");
     try { return sim->impl->energy_grad(x, y, g_out, grad_out); } catch (...) { return fail(HQN_ERR_NO_MEMORY, "exception"); }
+}
+
+int sim_energy_grad_device(sim_handle *sim, const double *x_dev, const double *y_dev, double *g_out,
+                           double *grad_dev) {
+    if (!sim || !x_dev || !y_dev) return fail(HQN_ERR_ARG, "null argument");
+    return sim->impl->energy_grad_device(x_dev, y_dev, g_out, grad_dev);
 }
 
 int sim_solve_A0(sim_handle *sim, const double *q, double *r) {

@@ -1077,6 +1077,41 @@ __global__ void __launch_bounds__(VBS) k_positions(const V4<R> *rest, const V4<R
     }
 }
 
+// Caller-order float64 positions (n x 3, device) -> internal displacements
+// u = x - X, with X the float64 rest positions in internal order (vertex i
+// of the internal order is caller vertex perm[i]); subtracted in float64 and
+// rounded once, as the host-side transfers do.
+template <typename R>
+__global__ void __launch_bounds__(VBS) k_from_caller(const double *X, const double *src, const int *perm, int v0,
+                                                    int n, V4<R> *dst) {
+    const int i = blockIdx.x * VBS + threadIdx.x;
+    if (i < n) {
+        const int v = perm[i];
+        V4<R> o;
+        o.x = (R)(src[3 * (size_t)v] - X[3 * (size_t)i]);
+        o.y = (R)(src[3 * (size_t)v + 1] - X[3 * (size_t)i + 1]);
+        o.z = (R)(src[3 * (size_t)v + 2] - X[3 * (size_t)i + 2]);
+        o.w = R(0);
+        dst[v0 + i] = o;
+    }
+}
+
+// Internal vectors -> caller-order float64 (n x 3, device); rows of clamped
+// vertices (internal index >= nf) are zero.
+template <typename R>
+__global__ void __launch_bounds__(VBS) k_to_caller(const V4<R> *src, const int *perm, int v0, int n, int nf,
+                                                  double *dst) {
+    const int i = blockIdx.x * VBS + threadIdx.x;
+    if (i < n) {
+        const int v = perm[i];
+        const V4<R> a = src[v0 + i];
+        const bool fixed = i >= nf;
+        dst[3 * (size_t)v] = fixed ? 0.0 : (double)a.x;
+        dst[3 * (size_t)v + 1] = fixed ? 0.0 : (double)a.y;
+        dst[3 * (size_t)v + 2] = fixed ? 0.0 : (double)a.z;
+    }
+}
+
 // Caller-given history of simulation 0 (sim_direction): row `a` of the Gram
 // matrix, s_a^T t_b for the slots b < count, rho_a = s_a^T t_a and
 // s_a^T grad.  With a == count - 1 the last block also runs the first loop
@@ -1198,6 +1233,14 @@ template <typename R> void launch_positions(const DevSim<R> &s, const int *perm,
                                             cudaStream_t st) {
     if (n > 0) k_positions<R><<<(n + VBS - 1) / VBS, VBS, 0, st>>>(s.rest, s.u_cur, perm, v0, n, out);
 }
+template <typename R> void launch_from_caller(const double *X, const double *src, const int *perm, int v0, int n,
+                                              V4<R> *dst, cudaStream_t st) {
+    if (n > 0) k_from_caller<R><<<(n + VBS - 1) / VBS, VBS, 0, st>>>(X, src, perm, v0, n, dst);
+}
+template <typename R> void launch_to_caller(const V4<R> *src, const int *perm, int v0, int n, int nf, double *dst,
+                                            cudaStream_t st) {
+    if (n > 0) k_to_caller<R><<<(n + VBS - 1) / VBS, VBS, 0, st>>>(src, perm, v0, n, nf, dst);
+}
 template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream_t st, int nblocks) {
     k_hist_row<R><<<nblocks, VBS, 0, st>>>(s, a);
 }
@@ -1215,7 +1258,9 @@ template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream
     template void launch_commit<R>(const DevSim<R> &, cudaStream_t);                 \
     template void launch_pcg<R>(const DevSim<R> &, const V4<R> *, V4<R> *, int, cudaStream_t); \
     template void launch_hist_row<R>(const DevSim<R> &, int, cudaStream_t, int);       \
-    template void launch_positions<R>(const DevSim<R> &, const int *, int, int, V4<R> *, cudaStream_t);
+    template void launch_positions<R>(const DevSim<R> &, const int *, int, int, V4<R> *, cudaStream_t); \
+    template void launch_from_caller<R>(const double *, const double *, const int *, int, int, V4<R> *, cudaStream_t); \
+    template void launch_to_caller<R>(const V4<R> *, const int *, int, int, int, double *, cudaStream_t);
 
 HQN_INST(float)
 HQN_INST(double)

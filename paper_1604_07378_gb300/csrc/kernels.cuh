@@ -92,6 +92,13 @@ template <typename R> void launch_commit(const DevSim<R> &s, cudaStream_t st);
 // out[perm[i]] = X + u_cur of the n vertices from batch vertex v0 (caller order).
 template <typename R> void launch_positions(const DevSim<R> &s, const int *perm, int v0, int n, V4<R> *out,
                                             cudaStream_t st);
+// Caller-order float64 vectors (device, n x 3) <-> internal V4 vectors of the
+// n vertices from batch vertex v0: displacements from the float64 rest
+// positions X (internal order), and back with clamped rows (>= nf) zero.
+template <typename R> void launch_from_caller(const double *X, const double *src, const int *perm, int v0, int n,
+                                              V4<R> *dst, cudaStream_t st);
+template <typename R> void launch_to_caller(const V4<R> *src, const int *perm, int v0, int n, int nf, double *dst,
+                                            cudaStream_t st);
 // Caller-given history of simulation 0: Gram row a, rho_a and s_a^T grad
 // (run for a = 0..count-1).
 template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream_t st, int nblocks);

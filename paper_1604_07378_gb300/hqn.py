@@ -123,6 +123,8 @@ def library(path: str | None = None):
     lib.sim_step.argtypes = [C.c_void_p, C.c_int32, C.POINTER(StepStats)]
     lib.sim_energy_grad.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
     lib.sim_solve_A0.argtypes = [C.c_void_p, _dp, _dp]
+    lib.sim_energy_grad_device.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, _dp, C.c_void_p]
+    lib.sim_energy_grad_device.restype = C.c_int
     lib.sim_direction.argtypes = [C.c_void_p, _dp, C.c_int32, _dp, _dp, _dp]
     lib.sim_get_info.argtypes = [C.c_void_p, C.POINTER(Info)]
     lib.hqn_measure_peak.argtypes = [C.c_int32, _dp]
@@ -336,6 +338,21 @@ class Sim:
         grad = np.empty((self.n, 3))
         _check(library().sim_energy_grad(self._h, _ptr(x), _ptr(y), C.byref(g), _ptr(grad)),
                "sim_energy_grad")
+        return g.value, grad
+
+    def energy_grad_device(self, x, y, grad=None):
+        """``sim_energy_grad_device``: x, y are torch float64 CUDA tensors
+        (n x 3, caller order); returns (g, grad) with grad a torch tensor on
+        the same device (the given one if passed)."""
+        import torch
+        for t in (x, y):
+            if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and tuple(t.shape) == (self.n, 3)):
+                raise ValueError("expected contiguous float64 CUDA tensors of shape (n, 3)")
+        if grad is None:
+            grad = torch.empty_like(x)
+        g = C.c_double()
+        _check(library().sim_energy_grad_device(self._h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                                C.byref(g), C.c_void_p(grad.data_ptr())), "sim_energy_grad_device")
         return g.value, grad
 
     def solve_A0(self, q):

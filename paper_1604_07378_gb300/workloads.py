@@ -84,6 +84,10 @@ class Workload:
     meta: dict = field(default_factory=dict)
     colliders: tuple = ()         # Collider instances
     contact_scale: float = 100.0  # collision weight w_v = contact_scale * m_v / h^2
+    # several materials in one mesh: `material` is material 0, these follow it,
+    # and tet_material[t] is tet t's index into (material,) + extra_materials
+    extra_materials: tuple = ()
+    tet_material: np.ndarray | None = None
 
     @property
     def n_verts(self) -> int:
@@ -340,3 +344,14 @@ def large_48x48x192() -> Workload:
     return lattice_workload((48, 48, 192), Material(NEOHOOKEAN, 5e5, 0.4), clamp_axis=2,
                             seed=1608, v_range=0.5, v_mode="body", iters=20, history=8,
                             name="bar48x48x192_nh")
+
+
+def two_material_bar(dims, mat_a: Material, mat_b: Material, *, seed: int = 0, v_range: float = 0.0,
+                     v_mode: str = "body", name: str = "two_material") -> Workload:
+    """A Kuhn lattice (z = 0 face clamped) whose tets with centroid x below
+    half the bar's length take mat_a and the others mat_b."""
+    w = lattice_workload(dims, mat_a, seed=seed, v_range=v_range, v_mode=v_mode, name=name)
+    cx = w.rest_pos[w.tets].mean(axis=1)[:, 0]
+    w.extra_materials = (mat_b,)
+    w.tet_material = (cx >= 0.5 * dims[0] * 0.05).astype(np.int32)
+    return w

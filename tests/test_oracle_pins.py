@@ -792,3 +792,63 @@ def test_line_search_exhaustion_keeps_x_k_and_ends_the_step():
     x2, st2 = O.solve_step(P, w.q_cur, w.q_prev, iters=10, m=5, ls_max=2)
     assert not st2.exhausted and st2.trials == st_full.trials
     np.testing.assert_array_equal(x2, its_full[-1])
+
+
+# ---------------------------------------------------------------- several materials in one mesh
+
+def _submesh_problem(w, mat, sel):
+    """The same vertices with only the tets `sel`, all of material `mat`."""
+    return O.build_problem(w.rest_pos, w.tets[sel], w.clamped, O._material_of(mat), mat.density, w.h, w.gravity)
+
+
+def test_two_materials_are_the_sum_of_their_parts():
+    """Eq. PD's energy and L are sums over elements, each with its own
+    material: on a bar of Neo-Hookean and StVK halves (different densities),
+    the elastic energy, its gradient, the lumped mass and L equal those of
+    the two single-material halves added up (independently built
+    problems); with both materials equal the mesh is the one-material mesh."""
+    a = W.Material(W.NEOHOOKEAN, 2e5, 0.4, density=900.0)
+    b = W.Material(W.STVK, 6e5, 0.35, density=1300.0)
+    w = W.two_material_bar((4, 2, 3), a, b, seed=3, v_range=0.2)
+    P = O.problem_from_workload(w)
+    assert set(np.unique(P.tmat)) == {0, 1} and P.k_tet.min() < P.k_tet.max()
+    P0 = _submesh_problem(w, a, w.tet_material == 0)
+    P1 = _submesh_problem(w, b, w.tet_material == 1)
+    rng = np.random.default_rng(8)
+    x = w.q_cur + 3e-3 * rng.normal(size=w.q_cur.shape)
+    e = O.elastic_energy_per_tet(P, x)
+    assert abs(e.sum() - (O.elastic_energy_per_tet(P0, x).sum() + O.elastic_energy_per_tet(P1, x).sum())) \
+        <= 1e-12 * abs(e.sum())
+    np.testing.assert_allclose(P.mass, P0.mass + P1.mass, rtol=1e-14)
+    y = w.q_cur.copy()
+    # the inertia term splits with the mass: g = g_0 + g_1
+    g = O.gradient(P, x, y)
+    np.testing.assert_allclose(g, O.gradient(P0, x, y) + O.gradient(P1, x, y), rtol=1e-10,
+                               atol=1e-12 * np.abs(g).max())
+    assert abs(O.objective(P, x, y) - O.objective(P0, x, y) - O.objective(P1, x, y)) <= 1e-12 * O.objective(P, x, y)
+    Lsum = (O.laplacian(P0) + O.laplacian(P1)).toarray()
+    np.testing.assert_allclose(O.laplacian(P).toarray(), Lsum, rtol=1e-12, atol=1e-12 * np.abs(Lsum).max())
+    # both halves of one material: the one-material mesh, bit for bit
+    w2 = W.two_material_bar((4, 2, 3), a, a, seed=3, v_range=0.2)
+    Pa, Pone = O.problem_from_workload(w2), _submesh_problem(w2, a, slice(None))
+    np.testing.assert_array_equal(O.gradient(Pa, x, y), O.gradient(Pone, x, y))
+    assert O.objective(Pa, x, y) == O.objective(Pone, x, y)
+
+
+def test_two_materials_gradient_matches_central_differences():
+    a = W.Material(W.NEOHOOKEAN, 2e5, 0.4, density=900.0)
+    b = W.Material(W.COROTATED, 6e5, 0.35, density=1300.0)
+    w = W.two_material_bar((3, 2, 2), a, b, seed=4)
+    P = O.problem_from_workload(w)
+    rng = np.random.default_rng(2)
+    x = w.q_cur + 4e-3 * rng.normal(size=w.q_cur.shape)
+    y = w.q_cur + 1e-3 * rng.normal(size=w.q_cur.shape)
+    g = O.gradient(P, x, y)
+    eps = 1e-6
+    for v in P.free[::3]:
+        for c in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[v, c] += eps
+            xm[v, c] -= eps
+            fd = (O.objective(P, xp, y) - O.objective(P, xm, y)) / (2 * eps)
+            assert abs(fd - g[v, c]) <= 1e-6 * max(1.0, abs(g[v, c])), (v, c, fd, g[v, c])
