@@ -98,7 +98,16 @@ typedef struct {
     const int32_t *tets;      /* n_tets x 4 vertex indices; det[X1-X0,X2-X0,X3-X0] > 0 */
     const uint8_t *clamped;   /* n_verts flags, nonzero = position prescribed (held
                                  at its current state); NULL = none clamped          */
+    /* Several materials in one mesh.  The energy of Eq. PD is a sum over
+     * elements, so each tet may have its own material: its energy density,
+     * its share of the lumped mass (that material's density) and its weight
+     * V k in L (k of Eq. stiffness fitted per material) are its material's.
+     * n_materials = 0 or 1: every tet has material 0 and tet_material is
+     * ignored (may be NULL). */
+    int32_t        n_materials;  /* 0 .. HQN_MAX_MATERIALS                          */
+    const int32_t *tet_material; /* n_tets indices in [0, n_materials)              */
 } hqn_mesh;
+#define HQN_MAX_MATERIALS 16
 
 typedef struct {
     int32_t       kind;       /* hqn_material_kind                                    */
@@ -302,8 +311,9 @@ int hqn_analyse(const hqn_mesh *mesh, const hqn_material *material,
  * of Eq. stiffness, A0 = M/h^2 + sum_t V_t k G_t^T G_t on the free vertices
  * (Eq. PDmatrixForm, PDsolution), its nested-dissection ordering and float64
  * supernodal Cholesky factor, and the device operators of the triangular
- * solves.  The state starts at rest (q_l = q_{l-1} = X).  `stream` is a
- * cudaStream_t (NULL = legacy default stream).
+ * solves.  `material` points to max(1, mesh->n_materials) materials.  The
+ * state starts at rest (q_l = q_{l-1} = X).  `stream` is a cudaStream_t
+ * (NULL = legacy default stream).
  * Errors: HQN_ERR_ARG, HQN_ERR_DEGENERATE_TET, HQN_ERR_NONFINITE,
  * HQN_ERR_NOT_SPD, HQN_ERR_CUDA, HQN_ERR_NO_MEMORY.  *out is NULL on error. */
 int sim_create(const hqn_mesh *mesh, const hqn_material *material,
@@ -317,8 +327,9 @@ int sim_create(const hqn_mesh *mesh, const hqn_material *material,
  * simulation takes exactly the iterations and line-search trials it would
  * take alone (a finished simulation idles while others continue), so its
  * results equal those of a handle made by sim_create for it alone.
- * meshes and materials are arrays of `count`.  Errors as sim_create; a
- * failing simulation is named in hqn_last_error().
+ * meshes is an array of `count`; materials holds the meshes' material arrays
+ * back to back (max(1, n_materials) of them per mesh, in mesh order).
+ * Errors as sim_create; a failing simulation is named in hqn_last_error().
  * For a batch handle, sim_set_state, sim_get_state, sim_energy_grad,
  * sim_solve_A0 and sim_direction act on simulation 0; sim_step advances all
  * simulations and its stats carry simulation 0's per-iteration record with

@@ -224,6 +224,18 @@ struct Sim final : SimBase {
             const V4<R> *p_rest;
             if ((rc = upload(p_rest, rest.data(), rest.size()))) return rc;
             ds.rest = p_rest;
+            // per-tet material indices, only when some mesh has several materials
+            bool several = false;
+            for (const Setup &q : S) several = several || q.mats.size() > 1;
+            ds.tmat = nullptr;
+            if (several) {
+                std::vector<uint8_t> tm(T, 0);
+                for (int k = 0; k < ns; ++k)
+                    for (int t = 0; t < S[k].T; ++t) tm[t0[k] + t] = S[k].tmat[t];
+                const uint8_t *p_tm;
+                if ((rc = upload(p_tm, tm.data(), tm.size()))) return rc;
+                ds.tmat = p_tm;
+            }
             ds.tets = p_t; ds.dminv = p_dm; ds.vol = p_vol; ds.mh2 = p_mh2; ds.vt_ptr = p_ptr; ds.corner_pos = p_pos;
         }
         // ---- vectors, rings, partials, control blocks
@@ -294,6 +306,21 @@ struct Sim final : SimBase {
                 dc.ring = hc.kind == HQN_COLLIDER_TORUS ? (R)hc.major_radius : R(0);
             }
             matdev_from_host(s.mat, D.mat);
+            D.n_mats = (int)s.mats.size();
+            if (D.n_mats > 1) {
+                std::vector<MatDev<R>> md(D.n_mats);
+                std::vector<R> km(D.n_mats);
+                for (int m = 0; m < D.n_mats; ++m) {
+                    matdev_from_host(s.mats[m], md[m]);
+                    km[m] = (R)s.kmat[m];
+                }
+                const MatDev<R> *p_md;
+                const R *p_km;
+                if ((rc = upload(p_md, md.data(), md.size()))) return rc;
+                if ((rc = upload(p_km, km.data(), km.size()))) return rc;
+                D.mats = p_md;
+                D.kmat = p_km;
+            }
             D.v0 = v0[k]; D.t0 = t0[k];
             D.vb0 = vb0[k]; D.nvb = (s.n + VBS - 1) / VBS;
             D.tb0 = tb0[k]; D.ntb = (s.T + TBS - 1) / TBS;
@@ -1143,8 +1170,10 @@ int make_batch(int count, const hqn_mesh *meshes, const hqn_material *materials,
     b->S.resize(count);
     std::vector<int> rcs(count, HQN_OK);
     std::vector<std::string> errs(count);
+    std::vector<int> moff(count + 1, 0);  // first material of each mesh
+    for (int k = 0; k < count; ++k) moff[k + 1] = moff[k] + std::max(1, (int)meshes[k].n_materials);
 #pragma omp parallel for schedule(dynamic, 1) if (count > 1)
-    for (int k = 0; k < count; ++k) rcs[k] = build_setup(meshes[k], materials[k], prm, b->S[k], errs[k]);
+    for (int k = 0; k < count; ++k) rcs[k] = build_setup(meshes[k], materials + moff[k], prm, b->S[k], errs[k]);
     for (int k = 0; k < count; ++k)
         if (rcs[k] != HQN_OK)
             return fail(rcs[k], count > 1 ? "simulation " + std::to_string(k) + ": " + errs[k] : errs[k]);
@@ -1403,7 +1432,7 @@ int hqn_analyse(const hqn_mesh *mesh, const hqn_material *material, const hqn_pa
     try {
         Setup S;
         std::string err;
-        const int rc = build_setup(*mesh, *material, *params, S, err);
+        const int rc = build_setup(*mesh, material, *params, S, err);
         if (rc != HQN_OK) return fail(rc, err);
         info->n_verts = S.n;
         info->n_tets = S.T;

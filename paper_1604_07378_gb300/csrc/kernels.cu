@@ -292,8 +292,14 @@ __global__ void __launch_bounds__(TBS, 8) k_tet(DevSim<R> s, int mode, CondHandl
         def_grad(du, Di, G);
         const R vol = s.vol[t];
         R g[4][3];
-        tet_grad(D.mat, G, Di, vol, g);
-        if (!grad_mode) e[0] = A::add(e[0], vol * tet_psi(D.mat, G));
+        // the tet's material: the simulation's only one, or its own from the
+        // mesh's table (one branch per tet, uniform for one-material meshes)
+        auto eval = [&](const MatDev<R> &M) {
+            tet_grad(M, G, Di, vol, g);
+            if (!grad_mode) e[0] = A::add(e[0], vol * tet_psi(M, G));
+        };
+        if (D.n_mats > 1) eval(D.mats[s.tmat[t]]);
+        else eval(D.mat);
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             V4<R> o;
@@ -384,14 +390,18 @@ __global__ void __launch_bounds__(TBS) k_ls(DevSim<R> s, CondHandles h) {
         def_grad(Duk, Di, Gk);
         def_grad(Dd, Di, Gd);
         const R vol = s.vol[t];
-        PsiRay<R> ray;
-        psi_ray_setup(D.mat, Gk, Gd, ray);
-        double a = a0;
+        auto eval = [&](const MatDev<R> &M) {
+            PsiRay<R> ray;
+            psi_ray_setup(M, Gk, Gd, ray);
+            double a = a0;
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            e[j] = A::add(e[j], vol * psi_ray_eval(D.mat, ray, (R)a));
-            a *= bt;
-        }
+            for (int j = 0; j < K; ++j) {
+                e[j] = A::add(e[j], vol * psi_ray_eval(M, ray, (R)a));
+                a *= bt;
+            }
+        };
+        if (D.n_mats > 1) eval(D.mats[s.tmat[t]]);
+        else eval(D.mat);
     }
     double tot[K];
     block_sum_exact<TBS, K, R>(e, tot);
@@ -947,7 +957,7 @@ __global__ void __launch_bounds__(TBS, 8) k_pcg_tet(DevSim<R> s) {
     edge_diffs(p0, p1, p2, p3, du);
     load_dm(s, t, Di);
     def_grad(du, Di, G);
-    const R w = s.vol[t] * D.c.kstiff;
+    const R w = s.vol[t] * (D.n_mats > 1 ? D.kmat[s.tmat[t]] : D.c.kstiff);
     R g[4][3];
 #pragma unroll
     for (int j = 0; j < 3; ++j)

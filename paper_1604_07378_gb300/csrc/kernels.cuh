@@ -15,7 +15,10 @@ constexpr int TBS = 128;  // threads per block of the tet kernels
 template <typename R>
 struct SimDesc {
     StepConst<R> c;             // n, nf, T, history m, iterations, ... of this simulation
-    MatDev<R> mat;
+    MatDev<R> mat;              // material 0
+    int n_mats;                 // materials of the mesh (> 1: by tet, DevSim::tmat)
+    const MatDev<R> *mats;      // n_mats materials (device) when n_mats > 1
+    const R *kmat;              // their stiffness k (the matrix-free A0 of the PCG solve)
     int v0, t0;                 // its first vertex / tet in the batch arrays
     int vb0, nvb;               // its vertex-kernel blocks [vb0, vb0 + nvb), nvb = ceil(n / VBS)
     int tb0, ntb;               // its tet-kernel blocks [tb0, tb0 + ntb), ntb = ceil(T / TBS)
@@ -38,6 +41,7 @@ struct DevSim {
     const int4 *tets;           // Tn, batch vertex ids
     const R *dminv;             // 9 x Tn (SoA), Dm^{-1}[j][b] at (3j + b) * Tn + t
     const R *vol;               // Tn
+    const uint8_t *tmat;        // Tn material indices (null when every simulation has one material)
     const R *mh2;               // batch vertices: m_v / h^2
     const V4<R> *rest;          // batch vertices: rest positions X (collision terms)
     const int *vt_ptr;          // batch vertices + 1

@@ -612,7 +612,7 @@ int plan_sweeps(Setup &S, const hqn_params &prm, std::string &err) {
     return HQN_OK;
 }
 
-int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_params &prm,
+int build_setup(const hqn_mesh &mesh, const hqn_material *mats_in, const hqn_params &prm,
                 Setup &S, std::string &err) {
     auto t_start = std::chrono::steady_clock::now();
     const int n = mesh.n_verts, T = mesh.n_tets;
@@ -636,19 +636,43 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
             err = "tet vertex index out of range";
             return HQN_ERR_ARG;
         }
-    if (!(matin.density > 0) || !std::isfinite(matin.E) || !std::isfinite(matin.nu)) {
-        err = "material density must be positive and E, nu finite";
-        return matin.density <= 0 ? HQN_ERR_NOT_SPD : HQN_ERR_NONFINITE;
+    // ---- materials: one, or one per index of mesh.tet_material
+    const int nmat = mesh.n_materials > 0 ? mesh.n_materials : 1;
+    if (!mats_in || nmat > HQN_MAX_MATERIALS || (nmat > 1 && !mesh.tet_material)) {
+        err = "need 1..HQN_MAX_MATERIALS materials (and tet_material for more than one)";
+        return HQN_ERR_ARG;
     }
-    MaterialHost &M = S.mat;
-    if (int rc = material_from_api(matin, M, err)) return rc;
-    S.k = fit_stiffness(M, prm.x_start, prm.x_end);
-    if (!(S.k > 0) || !std::isfinite(S.k)) {
-        err = "stiffness fit is not positive";
-        return HQN_ERR_NOT_SPD;
+    S.mats.assign(nmat, MaterialHost{});
+    S.kmat.assign(nmat, 0.0);
+    S.dens.assign(nmat, 0.0);
+    for (int m = 0; m < nmat; ++m) {
+        const hqn_material &matin = mats_in[m];
+        if (!(matin.density > 0) || !std::isfinite(matin.E) || !std::isfinite(matin.nu)) {
+            err = "material density must be positive and E, nu finite";
+            return matin.density <= 0 ? HQN_ERR_NOT_SPD : HQN_ERR_NONFINITE;
+        }
+        if (int rc = material_from_api(matin, S.mats[m], err)) return rc;
+        S.kmat[m] = fit_stiffness(S.mats[m], prm.x_start, prm.x_end);
+        if (!(S.kmat[m] > 0) || !std::isfinite(S.kmat[m])) {
+            err = "stiffness fit is not positive";
+            return HQN_ERR_NOT_SPD;
+        }
+        S.dens[m] = matin.density;
     }
+    std::vector<uint8_t> tmat0(T, 0);
+    if (nmat > 1)
+        for (int t = 0; t < T; ++t) {
+            const int m = mesh.tet_material[t];
+            if (m < 0 || m >= nmat) {
+                err = "tet_material index out of range";
+                return HQN_ERR_ARG;
+            }
+            tmat0[t] = (uint8_t)m;
+        }
+    S.mat = S.mats[0];
+    S.k = S.kmat[0];
     S.h = prm.h;
-    S.density = matin.density;
+    S.density = S.dens[0];
 
     // ---- rest data in caller order
     std::vector<double> dminv0((size_t)T * 9), vol0(T);
@@ -750,8 +774,10 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
     S.tets.resize(4 * (size_t)T);
     S.dminv.resize(9 * (size_t)T);
     S.vol.resize(T);
+    S.tmat.assign(T, 0);
     for (int i = 0; i < T; ++i) {
         const int t = torder[i];
+        S.tmat[i] = tmat0[t];
         for (int a = 0; a < 4; ++a) S.tets[4 * i + a] = S.iperm[mesh.tets[4 * t + a]];
         for (int e = 0; e < 9; ++e) S.dminv[9 * (size_t)i + e] = dminv0[9 * (size_t)t + e];
         S.vol[i] = vol0[t];
@@ -759,7 +785,7 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
     // lumped mass: a quarter of each incident tet's mass
     S.mass.assign(n, 0.0);
     for (int t = 0; t < T; ++t)
-        for (int a = 0; a < 4; ++a) S.mass[S.tets[4 * t + a]] += 0.25 * matin.density * S.vol[t];
+        for (int a = 0; a < 4; ++a) S.mass[S.tets[4 * t + a]] += 0.25 * S.dens[S.tmat[t]] * S.vol[t];
     // vertex -> corner slots, ascending tet
     S.vt_ptr.assign(n + 1, 0);
     for (int t = 0; t < T; ++t)
@@ -787,7 +813,7 @@ int build_setup(const hqn_mesh &mesh, const hqn_material &matin, const hqn_param
             }
             G[i][0] = -s;
         }
-        const double w = S.vol[t] * S.k;
+        const double w = S.vol[t] * S.kmat[S.tmat[t]];
         for (int a = 0; a < 4; ++a)
             for (int b = 0; b < 4; ++b) {
                 const int va = S.tets[4 * t + a], vb = S.tets[4 * t + b];

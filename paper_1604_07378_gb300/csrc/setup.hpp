@@ -59,7 +59,13 @@ struct ItemLists {
 struct Setup {
     int n = 0, T = 0, n_free = 0;
     double h = 1.0 / 30.0, k = 0.0, density = 0.0;
-    MaterialHost mat;
+    MaterialHost mat;                // material 0 (the only one unless the mesh has several)
+    // several materials in one mesh (hqn_mesh.tet_material): each tet's
+    // material index in the sorted tet order, the materials, their fitted k
+    // and densities (one entry each when the mesh has one material)
+    std::vector<uint8_t> tmat;
+    std::vector<MaterialHost> mats;
+    std::vector<double> kmat, dens;
     // vertex renumbering: perm[new] = caller's id; iperm[caller's id] = new.
     // Free vertices come first in elimination order, then the clamped ones.
     std::vector<int> perm, iperm;
@@ -103,7 +109,8 @@ struct Setup {
 int plan_sweeps(Setup &S, const hqn_params &prm, std::string &err);
 
 // Builds everything; returns an HQN_* status and a message on failure.
-int build_setup(const hqn_mesh &mesh, const hqn_material &mat, const hqn_params &prm,
+// mat points to max(1, mesh.n_materials) materials.
+int build_setup(const hqn_mesh &mesh, const hqn_material *mat, const hqn_params &prm,
                 Setup &S, std::string &err);
 
 // Lame parameters and the kernel form of an API material, checked

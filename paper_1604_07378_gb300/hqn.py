@@ -39,7 +39,10 @@ _up = C.POINTER(C.c_uint8)
 
 class Mesh(C.Structure):
     _fields_ = [("n_verts", C.c_int32), ("n_tets", C.c_int32), ("rest_pos", _dp),
-                ("tets", _ip), ("clamped", _up)]
+                ("tets", _ip), ("clamped", _up), ("n_materials", C.c_int32), ("tet_material", _ip)]
+
+
+MAX_MATERIALS = 16
 
 
 class Material(C.Structure):
@@ -218,19 +221,38 @@ def default_params(**kw) -> Params:
     return p
 
 
-class _MeshArgs:
-    """hqn_mesh and hqn_material views of caller arrays (kept alive here)."""
+def _material_struct(m, keep):
+    """hqn_material of a workloads.Material (its spline array kept in `keep`)."""
+    sp = None if m.spline is None else np.ascontiguousarray(m.spline, dtype=np.float64)
+    keep.append(sp)
+    return Material(m.kind, m.E, m.nu, m.density, None if sp is None else _ptr(sp),
+                    float(getattr(m, "kappa", 0.0)), (C.c_double * 3)(*getattr(m, "fiber", (0.0, 0.0, 0.0))))
 
-    def __init__(self, rest_pos, tets, clamped, kind, E, nu, density, spline, kappa, fiber):
+
+class _MeshArgs:
+    """hqn_mesh and hqn_material views of caller arrays (kept alive here).
+    extra_materials (workloads.Material) and tet_material: several materials
+    in the mesh, material 0 being the one given by kind, E, nu, ...."""
+
+    def __init__(self, rest_pos, tets, clamped, kind, E, nu, density, spline, kappa, fiber,
+                 extra_materials=(), tet_material=None):
         self.X = np.ascontiguousarray(rest_pos, dtype=np.float64)
         self.tets = np.ascontiguousarray(tets, dtype=np.int32)
         self.n = self.X.shape[0]
         self.cl = None if clamped is None else np.ascontiguousarray(clamped, dtype=np.uint8)
+        nm = 1 + len(extra_materials)
+        self.tm = None if nm == 1 else np.ascontiguousarray(tet_material, dtype=np.int32)
         self.mesh = Mesh(self.n, self.tets.shape[0], _ptr(self.X), _ptr(self.tets, _ip),
-                         None if self.cl is None else _ptr(self.cl, _up))
+                         None if self.cl is None else _ptr(self.cl, _up), nm,
+                         None if self.tm is None else _ptr(self.tm, _ip))
         self.spline = None if spline is None else np.ascontiguousarray(spline, dtype=np.float64)
-        self.mat = Material(kind, E, nu, density, None if self.spline is None else _ptr(self.spline),
-                            float(kappa), (C.c_double * 3)(*fiber))
+        self._keep = []
+        self.mats = (Material * nm)()
+        self.mats[0] = Material(kind, E, nu, density, None if self.spline is None else _ptr(self.spline),
+                                float(kappa), (C.c_double * 3)(*fiber))
+        for i, m in enumerate(extra_materials):
+            self.mats[1 + i] = _material_struct(m, self._keep)
+        self.mat = self.mats[0]
 
 
 def _workload_kwargs(w, pkw):
@@ -243,19 +265,25 @@ def _workload_kwargs(w, pkw):
     if getattr(w, "colliders", ()):
         pkw.setdefault("colliders", w.colliders)
         pkw.setdefault("contact_scale", w.contact_scale)
+    extra = tuple(getattr(w, "extra_materials", ()))
+    if extra:
+        pkw.setdefault("extra_materials", extra)
+        pkw.setdefault("tet_material", w.tet_material)
     return (w.rest_pos, w.tets, w.clamped), dict(kind=m.kind, E=m.E, nu=m.nu, density=m.density,
                                                  spline=m.spline, kappa=getattr(m, "kappa", 0.0),
                                                  fiber=getattr(m, "fiber", (0.0, 0.0, 0.0)), **pkw)
 
 
 def analyse(rest_pos, tets, clamped=None, *, kind=NEOHOOKEAN, E=1e5, nu=0.45, density=1000.0,
-            spline=None, kappa=0.0, fiber=(0.0, 0.0, 0.0), params: Params | None = None, **pkw) -> dict:
+            spline=None, kappa=0.0, fiber=(0.0, 0.0, 0.0), extra_materials=(), tet_material=None,
+            params: Params | None = None, **pkw) -> dict:
     """Host-only set-up statistics of one mesh (``hqn_analyse``; no GPU):
     the factor's supernodes, levels and entries, the fitted stiffness."""
-    a = _MeshArgs(rest_pos, tets, clamped, kind, E, nu, density, spline, kappa, fiber)
+    a = _MeshArgs(rest_pos, tets, clamped, kind, E, nu, density, spline, kappa, fiber, extra_materials,
+                  tet_material)
     p = params if params is not None else default_params(**pkw)
     i = Info()
-    _check(library().hqn_analyse(C.byref(a.mesh), C.byref(a.mat), C.byref(p), C.byref(i)), "hqn_analyse")
+    _check(library().hqn_analyse(C.byref(a.mesh), a.mats, C.byref(p), C.byref(i)), "hqn_analyse")
     return {f: getattr(i, f) for f, _ in Info._fields_}
 
 
@@ -268,14 +296,15 @@ class Sim:
     """One simulation handle (``sim_create`` ... ``sim_destroy``)."""
 
     def __init__(self, rest_pos, tets, clamped=None, *, kind=NEOHOOKEAN, E=1e5, nu=0.45,
-                 density=1000.0, spline=None, kappa=0.0, fiber=(0.0, 0.0, 0.0),
-                 params: Params | None = None, stream=None, **pkw):
+                 density=1000.0, spline=None, kappa=0.0, fiber=(0.0, 0.0, 0.0), extra_materials=(),
+                 tet_material=None, params: Params | None = None, stream=None, **pkw):
         lib = library()
-        self._args = _MeshArgs(rest_pos, tets, clamped, kind, E, nu, density, spline, kappa, fiber)
+        self._args = _MeshArgs(rest_pos, tets, clamped, kind, E, nu, density, spline, kappa, fiber,
+                               extra_materials, tet_material)
         self.n = self._args.n
         self.params = params if params is not None else default_params(**pkw)
         h = C.c_void_p()
-        _check(lib.sim_create(C.byref(self._args.mesh), C.byref(self._args.mat), C.byref(self.params),
+        _check(lib.sim_create(C.byref(self._args.mesh), self._args.mats, C.byref(self.params),
                               C.c_void_p(stream or 0), C.byref(h)), "sim_create")
         self._h = h
         self.last_status = 0
@@ -428,21 +457,20 @@ class Batch:
             raise ValueError("empty batch")
         self._keep = []
         meshes = (Mesh * len(ws))()
-        mats = (Material * len(ws))()
+        all_mats = []
         self.n = []
         for k, w in enumerate(ws):
             X = np.ascontiguousarray(w.rest_pos, dtype=np.float64)
             tets = np.ascontiguousarray(w.tets, dtype=np.int32)
             cl = None if w.clamped is None else np.ascontiguousarray(w.clamped, dtype=np.uint8)
-            m = w.material
-            sp = None if m.spline is None else np.ascontiguousarray(m.spline, dtype=np.float64)
-            self._keep += [X, tets, cl, sp]
+            ms = (w.material,) + tuple(getattr(w, "extra_materials", ()))
+            tm = None if len(ms) == 1 else np.ascontiguousarray(w.tet_material, dtype=np.int32)
+            self._keep += [X, tets, cl, tm]
             meshes[k] = Mesh(X.shape[0], tets.shape[0], _ptr(X), _ptr(tets, _ip),
-                             None if cl is None else _ptr(cl, _up))
-            mats[k] = Material(m.kind, m.E, m.nu, m.density, None if sp is None else _ptr(sp),
-                               float(getattr(m, "kappa", 0.0)),
-                               (C.c_double * 3)(*getattr(m, "fiber", (0.0, 0.0, 0.0))))
+                             None if cl is None else _ptr(cl, _up), len(ms), None if tm is None else _ptr(tm, _ip))
+            all_mats += [_material_struct(m, self._keep) for m in ms]
             self.n.append(X.shape[0])
+        mats = (Material * len(all_mats))(*all_mats)
         w0 = ws[0]
         pkw.setdefault("iters", w0.iters)
         pkw.setdefault("history_m", w0.history)

@@ -429,3 +429,87 @@ def test_sweep_wait_timeout_is_reported(use_graph):
         sim.set_state(w.q_cur, w.q_prev)
         assert sim.step(1) >= 0
         assert rel(sim.get_state()[0], x_ref) <= 1e-4
+
+
+# ---------------------------------------------------------------- several materials in one mesh
+
+TWO_MAT = W.two_material_bar((6, 4, 5), W.Material(W.NEOHOOKEAN, 2e5, 0.4, density=900.0),
+                             W.Material(W.STVK, 8e5, 0.35, density=1300.0), seed=14, v_range=0.4,
+                             name="two_material")
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_two_material_mesh_energy_solve_step(prec):
+    """hqn_mesh.tet_material: each tet evaluated with its own material, its
+    mass share and its weight in A0 from that material -- against the
+    oracle: energy and gradient, A0^{-1}, one whole step (FP64 with the
+    oracle's trial counts) and the Jacobi-PCG step (matrix-free A0 with the
+    per-tet stiffness)."""
+    w = TWO_MAT
+    P = problem_for(w)
+    assert len(P.mats) == 2
+    y = O.predictor(P, w.q_cur, w.q_prev)
+    x = perturbed(w, 4e-3, 2)
+    q = np.random.default_rng(3).normal(size=(w.n_verts, 3))
+    x_ref, st = O.solve_step(P, w.q_cur, w.q_prev, iters=w.iters, m=w.history)
+    with sim_for(w, prec, use_graph=0) as sim:
+        g, grad = sim.energy_grad(x, y)
+        r = sim.solve_A0(q)
+        sim.set_state(w.q_cur, w.q_prev)
+        rc, stats = sim.step(1, stats=True)
+        qc, _ = sim.get_state()
+    tol = 1e-11 if prec == FP64 else 1e-5
+    assert rel(grad, O.gradient(P, x, y)) <= tol
+    assert abs(g - O.objective(P, x, y)) <= (1e-11 if prec == FP64 else 2e-6) * abs(O.objective(P, x, y))
+    assert rel(r, O.solve_A(P, q)) <= (1e-11 if prec == FP64 else 2e-5)
+    assert rc >= 0 and rel(qc, x_ref) <= (1e-9 if prec == FP64 else 1e-4)
+    assert rel_step(qc, x_ref, w.q_cur) <= STEP_TOL[prec]
+    if prec == FP64:
+        assert stats["trials"] == st.trials
+    x_pcg, _ = O.solve_step(P, w.q_cur, w.q_prev, iters=w.iters, m=w.history, pcg_iters=15)
+    with sim_for(w, prec, a0_solver=1, pcg_iters=15) as sim:
+        sim.set_state(w.q_cur, w.q_prev)
+        assert sim.step(1) >= 0
+        assert rel(sim.get_state()[0], x_pcg) <= (1e-9 if prec == FP64 else 1e-4)
+
+
+def test_two_material_mesh_in_a_batch_bitwise():
+    """A batch mixing a two-material mesh with one-material meshes agrees bit
+    for bit with single handles."""
+    from paper_1604_07378_gb300 import hqn
+    ws = [WORKLOADS[1], TWO_MAT, WORKLOADS[0]]
+    with hqn.Batch(ws, precision=FP32) as b:
+        for i, w in enumerate(ws):
+            b.set_state(i, w.q_cur, w.q_prev)
+        assert b.step(2)[0] >= 0
+        got = [b.get_state(i)[0] for i in range(len(ws))]
+    for i, w in enumerate(ws):
+        with sim_for(w, FP32) as sim:
+            sim.set_state(w.q_cur, w.q_prev)
+            sim.step(2)
+            np.testing.assert_array_equal(got[i], sim.get_state()[0])
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_energy_gradient_device_pointers(prec):
+    """sim_energy_grad_device: the same g and grad g as sim_energy_grad (bit
+    for bit: the same conversions, done on the device) and as the oracle, on
+    caller-order float64 device arrays, clamped rows moved too."""
+    torch = pytest.importorskip("torch")
+    w = WORKLOADS[1]
+    P = problem_for(w)
+    rng = np.random.default_rng(31)
+    x = w.q_cur + 3e-3 * rng.normal(size=w.q_cur.shape)
+    y = O.predictor(P, w.q_cur, w.q_prev)
+    stream = torch.cuda.current_stream()
+    with sim_for(w, prec, use_graph=0, stream=stream.cuda_stream) as sim:
+        g_h, grad_h = sim.energy_grad(x, y)
+        xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+        yd = torch.tensor(y, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            g_d, grad_d = sim.energy_grad_device(xd, yd)
+            grad_d = grad_d.cpu().numpy()
+            assert g_d == g_h
+            np.testing.assert_array_equal(grad_d, grad_h)
+    assert abs(g_d - O.objective(P, x, y)) <= (1e-11 if prec == FP64 else 2e-6) * abs(O.objective(P, x, y))
+    assert rel(grad_d, O.gradient(P, x, y)) <= (1e-11 if prec == FP64 else 1e-5)
