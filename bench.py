@@ -37,6 +37,17 @@ METRIC = "time-steps/s & tet grad-evals/s at 384k tets, FP32 vs FP64 GPU, pos er
 SOLVE_TRAFFIC_BYTES = None
 UNIT = "time-steps/s"
 WORKLOAD = "cube40_neohookean"
+# FP32 floating-point operations of the tet pass per tet (2 x FFMA + FADD +
+# FMUL, from ncu's sass instruction counters on one k_tet launch of cube40,
+# TET_EVAL: 46.85M FFMA, 55.68M FADD, 28.03M FMUL over 384,000 tets; MUFU
+# operations not counted); None when the kernel changes until re-captured.
+TET_FLOPS_PER_TET = 462.0
+# per-tet-evaluation algorithmic bytes of the tet pass (idx 16 + Dm^-1 36 +
+# V 4 B, plus the vertex data of x_k, d, x, grad, y and mass per vertex
+# spread over the tets, 64 B x n / T); the solve's 2 nnz(L) x 4 B + 2 x 12 B
+# x n_f; the two-loop's (96 m + 48) B per vertex per iteration
+TET_BYTES = 56.0
+VERT_BYTES = 64.0
 
 
 def _peaks():
@@ -213,11 +224,20 @@ def run_ours(args, rank, world, dist):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
+    from paper_1604_07378_gb300 import autotune
     w = W.cube40(W.NEOHOOKEAN)
     T = w.n_tets
     graph = 0 if args.no_graph else 1
+    # the autotuner's choice for this mesh and GPU, if its cache has one and
+    # no shape is forced on the command line
+    forced = args.leaf_size or any(solve_shapes(args).values())
+    tune_cache = None if forced or args.no_tune_cache else autotune.DEFAULT_CACHE
+    tuned = None
+    if tune_cache and os.path.exists(tune_cache):
+        tuned = autotune.lookup(tune_cache, torch.cuda.get_device_name(dev), autotune.mesh_key(w.rest_pos, w.tets,
+                                w.clamped), hqn.FP32_MIXED)
     sim = hqn.Sim.from_workload(w, precision=hqn.FP32_MIXED, stream=stream.cuda_stream, use_graph=graph,
-                                leaf_size=args.leaf_size, **solve_shapes(args))
+                                leaf_size=args.leaf_size, tune_cache=tune_cache, **solve_shapes(args))
     info = sim.info()
     sim.set_state(w.q_cur, w.q_prev)
     sim.step(args.warmup)
@@ -293,6 +313,7 @@ def run_ours(args, rank, world, dist):
     sim.step(1)
     x32, _ = sim.get_state()
     ex = float(np.linalg.norm(x32 - x64) / np.linalg.norm(x64))
+    ex_step = float(np.linalg.norm(x32 - x64) / np.linalg.norm(x64 - w.q_cur))
     k64 = max(2, min(args.steps, 4))
     sim64.set_state(w.q_cur, w.q_prev)
     torch.cuda.synchronize()
@@ -328,6 +349,35 @@ def run_ours(args, rank, world, dist):
                 "algorithmic_bytes_per_launch": bytes_launch}
     roof["peak_source"] = f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src
 
+    # ---- the whole step against the HBM roofline: algorithmic bytes of every
+    # stage of a step (tet passes, solves, two-loop) over the step's time
+    nf = info["n_free"]
+    m = w.history
+    solve_bytes = 2 * info["factor_nnz"] * 4 + 2 * 12 * nf
+    step_bytes = (tet_evals_step * (TET_BYTES + VERT_BYTES * n / T) + iters * solve_bytes
+                  + iters * (96 * m + 48) * n)
+    roof_step = {"bound": "hbm", "algorithmic_bytes_per_step": step_bytes,
+                 "achieved": step_bytes / (ms_step * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": step_bytes / (ms_step * 1e-3) / 1e9 / peaks["hbm_gbs"], "peak_source": roof["peak_source"]}
+
+    # ---- the FP32 pipe: measured FMA-chain peak and the tet pass against it
+    clk_peak = ClockSampler(dev.index)
+    clk_peak.start()
+    fp32_peak = hqn.measure_peak(hqn.FP32_MIXED)
+    fp64_peak = hqn.measure_peak(hqn.FP64_PLAIN)
+    peak_clocks = clk_peak.stop()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fma = {"fp32_tflops_measured": fp32_peak / 1e12, "fp64_tflops_measured": fp64_peak / 1e12,
+           "sm_mhz_during": peak_clocks.get("sm_mhz"),
+           "fp32_tflops_nominal_at_that_clock": (sms * 128 * 2 * peak_clocks["sm_mhz"] * 1e6 / 1e12
+                                                 if peak_clocks.get("sm_mhz") else None)}
+    tet_flops = None
+    if TET_FLOPS_PER_TET:
+        achieved = TET_FLOPS_PER_TET * T / (stage_ms["tet"] * 1e-3)
+        tet_flops = {"bound": "fp32", "flops_per_tet": TET_FLOPS_PER_TET, "achieved_tflops": achieved / 1e12,
+                     "peak_tflops": fp32_peak / 1e12, "frac": achieved / fp32_peak,
+                     "hbm_frac": T * (TET_BYTES + 64.0) / (stage_ms["tet"] * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -338,6 +388,11 @@ def run_ours(args, rank, world, dist):
                    "history_m": w.history, "h": w.h, "parallelism": f"replicas{world}",
                    "initial_velocity": "one seeded body velocity, U[-0.5, 0.5]^3 m/s",
                    "chained_sweeps": bool(info.get("chained_sweeps", 0)),
+                   "solve_shapes": {k: info[k] for k in ("n_levels", "solve_dense_top", "dense_top_cols",
+                                                         "solve_threads", "solve_item_kb", "solve_items",
+                                                         "solve_leaf_kb", "solve_leaf_threads",
+                                                         "solve_prefetch")},
+                   "tuned": tuned is not None,
                    "l2": "working set %.0f MB > 129 MB L2 (factor alone %.0f MB)" % (
                        info["device_bytes"] / 1e6, info["factor_entries"] * 4 / 1e6)},
         "tet_grad_evals_per_s": world * tet_evals_step * args.steps / (ms / 1e3),
@@ -345,8 +400,10 @@ def run_ours(args, rank, world, dist):
         "fp64_plain": {"value": 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64,
                        "tet_grad_evals_per_s": tev64 * 1e3 / ms64, "steps": k64},
         "pos_err_fp32_vs_fp64_gpu": ex,
+        "pos_err_step_fp32_vs_fp64_gpu": ex_step,
         "stage_ms_per_launch": stage_ms, "stage_ms_per_step": per_step,
-        "roofline": roof, "clocks": clocks,
+        "roofline": roof, "roofline_step": roof_step, "fma_peak": fma, "tet_flop_roofline": tet_flops,
+        "clocks": clocks,
         "e2e": {"value": job_throughput(world, e2e_steps, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": None,
@@ -370,6 +427,7 @@ def run_ours(args, rank, world, dist):
         line["convergence"] = run_convergence(args, stream)
     if not args.no_configs:
         line["other_configs"] = run_other_configs(args, stream)
+        line["other_configs"].update(run_small_configs(args, stream))
     if rank == 0 and not args.no_cpu_baseline:
         host = host_description()
         one = oracle_steps(args.cpu_budget, 1, max_steps=2)
@@ -479,6 +537,49 @@ def run_other_configs(args, stream):
     return out
 
 
+def _timed_steps(sim, stream, steps):
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc, st = sim.step(steps, stats=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, rc, st
+
+
+def run_small_configs(args, stream):
+    """The configurations beside the headline: the 4x4x16 bar in the plain
+    FP64 form over its 30 steps; cube40 with St. Venant-Kirchhoff; cube40
+    with the per-vertex iid initial velocities (a tangled mesh whose line
+    search backtracks), over its first 20 steps."""
+    from paper_1604_07378_gb300 import hqn
+    from paper_1604_07378_gb300 import workloads as W
+
+    out = {}
+    w = W.bar_4x4x16_fp64()
+    with hqn.Sim.from_workload(w, precision=hqn.FP64_PLAIN, stream=stream.cuda_stream) as sim:
+        sim.set_state(w.q_cur, w.q_prev)
+        sim.step(2)
+        sim.set_state(w.q_cur, w.q_prev)
+        ms, rc, st = _timed_steps(sim, stream, 30)
+    out["bar4x4x16_fp64_plain"] = {"tets": w.n_tets, "vertices": w.n_verts, "precision": "f64", "steps": 30,
+                                   "steps_per_s": 1e3 / ms, "ms_per_step": ms, "status": rc,
+                                   "ls_trials_per_iter": st["trials_total"] / max(1, st["iters_total"])}
+    for key, wl in (("cube40_stvk", W.cube40(W.STVK)),
+                    ("cube40_neohookean_iid_velocity", W.cube40(W.NEOHOOKEAN, v_mode="iid"))):
+        with hqn.Sim.from_workload(wl, precision=hqn.FP32_MIXED, stream=stream.cuda_stream) as sim:
+            sim.set_state(wl.q_cur, wl.q_prev)
+            sim.step(2)
+            sim.set_state(wl.q_cur, wl.q_prev)
+            ms, rc, st = _timed_steps(sim, stream, 20)
+        out[key] = {"tets": wl.n_tets, "steps": 20, "steps_per_s": 1e3 / ms, "ms_per_step": ms, "status": rc,
+                    "tet_grad_evals_per_s": wl.n_tets * (st["trials_total"] + 20) / 20 * 1e3 / ms,
+                    "ls_trials_per_iter": st["trials_total"] / max(1, st["iters_total"]),
+                    "initial_velocity": wl.meta.get("v_mode", "body")}
+    return out
+
+
 def run_convergence(args, stream):
     """Eq. RelativeError of one frame of the twisting spline bar (80x40x40 at
     half resolution, 96,000 tets, FP64): (g(x_k) - g(x*)) / (g(x_0) - g(x*))
@@ -510,8 +611,16 @@ def run_convergence(args, stream):
     out = {"workload": "splinebar40x20x20_twist90", "tets": w.n_tets, "precision": "f64",
            "g_star_reference": "min g of an L-BFGS (m = 16) step of up to 500 iterations",
            "g_star_iterations": len(gs), "g_star_status": st_star["status"], "methods": {}}
+    from paper_1604_07378_gb300 import chebyshev
+    # rho of Alg. 3 estimated from a projective-dynamics run on the same frame
+    st_pd, _ = run(150, history_m=0)
+    rho_est = chebyshev.estimate_rho([st_pd["g0"]] + st_pd["g"])
+    out["cheb_rho_estimated"] = rho_est
+    out["cheb_rho_estimate"] = "sqrt of the median ratio of successive g decrements over the last 12 " \
+                               "iterations of a 150-iteration projective-dynamics (m = 0) step"
     for name, kw in (("pd_m0", dict(history_m=0)), ("lbfgs_m2", dict(history_m=2)),
                      ("lbfgs_m5", dict(history_m=5)), ("lbfgs_m8", dict(history_m=8)),
+                     ("chebyshev_S10_rho_estimated", dict(direction=1, cheb_S=10, cheb_rho=rho_est)),
                      ("chebyshev_S10_rho0.99", dict(direction=1, cheb_S=10, cheb_rho=0.99))):
         st, dt = run(60, **kw)
         g = st["g"][:60]
@@ -656,6 +765,7 @@ def main():
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the spline-bar and large-bar measurements")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--no-tune-cache", action="store_true", help="ignore the autotuner's cache (library defaults)")
     ap.add_argument("--leaf-size", type=int, default=0,
                     help="max vertices of a nested-dissection leaf (0 = the library default)")
     ap.add_argument("--solve-threads", type=int, default=0, help="threads per sweep block (0 = default)")

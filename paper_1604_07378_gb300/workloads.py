@@ -251,12 +251,14 @@ def bar_4x4x16_fp64() -> Workload:
                             seed=1604, name="bar4x4x16_nh")
 
 
-def cube40(kind: int = NEOHOOKEAN, n: int = 40) -> Workload:
+def cube40(kind: int = NEOHOOKEAN, n: int = 40, v_mode: str = "body") -> Workload:
     """n^3 cube lattice (n=40: 384,000 tets, 68,921 vertices), E=5e5 nu=0.4,
     z=0 face clamped, the free vertices set moving with one seeded velocity
-    drawn from U[-0.5, 0.5]^3 m/s."""
-    return lattice_workload((n, n, n), Material(kind, 5e5, 0.4), clamp_axis=2, seed=1605,
-                            v_range=0.5, v_mode="body", name=f"cube{n}_{MATERIAL_NAMES[kind]}")
+    drawn from U[-0.5, 0.5]^3 m/s (v_mode "iid": every vertex's own)."""
+    w = lattice_workload((n, n, n), Material(kind, 5e5, 0.4), clamp_axis=2, seed=1605,
+                         v_range=0.5, v_mode=v_mode, name=f"cube{n}_{MATERIAL_NAMES[kind]}")
+    w.meta["v_mode"] = v_mode
+    return w
 
 
 def spline_bar_80x40x40(scale: int = 1) -> Workload:

@@ -852,3 +852,31 @@ def test_two_materials_gradient_matches_central_differences():
             xm[v, c] -= eps
             fd = (O.objective(P, xp, y) - O.objective(P, xm, y)) / (2 * eps)
             assert abs(fd - g[v, c]) <= 1e-6 * max(1.0, abs(g[v, c])), (v, c, fd, g[v, c])
+
+
+def test_chebyshev_rho_estimate_matches_the_spectral_radius():
+    """The rho estimate from a projective-dynamics run's objective values
+    (paper_1604_07378_gb300/chebyshev.py) against the spectral radius of the
+    iteration's linearisation at the minimiser, I - A0^{-1} H with H the
+    (finite-difference) Hessian of g at x*, by a dense eigensolve on a tiny
+    mesh."""
+    from paper_1604_07378_gb300 import chebyshev
+    w, P = _problem((2, 2, 3), kind=W.STVK, v=0.6, seed=9)
+    x_star, _ = O.newton_minimise(P, w.q_cur, w.q_prev)
+    y = O.predictor(P, w.q_cur, w.q_prev)
+    free, nf = P.free, P.free.size
+    eps = 1e-7
+    H = np.zeros((3 * nf, 3 * nf))
+    for j in range(3 * nf):
+        vj, cj = divmod(j, 3)
+        xp, xm = x_star.copy(), x_star.copy()
+        xp[free[vj], cj] += eps
+        xm[free[vj], cj] -= eps
+        H[:, j] = (O.gradient(P, xp, y)[free].ravel() - O.gradient(P, xm, y)[free].ravel()) / (2 * eps)
+    A = np.kron(O.assemble_A(P).toarray(), np.eye(3))
+    rho_exact = float(np.max(np.abs(np.linalg.eigvals(np.eye(3 * nf) - np.linalg.solve(A, 0.5 * (H + H.T))))))
+    assert 0.3 < rho_exact < 1.0
+    # the slowest mode dominates once the faster ones have died out
+    _, st = O.solve_step(P, w.q_cur, w.q_prev, iters=150, m=0)
+    rho = chebyshev.estimate_rho([st.g0] + st.g)
+    assert abs(rho - rho_exact) <= 0.01 * rho_exact, (rho, rho_exact)
