@@ -126,3 +126,28 @@ def test_collider_parameters_are_checked(hqn):
         with pytest.raises(hqn.HQNError) as e:
             hqn.analyse_workload(w, colliders=(c,))
         assert e.value.code == hqn.HQN_ERR_ARG, c
+
+
+def test_non_spd_and_material_table_errors(hqn, lat12):
+    """A negative density makes A0 = M/h^2 + L indefinite: HQN_ERR_NOT_SPD
+    from the host set-up.  A per-tet material index outside the mesh's
+    material table, or too many materials, is HQN_ERR_ARG."""
+    w = lat12
+    with pytest.raises(hqn.HQNError) as e:
+        hqn.analyse(w.rest_pos, w.tets, w.clamped, kind=W.NEOHOOKEAN, E=5e5, nu=0.4, density=-1000.0)
+    assert e.value.code == hqn.HQN_ERR_NOT_SPD
+    b = W.Material(W.STVK, 6e5, 0.35)
+    tm = np.zeros(w.n_tets, np.int32)
+    tm[3] = 2  # two materials: indices 0 and 1 only
+    with pytest.raises(hqn.HQNError) as e:
+        hqn.analyse(w.rest_pos, w.tets, w.clamped, kind=W.NEOHOOKEAN, E=5e5, nu=0.4, extra_materials=(b,),
+                    tet_material=tm)
+    assert e.value.code == hqn.HQN_ERR_ARG
+    with pytest.raises(hqn.HQNError) as e:
+        hqn.analyse(w.rest_pos, w.tets, w.clamped, kind=W.NEOHOOKEAN, E=5e5, nu=0.4,
+                    extra_materials=(b,) * hqn.MAX_MATERIALS, tet_material=np.zeros(w.n_tets, np.int32))
+    assert e.value.code == hqn.HQN_ERR_ARG
+    tm[3] = 1
+    a = hqn.analyse(w.rest_pos, w.tets, w.clamped, kind=W.NEOHOOKEAN, E=5e5, nu=0.4, extra_materials=(b,),
+                    tet_material=tm)
+    assert a["n_tets"] == w.n_tets
