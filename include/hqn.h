@@ -177,14 +177,14 @@ typedef struct {
                                most 5,000 columns (the host's cost grows as the
                                cube of the columns); -1 = none.  Set at
                                sim_create (not by sim_set_solve_shapes)        */
-    int32_t solve_prefetch; /* L2 prefetches issued by the sweeps' levels: 1..8 =
-                               a level's blocks also prefetch the factor rows of
-                               the level this many launches ahead; 0 (default) =
-                               only the dense top block's matrix, streamed into
-                               L2 by the forward levels before it; -1 = none.
-                               (On a 40^3 lattice the factor-row prefetch left
-                               the solve's time unchanged and cost the step 3%
-                               of L2 hits elsewhere.)                            */
+    int32_t solve_prefetch; /* a level's blocks ask L2 to prefetch the factor rows
+                               of the level this many launches ahead: 1..8; 0 or
+                               -1 = none (default; on a 40^3 lattice it left the
+                               solve's time unchanged and cost the step 3% of L2
+                               hits elsewhere)                                   */
+    int32_t solve_dense_prefetch; /* 1 = the forward levels before the dense top
+                               block stream its matrix into L2 (a faster solve,
+                               a slower step on a 40^3 lattice); 0 = no (default) */
     /* Collisions (Sec. 4.3) against analytic colliders, shared by every
      * simulation of a handle.  At the start of each iteration (before the
      * gradient at x_k) every free vertex that penetrates a collider and does
@@ -239,8 +239,9 @@ typedef struct {
      * batch, the keys of all meshes folded in order), the precision and the
      * current device's name there, and, on a hit, replace leaf_size,
      * solve_threads, solve_item_kb, solve_items, solve_prefetch (and
-     * solve_leaf_kb, solve_leaf_threads, solve_dense_top and ls_batch if
-     * the entry has them) by the tuned values.  A missing file
+     * solve_leaf_kb, solve_leaf_threads, solve_dense_top,
+     * solve_dense_prefetch and ls_batch if the entry has them) by the tuned
+     * values.  A missing file
      * or entry leaves the parameters as given; a malformed file is
      * HQN_ERR_ARG. */
     const char *tune_cache;
@@ -281,6 +282,7 @@ typedef struct {
     int32_t solve_leaf_kb;
     int32_t solve_leaf_threads;
     int32_t solve_prefetch;     /* 0 = no prefetch                                        */
+    int32_t solve_dense_prefetch;
     int32_t solve_dense_top;    /* top levels solved by the dense block (0 = none), of the
                                    first simulation                                       */
     int32_t dense_top_cols;     /* columns of that block (largest simulation)              */
@@ -436,7 +438,8 @@ int sim_time_stage(sim_handle *sim, int32_t stage, int32_t reps, double *ms);
 
 /* New sweep shapes on an existing handle: the fields solve_threads,
  * solve_item_kb, solve_items, solve_leaf_kb, solve_leaf_threads and
- * solve_prefetch of *shapes (0 = default; the other fields are ignored).  The
+ * solve_prefetch and solve_dense_prefetch of *shapes (0 = default; the other
+ * fields are ignored).  The
  * work items are re-planned from the handle's own factor (no
  * refactorisation) and the step graph is rebuilt.  Results change by
  * rounding only (other row splits), or not at all (threads, prefetch).
@@ -456,7 +459,8 @@ uint64_t hqn_mesh_key(const hqn_mesh *mesh);
  *   hqn-tune 1 device=<name, spaces as '_'> precision=<0|1> key=<16 hex>
  *     leaf_size=<n> solve_threads=<n> solve_item_kb=<n> solve_items=<n>
  *     solve_prefetch=<n> [solve_leaf_kb=<n>] [solve_leaf_threads=<n>]
- *     [solve_dense_top=<n>] [ls_batch=<n>] [other key=value pairs, ignored]
+ *     [solve_dense_top=<n>] [solve_dense_prefetch=<0|1>] [ls_batch=<n>]
+ *     [other key=value pairs, ignored]
  * Returns 1 and writes the entry's values into *params on a hit, 0 when the
  * file or the entry does not exist (params unchanged), HQN_ERR_ARG for a
  * malformed file or argument. */

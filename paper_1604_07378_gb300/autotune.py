@@ -13,8 +13,8 @@ current GPU, on the mesh itself:
    (sim_set_solve_shapes re-plans the work items without refactorising)
    and one solve is timed with CUDA events on the device (sim_time_stage,
    best of three means);
-2. the best shape of each handle, and the library's defaults, are timed
-   as whole time steps (one CUDA graph each);
+2. the three fastest shapes of each handle, and the library's defaults,
+   are timed as whole time steps (one CUDA graph each);
 3. the fastest is written to the cache file as one line, keyed by the
    device name, the precision and the mesh's hash (hqn_mesh_key).
 
@@ -37,13 +37,14 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_c
 LEAF_SIZES = (64, 128)
 DENSE_TOPS = (-1, 2, 3)
 SHAPE_KEYS = ("solve_threads", "solve_item_kb", "solve_items", "solve_prefetch", "solve_leaf_kb",
-              "solve_leaf_threads")
+              "solve_leaf_threads", "solve_dense_prefetch")
 # the re-plannable sweep shapes (hqn_params.solve_*; 0 = default)
-SHAPE_GRID = tuple(dict(solve_threads=256, solve_item_kb=kb, solve_items=n, solve_prefetch=pf,
+SHAPE_GRID = tuple(dict(solve_threads=256, solve_item_kb=kb, solve_items=n, solve_dense_prefetch=dp,
                         solve_leaf_kb=lkb, solve_leaf_threads=lt)
                    for kb, n in ((64, 400), (48, 304), (96, 304))
                    for lkb, lt in ((0, 0), (24, 128), (32, 128), (48, 256))
-                   for pf in (0, -1))
+                   for dp in (0, 1))
+STEP_FINALISTS = 3  # the fastest solves of each handle, timed again as whole steps
 
 
 def mesh_key(rest_pos, tets, clamped=None) -> int:
@@ -117,10 +118,15 @@ def tune_workload(w, precision=hqn.FP32_MIXED, stream=None, leaf_sizes=LEAF_SIZE
                     timed.append((t, g))
                 if not timed:
                     continue
-                t_best, g_best = min(timed)
-                sim.set_solve_shapes(**grid[g_best])
-                results.append({"leaf_size": leaf, "solve_dense_top": top, **grid[g_best], "solve_ms": t_best,
-                                "step_ms": _step_ms(sim, w, steps), "shapes_timed": len(timed)})
+                # a shape may speed the solve and slow the rest of the step
+                # (L2 traffic), so the whole step decides among the finalists
+                finals = []
+                for t_solve, g in sorted(timed)[:STEP_FINALISTS]:
+                    sim.set_solve_shapes(**grid[g])
+                    finals.append((_step_ms(sim, w, steps), t_solve, g))
+                t_step, t_solve, g_best = min(finals)
+                results.append({"leaf_size": leaf, "solve_dense_top": top, **grid[g_best], "solve_ms": t_solve,
+                                "step_ms": t_step, "shapes_timed": len(timed)})
     with hqn.Sim.from_workload(w, precision=precision, stream=stream) as sim:
         info = sim.info()
         default = {"leaf_size": 0, "solve_dense_top": 0, **{k: 0 for k in SHAPE_KEYS},

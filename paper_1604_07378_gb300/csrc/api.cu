@@ -668,7 +668,7 @@ struct Sim final : SimBase {
             std::vector<int> fwd_launches;
             for (int l = 0; l < L; ++l)
                 if (fwd_ptr[l + 1] > fwd_ptr[l]) fwd_launches.push_back(l);
-            if (dense_bytes > 0 && prm.solve_prefetch >= 0 && fwd_launches.size() >= 3) {
+            if (dense_bytes > 0 && prm.solve_dense_prefetch > 0 && fwd_launches.size() >= 3) {
                 const int first = 1, last = (int)fwd_launches.size() - 2;  // inclusive
                 const int nl = last - first + 1;
                 constexpr int64_t kPiece = 256 * 1024;
@@ -710,6 +710,7 @@ struct Sim final : SimBase {
         p.solve_prefetch = sh.solve_prefetch;
         p.solve_leaf_kb = sh.solve_leaf_kb;
         p.solve_leaf_threads = sh.solve_leaf_threads;
+        p.solve_dense_prefetch = sh.solve_dense_prefetch;
         if (const int rc = check_solve_shapes(p)) return rc;
         int rc;
         std::string err;
@@ -1157,6 +1158,7 @@ struct Sim final : SimBase {
         o->solve_leaf_kb = prm.solve_leaf_kb > 0 ? prm.solve_leaf_kb : o->solve_item_kb;
         o->solve_leaf_threads = dsol.leaf_threads;
         o->solve_prefetch = dsol.prefetch;
+        o->solve_dense_prefetch = prm.solve_dense_prefetch;
         o->solve_dense_top = S.empty() ? 0 : S[0].top_levels;
         o->dense_top_cols = dense_cols;
         o->n_sims = ns;
@@ -1214,6 +1216,8 @@ int check_solve_shapes(const hqn_params &p) {
         return fail(HQN_ERR_ARG, "solve_items must be 0 or in [16, 4096]");
     if (p.solve_dense_top < -1 || p.solve_dense_top > 8)
         return fail(HQN_ERR_ARG, "solve_dense_top must be -1 (none), 0 (automatic) or in [1, 8]");
+    if (p.solve_dense_prefetch != 0 && p.solve_dense_prefetch != 1)
+        return fail(HQN_ERR_ARG, "solve_dense_prefetch must be 0 or 1");
     if (p.solve_prefetch < -1 || p.solve_prefetch > 8)
         return fail(HQN_ERR_ARG, "solve_prefetch must be -1 (none), 0 (default) or in [1, 8]");
     return HQN_OK;
@@ -1344,6 +1348,7 @@ void hqn_default_params(hqn_params *p) {
     p->solve_item_kb = 64;
     p->solve_items = 400;
     p->solve_prefetch = 0;
+    p->solve_dense_prefetch = 0;
     p->solve_dense_top = 0;
     p->wait_polls = 0;
     p->fault_test = 0;
@@ -1452,6 +1457,7 @@ int hqn_analyse(const hqn_mesh *mesh, const hqn_material *material, const hqn_pa
         info->solve_leaf_threads = params->solve_leaf_threads > 0 ? params->solve_leaf_threads : info->solve_threads;
         info->solve_items = params->solve_items > 0 ? params->solve_items : 400;
         info->solve_prefetch = params->solve_prefetch <= 0 ? 0 : params->solve_prefetch;
+        info->solve_dense_prefetch = params->solve_dense_prefetch;
         info->solve_dense_top = S.top_levels;
         info->dense_top_cols = S.n_top;
         info->n_sims = 1;

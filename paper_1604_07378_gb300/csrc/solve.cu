@@ -563,7 +563,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_bwd(DevSolve<R> S, int item0,
 // tiles (I, J), J <= I, each a contiguous row-major block, zero-padded past
 // the last column.  A block takes one tile: every row of the tile gives a
 // row product S_IJ f_J (for band I), and an off-diagonal tile also gives the
-// column products S_IJ^T f_I (for band J) from the same loaded rows.  Each
+// column products S_IJ^T f_I (for band J) from the same rows.  The tile
+// arrives in shared memory by one bulk copy, issued before the wait on the
+// previous level (the matrix does not depend on the solve).  Each
 // product lands in its band's partial slot (slot J for row products, slot I
 // for column products); the last of a band's nb contributions to arrive adds
 // the slots in order and writes r.
@@ -571,21 +573,6 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_bwd(DevSolve<R> S, int item0,
 //                         {n_top, first band of the simulation, nb, tcol offset}
 //                         {bptr offset, 0, 0, 0}
 constexpr int TS = 128;
-
-__device__ __forceinline__ float4 ld_stream(const float4 *p, uint64_t pol) {
-    float4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p), "l"(pol));
-    return v;
-}
-__device__ __forceinline__ double2 ld_stream(const double2 *p, uint64_t pol) {
-    double2 v;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
-                 : "=d"(v.x), "=d"(v.y)
-                 : "l"(p), "l"(pol));
-    return v;
-}
 
 // f of Eq. PDsolution's right-hand side on TS columns of T from c0 (zero past
 // n): q minus the (<= 4) update entries from below T, entries e.
@@ -613,11 +600,15 @@ __device__ __forceinline__ void dense_gather(const DevSolve<R> &S, const V4<R> *
 }
 
 template <typename R, int NT>
-__global__ void __launch_bounds__(NT, 768 / NT) k_dense(DevSolve<R> S, const V4<R> *rhs, V4<R> *r) {
+__global__ void __launch_bounds__(NT) k_dense(DevSolve<R> S, const V4<R> *rhs, V4<R> *r) {
     constexpr int NW = NT / 32;
     constexpr int RPW = TS / NW;  // rows per warp
-    // one lane holds TS / 32 consecutive columns of a row: 4 floats (one
-    // 16-byte load) or 4 doubles (two)
+    // the tile (TS x TS entries, dynamic shared memory) arrives by one bulk
+    // copy issued before the wait on the previous level; one lane holds
+    // TS / 32 = 4 consecutive columns of a row
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    R *tile = reinterpret_cast<R *>(smem_raw);
+    __shared__ __align__(8) uint64_t bar;
     __shared__ __align__(16) R fJ[3 * TS], fI[3 * TS];
     __shared__ __align__(16) R colpart[NW][3][TS];
     __shared__ int colvJ[TS], colvI[TS];
@@ -626,14 +617,16 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_dense(DevSolve<R> S, const V4<
     const int4 *rec = S.dense_tiles + 3 * (size_t)blockIdx.x;
     const int4 a = rec[0], b = rec[1], c = rec[2];
     const long long off = (long long)(unsigned)a.x | ((long long)a.y << 32);
+    if (threadIdx.x == 0) {
+        bulk_bar_init(&bar);
+        bulk_load_issue(&bar, tile, S.dense_inv + off, (uint32_t)(TS * TS * sizeof(R)));
+    }
     const int I = a.z, J = a.w;
     const int n = b.x, band0 = b.y, nb = b.z, tc0 = b.w;
     const bool diag = I == J;
     const int rI = I * TS, cJ = J * TS;
     const int nI = min(TS, n - rI), nJ = min(TS, n - cJ);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
     // before the wait: the index data of the gathers (nothing the solve writes)
     const int *tcol = S.dense_col + tc0;
     const int *bptr = S.dense_bptr + c.x;
@@ -653,7 +646,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_dense(DevSolve<R> S, const V4<
     __syncthreads();
     dense_gather<R>(S, rhs, colvJ, bndJ, nJ, fJ, threadIdx.x, NT);
     if (!diag) dense_gather<R>(S, rhs, colvI, bndI, nI, fI, threadIdx.x, NT);
-    __syncthreads();
+    if (!bulk_load_finish(&bar, 0u, S.err, S.wait_polls, true)) return;  // (its barrier also orders f)
     const R *fi = diag ? fJ : fI;
     // this lane's columns of f_J
     R fj[3][4];
@@ -668,49 +661,34 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_dense(DevSolve<R> S, const V4<
     for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) ca[k][cc] = R(0);
-    const R *tile = S.dense_inv + off;
     V4<R> *part = S.dense_part + (size_t)band0 * S.dense_nct_max * TS;
-    constexpr int BATCH = 4;  // rows whose loads are in flight together
-    for (int i0 = warp * RPW; i0 < warp * RPW + RPW; i0 += BATCH) {
-        R q[BATCH][4];
+    for (int i = warp * RPW; i < warp * RPW + RPW; ++i) {
+        const R *row = tile + (size_t)i * TS + 4 * lane;
+        R q[4];
 #pragma unroll
-        for (int h = 0; h < BATCH; ++h) {
-            const R *row = tile + (size_t)(i0 + h) * TS + 4 * lane;
-            if (sizeof(R) == 4) {
-                const float4 v = ld_stream(reinterpret_cast<const float4 *>(row), pol);
-                q[h][0] = v.x; q[h][1] = v.y; q[h][2] = v.z; q[h][3] = v.w;
-            } else {
-                const double2 v0 = ld_stream(reinterpret_cast<const double2 *>(row), pol);
-                const double2 v1 = ld_stream(reinterpret_cast<const double2 *>(row) + 1, pol);
-                q[h][0] = v0.x; q[h][1] = v0.y; q[h][2] = v1.x; q[h][3] = v1.y;
-            }
+        for (int cc = 0; cc < 4; ++cc) q[cc] = row[cc];
+        R px = R(0), py = R(0), pz = R(0);
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            px += q[cc] * fj[0][cc];
+            py += q[cc] * fj[1][cc];
+            pz += q[cc] * fj[2][cc];
         }
-#pragma unroll
-        for (int h = 0; h < BATCH; ++h) {
-            const int i = i0 + h;
-            R px = R(0), py = R(0), pz = R(0);
+        px = group_sum<R, 32>(px);
+        py = group_sum<R, 32>(py);
+        pz = group_sum<R, 32>(pz);
+        if (lane == 0 && i < nI) {
+            V4<R> o;
+            o.x = px; o.y = py; o.z = pz; o.w = R(0);
+            part[((size_t)I * S.dense_nct_max + J) * TS + i] = o;  // band I, slot J
+        }
+        if (!diag) {
+            const R gx = fi[i], gy = fi[TS + i], gz = fi[2 * TS + i];
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
-                px += q[h][cc] * fj[0][cc];
-                py += q[h][cc] * fj[1][cc];
-                pz += q[h][cc] * fj[2][cc];
-            }
-            px = group_sum<R, 32>(px);
-            py = group_sum<R, 32>(py);
-            pz = group_sum<R, 32>(pz);
-            if (lane == 0 && i < nI) {
-                V4<R> o;
-                o.x = px; o.y = py; o.z = pz; o.w = R(0);
-                part[((size_t)I * S.dense_nct_max + J) * TS + i] = o;  // band I, slot J
-            }
-            if (!diag) {
-                const R gx = fi[i], gy = fi[TS + i], gz = fi[2 * TS + i];
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) {
-                    ca[0][cc] += q[h][cc] * gx;
-                    ca[1][cc] += q[h][cc] * gy;
-                    ca[2][cc] += q[h][cc] * gz;
-                }
+                ca[0][cc] += q[cc] * gx;
+                ca[1][cc] += q[cc] * gy;
+                ca[2][cc] += q[cc] * gz;
             }
         }
     }
@@ -836,6 +814,7 @@ void launch_sweeps(const DevSolve<R> &s, const V4<R> *q, V4<R> *z, V4<R> *r) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)s.n_dense_tiles);
         cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = (size_t)TS * TS * sizeof(R);
         cfg.stream = st_of(s);
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -870,7 +849,9 @@ cudaError_t prepare_nt() {
 template <typename R> size_t solve_block_smem(int qcap, int ld) { return sweep_smem<R>(qcap, ld); }
 
 template <typename R> cudaError_t solve_prepare() {
-    cudaError_t e = prepare_nt<R, 128>();
+    cudaError_t e = cudaFuncSetAttribute(k_dense<R, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(TS * TS * sizeof(R)));
+    if (e == cudaSuccess) e = prepare_nt<R, 128>();
     if (e == cudaSuccess) e = prepare_nt<R, 256>();
     if (e == cudaSuccess) e = prepare_nt<R, 512>();
     return e;

@@ -6,7 +6,7 @@
 //   hqn-tune 1 device=<name> precision=<0|1> key=<16 hex digits> leaf_size=<n>
 //       solve_threads=<n> solve_item_kb=<n> solve_items=<n> solve_prefetch=<n>
 //       [solve_leaf_kb=<n>] [solve_leaf_threads=<n>] [solve_dense_top=<n>]
-//       [ls_batch=<n>] [any other key=value, ignored]
+//       [solve_dense_prefetch=<0|1>] [ls_batch=<n>] [any other key=value, ignored]
 // <name> is the CUDA device name with every space replaced by '_'.  The
 // autotuner (paper_1604_07378_gb300/autotune.py) writes these lines.
 #include <cstdio>
@@ -99,6 +99,7 @@ int hqn_tune_lookup(const char *path, const char *device, uint64_t key, int32_t 
             else if (k == "solve_leaf_kb") ok = parse_int(v, 0, 160, &p.solve_leaf_kb);
             else if (k == "solve_leaf_threads") ok = parse_int(v, 0, 512, &p.solve_leaf_threads);
             else if (k == "solve_dense_top") ok = parse_int(v, -1, 8, &p.solve_dense_top);
+            else if (k == "solve_dense_prefetch") ok = parse_int(v, 0, 1, &p.solve_dense_prefetch);
             if (!ok) break;
         }
         if (!ok || l_dev.empty() || l_key.size() != 16 || l_prec < 0) return HQN_ERR_ARG;

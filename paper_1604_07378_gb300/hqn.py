@@ -68,7 +68,7 @@ class Params(C.Structure):
                 ("tet_block", C.c_int32), ("ls_batch", C.c_int32), ("solve_threads", C.c_int32),
                 ("solve_item_kb", C.c_int32), ("solve_items", C.c_int32), ("solve_leaf_kb", C.c_int32),
                 ("solve_leaf_threads", C.c_int32), ("solve_dense_top", C.c_int32), ("solve_prefetch", C.c_int32),
-                ("n_colliders", C.c_int32), ("contact_scale", C.c_double),
+                ("solve_dense_prefetch", C.c_int32), ("n_colliders", C.c_int32), ("contact_scale", C.c_double),
                 ("colliders", Collider * MAX_COLLIDERS), ("a0_solver", C.c_int32), ("pcg_iters", C.c_int32),
                 ("direction", C.c_int32), ("cheb_S", C.c_int32), ("cheb_rho", C.c_double),
                 ("merge_depths", C.c_int32), ("wait_polls", C.c_int32), ("fault_test", C.c_int32),
@@ -91,7 +91,7 @@ class Info(C.Structure):
                 ("graph_mode", C.c_int32), ("n_update_entries", C.c_int64),
                 ("chained_sweeps", C.c_int32), ("solve_threads", C.c_int32), ("solve_item_kb", C.c_int32),
                 ("solve_items", C.c_int32), ("solve_leaf_kb", C.c_int32), ("solve_leaf_threads", C.c_int32),
-                ("solve_prefetch", C.c_int32), ("solve_dense_top", C.c_int32),
+                ("solve_prefetch", C.c_int32), ("solve_dense_prefetch", C.c_int32), ("solve_dense_top", C.c_int32),
                 ("dense_top_cols", C.c_int32), ("n_sims", C.c_int32)]
 
 

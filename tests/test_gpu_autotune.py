@@ -62,7 +62,7 @@ def test_tuning_writes_a_cache_that_sim_create_applies(tmp_path):
     from paper_1604_07378_gb300 import autotune, hqn
     w = W9
     cache = str(tmp_path / "cache.txt")
-    grid = (dict(solve_prefetch=-1), dict(solve_item_kb=32, solve_items=800, solve_leaf_kb=16, solve_leaf_threads=128),
+    grid = (dict(solve_dense_prefetch=1), dict(solve_item_kb=32, solve_items=800, solve_leaf_kb=16, solve_leaf_threads=128),
             dict(solve_threads=512, solve_item_kb=96, solve_items=152))
     res = autotune.tune_workload(w, leaf_sizes=(32, 64), dense_tops=(0, 2), grid=grid, reps=5, steps=3, cache=cache)
     assert res["step_ms"] <= res["default_step_ms"]

@@ -106,11 +106,11 @@ LAT30 = W.lattice_workload((30, 30, 30), W.Material(W.NEOHOOKEAN, 5e5, 0.4), cla
 
 
 # shapes of the sweeps (hqn_params.solve_*): block threads, work-item size
-# and count, L2 prefetch distance
+# and count, L2 prefetches (factor rows ahead; the dense block's matrix)
 SHAPES = {"default": {}, "t512": dict(solve_threads=512),
           "small_items": dict(solve_item_kb=16, solve_items=2000, solve_prefetch=1),
           "big_items": dict(solve_item_kb=128, solve_items=152, solve_threads=512, solve_prefetch=4),
-          "no_prefetch": dict(solve_prefetch=-1),
+          "no_prefetch": dict(solve_prefetch=-1), "dense_prefetch": dict(solve_dense_prefetch=1, solve_dense_top=3),
           "dense_top1": dict(solve_dense_top=1), "dense_top3": dict(solve_dense_top=3, solve_prefetch=2),
           "no_dense_top": dict(solve_dense_top=-1),
           "leaf_items": dict(solve_leaf_kb=16, solve_leaf_threads=128, solve_threads=512)}
@@ -220,7 +220,7 @@ def test_sweep_shapes_agree_bitwise():
     themselves) give the same result every time."""
     w = WORKLOADS[1]
     out = []
-    for kw in ({}, dict(solve_threads=512), dict(solve_prefetch=-1), dict(solve_prefetch=6)):
+    for kw in ({}, dict(solve_threads=512), dict(solve_dense_prefetch=1), dict(solve_prefetch=6)):
         with sim_for(w, FP32, use_graph=1, **kw) as sim:
             sim.set_state(w.q_cur, w.q_prev)
             sim.step(3)

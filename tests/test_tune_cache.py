@@ -22,9 +22,9 @@ def at():
     return autotune
 
 
-def _choice(leaf, t, kb, n, pf, top=0, lkb=0, lt=0):
+def _choice(leaf, t, kb, n, pf, top=0, lkb=0, lt=0, dp=0):
     return {"leaf_size": leaf, "solve_dense_top": top, "solve_threads": t, "solve_item_kb": kb, "solve_items": n,
-            "solve_prefetch": pf, "solve_leaf_kb": lkb, "solve_leaf_threads": lt}
+            "solve_prefetch": pf, "solve_leaf_kb": lkb, "solve_leaf_threads": lt, "solve_dense_prefetch": dp}
 
 
 def test_mesh_key_identifies_the_mesh(at):
@@ -45,13 +45,13 @@ def test_lookup_hits_misses_and_overrides(at, tmp_path):
     path = str(tmp_path / "cache.txt")
     assert at.lookup(path, DEV, 123, 1) is None  # no file yet
     lines = ["# tuned on a GB300",
-             at.cache_line(DEV, 1, 123, _choice(128, 512, 96, 152, 3, 3, 24, 128), step_ms=2.0, workload="cube40"),
+             at.cache_line(DEV, 1, 123, _choice(128, 512, 96, 152, 3, 3, 24, 128, 1), step_ms=2.0, workload="cube40"),
              at.cache_line(DEV, 0, 123, _choice(64, 256, 64, 400, 2)),
              at.cache_line("Other GPU", 1, 123, _choice(256, 256, 32, 800, -1)),
              at.cache_line(DEV, 1, 999, _choice(256, 256, 32, 800, 1))]
     with open(path, "w") as f:
         f.write("\n".join(lines) + "\n")
-    assert at.lookup(path, DEV, 123, 1) == {**_choice(128, 512, 96, 152, 3, 3, 24, 128), "ls_batch": 8}
+    assert at.lookup(path, DEV, 123, 1) == {**_choice(128, 512, 96, 152, 3, 3, 24, 128, 1), "ls_batch": 8}
     assert at.lookup(path, DEV, 123, 0) == {**_choice(64, 256, 64, 400, 2), "ls_batch": 8}
     assert at.lookup(path, "Other GPU", 123, 1)["solve_prefetch"] == -1
     assert at.lookup(path, DEV, 124, 1) is None
