@@ -443,12 +443,13 @@ struct Sim final : SimBase {
 
     // The dense top block of every simulation that has one (Setup::n_top > 0):
     // the lower block triangle of S^{-1} as TS x TS tiles (J <= I), each a
-    // contiguous row-major block zero-padded past the last column; the
-    // block's columns and its boundary update entries in batch numbering;
-    // one tile record per tile (solve.cu, k_dense).
+    // contiguous row-major block with rows LDT entries apart, zero past the
+    // last row and column; the block's columns and its boundary update
+    // entries in batch numbering; one tile record per tile (solve.cu, k_dense).
     int init_dense_top(const std::vector<int> &v0, const std::vector<int> &u0) {
         int rc;
-        constexpr int TS = 128;  // the tile edge of k_dense (solve.cu)
+        constexpr int TS = 128;                         // the tile edge of k_dense (solve.cu)
+        constexpr int LDT = TS + 16 / (int)sizeof(R);  // its rows, padded by 16 bytes
         std::vector<R> inv;
         std::vector<int> col, bptr, bidx;
         std::vector<int4> tiles;
@@ -469,10 +470,10 @@ struct Sim final : SimBase {
             for (int I = 0; I < nb; ++I)
                 for (int J = 0; J <= I; ++J) {
                     const int64_t off = (int64_t)inv.size();
-                    inv.resize(inv.size() + (size_t)TS * TS, R(0));
+                    inv.resize(inv.size() + (size_t)TS * LDT, R(0));
                     for (int i = 0; i < TS && I * TS + i < n; ++i)
                         for (int j = 0; j < TS && J * TS + j < n; ++j)
-                            inv[off + (size_t)i * TS + j] = (R)s.top_inv[(size_t)(I * TS + i) * n + J * TS + j];
+                            inv[off + (size_t)i * LDT + j] = (R)s.top_inv[(size_t)(I * TS + i) * n + J * TS + j];
                     tiles.push_back(make_int4((int)(off & 0xffffffffLL), (int)(off >> 32), I, J));
                     tiles.push_back(make_int4(n, bands, nb, tc0));
                     tiles.push_back(make_int4(bp0, 0, 0, 0));
@@ -482,6 +483,11 @@ struct Sim final : SimBase {
         }
         dsol.n_dense_tiles = (int)(tiles.size() / 3);
         dsol.dense_nct_max = nb_max;
+        {
+            int dev = 0;
+            CK(cudaGetDevice(&dev));
+            CK(cudaDeviceGetAttribute(&dsol.n_sm, cudaDevAttrMultiProcessorCount, dev));
+        }
         dense_bytes = (int64_t)inv.size() * (int64_t)sizeof(R);
         if (dsol.n_dense_tiles == 0) return HQN_OK;
         const int4 *p_t;

@@ -154,6 +154,7 @@ struct DevSolve {
     // of every band (dense_nct_max slots of TS rows: one per block column)
     // and the bands' arrival counters (re-armed by the last contribution).
     int n_dense_tiles, dense_nct_max;
+    int n_sm;                   // host: SMs of the device (the dense launch's grid)
     const int4 *dense_tiles;
     const R *dense_inv;
     const int *dense_col, *dense_bptr, *dense_bidx;

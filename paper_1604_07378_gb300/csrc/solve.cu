@@ -35,7 +35,8 @@
 // chain of levels, and a level's own bulk copies then read L2.
 //
 // When the top levels are solved by the dense block, the forward launches
-// before it also prefetch its matrix into L2 the same way.
+// before it may also prefetch its matrix into L2 the same way
+// (solve_dense_prefetch).
 //
 // Every wait is bounded (wait_polls polls of the copy's mbarrier); past the
 // bound the block flags the error in the handle's control block and leaves
@@ -560,184 +561,271 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_bwd(DevSolve<R> S, int item0,
 // replaces both sweeps' top levels.
 //
 // S^{-1} is symmetric, so only its lower block triangle is stored: TS x TS
-// tiles (I, J), J <= I, each a contiguous row-major block, zero-padded past
-// the last column.  A block takes one tile: every row of the tile gives a
-// row product S_IJ f_J (for band I), and an off-diagonal tile also gives the
-// column products S_IJ^T f_I (for band J) from the same rows.  The tile
-// arrives in shared memory by one bulk copy, issued before the wait on the
-// previous level (the matrix does not depend on the solve).  Each
-// product lands in its band's partial slot (slot J for row products, slot I
-// for column products); the last of a band's nb contributions to arrive adds
-// the slots in order and writes r.
+// tiles (I, J), J <= I, each a contiguous row-major block with rows padded
+// by 16 bytes (LDT entries apart), zero past the last row and column.  Every row of a tile gives a row product
+// S_IJ f_J (for band I); an off-diagonal tile also gives the column products
+// S_IJ^T f_I (for band J) from the same entries.  Each product lands in its
+// band's partial slot (slot J for row products, slot I for column products);
+// the last of a band's nb contributions to arrive adds the slots in order and
+// writes r.
 //   tile record (3 int4): {tile offset lo, hi, I, J}
 //                         {n_top, first band of the simulation, nb, tcol offset}
 //                         {bptr offset, 0, 0, 0}
+//
+// The launch is persistent: block b takes the consecutive tiles
+// [b T / G, (b + 1) T / G) of the T tiles (G blocks, BPS per SM, at most
+// TPB tiles each) and streams them through a ring of NBUF half-tile buffers
+// in shared memory.  With two blocks per SM (float), one block's arrival on
+// a band (a fence and an atomic, about a microsecond) overlaps the other's
+// products.  A half tile (HR padded rows) arrives by one
+// bulk copy.  With the padding a thread per row reads its row in 16-byte
+// pieces without bank conflicts (consecutive rows start 16 bytes apart in
+// bank order), and a thread per column reads its column with the warp's 32
+// columns side by side.  The first NBUF half tiles
+// are requested before the wait on the previous level (the matrix does not
+// depend on the solve), and each buffer is refilled as soon as the block has
+// read it, so the copies run while the block computes.  f_J and f_I of all
+// the block's tiles are gathered once, after the wait, into shared memory.
 constexpr int TS = 128;
 
-// f of Eq. PDsolution's right-hand side on TS columns of T from c0 (zero past
-// n): q minus the (<= 4) update entries from below T, entries e.
-template <typename R>
-__device__ __forceinline__ void dense_gather(const DevSolve<R> &S, const V4<R> *rhs, const int *colv, const int4 *bnd,
-                                             int n_valid, R *f, int tid, int nt) {
-    for (int j = tid; j < TS; j += nt) {
-        R fx = R(0), fy = R(0), fz = R(0);
-        if (j < n_valid) {
-            const int4 e = bnd[j];
-            const V4<R> v = ld_cg(rhs + colv[j]);
-            V4<R> u[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) u[k].x = u[k].y = u[k].z = R(0);
-            if (e.x >= 0) u[0] = ld_cg(S.u + e.x);
-            if (e.y >= 0) u[1] = ld_cg(S.u + e.y);
-            if (e.z >= 0) u[2] = ld_cg(S.u + e.z);
-            if (e.w >= 0) u[3] = ld_cg(S.u + e.w);
-            fx = v.x - u[0].x - u[1].x - u[2].x - u[3].x;
-            fy = v.y - u[0].y - u[1].y - u[2].y - u[3].y;
-            fz = v.z - u[0].z - u[1].z - u[2].z - u[3].z;
-        }
-        f[j] = fx; f[TS + j] = fy; f[2 * TS + j] = fz;
-    }
+template <typename R> struct DenseShape {
+    static constexpr bool F = sizeof(R) == 4;
+    static constexpr int NT = F ? 256 : 512;          // threads per block
+    static constexpr int BPS = F ? 2 : 1;             // blocks per SM
+    static constexpr int TPB = F ? 4 : 8;             // most tiles per block
+    static constexpr int NBUF = 2;                    // half-tile buffers per block
+    static constexpr int HR = TS / 2;                 // rows per buffer
+    static constexpr int CPR = 16 / (int)sizeof(R);  // entries per 16-byte piece
+    static constexpr int LDT = TS + CPR;             // padded row
+    static constexpr int UB = HR * LDT;               // entries per buffer
+    static constexpr int RP = NT / HR;                // threads per row (row products)
+    static constexpr int CP = NT / TS;                // threads per column (column products)
+    // dynamic shared memory: buffers, f cache (2 TPB bands x 3 x TS), row
+    // partials (2 x RP x 3 x HR), column partials (CP x 3 x TS)
+    static constexpr size_t SMEM = sizeof(R) * ((size_t)NBUF * UB + 2 * TPB * 3 * TS + 2 * RP * 3 * HR + CP * 3 * TS);
+};
+
+// The grid of the dense launch for T tiles on nsm SMs.
+template <typename R> int dense_grid(int tiles, int nsm) {
+    using D = DenseShape<R>;
+    const int g = std::max(D::BPS * nsm, (tiles + D::TPB - 1) / D::TPB);
+    return std::min(g, tiles);
 }
 
-template <typename R, int NT>
-__global__ void __launch_bounds__(NT) k_dense(DevSolve<R> S, const V4<R> *rhs, V4<R> *r) {
-    constexpr int NW = NT / 32;
-    constexpr int RPW = TS / NW;  // rows per warp
-    // the tile (TS x TS entries, dynamic shared memory) arrives by one bulk
-    // copy issued before the wait on the previous level; one lane holds
-    // TS / 32 = 4 consecutive columns of a row
+// Thread 0: requests half tile u of the block (tile t0 + u / 2, rows from
+// HR (u & 1)) into buffer u % NBUF.
+template <typename R>
+__device__ __forceinline__ void dense_issue(const DevSolve<R> &S, int t0, int u, R *buf, uint64_t *bar) {
+    using D = DenseShape<R>;
+    const int4 a = S.dense_tiles[3 * (size_t)(t0 + (u >> 1))];
+    const long long off = ((long long)(unsigned)a.x | ((long long)a.y << 32)) + (long long)(u & 1) * D::UB;
+    static_assert(D::HR * 2 == TS, "a unit is half a tile");
+    bulk_load_issue(bar + u % D::NBUF, buf + (size_t)(u % D::NBUF) * D::UB, S.dense_inv + off,
+                    (uint32_t)(D::UB * sizeof(R)));
+}
+
+template <typename R>
+__global__ void __launch_bounds__(DenseShape<R>::NT, DenseShape<R>::BPS)
+    k_dense(DevSolve<R> S, const V4<R> *rhs, V4<R> *r) {
+    using D = DenseShape<R>;
+    using VT = typename Vec16<R>::T;
+    constexpr int NT = D::NT, HR = D::HR, CPR = D::CPR, LDT = D::LDT, NBUF = D::NBUF;
+    constexpr int RP = D::RP, CP = D::CP, TPB = D::TPB;
+    constexpr int NE = (2 * TPB * TS + NT - 1) / NT;  // f entries gathered per thread
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    R *tile = reinterpret_cast<R *>(smem_raw);
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ __align__(16) R fJ[3 * TS], fI[3 * TS];
-    __shared__ __align__(16) R colpart[NW][3][TS];
-    __shared__ int colvJ[TS], colvI[TS];
-    __shared__ int4 bndJ[TS], bndI[TS];
-    __shared__ int lastJ, lastI;
-    const int4 *rec = S.dense_tiles + 3 * (size_t)blockIdx.x;
-    const int4 a = rec[0], b = rec[1], c = rec[2];
-    const long long off = (long long)(unsigned)a.x | ((long long)a.y << 32);
-    if (threadIdx.x == 0) {
-        bulk_bar_init(&bar);
-        bulk_load_issue(&bar, tile, S.dense_inv + off, (uint32_t)(TS * TS * sizeof(R)));
+    R *buf = reinterpret_cast<R *>(smem_raw);
+    R *fc = buf + (size_t)NBUF * D::UB;  // [2 TPB][3][TS]: f_J, f_I of each tile
+    R *rowp = fc + 2 * TPB * 3 * TS;     // [2][RP][3][HR]
+    R *colp = rowp + 2 * RP * 3 * HR;       // [CP][3][TS]
+    __shared__ __align__(8) uint64_t bar[NBUF];
+    __shared__ int lastI, lastJ;
+    const int tid = threadIdx.x;
+    const int T = S.n_dense_tiles, G = gridDim.x;
+    const int t0 = (int)((long long)blockIdx.x * T / G), t1 = (int)((long long)(blockIdx.x + 1) * T / G);
+    const int U = 2 * (t1 - t0);  // half tiles
+    if (tid == 0) {
+        for (int k = 0; k < NBUF; ++k) bulk_bar_init(&bar[k]);
+        for (int u = 0; u < NBUF && u < U; ++u) dense_issue<R>(S, t0, u, buf, bar);
     }
-    const int I = a.z, J = a.w;
-    const int n = b.x, band0 = b.y, nb = b.z, tc0 = b.w;
-    const bool diag = I == J;
-    const int rI = I * TS, cJ = J * TS;
-    const int nI = min(TS, n - rI), nJ = min(TS, n - cJ);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // before the wait: the index data of the gathers (nothing the solve writes)
-    const int *tcol = S.dense_col + tc0;
-    const int *bptr = S.dense_bptr + c.x;
-    for (int j = threadIdx.x; j < 2 * TS; j += NT) {
-        const bool jside = j < TS;
-        const int jj = jside ? j : j - TS, col = (jside ? cJ : rI) + jj;
-        if (!jside && diag) continue;
-        if (jj >= (jside ? nJ : nI)) continue;
+    // before the wait: the gathers' index data (nothing the solve writes).
+    // Entry e: slot e / TS (2 k: f_J of tile t0 + k, 2 k + 1: its f_I), column e % TS
+    int colv[NE];
+    int4 bnd[NE];
+#pragma unroll
+    for (int q = 0; q < NE; ++q) {
+        const int e = tid + q * NT;
+        colv[q] = -1;
+        bnd[q] = make_int4(-1, -1, -1, -1);
+        if (e >= U * TS) continue;
+        const int slot = e / TS, j = e % TS;
+        const int4 *rec = S.dense_tiles + 3 * (size_t)(t0 + (slot >> 1));
+        const int4 a = rec[0], b = rec[1], c = rec[2];
+        const int B = (slot & 1) ? a.z : a.w;
+        const int col = B * TS + j;
+        if (col >= b.x) continue;
+        const int *bptr = S.dense_bptr + c.x;
         const int k0 = bptr[col], k1 = bptr[col + 1];
-        const int4 e = make_int4(k1 > k0 ? S.dense_bidx[k0] : -1, k1 > k0 + 1 ? S.dense_bidx[k0 + 1] : -1,
-                                 k1 > k0 + 2 ? S.dense_bidx[k0 + 2] : -1, k1 > k0 + 3 ? S.dense_bidx[k0 + 3] : -1);
-        if (jside) { colvJ[jj] = tcol[col]; bndJ[jj] = e; }
-        else { colvI[jj] = tcol[col]; bndI[jj] = e; }
+        colv[q] = S.dense_col[b.w + col];
+        bnd[q] = make_int4(k1 > k0 ? S.dense_bidx[k0] : -1, k1 > k0 + 1 ? S.dense_bidx[k0 + 1] : -1,
+                           k1 > k0 + 2 ? S.dense_bidx[k0 + 2] : -1, k1 > k0 + 3 ? S.dense_bidx[k0 + 3] : -1);
     }
     pdl_trigger();
     pdl_wait();
-    __syncthreads();
-    dense_gather<R>(S, rhs, colvJ, bndJ, nJ, fJ, threadIdx.x, NT);
-    if (!diag) dense_gather<R>(S, rhs, colvI, bndI, nI, fI, threadIdx.x, NT);
-    if (!bulk_load_finish(&bar, 0u, S.err, S.wait_polls, true)) return;  // (its barrier also orders f)
-    const R *fi = diag ? fJ : fI;
-    // this lane's columns of f_J
-    R fj[3][4];
+    // f = q minus the (<= 4) update entries from below T, zero past n
 #pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-        fj[0][cc] = fJ[4 * lane + cc];
-        fj[1][cc] = fJ[TS + 4 * lane + cc];
-        fj[2][cc] = fJ[2 * TS + 4 * lane + cc];
-    }
-    R ca[3][4];  // column products of this lane's columns over the warp's rows
+    for (int q = 0; q < NE; ++q) {
+        const int e = tid + q * NT;
+        if (e >= U * TS) continue;
+        R fx = R(0), fy = R(0), fz = R(0);
+        if (colv[q] >= 0) {
+            const int4 eb = bnd[q];
+            const V4<R> v = ld_cg(rhs + colv[q]);
+            V4<R> u4[4];
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) ca[k][cc] = R(0);
-    V4<R> *part = S.dense_part + (size_t)band0 * S.dense_nct_max * TS;
-    for (int i = warp * RPW; i < warp * RPW + RPW; ++i) {
-        const R *row = tile + (size_t)i * TS + 4 * lane;
-        R q[4];
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) q[cc] = row[cc];
-        R px = R(0), py = R(0), pz = R(0);
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-            px += q[cc] * fj[0][cc];
-            py += q[cc] * fj[1][cc];
-            pz += q[cc] * fj[2][cc];
+            for (int k = 0; k < 4; ++k) u4[k].x = u4[k].y = u4[k].z = R(0);
+            if (eb.x >= 0) u4[0] = ld_cg(S.u + eb.x);
+            if (eb.y >= 0) u4[1] = ld_cg(S.u + eb.y);
+            if (eb.z >= 0) u4[2] = ld_cg(S.u + eb.z);
+            if (eb.w >= 0) u4[3] = ld_cg(S.u + eb.w);
+            fx = v.x - u4[0].x - u4[1].x - u4[2].x - u4[3].x;
+            fy = v.y - u4[0].y - u4[1].y - u4[2].y - u4[3].y;
+            fz = v.z - u4[0].z - u4[1].z - u4[2].z - u4[3].z;
         }
-        px = group_sum<R, 32>(px);
-        py = group_sum<R, 32>(py);
-        pz = group_sum<R, 32>(pz);
-        if (lane == 0 && i < nI) {
-            V4<R> o;
-            o.x = px; o.y = py; o.z = pz; o.w = R(0);
-            part[((size_t)I * S.dense_nct_max + J) * TS + i] = o;  // band I, slot J
+        R *f = fc + (size_t)(e / TS) * 3 * TS + e % TS;
+        f[0] = fx; f[TS] = fy; f[2 * TS] = fz;
+    }
+    // row products: thread (row ri, part rp) takes TS / RP columns of its row;
+    // column products: thread (column cj, part cq) takes HR / CP rows of the
+    // half tile, summed over both halves
+    const int ri = tid % HR, rp = tid / HR;
+    const int cj = tid % TS, cq = tid / TS;
+    constexpr int RCOLS = TS / RP, CROWS = HR / CP;
+    R ca0 = R(0), ca1 = R(0), ca2 = R(0);
+    for (int u = 0; u < U; ++u) {
+        const int nbuf = u % NBUF;
+        // (the barrier inside also orders the f gather before the first use)
+        if (!bulk_load_finish(&bar[nbuf], (uint32_t)((u / NBUF) & 1), S.err, S.wait_polls, true)) {
+            if (tid == 0)
+                for (int v = u + 1; v < u + NBUF && v < U; ++v)
+                    if (!bulk_load_wait(&bar[v % NBUF], (uint32_t)((v / NBUF) & 1), kDrainPolls)) atomicOr(S.err, 4u);
+            return;
+        }
+        const int k = u >> 1, h = u & 1;
+        const int4 *rec = S.dense_tiles + 3 * (size_t)(t0 + k);
+        const int4 a = rec[0], b = rec[1];
+        const int I = a.z, J = a.w;
+        const int n = b.x, band0 = b.y, nb = b.z, tc0 = b.w;
+        const bool diag = I == J;
+        const int nI = min(TS, n - I * TS), nJ = min(TS, n - J * TS);
+        const R *tile = buf + (size_t)nbuf * D::UB;
+        const R *fJ = fc + (size_t)(2 * k) * 3 * TS, *fI = fc + (size_t)(2 * k + 1) * 3 * TS;
+        {
+            const R *row = tile + (size_t)ri * LDT + rp * RCOLS;
+            R px = R(0), py = R(0), pz = R(0);
+#pragma unroll
+            for (int c = 0; c < RCOLS; c += CPR) {
+                const VT sv = *reinterpret_cast<const VT *>(row + c);
+                const R *s4 = reinterpret_cast<const R *>(&sv);
+                const int j0 = rp * RCOLS + c;
+                const VT fx = *reinterpret_cast<const VT *>(fJ + j0);
+                const VT fy = *reinterpret_cast<const VT *>(fJ + TS + j0);
+                const VT fz = *reinterpret_cast<const VT *>(fJ + 2 * TS + j0);
+                const R *gx = reinterpret_cast<const R *>(&fx);
+                const R *gy = reinterpret_cast<const R *>(&fy);
+                const R *gz = reinterpret_cast<const R *>(&fz);
+#pragma unroll
+                for (int e = 0; e < CPR; ++e) {
+                    px += s4[e] * gx[e];
+                    py += s4[e] * gy[e];
+                    pz += s4[e] * gz[e];
+                }
+            }
+            R *rw = rowp + (size_t)(u & 1) * RP * 3 * HR + (size_t)rp * 3 * HR + ri;
+            rw[0] = px; rw[HR] = py; rw[2 * HR] = pz;
         }
         if (!diag) {
-            const R gx = fi[i], gy = fi[TS + i], gz = fi[2 * TS + i];
+            const R *col = tile + cj;
+#pragma unroll 4
+            for (int i0 = cq * CROWS; i0 < cq * CROWS + CROWS; i0 += CPR) {
+                const int ig = h * HR + i0;
+                const VT gx = *reinterpret_cast<const VT *>(fI + ig);
+                const VT gy = *reinterpret_cast<const VT *>(fI + TS + ig);
+                const VT gz = *reinterpret_cast<const VT *>(fI + 2 * TS + ig);
+                const R *hx = reinterpret_cast<const R *>(&gx);
+                const R *hy = reinterpret_cast<const R *>(&gy);
+                const R *hz = reinterpret_cast<const R *>(&gz);
 #pragma unroll
-            for (int cc = 0; cc < 4; ++cc) {
-                ca[0][cc] += q[cc] * gx;
-                ca[1][cc] += q[cc] * gy;
-                ca[2][cc] += q[cc] * gz;
+                for (int e = 0; e < CPR; ++e) {
+                    const R sij = col[(size_t)(i0 + e) * LDT];
+                    ca0 += sij * hx[e];
+                    ca1 += sij * hy[e];
+                    ca2 += sij * hz[e];
+                }
             }
         }
-    }
-    if (!diag) {
-        // the warps' column products, added in warp order: band J, slot I
+        __syncthreads();  // the buffer is read; the row partials are written
+        if (tid == 0 && u + NBUF < U) dense_issue<R>(S, t0, u + NBUF, buf, bar);
+        V4<R> *part = S.dense_part + (size_t)band0 * S.dense_nct_max * TS;
+        if (tid < HR && h * HR + tid < nI) {
+            const R *rw = rowp + (size_t)(u & 1) * RP * 3 * HR + tid;
+            R sx = R(0), sy = R(0), sz = R(0);
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
+            for (int p = 0; p < RP; ++p) {
+                sx += rw[(size_t)p * 3 * HR];
+                sy += rw[(size_t)p * 3 * HR + HR];
+                sz += rw[(size_t)p * 3 * HR + 2 * HR];
+            }
+            V4<R> o;
+            o.x = sx; o.y = sy; o.z = sz; o.w = R(0);
+            part[((size_t)I * S.dense_nct_max + J) * TS + h * HR + tid] = o;  // band I, slot J
+        }
+        if (h == 0) continue;
+        // the tile is complete: its column products (band J, slot I), then
+        // the arrivals on band I (and band J)
+        if (!diag) {
+            R *cw = colp + (size_t)cq * 3 * TS + cj;
+            cw[0] = ca0; cw[TS] = ca1; cw[2 * TS] = ca2;
+            ca0 = ca1 = ca2 = R(0);
+            __syncthreads();
+            if (tid < nJ) {
+                R sx = R(0), sy = R(0), sz = R(0);
 #pragma unroll
-            for (int cc = 0; cc < 4; ++cc) colpart[warp][k][4 * lane + cc] = ca[k][cc];
+                for (int p = 0; p < CP; ++p) {
+                    sx += colp[(size_t)p * 3 * TS + tid];
+                    sy += colp[(size_t)p * 3 * TS + TS + tid];
+                    sz += colp[(size_t)p * 3 * TS + 2 * TS + tid];
+                }
+                V4<R> o;
+                o.x = sx; o.y = sy; o.z = sz; o.w = R(0);
+                part[((size_t)J * S.dense_nct_max + I) * TS + tid] = o;
+            }
+        }
         __syncthreads();
-        for (int j = threadIdx.x; j < nJ; j += NT) {
-            R sx = R(0), sy = R(0), sz = R(0);
-#pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                sx += colpart[w][0][j];
-                sy += colpart[w][1][j];
-                sz += colpart[w][2][j];
-            }
-            V4<R> o;
-            o.x = sx; o.y = sy; o.z = sz; o.w = R(0);
-            part[((size_t)J * S.dense_nct_max + I) * TS + j] = o;
+        if (tid == 0) {
+            __threadfence();  // release: this tile's partials before the counts
+            lastI = atomicAdd(S.dense_cnt + band0 + I, 1) == nb - 1;
+            lastJ = diag ? 0 : (atomicAdd(S.dense_cnt + band0 + J, 1) == nb - 1);
+            if (lastI || lastJ) __threadfence();  // acquire, ordered for the block by the barrier below
         }
-    }
-    // arrivals: band I (and band J); the nb-th contribution to a band adds
-    // its slots in order
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();  // release: this tile's partials before the counts
-        lastI = atomicAdd(S.dense_cnt + band0 + I, 1) == nb - 1;
-        lastJ = diag ? 0 : (atomicAdd(S.dense_cnt + band0 + J, 1) == nb - 1);
-        if (lastI || lastJ) __threadfence();  // acquire, ordered for the block by the barrier below
-    }
-    __syncthreads();
-    for (int side = 0; side < 2; ++side) {
-        const bool go = side == 0 ? lastI : lastJ;
-        if (!go) continue;
-        const int B = side == 0 ? I : J, nB = side == 0 ? nI : nJ;
-        const V4<R> *slots = part + (size_t)B * S.dense_nct_max * TS;
-        for (int i = threadIdx.x; i < nB; i += NT) {
-            R sx = R(0), sy = R(0), sz = R(0);
-            for (int t = 0; t < nb; ++t) {
-                const V4<R> p = ld_cg(slots + (size_t)t * TS + i);
-                sx += p.x; sy += p.y; sz += p.z;
+        __syncthreads();
+        const int *tcol = S.dense_col + tc0;
+        for (int side = 0; side < 2; ++side) {
+            const bool go = side == 0 ? lastI : lastJ;
+            if (!go) continue;
+            const int Bd = side == 0 ? I : J, nB = side == 0 ? nI : nJ;
+            const V4<R> *slots = part + (size_t)Bd * S.dense_nct_max * TS;
+            for (int i = tid; i < nB; i += NT) {
+                R sx = R(0), sy = R(0), sz = R(0);
+                for (int t = 0; t < nb; ++t) {
+                    const V4<R> p = ld_cg(slots + (size_t)t * TS + i);
+                    sx += p.x; sy += p.y; sz += p.z;
+                }
+                V4<R> o;
+                o.x = sx; o.y = sy; o.z = sz; o.w = R(0);
+                r[tcol[Bd * TS + i]] = o;
             }
-            V4<R> o;
-            o.x = sx; o.y = sy; o.z = sz; o.w = R(0);
-            r[tcol[B * TS + i]] = o;
+            if (tid == 0) S.dense_cnt[band0 + Bd] = 0;
         }
-        if (threadIdx.x == 0) S.dense_cnt[band0 + B] = 0;
     }
 }
 
@@ -812,16 +900,16 @@ void launch_sweeps(const DevSolve<R> &s, const V4<R> *q, V4<R> *z, V4<R> *r) {
     }
     if (s.n_dense_tiles > 0) {
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)s.n_dense_tiles);
-        cfg.blockDim = dim3(256);
-        cfg.dynamicSmemBytes = (size_t)TS * TS * sizeof(R);
+        cfg.gridDim = dim3((unsigned)dense_grid<R>(s.n_dense_tiles, s.n_sm));
+        cfg.blockDim = dim3(DenseShape<R>::NT);
+        cfg.dynamicSmemBytes = DenseShape<R>::SMEM;
         cfg.stream = st_of(s);
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
         attr[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = attr;
         cfg.numAttrs = s.pdl ? 1 : 0;
-        cudaLaunchKernelEx(&cfg, k_dense<R, 256>, s, q, r);
+        cudaLaunchKernelEx(&cfg, k_dense<R>, s, q, r);
     }
     for (int l = L - 1; l >= 0; --l) {
         if (s.bwd_lvl_cnt[l] <= 0) continue;
@@ -849,8 +937,8 @@ cudaError_t prepare_nt() {
 template <typename R> size_t solve_block_smem(int qcap, int ld) { return sweep_smem<R>(qcap, ld); }
 
 template <typename R> cudaError_t solve_prepare() {
-    cudaError_t e = cudaFuncSetAttribute(k_dense<R, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(TS * TS * sizeof(R)));
+    cudaError_t e = cudaFuncSetAttribute(k_dense<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)DenseShape<R>::SMEM);
     if (e == cudaSuccess) e = prepare_nt<R, 128>();
     if (e == cudaSuccess) e = prepare_nt<R, 256>();
     if (e == cudaSuccess) e = prepare_nt<R, 512>();
