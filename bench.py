@@ -584,7 +584,8 @@ def run_convergence(args, stream):
     """Eq. RelativeError of one frame of the twisting spline bar (80x40x40 at
     half resolution, 96,000 tets, FP64): (g(x_k) - g(x*)) / (g(x_0) - g(x*))
     after 10, 30 and 60 iterations for projective dynamics (m = 0), L-BFGS
-    with m = 2, 5, 8, 16 and the Chebyshev direction (S = 10, rho = 0.99),
+    with m = 2, 5, 8, 16, 100 and the Chebyshev direction (S = 10, rho
+    estimated from a projective-dynamics run, and rho = 0.99),
     with the time per iteration; x* is a 500-iteration L-BFGS (m = 16) run
     (the paper's Newton reference is not built on the GPU)."""
     import torch
@@ -620,6 +621,7 @@ def run_convergence(args, stream):
                                "iterations of a 150-iteration projective-dynamics (m = 0) step"
     for name, kw in (("pd_m0", dict(history_m=0)), ("lbfgs_m2", dict(history_m=2)),
                      ("lbfgs_m5", dict(history_m=5)), ("lbfgs_m8", dict(history_m=8)),
+                     ("lbfgs_m16", dict(history_m=16)), ("lbfgs_m100", dict(history_m=100)),
                      ("chebyshev_S10_rho_estimated", dict(direction=1, cheb_S=10, cheb_rho=rho_est)),
                      ("chebyshev_S10_rho0.99", dict(direction=1, cheb_S=10, cheb_rho=0.99))):
         st, dt = run(60, **kw)

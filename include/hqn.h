@@ -133,7 +133,13 @@ typedef struct {
     double  x_end;
     double  gravity[3];   /* [m/s^2], f_ext = m_v * gravity                           */
     int32_t iters;        /* quasi-Newton iterations per step; paper: 10 (Table 1)    */
-    int32_t history_m;    /* L-BFGS window; paper: 5 (Sec. 4.2); 0 = Alg. 1 direction  */
+    int32_t history_m;    /* L-BFGS window, 0..HQN_MAX_HISTORY; paper: 5 (Sec. 4.2), up
+                             to 100 in its convergence study (Sec. 5); 0 = Alg. 1
+                             direction.  Windows above 16 pairs keep the two
+                             loops' scalars in a device array of (m + 1)^2 +
+                             5 (m + 1) doubles per simulation and form the slot
+                             products in chunks of 16 slots (two more launches
+                             after the gather and after the solve)          */
     int32_t ls_max;       /* line-search trials before giving up (paper is silent)    */
     int32_t precision;    /* hqn_precision                                            */
     int32_t leaf_size;    /* max vertices of a nested-dissection leaf (0 = default:
@@ -247,7 +253,7 @@ typedef struct {
     const char *tune_cache;
 } hqn_params;
 
-#define HQN_MAX_HISTORY 16
+#define HQN_MAX_HISTORY 128
 #define HQN_MAX_ITERS   512
 
 /* Per-step record of the most recent step taken by sim_step. */

@@ -153,6 +153,7 @@ struct Sim final : SimBase {
         if (solve_block_smem<R>(item_kb * 1024 / (int)sizeof(R), max_ld) > (size_t)SOLVE_MAX_SMEM)
             return fail(HQN_ERR_UNSUPPORTED, "a separator is too large for the sweeps' shared memory");
         CK(solve_prepare<R>());
+        if (p.history_m > kShortHist) CK(long_hist_prepare<R>(p.history_m));
         if (st == nullptr) {  // the legacy default stream cannot be captured: use an own stream
             CK(cudaStreamCreateWithFlags(&own_stream, cudaStreamNonBlocking));
             st = own_stream;
@@ -263,8 +264,16 @@ struct Sim final : SimBase {
         // per-block partials: up to 3 + 3 (m + 1) sums (gather with a history
         // push), m + 2 (caller-given history rows), m + 1 or 4 (direction),
         // 16 (line-search pass)
-        if ((rc = alloc(ds.part_g, (size_t)(3 + 3 * (HQN_MAX_HISTORY + 1)) * nvb))) return rc;
-        if ((rc = alloc(ds.part_v, (size_t)(HQN_MAX_HISTORY + 1) * nvb))) return rc;
+        if ((rc = alloc(ds.part_g, (size_t)(3 + 3 * (kShortHist + 1)) * nvb))) return rc;
+        if ((rc = alloc(ds.part_v, (size_t)(kShortHist + 1) * nvb))) return rc;
+        // a long window: its scalars per simulation, and the partials of its
+        // slot products (3 LH_CHUNK per chunk and block)
+        double *lh_all = nullptr;
+        if (m > kShortHist) {
+            const size_t nch = (size_t)(m + 1 + LH_CHUNK - 1) / LH_CHUNK;
+            if ((rc = alloc(lh_all, LongHist::doubles(m) * (size_t)ns))) return rc;
+            if ((rc = alloc(ds.part_l, nch * 3 * LH_CHUNK * (size_t)nvb))) return rc;
+        }
         if ((rc = alloc(ds.part_ls, (size_t)16 * ntb))) return rc;
         if ((rc = alloc(ds.batch_ticket, 4))) return rc;
         if ((rc = alloc(d_ctl, ns))) return rc;
@@ -326,6 +335,7 @@ struct Sim final : SimBase {
             D.tb0 = tb0[k]; D.ntb = (s.T + TBS - 1) / TBS;
             D.ring0 = (long long)(m + 1) * v0[k];
             D.ctl = d_ctl + k;
+            D.lh = lh_all ? lh_all + LongHist::doubles(m) * (size_t)k : nullptr;
             for (int b = 0; b < D.nvb; ++b) vblk[D.vb0 + b] = k;
             for (int b = 0; b < D.ntb; ++b) tblk[D.tb0 + b] = k;
         }
@@ -875,7 +885,10 @@ struct Sim final : SimBase {
     // x_{k+1} = x_k + alpha d once the line search has accepted alpha: the
     // gather of its gradient with the history push (the corners are left by
     // the fused first trial or by the pass that accepted).
-    void enqueue_accept(CondHandles h, cudaStream_t s) { launch_gather(ds, G_ITER, h, s); }
+    void enqueue_accept(CondHandles h, cudaStream_t s) {
+        launch_gather(ds, G_ITER, h, s);
+        if (prm.history_m > kShortHist) launch_long_hist(ds, LD_PUSH, 0, s, 0);
+    }
     // One pass of the line search, then the gradient at the accepted point of
     // the simulations this pass accepted.
     void enqueue_ls_pass(CondHandles h, cudaStream_t s) {
@@ -1106,7 +1119,10 @@ struct Sim final : SimBase {
             CK(cudaMemcpyAsync(&d_ctl[k].active, &v[2], sizeof(int), cudaMemcpyHostToDevice, st));
             CK(cudaStreamSynchronize(st));
         }
-        for (int a = 0; a < np; ++a) launch_hist_row(ds, a, st, hdesc[0].nvb);
+        for (int a = 0; a < np; ++a) {
+            if (m > kShortHist) launch_long_hist(ds, LD_ROW, a, st, hdesc[0].nvb);
+            else launch_hist_row(ds, a, st, hdesc[0].nvb);
+        }
         enqueue_direction(CondHandles{0, 0, 0}, 0, st);
         CK(cudaGetLastError());
         if ((rc = read_ctl())) return rc;

@@ -40,6 +40,12 @@ struct MatDev {
     R fd[3];            // its unit rest direction d
 };
 
+// History windows up to this many pairs keep the scalars of Alg. 2's two
+// loops in the control block and the vectors' per-slot terms in registers;
+// longer windows (up to HQN_MAX_HISTORY) keep them in a device array of
+// their own (SimDesc::lh) and reduce over the slots in chunks.
+constexpr int kShortHist = 16;
+
 // Control block of one simulation's step, resident on the device.  Every
 // scalar decision of Alg. 1 / Alg. 2 (inner products, alpha, Armijo, history
 // bookkeeping) is taken here, by the last block of the kernel that produces
@@ -55,18 +61,21 @@ struct Ctl {
     double ls_a[3];    // inertia term along d: I(alpha) = a0 + a1 alpha + a2 alpha^2
     double pcg_rz, pcg_alpha, pcg_beta;  // Jacobi-PCG scalars (iterative A0^{-1})
     double cheb_omega; // Chebyshev weight omega_k of Alg. 3
-    double zeta[HQN_MAX_HISTORY + 1];  // first-loop coefficients by age (0 = newest)
-    double coef[HQN_MAX_HISTORY + 1];  // second-loop coefficients zeta - eta by age
-    double rho[HQN_MAX_HISTORY + 1];   // tr(t^T s) by ring slot
-    double sg[HQN_MAX_HISTORY + 1];    // s_a^T grad_k by ring slot
-    double tr0[HQN_MAX_HISTORY + 1];   // t_a^T r0 by ring slot (r0 = A0^{-1} q)
-    double gram[HQN_MAX_HISTORY + 1][HQN_MAX_HISTORY + 1];  // s_a^T t_b by ring slots
+    // (windows of m <= kShortHist pairs; longer ones use SimDesc::lh)
+    double zeta[kShortHist + 1];  // first-loop coefficients by age (0 = newest)
+    double coef[kShortHist + 1];  // second-loop coefficients zeta - eta by age
+    double rho[kShortHist + 1];   // tr(t^T s) by ring slot
+    double sg[kShortHist + 1];    // s_a^T grad_k by ring slot
+    double tr0[kShortHist + 1];   // t_a^T r0 by ring slot (r0 = A0^{-1} q)
+    double gram[kShortHist + 1][kShortHist + 1];  // s_a^T t_b by ring slots
     double iter_g[HQN_MAX_ITERS];
     int iter_trials[HQN_MAX_ITERS];
     int k;             // 1-based iteration index of x_k
     int trials;        // trials of the current line search
     int count;         // history pairs held (<= m)
     int head;          // ring slot of the newest pair (ring has m + 1 slots)
+    int hist_w;        // ring slot of the last pair pushed (long windows)
+    int hist_keep;     // that pair was kept (long windows)
     int stop;          // the step's iterations have ended early
     int status;        // worst status of the step (HQN_OK or a warning)
     int accepted;      // the last trial passed the Armijo test

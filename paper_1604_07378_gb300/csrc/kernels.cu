@@ -481,7 +481,7 @@ __device__ __forceinline__ R dotr(const V4<R> &a, const V4<R> &b) {
 // The history scalars the recursions need, staged in shared memory by the
 // last block of a simulation: the control block lives in global memory, and a
 // recursion run on it directly would pay a memory round trip per step.
-constexpr int MH = HQN_MAX_HISTORY + 1;
+constexpr int MH = kShortHist + 1;
 struct HistSmem {
     double gram[MH][MH];  // s_a^T t_b by ring slots
     double rho[MH], rinv[MH], sg[MH], tr0[MH], zeta[MH], coef[MH];  // rinv = 1 / rho
@@ -538,8 +538,13 @@ __device__ __forceinline__ void coef_recursion(HistSmem &h, int m) {
 // loop of Alg. 2 on scalars and ends the simulation's iterations when its
 // count is reached or its line search gave up.  The collision terms active
 // at the gathered point (Sec. 4.3) add 2 w_v gap n to its gradient.
+// MP1 = 0: a long window (m > kShortHist): the pair is pushed and kept or
+// dropped here, its slot products and the first loop follow in
+// launch_long_hist.
 template <typename R, int MP1>
 __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandles h) {
+    constexpr bool LONG = MP1 == 0;
+    constexpr int MPA = LONG ? 1 : MP1;  // register arrays
     const SimDesc<R> &D = sim_desc(s, s.vblk_sim);
     Ctl *ctl = D.ctl;
     const int m = s.m;
@@ -574,7 +579,7 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
             Xr = s.rest[gi];
             ul = s.u_cur[gi];
         }
-        V4<R> Sa[MP1], Ta[MP1];
+        V4<R> Sa[MPA], Ta[MPA];
         V4<R> *S = s.S + D.ring0, *Tt = s.Tt + D.ring0;
         const size_t n = (size_t)D.c.n;
         if (push) {
@@ -651,6 +656,18 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
             for (int k = 0; k < ND; ++k) dots[k] = sh[k];
         }
         // dots: rho, |s|^2, |t|^2, s_a^T t_w, s_w^T t_a, s_a^T grad
+        if constexpr (LONG) {
+            if (threadIdx.x == 0) {
+                keep = dots[0] > 1e-12 * sqrt(dots[1] * dots[2]);
+                ctl->hist_w = w;
+                ctl->hist_keep = keep;
+                if (keep) {
+                    LongHist(D.lh, m).rho[w] = dots[0];
+                    ctl->head = w;
+                    ctl->count = ctl->count < m ? ctl->count + 1 : m;
+                }
+            }
+        } else {
         __shared__ HistSmem hs;
         hist_load(ctl, hs, m);
         if (threadIdx.x == 0) {
@@ -684,6 +701,7 @@ __global__ void __launch_bounds__(VBS) k_gather(DevSim<R> s, int mode, CondHandl
             ctl->rho[w] = hs.rho[w];
             ctl->head = hs.head;
             ctl->count = hs.count;
+        }
         }
     }
     if (threadIdx.x == 0) {
@@ -728,21 +746,30 @@ __global__ void __launch_bounds__(VBS) k_q(DevSim<R> s) {
     // the order p = 0, 1, ...
     const V4<R> g = s.gk[gi];
     const V4<R> *Tt = s.Tt + D.ring0;
-    R z[MP1];
-    V4<R> t[MP1];
-#pragma unroll
-    for (int p = 0; p < MP1; ++p)
-        if (p < count) {
-            z[p] = (R)ctl->zeta[p];
-            t[p] = Tt[(size_t)ring_slot(head, p, m) * D.c.n + i];
-        }
     V4<R> q;
     q.x = -g.x; q.y = -g.y; q.z = -g.z; q.w = R(0);
-#pragma unroll
-    for (int p = 0; p < MP1; ++p)
-        if (p < count) {
-            q.x -= z[p] * t[p].x; q.y -= z[p] * t[p].y; q.z -= z[p] * t[p].z;
+    if constexpr (MP1 == 0) {  // a long window: the slots streamed one by one
+        const double *zeta = LongHist(D.lh, m).zeta;
+        for (int p = 0; p < count; ++p) {
+            const R zp = (R)zeta[p];
+            const V4<R> tp = Tt[(size_t)ring_slot(head, p, m) * D.c.n + i];
+            q.x -= zp * tp.x; q.y -= zp * tp.y; q.z -= zp * tp.z;
         }
+    } else {
+        R z[MP1];
+        V4<R> t[MP1];
+#pragma unroll
+        for (int p = 0; p < MP1; ++p)
+            if (p < count) {
+                z[p] = (R)ctl->zeta[p];
+                t[p] = Tt[(size_t)ring_slot(head, p, m) * D.c.n + i];
+            }
+#pragma unroll
+        for (int p = 0; p < MP1; ++p)
+            if (p < count) {
+                q.x -= z[p] * t[p].x; q.y -= z[p] * t[p].y; q.z -= z[p] * t[p].z;
+            }
+    }
     s.q[gi] = q;
 }
 
@@ -820,19 +847,28 @@ __global__ void __launch_bounds__(VBS) k_dir_final(DevSim<R> s, CondHandles h, i
         V4<R> dd = s.d[gi];
         const V4<R> g = s.gk[gi], x = s.xk[gi], yy = s.y[gi];
         const R mh = s.mh2[gi];
-        R c[MP1];
-        V4<R> sv[MP1];
-#pragma unroll
-        for (int p = 0; p < MP1; ++p)
-            if (p < count) {
-                c[p] = (R)ctl->coef[p];
-                sv[p] = S[(size_t)ring_slot(head, p, m) * D.c.n + i];
+        if constexpr (MP1 == 0) {  // a long window: the slots streamed one by one
+            const double *coef = LongHist(D.lh, m).coef;
+            for (int p = 0; p < count; ++p) {
+                const R cp = (R)coef[p];
+                const V4<R> sp = S[(size_t)ring_slot(head, p, m) * D.c.n + i];
+                dd.x += cp * sp.x; dd.y += cp * sp.y; dd.z += cp * sp.z;
             }
+        } else {
+            R c[MP1];
+            V4<R> sv[MP1];
 #pragma unroll
-        for (int p = 0; p < MP1; ++p)
-            if (p < count) {
-                dd.x += c[p] * sv[p].x; dd.y += c[p] * sv[p].y; dd.z += c[p] * sv[p].z;
-            }
+            for (int p = 0; p < MP1; ++p)
+                if (p < count) {
+                    c[p] = (R)ctl->coef[p];
+                    sv[p] = S[(size_t)ring_slot(head, p, m) * D.c.n + i];
+                }
+#pragma unroll
+            for (int p = 0; p < MP1; ++p)
+                if (p < count) {
+                    dd.x += c[p] * sv[p].x; dd.y += c[p] * sv[p].y; dd.z += c[p] * sv[p].z;
+                }
+        }
         V4<R> Xr = dd, ul = dd;
         if (D.c.ncol > 0) {
             Xr = s.rest[gi];
@@ -1130,7 +1166,7 @@ template <typename R>
 __global__ void __launch_bounds__(VBS) k_hist_row(DevSim<R> s, int a) {
     const SimDesc<R> &D = s.desc0;
     Ctl *ctl = D.ctl;
-    constexpr int NB = HQN_MAX_HISTORY + 2;
+    constexpr int NB = kShortHist + 2;
     double dots[NB];
 #pragma unroll
     for (int b = 0; b < NB; ++b) dots[b] = 0.0;
@@ -1170,6 +1206,148 @@ __global__ void __launch_bounds__(VBS) k_hist_row(DevSim<R> s, int a) {
     for (int p = threadIdx.x; p < count; p += VBS) ctl->zeta[p] = hs.zeta[p];
 }
 
+// ---------------------------------------------------------------- long history windows
+//
+// A window of m > kShortHist pairs keeps its scalars in LongHist (device
+// memory of its own) and forms the slot products of Alg. 2 in two launches:
+// k_ldots over (vertex blocks) x (chunks of LH_CHUNK slots), block partials
+// only, then k_lrec, one block per simulation, which adds each value's
+// partials in block order, updates the Gram matrix and scalars and runs a
+// loop's recursion on scalars column by column (after zeta_p / c_p is known,
+// every later term subtracts / adds its share in parallel; the first loop
+// adds its terms in the order of the short windows' recursion, the second
+// in the reverse order).
+
+template <typename R>
+__global__ void __launch_bounds__(VBS) k_ldots(DevSim<R> s, int mode, int a0) {
+    const SimDesc<R> &D = mode == LD_ROW ? s.desc0 : sim_desc(s, s.vblk_sim);
+    const Ctl *ctl = D.ctl;
+    const int m = s.m, c0 = blockIdx.y * LH_CHUNK;
+    constexpr int NV = 3 * LH_CHUNK;
+    R dr[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dr[v] = R(0);
+    const int vb = mode == LD_ROW ? (int)blockIdx.x : (int)blockIdx.x - D.vb0;
+    const int i = vb * VBS + threadIdx.x;
+    const bool on = ctl->active && (mode != LD_R0 || ctl->count > 0);
+    if (on && i < D.c.nf) {
+        const size_t n = (size_t)D.c.n;
+        const V4<R> *S = s.S + D.ring0, *Tt = s.Tt + D.ring0;
+        const int w = mode == LD_PUSH ? ctl->hist_w : a0;
+        V4<R> f0 = mode == LD_R0 ? s.d[D.v0 + i] : S[(size_t)w * n + i];  // r0, or s_w / s_a0
+        V4<R> f1 = f0, g = f0;
+        if (mode == LD_PUSH) f1 = Tt[(size_t)w * n + i];                     // t_w
+        if (mode != LD_R0) g = s.gk[D.v0 + i];
+#pragma unroll
+        for (int a = 0; a < LH_CHUNK; ++a) {
+            const int sl = c0 + a;
+            if (sl > m) break;
+            const V4<R> ta = Tt[(size_t)sl * n + i];
+            if (mode == LD_R0) {
+                dr[a] = dotr(ta, f0);
+            } else {
+                const V4<R> sa = S[(size_t)sl * n + i];
+                if (mode == LD_PUSH) {
+                    dr[a] = dotr(sa, f1);
+                    dr[LH_CHUNK + a] = dotr(f0, ta);
+                } else {
+                    dr[a] = dotr(f0, ta);
+                }
+                dr[2 * LH_CHUNK + a] = dotr(sa, g);
+            }
+        }
+    }
+    double out[NV];
+    block_sum_r<VBS, NV, R>(dr, out);
+    if (threadIdx.x == 0) {
+        double *part = s.part_l + (size_t)blockIdx.y * NV * gridDim.x + blockIdx.x;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) part[(size_t)v * gridDim.x] = out[v];
+    }
+}
+
+// Dynamic shared memory of k_lrec for a window of m pairs.
+inline size_t lrec_smem(int m) {
+    const size_t L = (size_t)m + 1, nch = (L + LH_CHUNK - 1) / LH_CHUNK;
+    return sizeof(double) * (L * L + 3 * LH_CHUNK * nch + 3 * L);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_lrec(DevSim<R> s, int mode, int a0, int nbx) {
+    const SimDesc<R> &D = (mode == LD_ROW || s.nsims == 1) ? s.desc0 : s.desc[blockIdx.x];
+    Ctl *ctl = D.ctl;
+    if (!ctl->active) return;
+    const int m = s.m, L = m + 1, count = ctl->count, head = ctl->head;
+    if (mode == LD_R0 && count == 0) return;
+    constexpr int NV = 3 * LH_CHUNK;
+    const int nch = (L + LH_CHUNK - 1) / LH_CHUNK;
+    LongHist H(D.lh, m);
+    extern __shared__ double lsm[];
+    double *G = lsm;                          // L x L Gram matrix
+    double *tot = G + (size_t)L * L;          // nch x NV totals
+    double *acc = tot + (size_t)NV * nch;     // L running sums of the recursion
+    double *rinv = acc + L;                   // 1 / rho by ring slot
+    double *out = rinv + L;                   // zeta or c by age
+    const int tid = threadIdx.x, nt = blockDim.x;
+    // the simulation's partials, value by value, added in block order
+    const int vb0 = mode == LD_ROW ? 0 : D.vb0, nb = mode == LD_ROW ? nbx : D.nvb;
+    for (int v = tid; v < NV * nch; v += nt) {
+        const int slot = (v / NV) * LH_CHUNK + v % LH_CHUNK;
+        tot[v] = slot <= m ? strided_sum(s.part_l + (size_t)v * nbx + vb0, 0, nb, 1) : 0.0;
+    }
+    __syncthreads();
+    auto val = [&](int q, int slot) { return tot[(slot / LH_CHUNK) * NV + q * LH_CHUNK + slot % LH_CHUNK]; };
+    bool zeta_rec = false;
+    if (mode == LD_PUSH) {
+        const int w = ctl->hist_w;
+        if (ctl->hist_keep)
+            for (int a = tid; a <= m; a += nt) {
+                H.gram[(size_t)a * L + w] = val(0, a);  // s_a^T t_w
+                H.gram[(size_t)w * L + a] = val(1, a);  // s_w^T t_a
+            }
+        for (int a = tid; a <= m; a += nt) H.sg[a] = val(2, a);
+        zeta_rec = true;
+    } else if (mode == LD_R0) {
+        for (int a = tid; a <= m; a += nt) H.tr0[a] = val(0, a);
+    } else {
+        for (int b = tid; b < count; b += nt) {
+            H.gram[(size_t)a0 * L + b] = val(0, b);  // s_a0^T t_b
+            H.sg[b] = val(2, b);
+            if (b == a0) H.rho[a0] = val(0, b);
+        }
+        zeta_rec = a0 == count - 1;
+        if (!zeta_rec) return;
+    }
+    __syncthreads();  // (global writes of this block, read back below)
+    for (int e = tid; e < L * L; e += nt) G[e] = H.gram[e];
+    for (int a = tid; a < L; a += nt) rinv[a] = 1.0 / H.rho[a];
+    if (zeta_rec) {
+        // zeta_p = (-s_p^T grad - sum_{p' < p} zeta_p' s_p^T t_p') / rho_p, newest first
+        for (int p = tid; p < count; p += nt) acc[p] = -H.sg[ring_slot(head, p, m)];
+        __syncthreads();
+        for (int p = 0; p < count; ++p) {
+            const int sp = ring_slot(head, p, m);
+            const double z = acc[p] * rinv[sp];
+            for (int q = p + 1 + tid; q < count; q += nt) acc[q] -= z * G[(size_t)ring_slot(head, q, m) * L + sp];
+            if (tid == 0) out[p] = z;
+            __syncthreads();
+        }
+        for (int p = tid; p < count; p += nt) H.zeta[p] = out[p];
+    } else {
+        // c_p = zeta_p - (t_p^T r0 + sum_{p' > p} c_p' s_p'^T t_p) / rho_p, oldest first
+        for (int p = tid; p < count; p += nt) acc[p] = H.tr0[ring_slot(head, p, m)];
+        __syncthreads();
+        for (int p = count - 1; p >= 0; --p) {
+            const int sp = ring_slot(head, p, m);
+            const double c = H.zeta[p] - acc[p] * rinv[sp];
+            for (int q = tid; q < p; q += nt) acc[q] += c * G[(size_t)sp * L + ring_slot(head, q, m)];
+            if (tid == 0) out[p] = c;
+            __syncthreads();
+        }
+        for (int p = tid; p < count; p += nt) H.coef[p] = out[p];
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
@@ -1198,7 +1376,8 @@ template <typename R> void launch_gather(const DevSim<R> &s, int mode, CondHandl
     else if (m <= 3) k_gather<R, 4><<<s.nvb, VBS, 0, st>>>(s, mode, h);
     else if (m <= 5) k_gather<R, 6><<<s.nvb, VBS, 0, st>>>(s, mode, h);
     else if (m <= 8) k_gather<R, 9><<<s.nvb, VBS, 0, st>>>(s, mode, h);
-    else k_gather<R, HQN_MAX_HISTORY + 1><<<s.nvb, VBS, 0, st>>>(s, mode, h);
+    else if (m <= kShortHist) k_gather<R, kShortHist + 1><<<s.nvb, VBS, 0, st>>>(s, mode, h);
+    else k_gather<R, 0><<<s.nvb, VBS, 0, st>>>(s, mode, h);
 }
 template <typename R> void launch_q(const DevSim<R> &s, cudaStream_t st) {
     const int m = s.m;
@@ -1206,7 +1385,8 @@ template <typename R> void launch_q(const DevSim<R> &s, cudaStream_t st) {
     else if (m <= 3) k_q<R, 4><<<s.nvb, VBS, 0, st>>>(s);
     else if (m <= 5) k_q<R, 6><<<s.nvb, VBS, 0, st>>>(s);
     else if (m <= 8) k_q<R, 9><<<s.nvb, VBS, 0, st>>>(s);
-    else k_q<R, HQN_MAX_HISTORY + 1><<<s.nvb, VBS, 0, st>>>(s);
+    else if (m <= kShortHist) k_q<R, kShortHist + 1><<<s.nvb, VBS, 0, st>>>(s);
+    else k_q<R, 0><<<s.nvb, VBS, 0, st>>>(s);
 }
 template <typename R> void launch_r0_dots(const DevSim<R> &s, cudaStream_t st) {
     const int m = s.m;
@@ -1214,7 +1394,8 @@ template <typename R> void launch_r0_dots(const DevSim<R> &s, cudaStream_t st) {
     if (m <= 3) k_r0_dots<R, 4><<<s.nvb, VBS, 0, st>>>(s);
     else if (m <= 5) k_r0_dots<R, 6><<<s.nvb, VBS, 0, st>>>(s);
     else if (m <= 8) k_r0_dots<R, 9><<<s.nvb, VBS, 0, st>>>(s);
-    else k_r0_dots<R, HQN_MAX_HISTORY + 1><<<s.nvb, VBS, 0, st>>>(s);
+    else if (m <= kShortHist) k_r0_dots<R, kShortHist + 1><<<s.nvb, VBS, 0, st>>>(s);
+    else launch_long_hist(s, LD_R0, 0, st, 0);
 }
 template <typename R>
 void launch_direction_final(const DevSim<R> &s, CondHandles h, int set_nd, cudaStream_t st) {
@@ -1223,7 +1404,8 @@ void launch_direction_final(const DevSim<R> &s, CondHandles h, int set_nd, cudaS
     else if (m <= 3) k_dir_final<R, 4><<<s.nvb, VBS, 0, st>>>(s, h, set_nd);
     else if (m <= 5) k_dir_final<R, 6><<<s.nvb, VBS, 0, st>>>(s, h, set_nd);
     else if (m <= 8) k_dir_final<R, 9><<<s.nvb, VBS, 0, st>>>(s, h, set_nd);
-    else k_dir_final<R, HQN_MAX_HISTORY + 1><<<s.nvb, VBS, 0, st>>>(s, h, set_nd);
+    else if (m <= kShortHist) k_dir_final<R, kShortHist + 1><<<s.nvb, VBS, 0, st>>>(s, h, set_nd);
+    else k_dir_final<R, 0><<<s.nvb, VBS, 0, st>>>(s, h, set_nd);
 }
 template <typename R> void launch_reset_history(const DevSim<R> &s, cudaStream_t st) {
     k_reset_history<R><<<1, 256, 0, st>>>(s);
@@ -1254,6 +1436,15 @@ template <typename R> void launch_to_caller(const V4<R> *src, const int *perm, i
 template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream_t st, int nblocks) {
     k_hist_row<R><<<nblocks, VBS, 0, st>>>(s, a);
 }
+template <typename R> void launch_long_hist(const DevSim<R> &s, int mode, int a0, cudaStream_t st, int nblocks) {
+    const int nch = (s.m + 1 + LH_CHUNK - 1) / LH_CHUNK;
+    const int gx = mode == LD_ROW ? nblocks : s.nvb;
+    k_ldots<R><<<dim3((unsigned)gx, (unsigned)nch), VBS, 0, st>>>(s, mode, a0);
+    k_lrec<R><<<mode == LD_ROW ? 1 : s.nsims, 256, lrec_smem(s.m), st>>>(s, mode, a0, gx);
+}
+template <typename R> cudaError_t long_hist_prepare(int m) {
+    return cudaFuncSetAttribute(k_lrec<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lrec_smem(m));
+}
 
 #define HQN_INST(R)                                                                  \
     template void launch_predict<R>(const DevSim<R> &, cudaStream_t);                \
@@ -1268,6 +1459,8 @@ template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream
     template void launch_commit<R>(const DevSim<R> &, cudaStream_t);                 \
     template void launch_pcg<R>(const DevSim<R> &, const V4<R> *, V4<R> *, int, cudaStream_t); \
     template void launch_hist_row<R>(const DevSim<R> &, int, cudaStream_t, int);       \
+    template void launch_long_hist<R>(const DevSim<R> &, int, int, cudaStream_t, int); \
+    template cudaError_t long_hist_prepare<R>(int);                                   \
     template void launch_positions<R>(const DevSim<R> &, const int *, int, int, V4<R> *, cudaStream_t); \
     template void launch_from_caller<R>(const double *, const double *, const int *, int, int, V4<R> *, cudaStream_t); \
     template void launch_to_caller<R>(const V4<R> *, const int *, int, int, int, double *, cudaStream_t);

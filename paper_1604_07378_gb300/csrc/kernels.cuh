@@ -10,6 +10,30 @@ namespace hqn {
 constexpr int VBS = 256;  // threads per block of the vertex kernels
 constexpr int TBS = 128;  // threads per block of the tet kernels
 
+// The scalars of Alg. 2's two loops for a window of m > kShortHist pairs
+// (L = m + 1 ring slots), one array of doubles(m) per simulation: the Gram
+// matrix s_a^T t_b by ring slots (row a), then rho, s_a^T grad and t_a^T r0
+// by ring slot, and the coefficients zeta and c = zeta - eta by age.
+struct LongHist {
+    int L;
+    double *gram, *rho, *sg, *tr0, *zeta, *coef;
+    static __host__ __device__ size_t doubles(int m) { return (size_t)(m + 1) * (m + 1) + 5 * (size_t)(m + 1); }
+    __host__ __device__ LongHist(double *base, int m) : L(m + 1) {
+        gram = base;
+        rho = gram + (size_t)L * L;
+        sg = rho + L;
+        tr0 = sg + L;
+        zeta = tr0 + L;
+        coef = zeta + L;
+    }
+};
+// Slot products of a long window, per block, over chunks of LH_CHUNK slots
+// (3 values per slot): LD_PUSH after a pair (s_w, t_w) is pushed:
+// s_a^T t_w, s_w^T t_a, s_a^T grad; LD_R0 after the solve: t_a^T r0;
+// LD_ROW for a caller-given pair a0: s_a0^T t_b and s_b^T grad.
+constexpr int LH_CHUNK = 16;
+enum { LD_PUSH = 0, LD_R0 = 1, LD_ROW = 2 };
+
 // One simulation of a batch, as the kernels see it (device-resident).  Every
 // block of a vertex or tet kernel belongs to exactly one simulation.
 template <typename R>
@@ -24,6 +48,7 @@ struct SimDesc {
     int tb0, ntb;               // its tet-kernel blocks [tb0, tb0 + ntb), ntb = ceil(T / TBS)
     long long ring0;            // its history ring: S / Tt entries [ring0, ring0 + (m + 1) n)
     Ctl *ctl;                   // its control block
+    double *lh;                 // m > kShortHist: the two loops' scalars, LongHist layout; else null
 };
 
 // Device view of a batch of simulations (a single simulation is a batch of
@@ -58,6 +83,7 @@ struct DevSim {
     const R *pcg_dinv;
     // per-block partial sums: part_x[k * (blocks of the kernel) + block]
     double *part_in, *part_el, *part_g, *part_v, *part_ls;
+    double *part_l;             // m > kShortHist: per-block partials of the slot products, 48 per chunk of 16 slots
     unsigned int *batch_ticket; // arrival counters of the simulations' last blocks (graph conditions)
 };
 
@@ -106,6 +132,14 @@ template <typename R> void launch_to_caller(const V4<R> *src, const int *perm, i
 // Caller-given history of simulation 0: Gram row a, rho_a and s_a^T grad
 // (run for a = 0..count-1).
 template <typename R> void launch_hist_row(const DevSim<R> &s, int a, cudaStream_t st, int nblocks);
+// Long windows (m > kShortHist): the slot products of `mode` (LD_*; a0 is
+// the caller's pair of LD_ROW) over the vertex blocks of the batch (or of
+// simulation 0's nblocks blocks for LD_ROW), then, one block per simulation,
+// their sums in block order, the Gram and scalar updates and the loop's
+// recursion on scalars (zeta after LD_PUSH / the last LD_ROW, c after LD_R0).
+template <typename R> void launch_long_hist(const DevSim<R> &s, int mode, int a0, cudaStream_t st, int nblocks);
+// Raises k_lrec's dynamic shared-memory limit for windows of m pairs.
+template <typename R> cudaError_t long_hist_prepare(int m);
 
 // ---- triangular solves (solve.cu)
 constexpr int SOLVE_MAX_SMEM = 200 * 1024;  // dynamic shared memory of one sweep block

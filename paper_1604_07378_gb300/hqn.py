@@ -30,7 +30,7 @@ STATIC_MAX_TETS, STATIC_MAX_VERTS = 65536, 262144
 NEOHOOKEAN, STVK, SPLINE_VL, COROTATED, POLY4 = 0, 1, 2, 3, 4
 STAGE_TET, STAGE_GATHER, STAGE_SOLVE, STAGE_LS_PASS, STAGE_TWO_LOOP = 0, 1, 2, 3, 4
 FP64_PLAIN, FP32_MIXED = 0, 1
-MAX_HISTORY, MAX_ITERS = 16, 512
+MAX_HISTORY, MAX_ITERS = 128, 512
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
