@@ -31,10 +31,11 @@ if ROOT not in sys.path:
 
 METRIC = "time-steps/s & tet grad-evals/s at 384k tets, FP32 vs FP64 GPU, pos err ≤1e-4"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one cube40 FP32
-# solve (default shapes), summed over its 20 sweep launches in an ncu capture
-# of this script's --no-graph run; None until captured on the current sweep
-# kernels.
-SOLVE_TRAFFIC_BYTES = None
+# solve (default shapes: 7 forward levels, the dense top block, 7 backward
+# levels), summed over its 15 launches in ncu captures of three launches each
+# (232.79 MB read, 0.004 MB written); None when a sweep kernel changes until
+# re-captured.
+SOLVE_TRAFFIC_BYTES = 232_794_112
 UNIT = "time-steps/s"
 WORKLOAD = "cube40_neohookean"
 # FP32 floating-point operations of the tet pass per tet (2 x FFMA + FADD +
@@ -332,11 +333,13 @@ def run_ours(args, rank, world, dist):
     if dominant == "solve":
         bytes_launch = 2 * info["factor_nnz"] * 4 + 2 * 12 * info["n_free"]
         achieved = bytes_launch / (stage_ms["solve"] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": "A0^-1 solve: forward + backward sweeps (k_fwd, k_bwd), one solve",
+        roof = {"bound": "hbm",
+                "kernel": "A0^-1 solve: forward sweep levels, dense top block, backward sweep levels "
+                          "(k_fwd, k_dense, k_bwd), one solve",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
                 # the capture holds for the default tree and schedule only
-                "traffic": SOLVE_TRAFFIC_BYTES if args.leaf_size == 0 else None,
+                "traffic": SOLVE_TRAFFIC_BYTES if args.leaf_size == 0 and tuned is None else None,
                 "algorithmic_bytes_per_launch": bytes_launch}
     else:
         # the tet pass (energy + corner gradients): idx 16 + Dm^-1 36 + V 4 B
