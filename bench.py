@@ -707,6 +707,10 @@ def run_batched(args, stream, rank=0, world=1, dist=None):
         ms = max_over_ranks(e0.elapsed_time(e1), dist, torch.device("cuda", torch.cuda.current_device())) / steps
         info = b.info()
         solve_ms = b.time_stage(hqn.STAGE_SOLVE, 10)
+        # the step's stages over the whole batch, one launch each (CUDA events)
+        stages = {name: b.time_stage(st, 10) for name, st in
+                  (("tet", hqn.STAGE_TET), ("gather", hqn.STAGE_GATHER), ("solve", hqn.STAGE_SOLVE),
+                   ("two_loop_with_solve", hqn.STAGE_TWO_LOOP))}
         b.close()
         # tet evaluations per batch step: every simulation's start-of-step pass
         # and line-search passes (ls_passes_total is summed over the batch;
@@ -719,7 +723,10 @@ def run_batched(args, stream, rank=0, world=1, dist=None):
                     "ls_trials_per_iter": tot["trials_total"] / max(tot["iters_total"], 1),
                     "create_s": create_s, "device_bytes": info["device_bytes"],
                     "solve_ms": solve_ms, "solve_hbm_frac_of_measured": solve_bytes / (solve_ms * 1e-3) / 1e9
-                    / peaks["hbm_gbs"]}
+                    / peaks["hbm_gbs"], "stage_ms_per_launch": stages,
+                    # simulation-iterations that ran, of sims x iterations x steps (the rest
+                    # ended early and idled in the batch's launches)
+                    "sim_iterations_active_fraction": tot["iters_total"] / (len(ws) * ws[0].iters * steps)}
     return out
 
 
