@@ -49,7 +49,10 @@ taken by the CUDA path, written separately):
 Parity pins: see tests/test_oracle_pins.py (finite differences, rest state,
 invariances, invariant-form materials, closed-form stiffness, SPD and residual
 of A0, secant condition, m = 0 reduction, the projective-dynamics identity,
-centre-of-mass motion, convergence to a Newton minimiser).
+centre-of-mass motion, convergence to a Newton minimiser).  One branch has
+no pin: the non-descent reset of solve_step (parity unpinned).  With every
+kept pair's rho > 0 the L-BFGS matrix is positive definite, so the branch is
+a safeguard against rounding that no input tried has reached.
 """
 from __future__ import annotations
 
