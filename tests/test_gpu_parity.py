@@ -513,3 +513,33 @@ def test_energy_gradient_device_pointers(prec):
             np.testing.assert_array_equal(grad_d, grad_h)
     assert abs(g_d - O.objective(P, x, y)) <= (1e-11 if prec == FP64 else 2e-6) * abs(O.objective(P, x, y))
     assert rel(grad_d, O.gradient(P, x, y)) <= (1e-11 if prec == FP64 else 1e-5)
+
+
+def _inverted_at(w, x):
+    X, T = w.rest_pos, w.tets
+    Ds = np.stack([x[T[:, k]] - x[T[:, 0]] for k in (1, 2, 3)], axis=2)
+    Dm = np.stack([X[T[:, k]] - X[T[:, 0]] for k in (1, 2, 3)], axis=2)
+    return int((np.linalg.det(Ds) * np.linalg.det(Dm) < 0).sum())
+
+
+# an 8^3 lattice whose every free vertex has its own velocity in [-1.5, 1.5]^3
+# m/s: about a third of its 3,072 tets are inverted at the predictor y, and the
+# line search backtracks (Neo-Hookean ~10 times per iteration, StVK in the
+# first iterations)
+TANGLED = [W.lattice_workload((8, 8, 8), W.Material(kind, 5e5, 0.4), clamp_axis=2, seed=31, v_range=1.5,
+                              v_mode="iid", name=f"tangled8_{W.MATERIAL_NAMES[kind]}")
+           for kind in (W.NEOHOOKEAN, W.STVK)]
+
+
+@pytest.mark.parametrize("w", TANGLED, ids=[w.name for w in TANGLED])
+@pytest.mark.parametrize("prec", [FP64, FP32], ids=["fp64", "fp32"])
+def test_tangled_lattice_step_parity(w, prec):
+    """Inverted elements at scale: a whole step of a lattice tangled by
+    per-vertex velocities (hundreds of inverted tets at y, rejected trials)
+    against the oracle; FP64 with the oracle's trial counts."""
+    P = problem_for(w)
+    assert _inverted_at(w, O.predictor(P, w.q_cur, w.q_prev)) > 500
+    stats, st, qc, x_ref = _step_parity(w, prec, 1, 1e-9 if prec == FP64 else 1e-4)
+    assert sum(st.trials) > w.iters
+    if prec == FP64:
+        assert stats["trials"] == st.trials
