@@ -467,6 +467,8 @@ uint64_t hqn_mesh_key(const hqn_mesh *mesh);
  *     solve_prefetch=<n> [solve_leaf_kb=<n>] [solve_leaf_threads=<n>]
  *     [solve_dense_top=<n>] [solve_dense_prefetch=<0|1>] [ls_batch=<n>]
  *     [other key=value pairs, ignored]
+ * (leaf_size=0, solve_dense_top=0 and the solve_* zeros keep the library's
+ * size-dependent defaults.)
  * Returns 1 and writes the entry's values into *params on a hit, 0 when the
  * file or the entry does not exist (params unchanged), HQN_ERR_ARG for a
  * malformed file or argument. */

@@ -15,7 +15,9 @@ current GPU, on the mesh itself:
    best of three means);
 2. the three fastest shapes of each handle, and the library's defaults,
    are timed as whole time steps (one CUDA graph each);
-3. the fastest is written to the cache file as one line, keyed by the
+3. the line search's trials per pass (ls_batch, a creation parameter) is
+   timed as whole steps with the fastest shapes, one handle per value;
+4. the fastest is written to the cache file as one line, keyed by the
    device name, the precision and the mesh's hash (hqn_mesh_key).
 
 sim_create reads the cache when hqn_params.tune_cache names it, so a tuned
@@ -36,6 +38,7 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_c
 
 LEAF_SIZES = (64, 128)
 DENSE_TOPS = (-1, 2, 3)
+LS_BATCHES = (4, 8, 16)  # trials per line-search pass (the library's default is 8)
 SHAPE_KEYS = ("solve_threads", "solve_item_kb", "solve_items", "solve_prefetch", "solve_leaf_kb",
               "solve_leaf_threads", "solve_dense_prefetch")
 # the re-plannable sweep shapes (hqn_params.solve_*; 0 = default)
@@ -63,6 +66,8 @@ def cache_line(device: str, precision: int, key: int, choice: dict, **extra) -> 
     fields = [f"device={device.replace(' ', '_')}", f"precision={int(precision)}", f"key={key:016x}",
               f"leaf_size={int(choice['leaf_size'])}", f"solve_dense_top={int(choice.get('solve_dense_top', 0))}"]
     fields += [f"{k}={int(choice.get(k, 0))}" for k in SHAPE_KEYS]
+    if choice.get("ls_batch"):
+        fields.append(f"ls_batch={int(choice['ls_batch'])}")
     fields += [f"{k}={v:.6g}" if isinstance(v, float) else f"{k}={v}" for k, v in extra.items()]
     return "hqn-tune 1 " + " ".join(fields)
 
@@ -94,9 +99,13 @@ def _step_ms(sim, w, steps):
 
 
 def tune_workload(w, precision=hqn.FP32_MIXED, stream=None, leaf_sizes=LEAF_SIZES, dense_tops=DENSE_TOPS,
-                  grid=SHAPE_GRID, reps=20, steps=10, cache: str | None = DEFAULT_CACHE) -> dict:
+                  grid=SHAPE_GRID, reps=20, steps=10, cache: str | None = DEFAULT_CACHE,
+                  ls_batches=LS_BATCHES, min_gain=0.01) -> dict:
     """Times the shapes on workload `w` (a workloads.Workload) and returns
-    the choice with its measurements; appends it to `cache` unless None."""
+    the choice with its measurements; appends it to `cache` unless None.
+    A candidate replaces the current choice only when its step is faster by
+    more than `min_gain` (a fraction: step times vary by about half a per
+    cent from run to run)."""
     results = []
     for leaf in leaf_sizes:
         for top in dense_tops:
@@ -132,12 +141,29 @@ def tune_workload(w, precision=hqn.FP32_MIXED, stream=None, leaf_sizes=LEAF_SIZE
         default = {"leaf_size": 0, "solve_dense_top": 0, **{k: 0 for k in SHAPE_KEYS},
                    "solve_ms": min(sim.time_stage(hqn.STAGE_SOLVE, reps) for _ in range(3)),
                    "step_ms": _step_ms(sim, w, steps), "levels": info["n_levels"]}
-    choice = min(results + [default], key=lambda r: r["step_ms"])
+    best = min(results, key=lambda r: r["step_ms"]) if results else default
+    choice = best if best["step_ms"] < default["step_ms"] * (1.0 - min_gain) else default
+    tuned = choice is not default
+    # trials per line-search pass, with the chosen shapes (a new handle each)
+    base_lb = hqn.default_params().ls_batch
+    shapes = {k: choice[k] for k in SHAPE_KEYS if choice.get(k)}
+    lb_timed = []
+    for lb in ls_batches:
+        if lb == base_lb:
+            continue
+        with hqn.Sim.from_workload(w, precision=precision, stream=stream, leaf_size=choice["leaf_size"],
+                                   solve_dense_top=choice["solve_dense_top"], ls_batch=lb, **shapes) as sim:
+            lb_timed.append((_step_ms(sim, w, steps), lb))
+    if lb_timed and min(lb_timed)[0] < choice["step_ms"] * (1.0 - min_gain):
+        t, lb = min(lb_timed)
+        choice = dict(choice, ls_batch=lb, step_ms=t)
+        tuned = True
     out = dict(choice)
+    out["ls_batch_step_ms"] = {str(lb): t for t, lb in lb_timed}
     out["default_step_ms"] = default["step_ms"]
     out["default_solve_ms"] = default["solve_ms"]
     out["candidates"] = results
-    if cache and choice is not default:
+    if cache and tuned:
         key = mesh_key(w.rest_pos, w.tets, w.clamped)
         line = cache_line(_device_name(), precision, key, choice, step_ms=float(choice["step_ms"]),
                           solve_ms=float(choice["solve_ms"]), workload=getattr(w, "name", "mesh"))

@@ -90,7 +90,7 @@ int hqn_tune_lookup(const char *path, const char *device, uint64_t key, int32_t 
             if (k == "device") l_dev = v;
             else if (k == "key") l_key = v;
             else if (k == "precision") ok = parse_int(v, 0, 1, &l_prec);
-            else if (k == "leaf_size") ok = have[0] = parse_int(v, 8, 4096, &p.leaf_size);
+            else if (k == "leaf_size") ok = have[0] = parse_int(v, 0, 4096, &p.leaf_size);
             else if (k == "solve_threads") ok = have[1] = parse_int(v, 0, 512, &p.solve_threads);
             else if (k == "solve_item_kb") ok = have[2] = parse_int(v, 0, 160, &p.solve_item_kb);
             else if (k == "solve_items") ok = have[3] = parse_int(v, 0, 4096, &p.solve_items);

@@ -69,15 +69,18 @@ def test_tuning_writes_a_cache_that_sim_create_applies(tmp_path):
     key = autotune.mesh_key(w.rest_pos, w.tets, w.clamped)
     dev = autotune._device_name()
     hit = autotune.lookup(cache, dev, key, FP32)
-    if res["leaf_size"] == 0:  # the defaults won: nothing written
+    if res["leaf_size"] == 0 and "ls_batch" not in res:  # the defaults won: nothing written
         assert hit is None
         return
     assert hit["leaf_size"] == res["leaf_size"] and hit["solve_items"] == res["solve_items"]
     assert hit["solve_dense_top"] == res["solve_dense_top"]
+    assert hit["ls_batch"] == res.get("ls_batch", 8)
     x_ref, _ = O.solve_step(problem_for(w), w.q_cur, w.q_prev, iters=w.iters, m=w.history)
     with hqn.Sim.from_workload(w, precision=FP32, tune_cache=cache) as sim:
         info = sim.info()
-        assert info["solve_items"] == res["solve_items"] and info["solve_item_kb"] == res["solve_item_kb"]
+        # (zeros in the entry keep the library's defaults: 400 items of 64 KB)
+        assert info["solve_items"] == (res["solve_items"] or 400)
+        assert info["solve_item_kb"] == (res["solve_item_kb"] or 64)
         sim.set_state(w.q_cur, w.q_prev)
         assert sim.step(1) >= 0
         assert rel(sim.get_state()[0], x_ref) <= 1e-4

@@ -81,3 +81,13 @@ def test_committed_cache_parses(at):
     """The cache shipped with the package is well formed."""
     if os.path.exists(at.DEFAULT_CACHE):
         at.lookup(at.DEFAULT_CACHE, DEV, 0, 1)
+
+
+def test_entry_with_library_defaults_and_a_tuned_ls_batch(at, tmp_path):
+    """An entry that keeps the library's size-dependent defaults (zeros) and
+    tunes only the line search's trials per pass."""
+    path = str(tmp_path / "cache.txt")
+    choice = {**_choice(0, 0, 0, 0, 0), "ls_batch": 4}
+    with open(path, "w") as f:
+        f.write(at.cache_line(DEV, 1, 77, choice, step_ms=1.0) + "\n")
+    assert at.lookup(path, DEV, 77, 1) == {**_choice(0, 0, 0, 0, 0), "ls_batch": 4}
