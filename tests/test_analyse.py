@@ -85,7 +85,10 @@ def test_rejects_degenerate_and_bad_input(hqn, lat12):
     with pytest.raises(hqn.HQNError) as e:
         hqn.analyse_workload(w, precision=7)
     assert e.value.code == hqn.HQN_ERR_ARG
-    for kw in (dict(ls_batch=3), dict(history_m=hqn.MAX_HISTORY + 1), dict(h=0.0), dict(gamma=1.0)):
+    assert hqn.MAX_HISTORY == 128  # the paper's convergence study runs m = 100
+    hqn.analyse_workload(w, history_m=hqn.MAX_HISTORY)
+    for kw in (dict(ls_batch=3), dict(history_m=hqn.MAX_HISTORY + 1), dict(history_m=-1), dict(h=0.0),
+               dict(gamma=1.0)):
         with pytest.raises(hqn.HQNError) as e:
             hqn.analyse_workload(w, **kw)
         assert e.value.code == hqn.HQN_ERR_ARG, kw
